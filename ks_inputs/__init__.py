@@ -1,0 +1,198 @@
+"""Seeded synthetic inputs shared by the CUDA path, the CPU oracle and the bench.
+
+This module holds no arithmetic of the method: it only draws random numbers
+(a counter-based splitmix64 stream), places pseudo-atoms and fills the initial
+orbital block X0.  Everything that depends on the discretisation (the mass
+matrix, M-orthonormalisation, potentials) lives on each side separately.
+
+Workload recipes (the synthetic stand-ins for the paper's molecules, which
+need geometries and pseudopotentials that are not available):
+
+  * ``c1``  cube side 10 bohr, 24^3 interior Q1 nodes, 2 atoms (Z=4) drawn
+            uniformly in [L/4, 3L/4]^3 with a 1.5 bohr minimum separation,
+            p=4 doubly occupied orbitals, Slater exchange only, Cayley step.
+  * ``c2``  cube side 20 bohr, 64^3 nodes, 32 atoms on a 4x4x2 simple lattice
+            jittered by U(-0.3, 0.3) bohr, p=64, Slater + PZ81, QR step.
+  * ``c3``  cube side 40 bohr, 128^3 nodes, 256 atoms on 8x8x4, p=512.
+  * ``c4``  256 jobs, N = round(exp(U(ln 20, ln 48))), spacing 0.4 bohr,
+            2..16 atoms placed uniformly in [1.5, L-1.5]^3, p = 2 * atoms.
+
+The grid has N interior nodes per edge and spacing h = L/(N+1); interior
+node (ix, iy, iz) sits at ((ix+1)h, (iy+1)h, (iz+1)h) and has flat index
+k = (iz*N + iy)*N + ix.  X is stored row-major n x p (orbital index fastest).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+GOLDEN_GAMMA = 0x9E3779B97F4A7C15
+MASK64 = (1 << 64) - 1
+
+# Stream ids inside one (seed, job) key.
+STREAM_ATOMS = 0
+STREAM_X0 = 1
+STREAM_JOBSIZE = 2
+STREAM_ARRIVALS = 3
+
+
+def _mix64(z: int) -> int:
+    """splitmix64 output function (Steele, Lea, Flood 2014)."""
+    z &= MASK64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & MASK64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & MASK64
+    return z ^ (z >> 31)
+
+
+def stream_key(seed: int, job: int, stream: int) -> int:
+    """Initial splitmix64 state for one named stream of one job."""
+    return _mix64((seed * 0x100000001B3) ^ (job * 0x10001) ^ (stream << 56))
+
+
+class SplitMix64:
+    """Counter-based splitmix64: the i-th output (i = 0, 1, ...) is
+    mix64(key + (i+1)*GOLDEN_GAMMA)."""
+
+    def __init__(self, key: int):
+        self.key = key & MASK64
+        self.count = 0
+
+    def next_u64(self) -> int:
+        self.count += 1
+        return _mix64(self.key + self.count * GOLDEN_GAMMA)
+
+    def uniform(self) -> float:
+        """Double in [0, 1): top 53 bits times 2^-53."""
+        return (self.next_u64() >> 11) * (1.0 / 9007199254740992.0)
+
+
+def uniform_block(key: int, count: int, start: int = 0) -> np.ndarray:
+    """Vectorised outputs start..start+count-1 of the stream `key` as doubles
+    in [0, 1)."""
+    idx = np.arange(start + 1, start + count + 1, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(key) + idx * np.uint64(GOLDEN_GAMMA)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+def initial_orbitals(seed: int, job: int, n: int, p: int) -> np.ndarray:
+    """X0 with entries U(-1, 1), filled in row-major order (node-major,
+    orbital fastest).  Not yet M-orthonormal."""
+    u = uniform_block(stream_key(seed, job, STREAM_X0), n * p)
+    return (2.0 * u - 1.0).reshape(n, p)
+
+
+@dataclass
+class System:
+    """One synthetic Kohn-Sham system (geometry and sizes only)."""
+    N: int                      # interior nodes per edge
+    L: float                    # cube side (bohr)
+    atoms: np.ndarray           # (natoms, 3) positions in bohr
+    Z: np.ndarray               # (natoms,) valence charges
+    p: int                      # number of orbitals
+    xc: int = 0                 # 0 = Slater exchange, 1 = Slater + PZ81
+    rc: float = 0.5             # erf smearing radius of the pseudo-atom
+    occ: float = 2.0            # occupation per orbital
+    retraction: str = "qr"      # "qr" or "cayley"
+    seed: int = 0
+    job: int = 0
+    name: str = ""
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def h(self) -> float:
+        return self.L / (self.N + 1)
+
+    @property
+    def n(self) -> int:
+        return self.N ** 3
+
+    def x0(self) -> np.ndarray:
+        return initial_orbitals(self.seed, self.job, self.n, self.p)
+
+
+def _random_atoms(rng: SplitMix64, natoms: int, lo: float, hi: float,
+                  dmin: float, relaxed: float, tries: int = 10_000) -> np.ndarray:
+    pos: list[tuple[float, float, float]] = []
+    for _ in range(natoms):
+        limit = dmin
+        t = 0
+        while True:
+            cand = tuple(lo + (hi - lo) * rng.uniform() for _ in range(3))
+            if all(math.dist(cand, q) >= limit for q in pos):
+                pos.append(cand)
+                break
+            t += 1
+            if t == tries:
+                limit = relaxed
+    return np.array(pos, dtype=np.float64).reshape(natoms, 3)
+
+
+def _lattice_atoms(rng: SplitMix64, L: float, nx: int, ny: int, nz: int,
+                   jitter: float) -> np.ndarray:
+    pos = []
+    for i in range(nx):
+        for j in range(ny):
+            for l in range(nz):
+                site = ((i + 0.5) * L / nx, (j + 0.5) * L / ny, (l + 0.5) * L / nz)
+                pos.append(tuple(s + jitter * (2.0 * rng.uniform() - 1.0) for s in site))
+    return np.array(pos, dtype=np.float64)
+
+
+def config_c1(seed: int = 1000) -> System:
+    L, N = 10.0, 24
+    rng = SplitMix64(stream_key(seed, 0, STREAM_ATOMS))
+    atoms = _random_atoms(rng, 2, L / 4, 3 * L / 4, 1.5, 1.5)
+    return System(N=N, L=L, atoms=atoms, Z=np.full(2, 4.0), p=4, xc=0,
+                  retraction="cayley", seed=seed, name="c1: 24^3 grid, 2 atoms, p=4, FP64 Cayley")
+
+
+def config_c2(seed: int = 1001) -> System:
+    L, N = 20.0, 64
+    rng = SplitMix64(stream_key(seed, 0, STREAM_ATOMS))
+    atoms = _lattice_atoms(rng, L, 4, 4, 2, 0.3)
+    return System(N=N, L=L, atoms=atoms, Z=np.full(32, 4.0), p=64, xc=1,
+                  retraction="qr", seed=seed, name="c2: 64^3 grid, 32 atoms, p=64, QR")
+
+
+def config_c3(seed: int = 1002) -> System:
+    L, N = 40.0, 128
+    rng = SplitMix64(stream_key(seed, 0, STREAM_ATOMS))
+    atoms = _lattice_atoms(rng, L, 8, 8, 4, 0.3)
+    return System(N=N, L=L, atoms=atoms, Z=np.full(256, 4.0), p=512, xc=1,
+                  retraction="qr", seed=seed, name="c3: 128^3 grid, 256 atoms, p=512, QR")
+
+
+def config_c4_jobs(seed: int = 1003, njobs: int = 256) -> list[System]:
+    jobs = []
+    for j in range(njobs):
+        rng = SplitMix64(stream_key(seed, j, STREAM_JOBSIZE))
+        N = int(round(math.exp(math.log(20) + (math.log(48) - math.log(20)) * rng.uniform())))
+        natoms = 2 + int(15 * rng.uniform())          # U{2..16}
+        L = 0.4 * (N + 1)
+        arng = SplitMix64(stream_key(seed, j, STREAM_ATOMS))
+        atoms = _random_atoms(arng, natoms, 1.5, L - 1.5, 1.2, 0.8)
+        jobs.append(System(N=N, L=L, atoms=atoms, Z=np.full(natoms, 4.0), p=2 * natoms,
+                           xc=1, retraction="qr", seed=seed, job=j,
+                           name=f"c4 job {j}: {N}^3, {natoms} atoms"))
+    return jobs
+
+
+def small_system(N: int = 6, L: float = 6.0, natoms: int = 1, p: int = 2,
+                 xc: int = 1, seed: int = 7, retraction: str = "qr",
+                 Z: float | None = None) -> System:
+    """A tiny system for brute-force checks (atoms placed like c4)."""
+    rng = SplitMix64(stream_key(seed, 0, STREAM_ATOMS))
+    lo, hi = 0.3 * L, 0.7 * L
+    atoms = _random_atoms(rng, natoms, lo, hi, 1.2, 0.8)
+    zval = float(2 * p) / natoms if Z is None else Z
+    return System(N=N, L=L, atoms=atoms, Z=np.full(natoms, zval), p=p, xc=xc,
+                  retraction=retraction, seed=seed, name=f"small {N}^3 p={p}")
+
+
+CONFIGS = {"c1": config_c1, "c2": config_c2, "c3": config_c3}
