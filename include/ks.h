@@ -1,0 +1,180 @@
+/*
+ * ks.h -- C ABI of the GB300 library for direct Kohn-Sham energy
+ * minimisation on the generalised Stiefel manifold X^T M X = I.
+ *
+ * Method: Zhang, Zhu, Wen, Zhou, "Gradient type optimization methods for
+ * electronic structure calculations".  The problem is Eq. opt (minimise the
+ * discretised KS energy subject to orthonormal orbitals, Sec. 3), with the
+ * mass-matrix constraint of the finite-element model (Eq. disOFinf, handled
+ * by the substitution y = B^{1/2} c of Eq. OFDFT-y).  The iteration is
+ * Alg. ConOptM: projected gradient (Eq. def-nablaE), a Cholesky-QR
+ * (Eq. QR, Alg. ChQR) or Cayley (Eq. WY3) retraction, Barzilai-Borwein steps
+ * (Eq. bb-1) and the nonmonotone Armijo search (Eq. NMLS-Armijo).
+ *
+ * Discretisation: Q1 finite elements on a cube of side L with N interior
+ * nodes per edge (h = L/(N+1)) and zero Dirichlet boundary values; stiffness
+ * K and consistent mass M are the 27-point trilinear operators.  Orbitals
+ * are stored row-major n x p (n = N^3, node index k = (iz*N + iy)*N + ix,
+ * orbital index fastest), FP64, densely packed (leading dimension p).
+ *
+ * Conventions for every call:
+ *   - the return value is a ks_status; no call aborts the process;
+ *   - pointers documented as DEVICE point to memory of the current CUDA
+ *     device that the caller owns; the library never frees them;
+ *   - work is issued on the problem's stream; calls that return host values
+ *     synchronise that stream before returning;
+ *   - a problem object is not thread-safe and must be used from one host
+ *     thread at a time;
+ *   - on failure the caller's output buffers are left unchanged except where
+ *     a call says otherwise, and ks_last_error_string() describes the error.
+ */
+#ifndef KS_H
+#define KS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  KS_OK = 0,
+  KS_EINVAL = 1,      /* invalid argument */
+  KS_ENOMEM = 2,      /* device allocation failed */
+  KS_ECUDA = 3,       /* CUDA runtime error */
+  KS_ENOCONV = 4,     /* Hartree CG or the outer iteration hit its limit */
+  KS_ENOTPD = 5,      /* Cholesky of a Gram matrix met a non-positive pivot */
+  KS_ESINGULAR = 6,   /* the Cayley system I + tau/2 V^T U is singular */
+  KS_ENAN = 7,        /* a non-finite value appeared */
+  KS_ETIMEOUT = 8     /* a bounded device-side wait gave up */
+} ks_status;
+
+/* Opaque problem handle; owns all device workspace of one system. */
+typedef struct ks_problem ks_problem;
+
+enum { KS_XC_SLATER = 0, KS_XC_SLATER_PZ81 = 1 };
+enum { KS_FP64 = 0, KS_MIXED = 1 };
+enum { KS_QR = 0, KS_CAYLEY = 1 };
+
+/* One discretised KS system (Eq. EKS discretised, Sec. 2.3). */
+typedef struct {
+  int N;              /* interior nodes per edge (>= 2) */
+  double L;           /* cube side in bohr */
+  int natoms;         /* number of pseudo-atoms (>= 0) */
+  const double *R;    /* HOST, 3*natoms positions (x, y, z) in bohr; copied */
+  const double *Z;    /* HOST, natoms valence charges; copied */
+  double rc;          /* erf radius of -Z erf(r/rc)/r (0.5) */
+  int p;              /* number of orbitals (>= 1) */
+  double occ;         /* occupation per orbital (2) */
+  int xc;             /* KS_XC_SLATER or KS_XC_SLATER_PZ81 */
+  double cg_tol;      /* Hartree CG: ||r||_2 <= cg_tol ||b||_2 (1e-10) */
+  int cg_maxit;       /* Hartree CG iteration limit */
+  int precision;      /* KS_FP64 (KS_MIXED is reserved) */
+  void *stream;       /* cudaStream_t to issue work on; NULL = library-owned */
+} ks_problem_desc;
+
+/* Parameters of Alg. ConOptM (the paper fixes none of their values). */
+typedef struct {
+  int retraction;     /* KS_QR or KS_CAYLEY */
+  double gtol;        /* stop when ||D||_M <= gtol (1e-6) */
+  int maxit;          /* iteration limit (300) */
+  double tau0;        /* first step and reset value (1e-3) */
+  double rho1;        /* Armijo constant, < 1/2 (1e-4) */
+  double delta;       /* backtracking factor (0.1) */
+  double eta;         /* nonmonotone weight (0.85) */
+  double tau_min;     /* BB clamp (1e-10) */
+  double tau_max;     /* BB clamp (1e10) */
+  int max_backtrack;  /* backtracks per iteration before accepting (10) */
+  double ortho_tol;   /* re-orthonormalise when ||X^T M X - I||_F > ortho_tol (1e-12) */
+  int ortho_every;    /* QR path: check ||X^T M X - I|| every this many iterations (20) */
+} ks_opts;
+
+typedef struct {
+  double E;           /* total energy (hartree) at the returned X */
+  double gradnorm;    /* ||D||_M at the returned X */
+  double ortho_err;   /* ||X^T M X - I||_F at the returned X */
+  double E_parts[5];  /* kinetic, external, Hartree, exchange-correlation, ion-ion */
+  int iters;          /* outer iterations taken */
+  int cg_iters_total; /* Hartree CG iterations over the whole run */
+  int backtracks;     /* total backtracking steps */
+  int status;         /* ks_status of the run (KS_ENOCONV when maxit was hit) */
+  double seconds;     /* wall time of the call */
+} ks_result;
+
+/* Defaults listed in ks_opts. */
+void ks_opts_default(ks_opts *opts);
+
+/* Create a problem: copies the geometry, allocates all device workspace,
+ * tabulates the external potential (sum of -Z erf(r/rc)/r) and the ion-ion
+ * energy (Eq. EKS, E_II).  *out is NULL on failure. */
+ks_status ks_problem_create(const ks_problem_desc *desc, ks_problem **out);
+ks_status ks_problem_destroy(ks_problem *prob);
+
+/* Bytes of device memory ks_problem_create would allocate (for admission);
+ * 0 for an invalid description. */
+size_t ks_problem_bytes(const ks_problem_desc *desc);
+
+/* Energy and derivative at X (Eq. EKS discretised; E_X = dE/dX, the
+ * paper's H(X)X of Eq. "partial deriv" with the occupation factor):
+ *   X   DEVICE n x p (need not be M-orthonormal for E and EX)
+ *   E   HOST, receives the total energy
+ *   EX  DEVICE n x p or NULL, receives dE/dX
+ *   D   DEVICE n x p or NULL, receives the projected gradient
+ *       D = M^{-1} E_X - X (E_X^T X) (Eq. def-nablaE in the M metric)
+ *   gradnorm  HOST or NULL, receives ||D||_M = sqrt(tr(D^T M D))
+ * The Hartree solve is warm-started from the previous call's potential. */
+ks_status ks_energy_grad(ks_problem *prob, const double *X, double *E,
+                         double *EX, double *D, double *gradnorm);
+
+/* Energy parts of the last evaluation: kinetic, external, Hartree,
+ * exchange-correlation, ion-ion (HOST array of 5). */
+ks_status ks_energy_parts(ks_problem *prob, double parts[5]);
+
+/* One retraction step from an M-orthonormal X along -D (Eqs. QR or WY3):
+ *   kind  KS_QR or KS_CAYLEY
+ *   X     DEVICE n x p, M-orthonormal
+ *   EX    DEVICE n x p, dE/dX at X (e.g. from ks_energy_grad)
+ *   tau   step size
+ *   Xout  DEVICE n x p, must not alias X or EX
+ * Returns KS_ENOTPD / KS_ESINGULAR when the small system cannot be solved. */
+ks_status ks_retract(ks_problem *prob, int kind, const double *X, const double *EX,
+                     double tau, double *Xout);
+
+/* X <- X L^{-T} with X^T M X = L L^T, applied twice (Cholesky QR in the M
+ * inner product, Alg. ChQR).  X is DEVICE n x p, updated in place. */
+ks_status ks_orthonormalize(ks_problem *prob, double *X);
+
+/* Alg. ConOptM from X_inout (DEVICE n x p, any full-rank block; it is
+ * M-orthonormalised first).  On return X_inout holds the last accepted
+ * iterate, also when the status is KS_ENOCONV. */
+ks_status ks_minimize(ks_problem *prob, double *X_inout, const ks_opts *opts,
+                      ks_result *result);
+
+/* Same as ks_minimize with X_inout in HOST memory: the initial block is
+ * copied to the device and the result copied back inside the call. */
+ks_status ks_minimize_host(ks_problem *prob, double *X_inout_host, const ks_opts *opts,
+                           ks_result *result);
+
+/* Kernels this library has launched in this process so far. */
+unsigned long long ks_kernel_launches(void);
+
+/* Optional timing of the library's kernels by class with CUDA events on the
+ * launching stream.  ks_profile_start() clears the totals and switches
+ * timing on; ks_profile_stop() waits for the recorded events, switches
+ * timing off and returns per class the summed milliseconds and the number
+ * of timed launch groups (HOST arrays of KS_PROF_CLASSES, either may be
+ * NULL).  Classes, in order: density, hartree_cg, potential, hamiltonian,
+ * mass, mass_inverse, gram, combine, small_factor, reduce, setup, other. */
+#define KS_PROF_CLASSES 12
+ks_status ks_profile_start(void);
+ks_status ks_profile_stop(double ms[KS_PROF_CLASSES], long long counts[KS_PROF_CLASSES]);
+const char *ks_profile_class_name(int cls);
+
+/* Text of the last error on the calling thread ("" if none). */
+const char *ks_last_error_string(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KS_H */

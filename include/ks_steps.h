@@ -1,0 +1,71 @@
+/*
+ * ks_steps.h -- one C entry point per step of the iteration, for callers that
+ * compose their own driver and for step-by-step verification.  Each call
+ * runs on the problem's stream with the problem's sizes (n = N^3 nodes, p
+ * orbitals), synchronises it before returning, and follows the conventions
+ * of ks.h (ks_status return value; DEVICE pointers are owned by the caller;
+ * outputs must not alias inputs).
+ */
+#ifndef KS_STEPS_H
+#define KS_STEPS_H
+
+#include "ks.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* External potential sum_a -Z_a erf(|r - R_a|/rc)/|r - R_a| on the nodes
+ * (E_ext of Eq. EKS).  vext: DEVICE n. */
+ks_status ks_step_vext(ks_problem *prob, double *vext);
+
+/* Ion-ion energy E_II of Eq. EKS (HOST scalar). */
+ks_status ks_step_eii(ks_problem *prob, double *eii);
+
+/* rho_k = f sum_i X_ki^2 (Sec. 2.3, rho(X) = diag(X X^T)).
+ * X: DEVICE n x p; rho: DEVICE n. */
+ks_status ks_step_density(ks_problem *prob, const double *X, double *rho);
+
+/* Hartree potential by conjugate gradients on K vH = 4 pi h^3 rho (the
+ * discrete L^+ rho of Sec. 2.3), stopping at ||r|| <= cg_tol ||b||.
+ *   rho    DEVICE n
+ *   vH     DEVICE n, in/out: the start vector when warm != 0, else ignored
+ *   resid  DEVICE n or NULL, receives r = 4 pi h^3 rho - K vH
+ *   iters  HOST or NULL, receives the iteration count
+ * Returns KS_ENOCONV when cg_maxit is reached. */
+ks_status ks_step_hartree(ks_problem *prob, const double *rho, double *vH, int warm,
+                          double *resid, int *iters);
+
+/* V_eff = Vext + vH + v_xc(rho) and the energies (HOST, 3): h^3 sum Vext rho,
+ * 1/2 h^3 sum vH rho + vH.resid/(8 pi), h^3 sum rho eps_xc(rho).  resid may
+ * be NULL (treated as zero).  rho, vH, veff: DEVICE n. */
+ks_status ks_step_potential(ks_problem *prob, const double *rho, const double *vH,
+                            const double *resid, double *veff, double energies[3]);
+
+/* E_X = f K X + 2 f h^3 Diag(veff) X, MX = M X (DEVICE n x p or NULL) and
+ * the kinetic energy (f/2) tr(X^T K X) (HOST). */
+ks_status ks_step_hamiltonian(ks_problem *prob, const double *X, const double *veff,
+                              double *EX, double *MX, double *kinetic);
+
+/* MX = M X (consistent Q1 mass).  DEVICE n x p. */
+ks_status ks_step_mass(ks_problem *prob, const double *X, double *MX);
+
+/* G = M^{-1} E (three tridiagonal line sweeps).  DEVICE n x p. */
+ks_status ks_step_mass_inverse(ks_problem *prob, const double *E, double *G);
+
+/* out = A^T B: A DEVICE n x pa, B DEVICE n x qb, out DEVICE pa x qb
+ * (1 <= pa, qb <= p). */
+ks_status ks_step_gram(ks_problem *prob, const double *A, int pa, const double *B, int qb,
+                       double *out);
+
+/* out = alpha (A1 C1 + A2 C2) + beta Bm: A1 DEVICE n x k1, C1 DEVICE k1 x q,
+ * A2 DEVICE n x k2 or NULL, C2 DEVICE k2 x q, Bm DEVICE n x q or NULL,
+ * out DEVICE n x q (1 <= k1, k2, q <= p). */
+ks_status ks_step_combine(ks_problem *prob, const double *A1, int k1, const double *C1,
+                          const double *A2, int k2, const double *C2, double alpha,
+                          double beta, const double *Bm, double *out, int q);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KS_STEPS_H */

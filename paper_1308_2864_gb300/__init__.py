@@ -1,0 +1,348 @@
+"""Python binding of the GB300 Kohn-Sham minimisation library (C ABI in
+include/ks.h and include/ks_steps.h).
+
+This module only marshals arguments: device buffers are torch tensors on the
+current CUDA device (FP64, contiguous, row-major n x p with the orbital index
+fastest) whose data pointers are handed to the library, and all arithmetic
+runs in the library's CUDA kernels.  There is no CPU fallback: importing
+works without a GPU, but every call needs the compiled library and a CUDA
+device, and raises otherwise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+KS_OK, KS_EINVAL, KS_ENOMEM, KS_ECUDA, KS_ENOCONV, KS_ENOTPD, KS_ESINGULAR, KS_ENAN, KS_ETIMEOUT = range(9)
+STATUS_NAMES = ["KS_OK", "KS_EINVAL", "KS_ENOMEM", "KS_ECUDA", "KS_ENOCONV", "KS_ENOTPD",
+                "KS_ESINGULAR", "KS_ENAN", "KS_ETIMEOUT"]
+KS_XC_SLATER, KS_XC_SLATER_PZ81 = 0, 1
+KS_FP64, KS_MIXED = 0, 1
+KS_QR, KS_CAYLEY = 0, 1
+
+
+class KSError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{name}: {message}")
+        self.status = status
+
+
+class ProblemDesc(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("L", ctypes.c_double), ("natoms", ctypes.c_int),
+                ("R", ctypes.POINTER(ctypes.c_double)), ("Z", ctypes.POINTER(ctypes.c_double)),
+                ("rc", ctypes.c_double), ("p", ctypes.c_int), ("occ", ctypes.c_double),
+                ("xc", ctypes.c_int), ("cg_tol", ctypes.c_double), ("cg_maxit", ctypes.c_int),
+                ("precision", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("retraction", ctypes.c_int), ("gtol", ctypes.c_double), ("maxit", ctypes.c_int),
+                ("tau0", ctypes.c_double), ("rho1", ctypes.c_double), ("delta", ctypes.c_double),
+                ("eta", ctypes.c_double), ("tau_min", ctypes.c_double), ("tau_max", ctypes.c_double),
+                ("max_backtrack", ctypes.c_int), ("ortho_tol", ctypes.c_double),
+                ("ortho_every", ctypes.c_int)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("E", ctypes.c_double), ("gradnorm", ctypes.c_double), ("ortho_err", ctypes.c_double),
+                ("E_parts", ctypes.c_double * 5), ("iters", ctypes.c_int),
+                ("cg_iters_total", ctypes.c_int), ("backtracks", ctypes.c_int),
+                ("status", ctypes.c_int), ("seconds", ctypes.c_double)]
+
+
+_LIB = None
+_P = ctypes.c_void_p
+_D = ctypes.c_double
+_I = ctypes.c_int
+_DP = ctypes.POINTER(ctypes.c_double)
+
+# (name, restype, argtypes) of every exported function.
+SIGNATURES = [
+    ("ks_opts_default", None, [ctypes.POINTER(Opts)]),
+    ("ks_problem_create", _I, [ctypes.POINTER(ProblemDesc), ctypes.POINTER(_P)]),
+    ("ks_problem_destroy", _I, [_P]),
+    ("ks_problem_bytes", ctypes.c_size_t, [ctypes.POINTER(ProblemDesc)]),
+    ("ks_energy_grad", _I, [_P, _P, _DP, _P, _P, _DP]),
+    ("ks_energy_parts", _I, [_P, _DP]),
+    ("ks_retract", _I, [_P, _I, _P, _P, _D, _P]),
+    ("ks_orthonormalize", _I, [_P, _P]),
+    ("ks_minimize", _I, [_P, _P, ctypes.POINTER(Opts), ctypes.POINTER(Result)]),
+    ("ks_minimize_host", _I, [_P, _DP, ctypes.POINTER(Opts), ctypes.POINTER(Result)]),
+    ("ks_last_error_string", ctypes.c_char_p, []),
+    ("ks_kernel_launches", ctypes.c_ulonglong, []),
+    ("ks_profile_start", _I, []),
+    ("ks_profile_stop", _I, [_DP, ctypes.POINTER(ctypes.c_longlong)]),
+    ("ks_profile_class_name", ctypes.c_char_p, [_I]),
+    ("ks_step_vext", _I, [_P, _P]),
+    ("ks_step_eii", _I, [_P, _DP]),
+    ("ks_step_density", _I, [_P, _P, _P]),
+    ("ks_step_hartree", _I, [_P, _P, _P, _I, _P, ctypes.POINTER(_I)]),
+    ("ks_step_potential", _I, [_P, _P, _P, _P, _P, _DP]),
+    ("ks_step_hamiltonian", _I, [_P, _P, _P, _P, _P, _DP]),
+    ("ks_step_mass", _I, [_P, _P, _P]),
+    ("ks_step_mass_inverse", _I, [_P, _P, _P]),
+    ("ks_step_gram", _I, [_P, _P, _I, _P, _I, _P]),
+    ("ks_step_combine", _I, [_P, _P, _I, _P, _P, _I, _P, _D, _D, _P, _P, _I]),
+]
+
+
+def library_path() -> str:
+    return _build.lib_path()
+
+
+def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load the compiled library (building it first when missing or stale)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = library_path()
+    if build_if_missing and (_build.needs_build()):
+        _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not found at {path}; run build() first")
+    lib = ctypes.CDLL(path)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _check(status: int):
+    if status != KS_OK:
+        msg = load_library().ks_last_error_string()
+        raise KSError(status, msg.decode() if msg else "")
+
+
+def _ptr(t) -> int | None:
+    """Device pointer of a CUDA FP64 contiguous tensor (None passes NULL)."""
+    if t is None:
+        return None
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous torch.float64 CUDA tensor")
+    return t.data_ptr()
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    load_library().ks_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "retraction" and isinstance(v, str):
+            v = KS_QR if v == "qr" else KS_CAYLEY
+        if not hasattr(o, k):
+            raise KeyError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+PROF_CLASSES = 12
+
+
+def kernel_launches() -> int:
+    """Kernels the library has launched in this process."""
+    return int(load_library().ks_kernel_launches())
+
+
+def profile_start():
+    _check(load_library().ks_profile_start())
+
+
+def profile_stop() -> dict:
+    """{class name: (milliseconds, timed launch groups)} since profile_start()."""
+    lib = load_library()
+    ms = (ctypes.c_double * PROF_CLASSES)()
+    cnt = (ctypes.c_longlong * PROF_CLASSES)()
+    _check(lib.ks_profile_stop(ms, cnt))
+    return {lib.ks_profile_class_name(i).decode(): (ms[i], cnt[i]) for i in range(PROF_CLASSES)}
+
+
+def result_dict(r: Result) -> dict:
+    return {"E": r.E, "gradnorm": r.gradnorm, "ortho_err": r.ortho_err,
+            "E_parts": list(r.E_parts), "iters": r.iters, "cg_iters_total": r.cg_iters_total,
+            "backtracks": r.backtracks, "status": r.status, "seconds": r.seconds}
+
+
+class Problem:
+    """One discretised KS system with its device workspace (ks_problem)."""
+
+    def __init__(self, N: int, L: float, atoms, Z, p: int, rc: float = 0.5, occ: float = 2.0,
+                 xc: int = KS_XC_SLATER_PZ81, cg_tol: float = 1e-10, cg_maxit: int = 20000,
+                 stream=None):
+        import torch
+        lib = load_library()
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        atoms = np.ascontiguousarray(np.asarray(atoms, dtype=np.float64).reshape(-1, 3))
+        Z = np.ascontiguousarray(np.asarray(Z, dtype=np.float64).reshape(-1))
+        self._atoms, self._Z = atoms, Z
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        d = ProblemDesc()
+        d.N, d.L, d.natoms = N, L, len(Z)
+        d.R = atoms.ctypes.data_as(_DP)
+        d.Z = Z.ctypes.data_as(_DP)
+        d.rc, d.p, d.occ, d.xc = rc, p, occ, xc
+        d.cg_tol, d.cg_maxit, d.precision = cg_tol, cg_maxit, KS_FP64
+        d.stream = ctypes.c_void_p(stream.cuda_stream)
+        self.desc = d
+        h = ctypes.c_void_p()
+        _check(lib.ks_problem_create(ctypes.byref(d), ctypes.byref(h)))
+        self._h = h
+        self.N, self.L, self.p, self.n = N, L, p, N ** 3
+        self.h = L / (N + 1)
+
+    @classmethod
+    def from_system(cls, s, **kw) -> "Problem":
+        return cls(N=s.N, L=s.L, atoms=s.atoms, Z=s.Z, p=s.p, rc=s.rc, occ=s.occ, xc=s.xc, **kw)
+
+    @staticmethod
+    def bytes_for(N: int, p: int) -> int:
+        d = ProblemDesc()
+        d.N, d.L, d.natoms, d.rc, d.p, d.occ, d.xc = N, 1.0, 0, 0.5, p, 2.0, 0
+        d.cg_tol, d.cg_maxit, d.precision = 1e-10, 100, KS_FP64
+        return load_library().ks_problem_bytes(ctypes.byref(d))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load_library().ks_problem_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ helpers
+    def empty_block(self):
+        import torch
+        return torch.empty((self.n, self.p), dtype=torch.float64, device="cuda")
+
+    def empty_vec(self):
+        import torch
+        return torch.empty(self.n, dtype=torch.float64, device="cuda")
+
+    # ------------------------------------------------------------ ks.h
+    def energy_grad(self, X, want_ex: bool = True, want_d: bool = False):
+        """(E, E_X or None, D or None, ||D||_M or None) at X."""
+        E = ctypes.c_double()
+        EX = self.empty_block() if want_ex else None
+        D = self.empty_block() if want_d else None
+        g = ctypes.c_double()
+        _check(load_library().ks_energy_grad(self._h, _ptr(X), ctypes.byref(E), _ptr(EX), _ptr(D),
+                                             ctypes.byref(g) if want_d else None))
+        return E.value, EX, D, (g.value if want_d else None)
+
+    def energy_parts(self) -> list[float]:
+        a = (ctypes.c_double * 5)()
+        _check(load_library().ks_energy_parts(self._h, a))
+        return list(a)
+
+    def retract(self, kind: int, X, EX, tau: float):
+        out = self.empty_block()
+        _check(load_library().ks_retract(self._h, kind, _ptr(X), _ptr(EX), tau, _ptr(out)))
+        return out
+
+    def orthonormalize(self, X):
+        _check(load_library().ks_orthonormalize(self._h, _ptr(X)))
+        return X
+
+    def minimize(self, X, **opts) -> dict:
+        """Alg. ConOptM in place on the device block X."""
+        o = default_opts(**opts)
+        r = Result()
+        st = load_library().ks_minimize(self._h, _ptr(X), ctypes.byref(o), ctypes.byref(r))
+        if st not in (KS_OK, KS_ENOCONV):
+            _check(st)
+        return result_dict(r)
+
+    def minimize_host(self, X: np.ndarray, **opts) -> dict:
+        """Alg. ConOptM on a host block (copied in and out inside the call)."""
+        if not (X.dtype == np.float64 and X.flags["C_CONTIGUOUS"] and X.shape == (self.n, self.p)):
+            raise TypeError("expected a C-contiguous float64 (n, p) array")
+        o = default_opts(**opts)
+        r = Result()
+        st = load_library().ks_minimize_host(self._h, X.ctypes.data_as(_DP), ctypes.byref(o),
+                                             ctypes.byref(r))
+        if st not in (KS_OK, KS_ENOCONV):
+            _check(st)
+        return result_dict(r)
+
+    # ------------------------------------------------------------ ks_steps.h
+    def step_vext(self):
+        out = self.empty_vec()
+        _check(load_library().ks_step_vext(self._h, _ptr(out)))
+        return out
+
+    def step_eii(self) -> float:
+        e = ctypes.c_double()
+        _check(load_library().ks_step_eii(self._h, ctypes.byref(e)))
+        return e.value
+
+    def step_density(self, X):
+        out = self.empty_vec()
+        _check(load_library().ks_step_density(self._h, _ptr(X), _ptr(out)))
+        return out
+
+    def step_hartree(self, rho, vH=None, warm: bool = False):
+        import torch
+        v = torch.zeros_like(rho) if vH is None else vH
+        r = torch.empty_like(rho)
+        it = ctypes.c_int()
+        _check(load_library().ks_step_hartree(self._h, _ptr(rho), _ptr(v), 1 if warm else 0,
+                                              _ptr(r), ctypes.byref(it)))
+        return v, r, it.value
+
+    def step_potential(self, rho, vH, resid=None):
+        veff = self.empty_vec()
+        e = (ctypes.c_double * 3)()
+        _check(load_library().ks_step_potential(self._h, _ptr(rho), _ptr(vH), _ptr(resid),
+                                                _ptr(veff), e))
+        return veff, list(e)
+
+    def step_hamiltonian(self, X, veff, want_mx: bool = True):
+        EX = self.empty_block()
+        MX = self.empty_block() if want_mx else None
+        k = ctypes.c_double()
+        _check(load_library().ks_step_hamiltonian(self._h, _ptr(X), _ptr(veff), _ptr(EX), _ptr(MX),
+                                                  ctypes.byref(k)))
+        return EX, MX, k.value
+
+    def step_mass(self, X):
+        out = self.empty_block()
+        _check(load_library().ks_step_mass(self._h, _ptr(X), _ptr(out)))
+        return out
+
+    def step_mass_inverse(self, E):
+        out = self.empty_block()
+        _check(load_library().ks_step_mass_inverse(self._h, _ptr(E), _ptr(out)))
+        return out
+
+    def step_gram(self, A, B):
+        import torch
+        pa, qb = A.shape[1], B.shape[1]
+        out = torch.empty((pa, qb), dtype=torch.float64, device="cuda")
+        _check(load_library().ks_step_gram(self._h, _ptr(A), pa, _ptr(B), qb, _ptr(out)))
+        return out
+
+    def step_combine(self, A1, C1, A2=None, C2=None, alpha: float = 1.0, beta: float = 0.0, Bm=None):
+        import torch
+        q = C1.shape[1]
+        out = torch.empty((A1.shape[0], q), dtype=torch.float64, device="cuda")
+        _check(load_library().ks_step_combine(
+            self._h, _ptr(A1), A1.shape[1], _ptr(C1), _ptr(A2), A2.shape[1] if A2 is not None else 0,
+            _ptr(C2), alpha, beta, _ptr(Bm), _ptr(out), q))
+        return out
+
+
+__all__ = ["Problem", "KSError", "load_library", "library_path", "default_opts",
+           "KS_QR", "KS_CAYLEY", "KS_XC_SLATER", "KS_XC_SLATER_PZ81", "SIGNATURES"]

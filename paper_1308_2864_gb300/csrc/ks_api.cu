@@ -1,0 +1,530 @@
+// The C ABI (include/ks.h): problem lifetime, energy and gradient, one
+// retraction step, M-orthonormalisation and the Alg. ConOptM driver.
+//
+// Host code here only sequences kernels and takes the scalar decisions of
+// the line search (Eq. NMLS-Armijo) and of the Barzilai-Borwein step
+// (Eq. bb-1) from device-computed traces; every array operation runs in the
+// kernels of this library.
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <utility>
+
+#include "ks_internal.cuh"
+
+namespace ks {
+
+namespace {
+thread_local char g_err[512] = "";
+}
+
+ks_status set_error(ks_status st, const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+ks_status cuda_error(cudaError_t e, const char *where) {
+  cudaGetLastError();
+  if (e == cudaErrorMemoryAllocation)
+    return set_error(KS_ENOMEM, "%s: %s", where, cudaGetErrorString(e));
+  return set_error(KS_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+// Index of the n x p blocks in Problem::blk.
+enum Block { B_X0 = 0, B_X1, B_X2, B_MX0, B_MX1, B_MX2, B_EX0, B_EX1, B_G, B_D0, B_D1, B_MD0, B_MD1 };
+
+// Offsets (in units of p*p) of the small matrices in the pp pool; the first
+// 6 p^2 are scratch of the factor kernels.
+enum Small { S_WORK = 0, S_S = 6, S_DMD, S_O, S_A, S_B, S_C1, S_C2, S_T, S_COUNT };
+
+static size_t gram_partials_len(int p, int sms) {
+  const size_t tiles = (size_t)((p + kTile - 1) / kTile) * ((p + kTile - 1) / kTile);
+  return ((size_t)4 * sms + tiles) * kTile * kTile;
+}
+
+size_t problem_bytes(int N, int p, int sms) {
+  const size_t n = (size_t)N * N * N;
+  size_t b = 8 * n * sizeof(double);                                  // n-vectors
+  b += (size_t)Problem::kNBlocks * n * p * sizeof(double);            // n x p blocks
+  b += (size_t)S_COUNT * p * p * sizeof(double);                      // small matrices
+  size_t part = gram_partials_len(p, sms);
+  const size_t red = (size_t)4 * 8 * sms;
+  const size_t cg = (size_t)3 * 2 * sms;
+  if (red > part) part = red;
+  if (cg > part) part = cg;
+  b += part * sizeof(double);
+  b += SC_COUNT * sizeof(double) + (size_t)N * sizeof(double) + 4096;
+  return b;
+}
+
+static ks_status validate(const ks_problem_desc *d) {
+  if (!d) return set_error(KS_EINVAL, "null description");
+  if (d->N < 2 || d->N > 2048) return set_error(KS_EINVAL, "N = %d out of range [2, 2048]", d->N);
+  if (!(d->L > 0.0)) return set_error(KS_EINVAL, "L must be positive");
+  if (d->p < 1 || (long long)d->p > (long long)d->N * d->N * d->N)
+    return set_error(KS_EINVAL, "p = %d out of range", d->p);
+  if (d->natoms < 0 || (d->natoms > 0 && (!d->R || !d->Z)))
+    return set_error(KS_EINVAL, "bad atom arrays");
+  if (!(d->rc > 0.0)) return set_error(KS_EINVAL, "rc must be positive");
+  if (d->xc != KS_XC_SLATER && d->xc != KS_XC_SLATER_PZ81) return set_error(KS_EINVAL, "bad xc");
+  if (d->precision != KS_FP64) return set_error(KS_EINVAL, "only KS_FP64 is available");
+  if (!(d->cg_tol > 0.0) || d->cg_maxit < 1) return set_error(KS_EINVAL, "bad CG parameters");
+  return KS_OK;
+}
+
+static void free_problem(Problem &P) {
+  auto f = [](void *q) { if (q) cudaFree(q); };
+  f(P.vext); f(P.rho); f(P.vH); f(P.veff); f(P.cg_r); f(P.cg_pa); f(P.cg_pb); f(P.cg_q);
+  for (auto &b : P.blk) f(b);
+  f(P.pp); f(P.partials); f(P.scal); f(P.atoms_dev); f(P.thomas_w); f(P.bar); f(P.dstatus);
+  if (P.scal_host) cudaFreeHost(P.scal_host);
+  if (P.dstatus_host) cudaFreeHost(P.dstatus_host);
+  if (P.own_stream && P.stream) cudaStreamDestroy(P.stream);
+}
+
+template <typename T>
+static ks_status dalloc(T **ptr, size_t count, Problem &P) {
+  const size_t bytes = count * sizeof(T) > 0 ? count * sizeof(T) : sizeof(T);
+  cudaError_t e = cudaMalloc((void **)ptr, bytes);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMalloc");
+  P.bytes += bytes;
+  return KS_OK;
+}
+
+static double *sm(Problem &P, int which) { return P.pp + (size_t)which * P.p * P.p; }
+
+// Copy device scalars and the status word to the host and wait.
+static ks_status sync_scalars(Problem &P) {
+  KS_CUDA_TRY(cudaMemcpyAsync(P.scal_host, P.scal, SC_COUNT * sizeof(double),
+                              cudaMemcpyDeviceToHost, P.stream));
+  KS_CUDA_TRY(cudaMemcpyAsync(P.dstatus_host, P.dstatus, sizeof(int), cudaMemcpyDeviceToHost,
+                              P.stream));
+  KS_CUDA_TRY(cudaStreamSynchronize(P.stream));
+  prof_collect();
+  const int st = *P.dstatus_host;
+  if (st != KS_OK) {
+    KS_CUDA_TRY(cudaMemsetAsync(P.dstatus, 0, sizeof(int), P.stream));
+    switch (st) {
+      case KS_ENOCONV: return set_error(KS_ENOCONV, "Hartree CG did not reach its tolerance");
+      case KS_ENOTPD: return set_error(KS_ENOTPD, "Cholesky met a non-positive pivot");
+      case KS_ESINGULAR: return set_error(KS_ESINGULAR, "Cayley system is singular");
+      case KS_ENAN: return set_error(KS_ENAN, "non-finite value in the Hartree CG");
+      case KS_ETIMEOUT: return set_error(KS_ETIMEOUT, "device grid barrier timed out");
+      default: return set_error(KS_ECUDA, "device status %d", st);
+    }
+  }
+  return KS_OK;
+}
+
+// ---------------------------------------------------------------- phases
+// Energy at X: density, Hartree CG (warm-started when a previous potential
+// exists), potential and energy sums, Hamiltonian stencil (E_X, M X).
+static ks_status evaluate(Problem &P, const double *X, double *EX, double *MX, double *E) {
+  KS_TRY(launch_density(P, X, P.rho));
+  KS_TRY(launch_cg(P, P.rho, P.vH, P.cg_r, P.vH_valid));
+  KS_TRY(launch_potential(P, P.rho, P.vH, P.cg_r, P.veff, true));
+  KS_TRY(launch_hamiltonian(P, X, P.veff, EX, MX, P.scal + SC_EKIN));
+  ks_status st = sync_scalars(P);
+  if (st != KS_OK) {
+    P.vH_valid = false;
+    return st;
+  }
+  P.vH_valid = true;
+  const double *s = P.scal_host;
+  P.last_parts[0] = s[SC_EKIN];
+  P.last_parts[1] = s[SC_EEXT];
+  P.last_parts[2] = s[SC_EH];
+  P.last_parts[3] = s[SC_EXC];
+  P.last_parts[4] = s[SC_EII];
+  P.last_cg_iters = (int)s[SC_CG_ITERS];
+  P.last_E = s[SC_EKIN] + s[SC_EEXT] + s[SC_EH] + s[SC_EXC] + s[SC_EII];
+  if (!std::isfinite(P.last_E)) return set_error(KS_ENAN, "non-finite energy");
+  *E = P.last_E;
+  return KS_OK;
+}
+
+struct Traces {
+  double dnorm2 = 0, ss = 0, sy = 0, yy = 0;
+};
+
+// Projected gradient at X (Eq. def-nablaE in the M metric):
+// G = M^{-1} E_X, S = E_X^T X, D = G - X S, MD = M D, ||D||_M^2, the BB
+// traces against `prev`, and the Grams the retraction needs.
+static ks_status project(Problem &P, int retraction, const double *X, const double *EX,
+                         const double *MX, double *D, double *MD, const BBPrev *prev,
+                         Traces *tr) {
+  const int p = P.p;
+  double *G = P.blk[B_G];
+  KS_TRY(launch_mass_inverse(P, EX, G));
+  KS_TRY(launch_gram(P, EX, p, X, p, sm(P, S_S)));
+  KS_TRY(launch_combine(P, X, p, sm(P, S_S), nullptr, 0, nullptr, -1.0, 1.0, G, D, p));
+  KS_TRY(launch_mass_dots(P, D, MD, X, MX, prev, P.scal + SC_DNORM2));
+  if (retraction == KS_QR) {
+    KS_TRY(launch_gram(P, D, p, MD, p, sm(P, S_DMD)));
+  } else {
+    KS_TRY(launch_transpose(P, sm(P, S_S), sm(P, S_A)));
+    KS_TRY(launch_gram(P, EX, p, G, p, sm(P, S_B)));
+    KS_TRY(launch_gram(P, X, p, MX, p, sm(P, S_O)));
+  }
+  KS_TRY(sync_scalars(P));
+  tr->dnorm2 = P.scal_host[SC_DNORM2];
+  if (prev) {
+    tr->ss = P.scal_host[SC_BB_SS];
+    tr->sy = P.scal_host[SC_BB_SY];
+    tr->yy = P.scal_host[SC_BB_YY];
+  }
+  if (!std::isfinite(tr->dnorm2)) return set_error(KS_ENAN, "non-finite gradient norm");
+  return KS_OK;
+}
+
+// X+ from X along -D with step tau (uses the Grams left by project()).
+static ks_status retract(Problem &P, int retraction, const double *X, const double *D,
+                         double tau, double *Xout) {
+  const int p = P.p;
+  if (retraction == KS_QR) {
+    KS_TRY(launch_qr_factor(P, sm(P, S_DMD), nullptr, tau, sm(P, S_C1), sm(P, S_C2)));
+    KS_TRY(launch_combine(P, X, p, sm(P, S_C1), D, p, sm(P, S_C2), 1.0, 0.0, nullptr, Xout, p));
+  } else {
+    KS_TRY(launch_cayley_factor(P, sm(P, S_A), sm(P, S_S), sm(P, S_B), sm(P, S_O), tau,
+                                sm(P, S_C1), sm(P, S_C2)));
+    KS_TRY(launch_combine(P, X, p, sm(P, S_C1), P.blk[B_G], p, sm(P, S_C2), 1.0, 0.0, nullptr,
+                          Xout, p));
+  }
+  return KS_OK;
+}
+
+// Cholesky QR in the M inner product, `passes` times; X is updated in place
+// (tmp is an n x p scratch block, MX receives M X of the result).
+static ks_status orthonormalize(Problem &P, double *X, double *tmp, double *MX, int passes) {
+  const int p = P.p;
+  for (int k = 0; k < passes; ++k) {
+    KS_TRY(launch_mass(P, X, MX));
+    KS_TRY(launch_gram(P, X, p, MX, p, sm(P, S_O)));
+    KS_TRY(launch_qr_factor(P, nullptr, sm(P, S_O), 0.0, sm(P, S_C1), nullptr));
+    KS_TRY(launch_combine(P, X, p, sm(P, S_C1), nullptr, 0, nullptr, 1.0, 0.0, nullptr, tmp, p));
+    KS_CUDA_TRY(cudaMemcpyAsync(X, tmp, (size_t)P.n * p * sizeof(double),
+                                cudaMemcpyDeviceToDevice, P.stream));
+  }
+  KS_TRY(launch_mass(P, X, MX));
+  return sync_scalars(P);
+}
+
+// ||X^T M X - I||_F
+static ks_status ortho_error(Problem &P, const double *X, const double *MX, double *err) {
+  KS_TRY(launch_gram(P, X, P.p, MX, P.p, sm(P, S_T)));
+  KS_TRY(launch_ortho_err(P, sm(P, S_T), P.scal + SC_ORTHO));
+  KS_TRY(sync_scalars(P));
+  *err = std::sqrt(P.scal_host[SC_ORTHO]);
+  return KS_OK;
+}
+
+// tau_{k,1} = ss/|sy| on odd k, tau_{k,2} = |sy|/yy on even k (Eq. bb-1),
+// reset to tau0 when not a positive finite number, then clamped.
+static double bb_step(int k, const Traces &t, const ks_opts &o) {
+  double num, den;
+  if (k % 2 == 1) { num = t.ss; den = std::fabs(t.sy); }
+  else { num = std::fabs(t.sy); den = t.yy; }
+  if (!(den > 0.0) || !std::isfinite(num) || !std::isfinite(den)) return o.tau0;
+  double tau = num / den;
+  if (!std::isfinite(tau) || tau <= 0.0) return o.tau0;
+  if (tau < o.tau_min) tau = o.tau_min;
+  if (tau > o.tau_max) tau = o.tau_max;
+  return tau;
+}
+
+static ks_status minimize_device(Problem &P, double *X_inout, const ks_opts &o, ks_result *res) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const int p = P.p;
+  const size_t bytes = (size_t)P.n * p * sizeof(double);
+  int ix[3] = {B_X0, B_X1, B_X2};        // cur, prev, trial
+  int imx[3] = {B_MX0, B_MX1, B_MX2};
+  int iex[2] = {B_EX0, B_EX1};           // cur, trial
+  int id[2] = {B_D0, B_D1};              // cur, prev
+  int imd[2] = {B_MD0, B_MD1};
+  auto X = [&](int s) { return P.blk[ix[s]]; };
+  auto MX = [&](int s) { return P.blk[imx[s]]; };
+  auto EX = [&](int s) { return P.blk[iex[s]]; };
+  auto D = [&](int s) { return P.blk[id[s]]; };
+  auto MD = [&](int s) { return P.blk[imd[s]]; };
+
+  KS_CUDA_TRY(cudaMemcpyAsync(X(0), X_inout, bytes, cudaMemcpyDeviceToDevice, P.stream));
+  KS_TRY(orthonormalize(P, X(0), X(2), MX(0), 2));
+  double E = 0;
+  KS_TRY(evaluate(P, X(0), EX(0), MX(0), &E));
+  Traces tr;
+  KS_TRY(project(P, o.retraction, X(0), EX(0), MX(0), D(0), MD(0), nullptr, &tr));
+  double C = E, Q = 1.0;
+  bool have_prev = false;
+  int k = 0, backtracks = 0, cg_total = P.last_cg_iters;
+  ks_status status = KS_OK;
+  while (std::sqrt(std::fmax(tr.dnorm2, 0.0)) > o.gtol && k < o.maxit) {
+    double tau = have_prev ? bb_step(k, tr, o) : o.tau0;
+    int h = 0;
+    double Et = 0;
+    for (;;) {
+      KS_TRY(retract(P, o.retraction, X(0), D(0), tau, X(2)));
+      KS_TRY(evaluate(P, X(2), EX(1), MX(2), &Et));
+      cg_total += P.last_cg_iters;
+      if (Et <= C - o.rho1 * tau * tr.dnorm2 || h == o.max_backtrack) break;
+      tau *= o.delta;
+      ++h;
+    }
+    backtracks += h;
+    const double Qn = o.eta * Q + 1.0;
+    C = (o.eta * Q * C + Et) / Qn;
+    Q = Qn;
+    // accept: prev <- cur, cur <- trial
+    std::swap(ix[1], ix[0]);
+    std::swap(ix[0], ix[2]);
+    std::swap(imx[1], imx[0]);
+    std::swap(imx[0], imx[2]);
+    std::swap(iex[0], iex[1]);
+    std::swap(id[0], id[1]);
+    std::swap(imd[0], imd[1]);
+    E = Et;
+    ++k;
+    bool reortho = false;
+    if (o.retraction == KS_CAYLEY || (o.ortho_every > 0 && k % o.ortho_every == 0)) {
+      double oerr = 0;
+      KS_TRY(ortho_error(P, X(0), MX(0), &oerr));
+      reortho = oerr > o.ortho_tol;
+    }
+    if (reortho) {
+      KS_TRY(orthonormalize(P, X(0), X(2), MX(0), 1));
+      KS_TRY(evaluate(P, X(0), EX(0), MX(0), &E));
+      cg_total += P.last_cg_iters;
+    }
+    BBPrev prev{X(1), MX(1), D(1), MD(1)};
+    KS_TRY(project(P, o.retraction, X(0), EX(0), MX(0), D(0), MD(0), &prev, &tr));
+    have_prev = true;
+  }
+  if (std::sqrt(std::fmax(tr.dnorm2, 0.0)) > o.gtol) status = KS_ENOCONV;
+  KS_CUDA_TRY(cudaMemcpyAsync(X_inout, X(0), bytes, cudaMemcpyDeviceToDevice, P.stream));
+  double oerr = 0;
+  KS_TRY(ortho_error(P, X(0), MX(0), &oerr));
+  if (res) {
+    res->E = E;
+    res->gradnorm = std::sqrt(std::fmax(tr.dnorm2, 0.0));
+    res->ortho_err = oerr;
+    for (int i = 0; i < 5; ++i) res->E_parts[i] = P.last_parts[i];
+    res->iters = k;
+    res->cg_iters_total = cg_total;
+    res->backtracks = backtracks;
+    res->status = status;
+    res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  if (status != KS_OK) set_error(status, "gradient norm above gtol after %d iterations", k);
+  return status;
+}
+
+}  // namespace ks
+
+using namespace ks;
+
+extern "C" {
+
+void ks_opts_default(ks_opts *o) {
+  if (!o) return;
+  o->retraction = KS_QR;
+  o->gtol = 1e-6;
+  o->maxit = 300;
+  o->tau0 = 1e-3;
+  o->rho1 = 1e-4;
+  o->delta = 0.1;
+  o->eta = 0.85;
+  o->tau_min = 1e-10;
+  o->tau_max = 1e10;
+  o->max_backtrack = 10;
+  o->ortho_tol = 1e-12;
+  o->ortho_every = 20;
+}
+
+const char *ks_last_error_string(void) { return g_err; }
+
+size_t ks_problem_bytes(const ks_problem_desc *d) {
+  if (validate(d) != KS_OK) return 0;
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess)
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaGetLastError();
+  return problem_bytes(d->N, d->p, sms);
+}
+
+ks_status ks_problem_create(const ks_problem_desc *d, ks_problem **out) {
+  if (!out) return set_error(KS_EINVAL, "null output handle");
+  *out = nullptr;
+  KS_TRY(validate(d));
+  ks_problem *kp = new (std::nothrow) ks_problem();
+  if (!kp) return set_error(KS_ENOMEM, "host allocation failed");
+  Problem &P = kp->P;
+  auto fail = [&](ks_status st) {
+    free_problem(P);
+    delete kp;
+    return st;
+  };
+  P.N = d->N;
+  P.n = d->N * d->N * d->N;
+  P.p = d->p;
+  P.natoms = d->natoms;
+  P.xc = d->xc;
+  P.L = d->L;
+  P.h = d->L / (d->N + 1);
+  P.rc = d->rc;
+  P.occ = d->occ;
+  P.cg_tol = d->cg_tol;
+  P.cg_maxit = d->cg_maxit;
+  P.atoms_host.resize((size_t)4 * (d->natoms > 0 ? d->natoms : 1), 0.0);
+  for (int a = 0; a < d->natoms; ++a) {
+    P.atoms_host[4 * a + 0] = d->R[3 * a + 0];
+    P.atoms_host[4 * a + 1] = d->R[3 * a + 1];
+    P.atoms_host[4 * a + 2] = d->R[3 * a + 2];
+    P.atoms_host[4 * a + 3] = d->Z[a];
+  }
+  cudaError_t e = cudaGetDevice(&P.device);
+  if (e != cudaSuccess) return fail(cuda_error(e, "cudaGetDevice"));
+  e = cudaDeviceGetAttribute(&P.sms, cudaDevAttrMultiProcessorCount, P.device);
+  if (e != cudaSuccess) return fail(cuda_error(e, "cudaDeviceGetAttribute"));
+  if (d->stream) {
+    P.stream = (cudaStream_t)d->stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&P.stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return fail(cuda_error(e, "cudaStreamCreate"));
+    P.own_stream = true;
+  }
+  const size_t n = P.n, np = (size_t)P.n * P.p;
+  ks_status st;
+#define ALLOC(ptr, cnt) \
+  if ((st = dalloc(&(ptr), (cnt), P)) != KS_OK) return fail(st);
+  ALLOC(P.vext, n); ALLOC(P.rho, n); ALLOC(P.vH, n); ALLOC(P.veff, n);
+  ALLOC(P.cg_r, n); ALLOC(P.cg_pa, n); ALLOC(P.cg_pb, n); ALLOC(P.cg_q, n);
+  for (auto &b : P.blk) { ALLOC(b, np); }
+  P.pp_len = (size_t)S_COUNT * P.p * P.p;
+  ALLOC(P.pp, P.pp_len);
+  P.cg_blocks = cg_grid_blocks(P.sms, P.n);
+  size_t part = gram_partials_len(P.p, P.sms);
+  if ((size_t)4 * 8 * P.sms > part) part = (size_t)4 * 8 * P.sms;
+  if ((size_t)3 * P.cg_blocks > part) part = (size_t)3 * P.cg_blocks;
+  P.partials_len = part;
+  ALLOC(P.partials, part);
+  ALLOC(P.scal, SC_COUNT);
+  ALLOC(P.atoms_dev, P.atoms_host.size());
+  ALLOC(P.thomas_w, (size_t)P.N);
+  ALLOC(P.bar, 1);
+  ALLOC(P.dstatus, 1);
+#undef ALLOC
+  e = cudaMallocHost((void **)&P.scal_host, SC_COUNT * sizeof(double));
+  if (e != cudaSuccess) return fail(cuda_error(e, "cudaMallocHost"));
+  e = cudaMallocHost((void **)&P.dstatus_host, sizeof(int));
+  if (e != cudaSuccess) return fail(cuda_error(e, "cudaMallocHost"));
+  e = cudaMemcpyAsync(P.atoms_dev, P.atoms_host.data(), P.atoms_host.size() * sizeof(double),
+                      cudaMemcpyHostToDevice, P.stream);
+  if (e != cudaSuccess) return fail(cuda_error(e, "copy atoms"));
+  e = cudaMemsetAsync(P.scal, 0, SC_COUNT * sizeof(double), P.stream);
+  if (e != cudaSuccess) return fail(cuda_error(e, "memset"));
+  e = cudaMemsetAsync(P.dstatus, 0, sizeof(int), P.stream);
+  if (e != cudaSuccess) return fail(cuda_error(e, "memset"));
+  e = cudaMemsetAsync(P.vH, 0, n * sizeof(double), P.stream);
+  if (e != cudaSuccess) return fail(cuda_error(e, "memset"));
+  if ((st = launch_setup(P)) != KS_OK) return fail(st);
+  if ((st = sync_scalars(P)) != KS_OK) return fail(st);
+  *out = kp;
+  return KS_OK;
+}
+
+ks_status ks_problem_destroy(ks_problem *kp) {
+  if (!kp) return KS_OK;
+  if (kp->P.stream) cudaStreamSynchronize(kp->P.stream);
+  free_problem(kp->P);
+  delete kp;
+  return KS_OK;
+}
+
+ks_status ks_energy_grad(ks_problem *kp, const double *X, double *E, double *EX, double *D,
+                         double *gradnorm) {
+  if (!kp || !X || !E) return set_error(KS_EINVAL, "null argument");
+  Problem &P = kp->P;
+  const size_t bytes = (size_t)P.n * P.p * sizeof(double);
+  double e = 0;
+  KS_TRY(evaluate(P, X, P.blk[B_EX0], P.blk[B_MX0], &e));
+  if (D || gradnorm) {
+    Traces tr;
+    KS_TRY(project(P, KS_QR, X, P.blk[B_EX0], P.blk[B_MX0], P.blk[B_D0], P.blk[B_MD0], nullptr,
+                   &tr));
+    if (gradnorm) *gradnorm = std::sqrt(std::fmax(tr.dnorm2, 0.0));
+    if (D) KS_CUDA_TRY(cudaMemcpyAsync(D, P.blk[B_D0], bytes, cudaMemcpyDeviceToDevice, P.stream));
+  }
+  if (EX) KS_CUDA_TRY(cudaMemcpyAsync(EX, P.blk[B_EX0], bytes, cudaMemcpyDeviceToDevice, P.stream));
+  KS_CUDA_TRY(cudaStreamSynchronize(P.stream));
+  *E = e;
+  return KS_OK;
+}
+
+ks_status ks_energy_parts(ks_problem *kp, double parts[5]) {
+  if (!kp || !parts) return set_error(KS_EINVAL, "null argument");
+  for (int i = 0; i < 5; ++i) parts[i] = kp->P.last_parts[i];
+  return KS_OK;
+}
+
+ks_status ks_retract(ks_problem *kp, int kind, const double *X, const double *EX, double tau,
+                     double *Xout) {
+  if (!kp || !X || !EX || !Xout) return set_error(KS_EINVAL, "null argument");
+  if (kind != KS_QR && kind != KS_CAYLEY) return set_error(KS_EINVAL, "bad retraction kind");
+  if (Xout == X || Xout == EX) return set_error(KS_EINVAL, "Xout aliases an input");
+  Problem &P = kp->P;
+  KS_TRY(launch_mass(P, X, P.blk[B_MX0]));
+  Traces tr;
+  KS_TRY(project(P, kind, X, EX, P.blk[B_MX0], P.blk[B_D0], P.blk[B_MD0], nullptr, &tr));
+  KS_TRY(retract(P, kind, X, P.blk[B_D0], tau, P.blk[B_X2]));
+  KS_TRY(sync_scalars(P));
+  KS_CUDA_TRY(cudaMemcpyAsync(Xout, P.blk[B_X2], (size_t)P.n * P.p * sizeof(double),
+                              cudaMemcpyDeviceToDevice, P.stream));
+  KS_CUDA_TRY(cudaStreamSynchronize(P.stream));
+  return KS_OK;
+}
+
+ks_status ks_orthonormalize(ks_problem *kp, double *X) {
+  if (!kp || !X) return set_error(KS_EINVAL, "null argument");
+  Problem &P = kp->P;
+  return orthonormalize(P, X, P.blk[B_X2], P.blk[B_MX2], 2);
+}
+
+ks_status ks_minimize(ks_problem *kp, double *X_inout, const ks_opts *opts, ks_result *res) {
+  if (!kp || !X_inout) return set_error(KS_EINVAL, "null argument");
+  ks_opts o;
+  if (opts) o = *opts;
+  else ks_opts_default(&o);
+  if (o.retraction != KS_QR && o.retraction != KS_CAYLEY)
+    return set_error(KS_EINVAL, "bad retraction");
+  if (!(o.delta > 0.0 && o.delta < 1.0) || !(o.eta >= 0.0 && o.eta < 1.0) || o.maxit < 0 ||
+      !(o.tau0 > 0.0) || o.max_backtrack < 0)
+    return set_error(KS_EINVAL, "bad line-search parameters");
+  kp->P.vH_valid = false;
+  return minimize_device(kp->P, X_inout, o, res);
+}
+
+ks_status ks_minimize_host(ks_problem *kp, double *Xh, const ks_opts *opts, ks_result *res) {
+  if (!kp || !Xh) return set_error(KS_EINVAL, "null argument");
+  const auto t0 = std::chrono::steady_clock::now();
+  Problem &P = kp->P;
+  const size_t bytes = (size_t)P.n * P.p * sizeof(double);
+  // The driver reads its input block only before the first iteration and
+  // writes its output only after the last one, so the block B_D1 (a
+  // previous-gradient slot during the iterations) can stage the host copy.
+  double *dX = P.blk[B_D1];
+  KS_CUDA_TRY(cudaMemcpyAsync(dX, Xh, bytes, cudaMemcpyHostToDevice, P.stream));
+  ks_status st = ks_minimize(kp, dX, opts, res);
+  if (st != KS_OK && st != KS_ENOCONV) return st;
+  KS_CUDA_TRY(cudaMemcpyAsync(Xh, dX, bytes, cudaMemcpyDeviceToHost, P.stream));
+  KS_CUDA_TRY(cudaStreamSynchronize(P.stream));
+  if (res)
+    res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,209 @@
+// FP64 tall-skinny products of the iteration (Sec. 3's O(np^2) part):
+//   gram:     out = A^T B (p x q Grams such as E_X^T X, D^T M D, X^T M X),
+//             split over row chunks; partial tiles are summed in chunk
+//             order, so the result is deterministic;
+//   combine:  out = A1 C1 + A2 C2 + beta B (the retraction updates
+//             X+ = X C1 + D C2 of Eq. QR / Eq. WY3 and D = G - X S).
+// FP64 arithmetic is the bound of both on GB300 (n p^2 FMAs against n p
+// words of traffic); tiles are 64 x 64 with a 4 x 4 register block per
+// thread, strided so that shared-memory reads are conflict-free.
+#include "ks_device.cuh"
+
+namespace ks {
+
+static int gram_chunks(const Problem &P, int pa, int qb) {
+  const int tiles = ((pa + kTile - 1) / kTile) * ((qb + kTile - 1) / kTile);
+  int chunks = (4 * P.sms + tiles - 1) / tiles;
+  const int maxc = (P.n + kTileK - 1) / kTileK;
+  if (chunks > maxc) chunks = maxc;
+  if (chunks < 1) chunks = 1;
+  return chunks;
+}
+
+__global__ void __launch_bounds__(256) gram_kernel(long long n, int pa, int qb, long long rows_per,
+                                                   const double *__restrict__ A,
+                                                   const double *__restrict__ B,
+                                                   double *__restrict__ part) {
+  __shared__ double As[kTileK][kTile];
+  __shared__ double Bs[kTileK][kTile];
+  const int tq = (qb + kTile - 1) / kTile;
+  const int ta = blockIdx.x / tq, tb = blockIdx.x % tq;
+  const int chunk = blockIdx.y;
+  const long long r0 = chunk * rows_per;
+  long long r1 = r0 + rows_per;
+  if (r1 > n) r1 = n;
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const int a0 = ta * kTile, b0 = tb * kTile;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  for (long long r = r0; r < r1; r += kTileK) {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int idx = tid + t * 256;
+      const int rr = idx >> 6, cc = idx & 63;
+      const long long row = r + rr;
+      const bool rowok = row < r1;
+      As[rr][cc] = (rowok && a0 + cc < pa) ? A[row * pa + a0 + cc] : 0.0;
+      Bs[rr][cc] = (rowok && b0 + cc < qb) ? B[row * qb + b0 + cc] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int rr = 0; rr < kTileK; ++rr) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = As[rr][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = Bs[rr][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  double *dst = part + (long long)chunk * pa * qb;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int a = a0 + ty + 16 * i;
+    if (a >= pa) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int b = b0 + tx + 16 * j;
+      if (b < qb) dst[(long long)a * qb + b] = acc[i][j];
+    }
+  }
+}
+
+__global__ void gram_reduce_kernel(int chunks, long long len, const double *__restrict__ part,
+                                   double *__restrict__ out) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= len) return;
+  double s = 0.0;
+  for (int c = 0; c < chunks; ++c) s += part[(long long)c * len + e];
+  out[e] = s;
+}
+
+ks_status launch_gram(Problem &P, const double *A, int pa, const double *B, int qb, double *out) {
+  const int chunks = gram_chunks(P, pa, qb);
+  long long rows_per = (P.n + chunks - 1) / chunks;
+  rows_per = (rows_per + kTileK - 1) / kTileK * kTileK;
+  const int tiles = ((pa + kTile - 1) / kTile) * ((qb + kTile - 1) / kTile);
+  const size_t need = (size_t)chunks * pa * qb;
+  if (need > P.partials_len)
+    return set_error(KS_EINVAL, "gram: partial buffer too small (%zu > %zu)", need, P.partials_len);
+  {
+    ProfScope ps_(P.stream, KP_GRAM);
+    gram_kernel<<<dim3(tiles, chunks), 256, 0, P.stream>>>(P.n, pa, qb, rows_per, A, B, P.partials);
+  }
+  KS_CUDA_TRY(cudaGetLastError());
+  const long long len = (long long)pa * qb;
+  {
+    ProfScope ps_(P.stream, KP_REDUCE);
+    gram_reduce_kernel<<<(int)((len + kThreads - 1) / kThreads), kThreads, 0, P.stream>>>(
+        chunks, len, P.partials, out);
+  }
+  KS_CUDA_TRY(cudaGetLastError());
+  return KS_OK;
+}
+
+__global__ void __launch_bounds__(256) combine_kernel(long long n, int q, const double *__restrict__ A1,
+                                                      int k1, const double *__restrict__ C1,
+                                                      const double *__restrict__ A2, int k2,
+                                                      const double *__restrict__ C2, double alpha,
+                                                      double beta,
+                                                      const double *__restrict__ Bm,
+                                                      double *__restrict__ out) {
+  __shared__ double As[kTile][kTileK + 1];
+  __shared__ double Cs[kTileK][kTile];
+  const long long r0 = (long long)blockIdx.x * kTile;
+  const int c0 = blockIdx.y * kTile;
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  for (int op = 0; op < 2; ++op) {
+    const double *A = op == 0 ? A1 : A2;
+    const double *C = op == 0 ? C1 : C2;
+    const int kk = op == 0 ? k1 : k2;
+    if (A == nullptr) continue;
+    for (int k0 = 0; k0 < kk; k0 += kTileK) {
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int idx = tid + t * 256;
+        const int rr = idx >> 4, cc = idx & 15;          // A tile: 64 rows x 16
+        const long long row = r0 + rr;
+        As[rr][cc] = (row < n && k0 + cc < kk) ? A[row * kk + k0 + cc] : 0.0;
+        const int cr = idx >> 6, ccol = idx & 63;         // C tile: 16 x 64
+        Cs[cr][ccol] = (k0 + cr < kk && c0 + ccol < q) ? C[(long long)(k0 + cr) * q + c0 + ccol] : 0.0;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int t = 0; t < kTileK; ++t) {
+        double av[4], cv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) av[i] = As[ty + 16 * i][t];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) cv[j] = Cs[t][tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], cv[j], acc[i][j]);
+      }
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const long long row = r0 + ty + 16 * i;
+    if (row >= n) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int col = c0 + tx + 16 * j;
+      if (col >= q) continue;
+      double v = alpha * acc[i][j];
+      if (Bm) v = fma(beta, Bm[row * q + col], v);
+      out[row * q + col] = v;
+    }
+  }
+}
+
+ks_status launch_combine(Problem &P, const double *A1, int k1, const double *C1,
+                         const double *A2, int k2, const double *C2, double alpha, double beta,
+                         const double *Bm, double *out, int q) {
+  dim3 grid((unsigned)((P.n + kTile - 1) / kTile), (unsigned)((q + kTile - 1) / kTile));
+  {
+    ProfScope ps_(P.stream, KP_COMBINE);
+    combine_kernel<<<grid, 256, 0, P.stream>>>(P.n, q, A1, k1, C1, A2, k2, C2, alpha, beta, Bm,
+                                                out);
+  }
+  KS_CUDA_TRY(cudaGetLastError());
+  return KS_OK;
+}
+
+__global__ void ortho_err_kernel(int p, const double *__restrict__ O, double *out) {
+  __shared__ double smem[33];
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    const int i = e / p, j = e % p;
+    const double d = O[e] - (i == j ? 1.0 : 0.0);
+    acc = fma(d, d, acc);
+  }
+  const double s = block_sum(acc, smem);
+  if (threadIdx.x == 0) *out = s;
+}
+
+ks_status launch_ortho_err(Problem &P, const double *O, double *out) {
+  {
+    ProfScope ps_(P.stream, KP_REDUCE);
+    ortho_err_kernel<<<1, kThreads, 0, P.stream>>>(P.p, O, out);
+  }
+  KS_CUDA_TRY(cudaGetLastError());
+  return KS_OK;
+}
+
+}  // namespace ks

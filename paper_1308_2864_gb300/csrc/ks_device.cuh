@@ -1,0 +1,112 @@
+// Device helpers: deterministic block reductions, a bounded software grid
+// barrier for cooperative launches, and uncached loads for data that other
+// blocks of the same launch have written.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "ks_internal.cuh"
+
+namespace ks {
+
+__device__ __forceinline__ double ldcg(const double *p) { return __ldcg(p); }
+
+// Sum over a block of blockDim.x (a multiple of 32, <= 1024) threads in a
+// fixed order: xor-butterfly inside each warp, then warp 0 adds the warp
+// sums in the same butterfly.  Every thread receives the result.
+__device__ __forceinline__ double block_sum(double v, double *smem /* >= 33 */) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) smem[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    double w = lane < nw ? smem[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    if (lane == 0) smem[32] = w;
+  }
+  __syncthreads();
+  double r = smem[32];
+  __syncthreads();
+  return r;
+}
+
+// Sum nb values src[0..nb) in a fixed order by the whole block (strided
+// partial sums in index order, then block_sum).  src may have been written
+// by other blocks of this launch, so it is read through L2.
+__device__ __forceinline__ double block_sum_array(const double *src, int nb, double *smem) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += ldcg(src + i);
+  return block_sum(acc, smem);
+}
+
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int *p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid-wide barrier for a cooperative launch (all blocks co-resident).
+// Every wait is bounded: a block that spins longer than kSpinLimit records
+// KS_ETIMEOUT in *status and leaves the barrier.  Returns false when the
+// status word holds an error, so that callers can return together.
+__device__ __forceinline__ bool grid_barrier(GridBarrier *bar, int *status) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
+    const unsigned int gen = ld_acquire_gpu(&bar->gen);
+    __threadfence();
+    const unsigned int arrived = atomicAdd(&bar->count, 1u);
+    if (arrived == nb - 1) {
+      atomicExch(&bar->count, 0u);
+      __threadfence();
+      atomicAdd(&bar->gen, 1u);
+    } else {
+      long long spins = 0;
+      unsigned int ns = 8;
+      while (ld_acquire_gpu(&bar->gen) == gen) {
+        if (++spins > kSpinLimit) {
+          atomicCAS(status, 0, (int)KS_ETIMEOUT);
+          break;
+        }
+        __nanosleep(ns);
+        if (ns < 256) ns <<= 1;
+      }
+    }
+    __threadfence();
+    s_ok = (*(volatile int *)status == 0);
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// 27-point Q1 stencil coefficient classes (see the stiffness/mass
+// construction in ks_stencil.cu): centre, face (6), edge (12), corner (8).
+struct StencilCoef {
+  double k0, kf, ke, kc;  // stiffness
+  double m0, mf, me, mc;  // mass
+};
+
+__host__ __device__ inline StencilCoef q1_coefficients(double h) {
+  // 1-D entries: K1 = (1/h)[-1, 2, -1], M1 = (h/6)[1, 4, 1]; the 3-D
+  // coefficient at an offset with j nonzero components is a sum of products
+  // of these (K = K1 M1 M1 + M1 K1 M1 + M1 M1 K1, M = M1 M1 M1).
+  const double k_0 = 2.0 / h, k_1 = -1.0 / h;
+  const double m_0 = 4.0 * h / 6.0, m_1 = h / 6.0;
+  StencilCoef c;
+  c.k0 = 3.0 * k_0 * m_0 * m_0;
+  c.kf = k_1 * m_0 * m_0 + 2.0 * m_1 * k_0 * m_0;
+  c.ke = 2.0 * k_1 * m_1 * m_0 + m_1 * m_1 * k_0;
+  c.kc = 3.0 * k_1 * m_1 * m_1;
+  c.m0 = m_0 * m_0 * m_0;
+  c.mf = m_1 * m_0 * m_0;
+  c.me = m_1 * m_1 * m_0;
+  c.mc = m_1 * m_1 * m_1;
+  return c;
+}
+
+}  // namespace ks

@@ -1,0 +1,186 @@
+// Internal declarations shared by the translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "ks.h"
+
+namespace ks {
+
+// ---------------------------------------------------------------- errors
+ks_status set_error(ks_status st, const char *fmt, ...);
+ks_status cuda_error(cudaError_t e, const char *where);
+
+#define KS_CUDA_TRY(call)                                              \
+  do {                                                                 \
+    cudaError_t e_ = (call);                                           \
+    if (e_ != cudaSuccess) return ::ks::cuda_error(e_, #call);         \
+  } while (0)
+
+#define KS_TRY(call)                                                   \
+  do {                                                                 \
+    ks_status s_ = (call);                                             \
+    if (s_ != KS_OK) return s_;                                        \
+  } while (0)
+
+// Device status word values beyond ks_status (bit flags are not used: the
+// first error wins).
+constexpr int kDevOk = 0;
+
+// Spin limit of every device-side wait (about a second with the back-off
+// used); after it the waiting block records KS_ETIMEOUT and returns.
+constexpr long long kSpinLimit = 1LL << 22;
+
+// ---------------------------------------------------------------- grid
+// Workspace of the software grid barrier used by cooperative kernels.
+struct GridBarrier {
+  unsigned int count;
+  unsigned int gen;
+};
+
+// Launch geometry of the cooperative CG kernel.
+constexpr int kCgThreads = 256;
+
+// Threads of generic one-dimensional kernels.
+constexpr int kThreads = 256;
+
+// Gram / update tiles (FP64): 64 x 64 output tile, 256 threads, 4 x 4 each.
+constexpr int kTile = 64;
+constexpr int kTileK = 16;
+
+// ---------------------------------------------------------------- state
+// Scalars kept on the device (indices into Problem::scal).
+enum Scalar : int {
+  SC_EKIN = 0,     // (f/2) sum X . KX
+  SC_EEXT,         // h^3 sum Vext rho
+  SC_EH,           // variational Hartree energy
+  SC_EXC,          // h^3 sum rho eps_xc
+  SC_EII,          // ion-ion energy
+  SC_DNORM2,       // ||D||_M^2
+  SC_BB_SS,        // tr(dX^T M dX)
+  SC_BB_SY,        // tr(dX^T M dD)
+  SC_BB_YY,        // tr(dD^T M dD)
+  SC_ORTHO,        // ||X^T M X - I||_F^2
+  SC_CG_ITERS,     // iterations of the last CG solve (as double)
+  SC_COUNT = 16
+};
+
+struct Problem {
+  // geometry and sizes
+  int N = 0, n = 0, p = 0, natoms = 0, xc = 0;
+  double L = 0, h = 0, rc = 0, occ = 0, cg_tol = 0;
+  int cg_maxit = 0;
+  std::vector<double> atoms_host;  // natoms x 4: x, y, z, Z
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0, sms = 0;
+  int cg_blocks = 0;               // cooperative grid of the CG kernel
+
+  // n-vectors
+  double *vext = nullptr, *rho = nullptr, *vH = nullptr, *veff = nullptr;
+  double *cg_r = nullptr, *cg_pa = nullptr, *cg_pb = nullptr, *cg_q = nullptr;
+  bool vH_valid = false;           // warm start available
+
+  // n x p blocks
+  static constexpr int kNBlocks = 13;
+  double *blk[kNBlocks] = {};
+
+  // p x p work (all FP64)
+  double *pp = nullptr;            // pool of small matrices
+  size_t pp_len = 0;
+
+  // reductions
+  double *partials = nullptr;      // Gram partial tiles and block partial sums
+  size_t partials_len = 0;
+  double *scal = nullptr;          // device scalars (SC_*)
+  double *scal_host = nullptr;     // pinned mirror
+  double *atoms_dev = nullptr;
+  double *thomas_w = nullptr;      // N pivots of the 1-D mass solve
+  GridBarrier *bar = nullptr;
+  int *dstatus = nullptr;          // device status word
+  int *dstatus_host = nullptr;     // pinned mirror
+
+  // last evaluation
+  double last_parts[5] = {0, 0, 0, 0, 0};
+  double last_E = 0;
+  int last_cg_iters = 0;
+
+  size_t bytes = 0;
+};
+
+size_t problem_bytes(int N, int p, int sms);
+
+// ---------------------------------------------------------------- profiling
+enum ProfClass : int {
+  KP_DENSITY = 0, KP_CG, KP_POTENTIAL, KP_HAMILTONIAN, KP_MASS, KP_MASS_INV,
+  KP_GRAM, KP_COMBINE, KP_SMALL, KP_REDUCE, KP_SETUP, KP_OTHER
+};
+// Counts `nlaunch` kernel launches and, when timing is on, brackets the
+// scope's launches with CUDA events on `s`.
+struct ProfScope {
+  ProfScope(cudaStream_t s, int cls, int nlaunch = 1);
+  ~ProfScope();
+  cudaStream_t stream;
+  int cls;
+  void *a;
+};
+// Accumulate the timings of completed launches (call after a stream sync).
+void prof_collect();
+
+// ---------------------------------------------------------------- kernels
+// ks_setup.cu
+ks_status launch_setup(Problem &P);
+// ks_density.cu: rho_k = f sum_i X_ki^2
+ks_status launch_density(Problem &P, const double *X, double *rho);
+// ks_cg.cu: K v = 4 pi h^3 rho; v in/out (warm if warm), r out
+ks_status launch_cg(Problem &P, const double *rho, double *v, double *r, bool warm);
+int cg_grid_blocks(int sms, int n);
+// ks_xc.cu: veff = vext + vH + v_xc(rho); energy partials; reduction helpers
+ks_status launch_potential(Problem &P, const double *rho, const double *vH, const double *r,
+                           double *veff, bool with_hartree);
+ks_status launch_reduce(Problem &P, const double *partials, int nchan, int nb, double *out,
+                        double scale = 1.0);
+// Blocks of the grid-stride reduction kernels (their partials are nchan x this).
+int reduce_blocks(const Problem &P, long long work);
+// ks_stencil.cu
+ks_status launch_hamiltonian(Problem &P, const double *X, const double *veff, double *EX,
+                             double *MX, double *ekin_out);
+ks_status launch_mass(Problem &P, const double *X, double *MX);
+// MD = M D; dnorm2 = sum D.MD; with prev != null also the BB traces.
+struct BBPrev { const double *X, *MX, *D, *MD; };
+ks_status launch_mass_dots(Problem &P, const double *D, double *MD, const double *X,
+                           const double *MX, const BBPrev *prev, double *out4);
+// ks_minv.cu: G = M^{-1} E
+ks_status launch_mass_inverse(Problem &P, const double *E, double *G);
+// ks_blas.cu
+// out (pa x qb) = A^T B with A n x pa, B n x qb (row-major, ld = pa, qb)
+ks_status launch_gram(Problem &P, const double *A, int pa, const double *B, int qb, double *out);
+// out (n x q) = alpha (A1 C1 + A2 C2) + beta Bm (A2/Bm may be null);
+// C1 k1 x q, C2 k2 x q.  out must not alias A1, A2 or Bm.
+ks_status launch_combine(Problem &P, const double *A1, int k1, const double *C1,
+                         const double *A2, int k2, const double *C2, double alpha, double beta,
+                         const double *Bm, double *out, int q);
+// sum of squares of (O - I) for a p x p O
+ks_status launch_ortho_err(Problem &P, const double *O, double *out);
+// ks_small.cu: small dense FP64 algebra in one CTA
+// QR step: R = I + tau^2 DMD (or R = O when DMD is null); L L^T = R;
+// C = L^{-T}; writes C1 = C and C2 = -tau C.
+ks_status launch_qr_factor(Problem &P, const double *DMD, const double *O, double tau,
+                           double *C1, double *C2);
+// Cayley step: builds N = [[A, O], [-B, -S]], solves (I + tau/2 N) P = [O; -S]
+// and writes C1 = I - tau P2 (p x p), C2 = -tau P1 (p x p), both for
+// X+ = X C1 + G C2.  A = X^T E_X, S = E_X^T X, B = E_X^T G, O = X^T M X.
+ks_status launch_cayley_factor(Problem &P, const double *A, const double *S, const double *B,
+                               const double *O, double tau, double *C1, double *C2);
+// Transpose a p x p matrix into out.
+ks_status launch_transpose(Problem &P, const double *A, double *out);
+
+}  // namespace ks
+
+struct ks_problem {
+  ks::Problem P;
+};

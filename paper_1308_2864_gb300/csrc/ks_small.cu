@@ -1,0 +1,229 @@
+// Small dense FP64 algebra of the retractions, one thread block each (the
+// p x p and 2p x 2p systems are serial in the paper too; here they stay on
+// the device so the iteration needs no host round trip for them):
+//   qr_factor:     Cholesky of Y^T M Y = I + tau^2 D^T M D (Prop. 3.1 in the
+//                  M metric; Alg. ChQR), then C = L^{-T}, giving
+//                  X+ = (X - tau D) L^{-T} = X C + D (-tau C)   (Eq. QR)
+//   cayley_factor: LU with partial pivoting of I + tau/2 V^T U (2p x 2p) and
+//                  the solve against V^T Y (Eq. WY3).
+#include "ks_device.cuh"
+
+namespace ks {
+
+constexpr int kSmallThreads = 1024;
+
+// Cholesky (lower) of the p x p matrix W in place, right-looking.  Returns
+// false (and records KS_ENOTPD) on a non-positive or non-finite pivot.
+__device__ bool block_cholesky(double *W, int p, int *status) {
+  __shared__ int s_fail;
+  if (threadIdx.x == 0) s_fail = 0;
+  __syncthreads();
+  for (int j = 0; j < p; ++j) {
+    if (threadIdx.x == 0) {
+      const double d = W[j * p + j];
+      if (!(d > 0.0) || !isfinite(d)) {
+        s_fail = 1;
+        atomicCAS(status, 0, (int)KS_ENOTPD);
+      } else {
+        W[j * p + j] = sqrt(d);
+      }
+    }
+    __syncthreads();
+    if (s_fail) return false;
+    const double djj = W[j * p + j];
+    for (int i = j + 1 + threadIdx.x; i < p; i += blockDim.x) W[i * p + j] /= djj;
+    __syncthreads();
+    // trailing lower triangle: W[i][k] -= W[i][j] W[k][j], j < k <= i
+    const int m = p - j - 1;
+    const int cnt = m * (m + 1) / 2;
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+      // map t to (i, k) with 0 <= k' <= i' < m
+      int ii = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+      while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
+      while (ii * (ii + 1) / 2 > t) --ii;
+      const int kk = t - ii * (ii + 1) / 2;
+      const int i = j + 1 + ii, k = j + 1 + kk;
+      W[i * p + k] = fma(-W[i * p + j], W[k * p + j], W[i * p + k]);
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
+// Linv = L^{-1} for lower-triangular L (forward substitution, one column
+// per thread).
+__device__ void block_tri_inverse(const double *L, double *Linv, int p) {
+  for (int c = threadIdx.x; c < p; c += blockDim.x) {
+    for (int i = 0; i < c; ++i) Linv[i * p + c] = 0.0;
+    Linv[c * p + c] = 1.0 / L[c * p + c];
+    for (int i = c + 1; i < p; ++i) {
+      double s = 0.0;
+      for (int k = c; k < i; ++k) s = fma(L[i * p + k], Linv[k * p + c], s);
+      Linv[i * p + c] = -s / L[i * p + i];
+    }
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kSmallThreads) qr_factor_kernel(int p, const double *DMD,
+                                                                  const double *O, double tau,
+                                                                  double *W, double *Linv,
+                                                                  double *C1, double *C2,
+                                                                  int *status) {
+  const double t2 = tau * tau;
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    const int i = e / p, j = e % p;
+    double r = O ? O[e] : (i == j ? 1.0 : 0.0);
+    if (DMD) r = fma(t2, DMD[e], r);
+    W[e] = r;
+  }
+  __syncthreads();
+  if (!block_cholesky(W, p, status)) return;
+  block_tri_inverse(W, Linv, p);
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    const int i = e / p, j = e % p;
+    const double c = Linv[j * p + i];      // (L^{-T})_{ij}
+    C1[e] = c;
+    if (C2) C2[e] = -tau * c;
+  }
+}
+
+ks_status launch_qr_factor(Problem &P, const double *DMD, const double *O, double tau,
+                           double *C1, double *C2) {
+  const int p = P.p;
+  double *W = P.pp, *Linv = P.pp + (size_t)p * p;
+  {
+    ProfScope ps_(P.stream, KP_SMALL);
+    qr_factor_kernel<<<1, kSmallThreads, 0, P.stream>>>(p, DMD, O, tau, W, Linv, C1, C2,
+                                                        P.dstatus);
+  }
+  KS_CUDA_TRY(cudaGetLastError());
+  return KS_OK;
+}
+
+// Solve (I + tau/2 N) P = R with N = [[A, O], [-B, -S]] and R = [O; -S]
+// (all p x p blocks, O = I when null), by Gaussian elimination with partial
+// pivoting on the augmented 2p x 3p matrix W.
+__global__ void __launch_bounds__(kSmallThreads) cayley_factor_kernel(
+    int p, const double *A, const double *S, const double *B, const double *O, double tau,
+    double *W, double *C1, double *C2, int *status) {
+  __shared__ double s_val[32];
+  __shared__ int s_idx[32];
+  __shared__ int s_piv;
+  __shared__ int s_fail;
+  const int n2 = 2 * p, w = 3 * p;
+  const double ht = 0.5 * tau;
+  for (int e = threadIdx.x; e < n2 * w; e += blockDim.x) {
+    const int i = e / w, j = e % w;
+    double v;
+    if (j < n2) {
+      const int bi = i / p, bj = j / p, ii = i % p, jj = j % p;
+      double nv;
+      if (bi == 0 && bj == 0) nv = A[ii * p + jj];
+      else if (bi == 0 && bj == 1) nv = O ? O[ii * p + jj] : (ii == jj ? 1.0 : 0.0);
+      else if (bi == 1 && bj == 0) nv = -B[ii * p + jj];
+      else nv = -S[ii * p + jj];
+      v = (i == j ? 1.0 : 0.0) + ht * nv;
+    } else {
+      const int jj = j - n2, ii = i % p;
+      if (i < p) v = O ? O[ii * p + jj] : (ii == jj ? 1.0 : 0.0);
+      else v = -S[ii * p + jj];
+    }
+    W[e] = v;
+  }
+  if (threadIdx.x == 0) s_fail = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int j = 0; j < n2; ++j) {
+    // pivot search over rows j..n2-1 (largest |W[i][j]|, lowest index on ties)
+    double best = -1.0;
+    int bi = n2;
+    for (int i = j + threadIdx.x; i < n2; i += blockDim.x) {
+      const double a = fabs(W[i * w + j]);
+      if (a > best) { best = a; bi = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) { s_val[warp] = best; s_idx[warp] = bi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double bb = -1.0;
+      int ib = n2;
+      for (int t = 0; t < (int)(blockDim.x >> 5); ++t)
+        if (s_val[t] > bb || (s_val[t] == bb && s_idx[t] < ib)) { bb = s_val[t]; ib = s_idx[t]; }
+      if (!(bb > 1e-300) || !isfinite(bb)) {
+        s_fail = 1;
+        atomicCAS(status, 0, (int)KS_ESINGULAR);
+      }
+      s_piv = ib;
+    }
+    __syncthreads();
+    if (s_fail) return;
+    const int pv = s_piv;
+    if (pv != j) {
+      for (int c = threadIdx.x; c < w; c += blockDim.x) {
+        const double t = W[j * w + c];
+        W[j * w + c] = W[pv * w + c];
+        W[pv * w + c] = t;
+      }
+      __syncthreads();
+    }
+    const double d = W[j * w + j];
+    const int rows = n2 - j - 1, cols = w - j - 1;
+    for (int t = threadIdx.x; t < rows * cols; t += blockDim.x) {
+      const int i = j + 1 + t / cols, c = j + 1 + t % cols;
+      W[i * w + c] = fma(-W[i * w + j] / d, W[j * w + c], W[i * w + c]);
+    }
+    __syncthreads();
+  }
+  // back substitution, one right-hand side column per thread
+  for (int c = threadIdx.x; c < p; c += blockDim.x) {
+    const int col = n2 + c;
+    for (int i = n2 - 1; i >= 0; --i) {
+      double s = W[i * w + col];
+      for (int k = i + 1; k < n2; ++k) s = fma(-W[i * w + k], W[k * w + col], s);
+      W[i * w + col] = s / W[i * w + i];
+    }
+  }
+  __syncthreads();
+  // X+ = X (I - tau P2) + G (-tau P1)
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    const int i = e / p, j = e % p;
+    const double p1 = W[i * w + n2 + j], p2 = W[(p + i) * w + n2 + j];
+    C1[e] = (i == j ? 1.0 : 0.0) - tau * p2;
+    C2[e] = -tau * p1;
+  }
+}
+
+ks_status launch_cayley_factor(Problem &P, const double *A, const double *S, const double *B,
+                               const double *O, double tau, double *C1, double *C2) {
+  {
+    ProfScope ps_(P.stream, KP_SMALL);
+    cayley_factor_kernel<<<1, kSmallThreads, 0, P.stream>>>(P.p, A, S, B, O, tau, P.pp, C1, C2,
+                                                            P.dstatus);
+  }
+  KS_CUDA_TRY(cudaGetLastError());
+  return KS_OK;
+}
+
+__global__ void transpose_kernel(int p, const double *A, double *out) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < p * p; e += gridDim.x * blockDim.x) {
+    const int i = e / p, j = e % p;
+    out[j * p + i] = A[e];
+  }
+}
+
+ks_status launch_transpose(Problem &P, const double *A, double *out) {
+  {
+    ProfScope ps_(P.stream, KP_OTHER);
+    transpose_kernel<<<(P.p * P.p + kThreads - 1) / kThreads, kThreads, 0, P.stream>>>(P.p, A, out);
+  }
+  KS_CUDA_TRY(cudaGetLastError());
+  return KS_OK;
+}
+
+}  // namespace ks

@@ -1,0 +1,244 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle on
+the same seeded inputs.  Deterministic steps are compared element by element
+at 1e-12 relative; the Hartree CG against its own tolerance; the full
+minimisation on final energies (1e-8 Ha) and invariants."""
+import math
+
+import numpy as np
+import pytest
+
+import ks_inputs as ki
+from oracle import energy as oe
+from oracle import fe as ofe
+from oracle import stiefel as ost
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REL = 1e-12
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def assert_rel(got, want, rel=REL, what=""):
+    got, want = np.asarray(got), np.asarray(want)
+    scale = max(np.abs(want).max(), 1e-300)
+    err = np.abs(got - want).max() / scale
+    assert err <= rel, f"{what}: max error {err:.3e} relative to max |want| > {rel:.1e}"
+
+
+def make(system, **kw):
+    import paper_1308_2864_gb300 as ks
+    return ks.Problem.from_system(system, **kw)
+
+
+# ragged sizes: n = 13^3 is not a multiple of any tile; p = 70 spans two
+# 64-wide tiles with a ragged tail; p = 5 is below a warp.
+SMALL = [
+    dict(N=13, L=7.0, natoms=2, p=5, Z=5.0, seed=3),
+    dict(N=11, L=6.0, natoms=3, p=70, Z=4.0, seed=4),
+]
+
+
+@pytest.fixture(params=SMALL, ids=["N13p5", "N11p70"])
+def case(request):
+    s = ki.small_system(**request.param)
+    model = oe.Model.from_system(s)
+    X = ost.m_orthonormalize(model, s.x0())
+    return s, model, X
+
+
+def test_vext_and_eii(case):
+    s, model, X = case
+    P = make(s)
+    assert_rel(host(P.step_vext()), model.vext(), what="vext")
+    assert P.step_eii() == pytest.approx(model.eii(), rel=1e-13)
+
+
+def test_density(case):
+    s, model, X = case
+    P = make(s)
+    assert_rel(host(P.step_density(dev(X))), oe.density(X, model.occ), what="rho")
+
+
+def test_hartree_cg(case):
+    s, model, X = case
+    P = make(s)
+    rho = oe.density(X, model.occ)
+    b = 4 * math.pi * model.h ** 3 * rho
+    v, r, it = P.step_hartree(dev(rho))
+    v = host(v)
+    # the oracle's own residual of the GPU potential meets the tolerance
+    res = b - ofe.apply_K(v, model.N, model.h)
+    assert np.linalg.norm(res) <= 1.05e-10 * np.linalg.norm(b)
+    assert np.allclose(host(r), res, atol=1e-13 * np.abs(b).max())
+    # same iteration count as plain CG from the same start, and the same answer
+    vo, ro, ito, ok = ofe.cg_solve(lambda x: ofe.apply_K(x, model.N, model.h), b, None, 1e-10, 10000)
+    assert ok and abs(it - ito) <= 1
+    assert_rel(v, vo, rel=1e-9, what="vH vs oracle CG")
+    assert_rel(v, ofe.poisson_exact(b, model.N, model.h), rel=1e-8, what="vH vs exact")
+    # warm start from the answer converges immediately
+    v2, _, it2 = P.step_hartree(dev(rho), dev(v), warm=True)
+    assert it2 <= 1
+
+
+def test_potential_and_energies(case):
+    s, model, X = case
+    P = make(s)
+    rho = oe.density(X, model.occ)
+    b = 4 * math.pi * model.h ** 3 * rho
+    vH = ofe.poisson_exact(b, model.N, model.h)
+    rng = np.random.default_rng(1)
+    resid = 1e-9 * rng.standard_normal(rho.shape)
+    veff, e = P.step_potential(dev(rho), dev(vH), dev(resid))
+    eps, vxc = oe.lda(rho, model.xc)
+    h3 = model.h ** 3
+    assert_rel(host(veff), model.vext() + vH + vxc, what="veff")
+    assert e[0] == pytest.approx(h3 * model.vext() @ rho, rel=REL)
+    assert e[1] == pytest.approx(0.5 * h3 * vH @ rho + vH @ resid / (8 * math.pi), rel=REL)
+    assert e[2] == pytest.approx(h3 * rho @ eps, rel=REL)
+
+
+def test_hamiltonian_stencil(case):
+    s, model, X = case
+    P = make(s)
+    rng = np.random.default_rng(2)
+    veff = rng.standard_normal(model.n)
+    EX, MX, kin = P.step_hamiltonian(dev(X), dev(veff))
+    KX = ofe.apply_K(X, model.N, model.h)
+    want = model.occ * KX + 2 * model.occ * model.h ** 3 * veff[:, None] * X
+    assert_rel(host(EX), want, what="E_X")
+    assert_rel(host(MX), ofe.apply_M(X, model.N, model.h), what="MX")
+    assert kin == pytest.approx(0.5 * model.occ * np.sum(X * KX), rel=REL)
+
+
+def test_mass_and_inverse(case):
+    s, model, X = case
+    P = make(s)
+    rng = np.random.default_rng(3)
+    E = rng.standard_normal(X.shape)
+    assert_rel(host(P.step_mass(dev(E))), ofe.apply_M(E, model.N, model.h), what="M E")
+    assert_rel(host(P.step_mass_inverse(dev(E))), ofe.mass_inverse(E, model.N, model.h),
+               rel=1e-11, what="M^-1 E")
+
+
+def test_gram_and_combine(case):
+    s, model, X = case
+    P = make(s)
+    rng = np.random.default_rng(4)
+    A = rng.standard_normal(X.shape)
+    B = rng.standard_normal(X.shape)
+    assert_rel(host(P.step_gram(dev(A), dev(B))), A.T @ B, what="A^T B")
+    C1 = rng.standard_normal((s.p, s.p))
+    C2 = rng.standard_normal((s.p, s.p))
+    out = P.step_combine(dev(A), dev(C1), dev(B), dev(C2), alpha=-0.5, beta=2.0, Bm=dev(X))
+    assert_rel(host(out), -0.5 * (A @ C1 + B @ C2) + 2.0 * X, what="combine")
+
+
+def test_energy_grad_and_projected_gradient(case):
+    s, model, X = case
+    P = make(s, cg_tol=1e-13)
+    E, EX, D, g = P.energy_grad(dev(X), want_ex=True, want_d=True)
+    ref = oe.evaluate(model, X)
+    pt = ost.project(model, X, ref)
+    assert E == pytest.approx(ref.E, rel=1e-12)
+    assert_rel(host(EX), ref.EX, rel=1e-11, what="E_X")
+    assert_rel(host(D), pt.D, rel=1e-10, what="D")
+    assert g == pytest.approx(pt.dnorm, rel=1e-10)
+    parts = P.energy_parts()
+    for got, key in zip(parts, ["kinetic", "external", "hartree", "xc", "ion"]):
+        assert got == pytest.approx(ref.parts[key], rel=1e-11, abs=1e-12)
+
+
+@pytest.mark.parametrize("kind", ["qr", "cayley"])
+def test_retract(case, kind):
+    import paper_1308_2864_gb300 as ks
+    s, model, X = case
+    P = make(s)
+    ref = oe.evaluate(model, X)
+    pt = ost.project(model, X, ref)
+    for tau in (1e-3, 0.05):
+        got = host(P.retract(ks.KS_QR if kind == "qr" else ks.KS_CAYLEY, dev(X), dev(ref.EX), tau))
+        want = (ost.retract_qr if kind == "qr" else ost.retract_cayley)(model, pt, tau)
+        assert_rel(got, want, rel=1e-11, what=f"{kind} tau={tau}")
+        assert ost.ortho_error(model, got) < 1e-12
+
+
+def test_orthonormalize(case):
+    s, model, X = case
+    P = make(s)
+    X0 = s.x0()
+    got = host(P.orthonormalize(dev(X0)))
+    assert_rel(got, ost.m_orthonormalize(model, X0), rel=1e-11, what="CholQR2")
+    assert ost.ortho_error(model, got) < 1e-13
+
+
+@pytest.mark.parametrize("retraction", ["qr", "cayley"])
+def test_minimize_matches_oracle(retraction):
+    # A case the oracle brute-force pins (resolved pseudo-atoms, rc = 1):
+    # both sides converge to the same KKT point from the same start.
+    s = ki.small_system(N=10, L=7.0, natoms=2, p=2, Z=1.0, seed=7)
+    s.rc = 1.0
+    model = oe.Model.from_system(s)
+    ref = ost.minimize(model, s.x0(), ost.Options(retraction=retraction, gtol=1e-8, maxit=2000))
+    assert ref.converged
+    P = make(s)
+    X = dev(s.x0())
+    r = P.minimize(X, retraction=retraction, gtol=1e-8, maxit=2000)
+    assert r["status"] == 0 and r["gradnorm"] <= 1e-8
+    assert r["E"] == pytest.approx(ref.E, abs=1e-8)
+    Xg = host(X)
+    assert ost.ortho_error(model, Xg) < 1e-12
+    # invariants: density and the Lagrange-multiplier spectrum
+    assert_rel(oe.density(Xg, 2.0), oe.density(ref.X, 2.0), rel=1e-5, what="rho")
+    lam_g = np.linalg.eigvalsh(Xg.T @ oe.evaluate(model, Xg).EX)
+    lam_o = np.linalg.eigvalsh(ref.X.T @ ref.point.ev.EX)
+    assert np.allclose(lam_g, lam_o, atol=1e-6)
+
+
+def test_c1_trajectory_matches_oracle_early():
+    # Config c1 (24^3, 2 atoms, p = 4, Slater, Cayley): the first 25
+    # iterations follow the oracle's trajectory closely (BB steps amplify
+    # rounding only slowly at the start).
+    s = ki.config_c1()
+    model = oe.Model.from_system(s)
+    ref = ost.minimize(model, s.x0(), ost.Options(retraction="cayley", maxit=25))
+    P = make(s)
+    r = P.minimize(dev(s.x0()), retraction="cayley", maxit=25)
+    assert r["iters"] == 25
+    assert r["E"] == pytest.approx(ref.E, rel=1e-7)
+    assert r["gradnorm"] == pytest.approx(ref.dnorm, rel=1e-4)
+
+
+def test_host_entry_point_matches_device_entry_point():
+    s = ki.small_system(N=9, L=6.0, natoms=1, p=3, Z=6.0, seed=2)
+    P = make(s)
+    Xh = np.ascontiguousarray(s.x0())
+    rh = P.minimize_host(Xh, maxit=15)
+    Xd = dev(s.x0())
+    rd = P.minimize(Xd, maxit=15)
+    assert rh["E"] == rd["E"]
+    assert np.array_equal(Xh, host(Xd))
+
+
+def test_invalid_arguments_are_reported():
+    import paper_1308_2864_gb300 as ks
+    with pytest.raises(ks.KSError) as e:
+        ks.Problem(N=1, L=1.0, atoms=np.zeros((0, 3)), Z=np.zeros(0), p=1)
+    assert e.value.status == ks.KS_EINVAL
+
+
+def test_cg_limit_reports_noconv():
+    import paper_1308_2864_gb300 as ks
+    s = ki.small_system(N=12, L=6.0, natoms=1, p=2, Z=4.0, seed=1)
+    P = make(s, cg_maxit=1)
+    X = ost.m_orthonormalize(oe.Model.from_system(s), s.x0())
+    with pytest.raises(ks.KSError) as e:
+        P.step_hartree(P.step_density(dev(X)))
+    assert e.value.status == ks.KS_ENOCONV
