@@ -70,8 +70,11 @@ typedef struct {
   int xc;             /* KS_XC_SLATER or KS_XC_SLATER_PZ81 */
   double cg_tol;      /* Hartree CG: ||r||_2 <= cg_tol ||b||_2 (1e-10) */
   int cg_maxit;       /* Hartree CG iteration limit */
-  int precision;      /* KS_FP64 (KS_MIXED is reserved) */
+  int precision;      /* KS_FP64 or KS_MIXED; informative only: the precision of a
+                         minimisation is chosen by ks_opts.precision */
   void *stream;       /* cudaStream_t to issue work on; NULL = library-owned */
+  int cg_precond;     /* 1: precondition the Hartree CG with the FP32 sine-basis inverse
+                         of K (default); 0: plain CG */
 } ks_problem_desc;
 
 /* Parameters of Alg. ConOptM (the paper fixes none of their values). */
@@ -88,6 +91,14 @@ typedef struct {
   int max_backtrack;  /* backtracks per iteration before accepting (10) */
   double ortho_tol;   /* re-orthonormalise when ||X^T M X - I||_F > ortho_tol (1e-12) */
   int ortho_every;    /* QR path: check ||X^T M X - I|| every this many iterations (20) */
+  int verbose;        /* > 0: print E, ||D||_M and tau to stderr every `verbose` iterations (0) */
+  int precision;      /* KS_FP64, or KS_MIXED: FP32 orbital blocks until ||D||_M <= polish_gtol
+                         (or no progress for stall_iters iterations), then an FP64 polish
+                         to gtol; the Hartree solve, energy sums and p x p algebra are FP64
+                         in both (KS_FP64) */
+  double polish_gtol; /* switch from the FP32 phase to the FP64 polish (1e-4) */
+  int stall_iters;    /* FP32 phase: stop after this many iterations without a 0.1 %
+                         improvement of the best ||D||_M (200) */
 } ks_opts;
 
 typedef struct {
@@ -100,6 +111,9 @@ typedef struct {
   int backtracks;     /* total backtracking steps */
   int status;         /* ks_status of the run (KS_ENOCONV when maxit was hit) */
   double seconds;     /* wall time of the call */
+  int mixed_iters;    /* KS_MIXED: iterations of the FP32 phase */
+  double mixed_gradnorm; /* KS_MIXED: ||D||_M at the end of the FP32 phase */
+  double mixed_E;     /* KS_MIXED: energy at the end of the FP32 phase */
 } ks_result;
 
 /* Defaults listed in ks_opts. */

@@ -37,9 +37,19 @@ XC_SLATER = 0
 XC_SLATER_PZ81 = 1
 
 # Perdew-Zunger (1981) parametrisation of the Ceperley-Alder correlation
-# energy, unpolarised gas, in hartree.
+# energy, unpolarised gas, in hartree.  gamma, beta1, beta2 (r_s >= 1) and
+# A, B (r_s < 1) are the published values.  The published C = 0.0020 and
+# D = -0.0116 are rounded values of the coefficients that make eps_c and
+# d eps_c / d r_s continuous at r_s = 1; rounded, they leave a 3.2e-5 Ha jump
+# in eps_c there, which makes the discrete energy discontinuous.  C and D are
+# therefore taken from the two continuity conditions:
+#   B + D = gamma / (1 + beta1 + beta2)
+#   A + C + D = -gamma (beta1/2 + beta2) / (1 + beta1 + beta2)^2
 PZ_GAMMA, PZ_BETA1, PZ_BETA2 = -0.1423, 1.0529, 0.3334
-PZ_A, PZ_B, PZ_C, PZ_D = 0.0311, -0.048, 0.0020, -0.0116
+PZ_A, PZ_B = 0.0311, -0.048
+_PZ_DEN1 = 1.0 + PZ_BETA1 + PZ_BETA2
+PZ_D = PZ_GAMMA / _PZ_DEN1 - PZ_B
+PZ_C = -PZ_GAMMA * (0.5 * PZ_BETA1 + PZ_BETA2) / (_PZ_DEN1 * _PZ_DEN1) - PZ_A - PZ_D
 RHO_FLOOR = 1e-30
 
 

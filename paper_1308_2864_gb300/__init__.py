@@ -38,7 +38,7 @@ class ProblemDesc(ctypes.Structure):
                 ("R", ctypes.POINTER(ctypes.c_double)), ("Z", ctypes.POINTER(ctypes.c_double)),
                 ("rc", ctypes.c_double), ("p", ctypes.c_int), ("occ", ctypes.c_double),
                 ("xc", ctypes.c_int), ("cg_tol", ctypes.c_double), ("cg_maxit", ctypes.c_int),
-                ("precision", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("precision", ctypes.c_int), ("stream", ctypes.c_void_p), ("cg_precond", ctypes.c_int)]
 
 
 class Opts(ctypes.Structure):
@@ -46,14 +46,18 @@ class Opts(ctypes.Structure):
                 ("tau0", ctypes.c_double), ("rho1", ctypes.c_double), ("delta", ctypes.c_double),
                 ("eta", ctypes.c_double), ("tau_min", ctypes.c_double), ("tau_max", ctypes.c_double),
                 ("max_backtrack", ctypes.c_int), ("ortho_tol", ctypes.c_double),
-                ("ortho_every", ctypes.c_int)]
+                ("ortho_every", ctypes.c_int), ("verbose", ctypes.c_int),
+                ("precision", ctypes.c_int), ("polish_gtol", ctypes.c_double),
+                ("stall_iters", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
     _fields_ = [("E", ctypes.c_double), ("gradnorm", ctypes.c_double), ("ortho_err", ctypes.c_double),
                 ("E_parts", ctypes.c_double * 5), ("iters", ctypes.c_int),
                 ("cg_iters_total", ctypes.c_int), ("backtracks", ctypes.c_int),
-                ("status", ctypes.c_int), ("seconds", ctypes.c_double)]
+                ("status", ctypes.c_int), ("seconds", ctypes.c_double),
+                ("mixed_iters", ctypes.c_int), ("mixed_gradnorm", ctypes.c_double),
+                ("mixed_E", ctypes.c_double)]
 
 
 _LIB = None
@@ -137,6 +141,8 @@ def default_opts(**kw) -> Opts:
     for k, v in kw.items():
         if k == "retraction" and isinstance(v, str):
             v = KS_QR if v == "qr" else KS_CAYLEY
+        if k == "precision" and isinstance(v, str):
+            v = KS_FP64 if v == "fp64" else KS_MIXED
         if not hasattr(o, k):
             raise KeyError(f"unknown option {k}")
         setattr(o, k, v)
@@ -167,7 +173,8 @@ def profile_stop() -> dict:
 def result_dict(r: Result) -> dict:
     return {"E": r.E, "gradnorm": r.gradnorm, "ortho_err": r.ortho_err,
             "E_parts": list(r.E_parts), "iters": r.iters, "cg_iters_total": r.cg_iters_total,
-            "backtracks": r.backtracks, "status": r.status, "seconds": r.seconds}
+            "backtracks": r.backtracks, "status": r.status, "seconds": r.seconds,
+            "mixed_iters": r.mixed_iters, "mixed_gradnorm": r.mixed_gradnorm, "mixed_E": r.mixed_E}
 
 
 class Problem:
@@ -175,7 +182,7 @@ class Problem:
 
     def __init__(self, N: int, L: float, atoms, Z, p: int, rc: float = 0.5, occ: float = 2.0,
                  xc: int = KS_XC_SLATER_PZ81, cg_tol: float = 1e-10, cg_maxit: int = 20000,
-                 stream=None):
+                 stream=None, cg_precond: bool = True):
         import torch
         lib = load_library()
         if not torch.cuda.is_available():
@@ -193,6 +200,7 @@ class Problem:
         d.rc, d.p, d.occ, d.xc = rc, p, occ, xc
         d.cg_tol, d.cg_maxit, d.precision = cg_tol, cg_maxit, KS_FP64
         d.stream = ctypes.c_void_p(stream.cuda_stream)
+        d.cg_precond = 1 if cg_precond else 0
         self.desc = d
         h = ctypes.c_void_p()
         _check(lib.ks_problem_create(ctypes.byref(d), ctypes.byref(h)))

@@ -50,12 +50,13 @@ static size_t gram_partials_len(int p, int sms) {
 
 size_t problem_bytes(int N, int p, int sms) {
   const size_t n = (size_t)N * N * N;
-  size_t b = 8 * n * sizeof(double);                                  // n-vectors
+  size_t b = 9 * n * sizeof(double) + 2 * n * sizeof(float);          // n-vectors
+  b += ((size_t)N * N + 2 * N) * sizeof(float);                      // sine basis
   b += (size_t)Problem::kNBlocks * n * p * sizeof(double);            // n x p blocks
   b += (size_t)S_COUNT * p * p * sizeof(double);                      // small matrices
   size_t part = gram_partials_len(p, sms);
   const size_t red = (size_t)4 * 8 * sms;
-  const size_t cg = (size_t)3 * 2 * sms;
+  const size_t cg = (size_t)4 * 2 * sms;
   if (red > part) part = red;
   if (cg > part) part = cg;
   b += part * sizeof(double);
@@ -73,7 +74,8 @@ static ks_status validate(const ks_problem_desc *d) {
     return set_error(KS_EINVAL, "bad atom arrays");
   if (!(d->rc > 0.0)) return set_error(KS_EINVAL, "rc must be positive");
   if (d->xc != KS_XC_SLATER && d->xc != KS_XC_SLATER_PZ81) return set_error(KS_EINVAL, "bad xc");
-  if (d->precision != KS_FP64) return set_error(KS_EINVAL, "only KS_FP64 is available");
+  if (d->precision != KS_FP64 && d->precision != KS_MIXED)
+    return set_error(KS_EINVAL, "bad precision");
   if (!(d->cg_tol > 0.0) || d->cg_maxit < 1) return set_error(KS_EINVAL, "bad CG parameters");
   return KS_OK;
 }
@@ -81,6 +83,7 @@ static ks_status validate(const ks_problem_desc *d) {
 static void free_problem(Problem &P) {
   auto f = [](void *q) { if (q) cudaFree(q); };
   f(P.vext); f(P.rho); f(P.vH); f(P.veff); f(P.cg_r); f(P.cg_pa); f(P.cg_pb); f(P.cg_q);
+  f(P.cg_z); f(P.cg_t1); f(P.cg_t2); f(P.dst_phi); f(P.dst_kap); f(P.dst_mu);
   for (auto &b : P.blk) f(b);
   f(P.pp); f(P.partials); f(P.scal); f(P.atoms_dev); f(P.thomas_w); f(P.bar); f(P.dstatus);
   if (P.scal_host) cudaFreeHost(P.scal_host);
@@ -123,13 +126,19 @@ static ks_status sync_scalars(Problem &P) {
 }
 
 // ---------------------------------------------------------------- phases
+// Typed view of the n x p block `b` (blocks hold FP64 capacity; the mixed
+// phase stores FP32 values in them).
+template <typename T>
+static T *blk(Problem &P, int b) { return reinterpret_cast<T *>(P.blk[b]); }
+
 // Energy at X: density, Hartree CG (warm-started when a previous potential
 // exists), potential and energy sums, Hamiltonian stencil (E_X, M X).
-static ks_status evaluate(Problem &P, const double *X, double *EX, double *MX, double *E) {
-  KS_TRY(launch_density(P, X, P.rho));
+template <typename T>
+static ks_status evaluate(Problem &P, const T *X, T *EX, T *MX, double *E) {
+  KS_TRY(launch_density<T>(P, X, P.rho));
   KS_TRY(launch_cg(P, P.rho, P.vH, P.cg_r, P.vH_valid));
   KS_TRY(launch_potential(P, P.rho, P.vH, P.cg_r, P.veff, true));
-  KS_TRY(launch_hamiltonian(P, X, P.veff, EX, MX, P.scal + SC_EKIN));
+  KS_TRY(launch_hamiltonian<T>(P, X, P.veff, EX, MX, P.scal + SC_EKIN));
   ks_status st = sync_scalars(P);
   if (st != KS_OK) {
     P.vH_valid = false;
@@ -156,21 +165,21 @@ struct Traces {
 // Projected gradient at X (Eq. def-nablaE in the M metric):
 // G = M^{-1} E_X, S = E_X^T X, D = G - X S, MD = M D, ||D||_M^2, the BB
 // traces against `prev`, and the Grams the retraction needs.
-static ks_status project(Problem &P, int retraction, const double *X, const double *EX,
-                         const double *MX, double *D, double *MD, const BBPrev *prev,
-                         Traces *tr) {
+template <typename T>
+static ks_status project(Problem &P, int retraction, const T *X, const T *EX, const T *MX, T *D,
+                         T *MD, const BBPrevT<T> *prev, Traces *tr) {
   const int p = P.p;
-  double *G = P.blk[B_G];
-  KS_TRY(launch_mass_inverse(P, EX, G));
-  KS_TRY(launch_gram(P, EX, p, X, p, sm(P, S_S)));
-  KS_TRY(launch_combine(P, X, p, sm(P, S_S), nullptr, 0, nullptr, -1.0, 1.0, G, D, p));
-  KS_TRY(launch_mass_dots(P, D, MD, X, MX, prev, P.scal + SC_DNORM2));
+  T *G = blk<T>(P, B_G);
+  KS_TRY(launch_mass_inverse<T>(P, EX, G));
+  KS_TRY(launch_gram<T>(P, EX, p, X, p, sm(P, S_S)));
+  KS_TRY(launch_combine<T>(P, X, p, sm(P, S_S), nullptr, 0, nullptr, -1.0, 1.0, G, D, p));
+  KS_TRY(launch_mass_dots<T>(P, D, MD, X, MX, prev, P.scal + SC_DNORM2));
   if (retraction == KS_QR) {
-    KS_TRY(launch_gram(P, D, p, MD, p, sm(P, S_DMD)));
+    KS_TRY(launch_gram<T>(P, D, p, MD, p, sm(P, S_DMD)));
   } else {
     KS_TRY(launch_transpose(P, sm(P, S_S), sm(P, S_A)));
-    KS_TRY(launch_gram(P, EX, p, G, p, sm(P, S_B)));
-    KS_TRY(launch_gram(P, X, p, MX, p, sm(P, S_O)));
+    KS_TRY(launch_gram<T>(P, EX, p, G, p, sm(P, S_B)));
+    KS_TRY(launch_gram<T>(P, X, p, MX, p, sm(P, S_O)));
   }
   KS_TRY(sync_scalars(P));
   tr->dnorm2 = P.scal_host[SC_DNORM2];
@@ -184,40 +193,44 @@ static ks_status project(Problem &P, int retraction, const double *X, const doub
 }
 
 // X+ from X along -D with step tau (uses the Grams left by project()).
-static ks_status retract(Problem &P, int retraction, const double *X, const double *D,
-                         double tau, double *Xout) {
+template <typename T>
+static ks_status retract(Problem &P, int retraction, const T *X, const T *D, double tau,
+                         T *Xout) {
   const int p = P.p;
   if (retraction == KS_QR) {
     KS_TRY(launch_qr_factor(P, sm(P, S_DMD), nullptr, tau, sm(P, S_C1), sm(P, S_C2)));
-    KS_TRY(launch_combine(P, X, p, sm(P, S_C1), D, p, sm(P, S_C2), 1.0, 0.0, nullptr, Xout, p));
+    KS_TRY(launch_combine<T>(P, X, p, sm(P, S_C1), D, p, sm(P, S_C2), 1.0, 0.0, nullptr, Xout, p));
   } else {
     KS_TRY(launch_cayley_factor(P, sm(P, S_A), sm(P, S_S), sm(P, S_B), sm(P, S_O), tau,
                                 sm(P, S_C1), sm(P, S_C2)));
-    KS_TRY(launch_combine(P, X, p, sm(P, S_C1), P.blk[B_G], p, sm(P, S_C2), 1.0, 0.0, nullptr,
-                          Xout, p));
+    KS_TRY(launch_combine<T>(P, X, p, sm(P, S_C1), blk<T>(P, B_G), p, sm(P, S_C2), 1.0, 0.0,
+                             nullptr, Xout, p));
   }
   return KS_OK;
 }
 
 // Cholesky QR in the M inner product, `passes` times; X is updated in place
-// (tmp is an n x p scratch block, MX receives M X of the result).
-static ks_status orthonormalize(Problem &P, double *X, double *tmp, double *MX, int passes) {
+// (tmp is an n x p scratch block, MX receives M X of the result).  The Gram
+// and the factor are FP64 in both precisions.
+template <typename T>
+static ks_status orthonormalize(Problem &P, T *X, T *tmp, T *MX, int passes) {
   const int p = P.p;
   for (int k = 0; k < passes; ++k) {
-    KS_TRY(launch_mass(P, X, MX));
-    KS_TRY(launch_gram(P, X, p, MX, p, sm(P, S_O)));
+    KS_TRY(launch_mass<T>(P, X, MX));
+    KS_TRY(launch_gram<T>(P, X, p, MX, p, sm(P, S_O)));
     KS_TRY(launch_qr_factor(P, nullptr, sm(P, S_O), 0.0, sm(P, S_C1), nullptr));
-    KS_TRY(launch_combine(P, X, p, sm(P, S_C1), nullptr, 0, nullptr, 1.0, 0.0, nullptr, tmp, p));
-    KS_CUDA_TRY(cudaMemcpyAsync(X, tmp, (size_t)P.n * p * sizeof(double),
-                                cudaMemcpyDeviceToDevice, P.stream));
+    KS_TRY(launch_combine<T>(P, X, p, sm(P, S_C1), nullptr, 0, nullptr, 1.0, 0.0, nullptr, tmp, p));
+    KS_CUDA_TRY(cudaMemcpyAsync(X, tmp, (size_t)P.n * p * sizeof(T), cudaMemcpyDeviceToDevice,
+                                P.stream));
   }
-  KS_TRY(launch_mass(P, X, MX));
+  KS_TRY(launch_mass<T>(P, X, MX));
   return sync_scalars(P);
 }
 
 // ||X^T M X - I||_F
-static ks_status ortho_error(Problem &P, const double *X, const double *MX, double *err) {
-  KS_TRY(launch_gram(P, X, P.p, MX, P.p, sm(P, S_T)));
+template <typename T>
+static ks_status ortho_error(Problem &P, const T *X, const T *MX, double *err) {
+  KS_TRY(launch_gram<T>(P, X, P.p, MX, P.p, sm(P, S_T)));
   KS_TRY(launch_ortho_err(P, sm(P, S_T), P.scal + SC_ORTHO));
   KS_TRY(sync_scalars(P));
   *err = std::sqrt(P.scal_host[SC_ORTHO]);
@@ -238,38 +251,52 @@ static double bb_step(int k, const Traces &t, const ks_opts &o) {
   return tau;
 }
 
-static ks_status minimize_device(Problem &P, double *X_inout, const ks_opts &o, ks_result *res) {
-  const auto t0 = std::chrono::steady_clock::now();
+struct PhaseResult {
+  double E = 0, dnorm = 0;
+  int iters = 0, cg = 0, backtracks = 0;
+  bool stalled = false;
+};
+
+// One run of Alg. ConOptM in storage precision T from the block Xstart
+// (copied in, then M-orthonormalised) until ||D||_M <= gtol, maxit
+// iterations, or -- when stall > 0 -- no 0.1 % improvement of the best
+// ||D||_M for `stall` iterations.  The final iterate is copied to Xend.
+template <typename T>
+static ks_status run_phase(Problem &P, const T *Xstart, T *Xend, const ks_opts &o, double gtol,
+                           int maxit, int stall, int first_k, double ortho_tol,
+                           PhaseResult *out) {
   const int p = P.p;
-  const size_t bytes = (size_t)P.n * p * sizeof(double);
+  const size_t bytes = (size_t)P.n * p * sizeof(T);
   int ix[3] = {B_X0, B_X1, B_X2};        // cur, prev, trial
   int imx[3] = {B_MX0, B_MX1, B_MX2};
   int iex[2] = {B_EX0, B_EX1};           // cur, trial
   int id[2] = {B_D0, B_D1};              // cur, prev
   int imd[2] = {B_MD0, B_MD1};
-  auto X = [&](int s) { return P.blk[ix[s]]; };
-  auto MX = [&](int s) { return P.blk[imx[s]]; };
-  auto EX = [&](int s) { return P.blk[iex[s]]; };
-  auto D = [&](int s) { return P.blk[id[s]]; };
-  auto MD = [&](int s) { return P.blk[imd[s]]; };
+  auto X = [&](int s) { return blk<T>(P, ix[s]); };
+  auto MX = [&](int s) { return blk<T>(P, imx[s]); };
+  auto EX = [&](int s) { return blk<T>(P, iex[s]); };
+  auto D = [&](int s) { return blk<T>(P, id[s]); };
+  auto MD = [&](int s) { return blk<T>(P, imd[s]); };
 
-  KS_CUDA_TRY(cudaMemcpyAsync(X(0), X_inout, bytes, cudaMemcpyDeviceToDevice, P.stream));
-  KS_TRY(orthonormalize(P, X(0), X(2), MX(0), 2));
+  KS_CUDA_TRY(cudaMemcpyAsync(X(0), Xstart, bytes, cudaMemcpyDeviceToDevice, P.stream));
+  KS_TRY(orthonormalize<T>(P, X(0), X(2), MX(0), 2));
   double E = 0;
-  KS_TRY(evaluate(P, X(0), EX(0), MX(0), &E));
+  KS_TRY(evaluate<T>(P, X(0), EX(0), MX(0), &E));
+  int cg_total = P.last_cg_iters;
   Traces tr;
-  KS_TRY(project(P, o.retraction, X(0), EX(0), MX(0), D(0), MD(0), nullptr, &tr));
+  KS_TRY(project<T>(P, o.retraction, X(0), EX(0), MX(0), D(0), MD(0), nullptr, &tr));
   double C = E, Q = 1.0;
   bool have_prev = false;
-  int k = 0, backtracks = 0, cg_total = P.last_cg_iters;
-  ks_status status = KS_OK;
-  while (std::sqrt(std::fmax(tr.dnorm2, 0.0)) > o.gtol && k < o.maxit) {
-    double tau = have_prev ? bb_step(k, tr, o) : o.tau0;
+  int k = 0, backtracks = 0, last_improve = 0;
+  double best = std::sqrt(std::fmax(tr.dnorm2, 0.0));
+  bool stalled = false;
+  while (std::sqrt(std::fmax(tr.dnorm2, 0.0)) > gtol && k < maxit) {
+    double tau = have_prev ? bb_step(first_k + k, tr, o) : o.tau0;
     int h = 0;
     double Et = 0;
     for (;;) {
-      KS_TRY(retract(P, o.retraction, X(0), D(0), tau, X(2)));
-      KS_TRY(evaluate(P, X(2), EX(1), MX(2), &Et));
+      KS_TRY(retract<T>(P, o.retraction, X(0), D(0), tau, X(2)));
+      KS_TRY(evaluate<T>(P, X(2), EX(1), MX(2), &Et));
       cg_total += P.last_cg_iters;
       if (Et <= C - o.rho1 * tau * tr.dnorm2 || h == o.max_backtrack) break;
       tau *= o.delta;
@@ -290,36 +317,89 @@ static ks_status minimize_device(Problem &P, double *X_inout, const ks_opts &o, 
     E = Et;
     ++k;
     bool reortho = false;
-    if (o.retraction == KS_CAYLEY || (o.ortho_every > 0 && k % o.ortho_every == 0)) {
+    if (o.retraction == KS_CAYLEY || sizeof(T) == 4 ||
+        (o.ortho_every > 0 && k % o.ortho_every == 0)) {
       double oerr = 0;
-      KS_TRY(ortho_error(P, X(0), MX(0), &oerr));
-      reortho = oerr > o.ortho_tol;
+      KS_TRY(ortho_error<T>(P, X(0), MX(0), &oerr));
+      reortho = oerr > ortho_tol;
     }
     if (reortho) {
-      KS_TRY(orthonormalize(P, X(0), X(2), MX(0), 1));
-      KS_TRY(evaluate(P, X(0), EX(0), MX(0), &E));
+      KS_TRY(orthonormalize<T>(P, X(0), X(2), MX(0), 1));
+      KS_TRY(evaluate<T>(P, X(0), EX(0), MX(0), &E));
       cg_total += P.last_cg_iters;
     }
-    BBPrev prev{X(1), MX(1), D(1), MD(1)};
-    KS_TRY(project(P, o.retraction, X(0), EX(0), MX(0), D(0), MD(0), &prev, &tr));
+    BBPrevT<T> prev{X(1), MX(1), D(1), MD(1)};
+    KS_TRY(project<T>(P, o.retraction, X(0), EX(0), MX(0), D(0), MD(0), &prev, &tr));
     have_prev = true;
+    const double dn = std::sqrt(std::fmax(tr.dnorm2, 0.0));
+    if (dn < 0.999 * best) {
+      best = dn;
+      last_improve = k;
+    } else if (stall > 0 && k - last_improve >= stall) {
+      stalled = true;
+      break;
+    }
+    if (o.verbose > 0 && (first_k + k) % o.verbose == 0)
+      fprintf(stderr, "ks_minimize[%s]: k=%d E=%.12f |D|=%.3e tau=%.3e h=%d cg=%d\n",
+              sizeof(T) == 8 ? "fp64" : "fp32", first_k + k, E, dn, tau, h, P.last_cg_iters);
   }
-  if (std::sqrt(std::fmax(tr.dnorm2, 0.0)) > o.gtol) status = KS_ENOCONV;
-  KS_CUDA_TRY(cudaMemcpyAsync(X_inout, X(0), bytes, cudaMemcpyDeviceToDevice, P.stream));
+  KS_CUDA_TRY(cudaMemcpyAsync(Xend, X(0), bytes, cudaMemcpyDeviceToDevice, P.stream));
+  out->E = E;
+  out->dnorm = std::sqrt(std::fmax(tr.dnorm2, 0.0));
+  out->iters = k;
+  out->cg = cg_total;
+  out->backtracks = backtracks;
+  out->stalled = stalled;
+  return KS_OK;
+}
+
+static ks_status minimize_device(Problem &P, double *X_inout, const ks_opts &o, ks_result *res) {
+  const auto t0 = std::chrono::steady_clock::now();
+  PhaseResult fr;
+  int iters = 0, cg = 0, backtracks = 0;
+  if (o.precision == KS_MIXED) {
+    // FP32 phase (Hartree, energy sums and p x p algebra stay FP64), then
+    // an FP64 polish from its last iterate.
+    float *xs = blk<float>(P, B_G);
+    KS_TRY(launch_convert(P, X_inout, xs));
+    PhaseResult mr;
+    KS_TRY(run_phase<float>(P, xs, xs, o, std::fmax(o.polish_gtol, o.gtol), o.maxit, o.stall_iters,
+                            0, std::fmax(o.ortho_tol, 1e-5), &mr));
+    iters += mr.iters;
+    cg += mr.cg;
+    backtracks += mr.backtracks;
+    P.mixed_iters = mr.iters;
+    P.mixed_dnorm = mr.dnorm;
+    P.mixed_E = mr.E;
+    double *xd = blk<double>(P, B_MD1);
+    KS_TRY(launch_convert(P, xs, xd));
+    KS_CUDA_TRY(cudaMemcpyAsync(X_inout, xd, (size_t)P.n * P.p * sizeof(double),
+                                cudaMemcpyDeviceToDevice, P.stream));
+  }
+  KS_TRY(run_phase<double>(P, X_inout, X_inout, o, o.gtol, o.maxit - iters, 0, iters, o.ortho_tol,
+                           &fr));
+  iters += fr.iters;
+  cg += fr.cg;
+  backtracks += fr.backtracks;
+  const ks_status status = fr.dnorm > o.gtol ? KS_ENOCONV : KS_OK;
   double oerr = 0;
-  KS_TRY(ortho_error(P, X(0), MX(0), &oerr));
+  KS_TRY(launch_mass<double>(P, X_inout, blk<double>(P, B_MX2)));
+  KS_TRY(ortho_error<double>(P, X_inout, blk<double>(P, B_MX2), &oerr));
   if (res) {
-    res->E = E;
-    res->gradnorm = std::sqrt(std::fmax(tr.dnorm2, 0.0));
+    res->E = fr.E;
+    res->gradnorm = fr.dnorm;
     res->ortho_err = oerr;
     for (int i = 0; i < 5; ++i) res->E_parts[i] = P.last_parts[i];
-    res->iters = k;
-    res->cg_iters_total = cg_total;
+    res->iters = iters;
+    res->cg_iters_total = cg;
     res->backtracks = backtracks;
     res->status = status;
     res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    res->mixed_iters = o.precision == KS_MIXED ? P.mixed_iters : 0;
+    res->mixed_gradnorm = o.precision == KS_MIXED ? P.mixed_dnorm : 0.0;
+    res->mixed_E = o.precision == KS_MIXED ? P.mixed_E : 0.0;
   }
-  if (status != KS_OK) set_error(status, "gradient norm above gtol after %d iterations", k);
+  if (status != KS_OK) set_error(status, "gradient norm above gtol after %d iterations", iters);
   return status;
 }
 
@@ -343,6 +423,10 @@ void ks_opts_default(ks_opts *o) {
   o->max_backtrack = 10;
   o->ortho_tol = 1e-12;
   o->ortho_every = 20;
+  o->verbose = 0;
+  o->precision = KS_FP64;
+  o->polish_gtol = 1e-4;
+  o->stall_iters = 200;
 }
 
 const char *ks_last_error_string(void) { return g_err; }
@@ -379,6 +463,7 @@ ks_status ks_problem_create(const ks_problem_desc *d, ks_problem **out) {
   P.occ = d->occ;
   P.cg_tol = d->cg_tol;
   P.cg_maxit = d->cg_maxit;
+  P.cg_precond = d->cg_precond ? 1 : 0;
   P.atoms_host.resize((size_t)4 * (d->natoms > 0 ? d->natoms : 1), 0.0);
   for (int a = 0; a < d->natoms; ++a) {
     P.atoms_host[4 * a + 0] = d->R[3 * a + 0];
@@ -402,14 +487,16 @@ ks_status ks_problem_create(const ks_problem_desc *d, ks_problem **out) {
 #define ALLOC(ptr, cnt) \
   if ((st = dalloc(&(ptr), (cnt), P)) != KS_OK) return fail(st);
   ALLOC(P.vext, n); ALLOC(P.rho, n); ALLOC(P.vH, n); ALLOC(P.veff, n);
-  ALLOC(P.cg_r, n); ALLOC(P.cg_pa, n); ALLOC(P.cg_pb, n); ALLOC(P.cg_q, n);
+  ALLOC(P.cg_r, n); ALLOC(P.cg_pa, n); ALLOC(P.cg_pb, n); ALLOC(P.cg_q, n); ALLOC(P.cg_z, n);
+  ALLOC(P.cg_t1, n); ALLOC(P.cg_t2, n);
+  ALLOC(P.dst_phi, (size_t)P.N * P.N); ALLOC(P.dst_kap, (size_t)P.N); ALLOC(P.dst_mu, (size_t)P.N);
   for (auto &b : P.blk) { ALLOC(b, np); }
   P.pp_len = (size_t)S_COUNT * P.p * P.p;
   ALLOC(P.pp, P.pp_len);
   P.cg_blocks = cg_grid_blocks(P.sms, P.n);
   size_t part = gram_partials_len(P.p, P.sms);
   if ((size_t)4 * 8 * P.sms > part) part = (size_t)4 * 8 * P.sms;
-  if ((size_t)3 * P.cg_blocks > part) part = (size_t)3 * P.cg_blocks;
+  if ((size_t)4 * P.cg_blocks > part) part = (size_t)4 * P.cg_blocks;
   P.partials_len = part;
   ALLOC(P.partials, part);
   ALLOC(P.scal, SC_COUNT);
@@ -432,6 +519,7 @@ ks_status ks_problem_create(const ks_problem_desc *d, ks_problem **out) {
   e = cudaMemsetAsync(P.vH, 0, n * sizeof(double), P.stream);
   if (e != cudaSuccess) return fail(cuda_error(e, "memset"));
   if ((st = launch_setup(P)) != KS_OK) return fail(st);
+  if ((st = launch_sine_setup(P)) != KS_OK) return fail(st);
   if ((st = sync_scalars(P)) != KS_OK) return fail(st);
   *out = kp;
   return KS_OK;
@@ -451,11 +539,11 @@ ks_status ks_energy_grad(ks_problem *kp, const double *X, double *E, double *EX,
   Problem &P = kp->P;
   const size_t bytes = (size_t)P.n * P.p * sizeof(double);
   double e = 0;
-  KS_TRY(evaluate(P, X, P.blk[B_EX0], P.blk[B_MX0], &e));
+  KS_TRY(evaluate<double>(P, X, P.blk[B_EX0], P.blk[B_MX0], &e));
   if (D || gradnorm) {
     Traces tr;
-    KS_TRY(project(P, KS_QR, X, P.blk[B_EX0], P.blk[B_MX0], P.blk[B_D0], P.blk[B_MD0], nullptr,
-                   &tr));
+    KS_TRY(project<double>(P, KS_QR, X, P.blk[B_EX0], P.blk[B_MX0], P.blk[B_D0], P.blk[B_MD0],
+                           nullptr, &tr));
     if (gradnorm) *gradnorm = std::sqrt(std::fmax(tr.dnorm2, 0.0));
     if (D) KS_CUDA_TRY(cudaMemcpyAsync(D, P.blk[B_D0], bytes, cudaMemcpyDeviceToDevice, P.stream));
   }
@@ -477,10 +565,10 @@ ks_status ks_retract(ks_problem *kp, int kind, const double *X, const double *EX
   if (kind != KS_QR && kind != KS_CAYLEY) return set_error(KS_EINVAL, "bad retraction kind");
   if (Xout == X || Xout == EX) return set_error(KS_EINVAL, "Xout aliases an input");
   Problem &P = kp->P;
-  KS_TRY(launch_mass(P, X, P.blk[B_MX0]));
+  KS_TRY(launch_mass<double>(P, X, P.blk[B_MX0]));
   Traces tr;
-  KS_TRY(project(P, kind, X, EX, P.blk[B_MX0], P.blk[B_D0], P.blk[B_MD0], nullptr, &tr));
-  KS_TRY(retract(P, kind, X, P.blk[B_D0], tau, P.blk[B_X2]));
+  KS_TRY(project<double>(P, kind, X, EX, P.blk[B_MX0], P.blk[B_D0], P.blk[B_MD0], nullptr, &tr));
+  KS_TRY(retract<double>(P, kind, X, P.blk[B_D0], tau, P.blk[B_X2]));
   KS_TRY(sync_scalars(P));
   KS_CUDA_TRY(cudaMemcpyAsync(Xout, P.blk[B_X2], (size_t)P.n * P.p * sizeof(double),
                               cudaMemcpyDeviceToDevice, P.stream));
@@ -491,7 +579,7 @@ ks_status ks_retract(ks_problem *kp, int kind, const double *X, const double *EX
 ks_status ks_orthonormalize(ks_problem *kp, double *X) {
   if (!kp || !X) return set_error(KS_EINVAL, "null argument");
   Problem &P = kp->P;
-  return orthonormalize(P, X, P.blk[B_X2], P.blk[B_MX2], 2);
+  return orthonormalize<double>(P, X, P.blk[B_X2], P.blk[B_MX2], 2);
 }
 
 ks_status ks_minimize(ks_problem *kp, double *X_inout, const ks_opts *opts, ks_result *res) {
@@ -501,6 +589,7 @@ ks_status ks_minimize(ks_problem *kp, double *X_inout, const ks_opts *opts, ks_r
   else ks_opts_default(&o);
   if (o.retraction != KS_QR && o.retraction != KS_CAYLEY)
     return set_error(KS_EINVAL, "bad retraction");
+  if (o.precision != KS_FP64 && o.precision != KS_MIXED) return set_error(KS_EINVAL, "bad precision");
   if (!(o.delta > 0.0 && o.delta < 1.0) || !(o.eta >= 0.0 && o.eta < 1.0) || o.maxit < 0 ||
       !(o.tau0 > 0.0) || o.max_backtrack < 0)
     return set_error(KS_EINVAL, "bad line-search parameters");

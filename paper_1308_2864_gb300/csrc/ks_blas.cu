@@ -20,12 +20,15 @@ static int gram_chunks(const Problem &P, int pa, int qb) {
   return chunks;
 }
 
+// T = double, or float for the mixed path (FP32 products and per-chunk
+// FP32 sums, chunk partials summed in FP64).
+template <typename T>
 __global__ void __launch_bounds__(256) gram_kernel(long long n, int pa, int qb, long long rows_per,
-                                                   const double *__restrict__ A,
-                                                   const double *__restrict__ B,
+                                                   const T *__restrict__ A,
+                                                   const T *__restrict__ B,
                                                    double *__restrict__ part) {
-  __shared__ double As[kTileK][kTile];
-  __shared__ double Bs[kTileK][kTile];
+  __shared__ T As[kTileK][kTile];
+  __shared__ T Bs[kTileK][kTile];
   const int tq = (qb + kTile - 1) / kTile;
   const int ta = blockIdx.x / tq, tb = blockIdx.x % tq;
   const int chunk = blockIdx.y;
@@ -34,11 +37,11 @@ __global__ void __launch_bounds__(256) gram_kernel(long long n, int pa, int qb, 
   if (r1 > n) r1 = n;
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
   const int a0 = ta * kTile, b0 = tb * kTile;
-  double acc[4][4];
+  T acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0;
   for (long long r = r0; r < r1; r += kTileK) {
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
@@ -46,13 +49,13 @@ __global__ void __launch_bounds__(256) gram_kernel(long long n, int pa, int qb, 
       const int rr = idx >> 6, cc = idx & 63;
       const long long row = r + rr;
       const bool rowok = row < r1;
-      As[rr][cc] = (rowok && a0 + cc < pa) ? A[row * pa + a0 + cc] : 0.0;
-      Bs[rr][cc] = (rowok && b0 + cc < qb) ? B[row * qb + b0 + cc] : 0.0;
+      As[rr][cc] = (rowok && a0 + cc < pa) ? A[row * pa + a0 + cc] : (T)0;
+      Bs[rr][cc] = (rowok && b0 + cc < qb) ? B[row * qb + b0 + cc] : (T)0;
     }
     __syncthreads();
 #pragma unroll
     for (int rr = 0; rr < kTileK; ++rr) {
-      double av[4], bv[4];
+      T av[4], bv[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) av[i] = As[rr][ty + 16 * i];
 #pragma unroll
@@ -72,7 +75,7 @@ __global__ void __launch_bounds__(256) gram_kernel(long long n, int pa, int qb, 
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int b = b0 + tx + 16 * j;
-      if (b < qb) dst[(long long)a * qb + b] = acc[i][j];
+      if (b < qb) dst[(long long)a * qb + b] = (double)acc[i][j];
     }
   }
 }
@@ -86,7 +89,8 @@ __global__ void gram_reduce_kernel(int chunks, long long len, const double *__re
   out[e] = s;
 }
 
-ks_status launch_gram(Problem &P, const double *A, int pa, const double *B, int qb, double *out) {
+template <typename T>
+ks_status launch_gram(Problem &P, const T *A, int pa, const T *B, int qb, double *out) {
   const int chunks = gram_chunks(P, pa, qb);
   long long rows_per = (P.n + chunks - 1) / chunks;
   rows_per = (rows_per + kTileK - 1) / kTileK * kTileK;
@@ -96,7 +100,7 @@ ks_status launch_gram(Problem &P, const double *A, int pa, const double *B, int 
     return set_error(KS_EINVAL, "gram: partial buffer too small (%zu > %zu)", need, P.partials_len);
   {
     ProfScope ps_(P.stream, KP_GRAM);
-    gram_kernel<<<dim3(tiles, chunks), 256, 0, P.stream>>>(P.n, pa, qb, rows_per, A, B, P.partials);
+    gram_kernel<T><<<dim3(tiles, chunks), 256, 0, P.stream>>>(P.n, pa, qb, rows_per, A, B, P.partials);
   }
   KS_CUDA_TRY(cudaGetLastError());
   const long long len = (long long)pa * qb;
@@ -109,25 +113,27 @@ ks_status launch_gram(Problem &P, const double *A, int pa, const double *B, int 
   return KS_OK;
 }
 
-__global__ void __launch_bounds__(256) combine_kernel(long long n, int q, const double *__restrict__ A1,
+template <typename T>
+__global__ void __launch_bounds__(256) combine_kernel(long long n, int q, const T *__restrict__ A1,
                                                       int k1, const double *__restrict__ C1,
-                                                      const double *__restrict__ A2, int k2,
-                                                      const double *__restrict__ C2, double alpha,
-                                                      double beta,
-                                                      const double *__restrict__ Bm,
-                                                      double *__restrict__ out) {
-  __shared__ double As[kTile][kTileK + 1];
-  __shared__ double Cs[kTileK][kTile];
+                                                      const T *__restrict__ A2, int k2,
+                                                      const double *__restrict__ C2, double alpha_d,
+                                                      double beta_d,
+                                                      const T *__restrict__ Bm,
+                                                      T *__restrict__ out) {
+  __shared__ T As[kTile][kTileK + 1];
+  __shared__ T Cs[kTileK][kTile];
+  const T alpha = (T)alpha_d, beta = (T)beta_d;
   const long long r0 = (long long)blockIdx.x * kTile;
   const int c0 = blockIdx.y * kTile;
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-  double acc[4][4];
+  T acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0;
   for (int op = 0; op < 2; ++op) {
-    const double *A = op == 0 ? A1 : A2;
+    const T *A = op == 0 ? A1 : A2;
     const double *C = op == 0 ? C1 : C2;
     const int kk = op == 0 ? k1 : k2;
     if (A == nullptr) continue;
@@ -137,14 +143,14 @@ __global__ void __launch_bounds__(256) combine_kernel(long long n, int q, const 
         const int idx = tid + t * 256;
         const int rr = idx >> 4, cc = idx & 15;          // A tile: 64 rows x 16
         const long long row = r0 + rr;
-        As[rr][cc] = (row < n && k0 + cc < kk) ? A[row * kk + k0 + cc] : 0.0;
+        As[rr][cc] = (row < n && k0 + cc < kk) ? A[row * kk + k0 + cc] : (T)0;
         const int cr = idx >> 6, ccol = idx & 63;         // C tile: 16 x 64
-        Cs[cr][ccol] = (k0 + cr < kk && c0 + ccol < q) ? C[(long long)(k0 + cr) * q + c0 + ccol] : 0.0;
+        Cs[cr][ccol] = (k0 + cr < kk && c0 + ccol < q) ? (T)C[(long long)(k0 + cr) * q + c0 + ccol] : (T)0;
       }
       __syncthreads();
 #pragma unroll
       for (int t = 0; t < kTileK; ++t) {
-        double av[4], cv[4];
+        T av[4], cv[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) av[i] = As[ty + 16 * i][t];
 #pragma unroll
@@ -165,25 +171,57 @@ __global__ void __launch_bounds__(256) combine_kernel(long long n, int q, const 
     for (int j = 0; j < 4; ++j) {
       const int col = c0 + tx + 16 * j;
       if (col >= q) continue;
-      double v = alpha * acc[i][j];
+      T v = alpha * acc[i][j];
       if (Bm) v = fma(beta, Bm[row * q + col], v);
       out[row * q + col] = v;
     }
   }
 }
 
-ks_status launch_combine(Problem &P, const double *A1, int k1, const double *C1,
-                         const double *A2, int k2, const double *C2, double alpha, double beta,
-                         const double *Bm, double *out, int q) {
+template <typename T>
+ks_status launch_combine(Problem &P, const T *A1, int k1, const double *C1, const T *A2, int k2,
+                         const double *C2, double alpha, double beta, const T *Bm, T *out, int q) {
   dim3 grid((unsigned)((P.n + kTile - 1) / kTile), (unsigned)((q + kTile - 1) / kTile));
   {
     ProfScope ps_(P.stream, KP_COMBINE);
-    combine_kernel<<<grid, 256, 0, P.stream>>>(P.n, q, A1, k1, C1, A2, k2, C2, alpha, beta, Bm,
+    combine_kernel<T><<<grid, 256, 0, P.stream>>>(P.n, q, A1, k1, C1, A2, k2, C2, alpha, beta, Bm,
                                                 out);
   }
   KS_CUDA_TRY(cudaGetLastError());
   return KS_OK;
 }
+
+template ks_status launch_gram<double>(Problem &, const double *, int, const double *, int,
+                                       double *);
+template ks_status launch_gram<float>(Problem &, const float *, int, const float *, int, double *);
+template ks_status launch_combine<double>(Problem &, const double *, int, const double *,
+                                          const double *, int, const double *, double, double,
+                                          const double *, double *, int);
+template ks_status launch_combine<float>(Problem &, const float *, int, const double *,
+                                         const float *, int, const double *, double, double,
+                                         const float *, float *, int);
+
+template <typename A, typename B>
+__global__ void convert_kernel(long long total, const A *__restrict__ in, B *__restrict__ out) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x)
+    out[e] = (B)in[e];
+}
+
+template <typename A, typename B>
+static ks_status convert_impl(Problem &P, const A *in, B *out) {
+  const long long total = (long long)P.n * P.p;
+  const int nb = reduce_blocks(P, total);
+  {
+    ProfScope ps_(P.stream, KP_OTHER);
+    convert_kernel<A, B><<<nb, kThreads, 0, P.stream>>>(total, in, out);
+  }
+  KS_CUDA_TRY(cudaGetLastError());
+  return KS_OK;
+}
+
+ks_status launch_convert(Problem &P, const double *in, float *out) { return convert_impl(P, in, out); }
+ks_status launch_convert(Problem &P, const float *in, double *out) { return convert_impl(P, in, out); }
 
 __global__ void ortho_err_kernel(int p, const double *__restrict__ O, double *out) {
   __shared__ double smem[33];

@@ -83,6 +83,10 @@ struct Problem {
   // n-vectors
   double *vext = nullptr, *rho = nullptr, *vH = nullptr, *veff = nullptr;
   double *cg_r = nullptr, *cg_pa = nullptr, *cg_pb = nullptr, *cg_q = nullptr;
+  double *cg_z = nullptr;          // preconditioned residual
+  float *cg_t1 = nullptr, *cg_t2 = nullptr;  // sine-transform work (FP32)
+  float *dst_phi = nullptr, *dst_kap = nullptr, *dst_mu = nullptr;
+  int cg_precond = 1;
   bool vH_valid = false;           // warm start available
 
   // n x p blocks
@@ -103,6 +107,10 @@ struct Problem {
   GridBarrier *bar = nullptr;
   int *dstatus = nullptr;          // device status word
   int *dstatus_host = nullptr;     // pinned mirror
+
+  // last mixed-precision phase
+  int mixed_iters = 0;
+  double mixed_dnorm = 0, mixed_E = 0;
 
   // last evaluation
   double last_parts[5] = {0, 0, 0, 0, 0};
@@ -134,10 +142,12 @@ void prof_collect();
 // ---------------------------------------------------------------- kernels
 // ks_setup.cu
 ks_status launch_setup(Problem &P);
-// ks_density.cu: rho_k = f sum_i X_ki^2
-ks_status launch_density(Problem &P, const double *X, double *rho);
+// ks_density.cu: rho_k = f sum_i X_ki^2 (X FP64 or FP32, rho FP64)
+template <typename T>
+ks_status launch_density(Problem &P, const T *X, double *rho);
 // ks_cg.cu: K v = 4 pi h^3 rho; v in/out (warm if warm), r out
 ks_status launch_cg(Problem &P, const double *rho, double *v, double *r, bool warm);
+ks_status launch_sine_setup(Problem &P);
 int cg_grid_blocks(int sms, int n);
 // ks_xc.cu: veff = vext + vH + v_xc(rho); energy partials; reduction helpers
 ks_status launch_potential(Problem &P, const double *rho, const double *vH, const double *r,
@@ -146,24 +156,33 @@ ks_status launch_reduce(Problem &P, const double *partials, int nchan, int nb, d
                         double scale = 1.0);
 // Blocks of the grid-stride reduction kernels (their partials are nchan x this).
 int reduce_blocks(const Problem &P, long long work);
-// ks_stencil.cu
-ks_status launch_hamiltonian(Problem &P, const double *X, const double *veff, double *EX,
-                             double *MX, double *ekin_out);
-ks_status launch_mass(Problem &P, const double *X, double *MX);
+// ks_stencil.cu (T = double or float; sums always returned in FP64)
+template <typename T>
+ks_status launch_hamiltonian(Problem &P, const T *X, const double *veff, T *EX, T *MX,
+                             double *ekin_out);
+template <typename T>
+ks_status launch_mass(Problem &P, const T *X, T *MX);
 // MD = M D; dnorm2 = sum D.MD; with prev != null also the BB traces.
-struct BBPrev { const double *X, *MX, *D, *MD; };
-ks_status launch_mass_dots(Problem &P, const double *D, double *MD, const double *X,
-                           const double *MX, const BBPrev *prev, double *out4);
+template <typename T>
+struct BBPrevT { const T *X, *MX, *D, *MD; };
+template <typename T>
+ks_status launch_mass_dots(Problem &P, const T *D, T *MD, const T *X, const T *MX,
+                           const BBPrevT<T> *prev, double *out4);
 // ks_minv.cu: G = M^{-1} E
-ks_status launch_mass_inverse(Problem &P, const double *E, double *G);
+template <typename T>
+ks_status launch_mass_inverse(Problem &P, const T *E, T *G);
 // ks_blas.cu
-// out (pa x qb) = A^T B with A n x pa, B n x qb (row-major, ld = pa, qb)
-ks_status launch_gram(Problem &P, const double *A, int pa, const double *B, int qb, double *out);
+// out (pa x qb, FP64) = A^T B with A n x pa, B n x qb (row-major, ld = pa, qb)
+template <typename T>
+ks_status launch_gram(Problem &P, const T *A, int pa, const T *B, int qb, double *out);
 // out (n x q) = alpha (A1 C1 + A2 C2) + beta Bm (A2/Bm may be null);
-// C1 k1 x q, C2 k2 x q.  out must not alias A1, A2 or Bm.
-ks_status launch_combine(Problem &P, const double *A1, int k1, const double *C1,
-                         const double *A2, int k2, const double *C2, double alpha, double beta,
-                         const double *Bm, double *out, int q);
+// C1 k1 x q, C2 k2 x q (FP64).  out must not alias A1, A2 or Bm.
+template <typename T>
+ks_status launch_combine(Problem &P, const T *A1, int k1, const double *C1, const T *A2, int k2,
+                         const double *C2, double alpha, double beta, const T *Bm, T *out, int q);
+// elementwise precision conversion of an n x p block
+ks_status launch_convert(Problem &P, const double *in, float *out);
+ks_status launch_convert(Problem &P, const float *in, double *out);
 // sum of squares of (O - I) for a p x p O
 ks_status launch_ortho_err(Problem &P, const double *O, double *out);
 // ks_small.cu: small dense FP64 algebra in one CTA

@@ -11,9 +11,10 @@ namespace ks {
 
 // Solve tridiag(1, 4, 1) y = scale * d along one axis, in place on `out`
 // (reading `in` on the forward pass).  w holds the pivots 1/(4 - w_{j-1}).
-__global__ void thomas_kernel(int N, int p, int axis, double scale,
-                              const double *__restrict__ w, const double *in,
-                              double *out) {
+template <typename T>
+__global__ void thomas_kernel(int N, int p, int axis, double scale_d,
+                              const double *__restrict__ w, const T *in, T *out) {
+  const T scale = (T)scale_d;
   const long long lines = (long long)N * N;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= lines * p) return;
@@ -34,42 +35,46 @@ __global__ void thomas_kernel(int N, int p, int axis, double scale,
   const long long e0 = base * p + i;
   const long long es = stride * p;
   // forward elimination
-  double prev = 0.0;
+  T prev = 0;
   for (int j = 0; j < N; ++j) {
     const long long e = e0 + j * es;
-    const double d = (scale * in[e] - prev) * w[j];
+    const T d = (scale * in[e] - prev) * (T)w[j];
     out[e] = d;
     prev = d;
   }
   // back substitution
-  double next = out[e0 + (long long)(N - 1) * es];
+  T next = out[e0 + (long long)(N - 1) * es];
   for (int j = N - 2; j >= 0; --j) {
     const long long e = e0 + j * es;
-    next = out[e] - w[j] * next;
+    next = out[e] - (T)w[j] * next;
     out[e] = next;
   }
 }
 
-ks_status launch_mass_inverse(Problem &P, const double *E, double *G) {
+template <typename T>
+ks_status launch_mass_inverse(Problem &P, const T *E, T *G) {
   const long long work = (long long)P.N * P.N * P.p;
   const int nb = (int)((work + kThreads - 1) / kThreads);
   const double s = 6.0 / P.h;
   {
     ProfScope ps_(P.stream, KP_MASS_INV);
-    thomas_kernel<<<nb, kThreads, 0, P.stream>>>(P.N, P.p, 0, s * s * s, P.thomas_w, E, G);
+    thomas_kernel<T><<<nb, kThreads, 0, P.stream>>>(P.N, P.p, 0, s * s * s, P.thomas_w, E, G);
   }
   KS_CUDA_TRY(cudaGetLastError());
   {
     ProfScope ps_(P.stream, KP_MASS_INV);
-    thomas_kernel<<<nb, kThreads, 0, P.stream>>>(P.N, P.p, 1, 1.0, P.thomas_w, G, G);
+    thomas_kernel<T><<<nb, kThreads, 0, P.stream>>>(P.N, P.p, 1, 1.0, P.thomas_w, G, G);
   }
   KS_CUDA_TRY(cudaGetLastError());
   {
     ProfScope ps_(P.stream, KP_MASS_INV);
-    thomas_kernel<<<nb, kThreads, 0, P.stream>>>(P.N, P.p, 2, 1.0, P.thomas_w, G, G);
+    thomas_kernel<T><<<nb, kThreads, 0, P.stream>>>(P.N, P.p, 2, 1.0, P.thomas_w, G, G);
   }
   KS_CUDA_TRY(cudaGetLastError());
   return KS_OK;
 }
+
+template ks_status launch_mass_inverse<double>(Problem &, const double *, double *);
+template ks_status launch_mass_inverse<float>(Problem &, const float *, float *);
 
 }  // namespace ks

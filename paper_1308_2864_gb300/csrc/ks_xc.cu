@@ -7,9 +7,15 @@
 
 namespace ks {
 
-// Perdew-Zunger parameters (hartree).
+// Perdew-Zunger parameters (hartree): gamma, beta1, beta2, A, B as
+// published; C and D from continuity of eps_c and d eps_c / d r_s at r_s = 1
+// (the published 0.0020 and -0.0116 are these rounded; rounded, they leave a
+// 3.2e-5 Ha jump that makes the energy discontinuous).
 constexpr double kPzGamma = -0.1423, kPzBeta1 = 1.0529, kPzBeta2 = 0.3334;
-constexpr double kPzA = 0.0311, kPzB = -0.048, kPzC = 0.0020, kPzD = -0.0116;
+constexpr double kPzA = 0.0311, kPzB = -0.048;
+constexpr double kPzDen1 = 1.0 + kPzBeta1 + kPzBeta2;
+constexpr double kPzD = kPzGamma / kPzDen1 - kPzB;
+constexpr double kPzC = -kPzGamma * (0.5 * kPzBeta1 + kPzBeta2) / (kPzDen1 * kPzDen1) - kPzA - kPzD;
 
 __device__ __forceinline__ void lda_point(double rho, int xc, double &eps, double &v) {
   if (!(rho >= 1e-30)) {

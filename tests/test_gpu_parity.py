@@ -67,9 +67,10 @@ def test_density(case):
     assert_rel(host(P.step_density(dev(X))), oe.density(X, model.occ), what="rho")
 
 
-def test_hartree_cg(case):
+@pytest.mark.parametrize("precond", [False, True], ids=["plain", "sine-preconditioned"])
+def test_hartree_cg(case, precond):
     s, model, X = case
-    P = make(s)
+    P = make(s, cg_precond=precond)
     rho = oe.density(X, model.occ)
     b = 4 * math.pi * model.h ** 3 * rho
     v, r, it = P.step_hartree(dev(rho))
@@ -78,11 +79,16 @@ def test_hartree_cg(case):
     res = b - ofe.apply_K(v, model.N, model.h)
     assert np.linalg.norm(res) <= 1.05e-10 * np.linalg.norm(b)
     assert np.allclose(host(r), res, atol=1e-13 * np.abs(b).max())
-    # same iteration count as plain CG from the same start, and the same answer
-    vo, ro, ito, ok = ofe.cg_solve(lambda x: ofe.apply_K(x, model.N, model.h), b, None, 1e-10, 10000)
-    assert ok and abs(it - ito) <= 1
-    assert_rel(v, vo, rel=1e-9, what="vH vs oracle CG")
     assert_rel(v, ofe.poisson_exact(b, model.N, model.h), rel=1e-8, what="vH vs exact")
+    if precond:
+        # the FP32 sine-basis inverse of K leaves only rounding-level error
+        assert it <= 4
+    else:
+        # same iteration count as plain CG from the same start, same answer
+        vo, ro, ito, ok = ofe.cg_solve(lambda x: ofe.apply_K(x, model.N, model.h), b, None,
+                                       1e-10, 10000)
+        assert ok and abs(it - ito) <= 1
+        assert_rel(v, vo, rel=1e-9, what="vH vs oracle CG")
     # warm start from the answer converges immediately
     v2, _, it2 = P.step_hartree(dev(rho), dev(v), warm=True)
     assert it2 <= 1
@@ -237,8 +243,27 @@ def test_invalid_arguments_are_reported():
 def test_cg_limit_reports_noconv():
     import paper_1308_2864_gb300 as ks
     s = ki.small_system(N=12, L=6.0, natoms=1, p=2, Z=4.0, seed=1)
-    P = make(s, cg_maxit=1)
+    P = make(s, cg_maxit=1, cg_precond=False)
     X = ost.m_orthonormalize(oe.Model.from_system(s), s.x0())
     with pytest.raises(ks.KSError) as e:
         P.step_hartree(P.step_density(dev(X)))
     assert e.value.status == ks.KS_ENOCONV
+
+
+@pytest.mark.parametrize("retraction", ["qr", "cayley"])
+def test_mixed_precision_then_fp64_polish(retraction):
+    # FP32 orbital blocks down to ||D|| <= 1e-4, then the FP64 polish: the
+    # final energy matches the FP64 oracle's minimiser like the FP64 run.
+    s = ki.small_system(N=10, L=7.0, natoms=2, p=2, Z=1.0, seed=7)
+    s.rc = 1.0
+    model = oe.Model.from_system(s)
+    ref = ost.minimize(model, s.x0(), ost.Options(retraction=retraction, gtol=1e-8, maxit=2000))
+    P = make(s)
+    X = dev(s.x0())
+    r = P.minimize(X, retraction=retraction, gtol=1e-8, maxit=3000, precision="mixed",
+                   polish_gtol=1e-4)
+    assert r["status"] == 0 and r["gradnorm"] <= 1e-8
+    assert r["mixed_iters"] > 0 and r["mixed_gradnorm"] <= 1e-3
+    assert abs(r["mixed_E"] - ref.E) <= 1e-5
+    assert r["E"] == pytest.approx(ref.E, abs=1e-8)
+    assert ost.ortho_error(model, host(X)) < 1e-12

@@ -18,15 +18,27 @@ def test_slater_uniform_gas_textbook():
 
 
 def test_pz81_branches_meet_at_rs1():
-    # The two PZ81 branches are independent fits that join (nearly
-    # continuously) at rs = 1; eps_c(1) is about -0.0596 Ha on both sides.
+    # The two PZ81 branches join at rs = 1 with continuous eps_c and v_c
+    # (about -0.0596 and -0.0668 Ha), and the continuity coefficients C, D
+    # round to the published 0.0020 and -0.0116.
     rho1 = 3.0 / (4.0 * math.pi)
-    below = energy.pz81(np.array([rho1 * (1 + 1e-12)]))
-    above = energy.pz81(np.array([rho1 * (1 - 1e-12)]))
+    below = energy.pz81(np.array([rho1 * (1 + 1e-13)]))
+    above = energy.pz81(np.array([rho1 * (1 - 1e-13)]))
     assert below[0][0] == pytest.approx(-0.0596, abs=1e-4)
-    assert above[0][0] == pytest.approx(-0.0596, abs=1e-4)
-    assert abs(below[0][0] - above[0][0]) < 5e-5
-    assert abs(below[1][0] - above[1][0]) < 5e-5
+    assert below[1][0] == pytest.approx(-0.0668, abs=1e-4)
+    assert abs(below[0][0] - above[0][0]) < 1e-13
+    assert abs(below[1][0] - above[1][0]) < 1e-12
+    assert round(energy.PZ_C, 4) == 0.0020 and round(energy.PZ_D, 4) == -0.0116
+
+
+def test_pz81_energy_is_smooth_across_rs1():
+    # one node's density swept through rs = 1: the discrete xc energy has no
+    # jump (the rounded published C, D would give 3.2e-5 Ha per electron)
+    rho1 = 3.0 / (4.0 * math.pi)
+    r = rho1 * (1.0 + np.linspace(-1e-6, 1e-6, 201))
+    e = r * energy.lda(r, energy.XC_SLATER_PZ81)[0]
+    d = np.diff(e)
+    assert np.abs(np.diff(d)).max() < 1e-12
 
 
 def test_pz81_high_density_limit():
