@@ -97,8 +97,14 @@ typedef struct {
                          to gtol; the Hartree solve, energy sums and p x p algebra are FP64
                          in both (KS_FP64) */
   double polish_gtol; /* switch from the FP32 phase to the FP64 polish (1e-4) */
-  int stall_iters;    /* FP32 phase: stop after this many iterations without a 0.1 %
-                         improvement of the best ||D||_M (200) */
+  int stall_iters;    /* 1: the FP32 phase also ends when the energy stagnates, i.e. the mean
+                         of df_k = |E_{k-1} - E_k| / (|E_{k-1}| + 1) over the last three
+                         iterations falls below stall_df (the stagnation measure of
+                         Sec. 4.1); 0: it ends only at polish_gtol or maxit (1) */
+  double stall_df;    /* stagnation threshold of the FP32 phase (1e-11) */
+  int resume;         /* 1: continue from the state of the last ks_minimize on this problem
+                         or from ks_state_load (X_inout is then output only); maxit counts
+                         all iterations including those before the checkpoint (0) */
 } ks_opts;
 
 typedef struct {
@@ -170,6 +176,18 @@ ks_status ks_minimize(ks_problem *prob, double *X_inout, const ks_opts *opts,
 ks_status ks_minimize_host(ks_problem *prob, double *X_inout_host, const ks_opts *opts,
                            ks_result *result);
 
+/* Checkpoint of the minimiser (line-search scalars, current and previous
+ * iterates with their M products, gradients and the Hartree potential) after
+ * the last iteration of the last ks_minimize call.  ks_state_bytes returns
+ * the size needed (0 when there is nothing to save); ks_state_save writes it
+ * to a HOST buffer; ks_state_load restores it into a problem with the same N
+ * and p, after which ks_minimize with opts.resume = 1 continues the run.  With
+ * the FP64 path the continued run is bitwise identical to an uninterrupted
+ * one (all reductions have a fixed order). */
+size_t ks_state_bytes(ks_problem *prob);
+ks_status ks_state_save(ks_problem *prob, void *host_buf, size_t bytes);
+ks_status ks_state_load(ks_problem *prob, const void *host_buf, size_t bytes);
+
 /* Kernels this library has launched in this process so far. */
 unsigned long long ks_kernel_launches(void);
 
@@ -184,6 +202,10 @@ unsigned long long ks_kernel_launches(void);
 ks_status ks_profile_start(void);
 ks_status ks_profile_stop(double ms[KS_PROF_CLASSES], long long counts[KS_PROF_CLASSES]);
 const char *ks_profile_class_name(int cls);
+/* Algorithmic work of the launches timed since ks_profile_start, per class:
+ * floating-point operations (an FMA counts 2) and minimal DRAM bytes (each
+ * input block read once, each output block written once). */
+ks_status ks_profile_work(double flops[KS_PROF_CLASSES], double bytes[KS_PROF_CLASSES]);
 
 /* Text of the last error on the calling thread ("" if none). */
 const char *ks_last_error_string(void);

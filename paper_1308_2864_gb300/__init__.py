@@ -48,7 +48,8 @@ class Opts(ctypes.Structure):
                 ("max_backtrack", ctypes.c_int), ("ortho_tol", ctypes.c_double),
                 ("ortho_every", ctypes.c_int), ("verbose", ctypes.c_int),
                 ("precision", ctypes.c_int), ("polish_gtol", ctypes.c_double),
-                ("stall_iters", ctypes.c_int)]
+                ("stall_iters", ctypes.c_int), ("stall_df", ctypes.c_double),
+                ("resume", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -80,9 +81,13 @@ SIGNATURES = [
     ("ks_minimize_host", _I, [_P, _DP, ctypes.POINTER(Opts), ctypes.POINTER(Result)]),
     ("ks_last_error_string", ctypes.c_char_p, []),
     ("ks_kernel_launches", ctypes.c_ulonglong, []),
+    ("ks_state_bytes", ctypes.c_size_t, [_P]),
+    ("ks_state_save", _I, [_P, ctypes.c_void_p, ctypes.c_size_t]),
+    ("ks_state_load", _I, [_P, ctypes.c_void_p, ctypes.c_size_t]),
     ("ks_profile_start", _I, []),
     ("ks_profile_stop", _I, [_DP, ctypes.POINTER(ctypes.c_longlong)]),
     ("ks_profile_class_name", ctypes.c_char_p, [_I]),
+    ("ks_profile_work", _I, [_DP, _DP]),
     ("ks_step_vext", _I, [_P, _P]),
     ("ks_step_eii", _I, [_P, _DP]),
     ("ks_step_density", _I, [_P, _P, _P]),
@@ -162,12 +167,17 @@ def profile_start():
 
 
 def profile_stop() -> dict:
-    """{class name: (milliseconds, timed launch groups)} since profile_start()."""
+    """{class name: (milliseconds, timed launch groups, flops, DRAM bytes)}
+    since profile_start() (algorithmic work, see ks_profile_work)."""
     lib = load_library()
     ms = (ctypes.c_double * PROF_CLASSES)()
     cnt = (ctypes.c_longlong * PROF_CLASSES)()
+    fl = (ctypes.c_double * PROF_CLASSES)()
+    by = (ctypes.c_double * PROF_CLASSES)()
     _check(lib.ks_profile_stop(ms, cnt))
-    return {lib.ks_profile_class_name(i).decode(): (ms[i], cnt[i]) for i in range(PROF_CLASSES)}
+    _check(lib.ks_profile_work(fl, by))
+    return {lib.ks_profile_class_name(i).decode(): (ms[i], cnt[i], fl[i], by[i])
+            for i in range(PROF_CLASSES)}
 
 
 def result_dict(r: Result) -> dict:
@@ -284,6 +294,20 @@ class Problem:
         if st not in (KS_OK, KS_ENOCONV):
             _check(st)
         return result_dict(r)
+
+    def state_save(self) -> bytes:
+        """Checkpoint of the last minimisation (host bytes)."""
+        lib = load_library()
+        nbytes = lib.ks_state_bytes(self._h)
+        if nbytes == 0:
+            raise KSError(KS_EINVAL, "no minimisation state to save")
+        buf = ctypes.create_string_buffer(nbytes)
+        _check(lib.ks_state_save(self._h, buf, nbytes))
+        return buf.raw
+
+    def state_load(self, data: bytes):
+        buf = ctypes.create_string_buffer(data, len(data))
+        _check(load_library().ks_state_load(self._h, buf, len(data)))
 
     # ------------------------------------------------------------ ks_steps.h
     def step_vext(self):

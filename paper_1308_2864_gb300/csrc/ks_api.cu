@@ -258,15 +258,18 @@ struct PhaseResult {
 };
 
 // One run of Alg. ConOptM in storage precision T from the block Xstart
-// (copied in, then M-orthonormalised) until ||D||_M <= gtol, maxit
-// iterations, or -- when stall > 0 -- no 0.1 % improvement of the best
-// ||D||_M for `stall` iterations.  The final iterate is copied to Xend.
+// (copied in, then M-orthonormalised) -- or, when `resume` is set, from the
+// state left in P.state by an earlier run or by ks_state_load -- until
+// ||D||_M <= gtol, `maxit` iterations in total, or (stall > 0) no 0.1 %
+// improvement of the best ||D||_M for `stall` iterations.  The final iterate
+// is copied to Xend and the loop state is kept in P.state.
 template <typename T>
 static ks_status run_phase(Problem &P, const T *Xstart, T *Xend, const ks_opts &o, double gtol,
-                           int maxit, int stall, int first_k, double ortho_tol,
+                           int maxit, int stall, int first_k, double ortho_tol, bool resume,
                            PhaseResult *out) {
   const int p = P.p;
   const size_t bytes = (size_t)P.n * p * sizeof(T);
+  Problem::RunState &S = P.state;
   int ix[3] = {B_X0, B_X1, B_X2};        // cur, prev, trial
   int imx[3] = {B_MX0, B_MX1, B_MX2};
   int iex[2] = {B_EX0, B_EX1};           // cur, trial
@@ -278,19 +281,50 @@ static ks_status run_phase(Problem &P, const T *Xstart, T *Xend, const ks_opts &
   auto D = [&](int s) { return blk<T>(P, id[s]); };
   auto MD = [&](int s) { return blk<T>(P, imd[s]); };
 
-  KS_CUDA_TRY(cudaMemcpyAsync(X(0), Xstart, bytes, cudaMemcpyDeviceToDevice, P.stream));
-  KS_TRY(orthonormalize<T>(P, X(0), X(2), MX(0), 2));
-  double E = 0;
-  KS_TRY(evaluate<T>(P, X(0), EX(0), MX(0), &E));
-  int cg_total = P.last_cg_iters;
-  Traces tr;
-  KS_TRY(project<T>(P, o.retraction, X(0), EX(0), MX(0), D(0), MD(0), nullptr, &tr));
-  double C = E, Q = 1.0;
+  double E = 0, C = 0, Q = 1.0, best = 0;
+  int k = 0, last_improve = 0, cg_total = 0;
   bool have_prev = false;
-  int k = 0, backtracks = 0, last_improve = 0;
-  double best = std::sqrt(std::fmax(tr.dnorm2, 0.0));
+  Traces tr;
+  if (resume) {
+    for (int i = 0; i < 3; ++i) { ix[i] = S.ix[i]; imx[i] = S.imx[i]; }
+    for (int i = 0; i < 2; ++i) { iex[i] = S.iex[i]; id[i] = S.id[i]; imd[i] = S.imd[i]; }
+    first_k = S.first_k;
+    k = S.k;
+    E = S.E; C = S.C; Q = S.Q; best = S.best; last_improve = S.last_improve;
+    have_prev = S.have_prev != 0;
+    P.vH_valid = true;
+    // regenerates D, MD, the small matrices and the traces exactly (all
+    // reductions have a fixed order)
+    BBPrevT<T> prev{X(1), MX(1), D(1), MD(1)};
+    KS_TRY(project<T>(P, S.retraction, X(0), EX(0), MX(0), D(0), MD(0),
+                      have_prev ? &prev : nullptr, &tr));
+  } else {
+    KS_CUDA_TRY(cudaMemcpyAsync(X(0), Xstart, bytes, cudaMemcpyDeviceToDevice, P.stream));
+    KS_TRY(orthonormalize<T>(P, X(0), X(2), MX(0), 2));
+    KS_TRY(evaluate<T>(P, X(0), EX(0), MX(0), &E));
+    cg_total = P.last_cg_iters;
+    KS_TRY(project<T>(P, o.retraction, X(0), EX(0), MX(0), D(0), MD(0), nullptr, &tr));
+    C = E;
+    best = std::sqrt(std::fmax(tr.dnorm2, 0.0));
+  }
+  const int k0 = k;
+  int backtracks = 0;
   bool stalled = false;
-  while (std::sqrt(std::fmax(tr.dnorm2, 0.0)) > gtol && k < maxit) {
+  double df[3] = {1.0, 1.0, 1.0}, Eprev = E;
+  auto save_state = [&]() {
+    S.valid = true;
+    S.elem = (int)sizeof(T);
+    S.retraction = o.retraction;
+    S.first_k = first_k;
+    S.k = k;
+    S.have_prev = have_prev ? 1 : 0;
+    S.C = C; S.Q = Q; S.E = E; S.best = best; S.last_improve = last_improve;
+    S.dnorm2 = tr.dnorm2; S.ss = tr.ss; S.sy = tr.sy; S.yy = tr.yy;
+    for (int i = 0; i < 3; ++i) { S.ix[i] = ix[i]; S.imx[i] = imx[i]; }
+    for (int i = 0; i < 2; ++i) { S.iex[i] = iex[i]; S.id[i] = id[i]; S.imd[i] = imd[i]; }
+  };
+  save_state();
+  while (std::sqrt(std::fmax(tr.dnorm2, 0.0)) > gtol && first_k + k < maxit) {
     double tau = have_prev ? bb_step(first_k + k, tr, o) : o.tau0;
     int h = 0;
     double Et = 0;
@@ -318,7 +352,7 @@ static ks_status run_phase(Problem &P, const T *Xstart, T *Xend, const ks_opts &
     ++k;
     bool reortho = false;
     if (o.retraction == KS_CAYLEY || sizeof(T) == 4 ||
-        (o.ortho_every > 0 && k % o.ortho_every == 0)) {
+        (o.ortho_every > 0 && (first_k + k) % o.ortho_every == 0)) {
       double oerr = 0;
       KS_TRY(ortho_error<T>(P, X(0), MX(0), &oerr));
       reortho = oerr > ortho_tol;
@@ -332,59 +366,95 @@ static ks_status run_phase(Problem &P, const T *Xstart, T *Xend, const ks_opts &
     KS_TRY(project<T>(P, o.retraction, X(0), EX(0), MX(0), D(0), MD(0), &prev, &tr));
     have_prev = true;
     const double dn = std::sqrt(std::fmax(tr.dnorm2, 0.0));
+    bool stop = false;
+    // energy stagnation measure of Sec. 4.1: df_k = |E_{k-1} - E_k| / (|E_{k-1}| + 1),
+    // averaged over the last three iterations
+    df[k % 3] = std::fabs(Eprev - E) / (std::fabs(Eprev) + 1.0);
+    Eprev = E;
     if (dn < 0.999 * best) {
       best = dn;
       last_improve = k;
-    } else if (stall > 0 && k - last_improve >= stall) {
-      stalled = true;
-      break;
     }
+    if (stall > 0 && k - k0 >= 3 && (df[0] + df[1] + df[2]) / 3.0 < o.stall_df) {
+      stalled = true;
+      stop = true;
+    }
+    save_state();
     if (o.verbose > 0 && (first_k + k) % o.verbose == 0)
       fprintf(stderr, "ks_minimize[%s]: k=%d E=%.12f |D|=%.3e tau=%.3e h=%d cg=%d\n",
               sizeof(T) == 8 ? "fp64" : "fp32", first_k + k, E, dn, tau, h, P.last_cg_iters);
+    if (stop) break;
   }
   KS_CUDA_TRY(cudaMemcpyAsync(Xend, X(0), bytes, cudaMemcpyDeviceToDevice, P.stream));
   out->E = E;
   out->dnorm = std::sqrt(std::fmax(tr.dnorm2, 0.0));
-  out->iters = k;
+  out->iters = k - k0;
   out->cg = cg_total;
   out->backtracks = backtracks;
   out->stalled = stalled;
   return KS_OK;
 }
 
-static ks_status minimize_device(Problem &P, double *X_inout, const ks_opts &o, ks_result *res) {
+static ks_status minimize_device(Problem &P, double *X_inout, const ks_opts &o, ks_result *res,
+                                 bool resume) {
   const auto t0 = std::chrono::steady_clock::now();
   PhaseResult fr;
   int iters = 0, cg = 0, backtracks = 0;
-  if (o.precision == KS_MIXED) {
+  const bool resume_fp32 = resume && P.state.elem == 4;
+  bool resume_fp64 = resume && P.state.elem == 8;
+  int done = resume ? P.state.first_k + P.state.k : 0;   // iterations before this call
+  if (o.precision == KS_MIXED && (!resume || resume_fp32)) {
     // FP32 phase (Hartree, energy sums and p x p algebra stay FP64), then
     // an FP64 polish from its last iterate.
     float *xs = blk<float>(P, B_G);
-    KS_TRY(launch_convert(P, X_inout, xs));
+    if (!resume) KS_TRY(launch_convert(P, X_inout, xs));
     PhaseResult mr;
     KS_TRY(run_phase<float>(P, xs, xs, o, std::fmax(o.polish_gtol, o.gtol), o.maxit, o.stall_iters,
-                            0, std::fmax(o.ortho_tol, 1e-5), &mr));
+                            0, std::fmax(o.ortho_tol, 1e-5), resume_fp32, &mr));
     iters += mr.iters;
     cg += mr.cg;
     backtracks += mr.backtracks;
-    P.mixed_iters = mr.iters;
+    P.mixed_iters = P.state.first_k + P.state.k;
     P.mixed_dnorm = mr.dnorm;
     P.mixed_E = mr.E;
     double *xd = blk<double>(P, B_MD1);
     KS_TRY(launch_convert(P, xs, xd));
     KS_CUDA_TRY(cudaMemcpyAsync(X_inout, xd, (size_t)P.n * P.p * sizeof(double),
                                 cudaMemcpyDeviceToDevice, P.stream));
+    done = P.mixed_iters;
+    resume_fp64 = false;
+    if (done >= o.maxit && !mr.stalled && mr.dnorm > std::fmax(o.polish_gtol, o.gtol)) {
+      // iteration limit inside the FP32 phase: no polish; the FP32 state
+      // stays resumable and X_inout holds the FP32 iterate in FP64
+      if (res) {
+        res->E = mr.E;
+        res->gradnorm = mr.dnorm;
+        res->ortho_err = -1.0;
+        for (int i = 0; i < 5; ++i) res->E_parts[i] = P.last_parts[i];
+        res->iters = iters;
+        res->cg_iters_total = cg;
+        res->backtracks = backtracks;
+        res->status = KS_ENOCONV;
+        res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        res->mixed_iters = P.mixed_iters;
+        res->mixed_gradnorm = P.mixed_dnorm;
+        res->mixed_E = P.mixed_E;
+      }
+      KS_CUDA_TRY(cudaStreamSynchronize(P.stream));
+      return set_error(KS_ENOCONV, "iteration limit reached in the FP32 phase");
+    }
+  } else if (resume && o.precision != KS_MIXED && P.state.elem != 8) {
+    return set_error(KS_EINVAL, "saved state is from an FP32 phase; resume it with KS_MIXED");
   }
-  KS_TRY(run_phase<double>(P, X_inout, X_inout, o, o.gtol, o.maxit - iters, 0, iters, o.ortho_tol,
-                           &fr));
+  KS_TRY(run_phase<double>(P, X_inout, X_inout, o, o.gtol, o.maxit, 0, done, o.ortho_tol,
+                           resume_fp64, &fr));
   iters += fr.iters;
   cg += fr.cg;
   backtracks += fr.backtracks;
   const ks_status status = fr.dnorm > o.gtol ? KS_ENOCONV : KS_OK;
   double oerr = 0;
-  KS_TRY(launch_mass<double>(P, X_inout, blk<double>(P, B_MX2)));
-  KS_TRY(ortho_error<double>(P, X_inout, blk<double>(P, B_MX2), &oerr));
+  KS_TRY(launch_mass<double>(P, X_inout, blk<double>(P, B_G)));
+  KS_TRY(ortho_error<double>(P, X_inout, blk<double>(P, B_G), &oerr));
   if (res) {
     res->E = fr.E;
     res->gradnorm = fr.dnorm;
@@ -401,6 +471,19 @@ static ks_status minimize_device(Problem &P, double *X_inout, const ks_opts &o, 
   }
   if (status != KS_OK) set_error(status, "gradient norm above gtol after %d iterations", iters);
   return status;
+}
+
+// Checkpoint layout: header, then the current X, MX, E_X, D, MD and the
+// previous X, MX, D, MD blocks (elem bytes per entry), then vH (FP64).
+struct StateHeader {
+  uint64_t magic;
+  int32_t version, N, p, elem, retraction, first_k, k, have_prev, last_improve;
+  double C, Q, E, dnorm2, ss, sy, yy, best;
+};
+constexpr uint64_t kStateMagic = 0x4b53535441544531ull;   // "KSSTATE1"
+
+static size_t state_bytes(const Problem &P, int elem) {
+  return sizeof(StateHeader) + (size_t)9 * P.n * P.p * elem + (size_t)P.n * sizeof(double);
 }
 
 }  // namespace ks
@@ -426,7 +509,9 @@ void ks_opts_default(ks_opts *o) {
   o->verbose = 0;
   o->precision = KS_FP64;
   o->polish_gtol = 1e-4;
-  o->stall_iters = 200;
+  o->stall_iters = 1;
+  o->stall_df = 1e-11;
+  o->resume = 0;
 }
 
 const char *ks_last_error_string(void) { return g_err; }
@@ -593,8 +678,9 @@ ks_status ks_minimize(ks_problem *kp, double *X_inout, const ks_opts *opts, ks_r
   if (!(o.delta > 0.0 && o.delta < 1.0) || !(o.eta >= 0.0 && o.eta < 1.0) || o.maxit < 0 ||
       !(o.tau0 > 0.0) || o.max_backtrack < 0)
     return set_error(KS_EINVAL, "bad line-search parameters");
-  kp->P.vH_valid = false;
-  return minimize_device(kp->P, X_inout, o, res);
+  if (o.resume && !kp->P.state.valid) return set_error(KS_EINVAL, "no saved state to resume");
+  if (!o.resume) kp->P.vH_valid = false;
+  return minimize_device(kp->P, X_inout, o, res, o.resume != 0);
 }
 
 ks_status ks_minimize_host(ks_problem *kp, double *Xh, const ks_opts *opts, ks_result *res) {
@@ -605,15 +691,84 @@ ks_status ks_minimize_host(ks_problem *kp, double *Xh, const ks_opts *opts, ks_r
   // The driver reads its input block only before the first iteration and
   // writes its output only after the last one, so the block B_D1 (a
   // previous-gradient slot during the iterations) can stage the host copy.
+  if (opts && opts->resume)
+    return set_error(KS_EINVAL, "resume needs the device entry point ks_minimize");
   double *dX = P.blk[B_D1];
   KS_CUDA_TRY(cudaMemcpyAsync(dX, Xh, bytes, cudaMemcpyHostToDevice, P.stream));
   ks_status st = ks_minimize(kp, dX, opts, res);
   if (st != KS_OK && st != KS_ENOCONV) return st;
   KS_CUDA_TRY(cudaMemcpyAsync(Xh, dX, bytes, cudaMemcpyDeviceToHost, P.stream));
   KS_CUDA_TRY(cudaStreamSynchronize(P.stream));
+  // the staging block may be one of the saved state's slots
+  P.state.valid = false;
   if (res)
     res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   return st;
+}
+
+size_t ks_state_bytes(ks_problem *kp) {
+  if (!kp || !kp->P.state.valid) return 0;
+  return state_bytes(kp->P, kp->P.state.elem);
+}
+
+ks_status ks_state_save(ks_problem *kp, void *host_buf, size_t bytes) {
+  if (!kp || !host_buf) return set_error(KS_EINVAL, "null argument");
+  Problem &P = kp->P;
+  const Problem::RunState &S = P.state;
+  if (!S.valid) return set_error(KS_EINVAL, "no minimisation state to save");
+  if (bytes < state_bytes(P, S.elem)) return set_error(KS_EINVAL, "buffer too small");
+  StateHeader hd{};
+  hd.magic = kStateMagic;
+  hd.version = 1;
+  hd.N = P.N; hd.p = P.p; hd.elem = S.elem; hd.retraction = S.retraction;
+  hd.first_k = S.first_k; hd.k = S.k; hd.have_prev = S.have_prev; hd.last_improve = S.last_improve;
+  hd.C = S.C; hd.Q = S.Q; hd.E = S.E; hd.dnorm2 = S.dnorm2;
+  hd.ss = S.ss; hd.sy = S.sy; hd.yy = S.yy; hd.best = S.best;
+  char *dst = (char *)host_buf;
+  std::memcpy(dst, &hd, sizeof(hd));
+  dst += sizeof(hd);
+  const int order[9] = {S.ix[0], S.imx[0], S.iex[0], S.id[0], S.imd[0],
+                        S.ix[1], S.imx[1], S.id[1], S.imd[1]};
+  const size_t blkb = (size_t)P.n * P.p * S.elem;
+  for (int i = 0; i < 9; ++i) {
+    KS_CUDA_TRY(cudaMemcpyAsync(dst, P.blk[order[i]], blkb, cudaMemcpyDeviceToHost, P.stream));
+    dst += blkb;
+  }
+  KS_CUDA_TRY(cudaMemcpyAsync(dst, P.vH, (size_t)P.n * sizeof(double), cudaMemcpyDeviceToHost,
+                              P.stream));
+  KS_CUDA_TRY(cudaStreamSynchronize(P.stream));
+  return KS_OK;
+}
+
+ks_status ks_state_load(ks_problem *kp, const void *host_buf, size_t bytes) {
+  if (!kp || !host_buf) return set_error(KS_EINVAL, "null argument");
+  Problem &P = kp->P;
+  StateHeader hd;
+  if (bytes < sizeof(hd)) return set_error(KS_EINVAL, "buffer too small");
+  std::memcpy(&hd, host_buf, sizeof(hd));
+  if (hd.magic != kStateMagic || hd.version != 1) return set_error(KS_EINVAL, "not a saved state");
+  if (hd.N != P.N || hd.p != P.p || (hd.elem != 4 && hd.elem != 8))
+    return set_error(KS_EINVAL, "saved state does not match this problem");
+  if (bytes < state_bytes(P, hd.elem)) return set_error(KS_EINVAL, "buffer too small");
+  Problem::RunState S;
+  S.valid = true;
+  S.elem = hd.elem; S.retraction = hd.retraction; S.first_k = hd.first_k; S.k = hd.k;
+  S.have_prev = hd.have_prev; S.last_improve = hd.last_improve;
+  S.C = hd.C; S.Q = hd.Q; S.E = hd.E; S.dnorm2 = hd.dnorm2;
+  S.ss = hd.ss; S.sy = hd.sy; S.yy = hd.yy; S.best = hd.best;
+  // canonical slots: current in slot 0, previous in slot 1
+  const int order[9] = {B_X0, B_MX0, B_EX0, B_D0, B_MD0, B_X1, B_MX1, B_D1, B_MD1};
+  const char *src = (const char *)host_buf + sizeof(hd);
+  const size_t blkb = (size_t)P.n * P.p * hd.elem;
+  for (int i = 0; i < 9; ++i) {
+    KS_CUDA_TRY(cudaMemcpyAsync(P.blk[order[i]], src, blkb, cudaMemcpyHostToDevice, P.stream));
+    src += blkb;
+  }
+  KS_CUDA_TRY(cudaMemcpyAsync(P.vH, src, (size_t)P.n * sizeof(double), cudaMemcpyHostToDevice,
+                              P.stream));
+  KS_CUDA_TRY(cudaStreamSynchronize(P.stream));
+  P.state = S;
+  return KS_OK;
 }
 
 }  // extern "C"

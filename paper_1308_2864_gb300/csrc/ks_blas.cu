@@ -99,7 +99,7 @@ ks_status launch_gram(Problem &P, const T *A, int pa, const T *B, int qb, double
   if (need > P.partials_len)
     return set_error(KS_EINVAL, "gram: partial buffer too small (%zu > %zu)", need, P.partials_len);
   {
-    ProfScope ps_(P.stream, KP_GRAM);
+    ProfScope ps_(P.stream, KP_GRAM, 2.0 * P.n * pa * qb, (double)P.n * (pa + qb) * sizeof(T));
     gram_kernel<T><<<dim3(tiles, chunks), 256, 0, P.stream>>>(P.n, pa, qb, rows_per, A, B, P.partials);
   }
   KS_CUDA_TRY(cudaGetLastError());
@@ -183,7 +183,8 @@ ks_status launch_combine(Problem &P, const T *A1, int k1, const double *C1, cons
                          const double *C2, double alpha, double beta, const T *Bm, T *out, int q) {
   dim3 grid((unsigned)((P.n + kTile - 1) / kTile), (unsigned)((q + kTile - 1) / kTile));
   {
-    ProfScope ps_(P.stream, KP_COMBINE);
+    ProfScope ps_(P.stream, KP_COMBINE, 2.0 * P.n * q * (k1 + (A2 ? k2 : 0)),
+                  (double)P.n * ((k1 + (A2 ? k2 : 0)) + q * (Bm ? 2 : 1)) * sizeof(T));
     combine_kernel<T><<<grid, 256, 0, P.stream>>>(P.n, q, A1, k1, C1, A2, k2, C2, alpha, beta, Bm,
                                                 out);
   }

@@ -45,10 +45,10 @@ ks_status launch_density(Problem &P, const T *X, double *rho) {
     const long long warps = P.n;
     long long blocks = (warps * 32 + kThreads - 1) / kThreads;
     if (blocks > 64LL * P.sms) blocks = 64LL * P.sms;
-    ProfScope ps_(P.stream, KP_DENSITY);
+    ProfScope ps_(P.stream, KP_DENSITY, 2.0 * P.n * P.p, (double)P.n * P.p * sizeof(T) + 8.0 * P.n);
     density_warp_kernel<T><<<(int)blocks, kThreads, 0, P.stream>>>(P.n, P.p, P.occ, X, rho);
   } else {
-    ProfScope ps_(P.stream, KP_DENSITY);
+    ProfScope ps_(P.stream, KP_DENSITY, 2.0 * P.n * P.p, (double)P.n * P.p * sizeof(T) + 8.0 * P.n);
     density_thread_kernel<T><<<(P.n + kThreads - 1) / kThreads, kThreads, 0, P.stream>>>(
         P.n, P.p, P.occ, X, rho);
   }

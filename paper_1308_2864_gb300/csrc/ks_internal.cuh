@@ -108,6 +108,19 @@ struct Problem {
   int *dstatus = nullptr;          // device status word
   int *dstatus_host = nullptr;     // pinned mirror
 
+  // State of the last ConOptM phase (for ks_state_save / resume): slot
+  // indices of the current/previous/trial blocks and the line-search scalars.
+  struct RunState {
+    bool valid = false;
+    int elem = 8;                  // bytes per element of the phase's blocks
+    int retraction = 0;
+    int first_k = 0, k = 0;        // iteration offset of the phase, iterations in it
+    int have_prev = 0;
+    double C = 0, Q = 1, E = 0, dnorm2 = 0, ss = 0, sy = 0, yy = 0, best = 0;
+    int last_improve = 0;
+    int ix[3] = {0, 1, 2}, imx[3] = {3, 4, 5}, iex[2] = {6, 7}, id[2] = {9, 10}, imd[2] = {11, 12};
+  } state;
+
   // last mixed-precision phase
   int mixed_iters = 0;
   double mixed_dnorm = 0, mixed_E = 0;
@@ -129,8 +142,10 @@ enum ProfClass : int {
 };
 // Counts `nlaunch` kernel launches and, when timing is on, brackets the
 // scope's launches with CUDA events on `s`.
+// `flops` and `bytes` are the algorithmic work of the launch (minimal
+// arithmetic and DRAM traffic), summed per class while timing is on.
 struct ProfScope {
-  ProfScope(cudaStream_t s, int cls, int nlaunch = 1);
+  ProfScope(cudaStream_t s, int cls, double flops = 0.0, double bytes = 0.0, int nlaunch = 1);
   ~ProfScope();
   cudaStream_t stream;
   int cls;

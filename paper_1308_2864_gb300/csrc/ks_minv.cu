@@ -57,17 +57,17 @@ ks_status launch_mass_inverse(Problem &P, const T *E, T *G) {
   const int nb = (int)((work + kThreads - 1) / kThreads);
   const double s = 6.0 / P.h;
   {
-    ProfScope ps_(P.stream, KP_MASS_INV);
+    ProfScope ps_(P.stream, KP_MASS_INV, 4.0 * P.n * P.p, 2.0 * P.n * P.p * sizeof(T));
     thomas_kernel<T><<<nb, kThreads, 0, P.stream>>>(P.N, P.p, 0, s * s * s, P.thomas_w, E, G);
   }
   KS_CUDA_TRY(cudaGetLastError());
   {
-    ProfScope ps_(P.stream, KP_MASS_INV);
+    ProfScope ps_(P.stream, KP_MASS_INV, 4.0 * P.n * P.p, 2.0 * P.n * P.p * sizeof(T));
     thomas_kernel<T><<<nb, kThreads, 0, P.stream>>>(P.N, P.p, 1, 1.0, P.thomas_w, G, G);
   }
   KS_CUDA_TRY(cudaGetLastError());
   {
-    ProfScope ps_(P.stream, KP_MASS_INV);
+    ProfScope ps_(P.stream, KP_MASS_INV, 4.0 * P.n * P.p, 2.0 * P.n * P.p * sizeof(T));
     thomas_kernel<T><<<nb, kThreads, 0, P.stream>>>(P.N, P.p, 2, 1.0, P.thomas_w, G, G);
   }
   KS_CUDA_TRY(cudaGetLastError());

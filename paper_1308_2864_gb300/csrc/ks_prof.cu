@@ -28,6 +28,8 @@ struct Profiler {
   std::vector<Pending> pending;
   double ms[KS_PROF_CLASSES] = {};
   long long count[KS_PROF_CLASSES] = {};
+  double flops[KS_PROF_CLASSES] = {};
+  double bytes[KS_PROF_CLASSES] = {};
 } g_prof;
 
 cudaEvent_t take_event() {
@@ -71,10 +73,13 @@ const char *kNames[KS_PROF_CLASSES] = {
 
 }  // namespace
 
-ProfScope::ProfScope(cudaStream_t s, int cls, int nlaunch) : stream(s), cls(cls), a(nullptr) {
+ProfScope::ProfScope(cudaStream_t s, int cls, double flops, double bytes, int nlaunch)
+    : stream(s), cls(cls), a(nullptr) {
   g_launches.fetch_add((unsigned long long)nlaunch, std::memory_order_relaxed);
   std::lock_guard<std::mutex> lk(g_prof.mu);
   if (!g_prof.on) return;
+  g_prof.flops[cls] += flops;
+  g_prof.bytes[cls] += bytes;
   a = take_event();
   if (a) cudaEventRecord((cudaEvent_t)a, stream);
 }
@@ -111,6 +116,8 @@ ks_status ks_profile_start(void) {
   for (int i = 0; i < KS_PROF_CLASSES; ++i) {
     ks::g_prof.ms[i] = 0.0;
     ks::g_prof.count[i] = 0;
+    ks::g_prof.flops[i] = 0.0;
+    ks::g_prof.bytes[i] = 0.0;
   }
   ks::g_prof.on = true;
   return KS_OK;
@@ -123,6 +130,15 @@ ks_status ks_profile_stop(double ms[KS_PROF_CLASSES], long long counts[KS_PROF_C
   for (int i = 0; i < KS_PROF_CLASSES; ++i) {
     if (ms) ms[i] = ks::g_prof.ms[i];
     if (counts) counts[i] = ks::g_prof.count[i];
+  }
+  return KS_OK;
+}
+
+ks_status ks_profile_work(double flops[KS_PROF_CLASSES], double bytes[KS_PROF_CLASSES]) {
+  std::lock_guard<std::mutex> lk(ks::g_prof.mu);
+  for (int i = 0; i < KS_PROF_CLASSES; ++i) {
+    if (flops) flops[i] = ks::g_prof.flops[i];
+    if (bytes) bytes[i] = ks::g_prof.bytes[i];
   }
   return KS_OK;
 }

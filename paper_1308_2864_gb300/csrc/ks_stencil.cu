@@ -132,7 +132,7 @@ ks_status launch_hamiltonian(Problem &P, const T *X, const double *veff, T *EX, 
   const int nb = reduce_blocks(P, total);
   const double h3 = P.h * P.h * P.h;
   {
-    ProfScope ps_(P.stream, KP_HAMILTONIAN);
+    ProfScope ps_(P.stream, KP_HAMILTONIAN, 34.0 * total, (double)total * sizeof(T) * (MX ? 3 : 2) + 8.0 * P.n);
     hamiltonian_kernel<T><<<nb, kThreads, 0, P.stream>>>(P.N, P.p, total, q1_coefficients(P.h),
                                                          P.occ, h3, X, veff, EX, MX, P.partials);
   }
@@ -145,7 +145,7 @@ ks_status launch_mass(Problem &P, const T *X, T *MX) {
   const long long total = (long long)P.n * P.p;
   const int nb = reduce_blocks(P, total);
   {
-    ProfScope ps_(P.stream, KP_MASS);
+    ProfScope ps_(P.stream, KP_MASS, 30.0 * total, 2.0 * total * sizeof(T));
     mass_kernel<T, 0><<<nb, kThreads, 0, P.stream>>>(P.N, P.p, total, q1_coefficients(P.h), X,
                                                      MX, nullptr, nullptr, nullptr, nullptr,
                                                      nullptr, nullptr, nullptr);
@@ -162,7 +162,7 @@ ks_status launch_mass_dots(Problem &P, const T *D, T *MD, const T *X, const T *M
   const StencilCoef c = q1_coefficients(P.h);
   if (prev) {
     {
-      ProfScope ps_(P.stream, KP_MASS);
+      ProfScope ps_(P.stream, KP_MASS, 40.0 * total, 8.0 * total * sizeof(T));
       mass_kernel<T, 2><<<nb, kThreads, 0, P.stream>>>(P.N, P.p, total, c, D, MD, X, MX,
                                                        prev->X, prev->MX, prev->D, prev->MD,
                                                        P.partials);
@@ -171,7 +171,7 @@ ks_status launch_mass_dots(Problem &P, const T *D, T *MD, const T *X, const T *M
     return launch_reduce(P, P.partials, 4, nb, out4);
   }
   {
-    ProfScope ps_(P.stream, KP_MASS);
+    ProfScope ps_(P.stream, KP_MASS, 32.0 * total, 2.0 * total * sizeof(T));
     mass_kernel<T, 1><<<nb, kThreads, 0, P.stream>>>(P.N, P.p, total, c, D, MD, nullptr,
                                                      nullptr, nullptr, nullptr, nullptr, nullptr,
                                                      P.partials);

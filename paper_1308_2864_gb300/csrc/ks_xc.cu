@@ -111,7 +111,7 @@ ks_status launch_potential(Problem &P, const double *rho, const double *vH, cons
   const int nb = reduce_blocks(P, P.n);
   const double h3 = P.h * P.h * P.h;
   {
-    ProfScope ps_(P.stream, KP_POTENTIAL);
+    ProfScope ps_(P.stream, KP_POTENTIAL, 40.0 * P.n, 40.0 * P.n);
     potential_kernel<<<nb, kThreads, 0, P.stream>>>(P.n, h3, P.xc, with_hartree ? 1 : 0, rho,
                                                     P.vext, vH, r, veff, P.partials);
   }

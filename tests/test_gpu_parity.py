@@ -267,3 +267,27 @@ def test_mixed_precision_then_fp64_polish(retraction):
     assert abs(r["mixed_E"] - ref.E) <= 1e-5
     assert r["E"] == pytest.approx(ref.E, abs=1e-8)
     assert ost.ortho_error(model, host(X)) < 1e-12
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_checkpoint_resume_is_bitwise(precision):
+    # 25 iterations + checkpoint + 20 more (in the same problem and after a
+    # load into a fresh one) reproduce an uninterrupted 45-iteration run.
+    s = ki.small_system(N=12, L=7.0, natoms=2, p=4, Z=4.0, seed=11)
+    kw = dict(retraction="qr", gtol=1e-12, precision=precision, polish_gtol=1e-12,
+              stall_iters=0)
+    P = make(s)
+    Xa = dev(s.x0())
+    ra = P.minimize(Xa, maxit=45, **kw)
+    P2 = make(s)
+    Xb = dev(s.x0())
+    P2.minimize(Xb, maxit=25, **kw)
+    blob = P2.state_save()
+    rb = P2.minimize(Xb, maxit=45, resume=1, **kw)
+    P3 = make(s)
+    P3.state_load(blob)
+    Xc = torch.empty_like(Xb)
+    rc = P3.minimize(Xc, maxit=45, resume=1, **kw)
+    assert ra["E"] == rb["E"] == rc["E"]
+    assert torch.equal(Xa, Xb) and torch.equal(Xa, Xc)
+    assert rb["iters"] == 20 and rc["iters"] == 20
