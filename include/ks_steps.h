@@ -1,10 +1,11 @@
 /*
  * ks_steps.h -- one C entry point per step of the iteration, for callers that
- * compose their own driver and for step-by-step verification.  Each call
- * runs on the problem's stream with the problem's sizes (n = N^3 nodes, p
- * orbitals), synchronises it before returning, and follows the conventions
- * of ks.h (ks_status return value; DEVICE pointers are owned by the caller;
- * outputs must not alias inputs).
+ * compose their own driver and for step-by-step verification.  Each
+ * ks_step_* call runs on the problem's stream with the problem's sizes
+ * (n = N^3 nodes, p orbitals), synchronises it before returning, and follows
+ * the conventions of ks.h (ks_status return value; DEVICE pointers are owned
+ * by the caller; outputs must not alias inputs).  ks_gram_noalloc at the end
+ * only enqueues (see its comment).
  */
 #ifndef KS_STEPS_H
 #define KS_STEPS_H
@@ -64,6 +65,29 @@ ks_status ks_step_gram(ks_problem *prob, const double *A, int pa, const double *
 ks_status ks_step_combine(ks_problem *prob, const double *A1, int k1, const double *C1,
                           const double *A2, int k2, const double *C2, double alpha,
                           double beta, const double *Bm, double *out, int q);
+
+/* Allocation-free variant of ks_step_gram, for callers that cannot call
+ * cudaMalloc: code that runs while a CUDA graph is being captured (where
+ * allocation calls are not permitted), hosts whose device memory is owned by
+ * their own allocator or a fixed budget, and latency-bound loops that must not
+ * pay for an allocation.  It needs no ks_problem (ks_problem_create
+ * allocates) and calls no allocating routine: the per-chunk partial sums live
+ * in a file-scope device array of 2^21 doubles (16 MiB) that every GPU which
+ * loads the library holds until the process exits.  The paper has no
+ * counterpart; this is a deployment convenience around the Gram of Sec. 3.
+ *   A    DEVICE n x pa (row-major, FP64)
+ *   B    DEVICE n x qb (row-major, FP64)
+ *   out  DEVICE pa x qb, receives A^T B
+ *   stream  cudaStream_t to issue on (NULL = legacy default stream)
+ * Requires pa * qb <= 2^21 (returns KS_EINVAL otherwise).  The first call on a
+ * device looks up the array's device address for that device (with it
+ * current); make that first call before any stream capture.  The call only
+ * enqueues work: the result is ready when `stream` reaches it.  All calls in
+ * the process share the one array and every call overwrites all of it that
+ * it reads, so calls whose executions overlap on the GPU (for example on two
+ * streams at once) race and must be serialised by the caller. */
+ks_status ks_gram_noalloc(const double *A, int pa, const double *B, int qb, long long n,
+                          double *out, void *stream);
 
 #ifdef __cplusplus
 }

@@ -98,6 +98,7 @@ SIGNATURES = [
     ("ks_step_mass_inverse", _I, [_P, _P, _P]),
     ("ks_step_gram", _I, [_P, _P, _I, _P, _I, _P]),
     ("ks_step_combine", _I, [_P, _P, _I, _P, _P, _I, _P, _D, _D, _P, _P, _I]),
+    ("ks_gram_noalloc", _I, [_P, _I, _P, _I, ctypes.c_longlong, _P, _P]),
 ]
 
 

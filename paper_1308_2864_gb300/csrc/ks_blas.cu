@@ -7,7 +7,10 @@
 // FP64 arithmetic is the bound of both on GB300 (n p^2 FMAs against n p
 // words of traffic); tiles are 64 x 64 with a 4 x 4 register block per
 // thread, strided so that shared-memory reads are conflict-free.
+#include <mutex>
+
 #include "ks_device.cuh"
+#include "ks_steps.h"
 
 namespace ks {
 
@@ -245,4 +248,70 @@ ks_status launch_ortho_err(Problem &P, const double *O, double *out) {
   return KS_OK;
 }
 
+// ---------------------------------------------------------------- no-alloc
+// Scratch of ks_gram_noalloc: the per-chunk partial Grams live in this
+// file-scope device array instead of memory from cudaMalloc.  Every GPU that
+// loads the library holds it (16 MiB) until the process exits.
+constexpr size_t kNoAllocDoubles = size_t(1) << 21;
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+namespace {
+std::mutex g_noalloc_mu;
+constexpr int kMaxDevices = 64;
+double *g_noalloc_ptr[kMaxDevices] = {};
+}  // namespace
+
 }  // namespace ks
+
+extern "C" ks_status ks_gram_noalloc(const double *A, int pa, const double *B, int qb,
+                                     long long n, double *out, void *stream) {
+  using namespace ks;
+  if (!A || !B || !out) return set_error(KS_EINVAL, "null argument");
+  if (pa < 1 || qb < 1 || n < 1) return set_error(KS_EINVAL, "bad sizes");
+  if ((size_t)pa * (size_t)qb > kNoAllocDoubles)
+    return set_error(KS_EINVAL, "ks_gram_noalloc: pa * qb = %zu exceeds the scratch capacity %zu",
+                     (size_t)pa * qb, kNoAllocDoubles);
+  int dev = 0;
+  KS_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return set_error(KS_EINVAL, "device index out of range");
+  double *scratch = nullptr;
+  {
+    // first call on this device: translate the array's host-side name into
+    // its device address (with this device current)
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void *ptr = nullptr;
+      KS_CUDA_TRY(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+      g_noalloc_ptr[dev] = (double *)ptr;
+    }
+    scratch = g_noalloc_ptr[dev];
+  }
+  int sms = 0;
+  KS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int tiles = ((pa + kTile - 1) / kTile) * ((qb + kTile - 1) / kTile);
+  long long chunks = (4LL * sms + tiles - 1) / tiles;
+  const long long maxc = (n + kTileK - 1) / kTileK;
+  const long long capc = (long long)(kNoAllocDoubles / ((size_t)pa * qb));
+  if (chunks > maxc) chunks = maxc;
+  if (chunks > capc) chunks = capc;
+  if (chunks < 1) chunks = 1;
+  long long rows_per = (n + chunks - 1) / chunks;
+  rows_per = (rows_per + kTileK - 1) / kTileK * kTileK;
+  cudaStream_t s = (cudaStream_t)stream;
+  {
+    // every partial tile is written in full (zeros for empty row ranges)
+    // before the reduction reads it, so nothing needs clearing
+    ProfScope ps_(s, KP_GRAM, 2.0 * n * pa * qb, (double)n * (pa + qb) * sizeof(double));
+    gram_kernel<double><<<dim3(tiles, (unsigned)chunks), 256, 0, s>>>(n, pa, qb, rows_per, A, B,
+                                                                       scratch);
+  }
+  KS_CUDA_TRY(cudaGetLastError());
+  const long long len = (long long)pa * qb;
+  {
+    ProfScope ps_(s, KP_REDUCE);
+    gram_reduce_kernel<<<(int)((len + kThreads - 1) / kThreads), kThreads, 0, s>>>((int)chunks, len,
+                                                                                   scratch, out);
+  }
+  KS_CUDA_TRY(cudaGetLastError());
+  return KS_OK;
+}
