@@ -1,6 +1,5 @@
 // 27-point Q1 stencils over blocks of orbitals (row-major n x p, orbital
-// index fastest, so a warp reading one neighbour of consecutive orbitals is
-// a coalesced access).
+// index fastest):
 //
 //   hamiltonian:  E_X = f K X + 2 f h^3 Diag(V_eff) X   (the derivative of
 //                 Eq. EKS discretised, Sec. 2.3's E_X = H(X) X), M X, and
@@ -8,176 +7,259 @@
 //   mass:         M X
 //   mass_dots:    M D, ||D||_M^2 = sum D . M D and the Barzilai-Borwein
 //                 traces of Eq. bb-1 in the M inner product.
+//
+// Plane-marching form.  For a plane z' and a node (x, y) let
+//   c(z') = X(x, y, z'),  f(z') = sum of the 4 in-plane face neighbours,
+//   e(z') = sum of the 4 in-plane corner neighbours.
+// The 27-point neighbourhood of (x, y, z) splits into classes
+//   centre = c(z), faces = f(z) + c(z-1) + c(z+1),
+//   edges = e(z) + f(z-1) + f(z+1), corners = e(z-1) + e(z+1),
+// and the Q1 coefficients depend only on the class (the stiffness face
+// coefficient is zero).  A block owns a TX x TY tile of nodes and a chunk of
+// PC orbitals, marches along z over a segment of planes, stages one plane
+// (with a one-node halo) in shared memory per step, and keeps (c, f, e) of
+// the last three planes in registers, so each plane sum is formed once and
+// used by three output planes.  Consecutive threads take consecutive
+// orbitals of one node, so every global access is a contiguous row segment.
 #include "ks_device.cuh"
 
 namespace ks {
 
-// Neighbour sums of one orbital column around node (ix, iy, iz) by class:
-// centre, faces, edges, corners (Dirichlet: outside nodes are zero).
-template <typename T>
-struct ClassSums {
-  T s0, sf, se, sc;
+enum StencilKind : int { SK_HAM = 0, SK_MASS = 1, SK_MASS_DOT = 2, SK_MASS_BB = 3 };
+
+constexpr int kStThreads = 256;
+constexpr int kStNodesPerThread = 4;
+
+template <int PC>
+struct StTile {
+  static constexpr int G = kStThreads / PC;                // node groups
+  static constexpr int NODES = G * kStNodesPerThread;      // nodes per tile
+  static constexpr int TX = PC >= 16 ? 8 : 16;
+  static constexpr int TY = NODES / TX;
+  static constexpr int HX = TX + 2, HY = TY + 2;
 };
 
-template <typename T>
-__device__ __forceinline__ ClassSums<T> class_sums(const T *__restrict__ A, int p, int i,
-                                                   int N, int ix, int iy, int iz) {
-  ClassSums<T> s{0, 0, 0, 0};
-  const long long NN = (long long)N * N;
-#pragma unroll
-  for (int dz = -1; dz <= 1; ++dz) {
-    const int z = iz + dz;
-    if (z < 0 || z >= N) continue;
-#pragma unroll
-    for (int dy = -1; dy <= 1; ++dy) {
-      const int y = iy + dy;
-      if (y < 0 || y >= N) continue;
-#pragma unroll
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int x = ix + dx;
-        if (x < 0 || x >= N) continue;
-        const int nzc = (dx != 0) + (dy != 0) + (dz != 0);
-        const T v = __ldg(A + (z * NN + (long long)y * N + x) * p + i);
-        if (nzc == 0) s.s0 = v;
-        else if (nzc == 1) s.sf += v;
-        else if (nzc == 2) s.se += v;
-        else s.sc += v;
-      }
-    }
-  }
-  return s;
-}
+struct StArgs {
+  int N, p, zseg, tiles_x, tiles_y, chunks;
+  StencilCoef c;
+  double occ, h3;
+  const void *A;              // input block (X or D)
+  void *out1;                 // E_X (SK_HAM) or M A
+  void *out2;                 // M X (SK_HAM, optional)
+  const double *veff;
+  const void *X, *MX, *Xp, *MXp, *Dp, *MDp;   // SK_MASS_BB
+  double *part;               // block partials, channel-major
+  int nb;                     // number of blocks (partials stride)
+};
 
-// T = double (FP64 path) or float (mixed path: stencil arithmetic in FP32,
-// per-thread partial sums in FP32, block and grid sums in FP64).
-template <typename T>
-__global__ void hamiltonian_kernel(int N, int p, long long total, StencilCoef cd, double occ_d,
-                                   double h3, const T *__restrict__ X,
-                                   const double *__restrict__ veff, T *__restrict__ EX,
-                                   T *__restrict__ MX, double *__restrict__ part) {
+template <typename T, int PC, int Kind>
+__global__ void __launch_bounds__(kStThreads) stencil_kernel(StArgs a) {
+  using Tl = StTile<PC>;
+  __shared__ T tile[Tl::HY * Tl::HX * PC];
   __shared__ double smem[33];
-  const T k0 = (T)cd.k0, ke = (T)cd.ke, kc = (T)cd.kc;
-  const T m0 = (T)cd.m0, mf = (T)cd.mf, me = (T)cd.me, mc = (T)cd.mc;
-  const T occ = (T)occ_d, vscale = (T)(2.0 * occ_d * h3);
-  T kin = 0;
-  const long long NN = (long long)N * N;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long k = e / p;
-    const int i = (int)(e - k * p);
-    const int ix = (int)(k % N), iy = (int)((k / N) % N), iz = (int)(k / NN);
-    const ClassSums<T> s = class_sums<T>(X, p, i, N, ix, iy, iz);
-    const T kx = k0 * s.s0 + ke * s.se + kc * s.sc;   // face coefficient is 0
-    EX[e] = occ * kx + vscale * (T)veff[k] * s.s0;
-    if (MX) MX[e] = m0 * s.s0 + mf * s.sf + me * s.se + mc * s.sc;
-    kin = fma(s.s0, kx, kin);
-  }
-  const double sb = block_sum((double)kin, smem);
-  if (threadIdx.x == 0) part[blockIdx.x] = sb;
-}
+  const int N = a.N, p = a.p;
+  // block -> (tile x, tile y, orbital chunk, z segment)
+  int b = blockIdx.x;
+  const int txi = b % a.tiles_x; b /= a.tiles_x;
+  const int tyi = b % a.tiles_y; b /= a.tiles_y;
+  const int oc = b % a.chunks; b /= a.chunks;
+  const int zs = b;
+  const int x0 = txi * Tl::TX, y0 = tyi * Tl::TY;
+  const int z0 = zs * a.zseg;
+  const int z1 = min(z0 + a.zseg, N);
+  const int lane = threadIdx.x % PC, grp = threadIdx.x / PC;
+  const int o = oc * PC + lane;
+  const bool ovalid = o < p;
+  const T *A = (const T *)a.A;
 
-// Mode 0: MX = M X only.  Mode 1: MD = M D and sum D.MD.  Mode 2: as 1 plus
-// the three BB traces against the previous iterate.
-template <typename T, int Mode>
-__global__ void mass_kernel(int N, int p, long long total, StencilCoef cd,
-                            const T *__restrict__ D, T *__restrict__ MD,
-                            const T *__restrict__ X, const T *__restrict__ MX,
-                            const T *__restrict__ Xp, const T *__restrict__ MXp,
-                            const T *__restrict__ Dp, const T *__restrict__ MDp,
-                            double *__restrict__ part) {
-  __shared__ double smem[33];
-  const T m0 = (T)cd.m0, mf = (T)cd.mf, me = (T)cd.me, mc = (T)cd.mc;
-  T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-  const long long NN = (long long)N * N;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long k = e / p;
-    const int i = (int)(e - k * p);
-    const int ix = (int)(k % N), iy = (int)((k / N) % N), iz = (int)(k / NN);
-    const ClassSums<T> s = class_sums<T>(D, p, i, N, ix, iy, iz);
-    const T md = m0 * s.s0 + mf * s.sf + me * s.se + mc * s.sc;
-    MD[e] = md;
-    if (Mode >= 1) a0 = fma(s.s0, md, a0);
-    if (Mode == 2) {
-      const T dx = X[e] - Xp[e];
-      const T dmx = MX[e] - MXp[e];
-      const T dd = s.s0 - Dp[e];
-      const T dmd = md - MDp[e];
-      a1 = fma(dx, dmx, a1);
-      a2 = fma(dx, dmd, a2);
-      a3 = fma(dd, dmd, a3);
-    }
+  int lx[kStNodesPerThread], ly[kStNodesPerThread];
+#pragma unroll
+  for (int r = 0; r < kStNodesPerThread; ++r) {
+    const int node = grp + r * Tl::G;
+    lx[r] = node % Tl::TX;
+    ly[r] = node / Tl::TX;
   }
-  if (Mode >= 1) {
-    const int nb = gridDim.x;
-    const double s0 = block_sum((double)a0, smem);
-    if (threadIdx.x == 0) part[blockIdx.x] = s0;
-    if (Mode == 2) {
-      const double s1 = block_sum((double)a1, smem);
-      const double s2 = block_sum((double)a2, smem);
-      const double s3 = block_sum((double)a3, smem);
-      if (threadIdx.x == 0) {
-        part[nb + blockIdx.x] = s1;
-        part[2 * nb + blockIdx.x] = s2;
-        part[3 * nb + blockIdx.x] = s3;
+  T c_old[kStNodesPerThread], f_old[kStNodesPerThread], e_old[kStNodesPerThread];
+  T c_mid[kStNodesPerThread], f_mid[kStNodesPerThread], e_mid[kStNodesPerThread];
+
+  // stage plane zp (with halo) and form (c, f, e) of this thread's nodes
+  auto plane = [&](int zp, T *c, T *f, T *e) {
+    __syncthreads();
+    const bool zok = zp >= 0 && zp < N;
+    for (int t = threadIdx.x; t < Tl::HY * Tl::HX * PC; t += kStThreads) {
+      const int l = t % PC, hn = t / PC;
+      const int hx = hn % Tl::HX, hy = hn / Tl::HX;
+      const int gx = x0 + hx - 1, gy = y0 + hy - 1, go = oc * PC + l;
+      T v = 0;
+      if (zok && gx >= 0 && gx < N && gy >= 0 && gy < N && go < p)
+        v = __ldg(A + (((long long)zp * N + gy) * N + gx) * p + go);
+      tile[t] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kStNodesPerThread; ++r) {
+      const int hx = lx[r] + 1, hy = ly[r] + 1;
+      auto at = [&](int dx, int dy) { return tile[((hy + dy) * Tl::HX + hx + dx) * PC + lane]; };
+      c[r] = at(0, 0);
+      f[r] = (at(-1, 0) + at(1, 0)) + (at(0, -1) + at(0, 1));
+      e[r] = (at(-1, -1) + at(1, -1)) + (at(-1, 1) + at(1, 1));
+    }
+  };
+
+  plane(z0 - 1, c_old, f_old, e_old);
+  plane(z0, c_mid, f_mid, e_mid);
+
+  const T k0 = (T)a.c.k0, ke = (T)a.c.ke, kc = (T)a.c.kc;
+  const T m0 = (T)a.c.m0, mf = (T)a.c.mf, me = (T)a.c.me, mc = (T)a.c.mc;
+  const T occ = (T)a.occ, vscale = (T)(2.0 * a.occ * a.h3);
+  T acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
+
+  for (int z = z0; z < z1; ++z) {
+    T c_new[kStNodesPerThread], f_new[kStNodesPerThread], e_new[kStNodesPerThread];
+    plane(z + 1, c_new, f_new, e_new);
+#pragma unroll
+    for (int r = 0; r < kStNodesPerThread; ++r) {
+      const int gx = x0 + lx[r], gy = y0 + ly[r];
+      const T centre = c_mid[r];
+      const T faces = f_mid[r] + (c_old[r] + c_new[r]);
+      const T edges = e_mid[r] + (f_old[r] + f_new[r]);
+      const T corners = e_old[r] + e_new[r];
+      if (ovalid && gx < N && gy < N) {
+        const long long k = ((long long)z * N + gy) * N + gx;
+        const long long idx = k * p + o;
+        const T m = m0 * centre + mf * faces + me * edges + mc * corners;
+        if (Kind == SK_HAM) {
+          const T kx = k0 * centre + ke * edges + kc * corners;
+          ((T *)a.out1)[idx] = occ * kx + vscale * (T)a.veff[k] * centre;
+          if (a.out2) ((T *)a.out2)[idx] = m;
+          acc0 = fma(centre, kx, acc0);
+        } else {
+          ((T *)a.out1)[idx] = m;
+          if (Kind >= SK_MASS_DOT) acc0 = fma(centre, m, acc0);
+          if (Kind == SK_MASS_BB) {
+            const T dx = ((const T *)a.X)[idx] - ((const T *)a.Xp)[idx];
+            const T dmx = ((const T *)a.MX)[idx] - ((const T *)a.MXp)[idx];
+            const T dd = centre - ((const T *)a.Dp)[idx];
+            const T dmd = m - ((const T *)a.MDp)[idx];
+            acc1 = fma(dx, dmx, acc1);
+            acc2 = fma(dx, dmd, acc2);
+            acc3 = fma(dd, dmd, acc3);
+          }
+        }
       }
+      c_old[r] = c_mid[r]; f_old[r] = f_mid[r]; e_old[r] = e_mid[r];
+      c_mid[r] = c_new[r]; f_mid[r] = f_new[r]; e_mid[r] = e_new[r];
+    }
+  }
+  if (Kind == SK_MASS) return;
+  const double s0 = block_sum((double)acc0, smem);
+  if (threadIdx.x == 0) a.part[blockIdx.x] = s0;
+  if (Kind == SK_MASS_BB) {
+    const double s1 = block_sum((double)acc1, smem);
+    const double s2 = block_sum((double)acc2, smem);
+    const double s3 = block_sum((double)acc3, smem);
+    if (threadIdx.x == 0) {
+      a.part[a.nb + blockIdx.x] = s1;
+      a.part[2 * a.nb + blockIdx.x] = s2;
+      a.part[3 * a.nb + blockIdx.x] = s3;
     }
   }
 }
 
-template <typename T>
-ks_status launch_hamiltonian(Problem &P, const T *X, const double *veff, T *EX, T *MX,
-                             double *ekin_out) {
-  const long long total = (long long)P.n * P.p;
-  const int nb = reduce_blocks(P, total);
-  const double h3 = P.h * P.h * P.h;
-  {
-    ProfScope ps_(P.stream, KP_HAMILTONIAN, 34.0 * total, (double)total * sizeof(T) * (MX ? 3 : 2) + 8.0 * P.n);
-    hamiltonian_kernel<T><<<nb, kThreads, 0, P.stream>>>(P.N, P.p, total, q1_coefficients(P.h),
-                                                         P.occ, h3, X, veff, EX, MX, P.partials);
+// Geometry of a launch: tiles, orbital chunks and z segments; the number of
+// segments is lowered until the block partials (nchan per block) fit.
+template <int PC>
+static ks_status stencil_geometry(const Problem &P, int nchan, StArgs &a) {
+  using Tl = StTile<PC>;
+  a.N = P.N;
+  a.p = P.p;
+  a.tiles_x = (P.N + Tl::TX - 1) / Tl::TX;
+  a.tiles_y = (P.N + Tl::TY - 1) / Tl::TY;
+  a.chunks = (P.p + PC - 1) / PC;
+  const long long base = (long long)a.tiles_x * a.tiles_y * a.chunks;
+  // aim for about 8 blocks per SM, with segments of at least 8 planes
+  long long segs = (8LL * P.sms + base - 1) / base;
+  const long long maxsegs = (P.N + 7) / 8;
+  if (segs > maxsegs) segs = maxsegs;
+  if (segs < 1) segs = 1;
+  for (;;) {
+    a.zseg = (int)((P.N + segs - 1) / segs);
+    const long long used = (P.N + a.zseg - 1) / a.zseg;
+    const long long nb = base * used;
+    if (nchan == 0 || (size_t)(nb * nchan) <= P.partials_len) {
+      if (nb > 0x7fffffffLL) return set_error(KS_EINVAL, "stencil: grid too large");
+      a.nb = (int)nb;
+      return KS_OK;
+    }
+    if (used == 1) return set_error(KS_EINVAL, "stencil: partial buffer too small");
+    segs = used / 2;
   }
-  KS_CUDA_TRY(cudaGetLastError());
-  return launch_reduce(P, P.partials, 1, nb, ekin_out, 0.5 * P.occ);
 }
 
-template <typename T>
-ks_status launch_mass(Problem &P, const T *X, T *MX) {
-  const long long total = (long long)P.n * P.p;
-  const int nb = reduce_blocks(P, total);
+template <typename T, int Kind>
+static ks_status stencil_launch(Problem &P, StArgs &a, int nchan, double flops, double bytes) {
+  KS_TRY((P.p >= 32 ? stencil_geometry<32>(P, nchan, a)
+          : P.p >= 16 ? stencil_geometry<16>(P, nchan, a)
+          : P.p >= 8 ? stencil_geometry<8>(P, nchan, a)
+                     : stencil_geometry<4>(P, nchan, a)));
+  a.c = q1_coefficients(P.h);
+  a.part = P.partials;
+  const int cls = Kind == SK_HAM ? KP_HAMILTONIAN : KP_MASS;
   {
-    ProfScope ps_(P.stream, KP_MASS, 30.0 * total, 2.0 * total * sizeof(T));
-    mass_kernel<T, 0><<<nb, kThreads, 0, P.stream>>>(P.N, P.p, total, q1_coefficients(P.h), X,
-                                                     MX, nullptr, nullptr, nullptr, nullptr,
-                                                     nullptr, nullptr, nullptr);
+    ProfScope ps_(P.stream, cls, flops, bytes);
+    if (P.p >= 32) stencil_kernel<T, 32, Kind><<<a.nb, kStThreads, 0, P.stream>>>(a);
+    else if (P.p >= 16) stencil_kernel<T, 16, Kind><<<a.nb, kStThreads, 0, P.stream>>>(a);
+    else if (P.p >= 8) stencil_kernel<T, 8, Kind><<<a.nb, kStThreads, 0, P.stream>>>(a);
+    else stencil_kernel<T, 4, Kind><<<a.nb, kStThreads, 0, P.stream>>>(a);
   }
   KS_CUDA_TRY(cudaGetLastError());
   return KS_OK;
 }
 
 template <typename T>
+ks_status launch_hamiltonian(Problem &P, const T *X, const double *veff, T *EX, T *MX,
+                             double *ekin_out) {
+  StArgs a{};
+  a.occ = P.occ;
+  a.h3 = P.h * P.h * P.h;
+  a.A = X;
+  a.out1 = EX;
+  a.out2 = MX;
+  a.veff = veff;
+  const double total = (double)P.n * P.p;
+  KS_TRY((stencil_launch<T, SK_HAM>(P, a, 1, 27.0 * total,
+                                    total * sizeof(T) * (MX ? 3 : 2) + 8.0 * P.n)));
+  return launch_reduce(P, P.partials, 1, a.nb, ekin_out, 0.5 * P.occ);
+}
+
+template <typename T>
+ks_status launch_mass(Problem &P, const T *X, T *MX) {
+  StArgs a{};
+  a.A = X;
+  a.out1 = MX;
+  const double total = (double)P.n * P.p;
+  return stencil_launch<T, SK_MASS>(P, a, 0, 21.0 * total, 2.0 * total * sizeof(T));
+}
+
+template <typename T>
 ks_status launch_mass_dots(Problem &P, const T *D, T *MD, const T *X, const T *MX,
                            const BBPrevT<T> *prev, double *out4) {
-  const long long total = (long long)P.n * P.p;
-  const int nb = reduce_blocks(P, total);
-  const StencilCoef c = q1_coefficients(P.h);
+  StArgs a{};
+  a.A = D;
+  a.out1 = MD;
+  const double total = (double)P.n * P.p;
   if (prev) {
-    {
-      ProfScope ps_(P.stream, KP_MASS, 40.0 * total, 8.0 * total * sizeof(T));
-      mass_kernel<T, 2><<<nb, kThreads, 0, P.stream>>>(P.N, P.p, total, c, D, MD, X, MX,
-                                                       prev->X, prev->MX, prev->D, prev->MD,
-                                                       P.partials);
-    }
-    KS_CUDA_TRY(cudaGetLastError());
-    return launch_reduce(P, P.partials, 4, nb, out4);
+    a.X = X;
+    a.MX = MX;
+    a.Xp = prev->X;
+    a.MXp = prev->MX;
+    a.Dp = prev->D;
+    a.MDp = prev->MD;
+    KS_TRY((stencil_launch<T, SK_MASS_BB>(P, a, 4, 31.0 * total, 8.0 * total * sizeof(T))));
+    return launch_reduce(P, P.partials, 4, a.nb, out4);
   }
-  {
-    ProfScope ps_(P.stream, KP_MASS, 32.0 * total, 2.0 * total * sizeof(T));
-    mass_kernel<T, 1><<<nb, kThreads, 0, P.stream>>>(P.N, P.p, total, c, D, MD, nullptr,
-                                                     nullptr, nullptr, nullptr, nullptr, nullptr,
-                                                     P.partials);
-  }
-  KS_CUDA_TRY(cudaGetLastError());
-  return launch_reduce(P, P.partials, 1, nb, out4);
+  KS_TRY((stencil_launch<T, SK_MASS_DOT>(P, a, 1, 23.0 * total, 2.0 * total * sizeof(T))));
+  return launch_reduce(P, P.partials, 1, a.nb, out4);
 }
 
 #define KS_INST(T)                                                                        \
