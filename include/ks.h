@@ -47,7 +47,8 @@ typedef enum {
   KS_ENOTPD = 5,      /* Cholesky of a Gram matrix met a non-positive pivot */
   KS_ESINGULAR = 6,   /* the Cayley system I + tau/2 V^T U is singular */
   KS_ENAN = 7,        /* a non-finite value appeared */
-  KS_ETIMEOUT = 8     /* a bounded device-side wait gave up */
+  KS_ETIMEOUT = 8,    /* a bounded device-side wait gave up */
+  KS_EAGAIN = 9       /* ks_server_poll: the job has not finished yet */
 } ks_status;
 
 /* Opaque problem handle; owns all device workspace of one system. */
@@ -206,6 +207,48 @@ const char *ks_profile_class_name(int cls);
  * floating-point operations (an FMA counts 2) and minimal DRAM bytes (each
  * input block read once, each output block written once). */
 ks_status ks_profile_work(double flops[KS_PROF_CLASSES], double bytes[KS_PROF_CLASSES]);
+
+/* ------------------------------------------------------------------ serving
+ * A server runs minimisation jobs (one KS system each) with continuous
+ * batching: jobs are admitted in arrival order as soon as a slot is free and
+ * their device memory (ks_problem_bytes plus the n x p block) fits in the
+ * HBM budget; each admitted job runs on its own stream and host worker, so
+ * admitted jobs overlap on the device, and a finishing job immediately
+ * makes room for the next.  Jobs share no device state and every reduction
+ * has a fixed order, so a job's result does not depend on what else runs.
+ * The server is thread-safe; it uses the CUDA device current at creation. */
+typedef struct ks_server ks_server;
+
+typedef struct {
+  int queued;                 /* jobs waiting for admission */
+  int running;                /* jobs admitted and not finished */
+  int peak_running;           /* maximum of running so far */
+  unsigned long long completed;
+  size_t bytes_in_use;        /* device bytes of the running jobs */
+  size_t peak_bytes_in_use;   /* maximum of bytes_in_use so far (<= budget) */
+  size_t budget;
+} ks_server_counters;
+
+/* max_slots: concurrent jobs (1..256); hbm_budget_bytes: admission limit. */
+ks_status ks_server_create(size_t hbm_budget_bytes, int max_slots, ks_server **out);
+
+/* Queue one job; desc->stream is ignored (each job gets its own stream), desc
+ * geometry and X0_host (HOST n x p initial block) are copied; opts may be NULL
+ * (defaults).  Returns KS_ENOMEM when the job alone exceeds the budget. */
+ks_status ks_server_submit(ks_server *srv, const ks_problem_desc *desc, const ks_opts *opts,
+                           const double *X0_host, uint64_t *job_id);
+
+/* Result of a job: KS_EAGAIN while it is queued or running (wait = 0), or
+ * blocks until it finishes (wait != 0).  On completion fills res, X_host
+ * (HOST n x p, may be NULL) and latency_s (submit to finish, may be NULL),
+ * then forgets the job (a job can be collected once). */
+ks_status ks_server_poll(ks_server *srv, uint64_t job_id, int wait, ks_result *res,
+                         double *X_host, double *latency_s);
+
+ks_status ks_server_stats(ks_server *srv, ks_server_counters *out);
+
+/* Waits for running jobs, drops queued ones, joins the workers. */
+ks_status ks_server_destroy(ks_server *srv);
 
 /* Text of the last error on the calling thread ("" if none). */
 const char *ks_last_error_string(void);

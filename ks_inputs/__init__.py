@@ -183,6 +183,33 @@ def config_c4_jobs(seed: int = 1003, njobs: int = 256) -> list[System]:
     return jobs
 
 
+def config_c5_jobs(seed: int = 1004, njobs: int = 512) -> list[System]:
+    """Serving stream: N log-uniform in [24, 96] (spacing 0.4 bohr), p
+    log-uniform in [8, 128] rounded to an even number, p/2 atoms (Z = 4)
+    placed like c4."""
+    jobs = []
+    for j in range(njobs):
+        rng = SplitMix64(stream_key(seed, j, STREAM_JOBSIZE))
+        N = int(round(math.exp(math.log(24) + (math.log(96) - math.log(24)) * rng.uniform())))
+        p = int(round(math.exp(math.log(8) + (math.log(128) - math.log(8)) * rng.uniform()) / 2)) * 2
+        p = min(max(p, 8), 128)
+        natoms = p // 2
+        L = 0.4 * (N + 1)
+        arng = SplitMix64(stream_key(seed, j, STREAM_ATOMS))
+        atoms = _random_atoms(arng, natoms, 1.5, L - 1.5, 1.2, 0.8)
+        jobs.append(System(N=N, L=L, atoms=atoms, Z=np.full(natoms, 4.0), p=p, xc=1,
+                           retraction="qr", seed=seed, job=j,
+                           name=f"c5 job {j}: {N}^3, p={p}"))
+    return jobs
+
+
+def poisson_arrivals(seed: int, njobs: int, rate: float) -> np.ndarray:
+    """Arrival times (s) of a Poisson stream with the given rate (jobs/s):
+    cumulative exponential gaps -ln(1-u)/rate from the arrivals stream."""
+    u = uniform_block(stream_key(seed, 0, STREAM_ARRIVALS), njobs)
+    return np.cumsum(-np.log1p(-u) / rate)
+
+
 def small_system(N: int = 6, L: float = 6.0, natoms: int = 1, p: int = 2,
                  xc: int = 1, seed: int = 7, retraction: str = "qr",
                  Z: float | None = None) -> System:

@@ -18,9 +18,10 @@ import numpy as np
 
 from . import build as _build
 
-KS_OK, KS_EINVAL, KS_ENOMEM, KS_ECUDA, KS_ENOCONV, KS_ENOTPD, KS_ESINGULAR, KS_ENAN, KS_ETIMEOUT = range(9)
+(KS_OK, KS_EINVAL, KS_ENOMEM, KS_ECUDA, KS_ENOCONV, KS_ENOTPD, KS_ESINGULAR, KS_ENAN, KS_ETIMEOUT,
+ KS_EAGAIN) = range(10)
 STATUS_NAMES = ["KS_OK", "KS_EINVAL", "KS_ENOMEM", "KS_ECUDA", "KS_ENOCONV", "KS_ENOTPD",
-                "KS_ESINGULAR", "KS_ENAN", "KS_ETIMEOUT"]
+                "KS_ESINGULAR", "KS_ENAN", "KS_ETIMEOUT", "KS_EAGAIN"]
 KS_XC_SLATER, KS_XC_SLATER_PZ81 = 0, 1
 KS_FP64, KS_MIXED = 0, 1
 KS_QR, KS_CAYLEY = 0, 1
@@ -61,6 +62,12 @@ class Result(ctypes.Structure):
                 ("mixed_E", ctypes.c_double)]
 
 
+class ServerStats(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_int), ("running", ctypes.c_int), ("peak_running", ctypes.c_int),
+                ("completed", ctypes.c_ulonglong), ("bytes_in_use", ctypes.c_size_t),
+                ("peak_bytes_in_use", ctypes.c_size_t), ("budget", ctypes.c_size_t)]
+
+
 _LIB = None
 _P = ctypes.c_void_p
 _D = ctypes.c_double
@@ -99,6 +106,12 @@ SIGNATURES = [
     ("ks_step_gram", _I, [_P, _P, _I, _P, _I, _P]),
     ("ks_step_combine", _I, [_P, _P, _I, _P, _P, _I, _P, _D, _D, _P, _P, _I]),
     ("ks_gram_noalloc", _I, [_P, _I, _P, _I, ctypes.c_longlong, _P, _P]),
+    ("ks_server_create", _I, [ctypes.c_size_t, _I, ctypes.POINTER(_P)]),
+    ("ks_server_submit", _I, [_P, ctypes.POINTER(ProblemDesc), ctypes.POINTER(Opts), _DP,
+                              ctypes.POINTER(ctypes.c_uint64)]),
+    ("ks_server_poll", _I, [_P, ctypes.c_uint64, _I, ctypes.POINTER(Result), _DP, _DP]),
+    ("ks_server_stats", _I, [_P, ctypes.POINTER(ServerStats)]),
+    ("ks_server_destroy", _I, [_P]),
 ]
 
 
@@ -377,5 +390,63 @@ class Problem:
         return out
 
 
-__all__ = ["Problem", "KSError", "load_library", "library_path", "default_opts",
+class Server:
+    """Continuous-batching job server (ks_server): submit systems as they
+    arrive, collect results; admission is bounded by an HBM budget and a
+    number of concurrent slots."""
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int):
+        lib = load_library()
+        h = ctypes.c_void_p()
+        _check(lib.ks_server_create(int(hbm_budget_bytes), int(max_slots), ctypes.byref(h)))
+        self._h = h
+
+    def submit(self, s, x0: np.ndarray | None = None, **opts) -> int:
+        """Queue the ks_inputs.System `s` (initial block s.x0() unless given)."""
+        x0 = np.ascontiguousarray(s.x0() if x0 is None else x0, dtype=np.float64)
+        atoms = np.ascontiguousarray(np.asarray(s.atoms, dtype=np.float64).reshape(-1, 3))
+        Z = np.ascontiguousarray(np.asarray(s.Z, dtype=np.float64).reshape(-1))
+        d = ProblemDesc()
+        d.N, d.L, d.natoms = s.N, s.L, len(Z)
+        d.R = atoms.ctypes.data_as(_DP)
+        d.Z = Z.ctypes.data_as(_DP)
+        d.rc, d.p, d.occ, d.xc = s.rc, s.p, s.occ, s.xc
+        d.cg_tol, d.cg_maxit, d.precision, d.cg_precond = 1e-10, 20000, KS_FP64, 1
+        o = default_opts(**opts)
+        jid = ctypes.c_uint64()
+        _check(load_library().ks_server_submit(self._h, ctypes.byref(d), ctypes.byref(o),
+                                               x0.ctypes.data_as(_DP), ctypes.byref(jid)))
+        return int(jid.value)
+
+    def poll(self, job_id: int, wait: bool = True, want_x: bool = False, n: int = 0, p: int = 0):
+        """None while running (wait=False); else (result dict, X or None, latency s)."""
+        r = Result()
+        lat = ctypes.c_double()
+        X = np.empty((n, p), dtype=np.float64) if want_x else None
+        st = load_library().ks_server_poll(self._h, job_id, 1 if wait else 0, ctypes.byref(r),
+                                           X.ctypes.data_as(_DP) if want_x else None,
+                                           ctypes.byref(lat))
+        if st == KS_EAGAIN:
+            return None
+        _check(st)
+        return result_dict(r), X, lat.value
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(load_library().ks_server_stats(self._h, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load_library().ks_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+__all__ = ["Server", "Problem", "KSError", "load_library", "library_path", "default_opts",
            "KS_QR", "KS_CAYLEY", "KS_XC_SLATER", "KS_XC_SLATER_PZ81", "SIGNATURES"]

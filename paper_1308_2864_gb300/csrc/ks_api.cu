@@ -80,22 +80,30 @@ static ks_status validate(const ks_problem_desc *d) {
   return KS_OK;
 }
 
+// Device memory is stream-ordered (cudaMallocAsync / cudaFreeAsync on the
+// problem's stream), so creating and destroying problems does not
+// synchronise the device while other problems run on other streams.
 static void free_problem(Problem &P) {
-  auto f = [](void *q) { if (q) cudaFree(q); };
+  cudaStream_t s = P.stream;
+  auto f = [s](void *q) { if (q) cudaFreeAsync(q, s); };
   f(P.vext); f(P.rho); f(P.vH); f(P.veff); f(P.cg_r); f(P.cg_pa); f(P.cg_pb); f(P.cg_q);
   f(P.cg_z); f(P.cg_t1); f(P.cg_t2); f(P.dst_phi); f(P.dst_kap); f(P.dst_mu);
   for (auto &b : P.blk) f(b);
-  f(P.pp); f(P.partials); f(P.scal); f(P.atoms_dev); f(P.thomas_w); f(P.bar); f(P.dstatus);
-  if (P.scal_host) cudaFreeHost(P.scal_host);
-  if (P.dstatus_host) cudaFreeHost(P.dstatus_host);
+  f(P.pp); f(P.partials); f(P.scal); f(P.atoms_dev); f(P.thomas_w); f(P.bar); f(P.red_counter); f(P.dstatus);
+  delete[] P.scal_host;
+  delete[] P.dstatus_host;
+  P.scal_host = nullptr;
+  P.dstatus_host = nullptr;
+  if (s) cudaStreamSynchronize(s);
+  cudaGetLastError();
   if (P.own_stream && P.stream) cudaStreamDestroy(P.stream);
 }
 
 template <typename T>
 static ks_status dalloc(T **ptr, size_t count, Problem &P) {
   const size_t bytes = count * sizeof(T) > 0 ? count * sizeof(T) : sizeof(T);
-  cudaError_t e = cudaMalloc((void **)ptr, bytes);
-  if (e != cudaSuccess) return cuda_error(e, "cudaMalloc");
+  cudaError_t e = cudaMallocAsync((void **)ptr, bytes, P.stream);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync");
   P.bytes += bytes;
   return KS_OK;
 }
@@ -351,8 +359,11 @@ static ks_status run_phase(Problem &P, const T *Xstart, T *Xend, const ks_opts &
     E = Et;
     ++k;
     bool reortho = false;
-    if (o.retraction == KS_CAYLEY || sizeof(T) == 4 ||
-        (o.ortho_every > 0 && (first_k + k) % o.ortho_every == 0)) {
+    // the Cayley path checks every iteration (Sec. 4.1); the QR path every
+    // ortho_every iterations (every 5 in the FP32 phase, whose rounding
+    // drifts faster)
+    const int every = sizeof(T) == 4 ? std::min(o.ortho_every, 5) : o.ortho_every;
+    if (o.retraction == KS_CAYLEY || (every > 0 && (first_k + k) % every == 0)) {
       double oerr = 0;
       KS_TRY(ortho_error<T>(P, X(0), MX(0), &oerr));
       reortho = oerr > ortho_tol;
@@ -578,7 +589,8 @@ ks_status ks_problem_create(const ks_problem_desc *d, ks_problem **out) {
   for (auto &b : P.blk) { ALLOC(b, np); }
   P.pp_len = (size_t)S_COUNT * P.p * P.p;
   ALLOC(P.pp, P.pp_len);
-  P.cg_blocks = cg_grid_blocks(P.sms, P.n);
+  P.cg_blocks = cg_grid_blocks(P.sms, P.n, P.N);
+  if (P.cg_blocks < 1) return fail(set_error(KS_ECUDA, "CG kernel configuration failed"));
   size_t part = gram_partials_len(P.p, P.sms);
   if ((size_t)4 * 8 * P.sms > part) part = (size_t)4 * 8 * P.sms;
   if ((size_t)4 * P.cg_blocks > part) part = (size_t)4 * P.cg_blocks;
@@ -588,21 +600,24 @@ ks_status ks_problem_create(const ks_problem_desc *d, ks_problem **out) {
   ALLOC(P.atoms_dev, P.atoms_host.size());
   ALLOC(P.thomas_w, (size_t)P.N);
   ALLOC(P.bar, 1);
+  ALLOC(P.red_counter, 1);
   ALLOC(P.dstatus, 1);
 #undef ALLOC
-  e = cudaMallocHost((void **)&P.scal_host, SC_COUNT * sizeof(double));
-  if (e != cudaSuccess) return fail(cuda_error(e, "cudaMallocHost"));
-  e = cudaMallocHost((void **)&P.dstatus_host, sizeof(int));
-  if (e != cudaSuccess) return fail(cuda_error(e, "cudaMallocHost"));
+  P.scal_host = new (std::nothrow) double[SC_COUNT];
+  P.dstatus_host = new (std::nothrow) int[1];
+  if (!P.scal_host || !P.dstatus_host) return fail(set_error(KS_ENOMEM, "host allocation failed"));
   e = cudaMemcpyAsync(P.atoms_dev, P.atoms_host.data(), P.atoms_host.size() * sizeof(double),
                       cudaMemcpyHostToDevice, P.stream);
   if (e != cudaSuccess) return fail(cuda_error(e, "copy atoms"));
   e = cudaMemsetAsync(P.scal, 0, SC_COUNT * sizeof(double), P.stream);
   if (e != cudaSuccess) return fail(cuda_error(e, "memset"));
+  e = cudaMemsetAsync(P.red_counter, 0, sizeof(unsigned int), P.stream);
+  if (e != cudaSuccess) return fail(cuda_error(e, "memset"));
   e = cudaMemsetAsync(P.dstatus, 0, sizeof(int), P.stream);
   if (e != cudaSuccess) return fail(cuda_error(e, "memset"));
   e = cudaMemsetAsync(P.vH, 0, n * sizeof(double), P.stream);
   if (e != cudaSuccess) return fail(cuda_error(e, "memset"));
+  if ((st = configure_small_kernels()) != KS_OK) return fail(st);
   if ((st = launch_setup(P)) != KS_OK) return fail(st);
   if ((st = launch_sine_setup(P)) != KS_OK) return fail(st);
   if ((st = sync_scalars(P)) != KS_OK) return fail(st);

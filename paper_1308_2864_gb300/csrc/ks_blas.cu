@@ -17,7 +17,9 @@ namespace ks {
 static int gram_chunks(const Problem &P, int pa, int qb) {
   const int tiles = ((pa + kTile - 1) / kTile) * ((qb + kTile - 1) / kTile);
   int chunks = (4 * P.sms + tiles - 1) / tiles;
-  const int maxc = (P.n + kTileK - 1) / kTileK;
+  // at least 256 rows per chunk, so small problems do not pay for many
+  // partial tiles
+  const int maxc = (P.n + 255) / 256;
   if (chunks > maxc) chunks = maxc;
   if (chunks < 1) chunks = 1;
   return chunks;
@@ -83,13 +85,21 @@ __global__ void __launch_bounds__(256) gram_kernel(long long n, int pa, int qb, 
   }
 }
 
+// out[e] = sum over chunks of part[c * len + e]: 8 threads per output, each
+// summing a strided eighth of the chunks, then a fixed butterfly (the order
+// is the same on every run).
 __global__ void gram_reduce_kernel(int chunks, long long len, const double *__restrict__ part,
                                    double *__restrict__ out) {
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= len) return;
-  double s = 0.0;
-  for (int c = 0; c < chunks; ++c) s += part[(long long)c * len + e];
-  out[e] = s;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long e = t >> 3;
+  const int sub = (int)(t & 7);
+  double acc = 0.0;
+  if (e < len)
+    for (int c = sub; c < chunks; c += 8) acc += part[(long long)c * len + e];
+  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+  if (sub == 0 && e < len) out[e] = acc;
 }
 
 template <typename T>
@@ -109,7 +119,7 @@ ks_status launch_gram(Problem &P, const T *A, int pa, const T *B, int qb, double
   const long long len = (long long)pa * qb;
   {
     ProfScope ps_(P.stream, KP_REDUCE);
-    gram_reduce_kernel<<<(int)((len + kThreads - 1) / kThreads), kThreads, 0, P.stream>>>(
+    gram_reduce_kernel<<<(int)((8 * len + kThreads - 1) / kThreads), kThreads, 0, P.stream>>>(
         chunks, len, P.partials, out);
   }
   KS_CUDA_TRY(cudaGetLastError());
@@ -309,8 +319,8 @@ extern "C" ks_status ks_gram_noalloc(const double *A, int pa, const double *B, i
   const long long len = (long long)pa * qb;
   {
     ProfScope ps_(s, KP_REDUCE);
-    gram_reduce_kernel<<<(int)((len + kThreads - 1) / kThreads), kThreads, 0, s>>>((int)chunks, len,
-                                                                                   scratch, out);
+    gram_reduce_kernel<<<(int)((8 * len + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+        (int)chunks, len, scratch, out);
   }
   KS_CUDA_TRY(cudaGetLastError());
   return KS_OK;

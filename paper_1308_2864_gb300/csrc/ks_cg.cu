@@ -40,6 +40,7 @@ struct CgArgs {
   int maxit;
   int warm;
   int precond;
+  int fused;                  // fused shared-memory preconditioner (N <= kFusedMaxN)
 };
 
 // (K v)_k for v = a + beta * b (b ignored when UseB is false), Dirichlet.
@@ -135,6 +136,102 @@ __device__ bool apply_precond(const CgArgs &a, long long tid, long long stride, 
   return true;
 }
 
+// Fused form for N <= kFusedMaxN, with the planes in shared memory (3 N^2
+// floats of dynamic shared memory: a plane, Phi and a work matrix):
+//   A: each z-plane P (N x N, rows y, columns x) -> Phi P Phi   (x and y)
+//   B: each y-slab S (rows z, columns x)          -> Phi (Lambda^{-1} o (Phi S))
+//   C: each z-plane                               -> Phi P Phi, written as z
+// (Phi is symmetric, so Phi P Phi transforms both in-plane axes), three grid
+// barriers per application instead of six.
+constexpr int kFusedMaxN = 128;
+
+// out = A B for N x N row-major matrices in shared memory (256 threads).
+__device__ __forceinline__ void smem_matmul(const float *A, const float *B, float *out, int N) {
+  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+    const int i = e / N, j = e % N;
+    float acc = 0.f;
+    for (int k = 0; k < N; ++k) acc = fmaf(A[i * N + k], B[k * N + j], acc);
+    out[e] = acc;
+  }
+}
+
+// Phi P Phi for the plane z of `in` (FP64 r or FP32 work), into out32 or,
+// for the last step, out64 with the r.z accumulation.
+template <bool InD, bool OutD>
+__device__ double fused_plane_pass(const CgArgs &a, const void *in, float *out32, double *out64,
+                                   float *sh) {
+  const int N = a.N;
+  const long long NN = (long long)N * N;
+  float *Pm = sh, *Ph = sh + NN, *W = sh + 2 * NN;
+  double rz = 0.0;
+  for (int z = blockIdx.x; z < N; z += gridDim.x) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < NN; e += blockDim.x) {
+      Pm[e] = InD ? (float)__ldcg((const double *)in + z * NN + e)
+                  : __ldcg((const float *)in + z * NN + e);
+    }
+    __syncthreads();
+    smem_matmul(Pm, Ph, W, N);      // x: P Phi
+    __syncthreads();
+    smem_matmul(Ph, W, Pm, N);      // y: Phi (P Phi)
+    __syncthreads();
+    for (int e = threadIdx.x; e < NN; e += blockDim.x) {
+      if (OutD) {
+        const double zv = (double)Pm[e];
+        out64[z * NN + e] = zv;
+        rz = fma(a.r[z * NN + e], zv, rz);
+      } else {
+        out32[z * NN + e] = Pm[e];
+      }
+    }
+  }
+  return rz;
+}
+
+// For each y: S[z][x] -> Phi (Lambda^{-1} o (Phi S)) along z.
+__device__ void fused_slab_pass(const CgArgs &a, const float *in, float *out, float *sh) {
+  const int N = a.N;
+  const long long NN = (long long)N * N;
+  float *Sm = sh, *Ph = sh + NN, *W = sh + 2 * NN;
+  for (int y = blockIdx.x; y < N; y += gridDim.x) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < NN; e += blockDim.x) {
+      const int zz = e / N, x = e % N;
+      Sm[e] = __ldcg(in + (long long)zz * NN + (long long)y * N + x);
+    }
+    __syncthreads();
+    smem_matmul(Ph, Sm, W, N);      // forward along z
+    __syncthreads();
+    for (int e = threadIdx.x; e < NN; e += blockDim.x) {
+      const int c = e / N, x = e % N;
+      const float lam = a.kap[x] * a.mu[y] * a.mu[c] + a.mu[x] * a.kap[y] * a.mu[c] +
+                        a.mu[x] * a.mu[y] * a.kap[c];
+      W[e] = W[e] / lam;
+    }
+    __syncthreads();
+    smem_matmul(Ph, W, Sm, N);      // inverse along z
+    __syncthreads();
+    for (int e = threadIdx.x; e < NN; e += blockDim.x) {
+      const int zz = e / N, x = e % N;
+      out[(long long)zz * NN + (long long)y * N + x] = Sm[e];
+    }
+  }
+}
+
+__device__ bool apply_precond_fused(const CgArgs &a, double *rz_l) {
+  extern __shared__ float dyn[];
+  const int N = a.N;
+  const int NN = N * N;
+  // Phi into shared memory once per application
+  for (int e = threadIdx.x; e < NN; e += blockDim.x) dyn[NN + e] = __ldg(a.phi + e);
+  fused_plane_pass<true, false>(a, a.r, a.t1, nullptr, dyn);
+  if (!grid_barrier(a.bar, a.status)) return false;
+  fused_slab_pass(a, a.t1, a.t2, dyn);
+  if (!grid_barrier(a.bar, a.status)) return false;
+  *rz_l = fused_plane_pass<false, true>(a, a.t2, nullptr, a.z, dyn);
+  return true;
+}
+
 __global__ void __launch_bounds__(kCgThreads) cg_kernel(CgArgs a) {
   __shared__ double smem[33];
   const int nb = gridDim.x;
@@ -174,7 +271,7 @@ __global__ void __launch_bounds__(kCgThreads) cg_kernel(CgArgs a) {
   const double *s_vec = a.precond ? a.z : a.r;
   if (a.precond && rr > thr) {
     double rz_l = 0.0;
-    if (!apply_precond(a, tid, stride, &rz_l)) return;
+    if (a.fused ? !apply_precond_fused(a, &rz_l) : !apply_precond(a, tid, stride, &rz_l)) return;
     const double s = block_sum(rz_l, smem);
     if (threadIdx.x == 0) partC[blockIdx.x] = s;
     if (!grid_barrier(a.bar, a.status)) return;
@@ -224,7 +321,8 @@ __global__ void __launch_bounds__(kCgThreads) cg_kernel(CgArgs a) {
     double rho_new = rr_new;
     if (a.precond && rr_new > thr) {
       double rz_l = 0.0;
-      if (!apply_precond(a, tid, stride, &rz_l)) return;
+      if (a.fused ? !apply_precond_fused(a, &rz_l) : !apply_precond(a, tid, stride, &rz_l))
+        return;
       const double s = block_sum(rz_l, smem);
       if (threadIdx.x == 0) partC[blockIdx.x] = s;
       if (!grid_barrier(a.bar, a.status)) return;
@@ -298,19 +396,33 @@ ks_status launch_cg(Problem &P, const double *rho, double *v, double *r, bool wa
   a.maxit = P.cg_maxit;
   a.warm = warm ? 1 : 0;
   a.precond = P.cg_precond;
+  a.fused = P.N <= kFusedMaxN ? 1 : 0;
+  const size_t dyn = a.fused ? cg_dynamic_smem(P.N) : 0;
   KS_CUDA_TRY(cudaMemsetAsync(P.bar, 0, sizeof(GridBarrier), P.stream));
   void *args[] = {&a};
   {
     ProfScope ps_(P.stream, KP_CG);
     KS_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)cg_kernel, dim3(P.cg_blocks),
-                                            dim3(kCgThreads), args, 0, P.stream));
+                                            dim3(kCgThreads), args, dyn, P.stream));
   }
   return KS_OK;
 }
 
-int cg_grid_blocks(int sms, int n) {
+size_t cg_dynamic_smem(int N) {
+  return N <= kFusedMaxN ? (size_t)3 * N * N * sizeof(float) : 0;
+}
+
+int cg_grid_blocks(int sms, int n, int N) {
+  const size_t dyn = cg_dynamic_smem(N);
+  // always opt in to the largest fused size, so that problems of different
+  // N (e.g. concurrent server jobs) never lower the limit under each other
+  if (cudaFuncSetAttribute(cg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)cg_dynamic_smem(kFusedMaxN)) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_kernel, kCgThreads, 0) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_kernel, kCgThreads, dyn) !=
       cudaSuccess || per_sm < 1)
     per_sm = 1;
   long long want = (n + kCgThreads - 1) / kCgThreads;

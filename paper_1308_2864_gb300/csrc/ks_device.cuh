@@ -43,6 +43,31 @@ __device__ __forceinline__ double block_sum_array(const double *src, int nb, dou
   return block_sum(acc, smem);
 }
 
+// Last-block reduction: every block has written its nchan partial sums to
+// part[c * nb + blockIdx.x] (thread 0); the block that arrives last sums
+// each channel over all blocks in index order (the same order whichever
+// block is last, so the result is deterministic), writes scale * sum to
+// out[c] and re-arms the counter for the next launch on the stream.
+__device__ __forceinline__ void grid_reduce_tail(const double *part, int nb, int nchan,
+                                                 double *out, double scale,
+                                                 unsigned int *counter, double *smem) {
+  __shared__ int s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int prev = atomicAdd(counter, 1u);
+    s_last = (prev == (unsigned int)nb - 1u);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int c = 0; c < nchan; ++c) {
+    const double sacc = block_sum_array(part + (long long)c * nb, nb, smem);
+    if (threadIdx.x == 0) out[c] = scale * sacc;
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
 __device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int *p) {
   unsigned int v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");

@@ -105,6 +105,7 @@ struct Problem {
   double *atoms_dev = nullptr;
   double *thomas_w = nullptr;      // N pivots of the 1-D mass solve
   GridBarrier *bar = nullptr;
+  unsigned int *red_counter = nullptr;  // last-block reduction counter (rests at 0)
   int *dstatus = nullptr;          // device status word
   int *dstatus_host = nullptr;     // pinned mirror
 
@@ -163,7 +164,8 @@ ks_status launch_density(Problem &P, const T *X, double *rho);
 // ks_cg.cu: K v = 4 pi h^3 rho; v in/out (warm if warm), r out
 ks_status launch_cg(Problem &P, const double *rho, double *v, double *r, bool warm);
 ks_status launch_sine_setup(Problem &P);
-int cg_grid_blocks(int sms, int n);
+int cg_grid_blocks(int sms, int n, int N);
+size_t cg_dynamic_smem(int N);
 // ks_xc.cu: veff = vext + vH + v_xc(rho); energy partials; reduction helpers
 ks_status launch_potential(Problem &P, const double *rho, const double *vH, const double *r,
                            double *veff, bool with_hartree);
@@ -210,6 +212,8 @@ ks_status launch_qr_factor(Problem &P, const double *DMD, const double *O, doubl
 // X+ = X C1 + G C2.  A = X^T E_X, S = E_X^T X, B = E_X^T G, O = X^T M X.
 ks_status launch_cayley_factor(Problem &P, const double *A, const double *S, const double *B,
                                const double *O, double tau, double *C1, double *C2);
+// Function attributes of the small kernels (once per problem creation).
+ks_status configure_small_kernels();
 // Transpose a p x p matrix into out.
 ks_status launch_transpose(Problem &P, const double *A, double *out);
 

@@ -88,12 +88,110 @@ __global__ void __launch_bounds__(kSmallThreads) qr_factor_kernel(int p, const d
   }
 }
 
+// Shared-memory variant for p <= kSmemMaxP: the matrix and L^{-1} stay in
+// shared memory (2 p^2 doubles); Cholesky, then L^{-1} column by column.
+constexpr int kSmemMaxP = 104;
+
+// 1/sqrt(d) for d > 0 in FP64: FP32 seed, then two Newton steps
+// y <- y (3 - d y^2) / 2 (each doubles the correct bits: 24 -> 48 -> 53).
+__device__ __forceinline__ double rsqrt_newton(double d) {
+  double y = (double)rsqrtf((float)d);
+  y = y * (1.5 - 0.5 * d * y * y);
+  y = y * (1.5 - 0.5 * d * y * y);
+  return y;
+}
+
+// On GB300 one SM retires two FP64 lanes per clock, so every FP64 warp
+// instruction costs the same whether its lanes are busy or not: the kernel
+// keeps warps dense (flat loops over the trailing triangle, one thread per
+// column in the substitution) and replaces divisions by reciprocals.
+__global__ void __launch_bounds__(kSmallThreads) qr_factor_smem_kernel(
+    int p, const double *DMD, const double *O, double tau, double *C1, double *C2, int *status) {
+  extern __shared__ double W[];          // p*p L, then p*p L^{-1} (column-major), p reciprocals
+  double *V = W + p * p;
+  double *rdiag = V + p * p;
+  __shared__ int s_fail;
+  const double t2 = tau * tau;
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    const int i = e / p, j = e % p;
+    double r = O ? O[e] : (i == j ? 1.0 : 0.0);
+    if (DMD) r = fma(t2, DMD[e], r);
+    W[e] = r;
+  }
+  if (threadIdx.x == 0) s_fail = 0;
+  __syncthreads();
+  for (int j = 0; j < p; ++j) {
+    if (threadIdx.x == 0) {
+      const double d = W[j * p + j];
+      if (!(d > 0.0) || !isfinite(d)) {
+        s_fail = 1;
+        atomicCAS(status, 0, (int)KS_ENOTPD);
+      } else {
+        const double y = rsqrt_newton(d);
+        W[j * p + j] = d * y;
+        rdiag[j] = y;
+      }
+    }
+    __syncthreads();
+    if (s_fail) return;
+    const double inv = rdiag[j];
+    for (int i = j + 1 + threadIdx.x; i < p; i += blockDim.x) W[i * p + j] *= inv;
+    __syncthreads();
+    const int m = p - j - 1;
+    for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+      const int ii = t / m, kk = t - ii * m;
+      if (kk <= ii) {
+        const int i = j + 1 + ii, k = j + 1 + kk;
+        W[i * p + k] = fma(-W[i * p + j], W[k * p + j], W[i * p + k]);
+      }
+    }
+    __syncthreads();
+  }
+  // L^{-1}: thread c solves L x = e_c; V[k * p + c] = (L^{-1})_{kc}
+  for (int c = threadIdx.x; c < p; c += blockDim.x) {
+    for (int k = 0; k < c; ++k) V[k * p + c] = 0.0;
+    V[c * p + c] = rdiag[c];
+    for (int i = c + 1; i < p; ++i) {
+      double acc = 0.0;
+      for (int k = c; k < i; ++k) acc = fma(W[i * p + k], V[k * p + c], acc);
+      V[i * p + c] = -acc * rdiag[i];
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    const int i = e / p, j = e % p;
+    const double cval = V[j * p + i];     // (L^{-T})_{ij} = (L^{-1})_{ji}
+    C1[e] = cval;
+    if (C2) C2[e] = -tau * cval;
+  }
+}
+
+// Opt the shared-memory factor kernel into its dynamic shared memory (on the
+// current device; called when a problem is created).
+ks_status configure_small_kernels() {
+  KS_CUDA_TRY(cudaFuncSetAttribute(
+      qr_factor_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      (int)(((size_t)2 * kSmemMaxP * kSmemMaxP + kSmemMaxP) * sizeof(double))));
+  return KS_OK;
+}
+
 ks_status launch_qr_factor(Problem &P, const double *DMD, const double *O, double tau,
                            double *C1, double *C2) {
   const int p = P.p;
+  const double pf = (double)p;
+  if (p <= kSmemMaxP) {
+    const size_t smem = ((size_t)2 * p * p + p) * sizeof(double);
+    {
+      ProfScope ps_(P.stream, KP_SMALL, 2.0 * pf * pf * pf / 3.0, 0.0);
+      qr_factor_smem_kernel<<<1, kSmallThreads, smem, P.stream>>>(p, DMD, O, tau, C1, C2,
+                                                                  P.dstatus);
+    }
+    KS_CUDA_TRY(cudaGetLastError());
+    return KS_OK;
+  }
   double *W = P.pp, *Linv = P.pp + (size_t)p * p;
   {
-    ProfScope ps_(P.stream, KP_SMALL);
+    ProfScope ps_(P.stream, KP_SMALL, 2.0 * pf * pf * pf / 3.0, 0.0);
     qr_factor_kernel<<<1, kSmallThreads, 0, P.stream>>>(p, DMD, O, tau, W, Linv, C1, C2,
                                                         P.dstatus);
   }

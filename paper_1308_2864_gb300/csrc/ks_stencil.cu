@@ -50,6 +50,9 @@ struct StArgs {
   const void *X, *MX, *Xp, *MXp, *Dp, *MDp;   // SK_MASS_BB
   double *part;               // block partials, channel-major
   int nb;                     // number of blocks (partials stride)
+  double *red_out;            // reduced channels (scaled by red_scale)
+  double red_scale;
+  unsigned int *counter;
 };
 
 template <typename T, int PC, int Kind>
@@ -164,6 +167,8 @@ __global__ void __launch_bounds__(kStThreads) stencil_kernel(StArgs a) {
       a.part[3 * a.nb + blockIdx.x] = s3;
     }
   }
+  grid_reduce_tail(a.part, a.nb, Kind == SK_MASS_BB ? 4 : 1, a.red_out, a.red_scale, a.counter,
+                   smem);
 }
 
 // Geometry of a launch: tiles, orbital chunks and z segments; the number of
@@ -204,6 +209,7 @@ static ks_status stencil_launch(Problem &P, StArgs &a, int nchan, double flops, 
                      : stencil_geometry<4>(P, nchan, a)));
   a.c = q1_coefficients(P.h);
   a.part = P.partials;
+  a.counter = P.red_counter;
   const int cls = Kind == SK_HAM ? KP_HAMILTONIAN : KP_MASS;
   {
     ProfScope ps_(P.stream, cls, flops, bytes);
@@ -226,10 +232,11 @@ ks_status launch_hamiltonian(Problem &P, const T *X, const double *veff, T *EX, 
   a.out1 = EX;
   a.out2 = MX;
   a.veff = veff;
+  a.red_out = ekin_out;
+  a.red_scale = 0.5 * P.occ;
   const double total = (double)P.n * P.p;
-  KS_TRY((stencil_launch<T, SK_HAM>(P, a, 1, 27.0 * total,
-                                    total * sizeof(T) * (MX ? 3 : 2) + 8.0 * P.n)));
-  return launch_reduce(P, P.partials, 1, a.nb, ekin_out, 0.5 * P.occ);
+  return stencil_launch<T, SK_HAM>(P, a, 1, 27.0 * total,
+                                   total * sizeof(T) * (MX ? 3 : 2) + 8.0 * P.n);
 }
 
 template <typename T>
@@ -247,6 +254,8 @@ ks_status launch_mass_dots(Problem &P, const T *D, T *MD, const T *X, const T *M
   StArgs a{};
   a.A = D;
   a.out1 = MD;
+  a.red_out = out4;
+  a.red_scale = 1.0;
   const double total = (double)P.n * P.p;
   if (prev) {
     a.X = X;
@@ -255,11 +264,9 @@ ks_status launch_mass_dots(Problem &P, const T *D, T *MD, const T *X, const T *M
     a.MXp = prev->MX;
     a.Dp = prev->D;
     a.MDp = prev->MD;
-    KS_TRY((stencil_launch<T, SK_MASS_BB>(P, a, 4, 31.0 * total, 8.0 * total * sizeof(T))));
-    return launch_reduce(P, P.partials, 4, a.nb, out4);
+    return stencil_launch<T, SK_MASS_BB>(P, a, 4, 31.0 * total, 8.0 * total * sizeof(T));
   }
-  KS_TRY((stencil_launch<T, SK_MASS_DOT>(P, a, 1, 23.0 * total, 2.0 * total * sizeof(T))));
-  return launch_reduce(P, P.partials, 1, a.nb, out4);
+  return stencil_launch<T, SK_MASS_DOT>(P, a, 1, 23.0 * total, 2.0 * total * sizeof(T));
 }
 
 #define KS_INST(T)                                                                        \

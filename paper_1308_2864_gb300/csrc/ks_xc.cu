@@ -49,7 +49,8 @@ __device__ __forceinline__ void lda_point(double rho, int xc, double &eps, doubl
 __global__ void potential_kernel(long long n, double h3, int xc, int with_h,
                                  const double *__restrict__ rho, const double *__restrict__ vext,
                                  const double *__restrict__ vH, const double *__restrict__ r,
-                                 double *__restrict__ veff, double *__restrict__ part) {
+                                 double *__restrict__ veff, double *__restrict__ part,
+                                 double *__restrict__ out, unsigned int *counter) {
   __shared__ double smem[33];
   const double inv8pi = 1.0 / (8.0 * M_PI);
   double e_ext = 0.0, e_h = 0.0, e_xc = 0.0;
@@ -77,6 +78,7 @@ __global__ void potential_kernel(long long n, double h3, int xc, int with_h,
     part[nb + blockIdx.x] = s1;
     part[2 * nb + blockIdx.x] = s2;
   }
+  grid_reduce_tail(part, nb, 3, out, 1.0, counter, smem);
 }
 
 // out[c] = scale * sum_{b < nb} part[c * nb + b], one block per channel, in
@@ -113,10 +115,11 @@ ks_status launch_potential(Problem &P, const double *rho, const double *vH, cons
   {
     ProfScope ps_(P.stream, KP_POTENTIAL, 40.0 * P.n, 40.0 * P.n);
     potential_kernel<<<nb, kThreads, 0, P.stream>>>(P.n, h3, P.xc, with_hartree ? 1 : 0, rho,
-                                                    P.vext, vH, r, veff, P.partials);
+                                                    P.vext, vH, r, veff, P.partials,
+                                                    P.scal + SC_EEXT, P.red_counter);
   }
   KS_CUDA_TRY(cudaGetLastError());
-  return launch_reduce(P, P.partials, 3, nb, P.scal + SC_EEXT);
+  return KS_OK;
 }
 
 }  // namespace ks

@@ -1,0 +1,111 @@
+"""Batched and served minimisation jobs through the continuous-batching server.
+
+  python -m paper_1308_2864_gb300.serve_bench --workload c4 --jobs 256 --slots 32
+  python -m paper_1308_2864_gb300.serve_bench --workload c5 --jobs 64 --rate-frac 0.5
+
+c4: uneven jobs (N in [20, 48], p = 2 x atoms in [4, 32]) all submitted at
+    once; reports solves/s and the latency spread.
+c5: a Poisson stream (N in [24, 96], p in [8, 128]); the arrival rate is a
+    fraction of the saturation throughput measured first on the same jobs
+    (or --rate jobs/s).  Reports p50/p99 latency (submit to result) and
+    solves/s.
+Each job runs Alg. ConOptM to ||D||_M <= gtol or --maxit iterations.  One JSON
+line per run on stdout.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def run(jobs, arrivals, slots, budget, opts):
+    """Submit jobs at the given arrival times (s from start, None = at once),
+    collect all results; returns (wall s, latencies, results, server stats)."""
+    import numpy as np
+    import paper_1308_2864_gb300 as ks
+    srv = ks.Server(hbm_budget_bytes=budget, max_slots=slots)
+    x0 = [np.ascontiguousarray(s.x0()) for s in jobs]
+    ids = [None] * len(jobs)
+    t0 = time.perf_counter()
+
+    def feeder():
+        for i, s in enumerate(jobs):
+            if arrivals is not None:
+                dt = arrivals[i] - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+            ids[i] = srv.submit(s, x0=x0[i], **opts)
+
+    th = threading.Thread(target=feeder)
+    th.start()
+    lat, res = [], []
+    for i in range(len(jobs)):
+        while ids[i] is None:
+            time.sleep(1e-4)
+        r, _, l = srv.poll(ids[i], wait=True)
+        lat.append(l)
+        res.append(r)
+    th.join()
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    return wall, lat, res, st
+
+
+def main(argv=None) -> int:
+    import numpy as np
+    import torch
+
+    import ks_inputs as ki
+
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--workload", default="c4", choices=["c4", "c5"])
+    ap.add_argument("--jobs", type=int, default=64)
+    ap.add_argument("--slots", type=int, default=16)
+    ap.add_argument("--budget-gb", type=float, default=180.0)
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--maxit", type=int, default=300)
+    ap.add_argument("--gtol", type=float, default=1e-6)
+    ap.add_argument("--rate", type=float, default=0.0, help="c5 arrivals per second")
+    ap.add_argument("--rate-frac", type=float, default=0.5,
+                    help="c5: arrival rate as a fraction of the measured saturation throughput")
+    a = ap.parse_args(argv)
+    torch.cuda.init()
+    jobs = (ki.config_c4_jobs(njobs=a.jobs) if a.workload == "c4"
+            else ki.config_c5_jobs(njobs=a.jobs))
+    opts = dict(retraction="qr", gtol=a.gtol, maxit=a.maxit, precision=a.precision)
+    budget = int(a.budget_gb * (1 << 30))
+    out = {"workload": a.workload, "jobs": a.jobs, "slots": a.slots, "precision": a.precision,
+           "maxit": a.maxit, "budget_gb": a.budget_gb}
+    wall, lat, res, st = run(jobs, None, a.slots, budget, opts)
+    sat = a.jobs / wall
+    out.update({"saturation_solves_per_s": sat, "batch_wall_s": wall,
+                "batch_p50_s": float(np.percentile(lat, 50)),
+                "batch_p99_s": float(np.percentile(lat, 99)),
+                "peak_running": st["peak_running"],
+                "peak_gb_in_use": st["peak_bytes_in_use"] / (1 << 30),
+                "converged": sum(r["status"] == 0 for r in res),
+                "iters_total": sum(r["iters"] for r in res)})
+    if a.workload == "c5":
+        rate = a.rate if a.rate > 0 else a.rate_frac * sat
+        arr = ki.poisson_arrivals(1004, a.jobs, rate)
+        wall, lat, res, st = run(jobs, arr, a.slots, budget, opts)
+        out.update({"rate_jobs_per_s": rate, "stream_wall_s": wall,
+                    "solves_per_s": a.jobs / wall,
+                    "p50_latency_s": float(np.percentile(lat, 50)),
+                    "p99_latency_s": float(np.percentile(lat, 99)),
+                    "stream_peak_running": st["peak_running"]})
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
