@@ -59,6 +59,14 @@ ks_status ks_step_mass_inverse(ks_problem *prob, const double *E, double *G);
 ks_status ks_step_gram(ks_problem *prob, const double *A, int pa, const double *B, int qb,
                        double *out);
 
+/* FP32 Gram of the mixed-precision phase, out = A^T B in FP64 (A: DEVICE
+ * n x pa FP32, B: DEVICE n x qb FP32, 1 <= pa, qb <= p).  For pa, qb > 8 it
+ * runs on the tensor cores with three TF32 products per term (hi.hi + hi.lo
+ * + lo.hi, about 2^-21 relative error per product) and FP32 accumulation
+ * within a chunk of rows; chunks are summed in FP64. */
+ks_status ks_step_gram_f32(ks_problem *prob, const float *A, int pa, const float *B, int qb,
+                           double *out);
+
 /* out = alpha (A1 C1 + A2 C2) + beta Bm: A1 DEVICE n x k1, C1 DEVICE k1 x q,
  * A2 DEVICE n x k2 or NULL, C2 DEVICE k2 x q, Bm DEVICE n x q or NULL,
  * out DEVICE n x q (1 <= k1, k2, q <= p). */

@@ -104,6 +104,7 @@ SIGNATURES = [
     ("ks_step_mass", _I, [_P, _P, _P]),
     ("ks_step_mass_inverse", _I, [_P, _P, _P]),
     ("ks_step_gram", _I, [_P, _P, _I, _P, _I, _P]),
+    ("ks_step_gram_f32", _I, [_P, _P, _I, _P, _I, _P]),
     ("ks_step_combine", _I, [_P, _P, _I, _P, _P, _I, _P, _D, _D, _P, _P, _I]),
     ("ks_gram_noalloc", _I, [_P, _I, _P, _I, ctypes.c_longlong, _P, _P]),
     ("ks_server_create", _I, [ctypes.c_size_t, _I, ctypes.POINTER(_P)]),
@@ -378,6 +379,18 @@ class Problem:
         pa, qb = A.shape[1], B.shape[1]
         out = torch.empty((pa, qb), dtype=torch.float64, device="cuda")
         _check(load_library().ks_step_gram(self._h, _ptr(A), pa, _ptr(B), qb, _ptr(out)))
+        return out
+
+    def step_gram_f32(self, A, B):
+        """FP32 Gram of the mixed phase (A, B float32 CUDA tensors)."""
+        import torch
+        for t in (A, B):
+            if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+                raise TypeError("expected contiguous torch.float32 CUDA tensors")
+        pa, qb = A.shape[1], B.shape[1]
+        out = torch.empty((pa, qb), dtype=torch.float64, device="cuda")
+        _check(load_library().ks_step_gram_f32(self._h, A.data_ptr(), pa, B.data_ptr(), qb,
+                                               _ptr(out)))
         return out
 
     def step_combine(self, A1, C1, A2=None, C2=None, alpha: float = 1.0, beta: float = 0.0, Bm=None):

@@ -618,6 +618,7 @@ ks_status ks_problem_create(const ks_problem_desc *d, ks_problem **out) {
   e = cudaMemsetAsync(P.vH, 0, n * sizeof(double), P.stream);
   if (e != cudaSuccess) return fail(cuda_error(e, "memset"));
   if ((st = configure_small_kernels()) != KS_OK) return fail(st);
+  if ((st = configure_tc_kernels()) != KS_OK) return fail(st);
   if ((st = launch_setup(P)) != KS_OK) return fail(st);
   if ((st = launch_sine_setup(P)) != KS_OK) return fail(st);
   if ((st = sync_scalars(P)) != KS_OK) return fail(st);

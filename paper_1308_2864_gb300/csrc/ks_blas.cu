@@ -102,8 +102,84 @@ __global__ void gram_reduce_kernel(int chunks, long long len, const double *__re
   if (sub == 0 && e < len) out[e] = acc;
 }
 
+// Small Grams (pa, qb <= kSmallPQ): each thread accumulates the whole pa x qb
+// outer-product sum of its rows in registers, so no arithmetic is spent on
+// padding (on GB300 every wasted FP64 FMA costs as much as a useful one);
+// warp butterflies then a fixed-order sum over the warps give the chunk
+// partial.
+constexpr int kSmallPQ = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(256) gram_small_kernel(long long n, int pa, int qb,
+                                                         long long rows_per,
+                                                         const T *__restrict__ A,
+                                                         const T *__restrict__ B,
+                                                         double *__restrict__ part) {
+  __shared__ double red[8][kSmallPQ * kSmallPQ];
+  const int chunk = blockIdx.x;
+  const long long r0 = chunk * rows_per;
+  long long r1 = r0 + rows_per;
+  if (r1 > n) r1 = n;
+  T acc[kSmallPQ][kSmallPQ];
+#pragma unroll
+  for (int a = 0; a < kSmallPQ; ++a)
+#pragma unroll
+    for (int b = 0; b < kSmallPQ; ++b) acc[a][b] = 0;
+  for (long long r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+    T av[kSmallPQ], bv[kSmallPQ];
+#pragma unroll
+    for (int a = 0; a < kSmallPQ; ++a) av[a] = a < pa ? A[r * pa + a] : (T)0;
+#pragma unroll
+    for (int b = 0; b < kSmallPQ; ++b) bv[b] = b < qb ? B[r * qb + b] : (T)0;
+#pragma unroll
+    for (int a = 0; a < kSmallPQ; ++a) {
+      if (a >= pa) break;
+#pragma unroll
+      for (int b = 0; b < kSmallPQ; ++b) {
+        if (b >= qb) break;
+        acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+      }
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int a = 0; a < kSmallPQ; ++a) {
+    if (a >= pa) break;
+#pragma unroll
+    for (int b = 0; b < kSmallPQ; ++b) {
+      if (b >= qb) break;
+      double v = (double)acc[a][b];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) red[warp][a * kSmallPQ + b] = v;
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < pa * qb; e += blockDim.x) {
+    const int a = e / qb, b = e % qb;
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w][a * kSmallPQ + b];
+    part[(long long)chunk * pa * qb + e] = v;
+  }
+}
+
 template <typename T>
 ks_status launch_gram(Problem &P, const T *A, int pa, const T *B, int qb, double *out) {
+  if (sizeof(T) == 4 && P.use_tc && pa > kSmallPQ && qb > kSmallPQ) {
+    // FP32 phase: tensor cores (3 x TF32), FP64 chunk partials
+    const int chunks = gram_tc_chunks(P, pa, qb);
+    if ((size_t)chunks * pa * qb > P.partials_len)
+      return set_error(KS_EINVAL, "gram: partial buffer too small");
+    KS_TRY(launch_gram_tc(P, (const float *)A, pa, (const float *)B, qb, P.partials, chunks));
+    const long long len = (long long)pa * qb;
+    {
+      ProfScope ps_(P.stream, KP_REDUCE);
+      gram_reduce_kernel<<<(int)((8 * len + kThreads - 1) / kThreads), kThreads, 0, P.stream>>>(
+          chunks, len, P.partials, out);
+    }
+    KS_CUDA_TRY(cudaGetLastError());
+    return KS_OK;
+  }
   const int chunks = gram_chunks(P, pa, qb);
   long long rows_per = (P.n + chunks - 1) / chunks;
   rows_per = (rows_per + kTileK - 1) / kTileK * kTileK;
@@ -113,7 +189,11 @@ ks_status launch_gram(Problem &P, const T *A, int pa, const T *B, int qb, double
     return set_error(KS_EINVAL, "gram: partial buffer too small (%zu > %zu)", need, P.partials_len);
   {
     ProfScope ps_(P.stream, KP_GRAM, 2.0 * P.n * pa * qb, (double)P.n * (pa + qb) * sizeof(T));
-    gram_kernel<T><<<dim3(tiles, chunks), 256, 0, P.stream>>>(P.n, pa, qb, rows_per, A, B, P.partials);
+    if (pa <= kSmallPQ && qb <= kSmallPQ)
+      gram_small_kernel<T><<<chunks, 256, 0, P.stream>>>(P.n, pa, qb, rows_per, A, B, P.partials);
+    else
+      gram_kernel<T><<<dim3(tiles, chunks), 256, 0, P.stream>>>(P.n, pa, qb, rows_per, A, B,
+                                                                P.partials);
   }
   KS_CUDA_TRY(cudaGetLastError());
   const long long len = (long long)pa * qb;
@@ -191,9 +271,56 @@ __global__ void __launch_bounds__(256) combine_kernel(long long n, int q, const 
   }
 }
 
+// Narrow updates (q <= kNarrowQ): one thread per output entry, the small
+// C matrices in shared memory, no padded arithmetic.
+constexpr int kNarrowQ = 32;
+constexpr int kNarrowK = 2 * kNarrowQ;
+
+template <typename T>
+__global__ void __launch_bounds__(256) combine_narrow_kernel(
+    long long n, int q, const T *__restrict__ A1, int k1, const double *__restrict__ C1,
+    const T *__restrict__ A2, int k2, const double *__restrict__ C2, double alpha_d,
+    double beta_d, const T *__restrict__ Bm, T *__restrict__ out) {
+  __shared__ T Cs[2][kNarrowK * kNarrowQ];
+  for (int e = threadIdx.x; e < k1 * q; e += blockDim.x) Cs[0][e] = (T)C1[e];
+  if (A2)
+    for (int e = threadIdx.x; e < k2 * q; e += blockDim.x) Cs[1][e] = (T)C2[e];
+  __syncthreads();
+  const T alpha = (T)alpha_d, beta = (T)beta_d;
+  const long long total = n * q;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long row = e / q;
+    const int col = (int)(e - row * q);
+    T acc = 0;
+    const T *a1 = A1 + row * k1;
+    for (int k = 0; k < k1; ++k) acc = fma(a1[k], Cs[0][k * q + col], acc);
+    if (A2) {
+      const T *a2 = A2 + row * k2;
+      for (int k = 0; k < k2; ++k) acc = fma(a2[k], Cs[1][k * q + col], acc);
+    }
+    T v = alpha * acc;
+    if (Bm) v = fma(beta, Bm[e], v);
+    out[e] = v;
+  }
+}
+
 template <typename T>
 ks_status launch_combine(Problem &P, const T *A1, int k1, const double *C1, const T *A2, int k2,
                          const double *C2, double alpha, double beta, const T *Bm, T *out, int q) {
+  if (q <= kNarrowQ && k1 <= kNarrowK && (!A2 || k2 <= kNarrowK)) {
+    const long long total = (long long)P.n * q;
+    long long nb = (total + 255) / 256;
+    if (nb > 32LL * P.sms) nb = 32LL * P.sms;
+    {
+      ProfScope ps_(P.stream, KP_COMBINE, 2.0 * P.n * q * (k1 + (A2 ? k2 : 0)),
+                    (double)P.n * ((k1 + (A2 ? k2 : 0)) + q * (Bm ? 2 : 1)) * sizeof(T));
+      combine_narrow_kernel<T><<<(int)nb, 256, 0, P.stream>>>(P.n, q, A1, k1, C1, A2, k2, C2,
+                                                              alpha, beta, Bm, out);
+    }
+    KS_CUDA_TRY(cudaGetLastError());
+    return KS_OK;
+  }
   dim3 grid((unsigned)((P.n + kTile - 1) / kTile), (unsigned)((q + kTile - 1) / kTile));
   {
     ProfScope ps_(P.stream, KP_COMBINE, 2.0 * P.n * q * (k1 + (A2 ? k2 : 0)),

@@ -87,6 +87,7 @@ struct Problem {
   float *cg_t1 = nullptr, *cg_t2 = nullptr;  // sine-transform work (FP32)
   float *dst_phi = nullptr, *dst_kap = nullptr, *dst_mu = nullptr;
   int cg_precond = 1;
+  int use_tc = 1;                  // tensor-core Grams in the FP32 phase
   bool vH_valid = false;           // warm start available
 
   // n x p blocks
@@ -214,6 +215,11 @@ ks_status launch_cayley_factor(Problem &P, const double *A, const double *S, con
                                const double *O, double tau, double *C1, double *C2);
 // Function attributes of the small kernels (once per problem creation).
 ks_status configure_small_kernels();
+// ks_tc.cu: FP32 Gram on the tensor cores (partials per chunk, FP64)
+ks_status configure_tc_kernels();
+int gram_tc_chunks(const Problem &P, int pa, int qb);
+ks_status launch_gram_tc(Problem &P, const float *A, int pa, const float *B, int qb,
+                         double *part, int chunks);
 // Transpose a p x p matrix into out.
 ks_status launch_transpose(Problem &P, const double *A, double *out);
 

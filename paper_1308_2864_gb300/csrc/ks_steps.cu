@@ -113,6 +113,14 @@ ks_status ks_step_gram(ks_problem *kp, const double *A, int pa, const double *B,
   return finish(kp->P);
 }
 
+ks_status ks_step_gram_f32(ks_problem *kp, const float *A, int pa, const float *B, int qb,
+                           double *out) {
+  if (!kp || !A || !B || !out) return set_error(KS_EINVAL, "null argument");
+  if (pa < 1 || qb < 1 || pa > kp->P.p || qb > kp->P.p) return set_error(KS_EINVAL, "bad sizes");
+  KS_TRY(launch_gram<float>(kp->P, A, pa, B, qb, out));
+  return finish(kp->P);
+}
+
 ks_status ks_step_combine(ks_problem *kp, const double *A1, int k1, const double *C1,
                           const double *A2, int k2, const double *C2, double alpha, double beta,
                           const double *Bm, double *out, int q) {

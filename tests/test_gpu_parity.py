@@ -291,3 +291,21 @@ def test_checkpoint_resume_is_bitwise(precision):
     assert ra["E"] == rb["E"] == rc["E"]
     assert torch.equal(Xa, Xb) and torch.equal(Xa, Xc)
     assert rb["iters"] == 20 and rc["iters"] == 20
+
+
+@pytest.mark.parametrize("shape", [(13, 70, 70), (16, 64, 64), (11, 130, 70), (9, 12, 9)])
+def test_fp32_gram_tensor_cores(shape):
+    # FP32 Gram of the mixed phase: tensor cores (3 x TF32) for pa, qb > 8,
+    # the register kernel below; compared with the exact FP64 product of
+    # the same FP32 inputs.  n = N^3 rows is ragged against the 32-row stage.
+    N, pa, qb = shape
+    s = ki.small_system(N=N, L=7.0, natoms=2, p=max(pa, qb), Z=4.0, seed=4)
+    P = make(s)
+    rng = np.random.default_rng(21)
+    A = rng.standard_normal((s.n, pa)).astype(np.float32)
+    B = rng.standard_normal((s.n, qb)).astype(np.float32)
+    got = host(P.step_gram_f32(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()))
+    want = A.astype(np.float64).T @ B.astype(np.float64)
+    # |A|^T |B| bounds the rounding of every entry
+    bound = np.abs(A.astype(np.float64)).T @ np.abs(B.astype(np.float64))
+    assert np.all(np.abs(got - want) <= 2e-6 * bound + 1e-12)
