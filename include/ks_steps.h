@@ -59,6 +59,11 @@ ks_status ks_step_mass_inverse(ks_problem *prob, const double *E, double *G);
 ks_status ks_step_gram(ks_problem *prob, const double *A, int pa, const double *B, int qb,
                        double *out);
 
+/* Tensor-core use of the FP32 phase: 0 never, 1 (default) for products of
+ * at least 256 x 256 columns, 2 always (pa, qb, q > 8 for the Gram, q > 32
+ * for the update). */
+ks_status ks_set_tensor_cores(ks_problem *prob, int mode);
+
 /* FP32 Gram of the mixed-precision phase, out = A^T B in FP64 (A: DEVICE
  * n x pa FP32, B: DEVICE n x qb FP32, 1 <= pa, qb <= p).  For pa, qb > 8 it
  * runs on the tensor cores with three TF32 products per term (hi.hi + hi.lo
@@ -66,6 +71,14 @@ ks_status ks_step_gram(ks_problem *prob, const double *A, int pa, const double *
  * within a chunk of rows; chunks are summed in FP64. */
 ks_status ks_step_gram_f32(ks_problem *prob, const float *A, int pa, const float *B, int qb,
                            double *out);
+
+/* FP32 update of the mixed-precision phase, out = alpha (A1 C1 + A2 C2) +
+ * beta Bm with FP32 blocks A1 (n x k1), A2 (n x k2 or NULL), Bm (n x q or NULL),
+ * out (n x q) and FP64 C1 (k1 x q), C2 (k2 x q), all DEVICE.  For q > 32 it runs
+ * on the tensor cores (three TF32 products per term). */
+ks_status ks_step_combine_f32(ks_problem *prob, const float *A1, int k1, const double *C1,
+                              const float *A2, int k2, const double *C2, double alpha,
+                              double beta, const float *Bm, float *out, int q);
 
 /* out = alpha (A1 C1 + A2 C2) + beta Bm: A1 DEVICE n x k1, C1 DEVICE k1 x q,
  * A2 DEVICE n x k2 or NULL, C2 DEVICE k2 x q, Bm DEVICE n x q or NULL,

@@ -105,6 +105,8 @@ SIGNATURES = [
     ("ks_step_mass_inverse", _I, [_P, _P, _P]),
     ("ks_step_gram", _I, [_P, _P, _I, _P, _I, _P]),
     ("ks_step_gram_f32", _I, [_P, _P, _I, _P, _I, _P]),
+    ("ks_set_tensor_cores", _I, [_P, _I]),
+    ("ks_step_combine_f32", _I, [_P, _P, _I, _P, _P, _I, _P, _D, _D, _P, _P, _I]),
     ("ks_step_combine", _I, [_P, _P, _I, _P, _P, _I, _P, _D, _D, _P, _P, _I]),
     ("ks_gram_noalloc", _I, [_P, _I, _P, _I, ctypes.c_longlong, _P, _P]),
     ("ks_server_create", _I, [ctypes.c_size_t, _I, ctypes.POINTER(_P)]),
@@ -381,6 +383,10 @@ class Problem:
         _check(load_library().ks_step_gram(self._h, _ptr(A), pa, _ptr(B), qb, _ptr(out)))
         return out
 
+    def set_tensor_cores(self, mode: int):
+        """FP32-phase tensor cores: 0 never, 1 wide products (default), 2 always."""
+        _check(load_library().ks_set_tensor_cores(self._h, mode))
+
     def step_gram_f32(self, A, B):
         """FP32 Gram of the mixed phase (A, B float32 CUDA tensors)."""
         import torch
@@ -391,6 +397,18 @@ class Problem:
         out = torch.empty((pa, qb), dtype=torch.float64, device="cuda")
         _check(load_library().ks_step_gram_f32(self._h, A.data_ptr(), pa, B.data_ptr(), qb,
                                                _ptr(out)))
+        return out
+
+    def step_combine_f32(self, A1, C1, A2=None, C2=None, alpha: float = 1.0, beta: float = 0.0,
+                         Bm=None):
+        """FP32 update of the mixed phase (A1, A2, Bm float32; C1, C2 float64)."""
+        import torch
+        q = C1.shape[1]
+        out = torch.empty((A1.shape[0], q), dtype=torch.float32, device="cuda")
+        ptr = lambda t: None if t is None else t.data_ptr()
+        _check(load_library().ks_step_combine_f32(
+            self._h, ptr(A1), A1.shape[1], _ptr(C1), ptr(A2), A2.shape[1] if A2 is not None else 0,
+            _ptr(C2), alpha, beta, ptr(Bm), ptr(out), q))
         return out
 
     def step_combine(self, A1, C1, A2=None, C2=None, alpha: float = 1.0, beta: float = 0.0, Bm=None):

@@ -14,6 +14,15 @@
 
 namespace ks {
 
+// Tensor cores for the FP32 phase when the products are wide enough for the
+// SIMT FP32 pipes to be the bound (use_tc = 1: from 256 columns; 2: always;
+// 0: never).  At p = 64 the SIMT kernels are as fast as the register-staged
+// tensor-core kernels, which do not yet overlap their loads deeply enough.
+static bool use_tensor_cores(const Problem &P, int a, int b) {
+  if (P.use_tc == 0 || a <= 8 || b <= 8) return false;
+  return P.use_tc == 2 || (a >= 256 && b >= 256);
+}
+
 static int gram_chunks(const Problem &P, int pa, int qb) {
   const int tiles = ((pa + kTile - 1) / kTile) * ((qb + kTile - 1) / kTile);
   int chunks = (4 * P.sms + tiles - 1) / tiles;
@@ -165,7 +174,7 @@ __global__ void __launch_bounds__(256) gram_small_kernel(long long n, int pa, in
 
 template <typename T>
 ks_status launch_gram(Problem &P, const T *A, int pa, const T *B, int qb, double *out) {
-  if (sizeof(T) == 4 && P.use_tc && pa > kSmallPQ && qb > kSmallPQ) {
+  if (sizeof(T) == 4 && use_tensor_cores(P, pa, qb)) {
     // FP32 phase: tensor cores (3 x TF32), FP64 chunk partials
     const int chunks = gram_tc_chunks(P, pa, qb);
     if ((size_t)chunks * pa * qb > P.partials_len)
@@ -308,6 +317,9 @@ __global__ void __launch_bounds__(256) combine_narrow_kernel(
 template <typename T>
 ks_status launch_combine(Problem &P, const T *A1, int k1, const double *C1, const T *A2, int k2,
                          const double *C2, double alpha, double beta, const T *Bm, T *out, int q) {
+  if (sizeof(T) == 4 && q > kNarrowQ && use_tensor_cores(P, k1, q))
+    return launch_combine_tc(P, (const float *)A1, k1, C1, (const float *)A2, k2, C2, alpha, beta,
+                             (const float *)Bm, (float *)out, q);
   if (q <= kNarrowQ && k1 <= kNarrowK && (!A2 || k2 <= kNarrowK)) {
     const long long total = (long long)P.n * q;
     long long nb = (total + 255) / 256;

@@ -87,7 +87,7 @@ struct Problem {
   float *cg_t1 = nullptr, *cg_t2 = nullptr;  // sine-transform work (FP32)
   float *dst_phi = nullptr, *dst_kap = nullptr, *dst_mu = nullptr;
   int cg_precond = 1;
-  int use_tc = 1;                  // tensor-core Grams in the FP32 phase
+  int use_tc = 1;                  // FP32-phase tensor cores: 0 never, 1 for wide products, 2 always
   bool vH_valid = false;           // warm start available
 
   // n x p blocks
@@ -220,6 +220,9 @@ ks_status configure_tc_kernels();
 int gram_tc_chunks(const Problem &P, int pa, int qb);
 ks_status launch_gram_tc(Problem &P, const float *A, int pa, const float *B, int qb,
                          double *part, int chunks);
+ks_status launch_combine_tc(Problem &P, const float *A1, int k1, const double *C1,
+                            const float *A2, int k2, const double *C2, double alpha, double beta,
+                            const float *Bm, float *out, int q);
 // Transpose a p x p matrix into out.
 ks_status launch_transpose(Problem &P, const double *A, double *out);
 

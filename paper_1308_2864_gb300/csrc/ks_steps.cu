@@ -113,6 +113,12 @@ ks_status ks_step_gram(ks_problem *kp, const double *A, int pa, const double *B,
   return finish(kp->P);
 }
 
+ks_status ks_set_tensor_cores(ks_problem *kp, int mode) {
+  if (!kp || mode < 0 || mode > 2) return set_error(KS_EINVAL, "bad argument");
+  kp->P.use_tc = mode;
+  return KS_OK;
+}
+
 ks_status ks_step_gram_f32(ks_problem *kp, const float *A, int pa, const float *B, int qb,
                            double *out) {
   if (!kp || !A || !B || !out) return set_error(KS_EINVAL, "null argument");
@@ -130,6 +136,18 @@ ks_status ks_step_combine(ks_problem *kp, const double *A1, int k1, const double
     return set_error(KS_EINVAL, "bad sizes");
   if (out == A1 || out == A2 || out == Bm) return set_error(KS_EINVAL, "output aliases input");
   KS_TRY(launch_combine(kp->P, A1, k1, C1, A2, k2, C2, alpha, beta, Bm, out, q));
+  return finish(kp->P);
+}
+
+ks_status ks_step_combine_f32(ks_problem *kp, const float *A1, int k1, const double *C1,
+                              const float *A2, int k2, const double *C2, double alpha, double beta,
+                              const float *Bm, float *out, int q) {
+  if (!kp || !A1 || !C1 || !out) return set_error(KS_EINVAL, "null argument");
+  const int p = kp->P.p;
+  if (k1 < 1 || k1 > p || q < 1 || q > p || (A2 && (k2 < 1 || k2 > p || !C2)))
+    return set_error(KS_EINVAL, "bad sizes");
+  if (out == A1 || out == A2 || out == Bm) return set_error(KS_EINVAL, "output aliases input");
+  KS_TRY(launch_combine<float>(kp->P, A1, k1, C1, A2, k2, C2, alpha, beta, Bm, out, q));
   return finish(kp->P);
 }
 

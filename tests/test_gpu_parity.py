@@ -301,6 +301,7 @@ def test_fp32_gram_tensor_cores(shape):
     N, pa, qb = shape
     s = ki.small_system(N=N, L=7.0, natoms=2, p=max(pa, qb), Z=4.0, seed=4)
     P = make(s)
+    P.set_tensor_cores(2)
     rng = np.random.default_rng(21)
     A = rng.standard_normal((s.n, pa)).astype(np.float32)
     B = rng.standard_normal((s.n, qb)).astype(np.float32)
@@ -309,3 +310,26 @@ def test_fp32_gram_tensor_cores(shape):
     # |A|^T |B| bounds the rounding of every entry
     bound = np.abs(A.astype(np.float64)).T @ np.abs(B.astype(np.float64))
     assert np.all(np.abs(got - want) <= 2e-6 * bound + 1e-12)
+
+
+@pytest.mark.parametrize("shape", [(13, 70, 70), (16, 64, 64), (9, 40, 33), (11, 12, 20)])
+def test_fp32_update_tensor_cores(shape):
+    # FP32 update X C1 + D C2 of the mixed phase (tensor cores for q > 32,
+    # one thread per entry below), against the exact FP64 result of the same
+    # FP32 inputs and the FP64 C matrices.
+    N, k, q = shape
+    s = ki.small_system(N=N, L=7.0, natoms=2, p=max(k, q), Z=4.0, seed=4)
+    P = make(s)
+    P.set_tensor_cores(2)
+    rng = np.random.default_rng(23)
+    A1 = rng.standard_normal((s.n, k)).astype(np.float32)
+    A2 = rng.standard_normal((s.n, k)).astype(np.float32)
+    Bm = rng.standard_normal((s.n, q)).astype(np.float32)
+    C1 = rng.standard_normal((k, q))
+    C2 = rng.standard_normal((k, q))
+    t = lambda a: torch.from_numpy(a).cuda()
+    got = host(P.step_combine_f32(t(A1), t(C1), t(A2), t(C2), alpha=-0.5, beta=2.0, Bm=t(Bm)))
+    A1d, A2d = A1.astype(np.float64), A2.astype(np.float64)
+    want = -0.5 * (A1d @ C1 + A2d @ C2) + 2.0 * Bm.astype(np.float64)
+    bound = 0.5 * (np.abs(A1d) @ np.abs(C1) + np.abs(A2d) @ np.abs(C2)) + 2.0 * np.abs(Bm)
+    assert np.all(np.abs(got - want) <= 4e-6 * bound + 1e-12)
