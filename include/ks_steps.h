@@ -48,6 +48,12 @@ ks_status ks_step_potential(ks_problem *prob, const double *rho, const double *v
 ks_status ks_step_hamiltonian(ks_problem *prob, const double *X, const double *veff,
                               double *EX, double *MX, double *kinetic);
 
+/* FP32 form of ks_step_hamiltonian used by the mixed-precision phase: X, EX,
+ * MX DEVICE n x p FP32 (MX may be NULL), veff DEVICE n FP64 (rounded to FP32
+ * once per node), kinetic HOST FP64 (FP32 terms, FP64 block sums). */
+ks_status ks_step_hamiltonian_f32(ks_problem *prob, const float *X, const double *veff,
+                                  float *EX, float *MX, double *kinetic);
+
 /* MX = M X (consistent Q1 mass).  DEVICE n x p. */
 ks_status ks_step_mass(ks_problem *prob, const double *X, double *MX);
 
@@ -64,18 +70,26 @@ ks_status ks_step_gram(ks_problem *prob, const double *A, int pa, const double *
  * for the update). */
 ks_status ks_set_tensor_cores(ks_problem *prob, int mode);
 
+/* Plane staging of the 27-point stencils: 1 (default) TMA tile loads into a
+ * shared-memory ring when the row pitch p * element size and the block's
+ * base address are multiples of 16 bytes, 0 plain loads always.  Both give
+ * the same sums in the same order. */
+ks_status ks_set_tma(ks_problem *prob, int mode);
+
 /* FP32 Gram of the mixed-precision phase, out = A^T B in FP64 (A: DEVICE
- * n x pa FP32, B: DEVICE n x qb FP32, 1 <= pa, qb <= p).  For pa, qb > 8 it
- * runs on the tensor cores with three TF32 products per term (hi.hi + hi.lo
- * + lo.hi, about 2^-21 relative error per product) and FP32 accumulation
- * within a chunk of rows; chunks are summed in FP64. */
+ * n x pa FP32, B: DEVICE n x qb FP32, 1 <= pa, qb <= p).  When
+ * ks_set_tensor_cores selects them (by default for pa, qb >= 256) it runs on
+ * the tensor cores with three TF32 products per term (hi.hi + hi.lo +
+ * lo.hi, about 2^-21 relative error per product); otherwise on the FP32
+ * pipes.  FP32 accumulation within a chunk of rows; chunks summed in FP64. */
 ks_status ks_step_gram_f32(ks_problem *prob, const float *A, int pa, const float *B, int qb,
                            double *out);
 
 /* FP32 update of the mixed-precision phase, out = alpha (A1 C1 + A2 C2) +
  * beta Bm with FP32 blocks A1 (n x k1), A2 (n x k2 or NULL), Bm (n x q or NULL),
- * out (n x q) and FP64 C1 (k1 x q), C2 (k2 x q), all DEVICE.  For q > 32 it runs
- * on the tensor cores (three TF32 products per term). */
+ * out (n x q) and FP64 C1 (k1 x q), C2 (k2 x q), all DEVICE.  C1, C2 are
+ * rounded to FP32 once per call.  For q > 32 it runs on the tensor cores
+ * when ks_set_tensor_cores selects them (three TF32 products per term). */
 ks_status ks_step_combine_f32(ks_problem *prob, const float *A1, int k1, const double *C1,
                               const float *A2, int k2, const double *C2, double alpha,
                               double beta, const float *Bm, float *out, int q);

@@ -101,11 +101,13 @@ SIGNATURES = [
     ("ks_step_hartree", _I, [_P, _P, _P, _I, _P, ctypes.POINTER(_I)]),
     ("ks_step_potential", _I, [_P, _P, _P, _P, _P, _DP]),
     ("ks_step_hamiltonian", _I, [_P, _P, _P, _P, _P, _DP]),
+    ("ks_step_hamiltonian_f32", _I, [_P, _P, _P, _P, _P, _DP]),
     ("ks_step_mass", _I, [_P, _P, _P]),
     ("ks_step_mass_inverse", _I, [_P, _P, _P]),
     ("ks_step_gram", _I, [_P, _P, _I, _P, _I, _P]),
     ("ks_step_gram_f32", _I, [_P, _P, _I, _P, _I, _P]),
     ("ks_set_tensor_cores", _I, [_P, _I]),
+    ("ks_set_tma", _I, [_P, _I]),
     ("ks_step_combine_f32", _I, [_P, _P, _I, _P, _P, _I, _P, _D, _D, _P, _P, _I]),
     ("ks_step_combine", _I, [_P, _P, _I, _P, _P, _I, _P, _D, _D, _P, _P, _I]),
     ("ks_gram_noalloc", _I, [_P, _I, _P, _I, ctypes.c_longlong, _P, _P]),
@@ -145,6 +147,16 @@ def _check(status: int):
     if status != KS_OK:
         msg = load_library().ks_last_error_string()
         raise KSError(status, msg.decode() if msg else "")
+
+
+def _ptr32(t) -> int | None:
+    """Device pointer of a CUDA FP32 contiguous tensor (None passes NULL)."""
+    if t is None:
+        return None
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise TypeError("expected a contiguous torch.float32 CUDA tensor")
+    return t.data_ptr()
 
 
 def _ptr(t) -> int | None:
@@ -366,6 +378,16 @@ class Problem:
                                                   ctypes.byref(k)))
         return EX, MX, k.value
 
+    def step_hamiltonian_f32(self, X, veff, want_mx: bool = True):
+        """FP32 stencil of the mixed phase: X float32 (n, p), veff float64 (n,)."""
+        import torch
+        EX = torch.empty((self.n, self.p), dtype=torch.float32, device="cuda")
+        MX = torch.empty_like(EX) if want_mx else None
+        k = ctypes.c_double()
+        _check(load_library().ks_step_hamiltonian_f32(self._h, _ptr32(X), _ptr(veff), _ptr32(EX),
+                                                      _ptr32(MX), ctypes.byref(k)))
+        return EX, MX, k.value
+
     def step_mass(self, X):
         out = self.empty_block()
         _check(load_library().ks_step_mass(self._h, _ptr(X), _ptr(out)))
@@ -386,6 +408,10 @@ class Problem:
     def set_tensor_cores(self, mode: int):
         """FP32-phase tensor cores: 0 never, 1 wide products (default), 2 always."""
         _check(load_library().ks_set_tensor_cores(self._h, mode))
+
+    def set_tma(self, mode: int):
+        """Stencil plane staging: 1 TMA ring (default, when aligned), 0 plain loads."""
+        _check(load_library().ks_set_tma(self._h, mode))
 
     def step_gram_f32(self, A, B):
         """FP32 Gram of the mixed phase (A, B float32 CUDA tensors)."""

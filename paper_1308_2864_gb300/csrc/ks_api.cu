@@ -54,6 +54,7 @@ size_t problem_bytes(int N, int p, int sms) {
   b += ((size_t)N * N + 2 * N) * sizeof(float);                      // sine basis
   b += (size_t)Problem::kNBlocks * n * p * sizeof(double);            // n x p blocks
   b += (size_t)S_COUNT * p * p * sizeof(double);                      // small matrices
+  b += (size_t)2 * p * p * sizeof(float);                             // FP32 coefficients
   size_t part = gram_partials_len(p, sms);
   const size_t red = (size_t)4 * 8 * sms;
   const size_t cg = (size_t)4 * 2 * sms;
@@ -89,7 +90,7 @@ static void free_problem(Problem &P) {
   f(P.vext); f(P.rho); f(P.vH); f(P.veff); f(P.cg_r); f(P.cg_pa); f(P.cg_pb); f(P.cg_q);
   f(P.cg_z); f(P.cg_t1); f(P.cg_t2); f(P.dst_phi); f(P.dst_kap); f(P.dst_mu);
   for (auto &b : P.blk) f(b);
-  f(P.pp); f(P.partials); f(P.scal); f(P.atoms_dev); f(P.thomas_w); f(P.bar); f(P.red_counter); f(P.dstatus);
+  f(P.pp); f(P.cf); f(P.partials); f(P.scal); f(P.atoms_dev); f(P.thomas_w); f(P.bar); f(P.red_counter); f(P.dstatus);
   delete[] P.scal_host;
   delete[] P.dstatus_host;
   P.scal_host = nullptr;
@@ -589,6 +590,7 @@ ks_status ks_problem_create(const ks_problem_desc *d, ks_problem **out) {
   for (auto &b : P.blk) { ALLOC(b, np); }
   P.pp_len = (size_t)S_COUNT * P.p * P.p;
   ALLOC(P.pp, P.pp_len);
+  ALLOC(P.cf, (size_t)2 * P.p * P.p);
   P.cg_blocks = cg_grid_blocks(P.sms, P.n, P.N);
   if (P.cg_blocks < 1) return fail(set_error(KS_ECUDA, "CG kernel configuration failed"));
   size_t part = gram_partials_len(P.p, P.sms);

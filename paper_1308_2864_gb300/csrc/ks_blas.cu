@@ -215,11 +215,14 @@ ks_status launch_gram(Problem &P, const T *A, int pa, const T *B, int qb, double
   return KS_OK;
 }
 
-template <typename T>
+// TC is the type of the coefficients C1, C2: double, or float copies made
+// once per update for the FP32 phase (converting in every block would put
+// a conversion per staged element on the FP64 pipe).
+template <typename T, typename TC>
 __global__ void __launch_bounds__(256) combine_kernel(long long n, int q, const T *__restrict__ A1,
-                                                      int k1, const double *__restrict__ C1,
+                                                      int k1, const TC *__restrict__ C1,
                                                       const T *__restrict__ A2, int k2,
-                                                      const double *__restrict__ C2, double alpha_d,
+                                                      const TC *__restrict__ C2, double alpha_d,
                                                       double beta_d,
                                                       const T *__restrict__ Bm,
                                                       T *__restrict__ out) {
@@ -236,7 +239,7 @@ __global__ void __launch_bounds__(256) combine_kernel(long long n, int q, const 
     for (int j = 0; j < 4; ++j) acc[i][j] = 0;
   for (int op = 0; op < 2; ++op) {
     const T *A = op == 0 ? A1 : A2;
-    const double *C = op == 0 ? C1 : C2;
+    const TC *C = op == 0 ? C1 : C2;
     const int kk = op == 0 ? k1 : k2;
     if (A == nullptr) continue;
     for (int k0 = 0; k0 < kk; k0 += kTileK) {
@@ -314,6 +317,15 @@ __global__ void __launch_bounds__(256) combine_narrow_kernel(
   }
 }
 
+// FP32 copies of the update coefficients (one launch for both matrices).
+__global__ void coef_convert_kernel(long long len1, const double *__restrict__ C1,
+                                    float *__restrict__ c1, long long len2,
+                                    const double *__restrict__ C2, float *__restrict__ c2) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < len1) c1[e] = (float)C1[e];
+  else if (e < len1 + len2) c2[e - len1] = (float)C2[e - len1];
+}
+
 template <typename T>
 ks_status launch_combine(Problem &P, const T *A1, int k1, const double *C1, const T *A2, int k2,
                          const double *C2, double alpha, double beta, const T *Bm, T *out, int q) {
@@ -334,11 +346,24 @@ ks_status launch_combine(Problem &P, const T *A1, int k1, const double *C1, cons
     return KS_OK;
   }
   dim3 grid((unsigned)((P.n + kTile - 1) / kTile), (unsigned)((q + kTile - 1) / kTile));
-  {
+  if (sizeof(T) == 4) {
+    float *c1 = P.cf, *c2 = P.cf + (size_t)P.p * P.p;
+    const long long len1 = (long long)k1 * q, len2 = A2 ? (long long)k2 * q : 0;
+    {
+      ProfScope ps_(P.stream, KP_REDUCE);
+      coef_convert_kernel<<<(int)((len1 + len2 + 255) / 256), 256, 0, P.stream>>>(
+          len1, C1, c1, len2, C2, c2);
+    }
+    KS_CUDA_TRY(cudaGetLastError());
     ProfScope ps_(P.stream, KP_COMBINE, 2.0 * P.n * q * (k1 + (A2 ? k2 : 0)),
                   (double)P.n * ((k1 + (A2 ? k2 : 0)) + q * (Bm ? 2 : 1)) * sizeof(T));
-    combine_kernel<T><<<grid, 256, 0, P.stream>>>(P.n, q, A1, k1, C1, A2, k2, C2, alpha, beta, Bm,
-                                                out);
+    combine_kernel<T, float><<<grid, 256, 0, P.stream>>>(P.n, q, A1, k1, c1, A2, k2,
+                                                         A2 ? c2 : nullptr, alpha, beta, Bm, out);
+  } else {
+    ProfScope ps_(P.stream, KP_COMBINE, 2.0 * P.n * q * (k1 + (A2 ? k2 : 0)),
+                  (double)P.n * ((k1 + (A2 ? k2 : 0)) + q * (Bm ? 2 : 1)) * sizeof(T));
+    combine_kernel<T, double><<<grid, 256, 0, P.stream>>>(P.n, q, A1, k1, C1, A2, k2, C2, alpha,
+                                                          beta, Bm, out);
   }
   KS_CUDA_TRY(cudaGetLastError());
   return KS_OK;

@@ -88,6 +88,7 @@ struct Problem {
   float *dst_phi = nullptr, *dst_kap = nullptr, *dst_mu = nullptr;
   int cg_precond = 1;
   int use_tc = 1;                  // FP32-phase tensor cores: 0 never, 1 for wide products, 2 always
+  int use_tma = 1;                 // TMA plane staging in the stencils (when the layout allows)
   bool vH_valid = false;           // warm start available
 
   // n x p blocks
@@ -96,6 +97,7 @@ struct Problem {
 
   // p x p work (all FP64)
   double *pp = nullptr;            // pool of small matrices
+  float *cf = nullptr;             // 2 p^2: FP32 copies of the update coefficients
   size_t pp_len = 0;
 
   // reductions

@@ -10,10 +10,22 @@
 namespace ks {
 
 // Solve tridiag(1, 4, 1) y = scale * d along one axis, in place on `out`
-// (reading `in` on the forward pass).  w holds the pivots 1/(4 - w_{j-1}).
+// (reading `in` on the forward pass).  w holds the pivots 1/(4 - w_{j-1});
+// they are copied to shared memory in the working precision once per block
+// (a conversion per step would run on the FP64 pipe).  Each sweep reads
+// kAhead entries of the line before it writes any of them, so a thread has
+// kAhead loads in flight instead of one (in and out may be the same array,
+// and the compiler cannot reorder loads across the stores by itself).
+constexpr int kAhead = 8;
+
 template <typename T>
-__global__ void thomas_kernel(int N, int p, int axis, double scale_d,
-                              const double *__restrict__ w, const T *in, T *out) {
+__global__ void __launch_bounds__(256) thomas_kernel(int N, int p, int axis, double scale_d,
+                                                     const double *__restrict__ w_d, const T *in,
+                                                     T *out) {
+  extern __shared__ unsigned char thomas_smem[];
+  T *w = reinterpret_cast<T *>(thomas_smem);
+  for (int j = threadIdx.x; j < N; j += blockDim.x) w[j] = (T)w_d[j];
+  __syncthreads();
   const T scale = (T)scale_d;
   const long long lines = (long long)N * N;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -32,22 +44,36 @@ __global__ void thomas_kernel(int N, int p, int axis, double scale_d,
     base = (long long)b * N + a;
     stride = (long long)N * N;
   }
-  const long long e0 = base * p + i;
+  const T *src = in + base * p + i;
+  T *dst = out + base * p + i;
   const long long es = stride * p;
   // forward elimination
   T prev = 0;
-  for (int j = 0; j < N; ++j) {
-    const long long e = e0 + j * es;
-    const T d = (scale * in[e] - prev) * (T)w[j];
-    out[e] = d;
-    prev = d;
+  for (int j0 = 0; j0 < N; j0 += kAhead) {
+    T v[kAhead];
+#pragma unroll
+    for (int u = 0; u < kAhead; ++u)
+      if (j0 + u < N) v[u] = src[(long long)(j0 + u) * es];
+#pragma unroll
+    for (int u = 0; u < kAhead; ++u)
+      if (j0 + u < N) {
+        prev = (scale * v[u] - prev) * w[j0 + u];
+        dst[(long long)(j0 + u) * es] = prev;
+      }
   }
-  // back substitution
-  T next = out[e0 + (long long)(N - 1) * es];
-  for (int j = N - 2; j >= 0; --j) {
-    const long long e = e0 + j * es;
-    next = out[e] - (T)w[j] * next;
-    out[e] = next;
+  // back substitution (prev holds entry N-1, which is final)
+  T next = prev;
+  for (int j1 = N - 2; j1 >= 0; j1 -= kAhead) {
+    T v[kAhead];
+#pragma unroll
+    for (int u = 0; u < kAhead; ++u)
+      if (j1 - u >= 0) v[u] = dst[(long long)(j1 - u) * es];
+#pragma unroll
+    for (int u = 0; u < kAhead; ++u)
+      if (j1 - u >= 0) {
+        next = v[u] - w[j1 - u] * next;
+        dst[(long long)(j1 - u) * es] = next;
+      }
   }
 }
 
@@ -56,19 +82,20 @@ ks_status launch_mass_inverse(Problem &P, const T *E, T *G) {
   const long long work = (long long)P.N * P.N * P.p;
   const int nb = (int)((work + kThreads - 1) / kThreads);
   const double s = 6.0 / P.h;
+  const size_t smem = (size_t)P.N * sizeof(T);
   {
     ProfScope ps_(P.stream, KP_MASS_INV, 4.0 * P.n * P.p, 2.0 * P.n * P.p * sizeof(T));
-    thomas_kernel<T><<<nb, kThreads, 0, P.stream>>>(P.N, P.p, 0, s * s * s, P.thomas_w, E, G);
+    thomas_kernel<T><<<nb, kThreads, smem, P.stream>>>(P.N, P.p, 0, s * s * s, P.thomas_w, E, G);
   }
   KS_CUDA_TRY(cudaGetLastError());
   {
     ProfScope ps_(P.stream, KP_MASS_INV, 4.0 * P.n * P.p, 2.0 * P.n * P.p * sizeof(T));
-    thomas_kernel<T><<<nb, kThreads, 0, P.stream>>>(P.N, P.p, 1, 1.0, P.thomas_w, G, G);
+    thomas_kernel<T><<<nb, kThreads, smem, P.stream>>>(P.N, P.p, 1, 1.0, P.thomas_w, G, G);
   }
   KS_CUDA_TRY(cudaGetLastError());
   {
     ProfScope ps_(P.stream, KP_MASS_INV, 4.0 * P.n * P.p, 2.0 * P.n * P.p * sizeof(T));
-    thomas_kernel<T><<<nb, kThreads, 0, P.stream>>>(P.N, P.p, 2, 1.0, P.thomas_w, G, G);
+    thomas_kernel<T><<<nb, kThreads, smem, P.stream>>>(P.N, P.p, 2, 1.0, P.thomas_w, G, G);
   }
   KS_CUDA_TRY(cudaGetLastError());
   return KS_OK;

@@ -21,6 +21,17 @@
 // the last three planes in registers, so each plane sum is formed once and
 // used by three output planes.  Consecutive threads take consecutive
 // orbitals of one node, so every global access is a contiguous row segment.
+//
+// Two ways of staging a plane:
+//   TMA (default when the row pitch p * sizeof(T) and the base address are
+//     multiples of 16 bytes): the (TX+2) x (TY+2) x PC halo box of a plane is
+//     one cp.async.bulk.tensor load into a ring of kStStages shared-memory
+//     stages, issued kStStages planes ahead by one thread and completed on
+//     an mbarrier; the zero Dirichlet halo comes from the copy's
+//     out-of-bounds fill.  V_eff of the output plane is staged in the
+//     working precision once per node.
+//   plain loads (any p): all threads copy the halo box element by element.
+#include "ks_async.cuh"
 #include "ks_device.cuh"
 
 namespace ks {
@@ -53,6 +64,16 @@ struct StArgs {
   double *red_out;            // reduced channels (scaled by red_scale)
   double red_scale;
   unsigned int *counter;
+  int *status;                // device status word (TMA waits that give up)
+};
+
+// Coefficients in the working precision, converted once per thread.
+template <typename T>
+struct StCoefT {
+  T k0, ke, kc, m0, mf, me, mc, occ, vscale;
+  __device__ explicit StCoefT(const StArgs &a)
+      : k0((T)a.c.k0), ke((T)a.c.ke), kc((T)a.c.kc), m0((T)a.c.m0), mf((T)a.c.mf),
+        me((T)a.c.me), mc((T)a.c.mc), occ((T)a.occ), vscale((T)(2.0 * a.occ * a.h3)) {}
 };
 
 template <typename T, int PC, int Kind>
@@ -171,6 +192,196 @@ __global__ void __launch_bounds__(kStThreads) stencil_kernel(StArgs a) {
                    smem);
 }
 
+constexpr int kStStages = 3;
+
+template <typename T, int PC>
+struct StRing {
+  using Tl = StTile<PC>;
+  static constexpr int BOX = Tl::HY * Tl::HX * PC;                 // elements of one halo box
+  static constexpr uint32_t BOX_BYTES = BOX * sizeof(T);
+  static constexpr int STAGE = ((BOX_BYTES + 127) / 128) * 128 / sizeof(T);   // 128-byte stages
+  // the stages plus slack to align the ring to 128 bytes at run time
+  static constexpr size_t SMEM = (size_t)kStStages * STAGE * sizeof(T) + 128;
+};
+
+struct StTmaArgs {
+  CUtensorMap map;            // (orbital, x, y, z) view of the input block
+  StArgs a;
+};
+
+template <typename T, int PC, int Kind>
+__global__ void __launch_bounds__(kStThreads, 2) stencil_tma_kernel(const __grid_constant__ StTmaArgs ta) {
+  using Tl = StTile<PC>;
+  using Rg = StRing<T, PC>;
+  constexpr int TXY = Tl::TX * Tl::TY;
+  static_assert(TXY <= kStThreads, "one V_eff loader per node");
+  extern __shared__ __align__(128) unsigned char st_ring_raw[];
+  T *ring = reinterpret_cast<T *>(st_ring_raw + ((128u - (smem_addr(st_ring_raw) & 127u)) & 127u));
+  __shared__ __align__(8) uint64_t full[kStStages];
+  __shared__ T vs[3][TXY];
+  __shared__ double smem[33];
+  const StArgs &a = ta.a;
+  const int N = a.N, p = a.p;
+  int b = blockIdx.x;
+  const int txi = b % a.tiles_x; b /= a.tiles_x;
+  const int tyi = b % a.tiles_y; b /= a.tiles_y;
+  const int oc = b % a.chunks; b /= a.chunks;
+  const int zs = b;
+  const int x0 = txi * Tl::TX, y0 = tyi * Tl::TY;
+  const int z0 = zs * a.zseg;
+  const int z1 = min(z0 + a.zseg, N);
+  const int nplanes = z1 - z0 + 2;          // planes z0 - 1 .. z1
+  const int lane = threadIdx.x % PC, grp = threadIdx.x / PC;
+  const int o = oc * PC + lane;
+  const bool ovalid = o < p;
+
+  if (threadIdx.x == 0) {
+    prefetch_tensor_map(&ta.map);
+#pragma unroll
+    for (int st = 0; st < kStStages; ++st) mbar_init(&full[st], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < kStStages && q < nplanes; ++q) {
+      mbar_arrive_expect_tx(&full[q], Rg::BOX_BYTES);
+      tma_load_4d(ring + q * Rg::STAGE, &ta.map, &full[q], oc * PC, x0 - 1, y0 - 1, z0 - 1 + q);
+    }
+  }
+
+  int lx[kStNodesPerThread], ly[kStNodesPerThread];
+#pragma unroll
+  for (int r = 0; r < kStNodesPerThread; ++r) {
+    const int node = grp + r * Tl::G;
+    lx[r] = node % Tl::TX;
+    ly[r] = node / Tl::TX;
+  }
+  // V_eff of plane z0 - 1 + q is read one iteration ahead by the thread that
+  // owns the node, converted once and kept in vs[q % 3]
+  const int vx = x0 + (int)threadIdx.x % Tl::TX, vy = y0 + (int)threadIdx.x / Tl::TX;
+  const bool vown = Kind == SK_HAM && (int)threadIdx.x < TXY && vx < N && vy < N;
+  double vreg = 0.0;
+  if (vown && z0 >= 1) vreg = a.veff[((long long)(z0 - 1) * N + vy) * N + vx];
+
+  const StCoefT<T> cf(a);
+  T acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
+  T c_old[kStNodesPerThread], f_old[kStNodesPerThread], e_old[kStNodesPerThread];
+  T c_mid[kStNodesPerThread], f_mid[kStNodesPerThread], e_mid[kStNodesPerThread];
+  int failed_at = -1;
+  for (int q = 0; q < nplanes; ++q) {
+    const int zp = z0 - 1 + q;
+    const int st = q % kStStages;
+    if (Kind == SK_HAM && (int)threadIdx.x < TXY) {
+      vs[q % 3][threadIdx.x] = (T)vreg;
+      vreg = 0.0;
+      if (vown && zp + 1 < N) vreg = a.veff[((long long)(zp + 1) * N + vy) * N + vx];
+    }
+    const bool got = mbar_wait_parity(&full[st], (uint32_t)((q / kStStages) & 1));
+    const T *tile = ring + st * Rg::STAGE;
+    T c_new[kStNodesPerThread], f_new[kStNodesPerThread], e_new[kStNodesPerThread];
+#pragma unroll
+    for (int r = 0; r < kStNodesPerThread; ++r) {
+      const int hx = lx[r] + 1, hy = ly[r] + 1;
+      auto at = [&](int dx, int dy) { return tile[((hy + dy) * Tl::HX + hx + dx) * PC + lane]; };
+      c_new[r] = at(0, 0);
+      f_new[r] = (at(-1, 0) + at(1, 0)) + (at(0, -1) + at(0, 1));
+      e_new[r] = (at(-1, -1) + at(1, -1)) + (at(-1, 1) + at(1, 1));
+    }
+    // every thread is done with this stage: refill it kStStages planes ahead
+    if (__syncthreads_or(!got)) {
+      failed_at = q;
+      break;
+    }
+    if (threadIdx.x == 0 && q + kStStages < nplanes) {
+      mbar_arrive_expect_tx(&full[st], Rg::BOX_BYTES);
+      tma_load_4d(ring + st * Rg::STAGE, &ta.map, &full[st], oc * PC, x0 - 1, y0 - 1,
+                  zp + kStStages);
+    }
+    if (q >= 2) {
+      const int z = zp - 1;
+      const T *vz = vs[(q + 2) % 3];
+      T bb[6][kStNodesPerThread];
+      if (Kind == SK_MASS_BB) {
+        // all loads of the plane first, so they are in flight together
+#pragma unroll
+        for (int r = 0; r < kStNodesPerThread; ++r) {
+          const int gx = x0 + lx[r], gy = y0 + ly[r];
+          if (ovalid && gx < N && gy < N) {
+            const long long idx = (((long long)z * N + gy) * N + gx) * p + o;
+            bb[0][r] = ((const T *)a.X)[idx];
+            bb[1][r] = ((const T *)a.MX)[idx];
+            bb[2][r] = ((const T *)a.Xp)[idx];
+            bb[3][r] = ((const T *)a.MXp)[idx];
+            bb[4][r] = ((const T *)a.Dp)[idx];
+            bb[5][r] = ((const T *)a.MDp)[idx];
+          }
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < kStNodesPerThread; ++r) {
+        const int gx = x0 + lx[r], gy = y0 + ly[r];
+        const T centre = c_mid[r];
+        const T faces = f_mid[r] + (c_old[r] + c_new[r]);
+        const T edges = e_mid[r] + (f_old[r] + f_new[r]);
+        const T corners = e_old[r] + e_new[r];
+        if (ovalid && gx < N && gy < N) {
+          const long long k = ((long long)z * N + gy) * N + gx;
+          const long long idx = k * p + o;
+          const T m = cf.m0 * centre + cf.mf * faces + cf.me * edges + cf.mc * corners;
+          if (Kind == SK_HAM) {
+            const T kx = cf.k0 * centre + cf.ke * edges + cf.kc * corners;
+            ((T *)a.out1)[idx] = cf.occ * kx + cf.vscale * vz[ly[r] * Tl::TX + lx[r]] * centre;
+            if (a.out2) ((T *)a.out2)[idx] = m;
+            acc0 = fma(centre, kx, acc0);
+          } else {
+            ((T *)a.out1)[idx] = m;
+            if (Kind >= SK_MASS_DOT) acc0 = fma(centre, m, acc0);
+            if (Kind == SK_MASS_BB) {
+              const T dx = bb[0][r] - bb[2][r];
+              const T dmx = bb[1][r] - bb[3][r];
+              const T dd = centre - bb[4][r];
+              const T dmd = m - bb[5][r];
+              acc1 = fma(dx, dmx, acc1);
+              acc2 = fma(dx, dmd, acc2);
+              acc3 = fma(dd, dmd, acc3);
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < kStNodesPerThread; ++r) {
+      c_old[r] = c_mid[r]; f_old[r] = f_mid[r]; e_old[r] = e_mid[r];
+      c_mid[r] = c_new[r]; f_mid[r] = f_new[r]; e_mid[r] = e_new[r];
+    }
+  }
+  if (failed_at >= 0) {
+    // record the timeout, give the copies still in flight a bounded wait,
+    // and still take part in the reduction so that its counter re-arms
+    if (threadIdx.x == 0) {
+      atomicCAS(a.status, 0, (int)KS_ETIMEOUT);
+      for (int q = failed_at; q < failed_at + kStStages && q < nplanes; ++q)
+        mbar_wait_parity(&full[q % kStStages], (uint32_t)((q / kStStages) & 1));
+    }
+    acc0 = acc1 = acc2 = acc3 = 0;
+  }
+  if (Kind == SK_MASS) return;
+  const double s0 = block_sum((double)acc0, smem);
+  if (threadIdx.x == 0) a.part[blockIdx.x] = s0;
+  if (Kind == SK_MASS_BB) {
+    const double s1 = block_sum((double)acc1, smem);
+    const double s2 = block_sum((double)acc2, smem);
+    const double s3 = block_sum((double)acc3, smem);
+    if (threadIdx.x == 0) {
+      a.part[a.nb + blockIdx.x] = s1;
+      a.part[2 * a.nb + blockIdx.x] = s2;
+      a.part[3 * a.nb + blockIdx.x] = s3;
+    }
+  }
+  grid_reduce_tail(a.part, a.nb, Kind == SK_MASS_BB ? 4 : 1, a.red_out, a.red_scale, a.counter,
+                   smem);
+}
+
 // Geometry of a launch: tiles, orbital chunks and z segments; the number of
 // segments is lowered until the block partials (nchan per block) fit.
 template <int PC>
@@ -201,25 +412,59 @@ static ks_status stencil_geometry(const Problem &P, int nchan, StArgs &a) {
   }
 }
 
-template <typename T, int Kind>
-static ks_status stencil_launch(Problem &P, StArgs &a, int nchan, double flops, double bytes) {
-  KS_TRY((P.p >= 32 ? stencil_geometry<32>(P, nchan, a)
-          : P.p >= 16 ? stencil_geometry<16>(P, nchan, a)
-          : P.p >= 8 ? stencil_geometry<8>(P, nchan, a)
-                     : stencil_geometry<4>(P, nchan, a)));
+// TMA form of one launch; false (and nothing launched) when the input
+// cannot be described by a tensor map (row pitch or base address not a
+// multiple of 16 bytes).
+template <typename T, int PC, int Kind>
+static bool stencil_launch_tma(Problem &P, const StArgs &a, int cls, double flops, double bytes,
+                               ks_status *st) {
+  using Tl = StTile<PC>;
+  using Rg = StRing<T, PC>;
+  *st = KS_OK;
+  if (!P.use_tma || ((size_t)P.p * sizeof(T)) % 16 != 0 ||
+      reinterpret_cast<uintptr_t>(a.A) % 16 != 0)
+    return false;
+  StTmaArgs ta;
+  ta.a = a;
+  const uint64_t dims[4] = {(uint64_t)P.p, (uint64_t)P.N, (uint64_t)P.N, (uint64_t)P.N};
+  const uint32_t box[4] = {(uint32_t)PC, (uint32_t)Tl::HX, (uint32_t)Tl::HY, 1u};
+  if (encode_tensor_map_4d(&ta.map, a.A, (int)sizeof(T), dims, box) != KS_OK) return false;
+  // ring + static shared memory (mbarriers, V_eff planes, reduction scratch:
+  // under 2 KiB) stay within the 48 KiB a block gets without an opt-in
+  static_assert(Rg::SMEM + 2048 <= 48 * 1024, "ring fits the default shared memory");
+  {
+    ProfScope ps_(P.stream, cls, flops, bytes);
+    stencil_tma_kernel<T, PC, Kind><<<a.nb, kStThreads, Rg::SMEM, P.stream>>>(ta);
+  }
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) *st = cuda_error(e, "stencil_tma_kernel");
+  return true;
+}
+
+template <typename T, int PC, int Kind>
+static ks_status stencil_launch_pc(Problem &P, StArgs &a, int nchan, double flops, double bytes) {
+  KS_TRY(stencil_geometry<PC>(P, nchan, a));
   a.c = q1_coefficients(P.h);
   a.part = P.partials;
   a.counter = P.red_counter;
+  a.status = P.dstatus;
   const int cls = Kind == SK_HAM ? KP_HAMILTONIAN : KP_MASS;
+  ks_status st;
+  if (stencil_launch_tma<T, PC, Kind>(P, a, cls, flops, bytes, &st)) return st;
   {
     ProfScope ps_(P.stream, cls, flops, bytes);
-    if (P.p >= 32) stencil_kernel<T, 32, Kind><<<a.nb, kStThreads, 0, P.stream>>>(a);
-    else if (P.p >= 16) stencil_kernel<T, 16, Kind><<<a.nb, kStThreads, 0, P.stream>>>(a);
-    else if (P.p >= 8) stencil_kernel<T, 8, Kind><<<a.nb, kStThreads, 0, P.stream>>>(a);
-    else stencil_kernel<T, 4, Kind><<<a.nb, kStThreads, 0, P.stream>>>(a);
+    stencil_kernel<T, PC, Kind><<<a.nb, kStThreads, 0, P.stream>>>(a);
   }
   KS_CUDA_TRY(cudaGetLastError());
   return KS_OK;
+}
+
+template <typename T, int Kind>
+static ks_status stencil_launch(Problem &P, StArgs &a, int nchan, double flops, double bytes) {
+  if (P.p >= 32) return stencil_launch_pc<T, 32, Kind>(P, a, nchan, flops, bytes);
+  if (P.p >= 16) return stencil_launch_pc<T, 16, Kind>(P, a, nchan, flops, bytes);
+  if (P.p >= 8) return stencil_launch_pc<T, 8, Kind>(P, a, nchan, flops, bytes);
+  return stencil_launch_pc<T, 4, Kind>(P, a, nchan, flops, bytes);
 }
 
 template <typename T>

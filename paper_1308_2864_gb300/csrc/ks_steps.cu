@@ -92,6 +92,17 @@ ks_status ks_step_hamiltonian(ks_problem *kp, const double *X, const double *vef
   return KS_OK;
 }
 
+ks_status ks_step_hamiltonian_f32(ks_problem *kp, const float *X, const double *veff, float *EX,
+                                  float *MX, double *kinetic) {
+  if (!kp || !X || !veff || !EX) return set_error(KS_EINVAL, "null argument");
+  Problem &P = kp->P;
+  KS_TRY(launch_hamiltonian<float>(P, X, veff, EX, MX, P.scal + SC_EKIN));
+  double k = 0;
+  KS_TRY(read_scalars(P, SC_EKIN, 1, &k));
+  if (kinetic) *kinetic = k;
+  return KS_OK;
+}
+
 ks_status ks_step_mass(ks_problem *kp, const double *X, double *MX) {
   if (!kp || !X || !MX) return set_error(KS_EINVAL, "null argument");
   KS_TRY(launch_mass(kp->P, X, MX));
@@ -116,6 +127,12 @@ ks_status ks_step_gram(ks_problem *kp, const double *A, int pa, const double *B,
 ks_status ks_set_tensor_cores(ks_problem *kp, int mode) {
   if (!kp || mode < 0 || mode > 2) return set_error(KS_EINVAL, "bad argument");
   kp->P.use_tc = mode;
+  return KS_OK;
+}
+
+ks_status ks_set_tma(ks_problem *kp, int mode) {
+  if (!kp || mode < 0 || mode > 1) return set_error(KS_EINVAL, "bad argument");
+  kp->P.use_tma = mode;
   return KS_OK;
 }
 

@@ -294,14 +294,15 @@ def test_checkpoint_resume_is_bitwise(precision):
 
 
 @pytest.mark.parametrize("shape", [(13, 70, 70), (16, 64, 64), (11, 130, 70), (9, 12, 9)])
-def test_fp32_gram_tensor_cores(shape):
+@pytest.mark.parametrize("tc", [0, 2], ids=["fp32-pipes", "tensor-cores"])
+def test_fp32_gram_tensor_cores(shape, tc):
     # FP32 Gram of the mixed phase: tensor cores (3 x TF32) for pa, qb > 8,
     # the register kernel below; compared with the exact FP64 product of
     # the same FP32 inputs.  n = N^3 rows is ragged against the 32-row stage.
     N, pa, qb = shape
     s = ki.small_system(N=N, L=7.0, natoms=2, p=max(pa, qb), Z=4.0, seed=4)
     P = make(s)
-    P.set_tensor_cores(2)
+    P.set_tensor_cores(tc)
     rng = np.random.default_rng(21)
     A = rng.standard_normal((s.n, pa)).astype(np.float32)
     B = rng.standard_normal((s.n, qb)).astype(np.float32)
@@ -313,14 +314,15 @@ def test_fp32_gram_tensor_cores(shape):
 
 
 @pytest.mark.parametrize("shape", [(13, 70, 70), (16, 64, 64), (9, 40, 33), (11, 12, 20)])
-def test_fp32_update_tensor_cores(shape):
+@pytest.mark.parametrize("tc", [0, 2], ids=["fp32-pipes", "tensor-cores"])
+def test_fp32_update_tensor_cores(shape, tc):
     # FP32 update X C1 + D C2 of the mixed phase (tensor cores for q > 32,
     # one thread per entry below), against the exact FP64 result of the same
     # FP32 inputs and the FP64 C matrices.
     N, k, q = shape
     s = ki.small_system(N=N, L=7.0, natoms=2, p=max(k, q), Z=4.0, seed=4)
     P = make(s)
-    P.set_tensor_cores(2)
+    P.set_tensor_cores(tc)
     rng = np.random.default_rng(23)
     A1 = rng.standard_normal((s.n, k)).astype(np.float32)
     A2 = rng.standard_normal((s.n, k)).astype(np.float32)
@@ -333,3 +335,77 @@ def test_fp32_update_tensor_cores(shape):
     want = -0.5 * (A1d @ C1 + A2d @ C2) + 2.0 * Bm.astype(np.float64)
     bound = 0.5 * (np.abs(A1d) @ np.abs(C1) + np.abs(A2d) @ np.abs(C2)) + 2.0 * np.abs(Bm)
     assert np.all(np.abs(got - want) <= 4e-6 * bound + 1e-12)
+
+
+# (N, p): p = 64 and 20 take the TMA ring in both precisions (row pitch a
+# multiple of 16 bytes), p = 6 only in FP64, p = 5 in neither; N = 13 and 9
+# leave ragged tiles in x, y and along z.
+STAGING = [(13, 64), (9, 20), (13, 6), (9, 5)]
+
+
+@pytest.mark.parametrize("shape", STAGING, ids=[f"N{n}p{p}" for n, p in STAGING])
+def test_stencil_staging_paths_agree(shape):
+    # TMA-staged and plain-load stencils form the same sums in the same
+    # order: bitwise equal outputs in FP64 and FP32.
+    N, p = shape
+    s = ki.small_system(N=N, L=7.0, natoms=2, p=p, Z=4.0, seed=5)
+    P = make(s)
+    rng = np.random.default_rng(31)
+    X = rng.standard_normal((s.n, p))
+    veff = dev(rng.standard_normal(s.n))
+    X64, X32 = dev(X), torch.from_numpy(X.astype(np.float32)).cuda()
+    out = {}
+    for mode in (0, 1):
+        P.set_tma(mode)
+        out[mode] = (P.step_hamiltonian(X64, veff), P.step_mass(X64),
+                     P.step_hamiltonian_f32(X32, veff))
+    (e0, m0, k0), mm0, (f0, fm0, fk0) = out[0]
+    (e1, m1, k1), mm1, (f1, fm1, fk1) = out[1]
+    assert torch.equal(e0, e1) and torch.equal(m0, m1) and torch.equal(mm0, mm1)
+    assert torch.equal(f0, f1) and torch.equal(fm0, fm1)
+    assert k0 == k1 and fk0 == fk1
+
+
+@pytest.mark.parametrize("shape", [(13, 64), (9, 20), (11, 5)])
+def test_fp32_hamiltonian_stencil(shape):
+    # FP32 stencil of the mixed phase against the FP64 oracle on the same
+    # FP32-rounded inputs: each entry sums 27 terms of FP32 products, so the
+    # error is bounded by a few ulps of the sum of absolute terms.
+    N, p = shape
+    s = ki.small_system(N=N, L=7.0, natoms=2, p=p, Z=4.0, seed=6)
+    model = oe.Model.from_system(s)
+    P = make(s)
+    rng = np.random.default_rng(32)
+    X = rng.standard_normal((s.n, p)).astype(np.float32).astype(np.float64)
+    veff = rng.standard_normal(s.n).astype(np.float32).astype(np.float64)
+    EX, MX, kin = P.step_hamiltonian_f32(torch.from_numpy(X.astype(np.float32)).cuda(), dev(veff))
+    KX = ofe.apply_K(X, model.N, model.h)
+    want = model.occ * KX + 2 * model.occ * model.h ** 3 * veff[:, None] * X
+    # sum of |terms|: |K| |X| is K with its off-centre entries negated, i.e.
+    # 2 K0 |X| - K |X| with K0 the centre coefficient
+    k0 = 2 * ofe.apply_K(np.eye(1, s.n, s.n // 2).T, model.N, model.h)[s.n // 2, 0]
+    absKX = k0 * np.abs(X) - ofe.apply_K(np.abs(X), model.N, model.h)
+    scale = (model.occ * absKX +
+             2 * model.occ * model.h ** 3 * np.abs(veff)[:, None] * np.abs(X))
+    err = np.abs(host(EX).astype(np.float64) - want)
+    assert np.all(err <= 64 * 2.0 ** -24 * scale + 1e-30)
+    mwant = ofe.apply_M(X, model.N, model.h)
+    mscale = ofe.apply_M(np.abs(X), model.N, model.h)    # M is entrywise positive
+    assert np.all(np.abs(host(MX).astype(np.float64) - mwant) <= 64 * 2.0 ** -24 * mscale)
+    assert kin == pytest.approx(0.5 * model.occ * np.sum(X * KX), rel=1e-5)
+
+
+def test_mixed_minimize_same_with_and_without_tma():
+    # the whole mixed run (FP32 phase with every stencil kind, then the FP64
+    # polish) is bitwise the same with either staging
+    s = ki.small_system(N=12, L=7.0, natoms=2, p=8, Z=4.0, seed=12)
+    kw = dict(retraction="qr", gtol=1e-7, maxit=60, precision="mixed", polish_gtol=1e-3)
+    res, Xs = [], []
+    for mode in (0, 1):
+        P = make(s)
+        P.set_tma(mode)
+        X = dev(s.x0())
+        res.append(P.minimize(X, **kw))
+        Xs.append(X)
+    assert res[0]["E"] == res[1]["E"] and res[0]["iters"] == res[1]["iters"]
+    assert torch.equal(Xs[0], Xs[1])
