@@ -96,7 +96,8 @@ typedef struct {
   int precision;      /* KS_FP64, or KS_MIXED: FP32 orbital blocks until ||D||_M <= polish_gtol
                          (or no progress for stall_iters iterations), then an FP64 polish
                          to gtol; the Hartree solve, energy sums and p x p algebra are FP64
-                         in both (KS_FP64) */
+                         in both (the FP32 phase evaluates eps_xc and v_xc in FP32 and
+                         solves to mixed_cg_tol) (KS_FP64) */
   double polish_gtol; /* switch from the FP32 phase to the FP64 polish (1e-4) */
   int stall_iters;    /* 1: the FP32 phase also ends when the energy stagnates, i.e. the mean
                          of df_k = |E_{k-1} - E_k| / (|E_{k-1}| + 1) over the last three
@@ -106,6 +107,10 @@ typedef struct {
   int resume;         /* 1: continue from the state of the last ks_minimize on this problem
                          or from ks_state_load (X_inout is then output only); maxit counts
                          all iterations including those before the checkpoint (0) */
+  double mixed_cg_tol; /* KS_MIXED: Hartree CG tolerance during the FP32 phase, clamped to
+                          [cg_tol, 1e-3]; FP32 orbitals carry about 1e-7 relative
+                          error, so a tighter solve buys nothing there (1e-7).  The FP64
+                          polish uses cg_tol. */
 } ks_opts;
 
 typedef struct {

@@ -146,7 +146,7 @@ template <typename T>
 static ks_status evaluate(Problem &P, const T *X, T *EX, T *MX, double *E) {
   KS_TRY(launch_density<T>(P, X, P.rho));
   KS_TRY(launch_cg(P, P.rho, P.vH, P.cg_r, P.vH_valid));
-  KS_TRY(launch_potential(P, P.rho, P.vH, P.cg_r, P.veff, true));
+  KS_TRY(launch_potential(P, P.rho, P.vH, P.cg_r, P.veff, true, sizeof(T) == 4));
   KS_TRY(launch_hamiltonian<T>(P, X, P.veff, EX, MX, P.scal + SC_EKIN));
   ks_status st = sync_scalars(P);
   if (st != KS_OK) {
@@ -262,6 +262,7 @@ static double bb_step(int k, const Traces &t, const ks_opts &o) {
 
 struct PhaseResult {
   double E = 0, dnorm = 0;
+  double last_tau = 0;             // last accepted step
   int iters = 0, cg = 0, backtracks = 0;
   bool stalled = false;
 };
@@ -275,7 +276,7 @@ struct PhaseResult {
 template <typename T>
 static ks_status run_phase(Problem &P, const T *Xstart, T *Xend, const ks_opts &o, double gtol,
                            int maxit, int stall, int first_k, double ortho_tol, bool resume,
-                           PhaseResult *out) {
+                           PhaseResult *out, double tau_first = 0.0) {
   const int p = P.p;
   const size_t bytes = (size_t)P.n * p * sizeof(T);
   Problem::RunState &S = P.state;
@@ -300,6 +301,7 @@ static ks_status run_phase(Problem &P, const T *Xstart, T *Xend, const ks_opts &
     first_k = S.first_k;
     k = S.k;
     E = S.E; C = S.C; Q = S.Q; best = S.best; last_improve = S.last_improve;
+    out->last_tau = S.last_tau;
     have_prev = S.have_prev != 0;
     P.vH_valid = true;
     // regenerates D, MD, the small matrices and the traces exactly (all
@@ -328,13 +330,14 @@ static ks_status run_phase(Problem &P, const T *Xstart, T *Xend, const ks_opts &
     S.k = k;
     S.have_prev = have_prev ? 1 : 0;
     S.C = C; S.Q = Q; S.E = E; S.best = best; S.last_improve = last_improve;
+    S.last_tau = out->last_tau;
     S.dnorm2 = tr.dnorm2; S.ss = tr.ss; S.sy = tr.sy; S.yy = tr.yy;
     for (int i = 0; i < 3; ++i) { S.ix[i] = ix[i]; S.imx[i] = imx[i]; }
     for (int i = 0; i < 2; ++i) { S.iex[i] = iex[i]; S.id[i] = id[i]; S.imd[i] = imd[i]; }
   };
   save_state();
   while (std::sqrt(std::fmax(tr.dnorm2, 0.0)) > gtol && first_k + k < maxit) {
-    double tau = have_prev ? bb_step(first_k + k, tr, o) : o.tau0;
+    double tau = have_prev ? bb_step(first_k + k, tr, o) : (tau_first > 0.0 ? tau_first : o.tau0);
     int h = 0;
     double Et = 0;
     for (;;) {
@@ -346,6 +349,7 @@ static ks_status run_phase(Problem &P, const T *Xstart, T *Xend, const ks_opts &
       ++h;
     }
     backtracks += h;
+    out->last_tau = tau;
     const double Qn = o.eta * Q + 1.0;
     C = (o.eta * Q * C + Et) / Qn;
     Q = Qn;
@@ -415,17 +419,23 @@ static ks_status minimize_device(Problem &P, double *X_inout, const ks_opts &o, 
   const bool resume_fp32 = resume && P.state.elem == 4;
   bool resume_fp64 = resume && P.state.elem == 8;
   int done = resume ? P.state.first_k + P.state.k : 0;   // iterations before this call
+  double polish_tau = 0.0;
   if (o.precision == KS_MIXED && (!resume || resume_fp32)) {
     // FP32 phase (Hartree, energy sums and p x p algebra stay FP64), then
     // an FP64 polish from its last iterate.
     float *xs = blk<float>(P, B_G);
     if (!resume) KS_TRY(launch_convert(P, X_inout, xs));
     PhaseResult mr;
-    KS_TRY(run_phase<float>(P, xs, xs, o, std::fmax(o.polish_gtol, o.gtol), o.maxit, o.stall_iters,
-                            0, std::fmax(o.ortho_tol, 1e-5), resume_fp32, &mr));
+    P.cg_tol_phase = o.mixed_cg_tol > P.cg_tol ? std::fmin(o.mixed_cg_tol, 1e-3) : 0.0;
+    const ks_status pst = run_phase<float>(P, xs, xs, o, std::fmax(o.polish_gtol, o.gtol), o.maxit,
+                                           o.stall_iters, 0, std::fmax(o.ortho_tol, 1e-5),
+                                           resume_fp32, &mr);
+    P.cg_tol_phase = 0.0;
+    KS_TRY(pst);
     iters += mr.iters;
     cg += mr.cg;
     backtracks += mr.backtracks;
+    polish_tau = mr.last_tau;
     P.mixed_iters = P.state.first_k + P.state.k;
     P.mixed_dnorm = mr.dnorm;
     P.mixed_E = mr.E;
@@ -458,8 +468,10 @@ static ks_status minimize_device(Problem &P, double *X_inout, const ks_opts &o, 
   } else if (resume && o.precision != KS_MIXED && P.state.elem != 8) {
     return set_error(KS_EINVAL, "saved state is from an FP32 phase; resume it with KS_MIXED");
   }
+  // the polish continues with the FP32 phase's last accepted step instead
+  // of restarting from tau0
   KS_TRY(run_phase<double>(P, X_inout, X_inout, o, o.gtol, o.maxit, 0, done, o.ortho_tol,
-                           resume_fp64, &fr));
+                           resume_fp64, &fr, polish_tau));
   iters += fr.iters;
   cg += fr.cg;
   backtracks += fr.backtracks;
@@ -490,7 +502,7 @@ static ks_status minimize_device(Problem &P, double *X_inout, const ks_opts &o, 
 struct StateHeader {
   uint64_t magic;
   int32_t version, N, p, elem, retraction, first_k, k, have_prev, last_improve;
-  double C, Q, E, dnorm2, ss, sy, yy, best;
+  double C, Q, E, dnorm2, ss, sy, yy, best, last_tau;
 };
 constexpr uint64_t kStateMagic = 0x4b53535441544531ull;   // "KSSTATE1"
 
@@ -524,6 +536,7 @@ void ks_opts_default(ks_opts *o) {
   o->stall_iters = 1;
   o->stall_df = 1e-11;
   o->resume = 0;
+  o->mixed_cg_tol = 1e-7;
 }
 
 const char *ks_last_error_string(void) { return g_err; }
@@ -737,11 +750,11 @@ ks_status ks_state_save(ks_problem *kp, void *host_buf, size_t bytes) {
   if (bytes < state_bytes(P, S.elem)) return set_error(KS_EINVAL, "buffer too small");
   StateHeader hd{};
   hd.magic = kStateMagic;
-  hd.version = 1;
+  hd.version = 2;
   hd.N = P.N; hd.p = P.p; hd.elem = S.elem; hd.retraction = S.retraction;
   hd.first_k = S.first_k; hd.k = S.k; hd.have_prev = S.have_prev; hd.last_improve = S.last_improve;
   hd.C = S.C; hd.Q = S.Q; hd.E = S.E; hd.dnorm2 = S.dnorm2;
-  hd.ss = S.ss; hd.sy = S.sy; hd.yy = S.yy; hd.best = S.best;
+  hd.ss = S.ss; hd.sy = S.sy; hd.yy = S.yy; hd.best = S.best; hd.last_tau = S.last_tau;
   char *dst = (char *)host_buf;
   std::memcpy(dst, &hd, sizeof(hd));
   dst += sizeof(hd);
@@ -764,7 +777,7 @@ ks_status ks_state_load(ks_problem *kp, const void *host_buf, size_t bytes) {
   StateHeader hd;
   if (bytes < sizeof(hd)) return set_error(KS_EINVAL, "buffer too small");
   std::memcpy(&hd, host_buf, sizeof(hd));
-  if (hd.magic != kStateMagic || hd.version != 1) return set_error(KS_EINVAL, "not a saved state");
+  if (hd.magic != kStateMagic || hd.version != 2) return set_error(KS_EINVAL, "not a saved state");
   if (hd.N != P.N || hd.p != P.p || (hd.elem != 4 && hd.elem != 8))
     return set_error(KS_EINVAL, "saved state does not match this problem");
   if (bytes < state_bytes(P, hd.elem)) return set_error(KS_EINVAL, "buffer too small");
@@ -773,7 +786,7 @@ ks_status ks_state_load(ks_problem *kp, const void *host_buf, size_t bytes) {
   S.elem = hd.elem; S.retraction = hd.retraction; S.first_k = hd.first_k; S.k = hd.k;
   S.have_prev = hd.have_prev; S.last_improve = hd.last_improve;
   S.C = hd.C; S.Q = hd.Q; S.E = hd.E; S.dnorm2 = hd.dnorm2;
-  S.ss = hd.ss; S.sy = hd.sy; S.yy = hd.yy; S.best = hd.best;
+  S.ss = hd.ss; S.sy = hd.sy; S.yy = hd.yy; S.best = hd.best; S.last_tau = hd.last_tau;
   // canonical slots: current in slot 0, previous in slot 1
   const int order[9] = {B_X0, B_MX0, B_EX0, B_D0, B_MD0, B_X1, B_MX1, B_D1, B_MD1};
   const char *src = (const char *)host_buf + sizeof(hd);

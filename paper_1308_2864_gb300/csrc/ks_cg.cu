@@ -418,7 +418,7 @@ ks_status launch_cg(Problem &P, const double *rho, double *v, double *r, bool wa
   a.bar = P.bar;
   a.status = P.dstatus;
   a.iters_out = P.scal + SC_CG_ITERS;
-  a.tol = P.cg_tol;
+  a.tol = P.cg_tol_phase > 0.0 ? P.cg_tol_phase : P.cg_tol;
   a.maxit = P.cg_maxit;
   a.warm = warm ? 1 : 0;
   a.precond = P.cg_precond;

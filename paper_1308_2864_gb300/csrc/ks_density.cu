@@ -6,24 +6,44 @@
 
 namespace ks {
 
-// p >= 32: one warp per node, lanes stride over the node's row (coalesced),
-// fixed butterfly sum.
+// p >= 32: a warp takes 32 consecutive nodes, eight at a time; for each
+// node the lanes stride over its row (coalesced) and a fixed butterfly sums
+// the row.  The eight rows are loaded before any is used, so a lane has
+// eight loads in flight.  Lane l keeps the sum of node l of the group and
+// converts and stores it once: the FP64 tail is one warp instruction per 32
+// nodes, not one per node (every FP64 warp instruction is a 16-cycle issue).
+constexpr int kDenRows = 8;
+
 template <typename T>
 __global__ void density_warp_kernel(int n, int p, double occ, const T *__restrict__ X,
                                     double *__restrict__ rho) {
   const int lane = threadIdx.x & 31;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long k = warp; k < n; k += nwarps) {
-    const T *row = X + k * p;
-    T acc = 0;
-    for (int i = lane; i < p; i += 32) {
-      const T x = row[i];
-      acc = fma(x, x, acc);
-    }
+  for (long long k0 = warp * 32; k0 < n; k0 += nwarps * 32) {
+    T mine = 0;
+    const int cnt = (int)min(32LL, (long long)n - k0);
+    for (int j0 = 0; j0 < cnt; j0 += kDenRows) {
+      T acc[kDenRows];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) rho[k] = occ * (double)acc;
+      for (int u = 0; u < kDenRows; ++u) acc[u] = 0;
+      for (int i = lane; i < p; i += 32) {
+        T v[kDenRows];
+#pragma unroll
+        for (int u = 0; u < kDenRows; ++u)
+          v[u] = j0 + u < cnt ? X[(k0 + j0 + u) * p + i] : (T)0;
+#pragma unroll
+        for (int u = 0; u < kDenRows; ++u) acc[u] = fma(v[u], v[u], acc[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < kDenRows; ++u) {
+        T a = acc[u];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == j0 + u) mine = a;
+      }
+    }
+    if (lane < cnt) rho[k0 + lane] = occ * (double)mine;
   }
 }
 
@@ -42,7 +62,7 @@ __global__ void density_thread_kernel(int n, int p, double occ, const T *__restr
 template <typename T>
 ks_status launch_density(Problem &P, const T *X, double *rho) {
   if (P.p >= 32) {
-    const long long warps = P.n;
+    const long long warps = (P.n + 31) / 32;
     long long blocks = (warps * 32 + kThreads - 1) / kThreads;
     if (blocks > 64LL * P.sms) blocks = 64LL * P.sms;
     ProfScope ps_(P.stream, KP_DENSITY, 2.0 * P.n * P.p, (double)P.n * P.p * sizeof(T) + 8.0 * P.n);

@@ -73,6 +73,7 @@ struct Problem {
   // geometry and sizes
   int N = 0, n = 0, p = 0, natoms = 0, xc = 0;
   double L = 0, h = 0, rc = 0, occ = 0, cg_tol = 0;
+  double cg_tol_phase = 0;         // > 0: Hartree tolerance of the running FP32 phase
   int cg_maxit = 0;
   std::vector<double> atoms_host;  // natoms x 4: x, y, z, Z
   cudaStream_t stream = nullptr;
@@ -121,6 +122,7 @@ struct Problem {
     int first_k = 0, k = 0;        // iteration offset of the phase, iterations in it
     int have_prev = 0;
     double C = 0, Q = 1, E = 0, dnorm2 = 0, ss = 0, sy = 0, yy = 0, best = 0;
+    double last_tau = 0;           // last accepted step (carried into the FP64 polish)
     int last_improve = 0;
     int ix[3] = {0, 1, 2}, imx[3] = {3, 4, 5}, iex[2] = {6, 7}, id[2] = {9, 10}, imd[2] = {11, 12};
   } state;
@@ -171,7 +173,7 @@ int cg_grid_blocks(int sms, int n, int N);
 size_t cg_dynamic_smem(int N);
 // ks_xc.cu: veff = vext + vH + v_xc(rho); energy partials; reduction helpers
 ks_status launch_potential(Problem &P, const double *rho, const double *vH, const double *r,
-                           double *veff, bool with_hartree);
+                           double *veff, bool with_hartree, bool fp32_xc = false);
 ks_status launch_reduce(Problem &P, const double *partials, int nchan, int nb, double *out,
                         double scale = 1.0);
 // Blocks of the grid-stride reduction kernels (their partials are nchan x this).

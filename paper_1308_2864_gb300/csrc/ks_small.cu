@@ -101,13 +101,44 @@ __device__ __forceinline__ double rsqrt_newton(double d) {
   return y;
 }
 
-// On GB300 one SM retires two FP64 lanes per clock, so every FP64 warp
-// instruction costs the same whether its lanes are busy or not: the kernel
-// keeps warps dense (flat loops over the trailing triangle, one thread per
-// column in the substitution) and replaces divisions by reciprocals.
+// Flat index t of the lower triangle (diagonal included, rows in order, row
+// i starting at i (i + 1) / 2) -> (i, c), c <= i.  FP32 square root plus an
+// integer correction: no FP64 instruction.
+__device__ __forceinline__ void tri_decode(int t, int &i, int &c) {
+  int r = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+  while (r > 0 && r * (r + 1) / 2 > t) --r;
+  while ((r + 1) * (r + 2) / 2 <= t) ++r;
+  i = r;
+  c = t - r * (r + 1) / 2;
+}
+
+// Pivot j: L_jj = sqrt(w) and its reciprocal; false on a non-positive or
+// non-finite w (records KS_ENOTPD).
+__device__ __forceinline__ bool chol_pivot(double w, int j, double *W, int p, double *rdiag,
+                                           int *s_fail, int *status) {
+  if (!(w > 0.0) || !isfinite(w)) {
+    *s_fail = 1;
+    atomicCAS(status, 0, (int)KS_ENOTPD);
+    return false;
+  }
+  const double y = rsqrt_newton(w);
+  W[j * p + j] = w * y;
+  rdiag[j] = y;
+  return true;
+}
+
+// Right-looking Cholesky W = L L^T merged with the inversion of L: with
+// R = I at the start, step j (i) scales column j of L by 1/L_jj and row j of
+// R by the same, which makes it row j of L^{-1}; (ii) for every row i > j
+// updates W[i][k] -= L_ij L_kj (j < k <= i) and R[i][c] -= L_ij V[j][c]
+// (c <= j).  Step (ii) is one flat loop over the lower triangle below row
+// j, so all warps stay busy; the thread that updates W[j+1][j+1] also takes
+// the next pivot, leaving two barriers per column.  On GB300 one SM retires
+// two FP64 lanes per clock, so dense warps and no divisions matter more
+// than anything else here.
 __global__ void __launch_bounds__(kSmallThreads) qr_factor_smem_kernel(
     int p, const double *DMD, const double *O, double tau, double *C1, double *C2, int *status) {
-  extern __shared__ double W[];          // p*p L, then p*p L^{-1} (column-major), p reciprocals
+  extern __shared__ double W[];          // p*p: W -> L; p*p: R -> L^{-1} (row-major); p reciprocals
   double *V = W + p * p;
   double *rdiag = V + p * p;
   __shared__ int s_fail;
@@ -117,47 +148,36 @@ __global__ void __launch_bounds__(kSmallThreads) qr_factor_smem_kernel(
     double r = O ? O[e] : (i == j ? 1.0 : 0.0);
     if (DMD) r = fma(t2, DMD[e], r);
     W[e] = r;
+    V[e] = i == j ? 1.0 : 0.0;
   }
   if (threadIdx.x == 0) s_fail = 0;
   __syncthreads();
+  if (threadIdx.x == 0) chol_pivot(W[0], 0, W, p, rdiag, &s_fail, status);
+  __syncthreads();
+  const int tend = p * (p + 1) / 2;
   for (int j = 0; j < p; ++j) {
-    if (threadIdx.x == 0) {
-      const double d = W[j * p + j];
-      if (!(d > 0.0) || !isfinite(d)) {
-        s_fail = 1;
-        atomicCAS(status, 0, (int)KS_ENOTPD);
-      } else {
-        const double y = rsqrt_newton(d);
-        W[j * p + j] = d * y;
-        rdiag[j] = y;
-      }
-    }
-    __syncthreads();
     if (s_fail) return;
     const double inv = rdiag[j];
-    for (int i = j + 1 + threadIdx.x; i < p; i += blockDim.x) W[i * p + j] *= inv;
+    const int below = p - j - 1;
+    for (int t = threadIdx.x; t < below + j + 1; t += blockDim.x) {
+      if (t < below) W[(j + 1 + t) * p + j] *= inv;
+      else V[j * p + (t - below)] *= inv;
+    }
     __syncthreads();
-    const int m = p - j - 1;
-    for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
-      const int ii = t / m, kk = t - ii * m;
-      if (kk <= ii) {
-        const int i = j + 1 + ii, k = j + 1 + kk;
-        W[i * p + k] = fma(-W[i * p + j], W[k * p + j], W[i * p + k]);
+    for (int t = (j + 1) * (j + 2) / 2 + threadIdx.x; t < tend; t += blockDim.x) {
+      int i, c;
+      tri_decode(t, i, c);
+      const double lij = W[i * p + j];
+      if (c <= j) {
+        V[i * p + c] = fma(-lij, V[j * p + c], V[i * p + c]);
+      } else {
+        const double w = fma(-lij, W[c * p + j], W[i * p + c]);
+        W[i * p + c] = w;
+        if (i == j + 1 && c == j + 1) chol_pivot(w, j + 1, W, p, rdiag, &s_fail, status);
       }
     }
     __syncthreads();
   }
-  // L^{-1}: thread c solves L x = e_c; V[k * p + c] = (L^{-1})_{kc}
-  for (int c = threadIdx.x; c < p; c += blockDim.x) {
-    for (int k = 0; k < c; ++k) V[k * p + c] = 0.0;
-    V[c * p + c] = rdiag[c];
-    for (int i = c + 1; i < p; ++i) {
-      double acc = 0.0;
-      for (int k = c; k < i; ++k) acc = fma(W[i * p + k], V[k * p + c], acc);
-      V[i * p + c] = -acc * rdiag[i];
-    }
-  }
-  __syncthreads();
   for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
     const int i = e / p, j = e % p;
     const double cval = V[j * p + i];     // (L^{-T})_{ij} = (L^{-1})_{ji}

@@ -65,15 +65,23 @@ struct StArgs {
   double red_scale;
   unsigned int *counter;
   int *status;                // device status word (TMA waits that give up)
+  float cf[9];                // k0, ke, kc, m0, mf, me, mc, occ, 2 occ h^3 rounded to FP32 (host)
 };
 
-// Coefficients in the working precision, converted once per thread.
+// Coefficients in the working precision (FP32 ones rounded on the host: a
+// per-thread conversion would be nine FP64-pipe instructions per thread).
 template <typename T>
 struct StCoefT {
   T k0, ke, kc, m0, mf, me, mc, occ, vscale;
-  __device__ explicit StCoefT(const StArgs &a)
-      : k0((T)a.c.k0), ke((T)a.c.ke), kc((T)a.c.kc), m0((T)a.c.m0), mf((T)a.c.mf),
-        me((T)a.c.me), mc((T)a.c.mc), occ((T)a.occ), vscale((T)(2.0 * a.occ * a.h3)) {}
+  __device__ explicit StCoefT(const StArgs &a) {
+    if constexpr (sizeof(T) == 4) {
+      k0 = a.cf[0]; ke = a.cf[1]; kc = a.cf[2]; m0 = a.cf[3]; mf = a.cf[4];
+      me = a.cf[5]; mc = a.cf[6]; occ = a.cf[7]; vscale = a.cf[8];
+    } else {
+      k0 = a.c.k0; ke = a.c.ke; kc = a.c.kc; m0 = a.c.m0; mf = a.c.mf;
+      me = a.c.me; mc = a.c.mc; occ = a.occ; vscale = 2.0 * a.occ * a.h3;
+    }
+  }
 };
 
 template <typename T, int PC, int Kind>
@@ -445,6 +453,9 @@ template <typename T, int PC, int Kind>
 static ks_status stencil_launch_pc(Problem &P, StArgs &a, int nchan, double flops, double bytes) {
   KS_TRY(stencil_geometry<PC>(P, nchan, a));
   a.c = q1_coefficients(P.h);
+  const double cd[9] = {a.c.k0, a.c.ke, a.c.kc, a.c.m0, a.c.mf, a.c.me, a.c.mc, a.occ,
+                        2.0 * a.occ * a.h3};
+  for (int i = 0; i < 9; ++i) a.cf[i] = (float)cd[i];
   a.part = P.partials;
   a.counter = P.red_counter;
   a.status = P.dstatus;

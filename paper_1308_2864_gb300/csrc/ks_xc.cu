@@ -17,35 +17,70 @@ constexpr double kPzDen1 = 1.0 + kPzBeta1 + kPzBeta2;
 constexpr double kPzD = kPzGamma / kPzDen1 - kPzB;
 constexpr double kPzC = -kPzGamma * (0.5 * kPzBeta1 + kPzBeta2) / (kPzDen1 * kPzDen1) - kPzA - kPzD;
 
-__device__ __forceinline__ void lda_point(double rho, int xc, double &eps, double &v) {
-  if (!(rho >= 1e-30)) {
-    eps = 0.0;
-    v = 0.0;
+// rho^(-1/3) for rho >= 1e-30: single-precision start, then two Newton steps
+// on f(z) = z^-3 - rho, z <- z (4 - rho z^3) / 3 (no division; each step
+// squares the relative error, 1e-7 -> 1e-14 -> below FP64 rounding).  On
+// GB300 every FP64 instruction is a 16-cycle issue, so this replaces two
+// library cube roots and three divisions per point.
+__device__ __forceinline__ double inv_cbrt(double rho) {
+  double z = (double)rcbrtf((float)rho);
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const double z3 = z * z * z;
+    z = z * fma(-rho, z3, 4.0) * (1.0 / 3.0);
+  }
+  return z;
+}
+
+// eps_xc and v_xc = d(rho eps_xc)/d rho at one point, in precision R
+// (FP64; FP32 for the mixed-precision phase, whose orbitals carry FP32
+// rounding already; the energy sums stay FP64 in both).
+//   Slater: eps_x = -(3/4) (3/pi)^(1/3) rho^(1/3), v_x = (4/3) eps_x;
+//   PZ81 (r_s = (3 / (4 pi rho))^(1/3)): eps_c = gamma / (1 + beta1 sqrt(r_s)
+//   + beta2 r_s) for r_s >= 1, A ln r_s + B + C r_s ln r_s + D r_s below;
+//   v_c = eps_c - (r_s / 3) d eps_c / d r_s.
+template <typename R>
+__device__ __forceinline__ void lda_point(double rho_d, int xc, R &eps, R &v) {
+  if (!(rho_d >= 1e-30)) {
+    eps = 0;
+    v = 0;
     return;
   }
-  const double c = cbrt(3.0 / M_PI);
-  const double r13 = cbrt(rho);
-  eps = -0.75 * c * r13;
+  const R c = (R)0.98474502184269654;              // (3/pi)^(1/3)
+  const R crs = (R)0.62035049089940001;            // (3/(4 pi))^(1/3)
+  const R rho = (R)rho_d;
+  R z;                                             // rho^(-1/3)
+  if constexpr (sizeof(R) == 8) z = inv_cbrt(rho_d);
+  else z = rcbrtf(rho);
+  const R r13 = rho * z * z;                       // rho^(1/3)
+  eps = (R)-0.75 * c * r13;
   v = -c * r13;
   if (xc == KS_XC_SLATER_PZ81) {
-    const double rs = cbrt(3.0 / (4.0 * M_PI * rho));
-    double ec, dec;
-    if (rs >= 1.0) {
-      const double srs = sqrt(rs);
-      const double den = 1.0 + kPzBeta1 * srs + kPzBeta2 * rs;
-      ec = kPzGamma / den;
-      dec = -kPzGamma * (0.5 * kPzBeta1 / srs + kPzBeta2) / (den * den);
+    const R rs = crs * z;
+    R ec, dec;
+    if (rs >= (R)1) {
+      R irs;                                       // 1 / sqrt(r_s)
+      if constexpr (sizeof(R) == 8) irs = rsqrt(rs);
+      else irs = rsqrtf(rs);
+      const R srs = rs * irs;
+      const R iden = (R)1 / ((R)1 + (R)kPzBeta1 * srs + (R)kPzBeta2 * rs);
+      ec = (R)kPzGamma * iden;
+      dec = -(R)kPzGamma * ((R)(0.5 * kPzBeta1) * irs + (R)kPzBeta2) * (iden * iden);
     } else {
-      const double lrs = log(rs);
-      ec = kPzA * lrs + kPzB + kPzC * rs * lrs + kPzD * rs;
-      dec = kPzA / rs + kPzC * (lrs + 1.0) + kPzD;
+      R lrs;
+      if constexpr (sizeof(R) == 8) lrs = log(rs);
+      else lrs = logf(rs);
+      ec = (R)kPzA * lrs + (R)kPzB + (R)kPzC * rs * lrs + (R)kPzD * rs;
+      // A / r_s = A rho^(1/3) / crs
+      dec = (R)kPzA * (r13 * (R)(1.0 / 0.62035049089940001)) + (R)kPzC * (lrs + (R)1) + (R)kPzD;
     }
     eps += ec;
-    v += ec - (rs / 3.0) * dec;
+    v += ec - (rs / (R)3) * dec;
   }
 }
 
 // Channels of the block partials: 0 = E_ext, 1 = E_H, 2 = E_xc.
+template <typename R>
 __global__ void potential_kernel(long long n, double h3, int xc, int with_h,
                                  const double *__restrict__ rho, const double *__restrict__ vext,
                                  const double *__restrict__ vH, const double *__restrict__ r,
@@ -57,9 +92,10 @@ __global__ void potential_kernel(long long n, double h3, int xc, int with_h,
   for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (long long)gridDim.x * blockDim.x) {
     const double rk = rho[k], ve = vext[k];
-    double eps, vxc;
-    lda_point(rk, xc, eps, vxc);
-    double v = ve + vxc;
+    R eps_r, vxc_r;
+    lda_point<R>(rk, xc, eps_r, vxc_r);
+    const double eps = (double)eps_r;
+    double v = ve + (double)vxc_r;
     e_ext = fma(h3 * ve, rk, e_ext);
     e_xc = fma(h3 * rk, eps, e_xc);
     if (with_h) {
@@ -109,14 +145,19 @@ ks_status launch_reduce(Problem &P, const double *partials, int nchan, int nb, d
 }
 
 ks_status launch_potential(Problem &P, const double *rho, const double *vH, const double *r,
-                           double *veff, bool with_hartree) {
+                           double *veff, bool with_hartree, bool fp32_xc) {
   const int nb = reduce_blocks(P, P.n);
   const double h3 = P.h * P.h * P.h;
   {
     ProfScope ps_(P.stream, KP_POTENTIAL, 40.0 * P.n, 40.0 * P.n);
-    potential_kernel<<<nb, kThreads, 0, P.stream>>>(P.n, h3, P.xc, with_hartree ? 1 : 0, rho,
-                                                    P.vext, vH, r, veff, P.partials,
-                                                    P.scal + SC_EEXT, P.red_counter);
+    if (fp32_xc)
+      potential_kernel<float><<<nb, kThreads, 0, P.stream>>>(
+          P.n, h3, P.xc, with_hartree ? 1 : 0, rho, P.vext, vH, r, veff, P.partials,
+          P.scal + SC_EEXT, P.red_counter);
+    else
+      potential_kernel<double><<<nb, kThreads, 0, P.stream>>>(
+          P.n, h3, P.xc, with_hartree ? 1 : 0, rho, P.vext, vH, r, veff, P.partials,
+          P.scal + SC_EEXT, P.red_counter);
   }
   KS_CUDA_TRY(cudaGetLastError());
   return KS_OK;
