@@ -255,6 +255,40 @@ ks_status ks_server_stats(ks_server *srv, ks_server_counters *out);
 /* Waits for running jobs, drops queued ones, joins the workers. */
 ks_status ks_server_destroy(ks_server *srv);
 
+/* ---------------------------------------------------------------------------
+ * Batched job table.  The paper minimises one system at a time; this is the
+ * throughput form for many small independent systems: Alg. ConOptM (QR
+ * retraction, Prop. 3.1) runs for every job of the table in lockstep
+ * iterations, and each step of an iteration (density, Hartree CG, potential,
+ * stencils, M^{-1}, Grams, updates, p x p factors) is ONE kernel launch over
+ * all jobs that are still iterating.  Every job keeps its own step size,
+ * nonmonotone line search, convergence test and iteration count; a job that
+ * backtracks repeats its trial while the others wait; a job that converges
+ * (or fails) drops out of the launches.  Per-job results agree with
+ * ks_minimize on the same system up to the order of floating-point sums.
+ *
+ * Limits: p <= 104 per job; njobs <= the number of CG blocks that fit on the
+ * device at once (several hundred on GB300); KS_QR only. */
+typedef struct ks_batch ks_batch;
+
+/* descs: njobs systems (stream fields ignored); stream: cudaStream_t for all
+ * work (NULL = library-owned).  Allocates every job's device state. */
+ks_status ks_batch_create(const ks_problem_desc *descs, int njobs, void *stream, ks_batch **out);
+
+/* Device bytes held by the batch. */
+size_t ks_batch_bytes(const ks_batch *batch);
+
+/* Minimise every job from X_inout[j] (HOST, n_j x p_j row-major FP64; the
+ * result overwrites it).  opts as for ks_minimize (retraction must be KS_QR;
+ * KS_MIXED runs the FP32 phase for all jobs, then the FP64 polish for the
+ * jobs that reached polish_gtol or stagnated); results: njobs entries.
+ * Returns KS_OK when every job converged, KS_ENOCONV when some did not (see
+ * results[j].status), another code when the batch could not run. */
+ks_status ks_batch_minimize(ks_batch *batch, double *const *X_inout, const ks_opts *opts,
+                            ks_result *results);
+
+ks_status ks_batch_destroy(ks_batch *batch);
+
 /* Text of the last error on the calling thread ("" if none). */
 const char *ks_last_error_string(void);
 

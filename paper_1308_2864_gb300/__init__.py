@@ -117,6 +117,11 @@ SIGNATURES = [
     ("ks_server_poll", _I, [_P, ctypes.c_uint64, _I, ctypes.POINTER(Result), _DP, _DP]),
     ("ks_server_stats", _I, [_P, ctypes.POINTER(ServerStats)]),
     ("ks_server_destroy", _I, [_P]),
+    ("ks_batch_create", _I, [ctypes.POINTER(ProblemDesc), _I, _P, ctypes.POINTER(_P)]),
+    ("ks_batch_bytes", ctypes.c_size_t, [_P]),
+    ("ks_batch_minimize", _I, [_P, ctypes.POINTER(_DP), ctypes.POINTER(Opts),
+                               ctypes.POINTER(Result)]),
+    ("ks_batch_destroy", _I, [_P]),
 ]
 
 
@@ -507,3 +512,58 @@ class Server:
 
 __all__ = ["Server", "Problem", "KSError", "load_library", "library_path", "default_opts",
            "KS_QR", "KS_CAYLEY", "KS_XC_SLATER", "KS_XC_SLATER_PZ81", "SIGNATURES"]
+
+
+class Batch:
+    """Job table of independent systems minimised together (ks_batch): every
+    kernel launch of an iteration covers all jobs still iterating."""
+
+    def __init__(self, systems, stream=None):
+        lib = load_library()
+        self.systems = list(systems)
+        n = len(self.systems)
+        descs = (ProblemDesc * n)()
+        self._keep = []
+        for d, s in zip(descs, self.systems):
+            atoms = np.ascontiguousarray(np.asarray(s.atoms, dtype=np.float64).reshape(-1, 3))
+            Z = np.ascontiguousarray(np.asarray(s.Z, dtype=np.float64).reshape(-1))
+            self._keep += [atoms, Z]
+            d.N, d.L, d.natoms = s.N, s.L, len(Z)
+            d.R = atoms.ctypes.data_as(_DP)
+            d.Z = Z.ctypes.data_as(_DP)
+            d.rc, d.p, d.occ, d.xc = s.rc, s.p, s.occ, s.xc
+            d.cg_tol, d.cg_maxit, d.precision, d.cg_precond = 1e-10, 20000, KS_FP64, 1
+        h = ctypes.c_void_p()
+        st = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+        _check(lib.ks_batch_create(descs, n, st, ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def bytes(self) -> int:
+        return load_library().ks_batch_bytes(self._h)
+
+    def minimize(self, X0=None, **opts):
+        """Minimise every job from X0[j] (default s.x0()); returns (list of
+        result dicts, list of final X arrays).  A job that did not converge
+        has status KS_ENOCONV in its result; no exception is raised for it."""
+        n = len(self.systems)
+        X = [np.ascontiguousarray(s.x0() if X0 is None else X0[j], dtype=np.float64).copy()
+             for j, s in enumerate(self.systems)]
+        ptrs = (_DP * n)(*[x.ctypes.data_as(_DP) for x in X])
+        res = (Result * n)()
+        o = default_opts(**opts)
+        st = load_library().ks_batch_minimize(self._h, ptrs, ctypes.byref(o), res)
+        if st not in (KS_OK, KS_ENOCONV):
+            _check(st)
+        return [result_dict(r) for r in res], X
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load_library().ks_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -36,12 +36,6 @@ ks_status cuda_error(cudaError_t e, const char *where) {
   return set_error(KS_ECUDA, "%s: %s", where, cudaGetErrorString(e));
 }
 
-// Index of the n x p blocks in Problem::blk.
-enum Block { B_X0 = 0, B_X1, B_X2, B_MX0, B_MX1, B_MX2, B_EX0, B_EX1, B_G, B_D0, B_D1, B_MD0, B_MD1 };
-
-// Offsets (in units of p*p) of the small matrices in the pp pool; the first
-// 6 p^2 are scratch of the factor kernels.
-enum Small { S_WORK = 0, S_S = 6, S_DMD, S_O, S_A, S_B, S_C1, S_C2, S_T, S_COUNT };
 
 static size_t gram_partials_len(int p, int sms) {
   const size_t tiles = (size_t)((p + kTile - 1) / kTile) * ((p + kTile - 1) / kTile);

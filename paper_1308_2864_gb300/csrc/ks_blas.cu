@@ -36,16 +36,16 @@ static int gram_chunks(const Problem &P, int pa, int qb) {
 
 // T = double, or float for the mixed path (FP32 products and per-chunk
 // FP32 sums, chunk partials summed in FP64).
+// One 64 x 64 output tile (index `tile`, row-major over the tile grid) of
+// one row chunk.
 template <typename T>
-__global__ void __launch_bounds__(256) gram_kernel(long long n, int pa, int qb, long long rows_per,
-                                                   const T *__restrict__ A,
-                                                   const T *__restrict__ B,
-                                                   double *__restrict__ part) {
+__device__ __forceinline__ void gram_tile_body(long long n, int pa, int qb, long long rows_per,
+                                               const T *__restrict__ A, const T *__restrict__ B,
+                                               double *__restrict__ part, int tile, int chunk) {
   __shared__ T As[kTileK][kTile];
   __shared__ T Bs[kTileK][kTile];
   const int tq = (qb + kTile - 1) / kTile;
-  const int ta = blockIdx.x / tq, tb = blockIdx.x % tq;
-  const int chunk = blockIdx.y;
+  const int ta = tile / tq, tb = tile % tq;
   const long long r0 = chunk * rows_per;
   long long r1 = r0 + rows_per;
   if (r1 > n) r1 = n;
@@ -94,6 +94,14 @@ __global__ void __launch_bounds__(256) gram_kernel(long long n, int pa, int qb, 
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) gram_kernel(long long n, int pa, int qb, long long rows_per,
+                                                   const T *__restrict__ A,
+                                                   const T *__restrict__ B,
+                                                   double *__restrict__ part) {
+  gram_tile_body<T>(n, pa, qb, rows_per, A, B, part, blockIdx.x, blockIdx.y);
+}
+
 // out[e] = sum over chunks of part[c * len + e]: 8 threads per output, each
 // summing a strided eighth of the chunks, then a fixed butterfly (the order
 // is the same on every run).
@@ -119,13 +127,10 @@ __global__ void gram_reduce_kernel(int chunks, long long len, const double *__re
 constexpr int kSmallPQ = 8;
 
 template <typename T>
-__global__ void __launch_bounds__(256) gram_small_kernel(long long n, int pa, int qb,
-                                                         long long rows_per,
-                                                         const T *__restrict__ A,
-                                                         const T *__restrict__ B,
-                                                         double *__restrict__ part) {
+__device__ __forceinline__ void gram_small_body(long long n, int pa, int qb, long long rows_per,
+                                                const T *__restrict__ A, const T *__restrict__ B,
+                                                double *__restrict__ part, int chunk) {
   __shared__ double red[8][kSmallPQ * kSmallPQ];
-  const int chunk = blockIdx.x;
   const long long r0 = chunk * rows_per;
   long long r1 = r0 + rows_per;
   if (r1 > n) r1 = n;
@@ -170,6 +175,15 @@ __global__ void __launch_bounds__(256) gram_small_kernel(long long n, int pa, in
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w][a * kSmallPQ + b];
     part[(long long)chunk * pa * qb + e] = v;
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) gram_small_kernel(long long n, int pa, int qb,
+                                                         long long rows_per,
+                                                         const T *__restrict__ A,
+                                                         const T *__restrict__ B,
+                                                         double *__restrict__ part) {
+  gram_small_body<T>(n, pa, qb, rows_per, A, B, part, blockIdx.x);
 }
 
 template <typename T>
@@ -219,18 +233,17 @@ ks_status launch_gram(Problem &P, const T *A, int pa, const T *B, int qb, double
 // once per update for the FP32 phase (converting in every block would put
 // a conversion per staged element on the FP64 pipe).
 template <typename T, typename TC>
-__global__ void __launch_bounds__(256) combine_kernel(long long n, int q, const T *__restrict__ A1,
-                                                      int k1, const TC *__restrict__ C1,
-                                                      const T *__restrict__ A2, int k2,
-                                                      const TC *__restrict__ C2, double alpha_d,
-                                                      double beta_d,
-                                                      const T *__restrict__ Bm,
-                                                      T *__restrict__ out) {
+__device__ __forceinline__ void combine_tile_body(long long n, int q, const T *__restrict__ A1,
+                                                  int k1, const TC *__restrict__ C1,
+                                                  const T *__restrict__ A2, int k2,
+                                                  const TC *__restrict__ C2, double alpha_d,
+                                                  double beta_d, const T *__restrict__ Bm,
+                                                  T *__restrict__ out, int bx, int by) {
   __shared__ T As[kTile][kTileK + 1];
   __shared__ T Cs[kTileK][kTile];
   const T alpha = (T)alpha_d, beta = (T)beta_d;
-  const long long r0 = (long long)blockIdx.x * kTile;
-  const int c0 = blockIdx.y * kTile;
+  const long long r0 = (long long)bx * kTile;
+  const int c0 = by * kTile;
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
   T acc[4][4];
 #pragma unroll
@@ -283,16 +296,28 @@ __global__ void __launch_bounds__(256) combine_kernel(long long n, int q, const 
   }
 }
 
+template <typename T, typename TC>
+__global__ void __launch_bounds__(256) combine_kernel(long long n, int q, const T *__restrict__ A1,
+                                                      int k1, const TC *__restrict__ C1,
+                                                      const T *__restrict__ A2, int k2,
+                                                      const TC *__restrict__ C2, double alpha_d,
+                                                      double beta_d,
+                                                      const T *__restrict__ Bm,
+                                                      T *__restrict__ out) {
+  combine_tile_body<T, TC>(n, q, A1, k1, C1, A2, k2, C2, alpha_d, beta_d, Bm, out, blockIdx.x,
+                           blockIdx.y);
+}
+
 // Narrow updates (q <= kNarrowQ): one thread per output entry, the small
 // C matrices in shared memory, no padded arithmetic.
 constexpr int kNarrowQ = 32;
 constexpr int kNarrowK = 2 * kNarrowQ;
 
 template <typename T>
-__global__ void __launch_bounds__(256) combine_narrow_kernel(
+__device__ __forceinline__ void combine_narrow_body(
     long long n, int q, const T *__restrict__ A1, int k1, const double *__restrict__ C1,
     const T *__restrict__ A2, int k2, const double *__restrict__ C2, double alpha_d,
-    double beta_d, const T *__restrict__ Bm, T *__restrict__ out) {
+    double beta_d, const T *__restrict__ Bm, T *__restrict__ out, int vb, int vnb) {
   __shared__ T Cs[2][kNarrowK * kNarrowQ];
   for (int e = threadIdx.x; e < k1 * q; e += blockDim.x) Cs[0][e] = (T)C1[e];
   if (A2)
@@ -300,8 +325,8 @@ __global__ void __launch_bounds__(256) combine_narrow_kernel(
   __syncthreads();
   const T alpha = (T)alpha_d, beta = (T)beta_d;
   const long long total = n * q;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
+  for (long long e = (long long)vb * blockDim.x + threadIdx.x; e < total;
+       e += (long long)vnb * blockDim.x) {
     const long long row = e / q;
     const int col = (int)(e - row * q);
     T acc = 0;
@@ -315,6 +340,15 @@ __global__ void __launch_bounds__(256) combine_narrow_kernel(
     if (Bm) v = fma(beta, Bm[e], v);
     out[e] = v;
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) combine_narrow_kernel(
+    long long n, int q, const T *__restrict__ A1, int k1, const double *__restrict__ C1,
+    const T *__restrict__ A2, int k2, const double *__restrict__ C2, double alpha_d,
+    double beta_d, const T *__restrict__ Bm, T *__restrict__ out) {
+  combine_narrow_body<T>(n, q, A1, k1, C1, A2, k2, C2, alpha_d, beta_d, Bm, out, blockIdx.x,
+                         gridDim.x);
 }
 
 // FP32 copies of the update coefficients (one launch for both matrices).
@@ -368,6 +402,214 @@ ks_status launch_combine(Problem &P, const T *A1, int k1, const double *C1, cons
   KS_CUDA_TRY(cudaGetLastError());
   return KS_OK;
 }
+
+// ---------------------------------------------------------------- batched
+// Grams of every active job: tiles x chunks blocks per job (64-tile kernel)
+// or chunks blocks (p <= kSmallPQ), then the chunk sums into pp + smOut p^2.
+template <typename T>
+__global__ void __launch_bounds__(256) gram_batch_kernel(const BJob *__restrict__ jobs,
+                                                         const int *__restrict__ start, int J,
+                                                         const unsigned char *__restrict__ active,
+                                                         int sA, int sB, int small) {
+  const int j = batch_job_of(start, J, blockIdx.x);
+  if (!active[j]) return;
+  const BJob &b = jobs[j];
+  const int vb = blockIdx.x - start[j];
+  const T *A = (const T *)b.blk[sA], *Bp = (const T *)b.blk[sB];
+  if (small) {
+    gram_small_body<T>(b.n, b.p, b.p, b.gram_rows_per, A, Bp, b.partials, vb);
+  } else {
+    const int tiles = ((b.p + kTile - 1) / kTile) * ((b.p + kTile - 1) / kTile);
+    gram_tile_body<T>(b.n, b.p, b.p, b.gram_rows_per, A, Bp, b.partials, vb % tiles, vb / tiles);
+  }
+}
+
+__global__ void gram_reduce_batch_kernel(const BJob *__restrict__ jobs,
+                                         const int *__restrict__ start, int J,
+                                         const unsigned char *__restrict__ active, int smOut) {
+  const int j = batch_job_of(start, J, blockIdx.x);
+  if (!active[j]) return;
+  const BJob &b = jobs[j];
+  const long long t = (long long)(blockIdx.x - start[j]) * blockDim.x + threadIdx.x;
+  const long long len = (long long)b.p * b.p;
+  const long long e = t >> 3;
+  const int sub = (int)(t & 7);
+  double acc = 0.0;
+  if (e < len)
+    for (int c = sub; c < b.gram_chunks; c += 8) acc += b.partials[(long long)c * len + e];
+  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+  if (sub == 0 && e < len) b.pp[(size_t)smOut * len + e] = acc;
+}
+
+template <typename T>
+ks_status batch_gram(Batch &B, int sA, int sB, int smOut) {
+  for (int small = 1; small >= 0; --small) {
+    const int m = small ? BM_GRAM_SMALL : BM_GRAM_TILED;
+    const int nb = B.total(m);
+    if (nb == 0) continue;
+    {
+      ProfScope ps_(B.stream, KP_GRAM);
+      gram_batch_kernel<T><<<nb, 256, 0, B.stream>>>(B.jobs_dev, B.map(m), B.J, B.active_dev, sA,
+                                                     sB, small);
+    }
+    KS_CUDA_TRY(cudaGetLastError());
+  }
+  const int nr = B.total(BM_GRAM_REDUCE);
+  {
+    ProfScope ps_(B.stream, KP_REDUCE);
+    gram_reduce_batch_kernel<<<nr, kThreads, 0, B.stream>>>(B.jobs_dev, B.map(BM_GRAM_REDUCE), B.J,
+                                                            B.active_dev, smOut);
+  }
+  KS_CUDA_TRY(cudaGetLastError());
+  return KS_OK;
+}
+
+// out = alpha (A1 C1 + A2 C2) + beta Bm with q = k1 = k2 = p per job; C from
+// pp (FP64; the 64-tile form of the FP32 phase reads the FP32 copies that
+// coef_batch_kernel leaves in cf).
+struct CombSlots {
+  int a1, c1, a2, c2, bm, out;
+  double alpha, beta;
+};
+
+__global__ void coef_batch_kernel(const BJob *__restrict__ jobs, const int *__restrict__ start,
+                                  int J, const unsigned char *__restrict__ active, int smC1,
+                                  int smC2) {
+  const int j = batch_job_of(start, J, blockIdx.x);
+  if (!active[j]) return;
+  const BJob &b = jobs[j];
+  const long long len = (long long)b.p * b.p;
+  const long long e = (long long)(blockIdx.x - start[j]) * blockDim.x + threadIdx.x;
+  if (e < len) b.cf[e] = (float)b.pp[(size_t)smC1 * len + e];
+  else if (smC2 >= 0 && e < 2 * len) b.cf[e] = (float)b.pp[(size_t)smC2 * len + e - len];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) combine_batch_kernel(const BJob *__restrict__ jobs,
+                                                            const int *__restrict__ start, int J,
+                                                            const unsigned char *__restrict__ active,
+                                                            CombSlots sl, int narrow) {
+  const int j = batch_job_of(start, J, blockIdx.x);
+  if (!active[j]) return;
+  const BJob &b = jobs[j];
+  const int p = b.p;
+  const long long len = (long long)p * p;
+  const int vb = blockIdx.x - start[j];
+  const T *A1 = (const T *)b.blk[sl.a1];
+  const T *A2 = sl.a2 >= 0 ? (const T *)b.blk[sl.a2] : nullptr;
+  const T *Bm = sl.bm >= 0 ? (const T *)b.blk[sl.bm] : nullptr;
+  T *out = (T *)b.blk[sl.out];
+  const double *C1 = b.pp + (size_t)sl.c1 * len;
+  const double *C2 = sl.c2 >= 0 ? b.pp + (size_t)sl.c2 * len : nullptr;
+  if (narrow) {
+    combine_narrow_body<T>(b.n, p, A1, p, C1, A2, p, C2, sl.alpha, sl.beta, Bm, out, vb,
+                           b.comb_nb);
+  } else {
+    const int ct = (p + kTile - 1) / kTile;
+    if (sizeof(T) == 4)
+      combine_tile_body<T, float>(b.n, p, A1, p, b.cf, A2, p, C2 ? b.cf + len : nullptr,
+                                  sl.alpha, sl.beta, Bm, out, vb / ct, vb % ct);
+    else
+      combine_tile_body<T, double>(b.n, p, A1, p, C1, A2, p, C2, sl.alpha, sl.beta, Bm, out,
+                                   vb / ct, vb % ct);
+  }
+}
+
+template <typename T>
+ks_status batch_combine(Batch &B, int sA1, int smC1, int sA2, int smC2, double alpha, double beta,
+                        int sBm, int sOut) {
+  const CombSlots sl{sA1, smC1, sA2, smC2, sBm, sOut, alpha, beta};
+  const int nt = B.total(BM_COMB_TILED);
+  if (sizeof(T) == 4 && nt > 0) {
+    {
+      ProfScope ps_(B.stream, KP_REDUCE);
+      coef_batch_kernel<<<B.total(BM_COEF), kThreads, 0, B.stream>>>(
+          B.jobs_dev, B.map(BM_COEF), B.J, B.active_dev, smC1, sA2 >= 0 ? smC2 : -1);
+    }
+    KS_CUDA_TRY(cudaGetLastError());
+  }
+  for (int narrow = 1; narrow >= 0; --narrow) {
+    const int m = narrow ? BM_COMB_NARROW : BM_COMB_TILED;
+    const int nb = B.total(m);
+    if (nb == 0) continue;
+    {
+      ProfScope ps_(B.stream, KP_COMBINE);
+      combine_batch_kernel<T><<<nb, 256, 0, B.stream>>>(B.jobs_dev, B.map(m), B.J, B.active_dev,
+                                                        sl, narrow);
+    }
+    KS_CUDA_TRY(cudaGetLastError());
+  }
+  return KS_OK;
+}
+
+// Precision conversion / copy of a block of every active job.
+template <typename A, typename Bt>
+__global__ void convert_batch_kernel(const BJob *__restrict__ jobs, const int *__restrict__ start,
+                                     int J, const unsigned char *__restrict__ active, int sIn,
+                                     int sOut) {
+  const int j = batch_job_of(start, J, blockIdx.x);
+  if (!active[j]) return;
+  const BJob &b = jobs[j];
+  const long long total = b.n * b.p;
+  const A *in = (const A *)b.blk[sIn];
+  Bt *out = (Bt *)b.blk[sOut];
+  const long long base = (long long)(blockIdx.x - start[j]) * blockDim.x * 4 + threadIdx.x;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const long long e = base + (long long)u * blockDim.x;
+    if (e < total) out[e] = (Bt)in[e];
+  }
+}
+
+template <typename Tin, typename Tout>
+ks_status batch_convert(Batch &B, int sIn, int sOut) {
+  {
+    ProfScope ps_(B.stream, KP_OTHER);
+    convert_batch_kernel<Tin, Tout><<<B.total(BM_COPY), kThreads, 0, B.stream>>>(
+        B.jobs_dev, B.map(BM_COPY), B.J, B.active_dev, sIn, sOut);
+  }
+  KS_CUDA_TRY(cudaGetLastError());
+  return KS_OK;
+}
+
+// ||O - I||_F^2 of every active job into its scalar row.
+__global__ void ortho_err_batch_kernel(const BJob *__restrict__ jobs,
+                                       const unsigned char *__restrict__ active, int smO) {
+  const int j = blockIdx.x;
+  if (!active[j]) return;
+  const BJob &b = jobs[j];
+  __shared__ double smem[33];
+  const int p = b.p;
+  const double *O = b.pp + (size_t)smO * p * p;
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    const int i = e / p, k = e % p;
+    const double d = O[e] - (i == k ? 1.0 : 0.0);
+    acc = fma(d, d, acc);
+  }
+  const double s = block_sum(acc, smem);
+  if (threadIdx.x == 0) b.scal[SC_ORTHO] = s;
+}
+
+ks_status batch_ortho_err(Batch &B, int smO) {
+  {
+    ProfScope ps_(B.stream, KP_REDUCE);
+    ortho_err_batch_kernel<<<B.J, kThreads, 0, B.stream>>>(B.jobs_dev, B.active_dev, smO);
+  }
+  KS_CUDA_TRY(cudaGetLastError());
+  return KS_OK;
+}
+
+template ks_status batch_gram<double>(Batch &, int, int, int);
+template ks_status batch_gram<float>(Batch &, int, int, int);
+template ks_status batch_combine<double>(Batch &, int, int, int, int, double, double, int, int);
+template ks_status batch_combine<float>(Batch &, int, int, int, int, double, double, int, int);
+template ks_status batch_convert<double, float>(Batch &, int, int);
+template ks_status batch_convert<float, double>(Batch &, int, int);
+template ks_status batch_convert<double, double>(Batch &, int, int);
+template ks_status batch_convert<float, float>(Batch &, int, int);
 
 template ks_status launch_gram<double>(Problem &, const double *, int, const double *, int,
                                        double *);

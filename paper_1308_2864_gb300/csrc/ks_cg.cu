@@ -32,7 +32,7 @@ struct CgArgs {
   float *t1, *t2;             // sine-transform work vectors
   const float *phi;           // N x N sine basis
   const float *kap, *mu;      // 1-D eigenvalues of K1 and M1
-  double *part;               // 4 * gridDim.x
+  double *part;               // 4 * vnb
   GridBarrier *bar;
   int *status;
   double *iters_out;
@@ -41,6 +41,7 @@ struct CgArgs {
   int warm;
   int precond;
   int fused;                  // fused shared-memory preconditioner (N <= kFusedMaxN)
+  int vb, vnb;                // this block's index among the vnb blocks that solve this system
 };
 
 // (K v)_k for v = a + beta * b (b ignored when UseB is false), Dirichlet.
@@ -123,15 +124,15 @@ __device__ __forceinline__ double sine_pass(const Tin *in, float *out32, double 
 // thread's share of r.z, or a NaN-free 0 and false when a barrier failed.
 __device__ bool apply_precond(const CgArgs &a, long long tid, long long stride, double *rz_l) {
   sine_pass<double, 0>(a.r, a.t1, nullptr, nullptr, 0, a, tid, stride);
-  if (!grid_barrier(a.bar, a.status)) return false;
+  if (!grid_barrier_n(a.bar, a.status, a.vnb)) return false;
   sine_pass<float, 0>(a.t1, a.t2, nullptr, nullptr, 1, a, tid, stride);
-  if (!grid_barrier(a.bar, a.status)) return false;
+  if (!grid_barrier_n(a.bar, a.status, a.vnb)) return false;
   sine_pass<float, 1>(a.t2, a.t1, nullptr, nullptr, 2, a, tid, stride);
-  if (!grid_barrier(a.bar, a.status)) return false;
+  if (!grid_barrier_n(a.bar, a.status, a.vnb)) return false;
   sine_pass<float, 0>(a.t1, a.t2, nullptr, nullptr, 2, a, tid, stride);
-  if (!grid_barrier(a.bar, a.status)) return false;
+  if (!grid_barrier_n(a.bar, a.status, a.vnb)) return false;
   sine_pass<float, 0>(a.t2, a.t1, nullptr, nullptr, 1, a, tid, stride);
-  if (!grid_barrier(a.bar, a.status)) return false;
+  if (!grid_barrier_n(a.bar, a.status, a.vnb)) return false;
   *rz_l = sine_pass<float, 2>(a.t1, nullptr, a.z, a.r, 0, a, tid, stride);
   return true;
 }
@@ -190,7 +191,7 @@ __device__ double fused_plane_pass(const CgArgs &a, const void *in, float *out32
   const long long NN = (long long)N * N;
   float *Pm = sh, *Ph = sh + NN, *W = sh + 2 * NN;
   double rz = 0.0;
-  for (int z = blockIdx.x; z < N; z += gridDim.x) {
+  for (int z = a.vb; z < N; z += a.vnb) {
     __syncthreads();
     for (int e = threadIdx.x; e < NN; e += blockDim.x) {
       Pm[e] = InD ? (float)__ldcg((const double *)in + z * NN + e)
@@ -219,7 +220,7 @@ __device__ void fused_slab_pass(const CgArgs &a, const float *in, float *out, fl
   const int N = a.N;
   const long long NN = (long long)N * N;
   float *Sm = sh, *Ph = sh + NN, *W = sh + 2 * NN;
-  for (int y = blockIdx.x; y < N; y += gridDim.x) {
+  for (int y = a.vb; y < N; y += a.vnb) {
     __syncthreads();
     for (int e = threadIdx.x; e < NN; e += blockDim.x) {
       const int zz = e / N, x = e % N;
@@ -251,19 +252,21 @@ __device__ bool apply_precond_fused(const CgArgs &a, double *rz_l) {
   // Phi into shared memory once per application
   for (int e = threadIdx.x; e < NN; e += blockDim.x) dyn[NN + e] = __ldg(a.phi + e);
   fused_plane_pass<true, false>(a, a.r, a.t1, nullptr, dyn);
-  if (!grid_barrier(a.bar, a.status)) return false;
+  if (!grid_barrier_n(a.bar, a.status, a.vnb)) return false;
   fused_slab_pass(a, a.t1, a.t2, dyn);
-  if (!grid_barrier(a.bar, a.status)) return false;
+  if (!grid_barrier_n(a.bar, a.status, a.vnb)) return false;
   *rz_l = fused_plane_pass<false, true>(a, a.t2, nullptr, a.z, dyn);
   return true;
 }
 
-__global__ void __launch_bounds__(kCgThreads) cg_kernel(CgArgs a) {
+// The whole PCG of one system on the blocks a.vb = 0 .. a.vnb - 1 (which must
+// be co-resident: a cooperative launch).
+__device__ void cg_body(const CgArgs &a) {
   __shared__ double smem[33];
-  const int nb = gridDim.x;
+  const int nb = a.vnb;
   double *partA = a.part, *partB = a.part + nb, *partC = a.part + 2 * nb, *partD = a.part + 3 * nb;
-  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long tid = (long long)a.vb * blockDim.x + threadIdx.x;
+  const long long stride = (long long)a.vnb * blockDim.x;
   const int N = a.N;
   const long long NN = (long long)N * N;
 
@@ -284,9 +287,9 @@ __global__ void __launch_bounds__(kCgThreads) cg_kernel(CgArgs a) {
   {
     const double s1 = block_sum(rr_l, smem);
     const double s2 = block_sum(bb_l, smem);
-    if (threadIdx.x == 0) { partB[blockIdx.x] = s1; partD[blockIdx.x] = s2; }
+    if (threadIdx.x == 0) { partB[a.vb] = s1; partD[a.vb] = s2; }
   }
-  if (!grid_barrier(a.bar, a.status)) return;
+  if (!grid_barrier_n(a.bar, a.status, a.vnb)) return;
   if (!a.warm) {
     for (long long k = tid; k < a.n; k += stride) a.x[k] = 0.0;
   }
@@ -299,8 +302,8 @@ __global__ void __launch_bounds__(kCgThreads) cg_kernel(CgArgs a) {
     double rz_l = 0.0;
     if (a.fused ? !apply_precond_fused(a, &rz_l) : !apply_precond(a, tid, stride, &rz_l)) return;
     const double s = block_sum(rz_l, smem);
-    if (threadIdx.x == 0) partC[blockIdx.x] = s;
-    if (!grid_barrier(a.bar, a.status)) return;
+    if (threadIdx.x == 0) partC[a.vb] = s;
+    if (!grid_barrier_n(a.bar, a.status, a.vnb)) return;
     rho_cg = block_sum_array(partC, nb, smem);
   }
 
@@ -323,9 +326,9 @@ __global__ void __launch_bounds__(kCgThreads) cg_kernel(CgArgs a) {
     }
     {
       const double s = block_sum(pq_l, smem);
-      if (threadIdx.x == 0) partA[blockIdx.x] = s;
+      if (threadIdx.x == 0) partA[a.vb] = s;
     }
-    if (!grid_barrier(a.bar, a.status)) return;
+    if (!grid_barrier_n(a.bar, a.status, a.vnb)) return;
     const double pq = block_sum_array(partA, nb, smem);
     if (!(pq > 0.0) || !isfinite(pq)) { bad = true; break; }
     const double alpha = rho_cg / pq;
@@ -339,9 +342,9 @@ __global__ void __launch_bounds__(kCgThreads) cg_kernel(CgArgs a) {
     }
     {
       const double s = block_sum(rl, smem);
-      if (threadIdx.x == 0) partB[blockIdx.x] = s;
+      if (threadIdx.x == 0) partB[a.vb] = s;
     }
-    if (!grid_barrier(a.bar, a.status)) return;
+    if (!grid_barrier_n(a.bar, a.status, a.vnb)) return;
     const double rr_new = block_sum_array(partB, nb, smem);
     if (!isfinite(rr_new)) { bad = true; break; }
     double rho_new = rr_new;
@@ -350,8 +353,8 @@ __global__ void __launch_bounds__(kCgThreads) cg_kernel(CgArgs a) {
       if (a.fused ? !apply_precond_fused(a, &rz_l) : !apply_precond(a, tid, stride, &rz_l))
         return;
       const double s = block_sum(rz_l, smem);
-      if (threadIdx.x == 0) partC[blockIdx.x] = s;
-      if (!grid_barrier(a.bar, a.status)) return;
+      if (threadIdx.x == 0) partC[a.vb] = s;
+      if (!grid_barrier_n(a.bar, a.status, a.vnb)) return;
       rho_new = block_sum_array(partC, nb, smem);
       if (!isfinite(rho_new)) { bad = true; break; }
     }
@@ -361,11 +364,34 @@ __global__ void __launch_bounds__(kCgThreads) cg_kernel(CgArgs a) {
     double *t = pold; pold = pnew; pnew = t;
     ++it;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (a.vb == 0 && threadIdx.x == 0) {
     *a.iters_out = (double)it;
     if (bad) atomicCAS(a.status, 0, (int)KS_ENAN);
     else if (rr > thr) atomicCAS(a.status, 0, (int)KS_ENOCONV);
   }
+}
+
+__global__ void __launch_bounds__(kCgThreads) cg_kernel(CgArgs a) {
+  a.vb = blockIdx.x;
+  a.vnb = gridDim.x;
+  cg_body(a);
+}
+
+// Many systems in one cooperative launch: block b solves system job_of[b]
+// as its block vb_of[b] of args[job].vnb; systems whose active flag is 0
+// return at once (all their blocks together).
+__global__ void __launch_bounds__(kCgThreads) cg_batch_kernel(const CgArgs *__restrict__ args,
+                                                              const int *__restrict__ job_of,
+                                                              const int *__restrict__ vb_of,
+                                                              const unsigned char *__restrict__ active,
+                                                              const double *__restrict__ tolw) {
+  const int j = job_of[blockIdx.x];
+  if (!active[j]) return;
+  CgArgs a = args[j];
+  a.vb = vb_of[blockIdx.x];
+  a.tol = tolw[2 * j];
+  a.warm = tolw[2 * j + 1] != 0.0 ? 1 : 0;
+  cg_body(a);
 }
 
 // Sine basis Phi_{jk} = sqrt(2/(N+1)) sin(j k pi/(N+1)) (j, k = 1..N) and
@@ -431,6 +457,133 @@ ks_status launch_cg(Problem &P, const double *rho, double *v, double *r, bool wa
     KS_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)cg_kernel, dim3(P.cg_blocks),
                                             dim3(kCgThreads), args, dyn, P.stream));
   }
+  return KS_OK;
+}
+
+// ---------------------------------------------------------------- batched
+__global__ void cg_batch_reset_kernel(const CgArgs *__restrict__ args, int J,
+                                      const unsigned char *__restrict__ active) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < J && active[j]) {
+    args[j].bar->count = 0u;
+    args[j].bar->gen = 0u;
+  }
+}
+
+// Blocks per job for the batched cooperative launch: one per 16384 nodes
+// (at least one, at most one per z-plane), a rule of the job alone, so that a
+// job's sums, and so its result, do not depend on the other jobs.  All blocks
+// of all jobs must be resident together (a job's blocks wait on each other at
+// its own barrier); when the rule asks for more than fit, every job's share
+// is scaled down.
+
+ks_status batch_cg_setup(Batch &B) {
+  const size_t dyn = cg_dynamic_smem(B.maxN <= kFusedMaxN ? B.maxN : 0);
+  KS_CUDA_TRY(cudaFuncSetAttribute(cg_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)cg_dynamic_smem(kFusedMaxN)));
+  int per_sm = 0;
+  KS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_batch_kernel, kCgThreads,
+                                                            dyn));
+  if (per_sm < 1) return set_error(KS_ECUDA, "batched CG kernel does not fit on an SM");
+  const long long cap = (long long)B.sms * per_sm;
+  if ((long long)B.J > cap)
+    return set_error(KS_EINVAL, "batch: %d jobs exceed the %lld co-resident CG blocks", B.J, cap);
+  std::vector<int> nb(B.J);
+  long long used = 0;
+  for (int j = 0; j < B.J; ++j) {
+    const BJob &b = B.jobs_host[j];
+    long long want = (b.n + 16383) / 16384;
+    const long long by_part = (long long)(B.probs[j]->P.partials_len / 4);
+    if (want > by_part) want = by_part;
+    if (want > B.probs[j]->P.N) want = B.probs[j]->P.N;
+    if (want < 1) want = 1;
+    nb[j] = (int)want;
+    used += want;
+  }
+  if (used > cap) {
+    const double scale = (double)(cap - B.J) / (double)(used - B.J > 0 ? used - B.J : 1);
+    used = 0;
+    for (int j = 0; j < B.J; ++j) {
+      nb[j] = 1 + (int)((nb[j] - 1) * scale);
+      used += nb[j];
+    }
+  }
+  std::vector<int> job_of, vb_of;
+  for (int j = 0; j < B.J; ++j)
+    for (int v = 0; v < nb[j]; ++v) { job_of.push_back(j); vb_of.push_back(v); }
+  B.cg_blocks = (int)job_of.size();
+  std::vector<CgArgs> args(B.J);
+  for (int j = 0; j < B.J; ++j) {
+    Problem &P = B.probs[j]->P;
+    const BJob &b = B.jobs_host[j];
+    CgArgs &a = args[j];
+    a.N = P.N;
+    a.n = P.n;
+    a.c = q1_coefficients(P.h);
+    a.bscale = 4.0 * M_PI * P.h * P.h * P.h;
+    a.rho = P.rho;
+    a.x = P.vH;
+    a.r = P.cg_r;
+    a.pa = P.cg_pa;
+    a.pb = P.cg_pb;
+    a.q = P.cg_q;
+    a.z = P.cg_z;
+    a.t1 = P.cg_t1;
+    a.t2 = P.cg_t2;
+    a.phi = P.dst_phi;
+    a.kap = P.dst_kap;
+    a.mu = P.dst_mu;
+    a.part = P.partials;
+    a.bar = P.bar;
+    a.status = b.status;
+    a.iters_out = b.scal + SC_CG_ITERS;
+    a.tol = P.cg_tol;
+    a.maxit = P.cg_maxit;
+    a.warm = 0;
+    a.precond = P.cg_precond;
+    a.fused = P.N <= kFusedMaxN ? 1 : 0;
+    a.vb = 0;
+    a.vnb = nb[j];
+  }
+  void *mem = nullptr;
+  const size_t abytes = ((sizeof(CgArgs) * B.J + 63) / 64) * 64;
+  const size_t tbytes = sizeof(double) * 2 * B.J, mbytes = sizeof(int) * job_of.size();
+  KS_CUDA_TRY(cudaMalloc(&mem, abytes + tbytes + 2 * mbytes));
+  B.cg_args_dev = mem;
+  B.cg_tolw_dev = reinterpret_cast<double *>(static_cast<char *>(mem) + abytes);
+  B.cg_job_of = reinterpret_cast<int *>(static_cast<char *>(mem) + abytes + tbytes);
+  B.cg_vb_of = B.cg_job_of + job_of.size();
+  KS_CUDA_TRY(cudaMemcpyAsync(B.cg_args_dev, args.data(), sizeof(CgArgs) * B.J,
+                              cudaMemcpyHostToDevice, B.stream));
+  KS_CUDA_TRY(cudaMemcpyAsync(B.cg_job_of, job_of.data(), mbytes, cudaMemcpyHostToDevice,
+                              B.stream));
+  KS_CUDA_TRY(cudaMemcpyAsync(B.cg_vb_of, vb_of.data(), mbytes, cudaMemcpyHostToDevice, B.stream));
+  KS_CUDA_TRY(cudaStreamSynchronize(B.stream));
+  B.bytes += abytes + tbytes + 2 * mbytes;
+  return KS_OK;
+}
+
+// Hartree solve of every active job (warm-started where B.warm says so) to
+// relative residual max(tol, the job's cg_tol), in one cooperative launch.
+ks_status batch_cg(Batch &B, double tol) {
+  for (int j = 0; j < B.J; ++j) {
+    const double t = tol > B.probs[j]->P.cg_tol ? tol : B.probs[j]->P.cg_tol;
+    B.cg_tolw_host[2 * j] = t;
+    B.cg_tolw_host[2 * j + 1] = B.warm[j] ? 1.0 : 0.0;
+  }
+  KS_CUDA_TRY(cudaMemcpyAsync(B.cg_tolw_dev, B.cg_tolw_host, sizeof(double) * 2 * B.J,
+                              cudaMemcpyHostToDevice, B.stream));
+  const CgArgs *args = static_cast<const CgArgs *>(B.cg_args_dev);
+  {
+    ProfScope ps_(B.stream, KP_CG, 0.0, 0.0, 2);
+    cg_batch_reset_kernel<<<(B.J + 127) / 128, 128, 0, B.stream>>>(args, B.J, B.active_dev);
+    const size_t dyn = cg_dynamic_smem(B.maxN <= kFusedMaxN ? B.maxN : 0);
+    void *kargs[] = {(void *)&args, (void *)&B.cg_job_of, (void *)&B.cg_vb_of,
+                     (void *)&B.active_dev, (void *)&B.cg_tolw_dev};
+    KS_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)cg_batch_kernel, dim3(B.cg_blocks),
+                                            dim3(kCgThreads), kargs, dyn, B.stream));
+  }
+  KS_CUDA_TRY(cudaGetLastError());
   return KS_OK;
 }
 

@@ -76,6 +76,38 @@ ks_status launch_density(Problem &P, const T *X, double *rho) {
   return KS_OK;
 }
 
+// Batched: one thread per node of every active job.
+template <typename T>
+__global__ void density_batch_kernel(const BJob *__restrict__ jobs, const int *__restrict__ start,
+                                     int J, const unsigned char *__restrict__ active, int sX) {
+  const int j = batch_job_of(start, J, blockIdx.x);
+  if (!active[j]) return;
+  const BJob &b = jobs[j];
+  const long long k = (long long)(blockIdx.x - start[j]) * blockDim.x + threadIdx.x;
+  if (k >= b.n) return;
+  const int p = b.p;
+  const T *row = (const T *)b.blk[sX] + k * p;
+  T acc = 0;
+  for (int i = 0; i < p; ++i) acc = fma(row[i], row[i], acc);
+  b.rho[k] = b.occ * (double)acc;
+}
+
+template <typename T>
+ks_status batch_density(Batch &B, int sX) {
+  const int nb = B.total(BM_DENSITY);
+  if (nb == 0) return KS_OK;
+  {
+    ProfScope ps_(B.stream, KP_DENSITY);
+    density_batch_kernel<T><<<nb, kThreads, 0, B.stream>>>(B.jobs_dev, B.map(BM_DENSITY), B.J,
+                                                           B.active_dev, sX);
+  }
+  KS_CUDA_TRY(cudaGetLastError());
+  return KS_OK;
+}
+
+template ks_status batch_density<double>(Batch &, int);
+template ks_status batch_density<float>(Batch &, int);
+
 template ks_status launch_density<double>(Problem &, const double *, double *);
 template ks_status launch_density<float>(Problem &, const float *, double *);
 

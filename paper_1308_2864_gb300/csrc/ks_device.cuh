@@ -74,15 +74,16 @@ __device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int *p) {
   return v;
 }
 
-// Grid-wide barrier for a cooperative launch (all blocks co-resident).
+// Barrier of the nb blocks that share `bar` inside a cooperative launch (all
+// blocks of the launch co-resident; nb = the whole grid, or the blocks of one
+// system in a batched launch).
 // Every wait is bounded: a block that spins longer than kSpinLimit records
 // KS_ETIMEOUT in *status and leaves the barrier.  Returns false when the
 // status word holds an error, so that callers can return together.
-__device__ __forceinline__ bool grid_barrier(GridBarrier *bar, int *status) {
+__device__ __forceinline__ bool grid_barrier_n(GridBarrier *bar, int *status, unsigned int nb) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
     const unsigned int gen = ld_acquire_gpu(&bar->gen);
     __threadfence();
     const unsigned int arrived = atomicAdd(&bar->count, 1u);
@@ -107,6 +108,11 @@ __device__ __forceinline__ bool grid_barrier(GridBarrier *bar, int *status) {
   }
   __syncthreads();
   return s_ok != 0;
+}
+
+// The same over the whole grid of the launch.
+__device__ __forceinline__ bool grid_barrier(GridBarrier *bar, int *status) {
+  return grid_barrier_n(bar, status, gridDim.x * gridDim.y * gridDim.z);
 }
 
 // 27-point Q1 stencil coefficient classes (see the stiffness/mass

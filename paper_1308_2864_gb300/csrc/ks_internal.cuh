@@ -230,6 +230,112 @@ ks_status launch_combine_tc(Problem &P, const float *A1, int k1, const double *C
 // Transpose a p x p matrix into out.
 ks_status launch_transpose(Problem &P, const double *A, double *out);
 
+// Index of the n x p blocks in Problem::blk.
+enum Block { B_X0 = 0, B_X1, B_X2, B_MX0, B_MX1, B_MX2, B_EX0, B_EX1, B_G, B_D0, B_D1, B_MD0, B_MD1 };
+
+// Offsets (in units of p*p) of the small matrices in the pp pool; the first
+// 6 p^2 are scratch of the factor kernels.
+enum Small { S_WORK = 0, S_S = 6, S_DMD, S_O, S_A, S_B, S_C1, S_C2, S_T, S_COUNT };
+
+// ---------------------------------------------------------------- batch
+// A job table of independent systems advanced together (ks_batch_*): every
+// launch of a step covers all jobs whose active flag is set.  Each job keeps
+// its buffers in its own Problem; BJob is the device-side view of them plus
+// the job's launch geometry.
+struct BJob {
+  int N, p;
+  long long n;
+  double h, occ, h3, cg_tol;
+  int xc, cg_maxit, cg_precond;
+  void *blk[Problem::kNBlocks];
+  double *vext, *rho, *vH, *veff, *cg_r;
+  double *pp;                      // small matrices, same layout as Problem::pp
+  float *cf;                       // FP32 copies of update coefficients (2 p^2)
+  double *partials;
+  unsigned int *red_counter;
+  double *thomas_w;
+  double *scal;                    // this job's row of the batch scalar table (SC_COUNT)
+  int *status;                     // this job's entry of the batch status table
+  double qc[8];                    // Q1 stencil classes k0, kf, ke, kc, m0, mf, me, mc
+  float qcf[9];                    // k0, ke, kc, m0, mf, me, mc, occ, 2 occ h^3 in FP32
+  int st_zseg, st_tiles_x, st_tiles_y, st_chunks, st_nb;   // stencil geometry (job's PC class)
+  int pot_nb;                      // potential blocks (grid-stride)
+  int gram_chunks;                 // row chunks of the Grams
+  long long gram_rows_per;
+  int comb_nb;                     // blocks of the narrow update
+};
+
+// Block maps of the batched launches: prefix sums over jobs of the blocks
+// each job takes in a launch family.
+enum BMap {
+  BM_DENSITY = 0, BM_POTENTIAL, BM_ST4, BM_ST8, BM_ST16, BM_ST32, BM_THOMAS, BM_GRAM_SMALL,
+  BM_GRAM_TILED, BM_GRAM_REDUCE, BM_COMB_NARROW, BM_COMB_TILED, BM_COEF, BM_COPY, BM_COUNT
+};
+
+struct Batch {
+  int J = 0, sms = 0, maxN = 0, maxp = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<ks_problem *> probs;
+  std::vector<BJob> jobs_host;
+  BJob *jobs_dev = nullptr;
+  int *maps_dev = nullptr;         // BM_COUNT x (J + 1)
+  std::vector<int> maps_host;
+  unsigned char *active_dev = nullptr, *active_host = nullptr;   // launch mask (pinned mirror)
+  double *tau_dev = nullptr, *tau_host = nullptr;                // per-job step (pinned mirror)
+  double *scal_dev = nullptr, *scal_host = nullptr;              // J x SC_COUNT
+  int *status_dev = nullptr, *status_host = nullptr;             // J
+  void *cg_args_dev = nullptr;     // J CgArgs
+  double *cg_tolw_dev = nullptr, *cg_tolw_host = nullptr;   // per job (tolerance, warm)
+  int *cg_job_of = nullptr, *cg_vb_of = nullptr;
+  int cg_blocks = 0;
+  std::vector<unsigned char> warm; // per job: a previous Hartree potential exists
+  char *ring_host = nullptr;       // pinned staging ring of the small uploads
+  size_t ring_bytes = 0, ring_used = 0;
+  size_t bytes = 0;
+  const int *map(int m) const { return maps_dev + (size_t)m * (J + 1); }
+  int total(int m) const { return maps_host[(size_t)m * (J + 1) + J]; }
+};
+
+// Device: the job whose block range [start[j], start[j+1]) holds block b.
+__device__ __forceinline__ int batch_job_of(const int *start, int J, int b) {
+  int lo = 0, hi = J;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(start + mid) <= b) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Batched launches (slots index BJob::blk, -1 = none; sm* are offsets in
+// units of p^2 into BJob::pp).  ks_density.cu, ks_cg.cu, ks_xc.cu,
+// ks_stencil.cu, ks_minv.cu, ks_blas.cu, ks_small.cu.
+template <typename T>
+ks_status batch_density(Batch &B, int sX);
+ks_status batch_cg(Batch &B, double tol);
+ks_status batch_cg_setup(Batch &B);
+ks_status batch_potential(Batch &B, bool fp32_xc);
+template <typename T>
+ks_status batch_hamiltonian(Batch &B, int sX, int sEX, int sMX);
+template <typename T>
+ks_status batch_mass(Batch &B, int sX, int sMX);
+template <typename T>
+ks_status batch_mass_dots(Batch &B, int sD, int sMD, int sX, int sMX, int sXp, int sMXp, int sDp,
+                          int sMDp);
+ks_status batch_stencil_geometry(Batch &B);
+template <typename T>
+ks_status batch_mass_inverse(Batch &B, int sE, int sG);
+template <typename T>
+ks_status batch_gram(Batch &B, int sA, int sB, int smOut);
+template <typename T>
+ks_status batch_combine(Batch &B, int sA1, int smC1, int sA2, int smC2, double alpha, double beta,
+                        int sBm, int sOut);
+template <typename Tin, typename Tout>
+ks_status batch_convert(Batch &B, int sIn, int sOut);
+ks_status batch_ortho_err(Batch &B, int smO);
+ks_status batch_qr_factor(Batch &B, int smDMD, int smO, bool with_tau, int smC1, int smC2);
+
 }  // namespace ks
 
 struct ks_problem {

@@ -18,17 +18,11 @@ namespace ks {
 // and the compiler cannot reorder loads across the stores by itself).
 constexpr int kAhead = 8;
 
+// One (line, orbital) pair t of a sweep; w: the pivots in shared memory.
 template <typename T>
-__global__ void __launch_bounds__(256) thomas_kernel(int N, int p, int axis, double scale_d,
-                                                     const double *__restrict__ w_d, const T *in,
-                                                     T *out) {
-  extern __shared__ unsigned char thomas_smem[];
-  T *w = reinterpret_cast<T *>(thomas_smem);
-  for (int j = threadIdx.x; j < N; j += blockDim.x) w[j] = (T)w_d[j];
-  __syncthreads();
-  const T scale = (T)scale_d;
+__device__ __forceinline__ void thomas_line(long long t, int N, int p, int axis, T scale,
+                                            const T *w, const T *in, T *out) {
   const long long lines = (long long)N * N;
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= lines * p) return;
   const int i = (int)(t % p);
   const long long line = t / p;
@@ -76,6 +70,61 @@ __global__ void __launch_bounds__(256) thomas_kernel(int N, int p, int axis, dou
       }
   }
 }
+
+template <typename T>
+__global__ void __launch_bounds__(256) thomas_kernel(int N, int p, int axis, double scale_d,
+                                                     const double *__restrict__ w_d, const T *in,
+                                                     T *out) {
+  extern __shared__ unsigned char thomas_smem[];
+  T *w = reinterpret_cast<T *>(thomas_smem);
+  for (int j = threadIdx.x; j < N; j += blockDim.x) w[j] = (T)w_d[j];
+  __syncthreads();
+  thomas_line<T>((long long)blockIdx.x * blockDim.x + threadIdx.x, N, p, axis, (T)scale_d, w, in,
+                 out);
+}
+
+// Batched: the blocks of job j cover its N^2 p (line, orbital) pairs.
+template <typename T>
+__global__ void __launch_bounds__(256) thomas_batch_kernel(const BJob *__restrict__ jobs,
+                                                           const int *__restrict__ start, int J,
+                                                           const unsigned char *__restrict__ active,
+                                                           int axis, int sIn, int sOut) {
+  const int j = batch_job_of(start, J, blockIdx.x);
+  if (!active[j]) return;
+  const BJob &b = jobs[j];
+  extern __shared__ unsigned char thomas_smem[];
+  T *w = reinterpret_cast<T *>(thomas_smem);
+  const int N = b.N;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) w[i] = (T)b.thomas_w[i];
+  __syncthreads();
+  double scale = 1.0;
+  if (axis == 0) {
+    const double s = 6.0 / b.h;
+    scale = s * s * s;
+  }
+  const T *in = (const T *)b.blk[axis == 0 ? sIn : sOut];
+  thomas_line<T>((long long)(blockIdx.x - start[j]) * blockDim.x + threadIdx.x, N, b.p, axis,
+                 (T)scale, w, in, (T *)b.blk[sOut]);
+}
+
+template <typename T>
+ks_status batch_mass_inverse(Batch &B, int sE, int sG) {
+  const int nb = B.total(BM_THOMAS);
+  if (nb == 0) return KS_OK;
+  const size_t smem = (size_t)B.maxN * sizeof(T);
+  for (int axis = 0; axis < 3; ++axis) {
+    {
+      ProfScope ps_(B.stream, KP_MASS_INV);
+      thomas_batch_kernel<T><<<nb, kThreads, smem, B.stream>>>(B.jobs_dev, B.map(BM_THOMAS), B.J,
+                                                               B.active_dev, axis, sE, sG);
+    }
+    KS_CUDA_TRY(cudaGetLastError());
+  }
+  return KS_OK;
+}
+
+template ks_status batch_mass_inverse<double>(Batch &, int, int);
+template ks_status batch_mass_inverse<float>(Batch &, int, int);
 
 template <typename T>
 ks_status launch_mass_inverse(Problem &P, const T *E, T *G) {

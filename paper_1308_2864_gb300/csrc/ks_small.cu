@@ -136,8 +136,9 @@ __device__ __forceinline__ bool chol_pivot(double w, int j, double *W, int p, do
 // the next pivot, leaving two barriers per column.  On GB300 one SM retires
 // two FP64 lanes per clock, so dense warps and no divisions matter more
 // than anything else here.
-__global__ void __launch_bounds__(kSmallThreads) qr_factor_smem_kernel(
-    int p, const double *DMD, const double *O, double tau, double *C1, double *C2, int *status) {
+__device__ __forceinline__ void qr_factor_smem_body(int p, const double *DMD, const double *O,
+                                                    double tau, double *C1, double *C2,
+                                                    int *status) {
   extern __shared__ double W[];          // p*p: W -> L; p*p: R -> L^{-1} (row-major); p reciprocals
   double *V = W + p * p;
   double *rdiag = V + p * p;
@@ -186,12 +187,45 @@ __global__ void __launch_bounds__(kSmallThreads) qr_factor_smem_kernel(
   }
 }
 
+__global__ void __launch_bounds__(kSmallThreads) qr_factor_smem_kernel(
+    int p, const double *DMD, const double *O, double tau, double *C1, double *C2, int *status) {
+  qr_factor_smem_body(p, DMD, O, tau, C1, C2, status);
+}
+
+// Batched: block j factors job j (p <= kSmemMaxP): R = I + tau_j^2 DMD
+// (with_tau) or R = O, written to C1 (and C2 = -tau_j C1 when smC2 >= 0).
+__global__ void __launch_bounds__(kSmallThreads) qr_factor_batch_kernel(
+    const BJob *__restrict__ jobs, const unsigned char *__restrict__ active,
+    const double *__restrict__ tau, int smDMD, int smO, int with_tau, int smC1, int smC2) {
+  const int j = blockIdx.x;
+  if (!active[j]) return;
+  const BJob &b = jobs[j];
+  const size_t len = (size_t)b.p * b.p;
+  qr_factor_smem_body(b.p, with_tau ? b.pp + smDMD * len : nullptr,
+                      smO >= 0 ? b.pp + smO * len : nullptr, with_tau ? tau[j] : 0.0,
+                      b.pp + smC1 * len, smC2 >= 0 ? b.pp + smC2 * len : nullptr, b.status);
+}
+
+ks_status batch_qr_factor(Batch &B, int smDMD, int smO, bool with_tau, int smC1, int smC2) {
+  if (B.maxp > kSmemMaxP) return set_error(KS_EINVAL, "batch: p above %d", kSmemMaxP);
+  const size_t smem = ((size_t)2 * B.maxp * B.maxp + B.maxp) * sizeof(double);
+  {
+    ProfScope ps_(B.stream, KP_SMALL);
+    qr_factor_batch_kernel<<<B.J, kSmallThreads, smem, B.stream>>>(
+        B.jobs_dev, B.active_dev, B.tau_dev, smDMD, smO, with_tau ? 1 : 0, smC1, smC2);
+  }
+  KS_CUDA_TRY(cudaGetLastError());
+  return KS_OK;
+}
+
 // Opt the shared-memory factor kernel into its dynamic shared memory (on the
 // current device; called when a problem is created).
 ks_status configure_small_kernels() {
-  KS_CUDA_TRY(cudaFuncSetAttribute(
-      qr_factor_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-      (int)(((size_t)2 * kSmemMaxP * kSmemMaxP + kSmemMaxP) * sizeof(double))));
+  const int smem = (int)(((size_t)2 * kSmemMaxP * kSmemMaxP + kSmemMaxP) * sizeof(double));
+  KS_CUDA_TRY(cudaFuncSetAttribute(qr_factor_smem_kernel,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  KS_CUDA_TRY(cudaFuncSetAttribute(qr_factor_batch_kernel,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   return KS_OK;
 }
 

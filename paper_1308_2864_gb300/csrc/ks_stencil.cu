@@ -84,14 +84,17 @@ struct StCoefT {
   }
 };
 
+// Plain-load form of one block (vb = the block's index in the system's
+// launch geometry); the single-system kernel and the batched kernel of a
+// job table both run it.
 template <typename T, int PC, int Kind>
-__global__ void __launch_bounds__(kStThreads) stencil_kernel(StArgs a) {
+__device__ __forceinline__ void stencil_plain_body(const StArgs &a, int vb) {
   using Tl = StTile<PC>;
   __shared__ T tile[Tl::HY * Tl::HX * PC];
   __shared__ double smem[33];
   const int N = a.N, p = a.p;
   // block -> (tile x, tile y, orbital chunk, z segment)
-  int b = blockIdx.x;
+  int b = vb;
   const int txi = b % a.tiles_x; b /= a.tiles_x;
   const int tyi = b % a.tiles_y; b /= a.tiles_y;
   const int oc = b % a.chunks; b /= a.chunks;
@@ -141,9 +144,10 @@ __global__ void __launch_bounds__(kStThreads) stencil_kernel(StArgs a) {
   plane(z0 - 1, c_old, f_old, e_old);
   plane(z0, c_mid, f_mid, e_mid);
 
-  const T k0 = (T)a.c.k0, ke = (T)a.c.ke, kc = (T)a.c.kc;
-  const T m0 = (T)a.c.m0, mf = (T)a.c.mf, me = (T)a.c.me, mc = (T)a.c.mc;
-  const T occ = (T)a.occ, vscale = (T)(2.0 * a.occ * a.h3);
+  const StCoefT<T> cf(a);
+  const T k0 = cf.k0, ke = cf.ke, kc = cf.kc;
+  const T m0 = cf.m0, mf = cf.mf, me = cf.me, mc = cf.mc;
+  const T occ = cf.occ, vscale = cf.vscale;
   T acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
 
   for (int z = z0; z < z1; ++z) {
@@ -185,19 +189,24 @@ __global__ void __launch_bounds__(kStThreads) stencil_kernel(StArgs a) {
   }
   if (Kind == SK_MASS) return;
   const double s0 = block_sum((double)acc0, smem);
-  if (threadIdx.x == 0) a.part[blockIdx.x] = s0;
+  if (threadIdx.x == 0) a.part[vb] = s0;
   if (Kind == SK_MASS_BB) {
     const double s1 = block_sum((double)acc1, smem);
     const double s2 = block_sum((double)acc2, smem);
     const double s3 = block_sum((double)acc3, smem);
     if (threadIdx.x == 0) {
-      a.part[a.nb + blockIdx.x] = s1;
-      a.part[2 * a.nb + blockIdx.x] = s2;
-      a.part[3 * a.nb + blockIdx.x] = s3;
+      a.part[a.nb + vb] = s1;
+      a.part[2 * a.nb + vb] = s2;
+      a.part[3 * a.nb + vb] = s3;
     }
   }
   grid_reduce_tail(a.part, a.nb, Kind == SK_MASS_BB ? 4 : 1, a.red_out, a.red_scale, a.counter,
                    smem);
+}
+
+template <typename T, int PC, int Kind>
+__global__ void __launch_bounds__(kStThreads) stencil_kernel(StArgs a) {
+  stencil_plain_body<T, PC, Kind>(a, blockIdx.x);
 }
 
 constexpr int kStStages = 3;
@@ -524,6 +533,121 @@ ks_status launch_mass_dots(Problem &P, const T *D, T *MD, const T *X, const T *M
   }
   return stencil_launch<T, SK_MASS_DOT>(P, a, 1, 23.0 * total, 2.0 * total * sizeof(T));
 }
+
+// ---------------------------------------------------------------- batched
+// Slots of one batched stencil launch (BJob::blk indices, -1 = none).
+struct StSlots {
+  int a, o1, o2, x, mx, xp, mxp, dp, mdp;
+};
+
+template <typename T, int PC, int Kind>
+__global__ void __launch_bounds__(kStThreads) stencil_batch_kernel(
+    const BJob *__restrict__ jobs, const int *__restrict__ start, int J,
+    const unsigned char *__restrict__ active, StSlots sl) {
+  const int j = batch_job_of(start, J, blockIdx.x);
+  if (!active[j]) return;
+  const BJob &b = jobs[j];
+  StArgs a;
+  a.N = b.N;
+  a.p = b.p;
+  a.zseg = b.st_zseg;
+  a.tiles_x = b.st_tiles_x;
+  a.tiles_y = b.st_tiles_y;
+  a.chunks = b.st_chunks;
+  a.c.k0 = b.qc[0]; a.c.kf = b.qc[1]; a.c.ke = b.qc[2]; a.c.kc = b.qc[3];
+  a.c.m0 = b.qc[4]; a.c.mf = b.qc[5]; a.c.me = b.qc[6]; a.c.mc = b.qc[7];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) a.cf[i] = b.qcf[i];
+  a.occ = b.occ;
+  a.h3 = b.h3;
+  a.A = b.blk[sl.a];
+  a.out1 = b.blk[sl.o1];
+  a.out2 = sl.o2 >= 0 ? b.blk[sl.o2] : nullptr;
+  a.veff = b.veff;
+  if (Kind == SK_MASS_BB) {
+    a.X = b.blk[sl.x];
+    a.MX = b.blk[sl.mx];
+    a.Xp = b.blk[sl.xp];
+    a.MXp = b.blk[sl.mxp];
+    a.Dp = b.blk[sl.dp];
+    a.MDp = b.blk[sl.mdp];
+  }
+  a.part = b.partials;
+  a.nb = b.st_nb;
+  a.red_out = b.scal + (Kind == SK_HAM ? SC_EKIN : SC_DNORM2);
+  a.red_scale = Kind == SK_HAM ? 0.5 * b.occ : 1.0;
+  a.counter = b.red_counter;
+  a.status = b.status;
+  stencil_plain_body<T, PC, Kind>(a, blockIdx.x - start[j]);
+}
+
+template <typename T, int Kind>
+static ks_status stencil_batch_launch(Batch &B, const StSlots &sl) {
+  const int maps[4] = {BM_ST4, BM_ST8, BM_ST16, BM_ST32};
+  const int cls = Kind == SK_HAM ? KP_HAMILTONIAN : KP_MASS;
+  for (int c = 0; c < 4; ++c) {
+    const int nb = B.total(maps[c]);
+    if (nb == 0) continue;
+    {
+      ProfScope ps_(B.stream, cls);
+      const int *st = B.map(maps[c]);
+      if (c == 0) stencil_batch_kernel<T, 4, Kind><<<nb, kStThreads, 0, B.stream>>>(B.jobs_dev, st, B.J, B.active_dev, sl);
+      else if (c == 1) stencil_batch_kernel<T, 8, Kind><<<nb, kStThreads, 0, B.stream>>>(B.jobs_dev, st, B.J, B.active_dev, sl);
+      else if (c == 2) stencil_batch_kernel<T, 16, Kind><<<nb, kStThreads, 0, B.stream>>>(B.jobs_dev, st, B.J, B.active_dev, sl);
+      else stencil_batch_kernel<T, 32, Kind><<<nb, kStThreads, 0, B.stream>>>(B.jobs_dev, st, B.J, B.active_dev, sl);
+    }
+    KS_CUDA_TRY(cudaGetLastError());
+  }
+  return KS_OK;
+}
+
+template <typename T>
+ks_status batch_hamiltonian(Batch &B, int sX, int sEX, int sMX) {
+  const StSlots sl{sX, sEX, sMX, -1, -1, -1, -1, -1, -1};
+  return stencil_batch_launch<T, SK_HAM>(B, sl);
+}
+
+template <typename T>
+ks_status batch_mass(Batch &B, int sX, int sMX) {
+  const StSlots sl{sX, sMX, -1, -1, -1, -1, -1, -1, -1};
+  return stencil_batch_launch<T, SK_MASS>(B, sl);
+}
+
+template <typename T>
+ks_status batch_mass_dots(Batch &B, int sD, int sMD, int sX, int sMX, int sXp, int sMXp, int sDp,
+                          int sMDp) {
+  const StSlots sl{sD, sMD, -1, sX, sMX, sXp, sMXp, sDp, sMDp};
+  if (sXp >= 0) return stencil_batch_launch<T, SK_MASS_BB>(B, sl);
+  return stencil_batch_launch<T, SK_MASS_DOT>(B, sl);
+}
+
+// Per job: PC class of its p and the block geometry of that class (room for
+// four reduction channels in its partials).
+ks_status batch_stencil_geometry(Batch &B) {
+  for (int j = 0; j < B.J; ++j) {
+    Problem &P = B.probs[j]->P;
+    BJob &b = B.jobs_host[j];
+    StArgs a{};
+    if (P.p >= 32) KS_TRY(stencil_geometry<32>(P, 4, a));
+    else if (P.p >= 16) KS_TRY(stencil_geometry<16>(P, 4, a));
+    else if (P.p >= 8) KS_TRY(stencil_geometry<8>(P, 4, a));
+    else KS_TRY(stencil_geometry<4>(P, 4, a));
+    b.st_zseg = a.zseg;
+    b.st_tiles_x = a.tiles_x;
+    b.st_tiles_y = a.tiles_y;
+    b.st_chunks = a.chunks;
+    b.st_nb = a.nb;
+  }
+  return KS_OK;
+}
+
+#define KS_BINST(T)                                                                        \
+  template ks_status batch_hamiltonian<T>(Batch &, int, int, int);                         \
+  template ks_status batch_mass<T>(Batch &, int, int);                                     \
+  template ks_status batch_mass_dots<T>(Batch &, int, int, int, int, int, int, int, int);
+KS_BINST(double)
+KS_BINST(float)
+#undef KS_BINST
 
 #define KS_INST(T)                                                                        \
   template ks_status launch_hamiltonian<T>(Problem &, const T *, const double *, T *, T *, \

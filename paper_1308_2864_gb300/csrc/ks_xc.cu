@@ -79,18 +79,23 @@ __device__ __forceinline__ void lda_point(double rho_d, int xc, R &eps, R &v) {
   }
 }
 
-// Channels of the block partials: 0 = E_ext, 1 = E_H, 2 = E_xc.
+// Channels of the block partials: 0 = E_ext, 1 = E_H, 2 = E_xc.  Block vb
+// of vnb (grid-stride over the n nodes); the last block to finish sums the
+// partials in block order.
 template <typename R>
-__global__ void potential_kernel(long long n, double h3, int xc, int with_h,
-                                 const double *__restrict__ rho, const double *__restrict__ vext,
-                                 const double *__restrict__ vH, const double *__restrict__ r,
-                                 double *__restrict__ veff, double *__restrict__ part,
-                                 double *__restrict__ out, unsigned int *counter) {
+__device__ __forceinline__ void potential_body(long long n, double h3, int xc, int with_h,
+                                               const double *__restrict__ rho,
+                                               const double *__restrict__ vext,
+                                               const double *__restrict__ vH,
+                                               const double *__restrict__ r,
+                                               double *__restrict__ veff, double *__restrict__ part,
+                                               double *__restrict__ out, unsigned int *counter,
+                                               int vb, int vnb) {
   __shared__ double smem[33];
   const double inv8pi = 1.0 / (8.0 * M_PI);
   double e_ext = 0.0, e_h = 0.0, e_xc = 0.0;
-  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
-       k += (long long)gridDim.x * blockDim.x) {
+  for (long long k = (long long)vb * blockDim.x + threadIdx.x; k < n;
+       k += (long long)vnb * blockDim.x) {
     const double rk = rho[k], ve = vext[k];
     R eps_r, vxc_r;
     lda_point<R>(rk, xc, eps_r, vxc_r);
@@ -105,16 +110,52 @@ __global__ void potential_kernel(long long n, double h3, int xc, int with_h,
     }
     veff[k] = v;
   }
-  const int nb = gridDim.x;
   const double s0 = block_sum(e_ext, smem);
   const double s1 = block_sum(e_h, smem);
   const double s2 = block_sum(e_xc, smem);
   if (threadIdx.x == 0) {
-    part[blockIdx.x] = s0;
-    part[nb + blockIdx.x] = s1;
-    part[2 * nb + blockIdx.x] = s2;
+    part[vb] = s0;
+    part[vnb + vb] = s1;
+    part[2 * vnb + vb] = s2;
   }
-  grid_reduce_tail(part, nb, 3, out, 1.0, counter, smem);
+  grid_reduce_tail(part, vnb, 3, out, 1.0, counter, smem);
+}
+
+template <typename R>
+__global__ void potential_kernel(long long n, double h3, int xc, int with_h,
+                                 const double *__restrict__ rho, const double *__restrict__ vext,
+                                 const double *__restrict__ vH, const double *__restrict__ r,
+                                 double *__restrict__ veff, double *__restrict__ part,
+                                 double *__restrict__ out, unsigned int *counter) {
+  potential_body<R>(n, h3, xc, with_h, rho, vext, vH, r, veff, part, out, counter, blockIdx.x,
+                    gridDim.x);
+}
+
+// Batched: job j takes pot_nb blocks.
+template <typename R>
+__global__ void potential_batch_kernel(const BJob *__restrict__ jobs, const int *__restrict__ start,
+                                       int J, const unsigned char *__restrict__ active) {
+  const int j = batch_job_of(start, J, blockIdx.x);
+  if (!active[j]) return;
+  const BJob &b = jobs[j];
+  potential_body<R>(b.n, b.h3, b.xc, 1, b.rho, b.vext, b.vH, b.cg_r, b.veff, b.partials,
+                    b.scal + SC_EEXT, b.red_counter, blockIdx.x - start[j], b.pot_nb);
+}
+
+ks_status batch_potential(Batch &B, bool fp32_xc) {
+  const int nb = B.total(BM_POTENTIAL);
+  if (nb == 0) return KS_OK;
+  {
+    ProfScope ps_(B.stream, KP_POTENTIAL);
+    if (fp32_xc)
+      potential_batch_kernel<float><<<nb, kThreads, 0, B.stream>>>(B.jobs_dev, B.map(BM_POTENTIAL),
+                                                                   B.J, B.active_dev);
+    else
+      potential_batch_kernel<double><<<nb, kThreads, 0, B.stream>>>(
+          B.jobs_dev, B.map(BM_POTENTIAL), B.J, B.active_dev);
+  }
+  KS_CUDA_TRY(cudaGetLastError());
+  return KS_OK;
 }
 
 // out[c] = scale * sum_{b < nb} part[c * nb + b], one block per channel, in
