@@ -384,6 +384,7 @@ ks_status build_maps(Batch &B) {
     b.gram_rows_per = rows;
     const long long tiles = ((p + kTile - 1) / kTile) * ((p + kTile - 1) / kTile);
     if (p <= 8) put(BM_GRAM_SMALL, j, chunks);
+    else if (p <= 32) put(BM_GRAM_MID, j, chunks);
     else put(BM_GRAM_TILED, j, tiles * chunks);
     put(BM_GRAM_REDUCE, j, (8 * p * p + kThreads - 1) / kThreads);
     if (p <= 32) {

@@ -25,6 +25,7 @@ static bool use_tensor_cores(const Problem &P, int a, int b) {
 
 static int gram_chunks(const Problem &P, int pa, int qb) {
   const int tiles = ((pa + kTile - 1) / kTile) * ((qb + kTile - 1) / kTile);
+  // (the small and mid kernels run one block per chunk: tiles = 1 there too)
   int chunks = (4 * P.sms + tiles - 1) / tiles;
   // at least 256 rows per chunk, so small problems do not pay for many
   // partial tiles
@@ -177,6 +178,63 @@ __device__ __forceinline__ void gram_small_body(long long n, int pa, int qb, lon
   }
 }
 
+// Mid-size Grams (kSmallPQ < pa, qb <= kMidPQ): the block keeps the whole
+// pa x qb result of its row chunk, one thread per output (up to four per
+// thread), staging kMidRows rows of A and B in shared memory at a time.
+// Threads map onto the pa qb outputs with no padding, so no FMA is spent on
+// entries outside the Gram (the 64-wide tile would spend (64/p)^2 times the
+// work at p = 16).
+constexpr int kMidPQ = 32, kMidRows = 32;
+
+template <typename T>
+__device__ __forceinline__ void gram_mid_body(long long n, int pa, int qb, long long rows_per,
+                                              const T *__restrict__ A, const T *__restrict__ B,
+                                              double *__restrict__ part, int chunk) {
+  __shared__ T As[kMidRows * kMidPQ];
+  __shared__ T Bs[kMidRows * kMidPQ];
+  const long long r0 = chunk * rows_per;
+  long long r1 = r0 + rows_per;
+  if (r1 > n) r1 = n;
+  const int outs = pa * qb;
+  int oa[4], ob[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int e = threadIdx.x + u * blockDim.x;
+    oa[u] = e < outs ? e / qb : 0;
+    ob[u] = e < outs ? e % qb : 0;
+  }
+  T acc[4] = {0, 0, 0, 0};
+  for (long long r = r0; r < r1; r += kMidRows) {
+    const int rows = (int)min((long long)kMidRows, r1 - r);
+    __syncthreads();
+    for (int t = threadIdx.x; t < rows * pa; t += blockDim.x) As[t] = A[r * pa + t];
+    for (int t = threadIdx.x; t < rows * qb; t += blockDim.x) Bs[t] = B[r * qb + t];
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (threadIdx.x + u * blockDim.x >= outs) break;
+      T a = acc[u];
+      for (int k = 0; k < rows; ++k) a = fma(As[k * pa + oa[u]], Bs[k * qb + ob[u]], a);
+      acc[u] = a;
+    }
+  }
+  double *dst = part + (long long)chunk * outs;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int e = threadIdx.x + u * blockDim.x;
+    if (e < outs) dst[e] = (double)acc[u];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) gram_mid_kernel(long long n, int pa, int qb,
+                                                       long long rows_per,
+                                                       const T *__restrict__ A,
+                                                       const T *__restrict__ B,
+                                                       double *__restrict__ part) {
+  gram_mid_body<T>(n, pa, qb, rows_per, A, B, part, blockIdx.x);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) gram_small_kernel(long long n, int pa, int qb,
                                                          long long rows_per,
@@ -214,6 +272,8 @@ ks_status launch_gram(Problem &P, const T *A, int pa, const T *B, int qb, double
     ProfScope ps_(P.stream, KP_GRAM, 2.0 * P.n * pa * qb, (double)P.n * (pa + qb) * sizeof(T));
     if (pa <= kSmallPQ && qb <= kSmallPQ)
       gram_small_kernel<T><<<chunks, 256, 0, P.stream>>>(P.n, pa, qb, rows_per, A, B, P.partials);
+    else if (pa <= kMidPQ && qb <= kMidPQ)
+      gram_mid_kernel<T><<<chunks, 256, 0, P.stream>>>(P.n, pa, qb, rows_per, A, B, P.partials);
     else
       gram_kernel<T><<<dim3(tiles, chunks), 256, 0, P.stream>>>(P.n, pa, qb, rows_per, A, B,
                                                                 P.partials);
@@ -416,8 +476,10 @@ __global__ void __launch_bounds__(256) gram_batch_kernel(const BJob *__restrict_
   const BJob &b = jobs[j];
   const int vb = blockIdx.x - start[j];
   const T *A = (const T *)b.blk[sA], *Bp = (const T *)b.blk[sB];
-  if (small) {
+  if (small == 1) {
     gram_small_body<T>(b.n, b.p, b.p, b.gram_rows_per, A, Bp, b.partials, vb);
+  } else if (small == 2) {
+    gram_mid_body<T>(b.n, b.p, b.p, b.gram_rows_per, A, Bp, b.partials, vb);
   } else {
     const int tiles = ((b.p + kTile - 1) / kTile) * ((b.p + kTile - 1) / kTile);
     gram_tile_body<T>(b.n, b.p, b.p, b.gram_rows_per, A, Bp, b.partials, vb % tiles, vb / tiles);
@@ -445,8 +507,8 @@ __global__ void gram_reduce_batch_kernel(const BJob *__restrict__ jobs,
 
 template <typename T>
 ks_status batch_gram(Batch &B, int sA, int sB, int smOut) {
-  for (int small = 1; small >= 0; --small) {
-    const int m = small ? BM_GRAM_SMALL : BM_GRAM_TILED;
+  for (int small = 2; small >= 0; --small) {
+    const int m = small == 2 ? BM_GRAM_MID : small == 1 ? BM_GRAM_SMALL : BM_GRAM_TILED;
     const int nb = B.total(m);
     if (nb == 0) continue;
     {

@@ -269,7 +269,7 @@ struct BJob {
 // each job takes in a launch family.
 enum BMap {
   BM_DENSITY = 0, BM_POTENTIAL, BM_ST4, BM_ST8, BM_ST16, BM_ST32, BM_THOMAS, BM_GRAM_SMALL,
-  BM_GRAM_TILED, BM_GRAM_REDUCE, BM_COMB_NARROW, BM_COMB_TILED, BM_COEF, BM_COPY, BM_COUNT
+  BM_GRAM_MID, BM_GRAM_TILED, BM_GRAM_REDUCE, BM_COMB_NARROW, BM_COMB_TILED, BM_COEF, BM_COPY, BM_COUNT
 };
 
 struct Batch {

@@ -5,6 +5,8 @@
 
 c4: uneven jobs (N in [20, 48], p = 2 x atoms in [4, 32]) all submitted at
     once; reports solves/s and the latency spread.
+    With --mode batch the same jobs run as one job table (ks_batch): every
+    kernel launch of an iteration covers all jobs still iterating.
 c5: a Poisson stream (N in [24, 96], p in [8, 128]); the arrival rate is a
     fraction of the saturation throughput measured first on the same jobs
     (or --rate jobs/s).  Reports p50/p99 latency (submit to result) and
@@ -77,6 +79,8 @@ def main(argv=None) -> int:
     ap.add_argument("--rate", type=float, default=0.0, help="c5 arrivals per second")
     ap.add_argument("--rate-frac", type=float, default=0.5,
                     help="c5: arrival rate as a fraction of the measured saturation throughput")
+    ap.add_argument("--mode", default="server", choices=["server", "batch"],
+                    help="c4: continuous-batching server (per-job streams) or one job table")
     a = ap.parse_args(argv)
     torch.cuda.init()
     jobs = (ki.config_c4_jobs(njobs=a.jobs) if a.workload == "c4"
@@ -84,7 +88,26 @@ def main(argv=None) -> int:
     opts = dict(retraction="qr", gtol=a.gtol, maxit=a.maxit, precision=a.precision)
     budget = int(a.budget_gb * (1 << 30))
     out = {"workload": a.workload, "jobs": a.jobs, "slots": a.slots, "precision": a.precision,
-           "maxit": a.maxit, "budget_gb": a.budget_gb}
+           "maxit": a.maxit, "budget_gb": a.budget_gb, "mode": a.mode}
+    if a.mode == "batch":
+        import paper_1308_2864_gb300 as ks
+        t0 = time.perf_counter()
+        B = ks.Batch(jobs)
+        t_create = time.perf_counter() - t0
+        B.minimize(maxit=2, **{k: v for k, v in opts.items() if k != "maxit"})   # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res, _ = B.minimize(**opts)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        out.update({"solves_per_s": a.jobs / wall, "batch_wall_s": wall, "create_s": t_create,
+                    "gb": B.bytes / (1 << 30),
+                    "converged": sum(r["status"] == 0 for r in res),
+                    "iters_total": sum(r["iters"] for r in res),
+                    "iters_max": max(r["iters"] for r in res)})
+        print(json.dumps(out), flush=True)
+        B.close()
+        return 0
     wall, lat, res, st = run(jobs, None, a.slots, budget, opts)
     sat = a.jobs / wall
     out.update({"saturation_solves_per_s": sat, "batch_wall_s": wall,

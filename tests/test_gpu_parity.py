@@ -409,3 +409,15 @@ def test_mixed_minimize_same_with_and_without_tma():
         Xs.append(X)
     assert res[0]["E"] == res[1]["E"] and res[0]["iters"] == res[1]["iters"]
     assert torch.equal(Xs[0], Xs[1])
+
+
+@pytest.mark.parametrize("shape", [(9, 20, 13), (11, 32, 32), (8, 9, 31)])
+def test_gram_mid_size(shape):
+    # 8 < pa, qb <= 32: one thread per Gram entry, no padded tile
+    N, pa, qb = shape
+    s = ki.small_system(N=N, L=7.0, natoms=2, p=max(pa, qb), Z=4.0, seed=4)
+    P = make(s)
+    rng = np.random.default_rng(41)
+    A = rng.standard_normal((s.n, pa))
+    B = rng.standard_normal((s.n, qb))
+    assert_rel(host(P.step_gram(dev(A), dev(B))), A.T @ B, rel=1e-13, what="A^T B")
