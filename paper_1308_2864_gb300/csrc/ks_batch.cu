@@ -397,6 +397,8 @@ ks_status build_maps(Batch &B) {
       put(BM_COMB_TILED, j, ((n + kTile - 1) / kTile) * ((p + kTile - 1) / kTile));
     }
     put(BM_COEF, j, (2 * p * p + kThreads - 1) / kThreads);
+    put(BM_CG_NODES, j, (n + kCgThreads - 1) / kCgThreads);
+    put(BM_CG_PLANES, j, b.N);
     put(BM_COPY, j, (n * p + 4 * kThreads - 1) / (4 * kThreads));
   }
   for (int m = 0; m < BM_COUNT; ++m) {
@@ -426,6 +428,8 @@ void free_batch(Batch &B) {
   if (B.scal_host) cudaFreeHost(B.scal_host);
   if (B.status_host) cudaFreeHost(B.status_host);
   if (B.cg_tolw_host) cudaFreeHost(B.cg_tolw_host);
+  if (B.cg_remaining_host) cudaFreeHost(B.cg_remaining_host);
+  if (B.cg_remaining_dev) cudaFree(B.cg_remaining_dev);
   if (B.ring_host) cudaFreeHost(B.ring_host);
   if (B.own_stream && B.stream) cudaStreamDestroy(B.stream);
   cudaGetLastError();
@@ -485,11 +489,13 @@ ks_status ks_batch_create(const ks_problem_desc *descs, int njobs, void *stream,
   BALLOC(B.status_dev, sizeof(int) * njobs);
   BALLOC(B.active_dev, (size_t)njobs);
   BALLOC(B.tau_dev, sizeof(double) * njobs);
+  BALLOC(B.cg_remaining_dev, sizeof(int));
   HALLOC(B.scal_host, sizeof(double) * SC_COUNT * njobs);
   HALLOC(B.status_host, sizeof(int) * njobs);
   HALLOC(B.active_host, (size_t)njobs);
   HALLOC(B.tau_host, sizeof(double) * njobs);
   HALLOC(B.cg_tolw_host, sizeof(double) * 2 * njobs);
+  HALLOC(B.cg_remaining_host, sizeof(int));
   B.ring_bytes = (size_t)64 * (((size_t)njobs * sizeof(double) + 255) / 256 * 256);
   HALLOC(B.ring_host, B.ring_bytes);
   if ((e = cudaMemsetAsync(B.scal_dev, 0, sizeof(double) * SC_COUNT * njobs, B.stream)) != cudaSuccess ||

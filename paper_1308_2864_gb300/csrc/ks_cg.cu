@@ -377,23 +377,6 @@ __global__ void __launch_bounds__(kCgThreads) cg_kernel(CgArgs a) {
   cg_body(a);
 }
 
-// Many systems in one cooperative launch: block b solves system job_of[b]
-// as its block vb_of[b] of args[job].vnb; systems whose active flag is 0
-// return at once (all their blocks together).
-__global__ void __launch_bounds__(kCgThreads) cg_batch_kernel(const CgArgs *__restrict__ args,
-                                                              const int *__restrict__ job_of,
-                                                              const int *__restrict__ vb_of,
-                                                              const unsigned char *__restrict__ active,
-                                                              const double *__restrict__ tolw) {
-  const int j = job_of[blockIdx.x];
-  if (!active[j]) return;
-  CgArgs a = args[j];
-  a.vb = vb_of[blockIdx.x];
-  a.tol = tolw[2 * j];
-  a.warm = tolw[2 * j + 1] != 0.0 ? 1 : 0;
-  cg_body(a);
-}
-
 // Sine basis Phi_{jk} = sqrt(2/(N+1)) sin(j k pi/(N+1)) (j, k = 1..N) and
 // the 1-D eigenvalues kappa_j = (2/h)(1 - cos t_j), mu_j = (h/3)(2 + cos t_j),
 // t_j = j pi/(N+1), in single precision for the preconditioner.
@@ -461,62 +444,246 @@ ks_status launch_cg(Problem &P, const double *rho, double *v, double *r, bool wa
 }
 
 // ---------------------------------------------------------------- batched
-__global__ void cg_batch_reset_kernel(const CgArgs *__restrict__ args, int J,
-                                      const unsigned char *__restrict__ active) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < J && active[j]) {
-    args[j].bar->count = 0u;
-    args[j].bar->gen = 0u;
+// The PCG of every job of a batch, one launch per CG phase over all jobs
+// (no grid barrier: a phase's last block of each job finishes that job's
+// reductions and scalar updates in device memory).  Phases:
+//   init   r = b - K x (x = 0 when cold), r.r, b.b, tolerance
+//   A/B/C  the fused sine-basis preconditioner, one block per (job, plane)
+//          resp. (job, y-slab); C writes z and r.z and updates rho, beta
+//   it1    p = s + beta p_old, q = K p, p.q -> alpha
+//   it2    x += alpha p, r -= alpha q, r.r -> convergence
+// A job that has converged (or failed) skips every later phase.  The host
+// reads the number of jobs still iterating once per CG iteration.
+struct CgState {
+  double rr, bb, thr, rho, beta, alpha;
+  int it, done, maxit, precond;
+};
+
+// Last block of one job's nb blocks: sums of the nchan partial channels
+// part[c * nb + vb] (in block order) into s[]; true in that block only.
+__device__ bool job_tail(double *part, int nb, int nchan, unsigned int *counter, double *smem,
+                         double *s) {
+  __shared__ int s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int prev = atomicAdd(counter, 1u);
+    s_last = (prev == (unsigned int)nb - 1u);
+  }
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+  for (int c = 0; c < nchan; ++c) s[c] = block_sum_array(part + (long long)c * nb, nb, smem);
+  if (threadIdx.x == 0) *counter = 0u;
+  return true;
+}
+
+struct CgBatchView {
+  const CgArgs *args;
+  CgState *st;
+  const int *start;                // block map of the phase
+  int J;
+  const unsigned char *active;
+  const double *tolw;              // per job: tolerance, warm flag
+  unsigned int *counters;          // one per job
+};
+
+__device__ __forceinline__ bool cg_job(const CgBatchView &v, int &j, int &vb, int &nb) {
+  j = batch_job_of(v.start, v.J, blockIdx.x);
+  if (!v.active[j] || v.st[j].done) return false;
+  vb = blockIdx.x - v.start[j];
+  nb = v.start[j + 1] - v.start[j];
+  return true;
+}
+
+__global__ void __launch_bounds__(kCgThreads) cg_b_init(CgBatchView v) {
+  __shared__ double smem[33];
+  const int j = batch_job_of(v.start, v.J, blockIdx.x);
+  if (!v.active[j]) return;
+  const int vb = blockIdx.x - v.start[j], nb = v.start[j + 1] - v.start[j];
+  const CgArgs &a = v.args[j];
+  const int warm = v.tolw[2 * j + 1] != 0.0;
+  const int N = a.N;
+  const long long NN = (long long)N * N;
+  double rr_l = 0.0, bb_l = 0.0;
+  for (long long k = (long long)vb * blockDim.x + threadIdx.x; k < a.n;
+       k += (long long)nb * blockDim.x) {
+    const double b = a.bscale * a.rho[k];
+    double kx = 0.0, dummy;
+    if (warm) {
+      const int ix = (int)(k % N), iy = (int)((k / N) % N), iz = (int)(k / NN);
+      kx = stiff_apply<false>(a.x, nullptr, 0.0, N, ix, iy, iz, a.c, &dummy);
+    } else {
+      a.x[k] = 0.0;
+    }
+    const double rk = b - kx;
+    a.r[k] = rk;
+    rr_l = fma(rk, rk, rr_l);
+    bb_l = fma(b, b, bb_l);
+  }
+  const double s1 = block_sum(rr_l, smem), s2 = block_sum(bb_l, smem);
+  if (threadIdx.x == 0) {
+    a.part[vb] = s1;
+    a.part[nb + vb] = s2;
+  }
+  double s[2];
+  if (!job_tail(a.part, nb, 2, v.counters + j, smem, s)) return;
+  if (threadIdx.x == 0) {
+    CgState &t = v.st[j];
+    const double tol = v.tolw[2 * j];
+    t.rr = s[0];
+    t.bb = s[1];
+    t.thr = tol * tol * s[1];
+    t.rho = s[0];
+    t.beta = 0.0;
+    t.it = 0;
+    t.maxit = a.maxit;
+    t.precond = a.precond;
+    t.done = t.rr <= t.thr ? 1 : 0;
+    *a.iters_out = 0.0;
   }
 }
 
-// Blocks per job for the batched cooperative launch: one per 16384 nodes
-// (at least one, at most one per z-plane), a rule of the job alone, so that a
-// job's sums, and so its result, do not depend on the other jobs.  All blocks
-// of all jobs must be resident together (a job's blocks wait on each other at
-// its own barrier); when the rule asks for more than fit, every job's share
-// is scaled down.
-
-ks_status batch_cg_setup(Batch &B) {
-  const size_t dyn = cg_dynamic_smem(B.maxN <= kFusedMaxN ? B.maxN : 0);
-  KS_CUDA_TRY(cudaFuncSetAttribute(cg_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)cg_dynamic_smem(kFusedMaxN)));
-  int per_sm = 0;
-  KS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_batch_kernel, kCgThreads,
-                                                            dyn));
-  if (per_sm < 1) return set_error(KS_ECUDA, "batched CG kernel does not fit on an SM");
-  const long long cap = (long long)B.sms * per_sm;
-  if ((long long)B.J > cap)
-    return set_error(KS_EINVAL, "batch: %d jobs exceed the %lld co-resident CG blocks", B.J, cap);
-  std::vector<int> nb(B.J);
-  long long used = 0;
-  for (int j = 0; j < B.J; ++j) {
-    const BJob &b = B.jobs_host[j];
-    long long want = (b.n + 16383) / 16384;
-    const long long by_part = (long long)(B.probs[j]->P.partials_len / 4);
-    if (want > by_part) want = by_part;
-    if (want > B.probs[j]->P.N) want = B.probs[j]->P.N;
-    if (want < 1) want = 1;
-    nb[j] = (int)want;
-    used += want;
-  }
-  if (used > cap) {
-    const double scale = (double)(cap - B.J) / (double)(used - B.J > 0 ? used - B.J : 1);
-    used = 0;
-    for (int j = 0; j < B.J; ++j) {
-      nb[j] = 1 + (int)((nb[j] - 1) * scale);
-      used += nb[j];
+// Preconditioner passes (fused form; jobs with N > kFusedMaxN are refused at
+// batch creation).  Stage 0: planes of r -> t1; 1: slabs t1 -> t2; 2: planes
+// t2 -> z with r.z, then rho and beta.
+template <int Stage>
+__global__ void __launch_bounds__(kCgThreads) cg_b_precond(CgBatchView v) {
+  __shared__ double smem[33];
+  extern __shared__ float dyn[];
+  int j, vb, nb;
+  if (!cg_job(v, j, vb, nb)) return;
+  CgArgs a = v.args[j];
+  if (!v.st[j].precond) return;
+  const int N = a.N, NN = N * N;
+  a.vb = vb;
+  a.vnb = nb;
+  for (int e = threadIdx.x; e < NN; e += blockDim.x) dyn[NN + e] = __ldg(a.phi + e);
+  if (Stage == 0) {
+    fused_plane_pass<true, false>(a, a.r, a.t1, nullptr, dyn);
+  } else if (Stage == 1) {
+    fused_slab_pass(a, a.t1, a.t2, dyn);
+  } else {
+    const double rz_l = fused_plane_pass<false, true>(a, a.t2, nullptr, a.z, dyn);
+    const double sum = block_sum(rz_l, smem);
+    if (threadIdx.x == 0) a.part[vb] = sum;
+    double s[1];
+    if (!job_tail(a.part, nb, 1, v.counters + j, smem, s)) return;
+    if (threadIdx.x == 0) {
+      CgState &t = v.st[j];
+      if (!isfinite(s[0])) {
+        t.done = 1;
+        atomicCAS(a.status, 0, (int)KS_ENAN);
+      } else {
+        t.beta = t.it == 0 ? 0.0 : s[0] / t.rho;
+        t.rho = s[0];
+      }
     }
   }
-  std::vector<int> job_of, vb_of;
-  for (int j = 0; j < B.J; ++j)
-    for (int v = 0; v < nb[j]; ++v) { job_of.push_back(j); vb_of.push_back(v); }
-  B.cg_blocks = (int)job_of.size();
+}
+
+__global__ void __launch_bounds__(kCgThreads) cg_b_it1(CgBatchView v) {
+  __shared__ double smem[33];
+  int j, vb, nb;
+  if (!cg_job(v, j, vb, nb)) return;
+  const CgArgs &a = v.args[j];
+  const CgState t = v.st[j];
+  const int N = a.N;
+  const long long NN = (long long)N * N;
+  const double *s_vec = t.precond ? a.z : a.r;
+  double *pold = (t.it % 2 == 0) ? a.pb : a.pa, *pnew = (t.it % 2 == 0) ? a.pa : a.pb;
+  double pq_l = 0.0;
+  for (long long k = (long long)vb * blockDim.x + threadIdx.x; k < a.n;
+       k += (long long)nb * blockDim.x) {
+    const int ix = (int)(k % N), iy = (int)((k / N) % N), iz = (int)(k / NN);
+    double pk;
+    const double qk = t.it == 0 ? stiff_apply<false>(s_vec, nullptr, 0.0, N, ix, iy, iz, a.c, &pk)
+                                : stiff_apply<true>(s_vec, pold, t.beta, N, ix, iy, iz, a.c, &pk);
+    pnew[k] = pk;
+    a.q[k] = qk;
+    pq_l = fma(pk, qk, pq_l);
+  }
+  const double sum = block_sum(pq_l, smem);
+  if (threadIdx.x == 0) a.part[vb] = sum;
+  double s[1];
+  if (!job_tail(a.part, nb, 1, v.counters + j, smem, s)) return;
+  if (threadIdx.x == 0) {
+    CgState &u = v.st[j];
+    if (!(s[0] > 0.0) || !isfinite(s[0])) {
+      u.done = 1;
+      atomicCAS(a.status, 0, (int)KS_ENAN);
+    } else {
+      u.alpha = u.rho / s[0];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kCgThreads) cg_b_it2(CgBatchView v) {
+  __shared__ double smem[33];
+  int j, vb, nb;
+  if (!cg_job(v, j, vb, nb)) return;
+  const CgArgs &a = v.args[j];
+  const CgState t = v.st[j];
+  const double *p = (t.it % 2 == 0) ? a.pa : a.pb;
+  double rl = 0.0;
+  for (long long k = (long long)vb * blockDim.x + threadIdx.x; k < a.n;
+       k += (long long)nb * blockDim.x) {
+    a.x[k] = fma(t.alpha, p[k], a.x[k]);
+    const double rk = fma(-t.alpha, a.q[k], a.r[k]);
+    a.r[k] = rk;
+    rl = fma(rk, rk, rl);
+  }
+  const double sum = block_sum(rl, smem);
+  if (threadIdx.x == 0) a.part[vb] = sum;
+  double s[1];
+  if (!job_tail(a.part, nb, 1, v.counters + j, smem, s)) return;
+  if (threadIdx.x == 0) {
+    CgState &u = v.st[j];
+    ++u.it;
+    u.rr = s[0];
+    *a.iters_out = (double)u.it;
+    if (!isfinite(s[0])) {
+      u.done = 1;
+      atomicCAS(a.status, 0, (int)KS_ENAN);
+    } else if (s[0] <= u.thr) {
+      u.done = 1;
+    } else if (u.it >= u.maxit) {
+      u.done = 1;
+      atomicCAS(a.status, 0, (int)KS_ENOCONV);
+    } else if (!u.precond) {
+      u.beta = s[0] / u.rho;
+      u.rho = s[0];
+    }
+  }
+}
+
+// Number of active jobs still iterating.
+__global__ void cg_b_count(const CgState *st, const unsigned char *active, int J, int *out) {
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  int c = 0;
+  for (int j = threadIdx.x; j < J; j += blockDim.x) c += active[j] && !st[j].done;
+  atomicAdd(&cnt, c);
+  __syncthreads();
+  if (threadIdx.x == 0) *out = cnt;
+}
+
+ks_status batch_cg_setup(Batch &B) {
+  if (B.maxN > kFusedMaxN)
+    return set_error(KS_EINVAL, "batch: N above %d (the fused Hartree preconditioner)", kFusedMaxN);
+  KS_CUDA_TRY(cudaFuncSetAttribute(cg_b_precond<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)cg_dynamic_smem(kFusedMaxN)));
+  KS_CUDA_TRY(cudaFuncSetAttribute(cg_b_precond<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)cg_dynamic_smem(kFusedMaxN)));
+  KS_CUDA_TRY(cudaFuncSetAttribute(cg_b_precond<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)cg_dynamic_smem(kFusedMaxN)));
   std::vector<CgArgs> args(B.J);
   for (int j = 0; j < B.J; ++j) {
     Problem &P = B.probs[j]->P;
     const BJob &b = B.jobs_host[j];
     CgArgs &a = args[j];
+    a = CgArgs{};
     a.N = P.N;
     a.n = P.n;
     a.c = q1_coefficients(P.h);
@@ -539,32 +706,30 @@ ks_status batch_cg_setup(Batch &B) {
     a.iters_out = b.scal + SC_CG_ITERS;
     a.tol = P.cg_tol;
     a.maxit = P.cg_maxit;
-    a.warm = 0;
     a.precond = P.cg_precond;
-    a.fused = P.N <= kFusedMaxN ? 1 : 0;
-    a.vb = 0;
-    a.vnb = nb[j];
+    a.fused = 1;
   }
   void *mem = nullptr;
-  const size_t abytes = ((sizeof(CgArgs) * B.J + 63) / 64) * 64;
-  const size_t tbytes = sizeof(double) * 2 * B.J, mbytes = sizeof(int) * job_of.size();
-  KS_CUDA_TRY(cudaMalloc(&mem, abytes + tbytes + 2 * mbytes));
+  const size_t abytes = ((sizeof(CgArgs) * B.J + 255) / 256) * 256;
+  const size_t sbytes = ((sizeof(CgState) * B.J + 255) / 256) * 256;
+  const size_t tbytes = sizeof(double) * 2 * B.J, cbytes = sizeof(unsigned int) * (B.J + 1);
+  KS_CUDA_TRY(cudaMalloc(&mem, abytes + sbytes + tbytes + cbytes));
+  char *m = static_cast<char *>(mem);
   B.cg_args_dev = mem;
-  B.cg_tolw_dev = reinterpret_cast<double *>(static_cast<char *>(mem) + abytes);
-  B.cg_job_of = reinterpret_cast<int *>(static_cast<char *>(mem) + abytes + tbytes);
-  B.cg_vb_of = B.cg_job_of + job_of.size();
+  B.cg_state_dev = m + abytes;
+  B.cg_tolw_dev = reinterpret_cast<double *>(m + abytes + sbytes);
+  B.cg_counters = reinterpret_cast<unsigned int *>(m + abytes + sbytes + tbytes);
+  KS_CUDA_TRY(cudaMemsetAsync(B.cg_state_dev, 0, sbytes, B.stream));
+  KS_CUDA_TRY(cudaMemsetAsync(B.cg_counters, 0, cbytes, B.stream));
   KS_CUDA_TRY(cudaMemcpyAsync(B.cg_args_dev, args.data(), sizeof(CgArgs) * B.J,
                               cudaMemcpyHostToDevice, B.stream));
-  KS_CUDA_TRY(cudaMemcpyAsync(B.cg_job_of, job_of.data(), mbytes, cudaMemcpyHostToDevice,
-                              B.stream));
-  KS_CUDA_TRY(cudaMemcpyAsync(B.cg_vb_of, vb_of.data(), mbytes, cudaMemcpyHostToDevice, B.stream));
   KS_CUDA_TRY(cudaStreamSynchronize(B.stream));
-  B.bytes += abytes + tbytes + 2 * mbytes;
+  B.bytes += abytes + sbytes + tbytes + cbytes;
   return KS_OK;
 }
 
 // Hartree solve of every active job (warm-started where B.warm says so) to
-// relative residual max(tol, the job's cg_tol), in one cooperative launch.
+// relative residual max(tol, the job's cg_tol).
 ks_status batch_cg(Batch &B, double tol) {
   for (int j = 0; j < B.J; ++j) {
     const double t = tol > B.probs[j]->P.cg_tol ? tol : B.probs[j]->P.cg_tol;
@@ -573,17 +738,44 @@ ks_status batch_cg(Batch &B, double tol) {
   }
   KS_CUDA_TRY(cudaMemcpyAsync(B.cg_tolw_dev, B.cg_tolw_host, sizeof(double) * 2 * B.J,
                               cudaMemcpyHostToDevice, B.stream));
-  const CgArgs *args = static_cast<const CgArgs *>(B.cg_args_dev);
+  CgBatchView nodes{static_cast<const CgArgs *>(B.cg_args_dev), static_cast<CgState *>(B.cg_state_dev),
+                    B.map(BM_CG_NODES), B.J, B.active_dev, B.cg_tolw_dev, B.cg_counters};
+  CgBatchView planes = nodes;
+  planes.start = B.map(BM_CG_PLANES);
+  const int nn = B.total(BM_CG_NODES), np = B.total(BM_CG_PLANES);
+  const size_t dyn = cg_dynamic_smem(B.maxN);
+  auto precond = [&]() -> ks_status {
+    cg_b_precond<0><<<np, kCgThreads, dyn, B.stream>>>(planes);
+    cg_b_precond<1><<<np, kCgThreads, dyn, B.stream>>>(planes);
+    cg_b_precond<2><<<np, kCgThreads, dyn, B.stream>>>(planes);
+    KS_CUDA_TRY(cudaGetLastError());
+    return KS_OK;
+  };
+  int maxit = 0;
+  for (int j = 0; j < B.J; ++j)
+    if (B.active_host[j] && B.probs[j]->P.cg_maxit > maxit) maxit = B.probs[j]->P.cg_maxit;
   {
-    ProfScope ps_(B.stream, KP_CG, 0.0, 0.0, 2);
-    cg_batch_reset_kernel<<<(B.J + 127) / 128, 128, 0, B.stream>>>(args, B.J, B.active_dev);
-    const size_t dyn = cg_dynamic_smem(B.maxN <= kFusedMaxN ? B.maxN : 0);
-    void *kargs[] = {(void *)&args, (void *)&B.cg_job_of, (void *)&B.cg_vb_of,
-                     (void *)&B.active_dev, (void *)&B.cg_tolw_dev};
-    KS_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)cg_batch_kernel, dim3(B.cg_blocks),
-                                            dim3(kCgThreads), kargs, dyn, B.stream));
+    ProfScope ps_(B.stream, KP_CG, 0.0, 0.0, 4);
+    cg_b_init<<<nn, kCgThreads, 0, B.stream>>>(nodes);
+    KS_CUDA_TRY(cudaGetLastError());
+    KS_TRY(precond());
   }
-  KS_CUDA_TRY(cudaGetLastError());
+  for (int it = 0; it < maxit; ++it) {
+    {
+      ProfScope ps_(B.stream, KP_CG, 0.0, 0.0, 6);
+      cg_b_it1<<<nn, kCgThreads, 0, B.stream>>>(nodes);
+      cg_b_it2<<<nn, kCgThreads, 0, B.stream>>>(nodes);
+      KS_CUDA_TRY(cudaGetLastError());
+      KS_TRY(precond());
+      cg_b_count<<<1, 256, 0, B.stream>>>(static_cast<const CgState *>(B.cg_state_dev),
+                                          B.active_dev, B.J, B.cg_remaining_dev);
+      KS_CUDA_TRY(cudaGetLastError());
+    }
+    KS_CUDA_TRY(cudaMemcpyAsync(B.cg_remaining_host, B.cg_remaining_dev, sizeof(int),
+                                cudaMemcpyDeviceToHost, B.stream));
+    KS_CUDA_TRY(cudaStreamSynchronize(B.stream));
+    if (*B.cg_remaining_host == 0) break;
+  }
   return KS_OK;
 }
 

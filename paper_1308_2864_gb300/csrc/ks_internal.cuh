@@ -269,7 +269,7 @@ struct BJob {
 // each job takes in a launch family.
 enum BMap {
   BM_DENSITY = 0, BM_POTENTIAL, BM_ST4, BM_ST8, BM_ST16, BM_ST32, BM_THOMAS, BM_GRAM_SMALL,
-  BM_GRAM_MID, BM_GRAM_TILED, BM_GRAM_REDUCE, BM_COMB_NARROW, BM_COMB_TILED, BM_COEF, BM_COPY, BM_COUNT
+  BM_GRAM_MID, BM_GRAM_TILED, BM_GRAM_REDUCE, BM_CG_NODES, BM_CG_PLANES, BM_COMB_NARROW, BM_COMB_TILED, BM_COEF, BM_COPY, BM_COUNT
 };
 
 struct Batch {
@@ -285,10 +285,11 @@ struct Batch {
   double *tau_dev = nullptr, *tau_host = nullptr;                // per-job step (pinned mirror)
   double *scal_dev = nullptr, *scal_host = nullptr;              // J x SC_COUNT
   int *status_dev = nullptr, *status_host = nullptr;             // J
-  void *cg_args_dev = nullptr;     // J CgArgs
+  void *cg_args_dev = nullptr;     // J CgArgs (Hartree PCG of each job)
+  void *cg_state_dev = nullptr;    // J per-job PCG scalars
   double *cg_tolw_dev = nullptr, *cg_tolw_host = nullptr;   // per job (tolerance, warm)
-  int *cg_job_of = nullptr, *cg_vb_of = nullptr;
-  int cg_blocks = 0;
+  unsigned int *cg_counters = nullptr;                      // per-job last-block counters
+  int *cg_remaining_dev = nullptr, *cg_remaining_host = nullptr;
   std::vector<unsigned char> warm; // per job: a previous Hartree potential exists
   char *ring_host = nullptr;       // pinned staging ring of the small uploads
   size_t ring_bytes = 0, ring_used = 0;
