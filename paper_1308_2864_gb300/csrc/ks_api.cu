@@ -39,7 +39,12 @@ ks_status cuda_error(cudaError_t e, const char *where) {
 
 static size_t gram_partials_len(int p, int sms) {
   const size_t tiles = (size_t)((p + kTile - 1) / kTile) * ((p + kTile - 1) / kTile);
-  return ((size_t)4 * sms + tiles) * kTile * kTile;
+  size_t len = ((size_t)4 * sms + tiles) * kTile * kTile;
+  // tensor-core Grams (p >= 256): one 128 x 256 tile per SM, p^2 per chunk
+  const size_t tc_tiles = (size_t)((p + 127) / 128) * ((p + 255) / 256);
+  const size_t tc = ((sms + tc_tiles - 1) / tc_tiles) * (size_t)p * p;
+  if (p >= 256 && tc > len) len = tc;
+  return len;
 }
 
 size_t problem_bytes(int N, int p, int sms) {
@@ -49,6 +54,7 @@ size_t problem_bytes(int N, int p, int sms) {
   b += (size_t)Problem::kNBlocks * n * p * sizeof(double);            // n x p blocks
   b += (size_t)S_COUNT * p * p * sizeof(double);                      // small matrices
   b += (size_t)2 * p * p * sizeof(float);                             // FP32 coefficients
+  b += tc_image_floats(p) * sizeof(float);                            // tensor-core image
   size_t part = gram_partials_len(p, sms);
   const size_t red = (size_t)4 * 8 * sms;
   const size_t cg = (size_t)4 * 2 * sms;
@@ -84,7 +90,7 @@ static void free_problem(Problem &P) {
   f(P.vext); f(P.rho); f(P.vH); f(P.veff); f(P.cg_r); f(P.cg_pa); f(P.cg_pb); f(P.cg_q);
   f(P.cg_z); f(P.cg_t1); f(P.cg_t2); f(P.dst_phi); f(P.dst_kap); f(P.dst_mu);
   for (auto &b : P.blk) f(b);
-  f(P.pp); f(P.cf); f(P.partials); f(P.scal); f(P.atoms_dev); f(P.thomas_w); f(P.bar); f(P.red_counter); f(P.dstatus);
+  f(P.pp); f(P.cf); f(P.tc_img); f(P.partials); f(P.scal); f(P.atoms_dev); f(P.thomas_w); f(P.bar); f(P.red_counter); f(P.dstatus);
   delete[] P.scal_host;
   delete[] P.dstatus_host;
   P.scal_host = nullptr;
@@ -598,6 +604,8 @@ ks_status ks_problem_create(const ks_problem_desc *d, ks_problem **out) {
   P.pp_len = (size_t)S_COUNT * P.p * P.p;
   ALLOC(P.pp, P.pp_len);
   ALLOC(P.cf, (size_t)2 * P.p * P.p);
+  P.tc_img_len = tc_image_floats(P.p);
+  ALLOC(P.tc_img, P.tc_img_len);
   P.cg_blocks = cg_grid_blocks(P.sms, P.n, P.N);
   if (P.cg_blocks < 1) return fail(set_error(KS_ECUDA, "CG kernel configuration failed"));
   size_t part = gram_partials_len(P.p, P.sms);

@@ -99,6 +99,8 @@ struct Problem {
   // p x p work (all FP64)
   double *pp = nullptr;            // pool of small matrices
   float *cf = nullptr;             // 2 p^2: FP32 copies of the update coefficients
+  float *tc_img = nullptr;         // coefficient image of the tensor-core update
+  size_t tc_img_len = 0;
   size_t pp_len = 0;
 
   // reductions
@@ -221,6 +223,7 @@ ks_status launch_cayley_factor(Problem &P, const double *A, const double *S, con
 ks_status configure_small_kernels();
 // ks_tc.cu: FP32 Gram on the tensor cores (partials per chunk, FP64)
 ks_status configure_tc_kernels();
+size_t tc_image_floats(int p);
 int gram_tc_chunks(const Problem &P, int pa, int qb);
 ks_status launch_gram_tc(Problem &P, const float *A, int pa, const float *B, int qb,
                          double *part, int chunks);

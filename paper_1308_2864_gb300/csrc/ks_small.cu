@@ -12,84 +12,8 @@ namespace ks {
 
 constexpr int kSmallThreads = 1024;
 
-// Cholesky (lower) of the p x p matrix W in place, right-looking.  Returns
-// false (and records KS_ENOTPD) on a non-positive or non-finite pivot.
-__device__ bool block_cholesky(double *W, int p, int *status) {
-  __shared__ int s_fail;
-  if (threadIdx.x == 0) s_fail = 0;
-  __syncthreads();
-  for (int j = 0; j < p; ++j) {
-    if (threadIdx.x == 0) {
-      const double d = W[j * p + j];
-      if (!(d > 0.0) || !isfinite(d)) {
-        s_fail = 1;
-        atomicCAS(status, 0, (int)KS_ENOTPD);
-      } else {
-        W[j * p + j] = sqrt(d);
-      }
-    }
-    __syncthreads();
-    if (s_fail) return false;
-    const double djj = W[j * p + j];
-    for (int i = j + 1 + threadIdx.x; i < p; i += blockDim.x) W[i * p + j] /= djj;
-    __syncthreads();
-    // trailing lower triangle: W[i][k] -= W[i][j] W[k][j], j < k <= i
-    const int m = p - j - 1;
-    const int cnt = m * (m + 1) / 2;
-    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-      // map t to (i, k) with 0 <= k' <= i' < m
-      int ii = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
-      while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
-      while (ii * (ii + 1) / 2 > t) --ii;
-      const int kk = t - ii * (ii + 1) / 2;
-      const int i = j + 1 + ii, k = j + 1 + kk;
-      W[i * p + k] = fma(-W[i * p + j], W[k * p + j], W[i * p + k]);
-    }
-    __syncthreads();
-  }
-  return true;
-}
-
-// Linv = L^{-1} for lower-triangular L (forward substitution, one column
-// per thread).
-__device__ void block_tri_inverse(const double *L, double *Linv, int p) {
-  for (int c = threadIdx.x; c < p; c += blockDim.x) {
-    for (int i = 0; i < c; ++i) Linv[i * p + c] = 0.0;
-    Linv[c * p + c] = 1.0 / L[c * p + c];
-    for (int i = c + 1; i < p; ++i) {
-      double s = 0.0;
-      for (int k = c; k < i; ++k) s = fma(L[i * p + k], Linv[k * p + c], s);
-      Linv[i * p + c] = -s / L[i * p + i];
-    }
-  }
-  __syncthreads();
-}
-
-__global__ void __launch_bounds__(kSmallThreads) qr_factor_kernel(int p, const double *DMD,
-                                                                  const double *O, double tau,
-                                                                  double *W, double *Linv,
-                                                                  double *C1, double *C2,
-                                                                  int *status) {
-  const double t2 = tau * tau;
-  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
-    const int i = e / p, j = e % p;
-    double r = O ? O[e] : (i == j ? 1.0 : 0.0);
-    if (DMD) r = fma(t2, DMD[e], r);
-    W[e] = r;
-  }
-  __syncthreads();
-  if (!block_cholesky(W, p, status)) return;
-  block_tri_inverse(W, Linv, p);
-  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
-    const int i = e / p, j = e % p;
-    const double c = Linv[j * p + i];      // (L^{-T})_{ij}
-    C1[e] = c;
-    if (C2) C2[e] = -tau * c;
-  }
-}
-
-// Shared-memory variant for p <= kSmemMaxP: the matrix and L^{-1} stay in
-// shared memory (2 p^2 doubles); Cholesky, then L^{-1} column by column.
+// The factor keeps W, L^{-1} and the pivots (2 p^2 + p doubles) in shared
+// memory up to p = kSmemMaxP, in global scratch (L2-resident) above.
 constexpr int kSmemMaxP = 104;
 
 // 1/sqrt(d) for d > 0 in FP64: FP32 seed, then two Newton steps
@@ -136,12 +60,11 @@ __device__ __forceinline__ bool chol_pivot(double w, int j, double *W, int p, do
 // the next pivot, leaving two barriers per column.  On GB300 one SM retires
 // two FP64 lanes per clock, so dense warps and no divisions matter more
 // than anything else here.
-__device__ __forceinline__ void qr_factor_smem_body(int p, const double *DMD, const double *O,
-                                                    double tau, double *C1, double *C2,
-                                                    int *status) {
-  extern __shared__ double W[];          // p*p: W -> L; p*p: R -> L^{-1} (row-major); p reciprocals
-  double *V = W + p * p;
-  double *rdiag = V + p * p;
+// W (p*p: W -> L), V (p*p: R -> L^{-1}, row-major) and rdiag (p) live in
+// shared memory (p <= kSmemMaxP) or in global scratch (larger p).
+__device__ __forceinline__ void qr_factor_body(int p, const double *DMD, const double *O,
+                                               double tau, double *C1, double *C2, int *status,
+                                               double *W, double *V, double *rdiag) {
   __shared__ int s_fail;
   const double t2 = tau * tau;
   for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
@@ -187,9 +110,24 @@ __device__ __forceinline__ void qr_factor_smem_body(int p, const double *DMD, co
   }
 }
 
+__device__ __forceinline__ void qr_factor_smem_body(int p, const double *DMD, const double *O,
+                                                    double tau, double *C1, double *C2,
+                                                    int *status) {
+  extern __shared__ double sh_w[];
+  qr_factor_body(p, DMD, O, tau, C1, C2, status, sh_w, sh_w + p * p, sh_w + 2 * p * p);
+}
+
 __global__ void __launch_bounds__(kSmallThreads) qr_factor_smem_kernel(
     int p, const double *DMD, const double *O, double tau, double *C1, double *C2, int *status) {
   qr_factor_smem_body(p, DMD, O, tau, C1, C2, status);
+}
+
+// Larger p: the same algorithm on global scratch (2 p^2 + p doubles).
+__global__ void __launch_bounds__(kSmallThreads) qr_factor_global_kernel(
+    int p, const double *DMD, const double *O, double tau, double *C1, double *C2, int *status,
+    double *scratch) {
+  qr_factor_body(p, DMD, O, tau, C1, C2, status, scratch, scratch + (size_t)p * p,
+                 scratch + 2 * (size_t)p * p);
 }
 
 // Batched: block j factors job j (p <= kSmemMaxP): R = I + tau_j^2 DMD
@@ -243,11 +181,10 @@ ks_status launch_qr_factor(Problem &P, const double *DMD, const double *O, doubl
     KS_CUDA_TRY(cudaGetLastError());
     return KS_OK;
   }
-  double *W = P.pp, *Linv = P.pp + (size_t)p * p;
   {
     ProfScope ps_(P.stream, KP_SMALL, 2.0 * pf * pf * pf / 3.0, 0.0);
-    qr_factor_kernel<<<1, kSmallThreads, 0, P.stream>>>(p, DMD, O, tau, W, Linv, C1, C2,
-                                                        P.dstatus);
+    qr_factor_global_kernel<<<1, kSmallThreads, 0, P.stream>>>(p, DMD, O, tau, C1, C2, P.dstatus,
+                                                               P.pp + (size_t)S_WORK * p * p);
   }
   KS_CUDA_TRY(cudaGetLastError());
   return KS_OK;

@@ -1,18 +1,20 @@
-// Tall-skinny Gram A^T B of the FP32 phase on the 5th-generation tensor
-// cores (tcgen05, kind::tf32), accumulator in tensor memory.
-//
-// A (n x pa) and B (n x qb) are row-major FP32.  A block owns a 128 x 64
-// output tile (columns a0.. of A, b0.. of B) and a chunk of rows; it stages
-// 32 rows at a time into shared memory in the K-major core-matrix layout
-// (8 rows x 16 bytes per core matrix, no swizzle), split into TF32 high and
-// low parts (x = hi + lo, hi = x with the low 13 mantissa bits cleared), and
-// one thread issues hi.hi + hi.lo + lo.hi products (3 x 4 MMAs of
-// 128 x 64 x 8 per stage) into one FP32 accumulator in tensor memory.  Two
-// stage buffers alternate; a stage buffer is refilled only after the MMAs
-// that read it have committed to its mbarrier.  All waits are bounded: a
-// block that waits too long records KS_ETIMEOUT and stops.  The chunk's
-// 128 x 64 partial is read back with tcgen05.ld and written as FP64 partials
-// that the caller sums in chunk order.
+// Tall-skinny products of the FP32 phase on the 5th-generation tensor cores
+// (tcgen05, kind::tf32), accumulators in tensor memory:
+//   gram:    A^T B with A (n x pa), B (n x qb) row-major FP32;
+//   combine: alpha (A1 C1 + A2 C2) + beta Bm with FP32 blocks and FP64 C.
+// Each block owns a 128 x 256 output tile (256 TMEM columns).  Operands are
+// staged 32 K-values at a time in the K-major core-matrix layout (8 rows x
+// 16 bytes per core matrix, no swizzle) and split into TF32 high and low
+// parts (x = hi + lo, hi = x with the low 13 mantissa bits cleared); one
+// thread issues hi.hi + hi.lo + lo.hi (3 x 4 MMAs of 128 x 256 x 8 per stage,
+// about 2^-21 relative error per product) into one FP32 accumulator.  Two
+// stage buffers alternate; a buffer is refilled only after the MMAs that
+// read it have committed to its mbarrier, and the next stage's global loads
+// are in flight (registers for the streamed blocks, cp.async for the
+// coefficient image of the update) while the current stage's MMAs run.
+// A warp stages an 8-row x 4-K patch per step, so its 32 shared-memory
+// stores hit 32 different banks.  All waits are bounded: a block that waits
+// too long records KS_ETIMEOUT and stops.
 #include <cstdint>
 
 #include "ks_device.cuh"
@@ -21,13 +23,16 @@ namespace ks {
 
 namespace {
 
-constexpr int kTcM = 128, kTcN = 64, kTcK = 32;   // tile rows, cols, rows per stage
+constexpr int kTcM = 128, kTcN = 256, kTcK = 32;  // tile rows, cols, K per stage
 constexpr int kTcThreads = 256;
-constexpr int kTcCols = 64;                       // TMEM columns allocated
+constexpr int kTcCols = 256;                      // TMEM columns allocated
 constexpr int kTileABytes = kTcM * kTcK * 4;      // 16 KiB
-constexpr int kTileBBytes = kTcN * kTcK * 4;      //  8 KiB
-constexpr int kStageBytes = 2 * kTileABytes + 2 * kTileBBytes;   // hi + lo of A and B
+constexpr int kTileBBytes = kTcN * kTcK * 4;      // 32 KiB
+constexpr int kStageBytes = 2 * kTileABytes + 2 * kTileBBytes;   // hi + lo of A and B: 96 KiB
 constexpr int kTcSmem = 2 * kStageBytes + 1024;   // two stages + alignment slack
+constexpr int kRegA = kTcM * kTcK / kTcThreads;   // 16 staged values per thread
+constexpr int kRegB = kTcN * kTcK / kTcThreads;   // 32
+constexpr int kOutLd = kTcM + 1;                  // transposed output tile row stride (floats)
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -50,7 +55,7 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
   return d;
 }
 
-// instruction descriptor: D FP32, A and B TF32, both K-major, N = 64, M = 128
+// instruction descriptor: D FP32, A and B TF32, both K-major, N = 256, M = 128
 constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
                             ((uint32_t)(kTcM >> 4) << 24);
 
@@ -77,330 +82,339 @@ __device__ __forceinline__ void split_tf32(float x, float &hi, float &lo) {
   lo = x - hi;
 }
 
-__global__ void __launch_bounds__(kTcThreads) gram_tc_kernel(long long n, int pa, int qb,
-                                                            long long rows_per, int tiles_b,
-                                                            const float *__restrict__ A,
-                                                            const float *__restrict__ B,
-                                                            double *__restrict__ part,
-                                                            int *status) {
+// Staging map of an R x 32 K-major tile: step i of warp w handles patch
+// g = w + 8 i, rows 8 (g % (R/8)) .. + 7 (lane & 7) and K-values
+// 4 (g / (R/8)) .. + 3 (lane >> 3).
+template <int R>
+__device__ __forceinline__ void patch(int warp, int lane, int i, int &r, int &k) {
+  const int g = warp + 8 * i;
+  r = (g % (R / 8)) * 8 + (lane & 7);
+  k = (g / (R / 8)) * 4 + (lane >> 3);
+}
+
+__device__ __forceinline__ void store_split(unsigned char *hi_base, unsigned char *lo_base, int r,
+                                            int k, float x) {
+  float hi, lo;
+  split_tf32(x, hi, lo);
+  const int off = kmajor_offset(r, k);
+  *(float *)(hi_base + off) = hi;
+  *(float *)(lo_base + off) = lo;
+}
+
+// 3 x 4 MMAs of one stage (K = 32) into the accumulator.
+__device__ __forceinline__ void issue_stage(uint32_t tmem, const unsigned char *st, bool first) {
+  const uint32_t sah = smem_u32(st), sal = sah + kTileABytes;
+  const uint32_t sbh = sah + 2 * kTileABytes, sbl = sbh + kTileBBytes;
+#pragma unroll
+  for (int ks = 0; ks < kTcK / 8; ++ks) {
+    const uint32_t o = ks * 256;
+    mma_tf32(tmem, smem_desc(sah + o), smem_desc(sbh + o), (!first || ks > 0) ? 1u : 0u);
+    mma_tf32(tmem, smem_desc(sah + o), smem_desc(sbl + o), 1u);
+    mma_tf32(tmem, smem_desc(sal + o), smem_desc(sbh + o), 1u);
+  }
+}
+
+__device__ __forceinline__ void commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+               :: "r"(smem_u32(bar)));
+}
+
+// 64 FP32 accumulator columns of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&v)[64]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
+      "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
+      "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+        "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+        "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+        "=r"(v[31]), "=r"(v[32]), "=r"(v[33]), "=r"(v[34]), "=r"(v[35]), "=r"(v[36]),
+        "=r"(v[37]), "=r"(v[38]), "=r"(v[39]), "=r"(v[40]), "=r"(v[41]), "=r"(v[42]),
+        "=r"(v[43]), "=r"(v[44]), "=r"(v[45]), "=r"(v[46]), "=r"(v[47]), "=r"(v[48]),
+        "=r"(v[49]), "=r"(v[50]), "=r"(v[51]), "=r"(v[52]), "=r"(v[53]), "=r"(v[54]),
+        "=r"(v[55]), "=r"(v[56]), "=r"(v[57]), "=r"(v[58]), "=r"(v[59]), "=r"(v[60]),
+        "=r"(v[61]), "=r"(v[62]), "=r"(v[63])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;");
+}
+
+// TMEM allocation (warp 0) and the two stage mbarriers (thread 0).
+__device__ __forceinline__ uint32_t tc_setup(uint32_t *tmem_slot, uint64_t *mbar) {
+  if ((threadIdx.x >> 5) == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_u32(tmem_slot)), "r"(kTcCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&mbar[0])), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&mbar[1])), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  return *tmem_slot;
+}
+
+__device__ __forceinline__ void tc_teardown(uint32_t tmem) {
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kTcCols));
+}
+
+// Wait for the commits of the last one or two stages; block-uniform result.
+__device__ __forceinline__ bool drain(uint64_t *mbar, uint32_t *phase, int issued, bool failed,
+                                      int *status) {
+  int ok = failed ? 0 : 1;
+  if (ok && issued > 0) {
+    const int last = (issued - 1) & 1;
+    if (issued >= 2 && !mbar_wait(smem_u32(&mbar[last ^ 1]), phase[last ^ 1])) ok = 0;
+    if (!mbar_wait(smem_u32(&mbar[last]), phase[last])) ok = 0;
+  }
+  ok = __syncthreads_and(ok);
+  if (!ok && threadIdx.x == 0 && !failed) atomicCAS(status, 0, (int)KS_ETIMEOUT);
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  return ok != 0;
+}
+
+// Before refilling stage buffer `buf`: wait for the MMAs of two stages ago.
+__device__ __forceinline__ bool reuse_wait(uint64_t *mbar, uint32_t *phase, int buf, int issued,
+                                           int *status) {
+  if (issued < 2) return true;
+  int ok = mbar_wait(smem_u32(&mbar[buf]), phase[buf]) ? 1 : 0;
+  phase[buf] ^= 1u;
+  if (!__syncthreads_and(ok)) {
+    if (threadIdx.x == 0) atomicCAS(status, 0, (int)KS_ETIMEOUT);
+    return false;
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) gram_tc_kernel(long long n, int pa, int qb,
+                                                               long long rows_per, int tiles_b,
+                                                               const float *__restrict__ A,
+                                                               const float *__restrict__ B,
+                                                               double *__restrict__ part,
+                                                               int *status) {
   extern __shared__ __align__(1024) unsigned char dyn_raw[];
   unsigned char *smem = (unsigned char *)(((uintptr_t)dyn_raw + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_slot;
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ta = blockIdx.x / tiles_b, tb = blockIdx.x % tiles_b;
   const int a0 = ta * kTcM, b0 = tb * kTcN;
   const int chunk = blockIdx.y;
   const long long r0 = chunk * rows_per;
   long long r1 = r0 + rows_per;
   if (r1 > n) r1 = n;
+  const uint32_t tmem = tc_setup(&tmem_slot, mbar);
 
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                 :: "r"(smem_u32(&tmem_slot)), "r"(kTcCols));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&mbar[0])), "r"(1));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&mbar[1])), "r"(1));
-    asm volatile("fence.mbarrier_init.release.cluster;");
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  const uint32_t tmem = tmem_slot;
-
-  uint32_t phase[2] = {0u, 0u};
-  int issued = 0;                       // stages issued so far
-  bool failed = false;                  // block-uniform
-  // only the valid columns of the tiles are staged each stage; the padding
-  // rows of the K-major tiles are zeroed once in both stage buffers
-  const int mw = min(kTcM, pa - a0), nw = min(kTcN, qb - b0);
-  for (int t = tid; t < 2 * (kTcM * kTcK + kTcN * kTcK); t += kTcThreads) {
-    const int b = t / (kTcM * kTcK + kTcN * kTcK);
-    int e = t % (kTcM * kTcK + kTcN * kTcK);
-    unsigned char *st = smem + b * kStageBytes;
-    if (e < kTcM * kTcK) {
-      const int k = e / kTcM, m = e % kTcM;
-      if (m >= mw) {
-        const int off = kmajor_offset(m, k);
-        *(float *)(st + off) = 0.f;
-        *(float *)(st + kTileABytes + off) = 0.f;
-      }
-    } else {
-      e -= kTcM * kTcK;
-      const int k = e / kTcN, c = e % kTcN;
-      if (c >= nw) {
-        const int off = kmajor_offset(c, k);
-        *(float *)(st + 2 * kTileABytes + off) = 0.f;
-        *(float *)(st + 2 * kTileABytes + kTileBBytes + off) = 0.f;
-      }
-    }
-  }
-  // register prefetch of one stage: A values (k, m < mw), B values (k, c < nw)
-  constexpr int kRegA = kTcM * kTcK / kTcThreads, kRegB = kTcN * kTcK / kTcThreads;
+  // next stage's values in registers: A (row k, column a0 + m), B (row k, column b0 + c)
   float ra[kRegA], rb[kRegB];
   auto fetch = [&](long long r) {
 #pragma unroll
     for (int i = 0; i < kRegA; ++i) {
-      const int t = tid + i * kTcThreads;
-      const int k = t / mw, m = t - k * mw;
+      int m, k;
+      patch<kTcM>(warp, lane, i, m, k);
       const long long row = r + k;
-      ra[i] = (k < kTcK && row < r1) ? A[row * pa + a0 + m] : 0.f;
+      ra[i] = (row < r1 && a0 + m < pa) ? A[row * pa + a0 + m] : 0.f;
     }
 #pragma unroll
     for (int i = 0; i < kRegB; ++i) {
-      const int t = tid + i * kTcThreads;
-      const int k = t / nw, c = t - k * nw;
+      int c, k;
+      patch<kTcN>(warp, lane, i, c, k);
       const long long row = r + k;
-      rb[i] = (k < kTcK && row < r1) ? B[row * qb + b0 + c] : 0.f;
+      rb[i] = (row < r1 && b0 + c < qb) ? B[row * qb + b0 + c] : 0.f;
     }
   };
-  __syncthreads();
+  uint32_t phase[2] = {0u, 0u};
+  int issued = 0;
+  bool failed = false;
   if (r0 < r1) fetch(r0);
   for (long long r = r0; r < r1; r += kTcK, ++issued) {
     const int buf = issued & 1;
     unsigned char *st = smem + buf * kStageBytes;
-    float *ah = (float *)st, *al = (float *)(st + kTileABytes);
-    float *bh = (float *)(st + 2 * kTileABytes), *bl = (float *)(st + 2 * kTileABytes + kTileBBytes);
-    // the buffer was last read by stage issued-2: wait for its commit
-    if (issued >= 2) {
-      int ok = 1;
-      if (!mbar_wait(smem_u32(&mbar[buf]), phase[buf])) ok = 0;
-      phase[buf] ^= 1u;
-      if (!__syncthreads_and(ok)) {
-        if (tid == 0) atomicCAS(status, 0, (int)KS_ETIMEOUT);
-        failed = true;
-        break;
-      }
+    if (!reuse_wait(mbar, phase, buf, issued, status)) {
+      failed = true;
+      break;
     }
 #pragma unroll
     for (int i = 0; i < kRegA; ++i) {
-      const int t = tid + i * kTcThreads;
-      const int k = t / mw, m = t - k * mw;
-      if (k < kTcK) {
-        float hi, lo;
-        split_tf32(ra[i], hi, lo);
-        const int off = kmajor_offset(m, k);
-        *(float *)((unsigned char *)ah + off) = hi;
-        *(float *)((unsigned char *)al + off) = lo;
-      }
+      int m, k;
+      patch<kTcM>(warp, lane, i, m, k);
+      store_split(st, st + kTileABytes, m, k, ra[i]);
     }
 #pragma unroll
     for (int i = 0; i < kRegB; ++i) {
-      const int t = tid + i * kTcThreads;
-      const int k = t / nw, c = t - k * nw;
-      if (k < kTcK) {
-        float hi, lo;
-        split_tf32(rb[i], hi, lo);
-        const int off = kmajor_offset(c, k);
-        *(float *)((unsigned char *)bh + off) = hi;
-        *(float *)((unsigned char *)bl + off) = lo;
-      }
+      int c, k;
+      patch<kTcN>(warp, lane, i, c, k);
+      store_split(st + 2 * kTileABytes, st + 2 * kTileABytes + kTileBBytes, c, k, rb[i]);
     }
-    // next stage's loads overlap this stage's MMAs
-    if (r + kTcK < r1) fetch(r + kTcK);
+    if (r + kTcK < r1) fetch(r + kTcK);          // in flight during this stage's MMAs
     asm volatile("fence.proxy.async.shared::cta;");
     __syncthreads();
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t sah = smem_u32(ah), sal = smem_u32(al), sbh = smem_u32(bh), sbl = smem_u32(bl);
-#pragma unroll
-      for (int ks = 0; ks < kTcK / 8; ++ks) {
-        const uint32_t o = ks * 256;
-        mma_tf32(tmem, smem_desc(sah + o), smem_desc(sbh + o), (issued > 0 || ks > 0) ? 1u : 0u);
-        mma_tf32(tmem, smem_desc(sah + o), smem_desc(sbl + o), 1u);
-        mma_tf32(tmem, smem_desc(sal + o), smem_desc(sbh + o), 1u);
-      }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                   :: "r"(smem_u32(&mbar[buf])));
+      issue_stage(tmem, st, issued == 0);
+      commit(&mbar[buf]);
     }
   }
-  // drain: wait for the last one or two stages
-  int ok = failed ? 0 : 1;
-  if (ok && issued > 0) {
-    const int last = (issued - 1) & 1;
-    if (issued >= 2 && !mbar_wait(smem_u32(&mbar[last ^ 1]), phase[last ^ 1])) ok = 0;
-    if (!mbar_wait(smem_u32(&mbar[last]), phase[last])) ok = 0;
-  }
-  ok = __syncthreads_and(ok);
-  if (!ok && tid == 0 && !failed) atomicCAS(status, 0, (int)KS_ETIMEOUT);
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  if (ok && warp < 4) {
-    uint32_t v[kTcN];
-    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
-        "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
-        "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
-          "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
-          "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
-          "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
-          "=r"(v[31]), "=r"(v[32]), "=r"(v[33]), "=r"(v[34]), "=r"(v[35]), "=r"(v[36]),
-          "=r"(v[37]), "=r"(v[38]), "=r"(v[39]), "=r"(v[40]), "=r"(v[41]), "=r"(v[42]),
-          "=r"(v[43]), "=r"(v[44]), "=r"(v[45]), "=r"(v[46]), "=r"(v[47]), "=r"(v[48]),
-          "=r"(v[49]), "=r"(v[50]), "=r"(v[51]), "=r"(v[52]), "=r"(v[53]), "=r"(v[54]),
-          "=r"(v[55]), "=r"(v[56]), "=r"(v[57]), "=r"(v[58]), "=r"(v[59]), "=r"(v[60]),
-          "=r"(v[61]), "=r"(v[62]), "=r"(v[63])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;");
-    const int arow = a0 + warp * 32 + (tid & 31);
-    if (arow < pa) {
-      double *dst = part + (long long)chunk * pa * qb + (long long)arow * qb;
-      for (int j = 0; j < kTcN; ++j)
-        if (b0 + j < qb) dst[b0 + j] = issued > 0 ? (double)__uint_as_float(v[j]) : 0.0;
+  const bool ok = drain(mbar, phase, issued, failed, status);
+  if (ok) {
+    // warps w and w + 4 read the same 32 lanes (rows), each half of the columns
+    const int arow = a0 + (warp & 3) * 32 + lane;
+    const int half = warp >> 2;
+    double *dst = part + (long long)chunk * pa * qb + (long long)arow * qb;
+#pragma unroll 1
+    for (int blk = 0; blk < 2; ++blk) {
+      const int cb = half * 128 + blk * 64;
+      uint32_t v[64];
+      tmem_ld64(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)cb, v);
+      if (arow < pa)
+        for (int j = 0; j < 64; ++j)
+          if (b0 + cb + j < qb) dst[b0 + cb + j] = issued > 0 ? (double)__uint_as_float(v[j]) : 0.0;
     }
   }
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  __syncthreads();
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kTcCols));
+  tc_teardown(tmem);
 }
 
-// out = alpha (A1 C1 + A2 C2) + beta Bm on the tensor cores: a block owns
-// 128 rows x 64 output columns; K runs over the columns of A1 then A2 in
-// stages of 32.  The A rows are already K-major (row-major blocks); the C
-// slices are transposed into the K-major layout.  Same 3 x TF32 split,
-// double buffering and bounded waits as the Gram kernel.
-__global__ void __launch_bounds__(kTcThreads) combine_tc_kernel(
-    long long n, int q, const float *__restrict__ A1, int k1, const double *__restrict__ C1,
-    const float *__restrict__ A2, int k2, const double *__restrict__ C2, float alpha, float beta,
+// Coefficient image of the update: for column tile ct (256 columns of
+// q) and stage s (K-values 32 s .. 32 s + 31 of [C1; C2]), the hi and lo
+// K-major tiles exactly as a stage buffer holds them, so a block copies
+// each stage's 64 KiB with cp.async.
+__global__ void combine_image_kernel(int q, int k1, const double *__restrict__ C1, int k2,
+                                     const double *__restrict__ C2, int stages, float *img) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long per_stage = (long long)kTcN * kTcK;
+  const long long total = (long long)((q + kTcN - 1) / kTcN) * stages * per_stage;
+  if (e >= total) return;
+  const int within = (int)(e % per_stage);
+  const long long ts = e / per_stage;             // ct * stages + s
+  const int s = (int)(ts % stages), ct = (int)(ts / stages);
+  const int c = within / kTcK, k = within % kTcK;
+  const int kk = s * kTcK + k, col = ct * kTcN + c;
+  double x = 0.0;
+  if (col < q) {
+    if (kk < k1) x = C1[(long long)kk * q + col];
+    else if (kk < k1 + k2) x = C2[(long long)(kk - k1) * q + col];
+  }
+  float hi, lo;
+  split_tf32((float)x, hi, lo);
+  unsigned char *base = (unsigned char *)(img + ts * 2 * per_stage);
+  const int off = kmajor_offset(c, k);
+  *(float *)(base + off) = hi;
+  *(float *)(base + kTileBBytes + off) = lo;
+}
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(smem_u32(dst)), "l"(src)
+               : "memory");
+}
+
+// out = alpha (A1 C1 + A2 C2) + beta Bm: a block owns 128 rows x 256
+// columns; K runs over the columns of A1 then A2 in stages of 32.
+__global__ void __launch_bounds__(kTcThreads, 1) combine_tc_kernel(
+    long long n, int q, const float *__restrict__ A1, int k1, const float *__restrict__ A2, int k2,
+    const float *__restrict__ img, int stages, float alpha, float beta,
     const float *__restrict__ Bm, float *__restrict__ out, int *status) {
   extern __shared__ __align__(1024) unsigned char dyn_raw[];
   unsigned char *smem = (unsigned char *)(((uintptr_t)dyn_raw + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_slot;
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long long row0 = (long long)blockIdx.x * kTcM;
-  const int c0 = blockIdx.y * kTcN;
+  const int ct = blockIdx.y, c0 = ct * kTcN;
   const int K = k1 + (A2 ? k2 : 0);
   const int nw = min(kTcN, q - c0);
+  const uint32_t tmem = tc_setup(&tmem_slot, mbar);
 
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                 :: "r"(smem_u32(&tmem_slot)), "r"(kTcCols));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&mbar[0])), "r"(1));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&mbar[1])), "r"(1));
-    asm volatile("fence.mbarrier_init.release.cluster;");
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  const uint32_t tmem = tmem_slot;
-
-  uint32_t phase[2] = {0u, 0u};
-  int issued = 0;
-  bool failed = false;
-  for (int kb = 0; kb < K; kb += kTcK, ++issued) {
-    const int buf = issued & 1;
-    unsigned char *st = smem + buf * kStageBytes;
-    float *ah = (float *)st, *al = (float *)(st + kTileABytes);
-    float *bh = (float *)(st + 2 * kTileABytes), *bl = (float *)(st + 2 * kTileABytes + kTileBBytes);
-    if (issued >= 2) {
-      int ok = 1;
-      if (!mbar_wait(smem_u32(&mbar[buf]), phase[buf])) ok = 0;
-      phase[buf] ^= 1u;
-      if (!__syncthreads_and(ok)) {
-        if (tid == 0) atomicCAS(status, 0, (int)KS_ETIMEOUT);
-        failed = true;
-        break;
-      }
-    }
-    // A slice: rows row0.., K columns kb..kb+31 (k-contiguous in memory)
-    for (int t = tid; t < kTcM * kTcK; t += kTcThreads) {
-      const int m = t / kTcK, k = t % kTcK;
+  float ra[kRegA];
+  auto fetch = [&](int kb) {
+#pragma unroll
+    for (int i = 0; i < kRegA; ++i) {
+      int m, k;
+      patch<kTcM>(warp, lane, i, m, k);
       const long long row = row0 + m;
       const int kk = kb + k;
       float x = 0.f;
       if (row < n && kk < K) x = kk < k1 ? A1[row * k1 + kk] : A2[row * k2 + (kk - k1)];
-      float hi, lo;
-      split_tf32(x, hi, lo);
-      const int off = kmajor_offset(m, k);
-      *(float *)((unsigned char *)ah + off) = hi;
-      *(float *)((unsigned char *)al + off) = lo;
+      ra[i] = x;
     }
-    // C slice transposed: element (c, k) = C[kb + k][c0 + c]
-    for (int t = tid; t < kTcN * kTcK; t += kTcThreads) {
-      const int k = t / kTcN, c = t % kTcN;
-      const int kk = kb + k;
-      float x = 0.f;
-      if (c < nw && kk < K)
-        x = (float)(kk < k1 ? C1[(long long)kk * q + c0 + c] : C2[(long long)(kk - k1) * q + c0 + c]);
-      float hi, lo;
-      split_tf32(x, hi, lo);
-      const int off = kmajor_offset(c, k);
-      *(float *)((unsigned char *)bh + off) = hi;
-      *(float *)((unsigned char *)bl + off) = lo;
+  };
+  // the stage's hi and lo coefficient tiles: 64 KiB, 16 x 16 bytes per thread
+  auto copy_image = [&](int s, unsigned char *st) {
+    const unsigned char *src = (const unsigned char *)(img + ((long long)ct * stages + s) * 2 *
+                                                             kTcN * kTcK);
+    unsigned char *dst = st + 2 * kTileABytes;
+#pragma unroll
+    for (int i = 0; i < 2 * kTileBBytes / 16 / kTcThreads; ++i) {
+      const int o = (tid + i * kTcThreads) * 16;
+      cp_async16(dst + o, src + o);
     }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  uint32_t phase[2] = {0u, 0u};
+  int issued = 0;
+  bool failed = false;
+  fetch(0);
+  for (int s = 0; s < stages; ++s, ++issued) {
+    const int buf = issued & 1;
+    unsigned char *st = smem + buf * kStageBytes;
+    if (!reuse_wait(mbar, phase, buf, issued, status)) {
+      failed = true;
+      break;
+    }
+    copy_image(s, st);
+#pragma unroll
+    for (int i = 0; i < kRegA; ++i) {
+      int m, k;
+      patch<kTcM>(warp, lane, i, m, k);
+      store_split(st, st + kTileABytes, m, k, ra[i]);
+    }
+    if (s + 1 < stages) fetch((s + 1) * kTcK);   // in flight during this stage's MMAs
+    asm volatile("cp.async.wait_all;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;");
     __syncthreads();
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t sah = smem_u32(ah), sal = smem_u32(al), sbh = smem_u32(bh), sbl = smem_u32(bl);
-#pragma unroll
-      for (int ks = 0; ks < kTcK / 8; ++ks) {
-        const uint32_t o = ks * 256;
-        mma_tf32(tmem, smem_desc(sah + o), smem_desc(sbh + o), (issued > 0 || ks > 0) ? 1u : 0u);
-        mma_tf32(tmem, smem_desc(sah + o), smem_desc(sbl + o), 1u);
-        mma_tf32(tmem, smem_desc(sal + o), smem_desc(sbh + o), 1u);
-      }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                   :: "r"(smem_u32(&mbar[buf])));
+      issue_stage(tmem, st, issued == 0);
+      commit(&mbar[buf]);
     }
   }
-  int ok = failed ? 0 : 1;
-  if (ok && issued > 0) {
-    const int last = (issued - 1) & 1;
-    if (issued >= 2 && !mbar_wait(smem_u32(&mbar[last ^ 1]), phase[last ^ 1])) ok = 0;
-    if (!mbar_wait(smem_u32(&mbar[last]), phase[last])) ok = 0;
-  }
-  ok = __syncthreads_and(ok);
-  if (!ok && tid == 0 && !failed) atomicCAS(status, 0, (int)KS_ETIMEOUT);
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  if (ok && warp < 4) {
-    uint32_t v[kTcN];
-    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
-        "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
-        "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
-          "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
-          "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
-          "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
-          "=r"(v[31]), "=r"(v[32]), "=r"(v[33]), "=r"(v[34]), "=r"(v[35]), "=r"(v[36]),
-          "=r"(v[37]), "=r"(v[38]), "=r"(v[39]), "=r"(v[40]), "=r"(v[41]), "=r"(v[42]),
-          "=r"(v[43]), "=r"(v[44]), "=r"(v[45]), "=r"(v[46]), "=r"(v[47]), "=r"(v[48]),
-          "=r"(v[49]), "=r"(v[50]), "=r"(v[51]), "=r"(v[52]), "=r"(v[53]), "=r"(v[54]),
-          "=r"(v[55]), "=r"(v[56]), "=r"(v[57]), "=r"(v[58]), "=r"(v[59]), "=r"(v[60]),
-          "=r"(v[61]), "=r"(v[62]), "=r"(v[63])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;");
-    const long long row = row0 + warp * 32 + (tid & 31);
-    if (row < n) {
+  const bool ok = drain(mbar, phase, issued, failed, status);
+  if (ok) {
+    // accumulator -> transposed tile T[c][m] in the (now idle) stage buffers,
+    // then row-contiguous, coalesced stores with the alpha / beta epilogue
+    float *T = reinterpret_cast<float *>(smem);
+    const int m = (warp & 3) * 32 + lane;
+    const int half = warp >> 2;
+#pragma unroll 1
+    for (int blk = 0; blk < 2; ++blk) {
+      const int cb = half * 128 + blk * 64;
+      uint32_t v[64];
+      tmem_ld64(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)cb, v);
+#pragma unroll
+      for (int j = 0; j < 64; ++j) T[(cb + j) * kOutLd + m] = __uint_as_float(v[j]);
+    }
+    __syncthreads();
+    for (int rr = warp; rr < kTcM; rr += kTcThreads / 32) {
+      const long long row = row0 + rr;
+      if (row >= n) break;
       float *dst = out + row * q + c0;
       const float *bm = Bm ? Bm + row * q + c0 : nullptr;
-      for (int j = 0; j < nw; ++j) {
-        float y = alpha * __uint_as_float(v[j]);
-        if (bm) y = fmaf(beta, bm[j], y);
-        dst[j] = y;
+      for (int c = lane; c < nw; c += 32) {
+        float y = alpha * T[c * kOutLd + rr];
+        if (bm) y = fmaf(beta, bm[c], y);
+        dst[c] = y;
       }
     }
   }
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  __syncthreads();
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kTcCols));
+  tc_teardown(tmem);
 }
 
 }  // namespace
@@ -413,29 +427,46 @@ ks_status configure_tc_kernels() {
   return KS_OK;
 }
 
+size_t tc_image_floats(int p) {
+  return (size_t)((p + kTcN - 1) / kTcN) * ((2 * p + kTcK - 1) / kTcK) * 2 * kTcN * kTcK;
+}
+
 ks_status launch_combine_tc(Problem &P, const float *A1, int k1, const double *C1,
                             const float *A2, int k2, const double *C2, double alpha, double beta,
                             const float *Bm, float *out, int q) {
-  dim3 grid((unsigned)((P.n + kTcM - 1) / kTcM), (unsigned)((q + kTcN - 1) / kTcN));
   const int K = k1 + (A2 ? k2 : 0);
+  const int stages = (K + kTcK - 1) / kTcK;
+  const long long img_len = (long long)((q + kTcN - 1) / kTcN) * stages * 2 * kTcN * kTcK;
+  if ((size_t)img_len > P.tc_img_len) return set_error(KS_EINVAL, "combine_tc: image too large");
+  {
+    ProfScope ps_(P.stream, KP_REDUCE);
+    const long long elems = img_len / 2;
+    combine_image_kernel<<<(int)((elems + 255) / 256), 256, 0, P.stream>>>(
+        q, k1, C1, A2 ? k2 : 0, C2, stages, P.tc_img);
+  }
+  KS_CUDA_TRY(cudaGetLastError());
+  dim3 grid((unsigned)((P.n + kTcM - 1) / kTcM), (unsigned)((q + kTcN - 1) / kTcN));
   {
     ProfScope ps_(P.stream, KP_COMBINE, 2.0 * P.n * q * K,
                   (double)P.n * (K + q * (Bm ? 2 : 1)) * sizeof(float));
-    combine_tc_kernel<<<grid, kTcThreads, kTcSmem, P.stream>>>(P.n, q, A1, k1, C1, A2, k2, C2,
-                                                               (float)alpha, (float)beta, Bm, out,
-                                                               P.dstatus);
+    combine_tc_kernel<<<grid, kTcThreads, kTcSmem, P.stream>>>(
+        P.n, q, A1, k1, A2, A2 ? k2 : 0, P.tc_img, stages, (float)alpha, (float)beta, Bm, out,
+        P.dstatus);
   }
   KS_CUDA_TRY(cudaGetLastError());
   return KS_OK;
 }
 
-// Chunks of the tensor-core Gram: about two blocks per SM over all tiles,
-// at least 512 rows per chunk.
+// Chunks of the tensor-core Gram: one block per SM over all tiles (each
+// block needs most of an SM's shared memory), at least 512 rows per chunk,
+// and no more chunks than the partial buffer holds.
 int gram_tc_chunks(const Problem &P, int pa, int qb) {
   const int tiles = ((pa + kTcM - 1) / kTcM) * ((qb + kTcN - 1) / kTcN);
-  int chunks = (2 * P.sms + tiles - 1) / tiles;
+  int chunks = (P.sms + tiles - 1) / tiles;
   const int maxc = (P.n + 511) / 512;
   if (chunks > maxc) chunks = maxc;
+  const long long room = (long long)(P.partials_len / ((size_t)pa * qb));
+  if (chunks > room) chunks = (int)room;
   if (chunks < 1) chunks = 1;
   return chunks;
 }

@@ -293,7 +293,8 @@ def test_checkpoint_resume_is_bitwise(precision):
     assert rb["iters"] == 20 and rc["iters"] == 20
 
 
-@pytest.mark.parametrize("shape", [(13, 70, 70), (16, 64, 64), (11, 130, 70), (9, 12, 9)])
+@pytest.mark.parametrize("shape", [(13, 70, 70), (16, 64, 64), (11, 130, 70), (9, 12, 9),
+                                   (9, 300, 260)])
 @pytest.mark.parametrize("tc", [0, 2], ids=["fp32-pipes", "tensor-cores"])
 def test_fp32_gram_tensor_cores(shape, tc):
     # FP32 Gram of the mixed phase: tensor cores (3 x TF32) for pa, qb > 8,
@@ -313,7 +314,8 @@ def test_fp32_gram_tensor_cores(shape, tc):
     assert np.all(np.abs(got - want) <= 2e-6 * bound + 1e-12)
 
 
-@pytest.mark.parametrize("shape", [(13, 70, 70), (16, 64, 64), (9, 40, 33), (11, 12, 20)])
+@pytest.mark.parametrize("shape", [(13, 70, 70), (16, 64, 64), (9, 40, 33), (11, 12, 20),
+                                   (9, 300, 300)])
 @pytest.mark.parametrize("tc", [0, 2], ids=["fp32-pipes", "tensor-cores"])
 def test_fp32_update_tensor_cores(shape, tc):
     # FP32 update X C1 + D C2 of the mixed phase (tensor cores for q > 32,
@@ -421,3 +423,21 @@ def test_gram_mid_size(shape):
     A = rng.standard_normal((s.n, pa))
     B = rng.standard_normal((s.n, qb))
     assert_rel(host(P.step_gram(dev(A), dev(B))), A.T @ B, rel=1e-13, what="A^T B")
+
+
+def test_qr_retract_large_p():
+    # p above the shared-memory limit of the p x p factor (global scratch)
+    import paper_1308_2864_gb300 as ks
+    s = ki.small_system(N=9, L=7.0, natoms=3, p=130, Z=4.0, seed=13)
+    model = oe.Model.from_system(s)
+    X = ost.m_orthonormalize(model, s.x0())
+    P = make(s)
+    ref = oe.evaluate(model, X)
+    pt = ost.project(model, X, ref)
+    for tau in (1e-3, 0.05):
+        got = host(P.retract(ks.KS_QR, dev(X), dev(ref.EX), tau))
+        assert_rel(got, ost.retract_qr(model, pt, tau), rel=1e-11, what=f"qr tau={tau}")
+        assert ost.ortho_error(model, got) < 1e-12
+    Y = dev(s.x0())
+    P.orthonormalize(Y)
+    assert ost.ortho_error(model, host(Y)) < 1e-12
