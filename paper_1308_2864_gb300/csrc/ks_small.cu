@@ -60,27 +60,18 @@ __device__ __forceinline__ bool chol_pivot(double w, int j, double *W, int p, do
 // the next pivot, leaving two barriers per column.  On GB300 one SM retires
 // two FP64 lanes per clock, so dense warps and no divisions matter more
 // than anything else here.
-// W (p*p: W -> L), V (p*p: R -> L^{-1}, row-major) and rdiag (p) live in
-// shared memory (p <= kSmemMaxP) or in global scratch (larger p).
-__device__ __forceinline__ void qr_factor_body(int p, const double *DMD, const double *O,
-                                               double tau, double *C1, double *C2, int *status,
-                                               double *W, double *V, double *rdiag) {
+// The loop of the merged factor on W (p x p, W -> L) and V (= I at the
+// start, -> L^{-1}); false (block-uniform) on a failed pivot.
+__device__ __forceinline__ bool chol_inv_core(double *W, double *V, double *rdiag, int p,
+                                              int *status) {
   __shared__ int s_fail;
-  const double t2 = tau * tau;
-  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
-    const int i = e / p, j = e % p;
-    double r = O ? O[e] : (i == j ? 1.0 : 0.0);
-    if (DMD) r = fma(t2, DMD[e], r);
-    W[e] = r;
-    V[e] = i == j ? 1.0 : 0.0;
-  }
   if (threadIdx.x == 0) s_fail = 0;
   __syncthreads();
   if (threadIdx.x == 0) chol_pivot(W[0], 0, W, p, rdiag, &s_fail, status);
   __syncthreads();
   const int tend = p * (p + 1) / 2;
   for (int j = 0; j < p; ++j) {
-    if (s_fail) return;
+    if (s_fail) return false;
     const double inv = rdiag[j];
     const int below = p - j - 1;
     for (int t = threadIdx.x; t < below + j + 1; t += blockDim.x) {
@@ -102,6 +93,23 @@ __device__ __forceinline__ void qr_factor_body(int p, const double *DMD, const d
     }
     __syncthreads();
   }
+  return true;
+}
+
+// W (p*p: W -> L), V (p*p: R -> L^{-1}, row-major) and rdiag (p) live in
+// shared memory (p <= kSmemMaxP).
+__device__ __forceinline__ void qr_factor_body(int p, const double *DMD, const double *O,
+                                               double tau, double *C1, double *C2, int *status,
+                                               double *W, double *V, double *rdiag) {
+  const double t2 = tau * tau;
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    const int i = e / p, j = e % p;
+    double r = O ? O[e] : (i == j ? 1.0 : 0.0);
+    if (DMD) r = fma(t2, DMD[e], r);
+    W[e] = r;
+    V[e] = i == j ? 1.0 : 0.0;
+  }
+  if (!chol_inv_core(W, V, rdiag, p, status)) return;
   for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
     const int i = e / p, j = e % p;
     const double cval = V[j * p + i];     // (L^{-T})_{ij} = (L^{-1})_{ji}
@@ -122,12 +130,154 @@ __global__ void __launch_bounds__(kSmallThreads) qr_factor_smem_kernel(
   qr_factor_smem_body(p, DMD, O, tau, C1, C2, status);
 }
 
-// Larger p: the same algorithm on global scratch (2 p^2 + p doubles).
-__global__ void __launch_bounds__(kSmallThreads) qr_factor_global_kernel(
-    int p, const double *DMD, const double *O, double tau, double *C1, double *C2, int *status,
-    double *scratch) {
-  qr_factor_body(p, DMD, O, tau, C1, C2, status, scratch, scratch + (size_t)p * p,
-                 scratch + 2 * (size_t)p * p);
+// ---------------------------------------------------------------- large p
+// p > kSmemMaxP: the same factorisation blocked by panels of kBlk columns,
+// so that the O(p^3) work spreads over the SMs (one SM retires only two
+// FP64 lanes per clock).  W (p x p, ld p) becomes L and V (= I at the
+// start) becomes L^{-1}; for each panel k:
+//   diag:   L_kk L_kk^T = W_kk and L_kk^{-1} (the merged kernel, one block)
+//   row/pn: V_km = L_kk^{-1} R_km (m <= k)  and  L_ik = W_ik L_kk^{-T} (i > k)
+//   update: W_ij -= L_ik L_jk^T (k < j <= i)  and  R_im -= L_ik V_km (i > k, m <= k)
+// (R is V before its rows are final; block rows below the panel are updated
+// by every panel above them, exactly the scalar algorithm by blocks).
+constexpr int kBlk = 32;
+constexpr int kBlkThreads = 256;
+
+__global__ void blk_init_kernel(int p, const double *DMD, const double *O, double tau, double *W,
+                                double *V) {
+  const double t2 = tau * tau;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)p * p;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / p), j = (int)(e % p);
+    double r = O ? O[e] : (i == j ? 1.0 : 0.0);
+    if (DMD) r = fma(t2, DMD[e], r);
+    W[e] = r;
+    V[e] = i == j ? 1.0 : 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(kBlkThreads) blk_diag_kernel(double *W, int p, int k0,
+                                                               double *Dinv, int *status) {
+  __shared__ double Ws[kBlk * kBlk], Vs[kBlk * kBlk], rd[kBlk];
+  const int nb = min(kBlk, p - k0);
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    const int i = e / nb, j = e % nb;
+    Ws[e] = W[(long long)(k0 + i) * p + k0 + j];
+    Vs[e] = i == j ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  if (!chol_inv_core(Ws, Vs, rd, nb, status)) return;
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    const int i = e / nb, j = e % nb;
+    W[(long long)(k0 + i) * p + k0 + j] = j <= i ? Ws[e] : 0.0;
+    Dinv[i * kBlk + j] = Vs[e];
+  }
+}
+
+// out (mr x mc, ld ldo) = (acc ? out : 0) + sgn * A (mr x kk, ld lda) op(B),
+// op(B) = B (kk x mc, ld ldb) or B^T (B mc x kk); both operands are staged
+// in shared memory before out is written, so out may alias either.
+__device__ void blk_gemm(double *out, int ldo, const double *A, int lda, const double *B, int ldb,
+                         bool transB, int mr, int mc, int kk, double sgn, bool acc) {
+  __shared__ double As[kBlk][kBlk + 1], Bs[kBlk][kBlk + 1];
+  for (int e = threadIdx.x; e < kBlk * kBlk; e += blockDim.x) {
+    const int r = e / kBlk, c = e % kBlk;
+    As[r][c] = (r < mr && c < kk) ? A[(long long)r * lda + c] : 0.0;
+    // Bs[k][c] = op(B)[k][c]
+    if (transB) Bs[r][c] = (c < mc && r < kk) ? B[(long long)c * ldb + r] : 0.0;
+    else Bs[r][c] = (r < kk && c < mc) ? B[(long long)r * ldb + c] : 0.0;
+  }
+  __syncthreads();
+  const int r = threadIdx.x >> 3, c0 = (threadIdx.x & 7) * 4;
+  double a4[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int k = 0; k < kk; ++k) {
+    const double a = As[r][k];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) a4[u] = fma(a, Bs[k][c0 + u], a4[u]);
+  }
+  if (r < mr)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int c = c0 + u;
+      if (c < mc) {
+        double *o = out + (long long)r * ldo + c;
+        *o = acc ? fma(sgn, a4[u], *o) : sgn * a4[u];
+      }
+    }
+}
+
+__device__ __forceinline__ int blk_size(int p, int b) { return min(kBlk, p - b * kBlk); }
+
+// rows of V (block row k) and the panel below the diagonal block
+__global__ void __launch_bounds__(kBlkThreads) blk_rowpanel_kernel(double *W, double *V, int p,
+                                                                   int k, const double *Dinv) {
+  const int K = (p + kBlk - 1) / kBlk;
+  const int nk = blk_size(p, k);
+  const int b = blockIdx.x;
+  if (b <= k) {                      // V_kb = L_kk^{-1} R_kb
+    const int m = b;
+    double *vb = V + (long long)k * kBlk * p + m * kBlk;
+    blk_gemm(vb, p, Dinv, kBlk, vb, p, false, nk, blk_size(p, m), nk, 1.0, false);
+  } else {                           // L_ik = W_ik L_kk^{-T}
+    const int i = k + (b - k);
+    if (i >= K) return;
+    double *wb = W + (long long)i * kBlk * p + k * kBlk;
+    blk_gemm(wb, p, wb, p, Dinv, kBlk, true, blk_size(p, i), nk, nk, 1.0, false);
+  }
+}
+
+__global__ void __launch_bounds__(kBlkThreads) blk_update_kernel(double *W, double *V, int p,
+                                                                 int k) {
+  const int K = (p + kBlk - 1) / kBlk;
+  const int nk = blk_size(p, k);
+  const int below = K - k - 1;
+  const int ntri = below * (below + 1) / 2;
+  int b = blockIdx.x;
+  if (b < ntri) {                    // W_ij -= L_ik L_jk^T, k < j <= i
+    int ii = (int)((sqrtf(8.0f * (float)b + 1.0f) - 1.0f) * 0.5f);
+    while (ii > 0 && ii * (ii + 1) / 2 > b) --ii;
+    while ((ii + 1) * (ii + 2) / 2 <= b) ++ii;
+    const int jj = b - ii * (ii + 1) / 2;
+    const int i = k + 1 + ii, j = k + 1 + jj;
+    blk_gemm(W + (long long)i * kBlk * p + j * kBlk, p, W + (long long)i * kBlk * p + k * kBlk, p,
+             W + (long long)j * kBlk * p + k * kBlk, p, true, blk_size(p, i), blk_size(p, j), nk,
+             -1.0, true);
+  } else {                           // R_im -= L_ik V_km, i > k, m <= k
+    b -= ntri;
+    const int i = k + 1 + b / (k + 1), m = b % (k + 1);
+    if (i >= K) return;
+    blk_gemm(V + (long long)i * kBlk * p + m * kBlk, p, W + (long long)i * kBlk * p + k * kBlk, p,
+             V + (long long)k * kBlk * p + m * kBlk, p, false, blk_size(p, i), blk_size(p, m), nk,
+             -1.0, true);
+  }
+}
+
+__global__ void blk_out_kernel(int p, const double *V, double tau, double *C1, double *C2) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)p * p;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / p), j = (int)(e % p);
+    const double c = V[(long long)j * p + i];
+    C1[e] = c;
+    if (C2) C2[e] = -tau * c;
+  }
+}
+
+static ks_status launch_qr_factor_blocked(Problem &P, const double *DMD, const double *O,
+                                          double tau, double *C1, double *C2) {
+  const int p = P.p, K = (p + kBlk - 1) / kBlk;
+  double *W = P.pp + (size_t)S_WORK * p * p, *V = W + (size_t)p * p, *Dinv = V + (size_t)p * p;
+  const int ng = (int)(((long long)p * p + 255) / 256);
+  blk_init_kernel<<<ng, 256, 0, P.stream>>>(p, DMD, O, tau, W, V);
+  for (int k = 0; k < K; ++k) {
+    blk_diag_kernel<<<1, kBlkThreads, 0, P.stream>>>(W, p, k * kBlk, Dinv, P.dstatus);
+    blk_rowpanel_kernel<<<K, kBlkThreads, 0, P.stream>>>(W, V, p, k, Dinv);
+    const int below = K - k - 1;
+    const int nupd = below * (below + 1) / 2 + below * (k + 1);
+    if (nupd > 0) blk_update_kernel<<<nupd, kBlkThreads, 0, P.stream>>>(W, V, p, k);
+  }
+  blk_out_kernel<<<ng, 256, 0, P.stream>>>(p, V, tau, C1, C2);
+  KS_CUDA_TRY(cudaGetLastError());
+  return KS_OK;
 }
 
 // Batched: block j factors job j (p <= kSmemMaxP): R = I + tau_j^2 DMD
@@ -182,9 +332,9 @@ ks_status launch_qr_factor(Problem &P, const double *DMD, const double *O, doubl
     return KS_OK;
   }
   {
-    ProfScope ps_(P.stream, KP_SMALL, 2.0 * pf * pf * pf / 3.0, 0.0);
-    qr_factor_global_kernel<<<1, kSmallThreads, 0, P.stream>>>(p, DMD, O, tau, C1, C2, P.dstatus,
-                                                               P.pp + (size_t)S_WORK * p * p);
+    const int K = (p + kBlk - 1) / kBlk;
+    ProfScope ps_(P.stream, KP_SMALL, 2.0 * pf * pf * pf / 3.0, 0.0, 3 * K + 1);
+    KS_TRY(launch_qr_factor_blocked(P, DMD, O, tau, C1, C2));
   }
   KS_CUDA_TRY(cudaGetLastError());
   return KS_OK;
