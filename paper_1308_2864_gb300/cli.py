@@ -2,6 +2,11 @@
 
   python -m paper_1308_2864_gb300.cli --config c2 --maxit 5 [--precision fp64|mixed]
                                       [--retraction qr|cayley] [--gtol 1e-6] [--verbose 0]
+                                      [--N 40] [--p 512]
+
+--N / --p shrink or change a configuration's grid and orbital count (same
+cube, atoms and functional), e.g. to profile the p = 512 kernels of c3 on a
+grid that fits a profiler's replay.
 
 Prints one JSON line with the result (energy, ||D||_M, iterations, time).
 Useful to profile a few iterations of the real workload.
@@ -33,9 +38,15 @@ def main(argv=None) -> int:
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--retraction", default=None, choices=["qr", "cayley"])
     ap.add_argument("--verbose", type=int, default=0)
+    ap.add_argument("--N", type=int, default=0, help="override the interior nodes per edge")
+    ap.add_argument("--p", type=int, default=0, help="override the number of orbitals")
     a = ap.parse_args(argv)
 
     s = ki.CONFIGS[a.config]()
+    if a.N > 0:
+        s.N = a.N
+    if a.p > 0:
+        s.p = a.p
     P = ks.Problem.from_system(s)
     X = torch.from_numpy(np.ascontiguousarray(s.x0())).cuda()
     t0 = time.perf_counter()

@@ -37,14 +37,40 @@ static int gram_chunks(const Problem &P, int pa, int qb) {
 
 // T = double, or float for the mixed path (FP32 products and per-chunk
 // FP32 sums, chunk partials summed in FP64).
+// K-values per stage of the 64-tile update: 32 in FP32 (more bytes in
+// flight per thread), 16 in FP64 (FP64-pipe-bound; keeps the two stage
+// buffers within the 48 KiB of static shared memory).  The Gram stages
+// kTileK rows (measured faster than 32 at p = 64).
+template <typename T>
+__host__ __device__ constexpr int stage_k() { return sizeof(T) == 4 ? 32 : 16; }
+
+// Vector of 4 consecutive T in shared memory (16- or 32-byte aligned).
+template <typename T>
+__device__ __forceinline__ void ld4(const T *p, T (&v)[4]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 q = *reinterpret_cast<const float4 *>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  } else {
+    const double2 q0 = reinterpret_cast<const double2 *>(p)[0];
+    const double2 q1 = reinterpret_cast<const double2 *>(p)[1];
+    v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+  }
+}
+
 // One 64 x 64 output tile (index `tile`, row-major over the tile grid) of
-// one row chunk.
+// one row chunk.  Thread (ty, tx) of 16 x 16 owns the contiguous 4 x 4 block
+// a0 + 4ty + i, b0 + 4tx + j, so a row step costs two vector shared-memory
+// loads for 16 FMAs; the next stage of rows is loaded into registers while
+// the current one is consumed, and two shared buffers alternate (one
+// barrier per stage).  Each entry is the same row-ascending FMA chain as a
+// one-output-per-thread loop.
 template <typename T>
 __device__ __forceinline__ void gram_tile_body(long long n, int pa, int qb, long long rows_per,
                                                const T *__restrict__ A, const T *__restrict__ B,
                                                double *__restrict__ part, int tile, int chunk) {
-  __shared__ T As[kTileK][kTile];
-  __shared__ T Bs[kTileK][kTile];
+  constexpr int SK = kTileK;
+  __shared__ __align__(16) T As[2][SK][kTile];
+  __shared__ __align__(16) T Bs[2][SK][kTile];
   const int tq = (qb + kTile - 1) / kTile;
   const int ta = tile / tq, tb = tile % tq;
   const long long r0 = chunk * rows_per;
@@ -57,39 +83,57 @@ __device__ __forceinline__ void gram_tile_body(long long n, int pa, int qb, long
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0;
-  for (long long r = r0; r < r1; r += kTileK) {
+  constexpr int kPer = SK * kTile / 256;         // staged values per thread and operand
+  T ra[kPer], rb[kPer];
+  auto fetch = [&](long long r) {
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
+    for (int t = 0; t < kPer; ++t) {
       const int idx = tid + t * 256;
       const int rr = idx >> 6, cc = idx & 63;
       const long long row = r + rr;
       const bool rowok = row < r1;
-      As[rr][cc] = (rowok && a0 + cc < pa) ? A[row * pa + a0 + cc] : (T)0;
-      Bs[rr][cc] = (rowok && b0 + cc < qb) ? B[row * qb + b0 + cc] : (T)0;
+      ra[t] = (rowok && a0 + cc < pa) ? A[row * pa + a0 + cc] : (T)0;
+      rb[t] = (rowok && b0 + cc < qb) ? B[row * qb + b0 + cc] : (T)0;
     }
-    __syncthreads();
+  };
+  auto stash = [&](int buf) {
 #pragma unroll
-    for (int rr = 0; rr < kTileK; ++rr) {
+    for (int t = 0; t < kPer; ++t) {
+      const int idx = tid + t * 256;
+      As[buf][idx >> 6][idx & 63] = ra[t];
+      Bs[buf][idx >> 6][idx & 63] = rb[t];
+    }
+  };
+  if (r0 < r1) {
+    fetch(r0);
+    stash(0);
+  }
+  __syncthreads();
+  int buf = 0;
+  for (long long r = r0; r < r1; r += SK, buf ^= 1) {
+    const bool more = r + SK < r1;
+    if (more) fetch(r + SK);
+#pragma unroll
+    for (int rr = 0; rr < SK; ++rr) {
       T av[4], bv[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) av[i] = As[rr][ty + 16 * i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) bv[j] = Bs[rr][tx + 16 * j];
+      ld4(&As[buf][rr][4 * ty], av);
+      ld4(&Bs[buf][rr][4 * tx], bv);
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
     }
+    if (more) stash(buf ^ 1);
     __syncthreads();
   }
   double *dst = part + (long long)chunk * pa * qb;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const int a = a0 + ty + 16 * i;
+    const int a = a0 + 4 * ty + i;
     if (a >= pa) continue;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int b = b0 + tx + 16 * j;
+      const int b = b0 + 4 * tx + j;
       if (b < qb) dst[(long long)a * qb + b] = (double)acc[i][j];
     }
   }
@@ -292,6 +336,15 @@ ks_status launch_gram(Problem &P, const T *A, int pa, const T *B, int qb, double
 // TC is the type of the coefficients C1, C2: double, or float copies made
 // once per update for the FP32 phase (converting in every block would put
 // a conversion per staged element on the FP64 pipe).
+// One 64 x 64 output tile: thread (ty, tx) owns rows r0 + 4ty + i and
+// columns c0 + 4tx + j.  The A slice is stored transposed (K-rows of 64
+// rows, padded to keep the vector loads aligned) and the C slice as is, so a
+// K-step costs two vector loads for 16 FMAs; stages of K-values run over
+// A1 C1 then A2 C2, the next one loaded into registers while the current
+// one is consumed (two shared buffers, one barrier per stage).  Each entry
+// is the same K-ascending FMA chain as before.
+constexpr int kAtLd = kTile + 4;
+
 template <typename T, typename TC>
 __device__ __forceinline__ void combine_tile_body(long long n, int q, const T *__restrict__ A1,
                                                   int k1, const TC *__restrict__ C1,
@@ -299,8 +352,9 @@ __device__ __forceinline__ void combine_tile_body(long long n, int q, const T *_
                                                   const TC *__restrict__ C2, double alpha_d,
                                                   double beta_d, const T *__restrict__ Bm,
                                                   T *__restrict__ out, int bx, int by) {
-  __shared__ T As[kTile][kTileK + 1];
-  __shared__ T Cs[kTileK][kTile];
+  constexpr int SK = stage_k<T>();
+  __shared__ __align__(16) T At[2][SK][kAtLd];
+  __shared__ __align__(16) T Cs[2][SK][kTile];
   const T alpha = (T)alpha_d, beta = (T)beta_d;
   const long long r0 = (long long)bx * kTile;
   const int c0 = by * kTile;
@@ -310,44 +364,64 @@ __device__ __forceinline__ void combine_tile_body(long long n, int q, const T *_
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0;
-  for (int op = 0; op < 2; ++op) {
-    const T *A = op == 0 ? A1 : A2;
-    const TC *C = op == 0 ? C1 : C2;
-    const int kk = op == 0 ? k1 : k2;
-    if (A == nullptr) continue;
-    for (int k0 = 0; k0 < kk; k0 += kTileK) {
+  const int s1 = (k1 + SK - 1) / SK;
+  const int s2 = A2 ? (k2 + SK - 1) / SK : 0;
+  const int stages = s1 + s2;
+  constexpr int kPer = SK * kTile / 256;         // staged values per thread and operand
+  T ra[kPer], rc[kPer];
+  auto fetch = [&](int s) {
+    const bool first = s < s1;
+    const T *A = first ? A1 : A2;
+    const TC *C = first ? C1 : C2;
+    const int kk = first ? k1 : k2;
+    const int k0 = (first ? s : s - s1) * SK;
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const int idx = tid + t * 256;
-        const int rr = idx >> 4, cc = idx & 15;          // A tile: 64 rows x 16
-        const long long row = r0 + rr;
-        As[rr][cc] = (row < n && k0 + cc < kk) ? A[row * kk + k0 + cc] : (T)0;
-        const int cr = idx >> 6, ccol = idx & 63;         // C tile: 16 x 64
-        Cs[cr][ccol] = (k0 + cr < kk && c0 + ccol < q) ? (T)C[(long long)(k0 + cr) * q + c0 + ccol] : (T)0;
-      }
-      __syncthreads();
-#pragma unroll
-      for (int t = 0; t < kTileK; ++t) {
-        T av[4], cv[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) av[i] = As[ty + 16 * i][t];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) cv[j] = Cs[t][tx + 16 * j];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], cv[j], acc[i][j]);
-      }
-      __syncthreads();
+    for (int t = 0; t < kPer; ++t) {
+      const int idx = tid + t * 256;
+      const int rr = idx / SK, cc = idx % SK;              // A slice: 64 rows x SK
+      const long long row = r0 + rr;
+      ra[t] = (row < n && k0 + cc < kk) ? A[row * kk + k0 + cc] : (T)0;
+      const int cr = idx >> 6, ccol = idx & 63;            // C slice: SK x 64
+      rc[t] = (k0 + cr < kk && c0 + ccol < q) ? (T)C[(long long)(k0 + cr) * q + c0 + ccol] : (T)0;
     }
+  };
+  auto stash = [&](int buf) {
+#pragma unroll
+    for (int t = 0; t < kPer; ++t) {
+      const int idx = tid + t * 256;
+      At[buf][idx % SK][idx / SK] = ra[t];
+      Cs[buf][idx >> 6][idx & 63] = rc[t];
+    }
+  };
+  if (stages > 0) {
+    fetch(0);
+    stash(0);
+  }
+  __syncthreads();
+  for (int s = 0; s < stages; ++s) {
+    const int buf = s & 1;
+    const bool more = s + 1 < stages;
+    if (more) fetch(s + 1);
+#pragma unroll
+    for (int t = 0; t < SK; ++t) {
+      T av[4], cv[4];
+      ld4(&At[buf][t][4 * ty], av);
+      ld4(&Cs[buf][t][4 * tx], cv);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], cv[j], acc[i][j]);
+    }
+    if (more) stash(buf ^ 1);
+    __syncthreads();
   }
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const long long row = r0 + ty + 16 * i;
+    const long long row = r0 + 4 * ty + i;
     if (row >= n) continue;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int col = c0 + tx + 16 * j;
+      const int col = c0 + 4 * tx + j;
       if (col >= q) continue;
       T v = alpha * acc[i][j];
       if (Bm) v = fma(beta, Bm[row * q + col], v);

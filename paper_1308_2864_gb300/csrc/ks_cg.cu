@@ -146,35 +146,38 @@ __device__ bool apply_precond(const CgArgs &a, long long tid, long long stride, 
 // barriers per application instead of six.
 constexpr int kFusedMaxN = 128;
 
-static_assert(kCgThreads == 256, "smem_matmul maps 256 threads to 8 x 32");
+// out = A B for N x N row-major matrices in shared memory (kCgThreads
+// threads, W = kCgThreads / 32 warps).  Each thread keeps a (64/W) x 2
+// block of outputs in registers (rows ty + W a, columns tx + 32 b of a 64 x 64
+// tile), so a k step costs 64/W broadcast loads of A and 2 conflict-free
+// loads of B for 128/W FMAs.  Every output is the same k-ascending FMA chain
+// as the one-output-per-thread form.
+constexpr int kCgWarps = kCgThreads / 32;
+constexpr int kRowsPerThread = 64 / kCgWarps;
+static_assert(64 % kCgWarps == 0, "warps must divide the 64-row tile");
 
-// out = A B for N x N row-major matrices in shared memory (256 threads).
-// Each thread keeps an 8 x 2 block of outputs in registers (rows ty + 8a,
-// columns tx + 32b of a 64 x 64 tile), so a k step costs 8 broadcast loads
-// of A and 2 conflict-free loads of B for 16 FMAs.  Every output is the
-// same k-ascending FMA chain as the one-output-per-thread form.
 __device__ __forceinline__ void smem_matmul(const float *A, const float *B, float *out, int N) {
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   for (int ib = 0; ib < N; ib += 64)
     for (int jb = 0; jb < N; jb += 64) {
-      float acc[8][2];
+      float acc[kRowsPerThread][2];
 #pragma unroll
-      for (int a = 0; a < 8; ++a) acc[a][0] = acc[a][1] = 0.f;
+      for (int a = 0; a < kRowsPerThread; ++a) acc[a][0] = acc[a][1] = 0.f;
       const int j0 = jb + tx, j1 = jb + tx + 32;
       for (int k = 0; k < N; ++k) {
         const float b0 = j0 < N ? B[k * N + j0] : 0.f;
         const float b1 = j1 < N ? B[k * N + j1] : 0.f;
 #pragma unroll
-        for (int a = 0; a < 8; ++a) {
-          const int i = ib + ty + 8 * a;
+        for (int a = 0; a < kRowsPerThread; ++a) {
+          const int i = ib + ty + kCgWarps * a;
           const float av = i < N ? A[i * N + k] : 0.f;
           acc[a][0] = fmaf(av, b0, acc[a][0]);
           acc[a][1] = fmaf(av, b1, acc[a][1]);
         }
       }
 #pragma unroll
-      for (int a = 0; a < 8; ++a) {
-        const int i = ib + ty + 8 * a;
+      for (int a = 0; a < kRowsPerThread; ++a) {
+        const int i = ib + ty + kCgWarps * a;
         if (i >= N) continue;
         if (j0 < N) out[i * N + j0] = acc[a][0];
         if (j1 < N) out[i * N + j1] = acc[a][1];

@@ -68,6 +68,9 @@ __device__ __forceinline__ void grid_reduce_tail(const double *part, int nb, int
   if (threadIdx.x == 0) *counter = 0u;
 }
 
+// Polls of a grid-barrier wait before the waiting thread starts to sleep.
+constexpr long long kSpinFree = 1 << 14;
+
 __device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int *p) {
   unsigned int v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -92,15 +95,19 @@ __device__ __forceinline__ bool grid_barrier_n(GridBarrier *bar, int *status, un
       __threadfence();
       atomicAdd(&bar->gen, 1u);
     } else {
+      // poll without sleeping first (a barrier between short phases is
+      // usually released within a few microseconds), then back off
       long long spins = 0;
-      unsigned int ns = 8;
+      unsigned int ns = 32;
       while (ld_acquire_gpu(&bar->gen) == gen) {
         if (++spins > kSpinLimit) {
           atomicCAS(status, 0, (int)KS_ETIMEOUT);
           break;
         }
-        __nanosleep(ns);
-        if (ns < 256) ns <<= 1;
+        if (spins > kSpinFree) {
+          __nanosleep(ns);
+          if (ns < 256) ns <<= 1;
+        }
       }
     }
     __threadfence();
