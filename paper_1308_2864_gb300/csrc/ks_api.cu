@@ -344,7 +344,9 @@ static ks_status run_phase(Problem &P, const T *Xstart, T *Xend, const ks_opts &
       KS_TRY(retract<T>(P, o.retraction, X(0), D(0), tau, X(2)));
       KS_TRY(evaluate<T>(P, X(2), EX(1), MX(2), &Et));
       cg_total += P.last_cg_iters;
-      if (Et <= C - o.rho1 * tau * tr.dnorm2 || h == o.max_backtrack) break;
+      if (Et <= C - o.rho1 * tau * tr.dnorm2 + armijo_slack<T>(P.last_parts) ||
+          h == o.max_backtrack)
+        break;
       tau *= o.delta;
       ++h;
     }

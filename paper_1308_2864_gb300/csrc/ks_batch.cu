@@ -279,7 +279,10 @@ ks_status run_phase(Batch &B, std::vector<JobState> &S, const ks_opts &o, double
           search[j] = 0;
           continue;
         }
-        if (s.Et <= s.C - o.rho1 * s.tau * s.dnorm2 || s.h == o.max_backtrack) {
+        const double parts[5] = {sc(B, j, SC_EKIN), sc(B, j, SC_EEXT), sc(B, j, SC_EH),
+                                 sc(B, j, SC_EXC), eii[j]};
+        if (s.Et <= s.C - o.rho1 * s.tau * s.dnorm2 + armijo_slack<T>(parts) ||
+            s.h == o.max_backtrack) {
           search[j] = 0;
         } else {
           s.tau *= o.delta;

@@ -240,6 +240,19 @@ enum Block { B_X0 = 0, B_X1, B_X2, B_MX0, B_MX1, B_MX2, B_EX0, B_EX1, B_G, B_D0,
 // 6 p^2 are scratch of the factor kernels.
 enum Small { S_WORK = 0, S_S = 6, S_DMD, S_O, S_A, S_B, S_C1, S_C2, S_T, S_COUNT };
 
+// Slack of the Armijo test for the rounding of the energy sums: in the FP64
+// phase a trial is not rejected for a rise below 4 eps sum |E_parts| (near
+// convergence the required decrease rho1 tau ||D||^2 falls below the
+// rounding of E, and an exact-arithmetic test would backtrack at random);
+// the FP32 phase keeps the strict test, so that it stalls and hands over.
+template <typename T>
+inline double armijo_slack(const double *parts) {
+  if (sizeof(T) != 8) return 0.0;
+  double a = 0.0;
+  for (int i = 0; i < 5; ++i) a += parts[i] < 0 ? -parts[i] : parts[i];
+  return 4.0 * 2.220446049250313e-16 * a;
+}
+
 // ---------------------------------------------------------------- batch
 // A job table of independent systems advanced together (ks_batch_*): every
 // launch of a step covers all jobs whose active flag is set.  Each job keeps
