@@ -36,6 +36,14 @@ METRIC = "time-to-||grad||<=1e-6 & solves/s, p50/p99 latency; mixed vs plain FP6
 WORKLOAD = "c2: cube 20 bohr, 64^3 Q1 grid, 32 atoms Z=4 jittered 4x4x2 lattice, p=64, Slater+PZ81, QR"
 GTOL = 1e-6
 MAXIT = 300
+# jobs of the batched-jobs recipe (seed 1003) that reach ||D||_M <= 1e-6 in
+# a few thousand iterations (1-9 s each)
+C4_TTS_JOBS = (1, 2, 4, 5)
+# DRAM bytes per launch of the FP64 update kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum of one ncu capture of its projection and retraction
+# launches on this workload, mean of the two; profiles/combine_c2_fp64.md).
+# Must be re-measured (or set to None) whenever that kernel changes.
+COMBINE_FP64_TRAFFIC_BYTES = 3.695e8
 
 
 def dist_env():
@@ -244,6 +252,38 @@ def run_gpu(args):
     c1_out["energy_difference_Ha"] = c1_out["mixed"]["energy"] - c1_out["fp64"]["energy"]
     P1.close()
 
+    # time to ||D||_M <= 1e-6 on converging systems of the batched-jobs
+    # recipe (grids 24^3..38^3, p = 26..32): plain FP64 against the mixed form
+    c4_out = {"jobs": [], "fp64_s": 0.0, "mixed_s": 0.0}
+    c4_jobs = ki.config_c4_jobs(njobs=8)
+    for j in C4_TTS_JOBS:
+        sj = c4_jobs[j]
+        with torch.cuda.stream(stream):
+            Pj = ks.Problem.from_system(sj, stream=stream)
+            Xj0 = torch.from_numpy(np.ascontiguousarray(sj.x0())).cuda()
+            Yj = torch.empty_like(Xj0)
+        row = {"job": j, "N": sj.N, "p": sj.p}
+        for prec in ("fp64", "mixed"):
+            o = dict(retraction="qr", gtol=GTOL, maxit=20000, precision=prec)
+            with torch.cuda.stream(stream):
+                Yj.copy_(Xj0)
+                Pj.minimize(Yj, **{**o, "maxit": 3})         # warm-up
+                Yj.copy_(Xj0)
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev1 = torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+                rj = Pj.minimize(Yj, **o)
+                ev1.record(stream)
+                ev1.synchronize()
+            secs = ev0.elapsed_time(ev1) / 1e3
+            row[prec] = {"seconds": secs, "iters": rj["iters"], "energy": rj["E"],
+                         "converged": rj["status"] == 0, "fp32_phase_iters": rj["mixed_iters"]}
+            c4_out[prec + "_s"] += secs
+        row["energy_difference_Ha"] = row["mixed"]["energy"] - row["fp64"]["energy"]
+        c4_out["jobs"].append(row)
+        Pj.close()
+    c4_out["speedup"] = c4_out["fp64_s"] / max(c4_out["mixed_s"], 1e-12)
+
     # end to end through the host entry point: X0 from pinned host memory in,
     # the final block back out, every step
     x0_np = s.x0()
@@ -274,7 +314,8 @@ def run_gpu(args):
     fp64_peak = 152 * 4 * 2.07e9 / 1e12       # TFLOP/s: 2 DFMA/clk/SM at 2070 MHz
     achieved = dfl / (dms / 1e3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-            "frac": achieved / fp64_peak, "traffic": None,
+            "frac": achieved / fp64_peak,
+            "traffic": COMBINE_FP64_TRAFFIC_BYTES if name == "combine" else None,
             "kernel": f"{name} (FP64)", "launches": dcnt,
             "peak_note": "FP64 FMA peak derived from 152 SMs x 4 flop/clk x 2.07 GHz "
                          "(probe measured 1.20 TFLOP/s at 1.99 GHz)"}
@@ -305,7 +346,8 @@ def run_gpu(args):
                              "final_gradnorm": rm["gradnorm"], "final_energy": rm["E"],
                              "energy_minus_fp64_Ha": rm["E"] - r0["E"],
                              "kernel_shares": mixed_kernel},
-                   "c1_time_to_solution": c1_out},
+                   "c1_time_to_solution": c1_out,
+                   "c4_time_to_solution": c4_out},
         "roofline": roof,
         "kernel_shares": shares,
         "cpu_baseline": {"value": cpu_value, "unit": "solves/s", "cores": threads, "kind": "oracle",
