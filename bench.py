@@ -39,10 +39,10 @@ MAXIT = 300
 # jobs of the batched-jobs recipe (seed 1003) that reach ||D||_M <= 1e-6 in
 # a few thousand iterations (1-9 s each)
 C4_TTS_JOBS = (1, 2, 4, 5)
-# DRAM bytes per launch of the FP64 update kernel (dram__bytes_read.sum +
+# DRAM bytes per launch of the FP64 update kernel: dram__bytes_read.sum +
 # dram__bytes_write.sum of one ncu capture of its projection and retraction
-# launches on this workload, mean of the two; profiles/combine_c2_fp64.md).
-# Must be re-measured (or set to None) whenever that kernel changes.
+# launches on this workload (mean of the two).  Must be re-measured, or set
+# to None, whenever that kernel changes.
 COMBINE_FP64_TRAFFIC_BYTES = 3.695e8
 
 

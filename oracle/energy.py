@@ -4,7 +4,8 @@ Continuous functional: Eq. EKS, E = T_KS + E_H + E_xc + E_ext + E_II
 (Sec. 2.1).  Discrete form: Sec. 2.3 gives
   E(X) = 1/2 tr(X^T L X) + tr(X^T E X) + 1/2 rho^T L^+ rho + rho^T eps_xc(rho),
   rho(X) = diag(X X^T),  E_X = H(X) X.
-Restated for Q1 elements with occupation f (readings listed in the design doc):
+Restated for Q1 elements with occupation f (where the paper is silent, the
+choices are stated here):
 
   rho_k  = f sum_i X_ki^2                               (nodal density)
   E(X)   = (f/2) tr(X^T K X)                              kinetic
