@@ -278,6 +278,24 @@ ks_status ks_batch_create(const ks_problem_desc *descs, int njobs, void *stream,
 /* Device bytes held by the batch. */
 size_t ks_batch_bytes(const ks_batch *batch);
 
+/* 1 (default): the step sequences of an iteration (trial step + energy,
+ * projection) run as CUDA graphs captured on first use per block-rotation
+ * state and replayed (a captured energy evaluation holds three Hartree CG
+ * iterations; jobs that need more continue outside the graph); 0: plain
+ * launches.  Both give the same results bitwise.  Graphs are not used while
+ * ks_profile_start timing is on. */
+ks_status ks_batch_set_graphs(ks_batch *batch, int enable);
+
+/* Autotuner of the batched launch shapes: times candidates of the Gram rows
+ * per block (1024..16384), the update's outputs per thread (2..16), the
+ * potential's nodes per thread (1..8) and the stencil's planes per block
+ * (default, 8..64) on this job table and keeps the fastest of each (out, may
+ * be NULL: the four choices).  Overwrites the jobs' device blocks (call it
+ * before ks_batch_minimize).  A tuned batch gives each job a decomposition
+ * chosen from the whole table's timings, so results agree with an untuned
+ * run up to the order of sums only. */
+ks_status ks_batch_autotune(ks_batch *batch, int out[4]);
+
 /* Minimise every job from X_inout[j] (HOST, n_j x p_j row-major FP64; the
  * result overwrites it).  opts as for ks_minimize (retraction must be KS_QR;
  * KS_MIXED runs the FP32 phase for all jobs, then the FP64 polish for the

@@ -119,6 +119,8 @@ SIGNATURES = [
     ("ks_server_destroy", _I, [_P]),
     ("ks_batch_create", _I, [ctypes.POINTER(ProblemDesc), _I, _P, ctypes.POINTER(_P)]),
     ("ks_batch_bytes", ctypes.c_size_t, [_P]),
+    ("ks_batch_set_graphs", _I, [_P, _I]),
+    ("ks_batch_autotune", _I, [_P, ctypes.POINTER(_I)]),
     ("ks_batch_minimize", _I, [_P, ctypes.POINTER(_DP), ctypes.POINTER(Opts),
                                ctypes.POINTER(Result)]),
     ("ks_batch_destroy", _I, [_P]),
@@ -541,6 +543,17 @@ class Batch:
     @property
     def bytes(self) -> int:
         return load_library().ks_batch_bytes(self._h)
+
+    def autotune(self) -> dict:
+        """Time the candidate launch shapes on this job table and keep the fastest."""
+        out = (_I * 4)()
+        _check(load_library().ks_batch_autotune(self._h, out))
+        return {"gram_rows": out[0], "comb_per_thread": out[1], "pot_per_thread": out[2],
+                "stencil_planes": out[3]}
+
+    def set_graphs(self, enable: bool):
+        """Replay the step sequences as CUDA graphs (default) or launch them plainly."""
+        _check(load_library().ks_batch_set_graphs(self._h, 1 if enable else 0))
 
     def minimize(self, X0=None, **opts):
         """Minimise every job from X0[j] (default s.x0()); returns (list of

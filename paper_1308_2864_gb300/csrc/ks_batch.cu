@@ -57,6 +57,60 @@ ks_status upload(Batch &B, void *dst, const void *src, size_t bytes) {
   return KS_OK;
 }
 
+// Device scalars, status words and the CG's remaining-job count to the
+// pinned host mirrors (capturable: fixed addresses, no synchronisation).
+ks_status copy_scalars(Batch &B) {
+  KS_CUDA_TRY(cudaMemcpyAsync(B.scal_host, B.scal_dev, sizeof(double) * SC_COUNT * B.J,
+                              cudaMemcpyDeviceToHost, B.stream));
+  KS_CUDA_TRY(cudaMemcpyAsync(B.status_host, B.status_dev, sizeof(int) * B.J,
+                              cudaMemcpyDeviceToHost, B.stream));
+  KS_CUDA_TRY(cudaMemcpyAsync(B.cg_remaining_host, B.cg_remaining_dev, sizeof(int),
+                              cudaMemcpyDeviceToHost, B.stream));
+  return KS_OK;
+}
+
+ks_status wait_batch(Batch &B) {
+  KS_CUDA_TRY(cudaStreamSynchronize(B.stream));
+  B.ring_used = 0;
+  prof_collect();
+  return KS_OK;
+}
+
+// Graph kinds of the captured step sequences.
+enum GraphKind { G_TRIAL = 1, G_EVAL, G_PROJECT };
+constexpr int kGraphCgIters = 3;   // CG iterations inside a captured evaluation
+
+bool graphs_usable(const Batch &B) { return B.use_graphs && !prof_enabled(); }
+
+// Run `issue` (launches on B.stream only) through the graph cached under
+// `key`, capturing it on first use.
+template <typename F>
+ks_status replay(Batch &B, const std::array<int, 14> &key, F issue) {
+  auto it = B.graphs.find(key);
+  if (it == B.graphs.end()) {
+    const unsigned long long l0 = ks_kernel_launches();
+    KS_CUDA_TRY(cudaStreamBeginCapture(B.stream, cudaStreamCaptureModeThreadLocal));
+    const ks_status st = issue();
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(B.stream, &g);
+    const long long nl = (long long)(ks_kernel_launches() - l0);
+    count_launches(-nl);
+    if (st != KS_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture");
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t e2 = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e2 != cudaSuccess) return cuda_error(e2, "cudaGraphInstantiate");
+    it = B.graphs.emplace(key, std::make_pair(exec, nl)).first;
+  }
+  KS_CUDA_TRY(cudaGraphLaunch(it->second.first, B.stream));
+  count_launches(it->second.second);
+  return KS_OK;
+}
+
 ks_status upload_mask(Batch &B, const std::vector<unsigned char> &m) {
   for (int j = 0; j < B.J; ++j) B.active_host[j] = m[j];
   return upload(B, B.active_dev, m.data(), (size_t)B.J);
@@ -125,15 +179,61 @@ ks_status check_status(Batch &B, std::vector<JobState> &S, const std::vector<uns
   return KS_OK;
 }
 
+// Energy of the jobs in the mask at slot sX: density, Hartree PCG,
+// potential and energy sums, Hamiltonian stencil, scalars to the host.
+template <typename T>
+ks_status launch_evaluate(Batch &B, int sX, int sEX, int sMX, int cg_iters) {
+  KS_TRY(batch_density<T>(B, sX));
+  KS_TRY(batch_cg_launch(B, cg_iters));
+  KS_TRY(batch_potential(B, sizeof(T) == 4));
+  KS_TRY(batch_hamiltonian<T>(B, sX, sEX, sMX));
+  return copy_scalars(B);
+}
+
+// QR retraction of the jobs in the mask (step B.tau_dev) into slot sOut.
+template <typename T>
+ks_status launch_retract(Batch &B, int sX, int sD, int sOut) {
+  KS_TRY(batch_qr_factor(B, S_DMD, -1, true, S_C1, S_C2));
+  return batch_combine<T>(B, sX, S_C1, sD, S_C2, 1.0, 0.0, -1, sOut);
+}
+
+// Runs the evaluation (after a retraction into sX when `trial_from` gives
+// the current and direction slots), through a cached graph when possible.
+// A graph holds kGraphCgIters CG iterations; jobs whose CG needs more
+// continue outside it, after which the potential and stencil are redone.
+template <typename T>
+ks_status run_evaluate(Batch &B, double cg_tol, int sX, int sEX, int sMX, int rX, int rD) {
+  KS_TRY(batch_cg_upload(B, cg_tol));
+  if (graphs_usable(B)) {
+    const std::array<int, 14> key = {rX >= 0 ? G_TRIAL : G_EVAL, (int)sizeof(T), sX, sEX, sMX,
+                                     rX, rD, kGraphCgIters, 0, 0, 0, 0, 0, 0};
+    KS_TRY(replay(B, key, [&]() -> ks_status {
+      if (rX >= 0) KS_TRY(launch_retract<T>(B, rX, rD, sX));
+      return launch_evaluate<T>(B, sX, sEX, sMX, kGraphCgIters);
+    }));
+    KS_TRY(wait_batch(B));
+    if (*B.cg_remaining_host == 0) return KS_OK;
+    KS_TRY(batch_cg_continue(B));
+    KS_TRY(batch_potential(B, sizeof(T) == 4));
+    KS_TRY(batch_hamiltonian<T>(B, sX, sEX, sMX));
+    KS_TRY(copy_scalars(B));
+    return wait_batch(B);
+  }
+  if (rX >= 0) KS_TRY(launch_retract<T>(B, rX, rD, sX));
+  KS_TRY(batch_density<T>(B, sX));
+  KS_TRY(batch_cg_launch(B, 0));
+  KS_TRY(batch_cg_continue(B));
+  KS_TRY(batch_potential(B, sizeof(T) == 4));
+  KS_TRY(batch_hamiltonian<T>(B, sX, sEX, sMX));
+  KS_TRY(copy_scalars(B));
+  return wait_batch(B);
+}
+
 template <typename T>
 ks_status evaluate(Batch &B, std::vector<JobState> &S, const std::vector<unsigned char> &mask,
                    double cg_tol, const std::vector<double> &eii, int sX, int sEX, int sMX,
-                   bool trial) {
-  KS_TRY(batch_density<T>(B, sX));
-  KS_TRY(batch_cg(B, cg_tol));
-  KS_TRY(batch_potential(B, sizeof(T) == 4));
-  KS_TRY(batch_hamiltonian<T>(B, sX, sEX, sMX));
-  KS_TRY(sync_batch(B));
+                   bool trial, int rX = -1, int rD = -1) {
+  KS_TRY(run_evaluate<T>(B, cg_tol, sX, sEX, sMX, rX, rD));
   KS_TRY(check_status(B, S, mask));
   for (int j = 0; j < B.J; ++j) {
     if (!mask[j] || !S[j].running) continue;
@@ -154,8 +254,7 @@ ks_status evaluate(Batch &B, std::vector<JobState> &S, const std::vector<unsigne
 // G = M^{-1} E_X, S = E_X^T X, D = G - X S, MD = M D with ||D||_M^2 and the
 // BB traces, D^T M D.
 template <typename T>
-ks_status project(Batch &B, std::vector<JobState> &S, const std::vector<unsigned char> &mask,
-                  const Slots &sl, bool prev) {
+ks_status launch_project(Batch &B, const Slots &sl, bool prev) {
   KS_TRY(batch_mass_inverse<T>(B, sl.iex[0], B_G));
   KS_TRY(batch_gram<T>(B, sl.iex[0], sl.ix[0], S_S));
   KS_TRY(batch_combine<T>(B, sl.ix[0], S_S, -1, -1, -1.0, 1.0, B_G, sl.id[0]));
@@ -165,7 +264,21 @@ ks_status project(Batch &B, std::vector<JobState> &S, const std::vector<unsigned
   else
     KS_TRY(batch_mass_dots<T>(B, sl.id[0], sl.imd[0], -1, -1, -1, -1, -1, -1));
   KS_TRY(batch_gram<T>(B, sl.id[0], sl.imd[0], S_DMD));
-  KS_TRY(sync_batch(B));
+  return copy_scalars(B);
+}
+
+template <typename T>
+ks_status project(Batch &B, std::vector<JobState> &S, const std::vector<unsigned char> &mask,
+                  const Slots &sl, bool prev) {
+  if (graphs_usable(B)) {
+    const std::array<int, 14> key = {G_PROJECT, (int)sizeof(T), sl.iex[0], sl.ix[0], sl.id[0],
+                                     sl.imd[0], sl.imx[0], sl.ix[1], sl.imx[1], sl.id[1],
+                                     sl.imd[1], prev ? 1 : 0, 0, 0};
+    KS_TRY(replay(B, key, [&]() { return launch_project<T>(B, sl, prev); }));
+  } else {
+    KS_TRY(launch_project<T>(B, sl, prev));
+  }
+  KS_TRY(wait_batch(B));
   KS_TRY(check_status(B, S, mask));
   for (int j = 0; j < B.J; ++j) {
     if (!mask[j] || !S[j].running) continue;
@@ -269,9 +382,8 @@ ks_status run_phase(Batch &B, std::vector<JobState> &S, const ks_opts &o, double
     while (any(search)) {
       KS_TRY(upload_mask(B, search));
       KS_TRY(upload_tau(B, tau));
-      KS_TRY(batch_qr_factor(B, S_DMD, -1, true, S_C1, S_C2));
-      KS_TRY(batch_combine<T>(B, sl.ix[0], S_C1, sl.id[0], S_C2, 1.0, 0.0, -1, sl.ix[2]));
-      KS_TRY(evaluate<T>(B, S, search, cg_tol, eii, sl.ix[2], sl.iex[1], sl.imx[2], true));
+      KS_TRY(evaluate<T>(B, S, search, cg_tol, eii, sl.ix[2], sl.iex[1], sl.imx[2], true,
+                         sl.ix[0], sl.id[0]));
       for (int j = 0; j < B.J; ++j) {
         if (!search[j]) continue;
         JobState &s = S[j];
@@ -368,7 +480,8 @@ ks_status build_maps(Batch &B) {
     const Problem &P = B.probs[j]->P;
     const long long n = b.n, p = b.p;
     put(BM_DENSITY, j, (n + 255) / 256);
-    long long pot = (n + 1023) / 1024;
+    const long long per_pot = 256LL * B.tune.pot_per_thread;
+    long long pot = (n + per_pot - 1) / per_pot;
     if (pot > 64) pot = 64;
     if (pot < 1) pot = 1;
     b.pot_nb = (int)pot;
@@ -376,7 +489,7 @@ ks_status build_maps(Batch &B) {
     const int cls = p >= 32 ? BM_ST32 : p >= 16 ? BM_ST16 : p >= 8 ? BM_ST8 : BM_ST4;
     put(cls, j, b.st_nb);
     put(BM_THOMAS, j, ((long long)b.N * b.N * p + 255) / 256);
-    long long chunks = (n + 4095) / 4096;
+    long long chunks = (n + B.tune.gram_rows - 1) / B.tune.gram_rows;
     const long long cap = (long long)(P.partials_len / (size_t)(p * p));
     if (chunks > cap) chunks = cap;
     if (chunks < 1) chunks = 1;
@@ -391,7 +504,8 @@ ks_status build_maps(Batch &B) {
     else put(BM_GRAM_TILED, j, tiles * chunks);
     put(BM_GRAM_REDUCE, j, (8 * p * p + kThreads - 1) / kThreads);
     if (p <= 32) {
-      long long nb = (n * p + 2047) / 2048;
+      const long long per_comb = 256LL * B.tune.comb_per_thread;
+      long long nb = (n * p + per_comb - 1) / per_comb;
       if (nb < 1) nb = 1;
       b.comb_nb = (int)nb;
       put(BM_COMB_NARROW, j, nb);
@@ -417,6 +531,8 @@ ks_status build_maps(Batch &B) {
 
 void free_batch(Batch &B) {
   if (B.stream) cudaStreamSynchronize(B.stream);
+  for (auto &kv : B.graphs) cudaGraphExecDestroy(kv.second.first);
+  B.graphs.clear();
   for (ks_problem *p : B.probs) ks_problem_destroy(p);
   B.probs.clear();
   if (B.jobs_dev) cudaFree(B.jobs_dev);
@@ -558,6 +674,95 @@ ks_status ks_batch_create(const ks_problem_desc *descs, int njobs, void *stream,
 }
 
 size_t ks_batch_bytes(const ks_batch *kb) { return kb ? kb->B.bytes : 0; }
+
+// Autotuner: each launch shape in turn, every candidate timed with CUDA
+// events (one warm-up launch, then the mean of three) on the job table with
+// zeroed FP32 blocks; the fastest is kept.
+ks_status ks_batch_autotune(ks_batch *kb, int out[4]) {
+  if (!kb) return set_error(KS_EINVAL, "null batch");
+  Batch &B = kb->B;
+  std::vector<unsigned char> all(B.J, 1);
+  KS_TRY(upload_mask(B, all));
+  for (int j = 0; j < B.J; ++j) {
+    const Problem &P = B.probs[j]->P;
+    for (int b : {B_X0, B_X1, B_X2, B_EX0, B_MX0})
+      KS_CUDA_TRY(cudaMemsetAsync(P.blk[b], 0, sizeof(double) * P.n * P.p, B.stream));
+    KS_CUDA_TRY(cudaMemsetAsync(P.pp, 0, sizeof(double) * P.pp_len, B.stream));
+  }
+  cudaEvent_t e0, e1;
+  KS_CUDA_TRY(cudaEventCreate(&e0));
+  KS_CUDA_TRY(cudaEventCreate(&e1));
+  auto rebuild = [&]() -> ks_status {
+    KS_TRY(batch_stencil_geometry(B));
+    KS_TRY(build_maps(B));
+    KS_CUDA_TRY(cudaMemcpyAsync(B.jobs_dev, B.jobs_host.data(), sizeof(BJob) * B.J,
+                                cudaMemcpyHostToDevice, B.stream));
+    KS_CUDA_TRY(cudaMemcpyAsync(B.maps_dev, B.maps_host.data(), sizeof(int) * B.maps_host.size(),
+                                cudaMemcpyHostToDevice, B.stream));
+    return KS_OK;
+  };
+  auto time_it = [&](auto launch, float *ms) -> ks_status {
+    KS_TRY(launch());
+    KS_CUDA_TRY(cudaEventRecord(e0, B.stream));
+    for (int r = 0; r < 3; ++r) KS_TRY(launch());
+    KS_CUDA_TRY(cudaEventRecord(e1, B.stream));
+    KS_CUDA_TRY(cudaEventSynchronize(e1));
+    KS_CUDA_TRY(cudaEventElapsedTime(ms, e0, e1));
+    return KS_OK;
+  };
+  auto tune = [&](int *field, std::initializer_list<int> cands, auto launch) -> ks_status {
+    float best = 1e30f;
+    int best_v = *field;
+    for (int v : cands) {
+      *field = v;
+      const ks_status st = rebuild();
+      if (st != KS_OK) continue;                 // a candidate the partials cannot hold
+      float ms = 0.f;
+      KS_TRY(time_it(launch, &ms));
+      if (ms < best) {
+        best = ms;
+        best_v = v;
+      }
+    }
+    *field = best_v;
+    return rebuild();
+  };
+  ks_status st = KS_OK;
+  if (st == KS_OK)
+    st = tune(&B.tune.gram_rows, {1024, 2048, 4096, 8192, 16384},
+              [&]() { return batch_gram<float>(B, B_X0, B_X1, S_T); });
+  if (st == KS_OK)
+    st = tune(&B.tune.comb_per_thread, {2, 4, 8, 16}, [&]() {
+      return batch_combine<float>(B, B_X0, S_C1, B_X1, S_C2, 1.0, 0.0, -1, B_X2);
+    });
+  if (st == KS_OK)
+    st = tune(&B.tune.pot_per_thread, {1, 2, 4, 8}, [&]() { return batch_potential(B, true); });
+  if (st == KS_OK)
+    st = tune(&B.tune.st_planes, {0, 8, 16, 32, 64},
+              [&]() { return batch_hamiltonian<float>(B, B_X0, B_EX0, B_MX0); });
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  KS_TRY(st);
+  // the timings left the reduction counters re-armed; the graphs hold the
+  // old launch shapes
+  for (auto &kv : B.graphs) cudaGraphExecDestroy(kv.second.first);
+  B.graphs.clear();
+  KS_CUDA_TRY(cudaMemsetAsync(B.status_dev, 0, sizeof(int) * B.J, B.stream));
+  KS_CUDA_TRY(cudaStreamSynchronize(B.stream));
+  if (out) {
+    out[0] = B.tune.gram_rows;
+    out[1] = B.tune.comb_per_thread;
+    out[2] = B.tune.pot_per_thread;
+    out[3] = B.tune.st_planes;
+  }
+  return KS_OK;
+}
+
+ks_status ks_batch_set_graphs(ks_batch *kb, int enable) {
+  if (!kb || enable < 0 || enable > 1) return set_error(KS_EINVAL, "bad argument");
+  kb->B.use_graphs = enable != 0;
+  return KS_OK;
+}
 
 ks_status ks_batch_minimize(ks_batch *kb, double *const *X_inout, const ks_opts *opts_in,
                             ks_result *results) {

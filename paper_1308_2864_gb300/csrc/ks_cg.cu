@@ -732,8 +732,45 @@ ks_status batch_cg_setup(Batch &B) {
 }
 
 // Hartree solve of every active job (warm-started where B.warm says so) to
-// relative residual max(tol, the job's cg_tol).
-ks_status batch_cg(Batch &B, double tol) {
+// relative residual max(tol, the job's cg_tol), in three pieces so that the
+// launches can be captured in a CUDA graph:
+//   batch_cg_upload   per-job tolerance and warm flag (host -> device)
+//   batch_cg_launch   init + preconditioner + `iters` CG iterations and the
+//                     count of jobs still iterating (no host synchronisation)
+//   batch_cg_continue more iterations, one host check each, until no job is
+//                     left (after a synchronisation that read the count)
+static CgBatchView cg_view(Batch &B, int map) {
+  return CgBatchView{static_cast<const CgArgs *>(B.cg_args_dev),
+                     static_cast<CgState *>(B.cg_state_dev), B.map(map), B.J, B.active_dev,
+                     B.cg_tolw_dev, B.cg_counters};
+}
+
+static ks_status cg_precond_launch(Batch &B) {
+  const CgBatchView planes = cg_view(B, BM_CG_PLANES);
+  const int np = B.total(BM_CG_PLANES);
+  const size_t dyn = cg_dynamic_smem(B.maxN);
+  cg_b_precond<0><<<np, kCgThreads, dyn, B.stream>>>(planes);
+  cg_b_precond<1><<<np, kCgThreads, dyn, B.stream>>>(planes);
+  cg_b_precond<2><<<np, kCgThreads, dyn, B.stream>>>(planes);
+  KS_CUDA_TRY(cudaGetLastError());
+  return KS_OK;
+}
+
+static ks_status cg_iteration_launch(Batch &B) {
+  const CgBatchView nodes = cg_view(B, BM_CG_NODES);
+  const int nn = B.total(BM_CG_NODES);
+  ProfScope ps_(B.stream, KP_CG, 0.0, 0.0, 6);
+  cg_b_it1<<<nn, kCgThreads, 0, B.stream>>>(nodes);
+  cg_b_it2<<<nn, kCgThreads, 0, B.stream>>>(nodes);
+  KS_CUDA_TRY(cudaGetLastError());
+  KS_TRY(cg_precond_launch(B));
+  cg_b_count<<<1, 256, 0, B.stream>>>(static_cast<const CgState *>(B.cg_state_dev), B.active_dev,
+                                      B.J, B.cg_remaining_dev);
+  KS_CUDA_TRY(cudaGetLastError());
+  return KS_OK;
+}
+
+ks_status batch_cg_upload(Batch &B, double tol) {
   for (int j = 0; j < B.J; ++j) {
     const double t = tol > B.probs[j]->P.cg_tol ? tol : B.probs[j]->P.cg_tol;
     B.cg_tolw_host[2 * j] = t;
@@ -741,45 +778,42 @@ ks_status batch_cg(Batch &B, double tol) {
   }
   KS_CUDA_TRY(cudaMemcpyAsync(B.cg_tolw_dev, B.cg_tolw_host, sizeof(double) * 2 * B.J,
                               cudaMemcpyHostToDevice, B.stream));
-  CgBatchView nodes{static_cast<const CgArgs *>(B.cg_args_dev), static_cast<CgState *>(B.cg_state_dev),
-                    B.map(BM_CG_NODES), B.J, B.active_dev, B.cg_tolw_dev, B.cg_counters};
-  CgBatchView planes = nodes;
-  planes.start = B.map(BM_CG_PLANES);
-  const int nn = B.total(BM_CG_NODES), np = B.total(BM_CG_PLANES);
-  const size_t dyn = cg_dynamic_smem(B.maxN);
-  auto precond = [&]() -> ks_status {
-    cg_b_precond<0><<<np, kCgThreads, dyn, B.stream>>>(planes);
-    cg_b_precond<1><<<np, kCgThreads, dyn, B.stream>>>(planes);
-    cg_b_precond<2><<<np, kCgThreads, dyn, B.stream>>>(planes);
+  return KS_OK;
+}
+
+ks_status batch_cg_launch(Batch &B, int iters) {
+  const CgBatchView nodes = cg_view(B, BM_CG_NODES);
+  {
+    ProfScope ps_(B.stream, KP_CG, 0.0, 0.0, 5);
+    cg_b_init<<<B.total(BM_CG_NODES), kCgThreads, 0, B.stream>>>(nodes);
     KS_CUDA_TRY(cudaGetLastError());
-    return KS_OK;
-  };
+    KS_TRY(cg_precond_launch(B));
+    cg_b_count<<<1, 256, 0, B.stream>>>(static_cast<const CgState *>(B.cg_state_dev),
+                                        B.active_dev, B.J, B.cg_remaining_dev);
+    KS_CUDA_TRY(cudaGetLastError());
+  }
+  for (int it = 0; it < iters; ++it) KS_TRY(cg_iteration_launch(B));
+  return KS_OK;
+}
+
+ks_status batch_cg_continue(Batch &B) {
   int maxit = 0;
   for (int j = 0; j < B.J; ++j)
     if (B.active_host[j] && B.probs[j]->P.cg_maxit > maxit) maxit = B.probs[j]->P.cg_maxit;
-  {
-    ProfScope ps_(B.stream, KP_CG, 0.0, 0.0, 4);
-    cg_b_init<<<nn, kCgThreads, 0, B.stream>>>(nodes);
-    KS_CUDA_TRY(cudaGetLastError());
-    KS_TRY(precond());
-  }
   for (int it = 0; it < maxit; ++it) {
-    {
-      ProfScope ps_(B.stream, KP_CG, 0.0, 0.0, 6);
-      cg_b_it1<<<nn, kCgThreads, 0, B.stream>>>(nodes);
-      cg_b_it2<<<nn, kCgThreads, 0, B.stream>>>(nodes);
-      KS_CUDA_TRY(cudaGetLastError());
-      KS_TRY(precond());
-      cg_b_count<<<1, 256, 0, B.stream>>>(static_cast<const CgState *>(B.cg_state_dev),
-                                          B.active_dev, B.J, B.cg_remaining_dev);
-      KS_CUDA_TRY(cudaGetLastError());
-    }
     KS_CUDA_TRY(cudaMemcpyAsync(B.cg_remaining_host, B.cg_remaining_dev, sizeof(int),
                                 cudaMemcpyDeviceToHost, B.stream));
     KS_CUDA_TRY(cudaStreamSynchronize(B.stream));
     if (*B.cg_remaining_host == 0) break;
+    KS_TRY(cg_iteration_launch(B));
   }
   return KS_OK;
+}
+
+ks_status batch_cg(Batch &B, double tol) {
+  KS_TRY(batch_cg_upload(B, tol));
+  KS_TRY(batch_cg_launch(B, 0));
+  return batch_cg_continue(B);
 }
 
 size_t cg_dynamic_smem(int N) {

@@ -3,7 +3,9 @@
 
 #include <cuda_runtime.h>
 #include <cstddef>
+#include <array>
 #include <cstdint>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -161,6 +163,11 @@ struct ProfScope {
 };
 // Accumulate the timings of completed launches (call after a stream sync).
 void prof_collect();
+// Per-launch timing switched on (no graph capture while it is).
+bool prof_enabled();
+// Adjust the launch counter (graph replays add their kernels; a capture
+// removes the launches it recorded, which did not run).
+void count_launches(long long delta);
 
 // ---------------------------------------------------------------- kernels
 // ks_setup.cu
@@ -288,8 +295,17 @@ enum BMap {
   BM_GRAM_MID, BM_GRAM_TILED, BM_GRAM_REDUCE, BM_CG_NODES, BM_CG_PLANES, BM_COMB_NARROW, BM_COMB_TILED, BM_COEF, BM_COPY, BM_COUNT
 };
 
+// Launch shapes of the batched kernels that the autotuner chooses.
+struct BatchTuning {
+  int gram_rows = 4096;            // Gram rows per chunk (block)
+  int comb_per_thread = 8;         // narrow update: outputs per thread
+  int pot_per_thread = 4;          // potential: nodes per thread
+  int st_planes = 0;               // stencil planes per block (0: default geometry)
+};
+
 struct Batch {
   int J = 0, sms = 0, maxN = 0, maxp = 0;
+  BatchTuning tune;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   std::vector<ks_problem *> probs;
@@ -309,6 +325,10 @@ struct Batch {
   std::vector<unsigned char> warm; // per job: a previous Hartree potential exists
   char *ring_host = nullptr;       // pinned staging ring of the small uploads
   size_t ring_bytes = 0, ring_used = 0;
+  // CUDA graphs of the step sequences, keyed by sequence kind, precision and
+  // block slots; value: executable graph and the kernel launches it holds
+  bool use_graphs = true;
+  std::map<std::array<int, 14>, std::pair<cudaGraphExec_t, long long>> graphs;
   size_t bytes = 0;
   const int *map(int m) const { return maps_dev + (size_t)m * (J + 1); }
   int total(int m) const { return maps_host[(size_t)m * (J + 1) + J]; }
@@ -331,6 +351,9 @@ __device__ __forceinline__ int batch_job_of(const int *start, int J, int b) {
 template <typename T>
 ks_status batch_density(Batch &B, int sX);
 ks_status batch_cg(Batch &B, double tol);
+ks_status batch_cg_upload(Batch &B, double tol);
+ks_status batch_cg_launch(Batch &B, int iters);
+ks_status batch_cg_continue(Batch &B);
 ks_status batch_cg_setup(Batch &B);
 ks_status batch_potential(Batch &B, bool fp32_xc);
 template <typename T>

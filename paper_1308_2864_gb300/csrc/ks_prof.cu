@@ -97,6 +97,16 @@ ProfScope::~ProfScope() {
   if (g_prof.pending.size() > 4096) resolve(false);
 }
 
+bool prof_enabled() {
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  return g_prof.on;
+}
+
+void count_launches(long long delta) {
+  if (delta >= 0) g_launches.fetch_add((unsigned long long)delta, std::memory_order_relaxed);
+  else g_launches.fetch_sub((unsigned long long)(-delta), std::memory_order_relaxed);
+}
+
 void prof_collect() {
   std::lock_guard<std::mutex> lk(g_prof.mu);
   if (!g_prof.pending.empty()) resolve(false);

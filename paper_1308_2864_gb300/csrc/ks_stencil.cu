@@ -402,7 +402,7 @@ __global__ void __launch_bounds__(kStThreads, 2) stencil_tma_kernel(const __grid
 // Geometry of a launch: tiles, orbital chunks and z segments; the number of
 // segments is lowered until the block partials (nchan per block) fit.
 template <int PC>
-static ks_status stencil_geometry(const Problem &P, int nchan, StArgs &a) {
+static ks_status stencil_geometry(const Problem &P, int nchan, StArgs &a, int planes = 0) {
   using Tl = StTile<PC>;
   a.N = P.N;
   a.p = P.p;
@@ -410,10 +410,12 @@ static ks_status stencil_geometry(const Problem &P, int nchan, StArgs &a) {
   a.tiles_y = (P.N + Tl::TY - 1) / Tl::TY;
   a.chunks = (P.p + PC - 1) / PC;
   const long long base = (long long)a.tiles_x * a.tiles_y * a.chunks;
-  // aim for about 8 blocks per SM, with segments of at least 8 planes
+  // aim for about 8 blocks per SM, with segments of at least 8 planes (or
+  // segments of `planes` planes when given)
   long long segs = (8LL * P.sms + base - 1) / base;
   const long long maxsegs = (P.N + 7) / 8;
   if (segs > maxsegs) segs = maxsegs;
+  if (planes > 0) segs = (P.N + planes - 1) / planes;
   if (segs < 1) segs = 1;
   for (;;) {
     a.zseg = (int)((P.N + segs - 1) / segs);
@@ -624,14 +626,15 @@ ks_status batch_mass_dots(Batch &B, int sD, int sMD, int sX, int sMX, int sXp, i
 // Per job: PC class of its p and the block geometry of that class (room for
 // four reduction channels in its partials).
 ks_status batch_stencil_geometry(Batch &B) {
+  const int planes = B.tune.st_planes;
   for (int j = 0; j < B.J; ++j) {
     Problem &P = B.probs[j]->P;
     BJob &b = B.jobs_host[j];
     StArgs a{};
-    if (P.p >= 32) KS_TRY(stencil_geometry<32>(P, 4, a));
-    else if (P.p >= 16) KS_TRY(stencil_geometry<16>(P, 4, a));
-    else if (P.p >= 8) KS_TRY(stencil_geometry<8>(P, 4, a));
-    else KS_TRY(stencil_geometry<4>(P, 4, a));
+    if (P.p >= 32) KS_TRY(stencil_geometry<32>(P, 4, a, planes));
+    else if (P.p >= 16) KS_TRY(stencil_geometry<16>(P, 4, a, planes));
+    else if (P.p >= 8) KS_TRY(stencil_geometry<8>(P, 4, a, planes));
+    else KS_TRY(stencil_geometry<4>(P, 4, a, planes));
     b.st_zseg = a.zseg;
     b.st_tiles_x = a.tiles_x;
     b.st_tiles_y = a.tiles_y;

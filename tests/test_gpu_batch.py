@@ -95,3 +95,35 @@ def test_batch_rejects_what_it_does_not_support():
     B = ks.Batch([easy(10, 2, 2, 1.0, 7)])
     with pytest.raises(ks.KSError):
         B.minimize(retraction="cayley", maxit=5)
+
+
+def test_batch_graphs_and_plain_launches_agree():
+    # the captured step sequences replay exactly the plain launches
+    import paper_1308_2864_gb300 as ks
+    jobs = [easy(10, 2, 2, 1.0, 7)] + harder()
+    out = []
+    for g in (True, False):
+        B = ks.Batch(jobs)
+        B.set_graphs(g)
+        out.append(B.minimize(retraction="qr", gtol=1e-12, maxit=15, precision="mixed",
+                              polish_gtol=1e-3))
+    for a, b, xa, xb in zip(out[0][0], out[1][0], out[0][1], out[1][1]):
+        assert a["E"] == b["E"] and a["iters"] == b["iters"]
+        assert np.array_equal(xa, xb)
+
+
+def test_batch_autotune_keeps_results_up_to_summation_order():
+    import paper_1308_2864_gb300 as ks
+    jobs = [easy(10, 2, 2, 1.0, 7)] + harder()
+    ref, Xr = ks.Batch(jobs).minimize(retraction="qr", gtol=1e-12, maxit=12)
+    B = ks.Batch(jobs)
+    choice = B.autotune()
+    assert choice["gram_rows"] in (1024, 2048, 4096, 8192, 16384)
+    assert choice["comb_per_thread"] in (2, 4, 8, 16)
+    assert choice["pot_per_thread"] in (1, 2, 4, 8)
+    assert choice["stencil_planes"] in (0, 8, 16, 32, 64)
+    res, Xs = B.minimize(retraction="qr", gtol=1e-12, maxit=12)
+    for a, b, xa, xb in zip(ref, res, Xr, Xs):
+        assert b["status"] == a["status"] and b["iters"] == a["iters"]
+        assert b["E"] == pytest.approx(a["E"], rel=1e-10)
+        assert np.abs(xb - xa).max() <= 1e-7 * np.abs(xa).max()
