@@ -16,6 +16,12 @@ need geometries and pseudopotentials that are not available):
   * ``c3``  cube side 40 bohr, 128^3 nodes, 256 atoms on 8x8x4, p=512.
   * ``c4``  256 jobs, N = round(exp(U(ln 20, ln 48))), spacing 0.4 bohr,
             2..16 atoms placed uniformly in [1.5, L-1.5]^3, p = 2 * atoms.
+  * ``of``  orbital-free (Thomas-Fermi-von Weizsaecker) aluminium-like
+            clusters: the sites of an s x s x s block of face-centred cubic
+            cells (cube edge 7.559 bohr, every corner and face centre of the
+            block), Z = 3 pseudo-atoms, 6 bohr of vacuum on each side, grid
+            spacing about 0.4 bohr, one "orbital" (p = 1) occupied by all
+            3 * atoms electrons, initial guess 1 + 0.1 U(-1, 1) per node.
 
 The grid has N interior nodes per edge and spacing h = L/(N+1); interior
 node (ix, iy, iz) sits at ((ix+1)h, (iy+1)h, (iz+1)h) and has flat index
@@ -87,6 +93,13 @@ def initial_orbitals(seed: int, job: int, n: int, p: int) -> np.ndarray:
     return (2.0 * u - 1.0).reshape(n, p)
 
 
+def initial_density_amplitude(seed: int, job: int, n: int) -> np.ndarray:
+    """Orbital-free start: a nearly uniform amplitude 1 + 0.1 U(-1, 1) per
+    node (n x 1).  Not yet M-normalised."""
+    u = uniform_block(stream_key(seed, job, STREAM_X0), n)
+    return (1.0 + 0.1 * (2.0 * u - 1.0)).reshape(n, 1)
+
+
 @dataclass
 class System:
     """One synthetic Kohn-Sham system (geometry and sizes only)."""
@@ -99,6 +112,8 @@ class System:
     rc: float = 0.5             # erf smearing radius of the pseudo-atom
     occ: float = 2.0            # occupation per orbital
     retraction: str = "qr"      # "qr" or "cayley"
+    kinetic: int = 0            # 0 = orbitals, (f/2) tr(X^T K X); 1 = TFW density functional (p = 1)
+    mu: float = 1.0             # weight of the von Weizsaecker term (kinetic = 1)
     seed: int = 0
     job: int = 0
     name: str = ""
@@ -113,6 +128,8 @@ class System:
         return self.N ** 3
 
     def x0(self) -> np.ndarray:
+        if self.kinetic == 1:
+            return initial_density_amplitude(self.seed, self.job, self.n)
         return initial_orbitals(self.seed, self.job, self.n, self.p)
 
 
@@ -220,6 +237,45 @@ def small_system(N: int = 6, L: float = 6.0, natoms: int = 1, p: int = 2,
     zval = float(2 * p) / natoms if Z is None else Z
     return System(N=N, L=L, atoms=atoms, Z=np.full(natoms, zval), p=p, xc=xc,
                   retraction=retraction, seed=seed, name=f"small {N}^3 p={p}")
+
+
+def fcc_cluster_sites(cells: int, a: float) -> np.ndarray:
+    """Sites of an s x s x s block of face-centred cubic cells with cube
+    edge a: every lattice point (corners and face centres) inside the block,
+    boundary included, with the block's corner at the origin."""
+    pts = set()
+    m = 2 * cells
+    for i in range(m + 1):
+        for j in range(m + 1):
+            for l in range(m + 1):
+                if (i + j + l) % 2 == 0:
+                    pts.add((i, j, l))
+    return np.array(sorted(pts), dtype=np.float64) * (0.5 * a)
+
+
+def config_of_al(cells: int = 4, seed: int = 1010, spacing: float = 0.4,
+                 margin: float = 6.0, mu: float = 1.0) -> System:
+    """Orbital-free aluminium-like cluster (see the module docstring)."""
+    a = 7.559
+    sites = fcc_cluster_sites(cells, a)
+    L0 = cells * a + 2.0 * margin
+    N = int(round(L0 / spacing)) - 1
+    L = spacing * (N + 1)
+    atoms = sites + 0.5 * (L - cells * a)
+    natoms = len(atoms)
+    return System(N=N, L=L, atoms=atoms, Z=np.full(natoms, 3.0), p=1, xc=1, rc=1.15,
+                  occ=3.0 * natoms, retraction="qr", kinetic=1, mu=mu, seed=seed,
+                  name=f"of: {cells}^3 fcc cells, {natoms} Al-like atoms, {N}^3 grid")
+
+
+def small_of_system(N: int = 6, L: float = 6.0, natoms: int = 2, Z: float = 1.0,
+                    seed: int = 11, mu: float = 1.0, xc: int = 1) -> System:
+    """A tiny orbital-free system (p = 1, every electron in the one amplitude)."""
+    rng = SplitMix64(stream_key(seed, 0, STREAM_ATOMS))
+    atoms = _random_atoms(rng, natoms, 0.3 * L, 0.7 * L, 1.2, 0.8)
+    return System(N=N, L=L, atoms=atoms, Z=np.full(natoms, Z), p=1, xc=xc, rc=1.0,
+                  occ=Z * natoms, retraction="cayley", kinetic=1, mu=mu, seed=seed,
+                  name=f"small OF {N}^3")
 
 
 CONFIGS = {"c1": config_c1, "c2": config_c2, "c3": config_c3}

@@ -13,7 +13,7 @@ import numpy as np
 from scipy.linalg import eigh
 
 from . import fe
-from .energy import Model, lda, density, evaluate
+from .energy import KIN_TFW, Model, lda, density, evaluate, thomas_fermi
 
 
 def lowest_pencil(H: np.ndarray, M: np.ndarray, p: int):
@@ -22,15 +22,19 @@ def lowest_pencil(H: np.ndarray, M: np.ndarray, p: int):
 
 
 def hamiltonian_dense(model: Model, rho: np.ndarray) -> np.ndarray:
-    """H(rho) = K/2 + h^3 Diag(Vext + vH(rho) + v_xc(rho)); E_X = 2 f H X."""
+    """H(rho) = K/2 + h^3 Diag(Vext + vH(rho) + v_xc(rho)); E_X = 2 f H X.
+    Orbital-free (TFW): H = mu K/2 + h^3 Diag(Vext + vH + v_xc + v_TF), the
+    discrete operator of Eq. OF_euler."""
     K, _ = fe.dense_K_M(model.N, model.h)
     h3 = model.h ** 3
     veff = model.vext().copy()
+    if model.kinetic == KIN_TFW and model.use_tf:
+        veff += thomas_fermi(rho)[1]
     if model.use_hartree:
         veff += fe.poisson_exact(4.0 * np.pi * h3 * rho, model.N, model.h)
     if model.use_xc:
         veff += lda(rho, model.xc)[1]
-    return 0.5 * K + h3 * np.diag(veff)
+    return 0.5 * model.kin_weight * K + h3 * np.diag(veff)
 
 
 def scf_reference(model: Model, alpha: float = 0.3, tol: float = 1e-13,

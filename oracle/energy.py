@@ -18,6 +18,19 @@ choices are stated here):
 E_X is the exact derivative of E (the paper's H(X)X up to the factor 2f of
 its own normalisation; the finite-difference test pins this).
 
+Orbital-free model (Sec. 2.2, Eq. TFW and Eq. OFeng; discretised as
+Eq. disOFinf with c^T M c = 1): one amplitude c = X (p = 1) carries all
+f = N_e electrons, rho_k = f c_k^2, and the kinetic term is the TFW density
+functional C_TF T_TF + mu T_vW.  With rho = phi^2 the von Weizsaecker term
+(1/8) int |grad rho|^2 / rho equals (1/2) int |grad phi|^2, which for the Q1
+interpolant of phi = sqrt(f) c is (f/2) c^T K c; the Thomas-Fermi term uses
+the same nodal quadrature as E_xc:
+
+  E(c)   = mu (f/2) c^T K c + h^3 sum_k C_TF rho_k^(5/3)   kinetic (TFW)
+         + external + Hartree + xc + ion-ion                as above
+  E_c    = mu f K c + 2 f h^3 Diag(Vext + vH + v_xc + v_TF) c,
+  v_TF   = (5/3) C_TF rho^(2/3),  C_TF = (3/10) (3 pi^2)^(2/3).
+
 When the Hartree potential comes from an inexact solve with residual
 r = 4 pi h^3 rho - K vH, the energy uses the variational form
 E_H = 1/2 h^3 rho^T vH + vH^T r / (8 pi), which equals the definition when
@@ -36,6 +49,9 @@ from . import fe
 
 XC_SLATER = 0
 XC_SLATER_PZ81 = 1
+KIN_ORBITALS = 0        # (f/2) tr(X^T K X), Eq. EKS
+KIN_TFW = 1             # Thomas-Fermi-von Weizsaecker, Eq. TFW (p = 1)
+C_TF = 0.3 * (3.0 * math.pi ** 2) ** (2.0 / 3.0)
 
 # Perdew-Zunger (1981) parametrisation of the Ceperley-Alder correlation
 # energy, unpolarised gas, in hartree.  gamma, beta1, beta2 (r_s >= 1) and
@@ -113,6 +129,19 @@ def pz81(rho: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
     return eps, eps - (rs / 3.0) * deps
 
 
+def thomas_fermi(rho: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """Thomas-Fermi kinetic energy per unit volume C_TF rho^(5/3) (the
+    integrand of T_TF in Eq. TFW, with its constant C_TF) and its derivative
+    v_TF = (5/3) C_TF rho^(2/3); both 0 below RHO_FLOOR."""
+    rho = np.asarray(rho, dtype=np.float64)
+    ok = rho >= RHO_FLOOR
+    r = np.where(ok, rho, 1.0)
+    r23 = np.cbrt(r) ** 2
+    e = C_TF * r * r23
+    v = (5.0 / 3.0) * C_TF * r23
+    return np.where(ok, e, 0.0), np.where(ok, v, 0.0)
+
+
 def lda(rho: np.ndarray, xc: int) -> tuple[np.ndarray, np.ndarray]:
     """LDA energy per electron eps_xc and potential v_xc; both are set to 0
     where rho < 1e-30."""
@@ -138,6 +167,9 @@ class Model:
     xc: int = XC_SLATER_PZ81
     rc: float = 0.5
     occ: float = 2.0
+    kinetic: int = KIN_ORBITALS
+    mu: float = 1.0                 # von Weizsaecker weight (KIN_TFW)
+    use_tf: bool = True             # KIN_TFW: include the Thomas-Fermi term
     use_ext: bool = True
     use_hartree: bool = True
     use_xc: bool = True
@@ -157,8 +189,19 @@ class Model:
 
     @classmethod
     def from_system(cls, s, **kw) -> "Model":
+        kw.setdefault("kinetic", getattr(s, "kinetic", KIN_ORBITALS))
+        kw.setdefault("mu", getattr(s, "mu", 1.0))
         return cls(N=s.N, L=s.L, atoms=np.asarray(s.atoms), Z=np.asarray(s.Z), p=s.p,
                    xc=s.xc, rc=s.rc, occ=s.occ, **kw)
+
+    def __post_init__(self):
+        if self.kinetic == KIN_TFW and self.p != 1:
+            raise ValueError("the TFW kinetic functional takes one amplitude (p = 1)")
+
+    @property
+    def kin_weight(self) -> float:
+        """Factor of (f/2) tr(X^T K X): 1 for orbitals, mu for TFW."""
+        return self.mu if self.kinetic == KIN_TFW else 1.0
 
     def vext(self) -> np.ndarray:
         if self._vext is None:
@@ -206,10 +249,15 @@ def evaluate(model: Model, X: np.ndarray, v_guess: np.ndarray | None = None) -> 
     X = np.asarray(X, dtype=np.float64)
     rho = density(X, f)
     KX = fe.apply_K(X, N, h)
-    e_kin = 0.5 * f * float(np.sum(X * KX))
+    w = model.kin_weight
+    e_kin = 0.5 * f * w * float(np.sum(X * KX))
     vext = model.vext()
     e_ext = h3 * float(vext @ rho)
     veff = vext.copy()
+    if model.kinetic == KIN_TFW and model.use_tf:
+        etf, vtf = thomas_fermi(rho)
+        e_kin += h3 * float(np.sum(etf))
+        veff += vtf
     vH = np.zeros_like(rho)
     e_h = 0.0
     it = 0
@@ -223,7 +271,7 @@ def evaluate(model: Model, X: np.ndarray, v_guess: np.ndarray | None = None) -> 
         e_xc = h3 * float(rho @ eps)
         veff += vxc
     e_ion = model.eii()
-    EX = f * KX + 2.0 * f * h3 * veff[:, None] * X
+    EX = w * f * KX + 2.0 * f * h3 * veff[:, None] * X
     parts = {"kinetic": e_kin, "external": e_ext, "hartree": e_h, "xc": e_xc, "ion": e_ion}
     return Evaluation(E=e_kin + e_ext + e_h + e_xc + e_ion, parts=parts, EX=EX,
                       rho=rho, vH=vH, veff=veff, cg_iters=it)

@@ -196,6 +196,8 @@ def minimize(model: Model, X0: np.ndarray, opt: Options | None = None,
     """Alg. ConOptM.  X0 is M-orthonormalised first unless told otherwise."""
     opt = opt or Options()
     retract = retract_qr if opt.retraction == "qr" else retract_cayley
+    if opt.retraction != "qr" and model.p == 1:
+        retract = retract_cayley_p1              # Lemma 3.1 (3): no 2 x 2 solve
     X = m_orthonormalize(model, X0) if orthonormalize else np.array(X0, dtype=np.float64)
     cur = point_at(model, X)
     C, Q = cur.E, 1.0

@@ -81,6 +81,10 @@ def main(argv=None) -> int:
                     help="c5: arrival rate as a fraction of the measured saturation throughput")
     ap.add_argument("--mode", default="server", choices=["server", "batch"],
                     help="c4: continuous-batching server (per-job streams) or one job table")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="batch mode: plain launches instead of the captured CUDA graphs")
+    ap.add_argument("--autotune", action="store_true",
+                    help="batch mode: time and keep the fastest launch shapes first")
     a = ap.parse_args(argv)
     torch.cuda.init()
     jobs = (ki.config_c4_jobs(njobs=a.jobs) if a.workload == "c4"
@@ -93,7 +97,11 @@ def main(argv=None) -> int:
         import paper_1308_2864_gb300 as ks
         t0 = time.perf_counter()
         B = ks.Batch(jobs)
+        B.set_graphs(not a.no_graphs)
         t_create = time.perf_counter() - t0
+        out["graphs"] = not a.no_graphs
+        if a.autotune:
+            out["autotune"] = B.autotune()
         B.minimize(maxit=2, **{k: v for k, v in opts.items() if k != "maxit"})   # warm-up
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -104,7 +112,8 @@ def main(argv=None) -> int:
                     "gb": B.bytes / (1 << 30),
                     "converged": sum(r["status"] == 0 for r in res),
                     "iters_total": sum(r["iters"] for r in res),
-                    "iters_max": max(r["iters"] for r in res)})
+                    "iters_max": max(r["iters"] for r in res),
+                    "ms_per_lockstep_iter": 1e3 * wall / max(1, max(r["iters"] for r in res))})
         print(json.dumps(out), flush=True)
         B.close()
         return 0
