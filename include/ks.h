@@ -57,6 +57,8 @@ typedef struct ks_problem ks_problem;
 enum { KS_XC_SLATER = 0, KS_XC_SLATER_PZ81 = 1 };
 enum { KS_FP64 = 0, KS_MIXED = 1 };
 enum { KS_QR = 0, KS_CAYLEY = 1 };
+enum { KS_KIN_ORBITALS = 0, KS_KIN_TFW = 1 };
+enum { KS_MASS_CONSISTENT = 0, KS_MASS_LUMPED = 1 };
 
 /* One discretised KS system (Eq. EKS discretised, Sec. 2.3). */
 typedef struct {
@@ -76,6 +78,20 @@ typedef struct {
   void *stream;       /* cudaStream_t to issue work on; NULL = library-owned */
   int cg_precond;     /* 1: precondition the Hartree CG with the FP32 sine-basis inverse
                          of K (default); 0: plain CG */
+  int kinetic;        /* KS_KIN_ORBITALS (0): the Kohn-Sham kinetic energy (occ/2) tr(X^T K X).
+                         KS_KIN_TFW (1): the orbital-free model of Sec. 2.2 with the
+                         Thomas-Fermi-von Weizsaecker functional of Eq. TFW; p must be 1,
+                         X is the amplitude c with rho = occ c^2 (occ = the electron count),
+                         c^T M c = 1 (Eq. disOFinf), and the kinetic energy is
+                         mu (occ/2) c^T K c + h^3 sum C_TF rho^(5/3),
+                         C_TF = (3/10) (3 pi^2)^(2/3) */
+  double mu;          /* KS_KIN_TFW: weight of the von Weizsaecker term (>= 0; 1 = full) */
+  int mass;           /* metric of the constraint X^T M X = I: KS_MASS_CONSISTENT (0), the Q1
+                         mass matrix; KS_MASS_LUMPED (1), its row sums M = h^3 I, under which
+                         the nodal density integrates to exactly occ * p electrons (the form
+                         the orbital-free model needs: a consistent-mass amplitude that
+                         oscillates node to node carries up to 27 times the electrons in the
+                         nodal density).  The stiffness K is the Q1 one in both. */
 } ks_problem_desc;
 
 /* Parameters of Alg. ConOptM (the paper fixes none of their values). */

@@ -37,14 +37,17 @@ ks_status ks_step_density(ks_problem *prob, const double *X, double *rho);
 ks_status ks_step_hartree(ks_problem *prob, const double *rho, double *vH, int warm,
                           double *resid, int *iters);
 
-/* V_eff = Vext + vH + v_xc(rho) and the energies (HOST, 3): h^3 sum Vext rho,
- * 1/2 h^3 sum vH rho + vH.resid/(8 pi), h^3 sum rho eps_xc(rho).  resid may
- * be NULL (treated as zero).  rho, vH, veff: DEVICE n. */
+/* V_eff = Vext + vH + v_xc(rho) (+ v_TF = (5/3) C_TF rho^(2/3) for the
+ * KS_KIN_TFW model) and the energies (HOST, 4): h^3 sum Vext rho,
+ * 1/2 h^3 sum vH rho + vH.resid/(8 pi), h^3 sum rho eps_xc(rho), and the
+ * Thomas-Fermi energy h^3 sum C_TF rho^(5/3) (0 for KS_KIN_ORBITALS).  resid
+ * may be NULL (treated as zero).  rho, vH, veff: DEVICE n. */
 ks_status ks_step_potential(ks_problem *prob, const double *rho, const double *vH,
-                            const double *resid, double *veff, double energies[3]);
+                            const double *resid, double *veff, double energies[4]);
 
-/* E_X = f K X + 2 f h^3 Diag(veff) X, MX = M X (DEVICE n x p or NULL) and
- * the kinetic energy (f/2) tr(X^T K X) (HOST). */
+/* E_X = w f K X + 2 f h^3 Diag(veff) X, MX = M X (DEVICE n x p or NULL) and
+ * the kinetic energy w (f/2) tr(X^T K X) (HOST), with w = 1 (KS_KIN_ORBITALS)
+ * or mu (KS_KIN_TFW: the von Weizsaecker term). */
 ks_status ks_step_hamiltonian(ks_problem *prob, const double *X, const double *veff,
                               double *EX, double *MX, double *kinetic);
 

@@ -21,7 +21,8 @@ need geometries and pseudopotentials that are not available):
             cells (cube edge 7.559 bohr, every corner and face centre of the
             block), Z = 3 pseudo-atoms, 6 bohr of vacuum on each side, grid
             spacing about 0.4 bohr, one "orbital" (p = 1) occupied by all
-            3 * atoms electrons, initial guess 1 + 0.1 U(-1, 1) per node.
+            3 * atoms electrons, lumped mass (h^3 I), initial guess
+            1 + 0.1 U(-1, 1) per node.
 
 The grid has N interior nodes per edge and spacing h = L/(N+1); interior
 node (ix, iy, iz) sits at ((ix+1)h, (iy+1)h, (iz+1)h) and has flat index
@@ -113,6 +114,7 @@ class System:
     occ: float = 2.0            # occupation per orbital
     retraction: str = "qr"      # "qr" or "cayley"
     kinetic: int = 0            # 0 = orbitals, (f/2) tr(X^T K X); 1 = TFW density functional (p = 1)
+    mass: int = 0               # 0 = consistent Q1 mass matrix; 1 = lumped (h^3 I)
     mu: float = 1.0             # weight of the von Weizsaecker term (kinetic = 1)
     seed: int = 0
     job: int = 0
@@ -264,17 +266,18 @@ def config_of_al(cells: int = 4, seed: int = 1010, spacing: float = 0.4,
     atoms = sites + 0.5 * (L - cells * a)
     natoms = len(atoms)
     return System(N=N, L=L, atoms=atoms, Z=np.full(natoms, 3.0), p=1, xc=1, rc=1.15,
-                  occ=3.0 * natoms, retraction="qr", kinetic=1, mu=mu, seed=seed,
+                  occ=3.0 * natoms, retraction="qr", kinetic=1, mu=mu, mass=1, seed=seed,
                   name=f"of: {cells}^3 fcc cells, {natoms} Al-like atoms, {N}^3 grid")
 
 
 def small_of_system(N: int = 6, L: float = 6.0, natoms: int = 2, Z: float = 1.0,
-                    seed: int = 11, mu: float = 1.0, xc: int = 1) -> System:
-    """A tiny orbital-free system (p = 1, every electron in the one amplitude)."""
+                    seed: int = 11, mu: float = 1.0, xc: int = 1, mass: int = 1) -> System:
+    """A tiny orbital-free system (p = 1, every electron in the one amplitude;
+    lumped mass unless told otherwise)."""
     rng = SplitMix64(stream_key(seed, 0, STREAM_ATOMS))
     atoms = _random_atoms(rng, natoms, 0.3 * L, 0.7 * L, 1.2, 0.8)
     return System(N=N, L=L, atoms=atoms, Z=np.full(natoms, Z), p=1, xc=xc, rc=1.0,
-                  occ=Z * natoms, retraction="cayley", kinetic=1, mu=mu, seed=seed,
+                  occ=Z * natoms, retraction="cayley", kinetic=1, mu=mu, mass=mass, seed=seed,
                   name=f"small OF {N}^3")
 
 

@@ -42,7 +42,7 @@ def scf_reference(model: Model, alpha: float = 0.3, tol: float = 1e-13,
     """Damped SCF: rho_in -> lowest p eigenvectors of (H(rho_in), M) ->
     rho_out; rho_in <- (1-alpha) rho_in + alpha rho_out until
     max|rho_out - rho_in| <= tol.  Returns (E, X, eigenvalues)."""
-    _, M = fe.dense_K_M(model.N, model.h)
+    M = model.dense_M()
     m0 = Model(**{**model.__dict__, "use_hartree": False, "use_xc": False})
     w, X = lowest_pencil(hamiltonian_dense(m0, np.zeros(model.n)), M, model.p)
     rho_in = density(X, model.occ)

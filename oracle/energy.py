@@ -49,6 +49,8 @@ from . import fe
 
 XC_SLATER = 0
 XC_SLATER_PZ81 = 1
+MASS_CONSISTENT = 0     # M = M1 (x) M1 (x) M1, the Q1 mass matrix
+MASS_LUMPED = 1         # M = h^3 I, its row sums (mass lumping)
 KIN_ORBITALS = 0        # (f/2) tr(X^T K X), Eq. EKS
 KIN_TFW = 1             # Thomas-Fermi-von Weizsaecker, Eq. TFW (p = 1)
 C_TF = 0.3 * (3.0 * math.pi ** 2) ** (2.0 / 3.0)
@@ -167,6 +169,7 @@ class Model:
     xc: int = XC_SLATER_PZ81
     rc: float = 0.5
     occ: float = 2.0
+    mass: int = MASS_CONSISTENT
     kinetic: int = KIN_ORBITALS
     mu: float = 1.0                 # von Weizsaecker weight (KIN_TFW)
     use_tf: bool = True             # KIN_TFW: include the Thomas-Fermi term
@@ -190,6 +193,7 @@ class Model:
     @classmethod
     def from_system(cls, s, **kw) -> "Model":
         kw.setdefault("kinetic", getattr(s, "kinetic", KIN_ORBITALS))
+        kw.setdefault("mass", getattr(s, "mass", MASS_CONSISTENT))
         kw.setdefault("mu", getattr(s, "mu", 1.0))
         return cls(N=s.N, L=s.L, atoms=np.asarray(s.atoms), Z=np.asarray(s.Z), p=s.p,
                    xc=s.xc, rc=s.rc, occ=s.occ, **kw)
@@ -197,6 +201,22 @@ class Model:
     def __post_init__(self):
         if self.kinetic == KIN_TFW and self.p != 1:
             raise ValueError("the TFW kinetic functional takes one amplitude (p = 1)")
+
+    def apply_M(self, X: np.ndarray) -> np.ndarray:
+        """M X: the Q1 mass matrix, or its row sums h^3 (lumped)."""
+        if self.mass == MASS_LUMPED:
+            return self.h ** 3 * np.asarray(X, dtype=np.float64)
+        return fe.apply_M(X, self.N, self.h)
+
+    def mass_inverse(self, X: np.ndarray) -> np.ndarray:
+        if self.mass == MASS_LUMPED:
+            return np.asarray(X, dtype=np.float64) / self.h ** 3
+        return fe.mass_inverse(X, self.N, self.h)
+
+    def dense_M(self) -> np.ndarray:
+        if self.mass == MASS_LUMPED:
+            return self.h ** 3 * np.eye(self.n)
+        return fe.dense_K_M(self.N, self.h)[1]
 
     @property
     def kin_weight(self) -> float:

@@ -53,7 +53,7 @@ def m_orthonormalize(model: Model, X: np.ndarray, passes: int = 2) -> np.ndarray
     `passes` times: O = X^T M X = L L^T, X <- X L^{-T}."""
     X = np.array(X, dtype=np.float64)
     for _ in range(passes):
-        O = X.T @ fe.apply_M(X, model.N, model.h)
+        O = X.T @ model.apply_M(X)
         Lc = cholesky(0.5 * (O + O.T), lower=True)
         X = solve_triangular(Lc, X.T, lower=True).T
     return X
@@ -62,18 +62,18 @@ def m_orthonormalize(model: Model, X: np.ndarray, passes: int = 2) -> np.ndarray
 def ortho_error(model: Model, X: np.ndarray, MX: np.ndarray | None = None) -> float:
     """||X^T M X - I||_F."""
     if MX is None:
-        MX = fe.apply_M(X, model.N, model.h)
+        MX = model.apply_M(X)
     return float(np.linalg.norm(X.T @ MX - np.eye(X.shape[1])))
 
 
 def project(model: Model, X: np.ndarray, ev: Evaluation) -> Point:
     """Riemannian gradient in the M metric (Eq. def-nablaE in Y = M^{1/2} X)."""
     N, h = model.N, model.h
-    G = fe.mass_inverse(ev.EX, N, h)
+    G = model.mass_inverse(ev.EX)
     S = ev.EX.T @ X
     D = G - X @ S
-    MD = fe.apply_M(D, N, h)
-    MX = fe.apply_M(X, N, h)
+    MD = model.apply_M(D)
+    MX = model.apply_M(X)
     return Point(X=X, MX=MX, ev=ev, G=G, S=S, D=D, MD=MD, dnorm2=float(np.sum(D * MD)))
 
 
@@ -84,7 +84,7 @@ def point_at(model: Model, X: np.ndarray, v_guess=None) -> Point:
 def retract_qr(model: Model, pt: Point, tau: float) -> np.ndarray:
     """Eq. QR with Alg. ChQR: Y = X - tau D; Y^T M Y = L L^T; Q = Y L^{-T}."""
     Y = pt.X - tau * pt.D
-    R = Y.T @ fe.apply_M(Y, model.N, model.h)
+    R = Y.T @ model.apply_M(Y)
     Lc = cholesky(0.5 * (R + R.T), lower=True)
     return solve_triangular(Lc, Y.T, lower=True).T
 
@@ -111,7 +111,7 @@ def retract_cayley(model: Model, pt: Point, tau: float) -> np.ndarray:
 
 def retract_cayley_dense(model: Model, pt: Point, tau: float) -> np.ndarray:
     """Eq. WY1 with the dense n x n skew matrix W, in Y = M^{1/2} X (tiny n)."""
-    _, M = fe.dense_K_M(model.N, model.h)
+    M = model.dense_M()
     Mh = np.real(sqrtm(M))
     Mmh = np.linalg.inv(Mh)
     Y = Mh @ pt.X

@@ -25,6 +25,8 @@ STATUS_NAMES = ["KS_OK", "KS_EINVAL", "KS_ENOMEM", "KS_ECUDA", "KS_ENOCONV", "KS
 KS_XC_SLATER, KS_XC_SLATER_PZ81 = 0, 1
 KS_FP64, KS_MIXED = 0, 1
 KS_QR, KS_CAYLEY = 0, 1
+KS_KIN_ORBITALS, KS_KIN_TFW = 0, 1
+KS_MASS_CONSISTENT, KS_MASS_LUMPED = 0, 1
 
 
 class KSError(RuntimeError):
@@ -39,7 +41,8 @@ class ProblemDesc(ctypes.Structure):
                 ("R", ctypes.POINTER(ctypes.c_double)), ("Z", ctypes.POINTER(ctypes.c_double)),
                 ("rc", ctypes.c_double), ("p", ctypes.c_int), ("occ", ctypes.c_double),
                 ("xc", ctypes.c_int), ("cg_tol", ctypes.c_double), ("cg_maxit", ctypes.c_int),
-                ("precision", ctypes.c_int), ("stream", ctypes.c_void_p), ("cg_precond", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("stream", ctypes.c_void_p), ("cg_precond", ctypes.c_int),
+                ("kinetic", ctypes.c_int), ("mu", ctypes.c_double), ("mass", ctypes.c_int)]
 
 
 class Opts(ctypes.Structure):
@@ -228,7 +231,8 @@ class Problem:
 
     def __init__(self, N: int, L: float, atoms, Z, p: int, rc: float = 0.5, occ: float = 2.0,
                  xc: int = KS_XC_SLATER_PZ81, cg_tol: float = 1e-10, cg_maxit: int = 20000,
-                 stream=None, cg_precond: bool = True):
+                 stream=None, cg_precond: bool = True, kinetic: int = 0, mu: float = 1.0,
+                 mass: int = 0):
         import torch
         lib = load_library()
         if not torch.cuda.is_available():
@@ -247,6 +251,7 @@ class Problem:
         d.cg_tol, d.cg_maxit, d.precision = cg_tol, cg_maxit, KS_FP64
         d.stream = ctypes.c_void_p(stream.cuda_stream)
         d.cg_precond = 1 if cg_precond else 0
+        d.kinetic, d.mu, d.mass = kinetic, mu, mass
         self.desc = d
         h = ctypes.c_void_p()
         _check(lib.ks_problem_create(ctypes.byref(d), ctypes.byref(h)))
@@ -256,6 +261,9 @@ class Problem:
 
     @classmethod
     def from_system(cls, s, **kw) -> "Problem":
+        kw.setdefault("kinetic", getattr(s, "kinetic", KS_KIN_ORBITALS))
+        kw.setdefault("mu", getattr(s, "mu", 1.0))
+        kw.setdefault("mass", getattr(s, "mass", KS_MASS_CONSISTENT))
         return cls(N=s.N, L=s.L, atoms=s.atoms, Z=s.Z, p=s.p, rc=s.rc, occ=s.occ, xc=s.xc, **kw)
 
     @staticmethod
@@ -372,7 +380,7 @@ class Problem:
 
     def step_potential(self, rho, vH, resid=None):
         veff = self.empty_vec()
-        e = (ctypes.c_double * 3)()
+        e = (ctypes.c_double * 4)()
         _check(load_library().ks_step_potential(self._h, _ptr(rho), _ptr(vH), _ptr(resid),
                                                 _ptr(veff), e))
         return veff, list(e)
@@ -476,6 +484,8 @@ class Server:
         d.Z = Z.ctypes.data_as(_DP)
         d.rc, d.p, d.occ, d.xc = s.rc, s.p, s.occ, s.xc
         d.cg_tol, d.cg_maxit, d.precision, d.cg_precond = 1e-10, 20000, KS_FP64, 1
+        d.kinetic, d.mu = getattr(s, "kinetic", KS_KIN_ORBITALS), getattr(s, "mu", 1.0)
+        d.mass = getattr(s, "mass", KS_MASS_CONSISTENT)
         o = default_opts(**opts)
         jid = ctypes.c_uint64()
         _check(load_library().ks_server_submit(self._h, ctypes.byref(d), ctypes.byref(o),
@@ -535,6 +545,8 @@ class Batch:
             d.Z = Z.ctypes.data_as(_DP)
             d.rc, d.p, d.occ, d.xc = s.rc, s.p, s.occ, s.xc
             d.cg_tol, d.cg_maxit, d.precision, d.cg_precond = 1e-10, 20000, KS_FP64, 1
+            d.kinetic, d.mu = getattr(s, "kinetic", KS_KIN_ORBITALS), getattr(s, "mu", 1.0)
+            d.mass = getattr(s, "mass", KS_MASS_CONSISTENT)
         h = ctypes.c_void_p()
         st = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
         _check(lib.ks_batch_create(descs, n, st, ctypes.byref(h)))

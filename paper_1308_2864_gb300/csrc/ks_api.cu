@@ -78,6 +78,15 @@ static ks_status validate(const ks_problem_desc *d) {
   if (d->precision != KS_FP64 && d->precision != KS_MIXED)
     return set_error(KS_EINVAL, "bad precision");
   if (!(d->cg_tol > 0.0) || d->cg_maxit < 1) return set_error(KS_EINVAL, "bad CG parameters");
+  if (d->mass != KS_MASS_CONSISTENT && d->mass != KS_MASS_LUMPED)
+    return set_error(KS_EINVAL, "bad mass model");
+  if (d->kinetic != KS_KIN_ORBITALS && d->kinetic != KS_KIN_TFW)
+    return set_error(KS_EINVAL, "bad kinetic model");
+  if (d->kinetic == KS_KIN_TFW) {
+    if (d->p != 1) return set_error(KS_EINVAL, "the TFW model takes one amplitude (p = 1)");
+    if (!(d->mu >= 0.0) || !std::isfinite(d->mu))
+      return set_error(KS_EINVAL, "TFW weight mu must be finite and >= 0");
+  }
   return KS_OK;
 }
 
@@ -155,13 +164,13 @@ static ks_status evaluate(Problem &P, const T *X, T *EX, T *MX, double *E) {
   }
   P.vH_valid = true;
   const double *s = P.scal_host;
-  P.last_parts[0] = s[SC_EKIN];
+  P.last_parts[0] = s[SC_EKIN] + s[SC_ETF];
   P.last_parts[1] = s[SC_EEXT];
   P.last_parts[2] = s[SC_EH];
   P.last_parts[3] = s[SC_EXC];
   P.last_parts[4] = s[SC_EII];
   P.last_cg_iters = (int)s[SC_CG_ITERS];
-  P.last_E = s[SC_EKIN] + s[SC_EEXT] + s[SC_EH] + s[SC_EXC] + s[SC_EII];
+  P.last_E = s[SC_EKIN] + s[SC_ETF] + s[SC_EEXT] + s[SC_EH] + s[SC_EXC] + s[SC_EII];
   if (!std::isfinite(P.last_E)) return set_error(KS_ENAN, "non-finite energy");
   *E = P.last_E;
   return KS_OK;
@@ -573,6 +582,12 @@ ks_status ks_problem_create(const ks_problem_desc *d, ks_problem **out) {
   P.h = d->L / (d->N + 1);
   P.rc = d->rc;
   P.occ = d->occ;
+  P.kinetic = d->kinetic;
+  P.mass = d->mass;
+  if (d->kinetic == KS_KIN_TFW) {
+    P.kin_w = d->mu;
+    P.ctf = 0.3 * std::pow(3.0 * M_PI * M_PI, 2.0 / 3.0);   // Eq. TFW's C_TF
+  }
   P.cg_tol = d->cg_tol;
   P.cg_maxit = d->cg_maxit;
   P.cg_precond = d->cg_precond ? 1 : 0;

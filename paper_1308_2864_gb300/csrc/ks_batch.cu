@@ -587,6 +587,9 @@ ks_status ks_batch_create(const ks_problem_desc *descs, int njobs, void *stream,
   }
   for (int j = 0; j < njobs; ++j) {
     if (descs[j].p > 104) return fail(set_error(KS_EINVAL, "batch: job %d has p > 104", j));
+    if (descs[j].kinetic != KS_KIN_ORBITALS || descs[j].mass != KS_MASS_CONSISTENT)
+      return fail(set_error(KS_EINVAL,
+                            "batch: job %d is orbital-free or lumped (single-system path only)", j));
     ks_problem_desc d = descs[j];
     d.stream = B.stream;
     ks_problem *p = nullptr;

@@ -61,6 +61,7 @@ enum Scalar : int {
   SC_EEXT,         // h^3 sum Vext rho
   SC_EH,           // variational Hartree energy
   SC_EXC,          // h^3 sum rho eps_xc
+  SC_ETF,          // h^3 sum C_TF rho^(5/3) (orbital-free model; follows SC_EXC)
   SC_EII,          // ion-ion energy
   SC_DNORM2,       // ||D||_M^2
   SC_BB_SS,        // tr(dX^T M dX)
@@ -75,6 +76,11 @@ struct Problem {
   // geometry and sizes
   int N = 0, n = 0, p = 0, natoms = 0, xc = 0;
   double L = 0, h = 0, rc = 0, occ = 0, cg_tol = 0;
+  // kinetic model: kin_w multiplies (occ/2) tr(X^T K X) (1, or mu of the
+  // TFW functional); ctf is the Thomas-Fermi constant (0 for orbitals)
+  int kinetic = KS_KIN_ORBITALS;
+  double kin_w = 1.0, ctf = 0.0;
+  int mass = KS_MASS_CONSISTENT;     // KS_MASS_LUMPED: M = h^3 I
   double cg_tol_phase = 0;         // > 0: Hartree tolerance of the running FP32 phase
   int cg_maxit = 0;
   std::vector<double> atoms_host;  // natoms x 4: x, y, z, Z

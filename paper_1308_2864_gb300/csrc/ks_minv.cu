@@ -126,8 +126,26 @@ ks_status batch_mass_inverse(Batch &B, int sE, int sG) {
 template ks_status batch_mass_inverse<double>(Batch &, int, int);
 template ks_status batch_mass_inverse<float>(Batch &, int, int);
 
+// G = s E elementwise (the inverse of the lumped mass h^3 I); E and G may alias.
+template <typename T>
+__global__ void scale_kernel(long long len, T s, const T *E, T *G) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x)
+    G[i] = s * E[i];
+}
+
 template <typename T>
 ks_status launch_mass_inverse(Problem &P, const T *E, T *G) {
+  if (P.mass == KS_MASS_LUMPED) {
+    const long long len = (long long)P.n * P.p;
+    long long nb = (len + 4LL * kThreads - 1) / (4LL * kThreads);
+    if (nb > 64LL * P.sms) nb = 64LL * P.sms;
+    const double h = P.h;
+    ProfScope ps_(P.stream, KP_MASS_INV, (double)len, 2.0 * len * sizeof(T));
+    scale_kernel<T><<<(int)nb, kThreads, 0, P.stream>>>(len, (T)(1.0 / (h * h * h)), E, G);
+    KS_CUDA_TRY(cudaGetLastError());
+    return KS_OK;
+  }
   const long long work = (long long)P.N * P.N * P.p;
   const int nb = (int)((work + kThreads - 1) / kThreads);
   const double s = 6.0 / P.h;

@@ -5,7 +5,8 @@
 //                  M metric; Alg. ChQR), then C = L^{-T}, giving
 //                  X+ = (X - tau D) L^{-T} = X C + D (-tau C)   (Eq. QR)
 //   cayley_factor: LU with partial pivoting of I + tau/2 V^T U (2p x 2p) and
-//                  the solve against V^T Y (Eq. WY3).
+//                  the solve against V^T Y (Eq. WY3); for p = 1 the closed
+//                  form of Lemma 3.1 (3) (Eq. WY-1d), no solve.
 #include "ks_device.cuh"
 
 namespace ks {
@@ -352,6 +353,25 @@ __global__ void __launch_bounds__(kSmallThreads) cayley_factor_kernel(
   __shared__ int s_fail;
   const int n2 = 2 * p, w = 3 * p;
   const double ht = 0.5 * tau;
+  if (p == 1) {
+    // x+ = x - beta1 a - beta2 x in the Y = M^{1/2} X coordinates, where
+    // a^T x = E_X^T X (S), a^T a = E_X^T M^{-1} E_X (B), x^T x = X^T M X (O);
+    // the denominator is 1 + (tau/2)^2 (a^T a x^T x - (a^T x)^2) >= 1
+    // (Cauchy-Schwarz), so the step always exists.
+    if (threadIdx.x == 0) {
+      const double ax = S[0], aa = B[0], xx = O ? O[0] : 1.0;
+      const double den = 1.0 + ht * ht * (aa * xx - ax * ax);
+      const double beta1 = tau * xx / den;
+      const double beta2 = -tau * (ax + ht * (ax * ax - aa * xx)) / den;
+      if (!isfinite(beta1) || !isfinite(beta2) || !(den > 0.0)) {
+        atomicCAS(status, 0, (int)KS_ESINGULAR);
+        return;
+      }
+      C1[0] = 1.0 - beta2;               // X+ = X C1 + G C2, G = M^{-1} E_X
+      C2[0] = -beta1;
+    }
+    return;
+  }
   for (int e = threadIdx.x; e < n2 * w; e += blockDim.x) {
     const int i = e / w, j = e % w;
     double v;

@@ -54,6 +54,7 @@ struct StArgs {
   int N, p, zseg, tiles_x, tiles_y, chunks;
   StencilCoef c;
   double occ, h3;
+  double kfac;                // factor of K X in E_X: occ, or mu occ (TFW kinetic)
   const void *A;              // input block (X or D)
   void *out1;                 // E_X (SK_HAM) or M A
   void *out2;                 // M X (SK_HAM, optional)
@@ -65,21 +66,21 @@ struct StArgs {
   double red_scale;
   unsigned int *counter;
   int *status;                // device status word (TMA waits that give up)
-  float cf[9];                // k0, ke, kc, m0, mf, me, mc, occ, 2 occ h^3 rounded to FP32 (host)
+  float cf[9];                // k0, ke, kc, m0, mf, me, mc, kfac, 2 occ h^3 rounded to FP32 (host)
 };
 
 // Coefficients in the working precision (FP32 ones rounded on the host: a
 // per-thread conversion would be nine FP64-pipe instructions per thread).
 template <typename T>
 struct StCoefT {
-  T k0, ke, kc, m0, mf, me, mc, occ, vscale;
+  T k0, ke, kc, m0, mf, me, mc, kin, vscale;
   __device__ explicit StCoefT(const StArgs &a) {
     if constexpr (sizeof(T) == 4) {
       k0 = a.cf[0]; ke = a.cf[1]; kc = a.cf[2]; m0 = a.cf[3]; mf = a.cf[4];
-      me = a.cf[5]; mc = a.cf[6]; occ = a.cf[7]; vscale = a.cf[8];
+      me = a.cf[5]; mc = a.cf[6]; kin = a.cf[7]; vscale = a.cf[8];
     } else {
       k0 = a.c.k0; ke = a.c.ke; kc = a.c.kc; m0 = a.c.m0; mf = a.c.mf;
-      me = a.c.me; mc = a.c.mc; occ = a.occ; vscale = 2.0 * a.occ * a.h3;
+      me = a.c.me; mc = a.c.mc; kin = a.kfac; vscale = 2.0 * a.occ * a.h3;
     }
   }
 };
@@ -147,7 +148,7 @@ __device__ __forceinline__ void stencil_plain_body(const StArgs &a, int vb) {
   const StCoefT<T> cf(a);
   const T k0 = cf.k0, ke = cf.ke, kc = cf.kc;
   const T m0 = cf.m0, mf = cf.mf, me = cf.me, mc = cf.mc;
-  const T occ = cf.occ, vscale = cf.vscale;
+  const T kin = cf.kin, vscale = cf.vscale;
   T acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
 
   for (int z = z0; z < z1; ++z) {
@@ -166,7 +167,7 @@ __device__ __forceinline__ void stencil_plain_body(const StArgs &a, int vb) {
         const T m = m0 * centre + mf * faces + me * edges + mc * corners;
         if (Kind == SK_HAM) {
           const T kx = k0 * centre + ke * edges + kc * corners;
-          ((T *)a.out1)[idx] = occ * kx + vscale * (T)a.veff[k] * centre;
+          ((T *)a.out1)[idx] = kin * kx + vscale * (T)a.veff[k] * centre;
           if (a.out2) ((T *)a.out2)[idx] = m;
           acc0 = fma(centre, kx, acc0);
         } else {
@@ -347,7 +348,7 @@ __global__ void __launch_bounds__(kStThreads, 2) stencil_tma_kernel(const __grid
           const T m = cf.m0 * centre + cf.mf * faces + cf.me * edges + cf.mc * corners;
           if (Kind == SK_HAM) {
             const T kx = cf.k0 * centre + cf.ke * edges + cf.kc * corners;
-            ((T *)a.out1)[idx] = cf.occ * kx + cf.vscale * vz[ly[r] * Tl::TX + lx[r]] * centre;
+            ((T *)a.out1)[idx] = cf.kin * kx + cf.vscale * vz[ly[r] * Tl::TX + lx[r]] * centre;
             if (a.out2) ((T *)a.out2)[idx] = m;
             acc0 = fma(centre, kx, acc0);
           } else {
@@ -464,7 +465,11 @@ template <typename T, int PC, int Kind>
 static ks_status stencil_launch_pc(Problem &P, StArgs &a, int nchan, double flops, double bytes) {
   KS_TRY(stencil_geometry<PC>(P, nchan, a));
   a.c = q1_coefficients(P.h);
-  const double cd[9] = {a.c.k0, a.c.ke, a.c.kc, a.c.m0, a.c.mf, a.c.me, a.c.mc, a.occ,
+  if (P.mass == KS_MASS_LUMPED) {      // row sums of M: h^3 on the centre
+    a.c.m0 = P.h * P.h * P.h;
+    a.c.mf = a.c.me = a.c.mc = 0.0;
+  }
+  const double cd[9] = {a.c.k0, a.c.ke, a.c.kc, a.c.m0, a.c.mf, a.c.me, a.c.mc, a.kfac,
                         2.0 * a.occ * a.h3};
   for (int i = 0; i < 9; ++i) a.cf[i] = (float)cd[i];
   a.part = P.partials;
@@ -472,7 +477,10 @@ static ks_status stencil_launch_pc(Problem &P, StArgs &a, int nchan, double flop
   a.status = P.dstatus;
   const int cls = Kind == SK_HAM ? KP_HAMILTONIAN : KP_MASS;
   ks_status st;
-  if (stencil_launch_tma<T, PC, Kind>(P, a, cls, flops, bytes, &st)) return st;
+  // one amplitude (PC = 1, p = 1) has an 8-byte row pitch, which no tensor
+  // map can describe: plain staging only
+  if constexpr (PC >= 4)
+    if (stencil_launch_tma<T, PC, Kind>(P, a, cls, flops, bytes, &st)) return st;
   {
     ProfScope ps_(P.stream, cls, flops, bytes);
     stencil_kernel<T, PC, Kind><<<a.nb, kStThreads, 0, P.stream>>>(a);
@@ -486,6 +494,7 @@ static ks_status stencil_launch(Problem &P, StArgs &a, int nchan, double flops, 
   if (P.p >= 32) return stencil_launch_pc<T, 32, Kind>(P, a, nchan, flops, bytes);
   if (P.p >= 16) return stencil_launch_pc<T, 16, Kind>(P, a, nchan, flops, bytes);
   if (P.p >= 8) return stencil_launch_pc<T, 8, Kind>(P, a, nchan, flops, bytes);
+  if (P.p == 1) return stencil_launch_pc<T, 1, Kind>(P, a, nchan, flops, bytes);
   return stencil_launch_pc<T, 4, Kind>(P, a, nchan, flops, bytes);
 }
 
@@ -494,13 +503,14 @@ ks_status launch_hamiltonian(Problem &P, const T *X, const double *veff, T *EX, 
                              double *ekin_out) {
   StArgs a{};
   a.occ = P.occ;
+  a.kfac = P.occ * P.kin_w;
   a.h3 = P.h * P.h * P.h;
   a.A = X;
   a.out1 = EX;
   a.out2 = MX;
   a.veff = veff;
   a.red_out = ekin_out;
-  a.red_scale = 0.5 * P.occ;
+  a.red_scale = 0.5 * a.kfac;
   const double total = (double)P.n * P.p;
   return stencil_launch<T, SK_HAM>(P, a, 1, 27.0 * total,
                                    total * sizeof(T) * (MX ? 3 : 2) + 8.0 * P.n);
@@ -561,6 +571,7 @@ __global__ void __launch_bounds__(kStThreads) stencil_batch_kernel(
 #pragma unroll
   for (int i = 0; i < 9; ++i) a.cf[i] = b.qcf[i];
   a.occ = b.occ;
+  a.kfac = b.occ;
   a.h3 = b.h3;
   a.A = b.blk[sl.a];
   a.out1 = b.blk[sl.o1];

@@ -65,7 +65,7 @@ ks_status ks_step_hartree(ks_problem *kp, const double *rho, double *vH, int war
 }
 
 ks_status ks_step_potential(ks_problem *kp, const double *rho, const double *vH,
-                            const double *resid, double *veff, double energies[3]) {
+                            const double *resid, double *veff, double energies[4]) {
   if (!kp || !rho || !vH || !veff) return set_error(KS_EINVAL, "null argument");
   Problem &P = kp->P;
   const double *r = resid;
@@ -74,10 +74,10 @@ ks_status ks_step_potential(ks_problem *kp, const double *rho, const double *vH,
     r = P.cg_q;
   }
   KS_TRY(launch_potential(P, rho, vH, r, veff, true));
-  double e[3];
-  KS_TRY(read_scalars(P, SC_EEXT, 3, e));
+  double e[4];
+  KS_TRY(read_scalars(P, SC_EEXT, 4, e));
   if (energies)
-    for (int i = 0; i < 3; ++i) energies[i] = e[i];
+    for (int i = 0; i < 4; ++i) energies[i] = e[i];
   return KS_OK;
 }
 

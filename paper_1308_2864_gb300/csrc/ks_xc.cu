@@ -79,11 +79,32 @@ __device__ __forceinline__ void lda_point(double rho_d, int xc, R &eps, R &v) {
   }
 }
 
-// Channels of the block partials: 0 = E_ext, 1 = E_H, 2 = E_xc.  Block vb
-// of vnb (grid-stride over the n nodes); the last block to finish sums the
-// partials in block order.
+// Thomas-Fermi kinetic energy per unit volume C_TF rho^(5/3) and its
+// derivative v_TF = (5/3) C_TF rho^(2/3) (the T_TF term of Eq. TFW), both 0
+// below the density floor; ctf = C_TF and vtf = (5/3) C_TF in precision R.
+template <typename R>
+__device__ __forceinline__ void tf_point(double rho_d, R ctf, R vtf, R &e, R &v) {
+  if (!(rho_d >= 1e-30)) {
+    e = 0;
+    v = 0;
+    return;
+  }
+  const R rho = (R)rho_d;
+  R z;                                             // rho^(-1/3)
+  if constexpr (sizeof(R) == 8) z = inv_cbrt(rho_d);
+  else z = rcbrtf(rho);
+  const R r23 = rho * z;                           // rho^(2/3)
+  v = vtf * r23;
+  e = ctf * rho * r23;
+}
+
+// Channels of the block partials: 0 = E_ext, 1 = E_H, 2 = E_xc and, when
+// ctf != 0 (orbital-free model), 3 = E_TF, with v_TF added to V_eff.  Block
+// vb of vnb (grid-stride over the n nodes); the last block to finish sums
+// the partials in block order.
 template <typename R>
 __device__ __forceinline__ void potential_body(long long n, double h3, int xc, int with_h,
+                                               double ctf,
                                                const double *__restrict__ rho,
                                                const double *__restrict__ vext,
                                                const double *__restrict__ vH,
@@ -93,7 +114,8 @@ __device__ __forceinline__ void potential_body(long long n, double h3, int xc, i
                                                int vb, int vnb) {
   __shared__ double smem[33];
   const double inv8pi = 1.0 / (8.0 * M_PI);
-  double e_ext = 0.0, e_h = 0.0, e_xc = 0.0;
+  const R ctf_r = (R)ctf, vtf_r = (R)(ctf * (5.0 / 3.0));
+  double e_ext = 0.0, e_h = 0.0, e_xc = 0.0, e_tf = 0.0;
   for (long long k = (long long)vb * blockDim.x + threadIdx.x; k < n;
        k += (long long)vnb * blockDim.x) {
     const double rk = rho[k], ve = vext[k];
@@ -108,27 +130,36 @@ __device__ __forceinline__ void potential_body(long long n, double h3, int xc, i
       v += vh;
       e_h += 0.5 * h3 * vh * rk + vh * r[k] * inv8pi;
     }
+    if (ctf != 0.0) {
+      R etf_r, vtf_p;
+      tf_point<R>(rk, ctf_r, vtf_r, etf_r, vtf_p);
+      v += (double)vtf_p;
+      e_tf = fma(h3, (double)etf_r, e_tf);
+    }
     veff[k] = v;
   }
   const double s0 = block_sum(e_ext, smem);
   const double s1 = block_sum(e_h, smem);
   const double s2 = block_sum(e_xc, smem);
+  const int nchan = ctf != 0.0 ? 4 : 3;
+  const double s3 = nchan == 4 ? block_sum(e_tf, smem) : 0.0;
   if (threadIdx.x == 0) {
     part[vb] = s0;
     part[vnb + vb] = s1;
     part[2 * vnb + vb] = s2;
+    if (nchan == 4) part[3 * vnb + vb] = s3;
   }
-  grid_reduce_tail(part, vnb, 3, out, 1.0, counter, smem);
+  grid_reduce_tail(part, vnb, nchan, out, 1.0, counter, smem);
 }
 
 template <typename R>
-__global__ void potential_kernel(long long n, double h3, int xc, int with_h,
+__global__ void potential_kernel(long long n, double h3, int xc, int with_h, double ctf,
                                  const double *__restrict__ rho, const double *__restrict__ vext,
                                  const double *__restrict__ vH, const double *__restrict__ r,
                                  double *__restrict__ veff, double *__restrict__ part,
                                  double *__restrict__ out, unsigned int *counter) {
-  potential_body<R>(n, h3, xc, with_h, rho, vext, vH, r, veff, part, out, counter, blockIdx.x,
-                    gridDim.x);
+  potential_body<R>(n, h3, xc, with_h, ctf, rho, vext, vH, r, veff, part, out, counter,
+                    blockIdx.x, gridDim.x);
 }
 
 // Batched: job j takes pot_nb blocks.
@@ -138,7 +169,7 @@ __global__ void potential_batch_kernel(const BJob *__restrict__ jobs, const int 
   const int j = batch_job_of(start, J, blockIdx.x);
   if (!active[j]) return;
   const BJob &b = jobs[j];
-  potential_body<R>(b.n, b.h3, b.xc, 1, b.rho, b.vext, b.vH, b.cg_r, b.veff, b.partials,
+  potential_body<R>(b.n, b.h3, b.xc, 1, 0.0, b.rho, b.vext, b.vH, b.cg_r, b.veff, b.partials,
                     b.scal + SC_EEXT, b.red_counter, blockIdx.x - start[j], b.pot_nb);
 }
 
@@ -193,11 +224,11 @@ ks_status launch_potential(Problem &P, const double *rho, const double *vH, cons
     ProfScope ps_(P.stream, KP_POTENTIAL, 40.0 * P.n, 40.0 * P.n);
     if (fp32_xc)
       potential_kernel<float><<<nb, kThreads, 0, P.stream>>>(
-          P.n, h3, P.xc, with_hartree ? 1 : 0, rho, P.vext, vH, r, veff, P.partials,
+          P.n, h3, P.xc, with_hartree ? 1 : 0, P.ctf, rho, P.vext, vH, r, veff, P.partials,
           P.scal + SC_EEXT, P.red_counter);
     else
       potential_kernel<double><<<nb, kThreads, 0, P.stream>>>(
-          P.n, h3, P.xc, with_hartree ? 1 : 0, rho, P.vext, vH, r, veff, P.partials,
+          P.n, h3, P.xc, with_hartree ? 1 : 0, P.ctf, rho, P.vext, vH, r, veff, P.partials,
           P.scal + SC_EEXT, P.red_counter);
   }
   KS_CUDA_TRY(cudaGetLastError());

@@ -1,7 +1,8 @@
 """Pins of the oracle's orbital-free model (Sec. 2.2: Eq. TFW, Eq. OFeng,
 Eq. OF_euler; discretised as Eq. disOFinf and minimised as Eq. OFDFT-y on
-the unit sphere of the M metric) against the free-electron gas, a continuum
-closed form, finite differences, the V = 0 spectrum and a dense SCF."""
+the unit sphere of the M metric, here the lumped mass h^3 I) against the
+free-electron gas, a continuum closed form, finite differences, the V = 0
+spectrum and a dense SCF."""
 import math
 
 import numpy as np
@@ -95,9 +96,31 @@ def test_of_parts():
     vw = 0.5 * model.occ * float(np.sum(c * KX))
     assert ev.parts["kinetic"] == pytest.approx(model.mu * vw + tf, rel=1e-14)
     assert tf > 0 and vw > 0
-    # the electron count the constraint fixes: f c^T M c = N_e
-    assert model.occ * float(c[:, 0] @ fe.apply_M(c, model.N, model.h)[:, 0]) == pytest.approx(
-        float(np.sum(model.Z)), rel=1e-13)
+    # the electron count the constraint fixes, f c^T M c = N_e, is the
+    # integral of the nodal density under the lumped mass
+    ne = float(np.sum(model.Z))
+    assert model.occ * float(c[:, 0] @ model.apply_M(c)[:, 0]) == pytest.approx(ne, rel=1e-13)
+    assert model.h ** 3 * float(np.sum(rho)) == pytest.approx(ne, rel=1e-13)
+
+
+def test_consistent_mass_lets_the_nodal_density_grow():
+    # Why the orbital-free systems take the lumped mass: under the consistent
+    # Q1 mass an amplitude oscillating node to node has c^T M c = 1 while its
+    # nodal density integrates to (3 / (2 + cos t))^3 -> 27 times the electron
+    # count (the M1 eigenvalue (h/3)(2 + cos t) of the highest sine mode against
+    # h for the row sums), a gain the external potential can exploit.
+    N, L = 9, 5.0
+    h = L / (N + 1)
+    i = np.arange(N)
+    z, y, x = np.meshgrid(i, i, i, indexing="ij")
+    t = np.pi * N / (N + 1)
+    phi = lambda k: np.sin((k + 1) * t)                     # highest 1-D sine mode
+    c = (phi(x) * phi(y) * phi(z)).reshape(-1, 1)
+    m = energy.Model(N=N, L=L, atoms=np.zeros((0, 3)), Z=np.zeros(0), p=1, occ=1.0)
+    c = c / math.sqrt(float(c[:, 0] @ m.apply_M(c)[:, 0]))
+    lumped = h ** 3 * float(np.sum(c * c))
+    assert lumped == pytest.approx((3.0 / (2.0 + math.cos(t))) ** 3, rel=1e-12)
+    assert lumped > 20
 
 
 def test_tfw_model_needs_one_amplitude():
@@ -112,8 +135,10 @@ def test_of_v0_minimiser_is_the_lowest_mode(retraction):
     # the (1,1,1) generalised eigenvalue of (K, M).
     model, s = _of_model(N=6, mu=0.5, use_tf=False, use_ext=False, use_hartree=False,
                          use_xc=False)
-    lam = fe.generalized_eigs_closed_form(model.N, model.h)
-    want = 0.5 * model.mu * model.occ * lam[0]
+    # lowest eigenvalue of K against h^3 I: K's (1,1,1) sine mode,
+    # 3 kappa_1 mu_1^2 (K = K1 M1 M1 + M1 K1 M1 + M1 M1 K1)
+    kap, mu1 = fe.eigen_1d(model.N, model.h)
+    want = 0.5 * model.mu * model.occ * 3.0 * kap[0] * mu1[0] ** 2 / model.h ** 3
     r = stiefel.minimize(model, s.x0(), stiefel.Options(retraction=retraction, gtol=1e-9,
                                                         maxit=2000))
     assert r.converged
@@ -134,7 +159,7 @@ def test_of_minimiser_matches_dense_scf(retraction, Z, natoms):
                                                         maxit=4000))
     assert r.converged
     H = brute.hamiltonian_dense(model, energy.density(r.X, model.occ))
-    _, M = fe.dense_K_M(model.N, model.h)
+    M = model.dense_M()
     w, V = brute.lowest_pencil(H, M, 1)
     lam = float(r.X[:, 0] @ H @ r.X[:, 0])
     assert np.abs(H @ r.X[:, 0] - lam * (M @ r.X[:, 0])).max() < 1e-7
