@@ -115,10 +115,13 @@ typedef struct {
                          in both (the FP32 phase evaluates eps_xc and v_xc in FP32 and
                          solves to mixed_cg_tol) (KS_FP64) */
   double polish_gtol; /* switch from the FP32 phase to the FP64 polish (1e-4) */
-  int stall_iters;    /* 1: the FP32 phase also ends when the energy stagnates, i.e. the mean
-                         of df_k = |E_{k-1} - E_k| / (|E_{k-1}| + 1) over the last three
+  int stall_iters;    /* 1: the FP32 phase also ends when it stagnates, i.e. the mean of
+                         df_k = |E_{k-1} - E_k| / (|E_{k-1}| + 1) over the last three
                          iterations falls below stall_df (the stagnation measure of
-                         Sec. 4.1); 0: it ends only at polish_gtol or maxit (1) */
+                         Sec. 4.1), or the best ||D||_M has not improved by 0.1 % for 500
+                         iterations (the FP32 rounding floor of systems whose energy is so
+                         large that df never falls that far); 0: it ends only at
+                         polish_gtol or maxit (1) */
   double stall_df;    /* stagnation threshold of the FP32 phase (1e-11) */
   int resume;         /* 1: continue from the state of the last ks_minimize on this problem
                          or from ks_state_load (X_inout is then output only); maxit counts

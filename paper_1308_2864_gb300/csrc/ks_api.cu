@@ -279,8 +279,9 @@ struct PhaseResult {
 // One run of Alg. ConOptM in storage precision T from the block Xstart
 // (copied in, then M-orthonormalised) -- or, when `resume` is set, from the
 // state left in P.state by an earlier run or by ks_state_load -- until
-// ||D||_M <= gtol, `maxit` iterations in total, or (stall > 0) no 0.1 %
-// improvement of the best ||D||_M for `stall` iterations.  The final iterate
+// ||D||_M <= gtol, `maxit` iterations in total, or (stall > 0) stagnation:
+// the energy measure of Sec. 4.1 below o.stall_df, or no 0.1 % improvement of
+// the best ||D||_M for kStallWindow iterations.  The final iterate
 // is copied to Xend and the loop state is kept in P.state.
 template <typename T>
 static ks_status run_phase(Problem &P, const T *Xstart, T *Xend, const ks_opts &o, double gtol,
@@ -402,7 +403,8 @@ static ks_status run_phase(Problem &P, const T *Xstart, T *Xend, const ks_opts &
       best = dn;
       last_improve = k;
     }
-    if (stall > 0 && k - k0 >= 3 && (df[0] + df[1] + df[2]) / 3.0 < o.stall_df) {
+    if (stall > 0 && k - k0 >= 3 &&
+        ((df[0] + df[1] + df[2]) / 3.0 < o.stall_df || k - last_improve >= kStallWindow)) {
       stalled = true;
       stop = true;
     }

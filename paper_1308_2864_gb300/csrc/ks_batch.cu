@@ -135,6 +135,7 @@ struct JobState {
   int first_k = 0;                 // iterations before this phase (BB parity, ortho cadence)
   double tau = 0, last_tau = 0, tau_first = 0;
   double df[3] = {1, 1, 1}, Eprev = 0;
+  int last_improve = 0;            // iteration of the last 0.1 % improvement of best
   bool stalled = false, converged = false;
   int slot = B_X0;                 // block holding the job's final X when it stopped
 };
@@ -351,6 +352,7 @@ ks_status run_phase(Batch &B, std::vector<JobState> &S, const ks_opts &o, double
     S[j].C = S[j].E;
     S[j].Q = 1.0;
     S[j].best = std::sqrt(std::fmax(S[j].dnorm2, 0.0));
+    S[j].last_improve = 0;
     S[j].Eprev = S[j].E;
     for (double &d : S[j].df) d = 1.0;
   }
@@ -456,8 +458,13 @@ ks_status run_phase(Batch &B, std::vector<JobState> &S, const ks_opts &o, double
       s.df[s.k % 3] = std::fabs(s.Eprev - s.E) / (std::fabs(s.Eprev) + 1.0);
       s.Eprev = s.E;
       const double dn = std::sqrt(std::fmax(s.dnorm2, 0.0));
-      if (dn < 0.999 * s.best) s.best = dn;
-      if (stall && s.k >= 3 && (s.df[0] + s.df[1] + s.df[2]) / 3.0 < o.stall_df) s.stalled = true;
+      if (dn < 0.999 * s.best) {
+        s.best = dn;
+        s.last_improve = s.k;
+      }
+      if (stall && s.k >= 3 &&
+          ((s.df[0] + s.df[1] + s.df[2]) / 3.0 < o.stall_df || s.k - s.last_improve >= kStallWindow))
+        s.stalled = true;
       if (o.verbose > 0 && s.k % o.verbose == 0)
         fprintf(stderr, "ks_batch[%s] job %d: k=%d E=%.12f |D|=%.3e tau=%.3e\n",
                 sizeof(T) == 8 ? "fp64" : "fp32", j, s.k, s.E, dn, s.tau);

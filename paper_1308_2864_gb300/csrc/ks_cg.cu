@@ -8,8 +8,9 @@
 // with Lambda_abc = k_a m_b m_c + m_a k_b m_c + m_a m_b k_c.  Applied in
 // single precision it is an SPD approximation of K^{-1} to about 1e-6, so
 // the FP64 CG reaches 1e-10 in two or three iterations.  Each sine transform
-// is a dense N x N product along one grid axis (six axis passes per
-// application, one grid barrier after each).
+// is a dense N x N product along one grid axis: fused in shared memory for
+// N <= 128 (three grid barriers per application), tiled through shared
+// memory above (six axis passes, one grid barrier after each).
 //
 // Each CG iteration needs two grid-wide reductions (p.q and r.r, plus r.z
 // when preconditioned).  The search direction p_j = s_j + beta p_{j-1}
@@ -80,60 +81,128 @@ __device__ __forceinline__ double stiff_apply(const double *a, const double *b, 
   return c.k0 * s0 + c.ke * se + c.kc * sc;
 }
 
-// One sine-transform pass along `axis` (0 = x, 1 = y, 2 = z):
-// out[.., j, ..] = sum_k Phi[j][k] in[.., k, ..].  Mode 1 (after the z
-// pass) divides by Lambda of the frequency triple; Mode 2 (the last inverse
-// pass) writes FP64 z and accumulates r.z.
+// Tiled form for N > kFusedMaxN: each axis pass is the product C = Phi X,
+// where the columns of X are the grid lines along the axis (element (s, k, c)
+// of slab s, axis index k and column c at s*ss + k*sa + c*sc).  A work item
+// is a tile of kTJ frequencies x kTC columns; the K dimension is staged in
+// chunks of kTK axis points (X chunk and Phi chunk in shared memory), and a
+// thread keeps a 4 x 8 block of outputs (rows tj + 16 a, columns tc + 16 b)
+// whose FMA chains run over k in ascending order.  Phi is symmetric and
+// orthogonal, so the same matrix serves the forward and the inverse passes.
+// Mode 1 (after the forward z pass) divides by Lambda of the frequency
+// triple; Mode 2 (the last inverse pass) writes FP64 z and accumulates r.z.
+constexpr int kTJ = 64, kTC = 128, kTK = 32, kTCPad = kTC + 1;
+static_assert(kCgThreads == 256, "the 16 x 16 thread grid of the tiled sine pass");
+
 template <typename Tin, int Mode>
-__device__ __forceinline__ double sine_pass(const Tin *in, float *out32, double *out64,
-                                            const double *r, int axis, const CgArgs &a,
-                                            long long tid, long long stride) {
+__device__ double tiled_pass(const CgArgs &a, const Tin *in, float *out32, double *out64, int axis,
+                             float *sh) {
   const int N = a.N;
   const long long NN = (long long)N * N;
-  const long long step = axis == 0 ? 1 : (axis == 1 ? N : NN);
+  long long sa, sc, ss, C;
+  int S;
+  if (axis == 0) { sa = 1; sc = N; ss = 0; S = 1; C = NN; }
+  else if (axis == 1) { sa = N; sc = 1; ss = NN; S = N; C = N; }
+  else { sa = NN; sc = 1; ss = 0; S = 1; C = NN; }
+  const long long ctiles = (C + kTC - 1) / kTC;
+  const int jblocks = (N + kTJ - 1) / kTJ;
+  const long long total = (long long)S * ctiles * jblocks;
+  float *Xs = sh, *Ps = sh + kTK * kTCPad;
+  const int tid = threadIdx.x, tj = tid >> 4, tc = tid & 15;
   double rz = 0.0;
-  for (long long e = tid; e < a.n; e += stride) {
-    const int ix = (int)(e % N), iy = (int)((e / N) % N), iz = (int)(e / NN);
-    const int j = axis == 0 ? ix : (axis == 1 ? iy : iz);
-    const long long base = e - (long long)j * step;
-    const float *row = a.phi + (long long)j * N;
-    float acc = 0.f;
-    for (int k = 0; k < N; ++k) {
-      float v;
-      if constexpr (sizeof(Tin) == 8) v = (float)__ldcg((const double *)in + base + k * step);
-      else v = __ldcg((const float *)in + base + k * step);
-      acc = fmaf(__ldg(row + k), v, acc);
+  for (long long w = a.vb; w < total; w += a.vnb) {
+    const int jb = (int)(w % jblocks) * kTJ;
+    const long long w2 = w / jblocks;
+    const long long c0 = (w2 % ctiles) * kTC;
+    const long long base = (w2 / ctiles) * ss;
+    float acc[4][8];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 8; ++v) acc[u][v] = 0.f;
+    for (int k0 = 0; k0 < N; k0 += kTK) {
+      __syncthreads();
+      // X chunk (kTK x kTC): consecutive threads take consecutive addresses
+      // (along the axis for the x pass, along the columns otherwise)
+      for (int t = tid; t < kTK * kTC; t += kCgThreads) {
+        const int kk = axis == 0 ? t % kTK : t / kTC;
+        const int cc = axis == 0 ? t / kTK : t % kTC;
+        const int k = k0 + kk;
+        const long long c = c0 + cc;
+        float v = 0.f;
+        if (k < N && c < C) {
+          const long long idx = base + k * sa + c * sc;
+          if constexpr (sizeof(Tin) == 8) v = (float)__ldcg((const double *)in + idx);
+          else v = __ldcg((const float *)in + idx);
+        }
+        Xs[kk * kTCPad + cc] = v;
+      }
+      // Phi chunk (kTK x kTJ): Ps[kk][jj] = Phi[k0 + kk][jb + jj]
+      for (int t = tid; t < kTK * kTJ; t += kCgThreads) {
+        const int jj = t % kTJ, kk = t / kTJ;
+        const int k = k0 + kk, j = jb + jj;
+        Ps[t] = (k < N && j < N) ? __ldg(a.phi + (long long)k * N + j) : 0.f;
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int kk = 0; kk < kTK; ++kk) {
+        float pv[4], xv[8];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) pv[u] = Ps[kk * kTJ + tj + 16 * u];
+#pragma unroll
+        for (int v = 0; v < 8; ++v) xv[v] = Xs[kk * kTCPad + tc + 16 * v];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(pv[u], xv[v], acc[u][v]);
+      }
     }
-    if (Mode == 1) {
-      const float lam = a.kap[ix] * a.mu[iy] * a.mu[iz] + a.mu[ix] * a.kap[iy] * a.mu[iz] +
-                        a.mu[ix] * a.mu[iy] * a.kap[iz];
-      acc = acc / lam;
-    }
-    if (Mode == 2) {
-      const double zv = (double)acc;
-      out64[e] = zv;
-      rz = fma(r[e], zv, rz);
-    } else {
-      out32[e] = acc;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = jb + tj + 16 * u;
+      if (j >= N) continue;
+#pragma unroll
+      for (int v = 0; v < 8; ++v) {
+        const long long c = c0 + tc + 16 * v;
+        if (c >= C) continue;
+        const long long idx = base + j * sa + c * sc;
+        float val = acc[u][v];
+        if (Mode == 1) {
+          const int ix = (int)(idx % N), iy = (int)((idx / N) % N), iz = (int)(idx / NN);
+          const float lam = a.kap[ix] * a.mu[iy] * a.mu[iz] + a.mu[ix] * a.kap[iy] * a.mu[iz] +
+                            a.mu[ix] * a.mu[iy] * a.kap[iz];
+          val = val / lam;
+        }
+        if (Mode == 2) {
+          const double zv = (double)val;
+          out64[idx] = zv;
+          rz = fma(a.r[idx], zv, rz);
+        } else {
+          out32[idx] = val;
+        }
+      }
     }
   }
   return rz;
 }
 
-// z = P^{-1} r (six passes, each followed by a grid barrier); returns this
-// thread's share of r.z, or a NaN-free 0 and false when a barrier failed.
-__device__ bool apply_precond(const CgArgs &a, long long tid, long long stride, double *rz_l) {
-  sine_pass<double, 0>(a.r, a.t1, nullptr, nullptr, 0, a, tid, stride);
+constexpr size_t kTiledSmem = (size_t)(kTK * kTCPad + kTK * kTJ) * sizeof(float);
+
+// z = P^{-1} r (six tiled passes, each followed by a grid barrier); returns
+// this thread's share of r.z, or false when a barrier failed.
+__device__ bool apply_precond(const CgArgs &a, double *rz_l) {
+  extern __shared__ float dyn[];
+  tiled_pass<double, 0>(a, a.r, a.t1, nullptr, 0, dyn);
   if (!grid_barrier_n(a.bar, a.status, a.vnb)) return false;
-  sine_pass<float, 0>(a.t1, a.t2, nullptr, nullptr, 1, a, tid, stride);
+  tiled_pass<float, 0>(a, a.t1, a.t2, nullptr, 1, dyn);
   if (!grid_barrier_n(a.bar, a.status, a.vnb)) return false;
-  sine_pass<float, 1>(a.t2, a.t1, nullptr, nullptr, 2, a, tid, stride);
+  tiled_pass<float, 1>(a, a.t2, a.t1, nullptr, 2, dyn);
   if (!grid_barrier_n(a.bar, a.status, a.vnb)) return false;
-  sine_pass<float, 0>(a.t1, a.t2, nullptr, nullptr, 2, a, tid, stride);
+  tiled_pass<float, 0>(a, a.t1, a.t2, nullptr, 2, dyn);
   if (!grid_barrier_n(a.bar, a.status, a.vnb)) return false;
-  sine_pass<float, 0>(a.t2, a.t1, nullptr, nullptr, 1, a, tid, stride);
+  tiled_pass<float, 0>(a, a.t2, a.t1, nullptr, 1, dyn);
   if (!grid_barrier_n(a.bar, a.status, a.vnb)) return false;
-  *rz_l = sine_pass<float, 2>(a.t1, nullptr, a.z, a.r, 0, a, tid, stride);
+  *rz_l = tiled_pass<float, 2>(a, a.t1, nullptr, a.z, 0, dyn);
   return true;
 }
 
@@ -303,7 +372,7 @@ __device__ void cg_body(const CgArgs &a) {
   const double *s_vec = a.precond ? a.z : a.r;
   if (a.precond && rr > thr) {
     double rz_l = 0.0;
-    if (a.fused ? !apply_precond_fused(a, &rz_l) : !apply_precond(a, tid, stride, &rz_l)) return;
+    if (a.fused ? !apply_precond_fused(a, &rz_l) : !apply_precond(a, &rz_l)) return;
     const double s = block_sum(rz_l, smem);
     if (threadIdx.x == 0) partC[a.vb] = s;
     if (!grid_barrier_n(a.bar, a.status, a.vnb)) return;
@@ -353,8 +422,7 @@ __device__ void cg_body(const CgArgs &a) {
     double rho_new = rr_new;
     if (a.precond && rr_new > thr) {
       double rz_l = 0.0;
-      if (a.fused ? !apply_precond_fused(a, &rz_l) : !apply_precond(a, tid, stride, &rz_l))
-        return;
+      if (a.fused ? !apply_precond_fused(a, &rz_l) : !apply_precond(a, &rz_l)) return;
       const double s = block_sum(rz_l, smem);
       if (threadIdx.x == 0) partC[a.vb] = s;
       if (!grid_barrier_n(a.bar, a.status, a.vnb)) return;
@@ -435,7 +503,7 @@ ks_status launch_cg(Problem &P, const double *rho, double *v, double *r, bool wa
   a.warm = warm ? 1 : 0;
   a.precond = P.cg_precond;
   a.fused = P.N <= kFusedMaxN ? 1 : 0;
-  const size_t dyn = a.fused ? cg_dynamic_smem(P.N) : 0;
+  const size_t dyn = cg_dynamic_smem(P.N);
   KS_CUDA_TRY(cudaMemsetAsync(P.bar, 0, sizeof(GridBarrier), P.stream));
   void *args[] = {&a};
   {
@@ -817,7 +885,7 @@ ks_status batch_cg(Batch &B, double tol) {
 }
 
 size_t cg_dynamic_smem(int N) {
-  return N <= kFusedMaxN ? (size_t)3 * N * N * sizeof(float) : 0;
+  return N <= kFusedMaxN ? (size_t)3 * N * N * sizeof(float) : kTiledSmem;
 }
 
 int cg_grid_blocks(int sms, int n, int N) {

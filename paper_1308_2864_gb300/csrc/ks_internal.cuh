@@ -35,6 +35,9 @@ constexpr int kDevOk = 0;
 
 // Spin limit of every device-side wait (about a second with the back-off
 // used); after it the waiting block records KS_ETIMEOUT and returns.
+// FP32 phase: iterations without a 0.1 % improvement of the best ||D||_M
+// after which the phase ends (its rounding floor reached).
+constexpr int kStallWindow = 500;
 constexpr long long kSpinLimit = 1LL << 22;
 
 // ---------------------------------------------------------------- grid

@@ -94,6 +94,26 @@ def test_hartree_cg(case, precond):
     assert it2 <= 1
 
 
+@pytest.mark.parametrize("N", [140, 161])
+def test_hartree_cg_tiled_preconditioner(N):
+    # above N = 128 the sine-basis preconditioner runs as tiled axis passes
+    # (ragged against the 64 x 128 tiles at both sizes): same answer and the
+    # same two-to-four iterations as the fused form
+    s = ki.config_of_al(cells=2)
+    s.N, s.L = N, 0.4 * (N + 1)
+    model = oe.Model.from_system(s)
+    rng = np.random.default_rng(5)
+    rho = rng.random(model.n)
+    b = 4 * math.pi * model.h ** 3 * rho
+    P = make(s)
+    v, r, it = P.step_hartree(dev(rho))
+    assert it <= 4
+    v = host(v)
+    res = b - ofe.apply_K(v, model.N, model.h)
+    assert np.linalg.norm(res) <= 1.05e-10 * np.linalg.norm(b)
+    assert_rel(v, ofe.poisson_exact(b, model.N, model.h), rel=1e-8, what="vH vs exact")
+
+
 def test_potential_and_energies(case):
     s, model, X = case
     P = make(s)
