@@ -130,9 +130,14 @@ class System:
         return self.N ** 3
 
     def x0(self) -> np.ndarray:
+        return self.x0_for(self.N)
+
+    def x0_for(self, N: int) -> np.ndarray:
+        """The seeded initial block drawn for an N^3 grid (the coarsest grid of
+        a refinement run)."""
         if self.kinetic == 1:
-            return initial_density_amplitude(self.seed, self.job, self.n)
-        return initial_orbitals(self.seed, self.job, self.n, self.p)
+            return initial_density_amplitude(self.seed, self.job, N ** 3)
+        return initial_orbitals(self.seed, self.job, N ** 3, self.p)
 
 
 def _random_atoms(rng: SplitMix64, natoms: int, lo: float, hi: float,

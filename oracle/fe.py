@@ -194,3 +194,36 @@ def cg_solve(apply_A, b: np.ndarray, x0: np.ndarray | None, tol: float,
         rr = rr_new
         it += 1
     return x, r, it, True
+
+
+def prolong_1d(Nc: int) -> np.ndarray:
+    """1-D Q1 interpolation from Nc interior nodes (spacing h) to Nf = 2 Nc + 1
+    (spacing h/2), zero Dirichlet values at both ends: fine node 2i+1 is
+    coarse node i, fine node 2i lies halfway between coarse nodes i-1 and i.
+    Returns the Nf x Nc matrix."""
+    Nf = 2 * Nc + 1
+    P = np.zeros((Nf, Nc))
+    for i in range(Nc):
+        P[2 * i + 1, i] = 1.0
+        P[2 * i, i] += 0.5
+        P[2 * i + 2, i] += 0.5
+    return P
+
+
+def prolong(X: np.ndarray, Nc: int) -> np.ndarray:
+    """Uniform refinement of a Q1 field (Alg. AdpConOptM's projection of the
+    coarse solution onto the next mesh): the fine nodal values of the same
+    trilinear function, (P1 (x) P1 (x) P1) X, applied along each axis."""
+    X = np.asarray(X, dtype=np.float64)
+    squeeze = X.ndim == 1
+    if squeeze:
+        X = X[:, None]
+    p = X.shape[1]
+    P1 = prolong_1d(Nc)
+    Nf = P1.shape[0]
+    F = X.reshape(Nc, Nc, Nc, p)
+    F = np.einsum("ai,ijkq->ajkq", P1, F)       # z
+    F = np.einsum("bj,ajkq->abkq", P1, F)       # y
+    F = np.einsum("ck,abkq->abcq", P1, F)       # x
+    out = F.reshape(Nf ** 3, p)
+    return out[:, 0] if squeeze else out

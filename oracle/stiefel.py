@@ -231,3 +231,37 @@ def minimize(model: Model, X0: np.ndarray, opt: Options | None = None,
             callback(k, cur)
     return Result(X=cur.X, E=cur.E, parts=cur.ev.parts, dnorm=cur.dnorm, iters=k,
                   converged=cur.dnorm <= opt.gtol, history=history, point=cur)
+
+
+def refine_levels(N: int, levels: int) -> list[int]:
+    """Grids of a uniform refinement ending at N: N_l = (N+1) / 2^(levels-1-l) - 1."""
+    if levels < 1 or (N + 1) % (1 << (levels - 1)) != 0:
+        raise ValueError("N + 1 must be divisible by 2^(levels - 1)")
+    out = [(N + 1) // (1 << (levels - 1 - l)) - 1 for l in range(levels)]
+    if out[0] < 2:
+        raise ValueError("coarsest grid below 2 nodes per edge")
+    return out
+
+
+def minimize_refine(model: Model, X0: np.ndarray, levels: int, opt: Options | None = None,
+                    coarse_gtol: float = 1e-3) -> list[Result]:
+    """Alg. AdpConOptM with uniform refinement and a fixed number of levels:
+    Alg. ConOptM on each grid of refine_levels(model.N, levels) in turn, the
+    coarser levels to coarse_gtol, each level started from the Q1
+    interpolant of the previous level's solution (M-orthonormalised on the
+    new grid).  X0 is the initial block on the coarsest grid.  Returns the
+    result of every level (the last one on model's own grid)."""
+    from dataclasses import replace
+    opt = opt or Options()
+    grids = refine_levels(model.N, levels)
+    results = []
+    X = X0
+    for l, Nl in enumerate(grids):
+        m = replace(model, N=Nl, _vext=None)
+        o = replace(opt, gtol=opt.gtol if l == levels - 1 else coarse_gtol)
+        r = minimize(m, X, o)
+        results.append(r)
+        if l < levels - 1:
+            X = fe.prolong(r.X, Nl)
+    return results
+
