@@ -201,6 +201,39 @@ ks_status ks_minimize(ks_problem *prob, double *X_inout, const ks_opts *opts,
 ks_status ks_minimize_host(ks_problem *prob, double *X_inout_host, const ks_opts *opts,
                            ks_result *result);
 
+/* Uniform refinement (Alg. AdpConOptM with every element refined and a fixed
+ * number of levels, Sec. 4.3).  Nested grids have N' = 2N + 1 interior nodes
+ * (spacing h/2, fine node 2i+1 = coarse node i).
+ *
+ * ks_prolong: Xf = (P1 x P1 x P1) Xc, the fine nodal values of the coarse
+ * Q1 (trilinear) field.  P1 carries weight 1 to coinciding nodes and 1/2 to
+ * midpoints; values beyond the ends are zero (Dirichlet).
+ *   Xc: DEVICE, Nc^3 x p, row-major (orbital fastest).
+ *   Xf: DEVICE, (2 Nc + 1)^3 x p.  Caller-owned; must not overlap Xc.
+ *   stream: cudaStream_t, or NULL for the legacy default stream.
+ * Returns KS_EINVAL for Nc outside [1, 1023], p < 1, null or overlapping
+ * pointers.  The call is asynchronous on `stream`. */
+ks_status ks_prolong(int Nc, int p, const double *Xc, double *Xf, void *stream);
+ks_status ks_prolong_f32(int Nc, int p, const float *Xc, float *Xf, void *stream);
+
+/* Alg. ConOptM on the grids N_l = (desc->N + 1) / 2^(levels-1-l) - 1,
+ * l = 0 .. levels-1, ending at desc->N.  Each level gets its own problem with
+ * the same geometry (desc with N replaced).
+ *   X0_host: HOST, the initial block on the coarsest grid (N_0^3 x p).
+ *   Levels l > 0 start from the prolongation of level l-1's final iterate.
+ *   Coarser levels stop at ||D||_M <= coarse_gtol.  A coarse level that
+ *     reaches opts->maxit still seeds the next.
+ *   The finest level runs to opts->gtol.
+ *   level_results: HOST, `levels` entries, one ks_result per level.
+ *   X_host_out: HOST (N^3 x p), or NULL; receives the finest level's final
+ *     block.
+ * Requires (desc->N + 1) divisible by 2^(levels-1) and N_0 >= 2; KS_EINVAL
+ * otherwise.  Returns the finest level's status, or the first error.  All
+ * device memory is freed before return. */
+ks_status ks_minimize_refine(const ks_problem_desc *desc, int levels, const double *X0_host,
+                             const ks_opts *opts, double coarse_gtol, double *X_host_out,
+                             ks_result *level_results);
+
 /* Checkpoint of the minimiser (line-search scalars, current and previous
  * iterates with their M products, gradients and the Hartree potential) after
  * the last iteration of the last ks_minimize call.  ks_state_bytes returns

@@ -261,13 +261,17 @@ def fcc_cluster_sites(cells: int, a: float) -> np.ndarray:
 
 
 def config_of_al(cells: int = 4, seed: int = 1010, spacing: float = 0.4,
-                 margin: float = 6.0, mu: float = 1.0) -> System:
-    """Orbital-free aluminium-like cluster (see the module docstring)."""
+                 margin: float = 6.0, mu: float = 1.0, N: int | None = None) -> System:
+    """Orbital-free aluminium-like cluster (see the module docstring).  With N
+    given, the grid has N interior nodes per edge and the spacing follows."""
     a = 7.559
     sites = fcc_cluster_sites(cells, a)
     L0 = cells * a + 2.0 * margin
-    N = int(round(L0 / spacing)) - 1
-    L = spacing * (N + 1)
+    if N is None:
+        N = int(round(L0 / spacing)) - 1
+        L = spacing * (N + 1)
+    else:
+        L = L0
     atoms = sites + 0.5 * (L - cells * a)
     natoms = len(atoms)
     return System(N=N, L=L, atoms=atoms, Z=np.full(natoms, 3.0), p=1, xc=1, rc=1.15,

@@ -89,6 +89,10 @@ SIGNATURES = [
     ("ks_orthonormalize", _I, [_P, _P]),
     ("ks_minimize", _I, [_P, _P, ctypes.POINTER(Opts), ctypes.POINTER(Result)]),
     ("ks_minimize_host", _I, [_P, _DP, ctypes.POINTER(Opts), ctypes.POINTER(Result)]),
+    ("ks_prolong", _I, [_I, _I, _P, _P, _P]),
+    ("ks_prolong_f32", _I, [_I, _I, _P, _P, _P]),
+    ("ks_minimize_refine", _I, [ctypes.POINTER(ProblemDesc), _I, _DP, ctypes.POINTER(Opts), _D,
+                                _DP, ctypes.POINTER(Result)]),
     ("ks_last_error_string", ctypes.c_char_p, []),
     ("ks_kernel_launches", ctypes.c_ulonglong, []),
     ("ks_state_bytes", ctypes.c_size_t, [_P]),
@@ -224,6 +228,65 @@ def result_dict(r: Result) -> dict:
             "E_parts": list(r.E_parts), "iters": r.iters, "cg_iters_total": r.cg_iters_total,
             "backtracks": r.backtracks, "status": r.status, "seconds": r.seconds,
             "mixed_iters": r.mixed_iters, "mixed_gradnorm": r.mixed_gradnorm, "mixed_E": r.mixed_E}
+
+
+def _system_desc(s, N: int | None = None, stream=None):
+    """ProblemDesc of a ks_inputs.System (and the arrays it points into)."""
+    atoms = np.ascontiguousarray(np.asarray(s.atoms, dtype=np.float64).reshape(-1, 3))
+    Z = np.ascontiguousarray(np.asarray(s.Z, dtype=np.float64).reshape(-1))
+    d = ProblemDesc()
+    d.N, d.L, d.natoms = s.N if N is None else N, s.L, len(Z)
+    d.R = atoms.ctypes.data_as(_DP)
+    d.Z = Z.ctypes.data_as(_DP)
+    d.rc, d.p, d.occ, d.xc = s.rc, s.p, s.occ, s.xc
+    d.cg_tol, d.cg_maxit, d.precision, d.cg_precond = 1e-10, 20000, KS_FP64, 1
+    d.kinetic, d.mu = getattr(s, "kinetic", KS_KIN_ORBITALS), getattr(s, "mu", 1.0)
+    d.mass = getattr(s, "mass", KS_MASS_CONSISTENT)
+    d.stream = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+    return d, (atoms, Z)
+
+
+def prolong(Xc, Nc: int):
+    """Q1 prolongation of the device block Xc (Nc^3 x p, FP64 or FP32) to the
+    grid with 2 Nc + 1 nodes per edge (ks_prolong), on the current stream."""
+    import torch
+    p = Xc.shape[1]
+    Nf = 2 * Nc + 1
+    out = torch.empty((Nf ** 3, p), dtype=Xc.dtype, device=Xc.device)
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    lib = load_library()
+    if Xc.dtype == torch.float64:
+        _check(lib.ks_prolong(Nc, p, _ptr(Xc), _ptr(out), st))
+    else:
+        _check(lib.ks_prolong_f32(Nc, p, _ptr32(Xc), _ptr32(out), st))
+    return out
+
+
+def refine_grids(N: int, levels: int) -> list[int]:
+    return [(N + 1) // (1 << (levels - 1 - l)) - 1 for l in range(levels)]
+
+
+def minimize_refine(s, levels: int, x0: np.ndarray | None = None, coarse_gtol: float = 1e-3,
+                    want_x: bool = True, **opts):
+    """Alg. AdpConOptM with uniform refinement (ks_minimize_refine) for the
+    ks_inputs.System `s`, ending on its own grid.  x0: the initial block on the
+    coarsest grid (default: the seeded one drawn for that grid).  Returns
+    (one result dict per level, the finest block or None)."""
+    import torch
+    grids = refine_grids(s.N, levels)
+    if x0 is None:
+        x0 = s.x0_for(grids[0])
+    x0 = np.ascontiguousarray(x0, dtype=np.float64)
+    d, keep = _system_desc(s, stream=torch.cuda.current_stream())
+    o = default_opts(**opts)
+    res = (Result * levels)()
+    X = np.empty((s.N ** 3, s.p), dtype=np.float64) if want_x else None
+    st = load_library().ks_minimize_refine(ctypes.byref(d), levels, x0.ctypes.data_as(_DP),
+                                           ctypes.byref(o), coarse_gtol,
+                                           X.ctypes.data_as(_DP) if want_x else None, res)
+    if st not in (0, KS_ENOCONV):
+        _check(st)
+    return [result_dict(r) for r in res], X
 
 
 class Problem:
