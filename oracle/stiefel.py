@@ -213,18 +213,24 @@ def minimize(model: Model, X0: np.ndarray, opt: Options | None = None,
         while True:
             Xn = retract(model, cur, tau)
             trial = point_at(model, Xn, cur.ev.vH)
-            if trial.E <= C - opt.rho1 * tau * cur.dnorm2 or h == opt.max_backtrack:
+            ok = trial.E <= C - opt.rho1 * tau * cur.dnorm2
+            if ok or h == opt.max_backtrack:
                 break
             tau *= opt.delta
             h += 1
         Qn = opt.eta * Q + 1.0
         C = (opt.eta * Q * C + trial.E) / Qn
         Q = Qn
+        if not ok:
+            # the last trial is taken without meeting the test: the
+            # nonmonotone reference restarts at its energy (C_k >= E_k holds)
+            C, Q = trial.E, 1.0
         oerr = ortho_error(model, trial.X, trial.MX)
         if opt.retraction != "qr" and oerr > opt.ortho_tol:
             trial = point_at(model, m_orthonormalize(model, trial.X, passes=1), cur.ev.vH)
         history.append({"k": k, "E": trial.E, "dnorm": trial.dnorm, "tau": tau, "h": h,
-                        "C": C, "Q": Q, "ortho": oerr, "cg": trial.ev.cg_iters})
+                        "C": C, "Q": Q, "ortho": oerr, "cg": trial.ev.cg_iters,
+                        "forced": not ok})
         prev, cur = cur, trial
         k += 1
         if callback is not None:

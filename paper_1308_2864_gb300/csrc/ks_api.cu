@@ -350,13 +350,16 @@ static ks_status run_phase(Problem &P, const T *Xstart, T *Xend, const ks_opts &
     double tau = have_prev ? bb_step(first_k + k, tr, o) : (tau_first > 0.0 ? tau_first : o.tau0);
     int h = 0;
     double Et = 0;
+    bool forced = false;
     for (;;) {
       KS_TRY(retract<T>(P, o.retraction, X(0), D(0), tau, X(2)));
       KS_TRY(evaluate<T>(P, X(2), EX(1), MX(2), &Et));
       cg_total += P.last_cg_iters;
-      if (Et <= C - o.rho1 * tau * tr.dnorm2 + armijo_slack<T>(P.last_parts) ||
-          h == o.max_backtrack)
+      const bool ok = Et <= C - o.rho1 * tau * tr.dnorm2 + armijo_slack<T>(P.last_parts);
+      if (ok || h == o.max_backtrack) {
+        forced = !ok;
         break;
+      }
       tau *= o.delta;
       ++h;
     }
@@ -365,6 +368,16 @@ static ks_status run_phase(Problem &P, const T *Xstart, T *Xend, const ks_opts &
     const double Qn = o.eta * Q + 1.0;
     C = (o.eta * Q * C + Et) / Qn;
     Q = Qn;
+    // FP64: a trial accepted without meeting the test restarts the nonmonotone
+    // reference at its energy (C = E, Q = 1; C_k >= E_k still holds), so that
+    // a reference left below the current energy cannot reject every later
+    // step.  The FP32 phase keeps the reference: there a run of rejected steps
+    // at its rounding floor freezes the energy, which ends the phase through
+    // the stagnation measure.
+    if (forced && sizeof(T) == 8) {
+      C = Et;
+      Q = 1.0;
+    }
     // accept: prev <- cur, cur <- trial
     std::swap(ix[1], ix[0]);
     std::swap(ix[0], ix[2]);

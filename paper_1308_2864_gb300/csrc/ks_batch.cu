@@ -136,6 +136,7 @@ struct JobState {
   double tau = 0, last_tau = 0, tau_first = 0;
   double df[3] = {1, 1, 1}, Eprev = 0;
   int last_improve = 0;            // iteration of the last 0.1 % improvement of best
+  bool forced = false;             // the last trial was accepted without meeting the test
   bool stalled = false, converged = false;
   int slot = B_X0;                 // block holding the job's final X when it stopped
 };
@@ -378,6 +379,7 @@ ks_status run_phase(Batch &B, std::vector<JobState> &S, const ks_opts &o, double
       s.tau = s.have_prev ? bb_step(s.first_k + s.k, s, o)
                           : (s.tau_first > 0.0 ? s.tau_first : o.tau0);
       s.h = 0;
+      s.forced = false;
       tau[j] = s.tau;
     }
     std::vector<unsigned char> search = m;
@@ -395,9 +397,10 @@ ks_status run_phase(Batch &B, std::vector<JobState> &S, const ks_opts &o, double
         }
         const double parts[5] = {sc(B, j, SC_EKIN), sc(B, j, SC_EEXT), sc(B, j, SC_EH),
                                  sc(B, j, SC_EXC), eii[j]};
-        if (s.Et <= s.C - o.rho1 * s.tau * s.dnorm2 + armijo_slack<T>(parts) ||
-            s.h == o.max_backtrack) {
+        const bool ok = s.Et <= s.C - o.rho1 * s.tau * s.dnorm2 + armijo_slack<T>(parts);
+        if (ok || s.h == o.max_backtrack) {
           search[j] = 0;
+          s.forced = !ok;
         } else {
           s.tau *= o.delta;
           tau[j] = s.tau;
@@ -415,6 +418,10 @@ ks_status run_phase(Batch &B, std::vector<JobState> &S, const ks_opts &o, double
       const double Qn = o.eta * s.Q + 1.0;
       s.C = (o.eta * s.Q * s.C + s.Et) / Qn;
       s.Q = Qn;
+      if (s.forced && sizeof(T) == 8) {   // FP64: restart the nonmonotone reference
+        s.C = s.Et;
+        s.Q = 1.0;
+      }
       s.E = s.Et;
       ++s.k;
     }

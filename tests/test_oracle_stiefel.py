@@ -167,3 +167,19 @@ def test_nonmonotone_reference_decreases_and_armijo_holds():
         prevC = h["C"]
     assert r.converged and r.dnorm <= 1e-8
     assert all(h["h"] < opt.max_backtrack for h in r.history)
+
+
+def test_forced_acceptance_restarts_the_reference():
+    # With no backtracking allowed and a first step far too long, trials are
+    # taken without meeting the Armijo test; each restarts the nonmonotone
+    # reference at its energy, so C_k >= E_k holds at every iteration (a
+    # reference left below the energy would reject every later step).
+    model, s = _model(N=6, L=6.0, natoms=2, p=2, Z=2.0)
+    opt = stiefel.Options(gtol=1e-8, maxit=60, max_backtrack=0, tau0=5.0)
+    r = stiefel.minimize(model, s.x0(), opt)
+    forced = [h for h in r.history if h["forced"]]
+    assert forced, "the long first step should fail the test"
+    for h in forced:
+        assert h["C"] == h["E"] and h["Q"] == 1.0
+    assert all(h["C"] >= h["E"] - 1e-12 * abs(h["E"]) for h in r.history)
+
