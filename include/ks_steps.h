@@ -73,6 +73,23 @@ ks_status ks_step_gram(ks_problem *prob, const double *A, int pa, const double *
  * for the update). */
 ks_status ks_set_tensor_cores(ks_problem *prob, int mode);
 
+/* FP64 Grams A^T B and updates A1 C1 + A2 C2 (ks_step_gram, ks_step_combine and
+ * every FP64 product of a minimisation) on the tensor cores by error-free
+ * splitting.  Each FP64 entry becomes 8 signed 6-bit digits below the
+ * largest exponent of its Gram column (update: of its row of A, of its
+ * column of C), 48 bits in all.  Every digit product is exact in a BF16 MMA
+ * whose FP32 accumulation stays exact (512-row chunks for the Gram, K <= 128
+ * for the update), and the digit groups are combined exactly before one FP64
+ * rounding.  The result differs from the FP64-pipe product by at most ~2^-46
+ * of sum_k |a_k| |b_k| (the dropped bits), against ~K 2^-53 for FP64
+ * summation.
+ *   mode 0: never (default);
+ *   mode 1: Grams whose operands both have at least 48 columns, and updates
+ *     with K <= 128 and at least 48 output columns;
+ *   mode 2: always (updates with K <= 128).
+ * KS_EINVAL for other modes. */
+ks_status ks_set_fp64_emulation(ks_problem *prob, int mode);
+
 /* Plane staging of the 27-point stencils: 1 (default) TMA tile loads into a
  * shared-memory ring when the row pitch p * element size and the block's
  * base address are multiples of 16 bytes, 0 plain loads always.  Both give

@@ -115,6 +115,7 @@ SIGNATURES = [
     ("ks_step_gram_f32", _I, [_P, _P, _I, _P, _I, _P]),
     ("ks_set_tensor_cores", _I, [_P, _I]),
     ("ks_set_tma", _I, [_P, _I]),
+    ("ks_set_fp64_emulation", _I, [_P, _I]),
     ("ks_step_combine_f32", _I, [_P, _P, _I, _P, _P, _I, _P, _D, _D, _P, _P, _I]),
     ("ks_step_combine", _I, [_P, _P, _I, _P, _P, _I, _P, _D, _D, _P, _P, _I]),
     ("ks_gram_noalloc", _I, [_P, _I, _P, _I, ctypes.c_longlong, _P, _P]),
@@ -486,6 +487,10 @@ class Problem:
     def set_tensor_cores(self, mode: int):
         """FP32-phase tensor cores: 0 never, 1 wide products (default), 2 always."""
         _check(load_library().ks_set_tensor_cores(self._h, mode))
+
+    def set_fp64_emulation(self, mode: int):
+        """FP64 Grams on the tensor cores by digit splitting: 0 never, 1 wide, 2 always."""
+        _check(load_library().ks_set_fp64_emulation(self._h, int(mode)))
 
     def set_tma(self, mode: int):
         """Stencil plane staging: 1 TMA ring (default, when aligned), 0 plain loads."""

@@ -55,6 +55,9 @@ size_t problem_bytes(int N, int p, int sms) {
   b += (size_t)S_COUNT * p * p * sizeof(double);                      // small matrices
   b += (size_t)2 * p * p * sizeof(float);                             // FP32 coefficients
   b += tc_image_floats(p) * sizeof(float);                            // tensor-core image
+  b += (size_t)(2 * p + 128) * sizeof(int);                           // split exponents
+  b += oz_image_bytes(p);                                             // split coefficients
+  b += n * sizeof(int);                                               // row exponents
   size_t part = gram_partials_len(p, sms);
   const size_t red = (size_t)4 * 8 * sms;
   const size_t cg = (size_t)4 * 2 * sms;
@@ -99,7 +102,7 @@ static void free_problem(Problem &P) {
   f(P.vext); f(P.rho); f(P.vH); f(P.veff); f(P.cg_r); f(P.cg_pa); f(P.cg_pb); f(P.cg_q);
   f(P.cg_z); f(P.cg_t1); f(P.cg_t2); f(P.dst_phi); f(P.dst_kap); f(P.dst_mu);
   for (auto &b : P.blk) f(b);
-  f(P.pp); f(P.cf); f(P.tc_img); f(P.partials); f(P.scal); f(P.atoms_dev); f(P.thomas_w); f(P.bar); f(P.red_counter); f(P.dstatus);
+  f(P.pp); f(P.cf); f(P.tc_img); f(P.oz_emax); f(P.oz_img); f(P.oz_rowexp); f(P.partials); f(P.scal); f(P.atoms_dev); f(P.thomas_w); f(P.bar); f(P.red_counter); f(P.dstatus);
   delete[] P.scal_host;
   delete[] P.dstatus_host;
   P.scal_host = nullptr;
@@ -638,6 +641,10 @@ ks_status ks_problem_create(const ks_problem_desc *d, ks_problem **out) {
   ALLOC(P.cf, (size_t)2 * P.p * P.p);
   P.tc_img_len = tc_image_floats(P.p);
   ALLOC(P.tc_img, P.tc_img_len);
+  P.oz_emax_len = 2 * P.p + 128;
+  ALLOC(P.oz_emax, (size_t)P.oz_emax_len);
+  ALLOC(P.oz_img, oz_image_bytes(P.p));
+  ALLOC(P.oz_rowexp, n);
   P.cg_blocks = cg_grid_blocks(P.sms, P.n, P.N);
   if (P.cg_blocks < 1) return fail(set_error(KS_ECUDA, "CG kernel configuration failed"));
   size_t part = gram_partials_len(P.p, P.sms);

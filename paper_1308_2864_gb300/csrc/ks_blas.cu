@@ -290,6 +290,23 @@ __global__ void __launch_bounds__(256) gram_small_kernel(long long n, int pa, in
 
 template <typename T>
 ks_status launch_gram(Problem &P, const T *A, int pa, const T *B, int qb, double *out) {
+  if (sizeof(T) == 8 && P.use_oz > 0 && pa + qb <= P.oz_emax_len &&
+      (P.use_oz == 2 || (pa >= 48 && qb >= 48))) {
+    // FP64: digit-split products on the tensor cores, FP64 chunk partials
+    const int chunks = gram_oz_chunks(P, pa, qb);
+    if ((size_t)chunks * pa * qb > P.partials_len)
+      return set_error(KS_EINVAL, "gram: partial buffer too small");
+    KS_TRY(launch_gram_oz(P, (const double *)A, pa, (const double *)B, qb, P.oz_emax, P.partials,
+                          chunks));
+    const long long len = (long long)pa * qb;
+    {
+      ProfScope ps_(P.stream, KP_REDUCE);
+      gram_reduce_kernel<<<(int)((8 * len + kThreads - 1) / kThreads), kThreads, 0, P.stream>>>(
+          chunks, len, P.partials, out);
+    }
+    KS_CUDA_TRY(cudaGetLastError());
+    return KS_OK;
+  }
   if (sizeof(T) == 4 && use_tensor_cores(P, pa, qb)) {
     // FP32 phase: tensor cores (3 x TF32), FP64 chunk partials
     const int chunks = gram_tc_chunks(P, pa, qb);
@@ -497,6 +514,9 @@ __global__ void coef_convert_kernel(long long len1, const double *__restrict__ C
 template <typename T>
 ks_status launch_combine(Problem &P, const T *A1, int k1, const double *C1, const T *A2, int k2,
                          const double *C2, double alpha, double beta, const T *Bm, T *out, int q) {
+  if (sizeof(T) == 8 && combine_oz_applies(P, k1, A2 ? k2 : 0, q))
+    return launch_combine_oz(P, (const double *)A1, k1, C1, (const double *)A2, k2, C2, alpha,
+                             beta, (const double *)Bm, (double *)out, q);
   if (sizeof(T) == 4 && q > kNarrowQ && use_tensor_cores(P, k1, q))
     return launch_combine_tc(P, (const float *)A1, k1, C1, (const float *)A2, k2, C2, alpha, beta,
                              (const float *)Bm, (float *)out, q);

@@ -100,6 +100,12 @@ struct Problem {
   float *dst_phi = nullptr, *dst_kap = nullptr, *dst_mu = nullptr;
   int cg_precond = 1;
   int use_tc = 1;                  // FP32-phase tensor cores: 0 never, 1 for wide products, 2 always
+  int use_oz = 0;                  // FP64 Grams on the tensor cores by digit splitting: 0 never,
+                                   // 1 when both sides have >= 48 columns, 2 always
+  int *oz_emax = nullptr;          // column exponents of the split operands
+  unsigned char *oz_img = nullptr; // split coefficients of the FP64 tensor-core update
+  int *oz_rowexp = nullptr;        // row exponents of the update's A (n)
+  int oz_emax_len = 0;
   int use_tma = 1;                 // TMA plane staging in the stencils (when the layout allows)
   bool vH_valid = false;           // warm start available
 
@@ -188,6 +194,14 @@ ks_status launch_density(Problem &P, const T *X, double *rho);
 ks_status launch_cg(Problem &P, const double *rho, double *v, double *r, bool warm);
 ks_status launch_sine_setup(Problem &P);
 int cg_grid_blocks(int sms, int n, int N);
+ks_status launch_gram_oz(Problem &P, const double *A, int pa, const double *B, int qb,
+                         int *emax, double *part, int chunks);
+int gram_oz_chunks(const Problem &P, int pa, int qb);
+size_t oz_image_bytes(int p);
+bool combine_oz_applies(const Problem &P, int k1, int k2, int q);
+ks_status launch_combine_oz(Problem &P, const double *A1, int k1, const double *C1,
+                            const double *A2, int k2, const double *C2, double alpha, double beta,
+                            const double *Bm, double *out, int q);
 size_t cg_dynamic_smem(int N);
 // ks_xc.cu: veff = vext + vH + v_xc(rho); energy partials; reduction helpers
 ks_status launch_potential(Problem &P, const double *rho, const double *vH, const double *r,

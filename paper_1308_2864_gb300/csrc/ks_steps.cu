@@ -130,6 +130,12 @@ ks_status ks_set_tensor_cores(ks_problem *kp, int mode) {
   return KS_OK;
 }
 
+ks_status ks_set_fp64_emulation(ks_problem *kp, int mode) {
+  if (!kp || mode < 0 || mode > 2) return set_error(KS_EINVAL, "bad argument");
+  kp->P.use_oz = mode;
+  return KS_OK;
+}
+
 ks_status ks_set_tma(ks_problem *kp, int mode) {
   if (!kp || mode < 0 || mode > 1) return set_error(KS_EINVAL, "bad argument");
   kp->P.use_tma = mode;

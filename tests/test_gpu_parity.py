@@ -461,3 +461,81 @@ def test_qr_retract_large_p():
     Y = dev(s.x0())
     P.orthonormalize(Y)
     assert ost.ortho_error(model, host(Y)) < 1e-12
+
+
+@pytest.mark.parametrize("shape", [(13, 70, 70), (16, 64, 64), (11, 130, 70), (9, 12, 9),
+                                   (45, 64, 64), (7, 1, 3)],
+                         ids=["N13p70", "N16p64", "N11pa130qb70", "N9p12", "N45p64-chunks", "N7p1"])
+def test_fp64_gram_on_tensor_cores(shape):
+    # digit-split FP64 Grams (mode 2: always) against FP64 A^T B: every entry
+    # within 2^-44 of sum_k |A_ki| |B_kj| (48 bits per operand below its
+    # column maximum), on columns spanning 16 orders of magnitude, signs,
+    # a zero column, and n beyond one 512-row chunk per block
+    N, pa, qb = shape
+    s = ki.small_system(N=N, L=7.0, natoms=2, p=max(pa, qb), seed=9)
+    P = make(s)
+    P.set_fp64_emulation(2)
+    rng = np.random.default_rng(N * 1000 + pa)
+    A = rng.standard_normal((N ** 3, pa)) * np.logspace(-8, 8, pa)[None, :]
+    B = rng.standard_normal((N ** 3, qb)) * np.logspace(5, -5, qb)[None, :]
+    if pa > 2:
+        A[:, 1] = 0.0
+    want = A.T @ B
+    bound = np.abs(A).T @ np.abs(B)
+    got = host(P.step_gram(dev(A), dev(B)))
+    assert np.all(np.abs(got - want) <= 2.0 ** -44 * bound + 1e-300)
+    P.set_fp64_emulation(0)
+    ref = host(P.step_gram(dev(A), dev(B)))
+    assert np.all(np.abs(ref - want) <= 1e-12 * bound + 1e-300)
+
+
+@pytest.mark.parametrize("retraction", ["qr", "cayley"])
+def test_fp64_emulated_grams_in_a_minimisation(retraction):
+    s = ki.small_system(N=10, L=7.0, natoms=2, p=2, Z=1.0, seed=7)
+    s.rc = 1.0
+    model = oe.Model.from_system(s)
+    ref = ost.minimize(model, s.x0(), ost.Options(retraction=retraction, gtol=1e-8, maxit=2000))
+    P = make(s)
+    P.set_fp64_emulation(2)
+    X = dev(s.x0())
+    r = P.minimize(X, retraction=retraction, gtol=1e-8, maxit=2000)
+    assert r["status"] == 0 and r["gradnorm"] <= 1e-8
+    assert r["E"] == pytest.approx(ref.E, abs=1e-8)
+    assert ost.ortho_error(model, host(X)) < 1e-12
+
+
+@pytest.mark.parametrize("shape", [(13, 64, 64, 64), (16, 32, 32, 70), (11, 5, 0, 5),
+                                   (45, 64, 64, 64), (9, 100, 28, 50)],
+                         ids=["N13k64+64q64", "N16k32+32q70", "N11k5q5", "N45k64+64q64",
+                              "N9k100+28q50"])
+def test_fp64_update_on_tensor_cores(shape):
+    # digit-split FP64 update out = alpha (A1 C1 + A2 C2) + beta Bm against
+    # FP64.  Each row of [A1 A2] and each column of [C1; C2] is split into 56
+    # bits below its own largest entry, so an entry of the product is within
+    # K 2^-50 max_k |A_ik| max_k |C_kj| (truncation and the dropped digit
+    # pairs) plus the FP64 rounding of the result; rows and columns span 12
+    # orders of magnitude
+    N, k1, k2, q = shape
+    s = ki.small_system(N=N, L=7.0, natoms=2, p=max(k1, k2, q), seed=9)
+    P = make(s)
+    P.set_fp64_emulation(2)
+    rng = np.random.default_rng(N * 100 + k1 + q)
+    n = N ** 3
+    A1 = rng.standard_normal((n, k1)) * np.logspace(-6, 6, n)[:, None]
+    C1 = rng.standard_normal((k1, q)) * np.logspace(3, -3, q)[None, :]
+    A2 = rng.standard_normal((n, k2)) if k2 else None
+    C2 = rng.standard_normal((k2, q)) if k2 else None
+    Bm = rng.standard_normal((n, q))
+    alpha, beta = -0.75, 1.5
+    A = np.hstack([A1, A2]) if k2 else A1
+    C = np.vstack([C1, C2]) if k2 else C1
+    prod = A @ C
+    split = (k1 + k2) * 2.0 ** -50 * np.abs(A).max(axis=1)[:, None] * np.abs(C).max(axis=0)[None, :]
+    got = host(P.step_combine(dev(A1), dev(C1), dev(A2) if k2 else None,
+                              dev(C2) if k2 else None, alpha=alpha, beta=beta, Bm=dev(Bm)))
+    want = alpha * prod + beta * Bm
+    tol = abs(alpha) * split + 4 * 2.0 ** -53 * (np.abs(alpha * prod) + np.abs(beta * Bm))
+    assert np.all(np.abs(got - want) <= tol)
+    got0 = host(P.step_combine(dev(A1), dev(C1), dev(A2) if k2 else None,
+                               dev(C2) if k2 else None, alpha=1.0, beta=0.0))
+    assert np.all(np.abs(got0 - prod) <= split + 4 * 2.0 ** -53 * np.abs(prod))
