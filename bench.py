@@ -5,7 +5,9 @@ jittered 4x4x2 lattice, Slater + PZ81) on one GB300.
 
 One step = one solve from the seeded initial block until ||D||_M <= 1e-6 or
 300 iterations (the iteration cap of the 24^3 protocol and of ks_opts), in
-the plain FP64 form (value) and in the FP32-phase mixed form (config.mixed).
+the plain FP64 form (value), in the FP32-phase mixed form (config.mixed) and
+in FP64 with the Grams and updates on the tensor cores by exact digit
+splitting (config.fp64_split).
 Prints ONE JSON line on rank 0.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
@@ -149,6 +151,12 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def class_shares(prof) -> dict:
+    """Share of each kernel class in the live per-class CUDA-event timings."""
+    total = max(sum(v[0] for v in prof.values()), 1e-9)
+    return {k: round(v[0] / total, 4) for k, v in prof.items() if v[1] > 0}
+
+
 def timed_solves(P, X, X0, opts, steps, warmup, stream, barrier, clk=None):
     """W untimed and K timed solves; returns (ms over the K solves, results,
     per-class profile, kernel launches in the timed region)."""
@@ -225,6 +233,12 @@ def run_gpu(args):
     value = world * args.steps / (ms_max / 1e3)
     ms_m, res_m, prof_m, _ = timed_solves(P, X, X0, mixed, args.steps, args.warmup, stream, barrier)
     ms_m = max_over_ranks(ms_m)
+    # the same FP64 solve with its Grams and updates on the tensor cores by
+    # exact digit splitting (ks_set_fp64_emulation 1)
+    P.set_fp64_emulation(1)
+    ms_s, res_s, prof_s, _ = timed_solves(P, X, X0, fp64, args.steps, args.warmup, stream, barrier)
+    ms_s = max_over_ranks(ms_s)
+    P.set_fp64_emulation(0)
 
     # time to ||D||_M <= 1e-6 on the 24^3 two-atom system (it converges in
     # ~1300 iterations): plain FP64 against the FP32 phase + FP64 polish
@@ -324,8 +338,7 @@ def run_gpu(args):
     per_iter, t_setup, threads = oracle_sample(3)
     cpu_value = 1.0 / (t_setup + per_iter * max(r0["iters"], 1))
     per_solve = [r["seconds"] for r in results]
-    mixed_kernel = {k: round(v[0] / max(sum(x[0] for x in prof_m.values()), 1e-9), 4)
-                    for k, v in prof_m.items() if v[1] > 0}
+    mixed_kernel = class_shares(prof_m)
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
@@ -346,6 +359,17 @@ def run_gpu(args):
                              "final_gradnorm": rm["gradnorm"], "final_energy": rm["E"],
                              "energy_minus_fp64_Ha": rm["E"] - r0["E"],
                              "kernel_shares": mixed_kernel},
+                   "fp64_split": {"solves_per_s": world * args.steps / (ms_s / 1e3),
+                                  "ms_per_step": ms_s / args.steps,
+                                  "ms_per_iteration": ms_s / args.steps / max(res_s[0]["iters"], 1),
+                                  "iters_per_solve": res_s[0]["iters"],
+                                  "final_gradnorm": res_s[0]["gradnorm"],
+                                  "final_energy": res_s[0]["E"],
+                                  "energy_minus_fp64_Ha": res_s[0]["E"] - r0["E"],
+                                  "kernel_shares": class_shares(prof_s),
+                                  "note": "Grams and updates as BF16 tcgen05 MMAs of exact digit "
+                                          "splits (48/56 bits per operand), folded in int64 "
+                                          "before one FP64 rounding"},
                    "c1_time_to_solution": c1_out,
                    "c4_time_to_solution": c4_out},
         "roofline": roof,

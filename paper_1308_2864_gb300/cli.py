@@ -2,7 +2,7 @@
 
   python -m paper_1308_2864_gb300.cli --config c2 --maxit 5 [--precision fp64|mixed]
                                       [--retraction qr|cayley] [--gtol 1e-6] [--verbose 0]
-                                      [--N 40] [--p 512]
+                                      [--N 40] [--p 512] [--fp64-emulation 0|1|2]
 
 --N / --p shrink or change a configuration's grid and orbital count (same
 cube, atoms and functional), e.g. to profile the p = 512 kernels of c3 on a
@@ -40,6 +40,8 @@ def main(argv=None) -> int:
     ap.add_argument("--verbose", type=int, default=0)
     ap.add_argument("--N", type=int, default=0, help="override the interior nodes per edge")
     ap.add_argument("--p", type=int, default=0, help="override the number of orbitals")
+    ap.add_argument("--fp64-emulation", type=int, default=0, choices=[0, 1, 2],
+                    help="FP64 Grams and updates on the tensor cores by digit splitting")
     a = ap.parse_args(argv)
 
     s = ki.CONFIGS[a.config]()
@@ -48,6 +50,7 @@ def main(argv=None) -> int:
     if a.p > 0:
         s.p = a.p
     P = ks.Problem.from_system(s)
+    P.set_fp64_emulation(a.fp64_emulation)
     X = torch.from_numpy(np.ascontiguousarray(s.x0())).cuda()
     t0 = time.perf_counter()
     r = P.minimize(X, retraction=a.retraction or s.retraction, maxit=a.maxit, gtol=a.gtol,
@@ -55,6 +58,7 @@ def main(argv=None) -> int:
     torch.cuda.synchronize()
     r["wall_s"] = time.perf_counter() - t0
     r["config"] = a.config
+    r["fp64_emulation"] = a.fp64_emulation
     print(json.dumps(r))
     return 0
 
