@@ -566,14 +566,16 @@ __global__ void __launch_bounds__(kOzThreads, 1) combine_oz_kernel(
     }
     {
       // groups 2..7 exactly into an int64 (group g shifted left by 7 (7 - g)
-      // bits, below 2^57), 8 and 9 in FP64; units 2^-49 of 2^(E_r + E_c - 2044)
+      // bits, below 2^57), 8 and 9 in FP32 (weight below 2^-42 of the leading
+      // group: the FP32 rounding stays below 2^-66 of the result); units
+      // 2^-49 of 2^(E_r + E_c - 2044)
       const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
       long long tot[32];
-      double tail[32];
+      float tail[32];
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
         tot[j] = 0;
-        tail[j] = 0.0;
+        tail[j] = 0.f;
       }
 #pragma unroll 1
       for (int g = 2; g <= kOzS + 1; ++g) {
@@ -585,20 +587,29 @@ __global__ void __launch_bounds__(kOzThreads, 1) combine_oz_kernel(
           for (int j = 0; j < 32; ++j)
             tot[j] += (long long)__float2int_rn(__uint_as_float(v[j])) * mul;
         } else {
-          const double w = g == 8 ? 1.0 / 128.0 : 1.0 / 16384.0;
+          const float w = g == 8 ? 1.f : 1.f / 128.f;
 #pragma unroll
-          for (int j = 0; j < 32; ++j) tail[j] = fma((double)__uint_as_float(v[j]), w, tail[j]);
+          for (int j = 0; j < 32; ++j) tail[j] = fmaf(__uint_as_float(v[j]), w, tail[j]);
         }
       }
       const long long r = r0 + orow;
       if (r < n) {
         const int er = erow[orow];
+        const bool unit = alpha == 1.0;
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int cj = c0 + ocol0 + j;
           if (cj >= q) continue;
-          const double v = oz_pow2((double)tot[j] + tail[j], er + ecol[ocol0 + j] - 2093);
-          double o = alpha * v;
+          const double x = fma((double)tail[j], 1.0 / 128.0, (double)tot[j]);
+          // x 2^e by adding e to the exponent field (integer pipe) when the
+          // result stays normal, else ldexp
+          const int e = er + ecol[ocol0 + j] - 2093;
+          const long long xb = __double_as_longlong(x);
+          const int ex = (int)((xb >> 52) & 0x7FF);
+          const double v = (ex >= 1 && ex + e >= 1 && ex + e <= 2046)
+                               ? __longlong_as_double(xb + ((long long)e << 52))
+                               : ldexp(x, e);
+          double o = unit ? v : alpha * v;
           if (Bm) o = fma(beta, Bm[r * q + cj], o);
           out[r * q + cj] = o;
         }
