@@ -240,6 +240,30 @@ def run_gpu(args):
     ms_s = max_over_ranks(ms_s)
     P.set_fp64_emulation(0)
 
+    # time to ||D||_M <= 1e-6 with and without the split products on a
+    # 48-orbital system that converges (14^3 grid, 24 atoms)
+    sp = ki.small_system(N=14, L=8.0, natoms=24, p=48, Z=4.0, seed=5)
+    sp.rc = 1.0
+    split_tts = {}
+    for mode in (0, 1):
+        with torch.cuda.stream(stream):
+            Ps = ks.Problem.from_system(sp, stream=stream)
+            Ps.set_fp64_emulation(mode)
+            Xs = torch.from_numpy(np.ascontiguousarray(sp.x0())).cuda()
+            stream.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rs = Ps.minimize(Xs, gtol=GTOL, maxit=20000)
+            e1.record(stream)
+            e1.synchronize()
+        split_tts["split" if mode else "fp64"] = {
+            "seconds": e0.elapsed_time(e1) / 1e3, "iters": rs["iters"], "energy": rs["E"],
+            "converged": rs["status"] == 0}
+        Ps.close()
+    split_tts["energy_difference_Ha"] = split_tts["split"]["energy"] - split_tts["fp64"]["energy"]
+    split_tts["system"] = "14^3 grid, 24 atoms (Z=4, rc=1), p=48, QR, to ||D||_M <= 1e-6"
+
     # time to ||D||_M <= 1e-6 on the 24^3 two-atom system (it converges in
     # ~1300 iterations): plain FP64 against the FP32 phase + FP64 polish
     c1 = ki.config_c1()
@@ -369,7 +393,8 @@ def run_gpu(args):
                                   "kernel_shares": class_shares(prof_s),
                                   "note": "Grams and updates as BF16 tcgen05 MMAs of exact digit "
                                           "splits (48/56 bits per operand), folded in int64 "
-                                          "before one FP64 rounding"},
+                                          "before one FP64 rounding",
+                                  "time_to_solution": split_tts},
                    "c1_time_to_solution": c1_out,
                    "c4_time_to_solution": c4_out},
         "roofline": roof,

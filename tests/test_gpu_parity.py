@@ -539,3 +539,21 @@ def test_fp64_update_on_tensor_cores(shape):
     got0 = host(P.step_combine(dev(A1), dev(C1), dev(A2) if k2 else None,
                                dev(C2) if k2 else None, alpha=1.0, beta=0.0))
     assert np.all(np.abs(got0 - prod) <= split + 4 * 2.0 ** -53 * np.abs(prod))
+
+
+def test_fp64_split_products_reach_the_same_minimiser():
+    # 48 orbitals (the split applies to Grams with >= 48 columns and to the
+    # updates): plain FP64 and split products converge to the same energy
+    import paper_1308_2864_gb300 as ks
+    s = ki.small_system(N=14, L=8.0, natoms=24, p=48, Z=4.0, seed=5)
+    s.rc = 1.0
+    E = []
+    for mode in (0, 1):
+        P = make(s)
+        P.set_fp64_emulation(mode)
+        X = dev(s.x0())
+        r = P.minimize(X, gtol=1e-6, maxit=20000)
+        assert r["status"] == 0 and r["gradnorm"] <= 1e-6
+        E.append(r["E"])
+        assert ost.ortho_error(oe.Model.from_system(s), host(X)) < 1e-11
+    assert E[1] == pytest.approx(E[0], abs=1e-9)
