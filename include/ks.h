@@ -130,6 +130,10 @@ typedef struct {
                           [cg_tol, 1e-3]; FP32 orbitals carry about 1e-7 relative
                           error, so a tighter solve buys nothing there (1e-7).  The FP64
                           polish uses cg_tol. */
+  int fp64_split;     /* 1: for this call, FP64 Grams and updates with at least 48 columns run on
+                         the tensor cores by exact digit splitting (ks_set_fp64_emulation 1);
+                         2: all of them; 0: the problem's own setting (0).  ks_batch_minimize
+                         ignores it (the batched kernels do not split) */
 } ks_opts;
 
 typedef struct {

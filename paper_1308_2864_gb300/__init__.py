@@ -53,7 +53,8 @@ class Opts(ctypes.Structure):
                 ("ortho_every", ctypes.c_int), ("verbose", ctypes.c_int),
                 ("precision", ctypes.c_int), ("polish_gtol", ctypes.c_double),
                 ("stall_iters", ctypes.c_int), ("stall_df", ctypes.c_double),
-                ("resume", ctypes.c_int), ("mixed_cg_tol", ctypes.c_double)]
+                ("resume", ctypes.c_int), ("mixed_cg_tol", ctypes.c_double),
+                ("fp64_split", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):

@@ -566,6 +566,7 @@ void ks_opts_default(ks_opts *o) {
   o->stall_df = 1e-11;
   o->resume = 0;
   o->mixed_cg_tol = 1e-7;
+  o->fp64_split = 0;
 }
 
 const char *ks_last_error_string(void) { return g_err; }
@@ -751,8 +752,13 @@ ks_status ks_minimize(ks_problem *kp, double *X_inout, const ks_opts *opts, ks_r
       !(o.tau0 > 0.0) || o.max_backtrack < 0)
     return set_error(KS_EINVAL, "bad line-search parameters");
   if (o.resume && !kp->P.state.valid) return set_error(KS_EINVAL, "no saved state to resume");
+  if (o.fp64_split < 0 || o.fp64_split > 2) return set_error(KS_EINVAL, "bad fp64_split");
   if (!o.resume) kp->P.vH_valid = false;
-  return minimize_device(kp->P, X_inout, o, res, o.resume != 0);
+  const int use_oz = kp->P.use_oz;
+  if (o.fp64_split > 0) kp->P.use_oz = o.fp64_split;
+  const ks_status st = minimize_device(kp->P, X_inout, o, res, o.resume != 0);
+  kp->P.use_oz = use_oz;
+  return st;
 }
 
 ks_status ks_minimize_host(ks_problem *kp, double *Xh, const ks_opts *opts, ks_result *res) {

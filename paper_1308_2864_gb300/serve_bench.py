@@ -81,6 +81,8 @@ def main(argv=None) -> int:
                     help="c5: arrival rate as a fraction of the measured saturation throughput")
     ap.add_argument("--mode", default="server", choices=["server", "batch"],
                     help="c4: continuous-batching server (per-job streams) or one job table")
+    ap.add_argument("--fp64-split", type=int, default=0, choices=[0, 1, 2],
+                    help="FP64 Grams and updates on the tensor cores by digit splitting")
     ap.add_argument("--no-graphs", action="store_true",
                     help="batch mode: plain launches instead of the captured CUDA graphs")
     ap.add_argument("--autotune", action="store_true",
@@ -89,10 +91,11 @@ def main(argv=None) -> int:
     torch.cuda.init()
     jobs = (ki.config_c4_jobs(njobs=a.jobs) if a.workload == "c4"
             else ki.config_c5_jobs(njobs=a.jobs))
-    opts = dict(retraction="qr", gtol=a.gtol, maxit=a.maxit, precision=a.precision)
+    opts = dict(retraction="qr", gtol=a.gtol, maxit=a.maxit, precision=a.precision,
+                fp64_split=a.fp64_split)
     budget = int(a.budget_gb * (1 << 30))
     out = {"workload": a.workload, "jobs": a.jobs, "slots": a.slots, "precision": a.precision,
-           "maxit": a.maxit, "budget_gb": a.budget_gb, "mode": a.mode}
+           "maxit": a.maxit, "budget_gb": a.budget_gb, "mode": a.mode, "fp64_split": a.fp64_split}
     if a.mode == "batch":
         import paper_1308_2864_gb300 as ks
         t0 = time.perf_counter()
