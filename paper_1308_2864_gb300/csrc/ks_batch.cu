@@ -518,8 +518,9 @@ ks_status build_maps(Batch &B) {
     else put(BM_GRAM_TILED, j, tiles * chunks);
     put(BM_GRAM_REDUCE, j, (8 * p * p + kThreads - 1) / kThreads);
     if (p <= 32) {
+      // the narrow update's work items are groups of 4 columns of a row
       const long long per_comb = 256LL * B.tune.comb_per_thread;
-      long long nb = (n * p + per_comb - 1) / per_comb;
+      long long nb = (n * ((p + 3) / 4) * 4 + per_comb - 1) / per_comb;
       if (nb < 1) nb = 1;
       b.comb_nb = (int)nb;
       put(BM_COMB_NARROW, j, nb);

@@ -229,6 +229,7 @@ __device__ __forceinline__ void gram_small_body(long long n, int pa, int qb, lon
 // entries outside the Gram (the 64-wide tile would spend (64/p)^2 times the
 // work at p = 16).
 constexpr int kMidPQ = 32, kMidRows = 32;
+static_assert(kMidRows * kMidPQ <= 4 * 256, "a stage is 4 values per thread of a 256-thread block");
 
 template <typename T>
 __device__ __forceinline__ void gram_mid_body(long long n, int pa, int qb, long long rows_per,
@@ -248,12 +249,30 @@ __device__ __forceinline__ void gram_mid_body(long long n, int pa, int qb, long 
     ob[u] = e < outs ? e % qb : 0;
   }
   T acc[4] = {0, 0, 0, 0};
+  // the next stage's values travel in registers while this stage computes
+  // (256 threads x 4 cover a stage of kMidRows x kMidPQ)
+  T ra[4], rb[4];
+  auto fetch = [&](long long r) {
+    const int rows = (int)min((long long)kMidRows, r1 - r);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int t = threadIdx.x + u * blockDim.x;
+      ra[u] = t < rows * pa ? A[r * pa + t] : (T)0;
+      rb[u] = t < rows * qb ? B[r * qb + t] : (T)0;
+    }
+  };
+  if (r0 < r1) fetch(r0);
   for (long long r = r0; r < r1; r += kMidRows) {
     const int rows = (int)min((long long)kMidRows, r1 - r);
     __syncthreads();
-    for (int t = threadIdx.x; t < rows * pa; t += blockDim.x) As[t] = A[r * pa + t];
-    for (int t = threadIdx.x; t < rows * qb; t += blockDim.x) Bs[t] = B[r * qb + t];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int t = threadIdx.x + u * blockDim.x;
+      if (t < rows * pa) As[t] = ra[u];
+      if (t < rows * qb) Bs[t] = rb[u];
+    }
     __syncthreads();
+    if (r + kMidRows < r1) fetch(r + kMidRows);
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       if (threadIdx.x + u * blockDim.x >= outs) break;
@@ -463,6 +482,7 @@ __global__ void __launch_bounds__(256) combine_kernel(long long n, int q, const 
 // C matrices in shared memory, no padded arithmetic.
 constexpr int kNarrowQ = 32;
 constexpr int kNarrowK = 2 * kNarrowQ;
+constexpr int kNarrowCols = 4;                     // output columns per thread
 
 template <typename T>
 __device__ __forceinline__ void combine_narrow_body(
@@ -475,21 +495,43 @@ __device__ __forceinline__ void combine_narrow_body(
     for (int e = threadIdx.x; e < k2 * q; e += blockDim.x) Cs[1][e] = (T)C2[e];
   __syncthreads();
   const T alpha = (T)alpha_d, beta = (T)beta_d;
-  const long long total = n * q;
+  // a thread takes kNarrowCols consecutive columns of one row, so each value
+  // of the row of A is loaded once for kNarrowCols FMAs (each output's FMA
+  // chain runs over k in ascending order, as with one output per thread)
+  const int ncg = (q + kNarrowCols - 1) / kNarrowCols;
+  const long long total = n * ncg;
   for (long long e = (long long)vb * blockDim.x + threadIdx.x; e < total;
        e += (long long)vnb * blockDim.x) {
-    const long long row = e / q;
-    const int col = (int)(e - row * q);
-    T acc = 0;
+    const long long row = e / ncg;
+    const int col0 = (int)(e - row * ncg) * kNarrowCols;
+    const int nc = q - col0 < kNarrowCols ? q - col0 : kNarrowCols;
+    T acc[kNarrowCols];
+#pragma unroll
+    for (int u = 0; u < kNarrowCols; ++u) acc[u] = 0;
     const T *a1 = A1 + row * k1;
-    for (int k = 0; k < k1; ++k) acc = fma(a1[k], Cs[0][k * q + col], acc);
+    for (int k = 0; k < k1; ++k) {
+      const T a = a1[k];
+#pragma unroll
+      for (int u = 0; u < kNarrowCols; ++u)
+        if (u < nc) acc[u] = fma(a, Cs[0][k * q + col0 + u], acc[u]);
+    }
     if (A2) {
       const T *a2 = A2 + row * k2;
-      for (int k = 0; k < k2; ++k) acc = fma(a2[k], Cs[1][k * q + col], acc);
+      for (int k = 0; k < k2; ++k) {
+        const T a = a2[k];
+#pragma unroll
+        for (int u = 0; u < kNarrowCols; ++u)
+          if (u < nc) acc[u] = fma(a, Cs[1][k * q + col0 + u], acc[u]);
+      }
     }
-    T v = alpha * acc;
-    if (Bm) v = fma(beta, Bm[e], v);
-    out[e] = v;
+#pragma unroll
+    for (int u = 0; u < kNarrowCols; ++u) {
+      if (u >= nc) break;
+      const long long o = row * q + col0 + u;
+      T v = alpha * acc[u];
+      if (Bm) v = fma(beta, Bm[o], v);
+      out[o] = v;
+    }
   }
 }
 
@@ -521,7 +563,7 @@ ks_status launch_combine(Problem &P, const T *A1, int k1, const double *C1, cons
     return launch_combine_tc(P, (const float *)A1, k1, C1, (const float *)A2, k2, C2, alpha, beta,
                              (const float *)Bm, (float *)out, q);
   if (q <= kNarrowQ && k1 <= kNarrowK && (!A2 || k2 <= kNarrowK)) {
-    const long long total = (long long)P.n * q;
+    const long long total = (long long)P.n * ((q + kNarrowCols - 1) / kNarrowCols);
     long long nb = (total + 255) / 256;
     if (nb > 32LL * P.sms) nb = 32LL * P.sms;
     {
