@@ -118,18 +118,32 @@ __device__ __forceinline__ void stencil_plain_body(const StArgs &a, int vb) {
   T c_old[kStNodesPerThread], f_old[kStNodesPerThread], e_old[kStNodesPerThread];
   T c_mid[kStNodesPerThread], f_mid[kStNodesPerThread], e_mid[kStNodesPerThread];
 
-  // stage plane zp (with halo) and form (c, f, e) of this thread's nodes
-  auto plane = [&](int zp, T *c, T *f, T *e) {
-    __syncthreads();
+  // the halo box of the next plane travels in registers (pf) while the
+  // current plane's outputs are formed; plane() stores it to the shared tile
+  // and forms (c, f, e) of this thread's nodes
+  constexpr int kBox = Tl::HY * Tl::HX * PC;
+  constexpr int kPf = (kBox + kStThreads - 1) / kStThreads;
+  T pf[kPf];
+  auto fetch = [&](int zp) {
     const bool zok = zp >= 0 && zp < N;
-    for (int t = threadIdx.x; t < Tl::HY * Tl::HX * PC; t += kStThreads) {
+#pragma unroll
+    for (int i = 0; i < kPf; ++i) {
+      const int t = threadIdx.x + i * kStThreads;
       const int l = t % PC, hn = t / PC;
       const int hx = hn % Tl::HX, hy = hn / Tl::HX;
       const int gx = x0 + hx - 1, gy = y0 + hy - 1, go = oc * PC + l;
       T v = 0;
-      if (zok && gx >= 0 && gx < N && gy >= 0 && gy < N && go < p)
+      if (t < kBox && zok && gx >= 0 && gx < N && gy >= 0 && gy < N && go < p)
         v = __ldg(A + (((long long)zp * N + gy) * N + gx) * p + go);
-      tile[t] = v;
+      pf[i] = v;
+    }
+  };
+  auto plane = [&](T *c, T *f, T *e) {
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kPf; ++i) {
+      const int t = threadIdx.x + i * kStThreads;
+      if (t < kBox) tile[t] = pf[i];
     }
     __syncthreads();
 #pragma unroll
@@ -142,8 +156,11 @@ __device__ __forceinline__ void stencil_plain_body(const StArgs &a, int vb) {
     }
   };
 
-  plane(z0 - 1, c_old, f_old, e_old);
-  plane(z0, c_mid, f_mid, e_mid);
+  fetch(z0 - 1);
+  plane(c_old, f_old, e_old);
+  fetch(z0);
+  plane(c_mid, f_mid, e_mid);
+  if (z0 < z1) fetch(z0 + 1);
 
   const StCoefT<T> cf(a);
   const T k0 = cf.k0, ke = cf.ke, kc = cf.kc;
@@ -153,7 +170,8 @@ __device__ __forceinline__ void stencil_plain_body(const StArgs &a, int vb) {
 
   for (int z = z0; z < z1; ++z) {
     T c_new[kStNodesPerThread], f_new[kStNodesPerThread], e_new[kStNodesPerThread];
-    plane(z + 1, c_new, f_new, e_new);
+    plane(c_new, f_new, e_new);                    // plane z + 1
+    if (z + 1 < z1) fetch(z + 2);                  // in flight during the outputs of plane z
 #pragma unroll
     for (int r = 0; r < kStNodesPerThread; ++r) {
       const int gx = x0 + lx[r], gy = y0 + ly[r];
