@@ -284,7 +284,10 @@ def run_gpu(args):
             r1 = P1.minimize(Y1, **o)
             ev1.record(stream)
             ev1.synchronize()
-        c1_out[prec] = {"seconds": ev0.elapsed_time(ev1) / 1e3, "iters": r1["iters"],
+        sec = ev0.elapsed_time(ev1) / 1e3
+        c1_out[prec] = {"seconds": sec, "iters": r1["iters"],
+                        "us_per_iteration": 1e6 * sec / max(r1["iters"], 1),
+                        "cg_iters_total": r1["cg_iters_total"], "backtracks": r1["backtracks"],
                         "fp32_phase_iters": r1["mixed_iters"], "gradnorm": r1["gradnorm"],
                         "energy": r1["E"], "converged": r1["status"] == 0}
     c1_out["energy_difference_Ha"] = c1_out["mixed"]["energy"] - c1_out["fp64"]["energy"]
