@@ -394,8 +394,10 @@ static ks_status run_phase(Problem &P, const T *Xstart, T *Xend, const ks_opts &
     bool reortho = false;
     // the Cayley path checks every iteration (Sec. 4.1); the QR path every
     // ortho_every iterations (every 5 in the FP32 phase, whose rounding
-    // drifts faster)
-    const int every = sizeof(T) == 4 ? std::min(o.ortho_every, 5) : o.ortho_every;
+    // drifts faster), and every iteration for one amplitude (p = 1: the check
+    // is one dot product, and the factor of Prop. 3.1 assumes c^T M c = 1,
+    // which an amplitude carrying all the electrons needs to the last bits)
+    const int every = p == 1 ? 1 : (sizeof(T) == 4 ? std::min(o.ortho_every, 5) : o.ortho_every);
     if (o.retraction == KS_CAYLEY || (every > 0 && (first_k + k) % every == 0)) {
       double oerr = 0;
       KS_TRY(ortho_error<T>(P, X(0), MX(0), &oerr));
