@@ -96,7 +96,7 @@ typedef struct {
 
 /* Parameters of Alg. ConOptM (the paper fixes none of their values). */
 typedef struct {
-  int retraction;     /* KS_QR or KS_CAYLEY */
+  int retraction;     /* KS_QR or KS_CAYLEY (KS_QR) */
   double gtol;        /* stop when ||D||_M <= gtol (1e-6) */
   int maxit;          /* iteration limit (300) */
   double tau0;        /* first step and reset value (1e-3) */
@@ -156,7 +156,11 @@ void ks_opts_default(ks_opts *opts);
 
 /* Create a problem: copies the geometry, allocates all device workspace,
  * tabulates the external potential (sum of -Z erf(r/rc)/r) and the ion-ion
- * energy (Eq. EKS, E_II).  *out is NULL on failure. */
+ * energy (Eq. EKS, E_II).  *out is NULL on failure.  The description is
+ * checked on the host before any device call: 2 <= N <= 2048, L > 0,
+ * 1 <= p <= N^3, natoms >= 0 with R and Z given when natoms > 0, rc > 0,
+ * known xc, precision, mass and kinetic values, cg_tol > 0, cg_maxit >= 1,
+ * and for KS_KIN_TFW p = 1 and a finite mu >= 0; KS_EINVAL otherwise. */
 ks_status ks_problem_create(const ks_problem_desc *desc, ks_problem **out);
 ks_status ks_problem_destroy(ks_problem *prob);
 
@@ -231,8 +235,9 @@ ks_status ks_prolong_f32(int Nc, int p, const float *Xc, float *Xf, void *stream
  *   level_results: HOST, `levels` entries, one ks_result per level.
  *   X_host_out: HOST (N^3 x p), or NULL; receives the finest level's final
  *     block.
- * Requires (desc->N + 1) divisible by 2^(levels-1) and N_0 >= 2; KS_EINVAL
- * otherwise.  Returns the finest level's status, or the first error.  All
+ * Requires a valid desc (the checks of ks_problem_create), (desc->N + 1)
+ * divisible by 2^(levels-1) and N_0 >= 2; KS_EINVAL otherwise, before any
+ * device call.  Returns the finest level's status, or the first error.  All
  * device memory is freed before return. */
 ks_status ks_minimize_refine(const ks_problem_desc *desc, int levels, const double *X0_host,
                              const ks_opts *opts, double coarse_gtol, double *X_host_out,
@@ -328,7 +333,9 @@ ks_status ks_server_destroy(ks_server *srv);
 typedef struct ks_batch ks_batch;
 
 /* descs: njobs systems (stream fields ignored); stream: cudaStream_t for all
- * work (NULL = library-owned).  Allocates every job's device state. */
+ * work (NULL = library-owned).  Allocates every job's device state.  Every
+ * description is checked first (the checks of ks_problem_create, p <= 104,
+ * orbital kinetic energy, consistent mass): KS_EINVAL before any device call. */
 ks_status ks_batch_create(const ks_problem_desc *descs, int njobs, void *stream, ks_batch **out);
 
 /* Device bytes held by the batch. */

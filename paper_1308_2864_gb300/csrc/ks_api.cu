@@ -68,7 +68,7 @@ size_t problem_bytes(int N, int p, int sms) {
   return b;
 }
 
-static ks_status validate(const ks_problem_desc *d) {
+ks_status validate_desc(const ks_problem_desc *d) {
   if (!d) return set_error(KS_EINVAL, "null description");
   if (d->N < 2 || d->N > 2048) return set_error(KS_EINVAL, "N = %d out of range [2, 2048]", d->N);
   if (!(d->L > 0.0)) return set_error(KS_EINVAL, "L must be positive");
@@ -574,7 +574,7 @@ void ks_opts_default(ks_opts *o) {
 const char *ks_last_error_string(void) { return g_err; }
 
 size_t ks_problem_bytes(const ks_problem_desc *d) {
-  if (validate(d) != KS_OK) return 0;
+  if (validate_desc(d) != KS_OK) return 0;
   int dev = 0, sms = 152;
   if (cudaGetDevice(&dev) == cudaSuccess)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -585,7 +585,7 @@ size_t ks_problem_bytes(const ks_problem_desc *d) {
 ks_status ks_problem_create(const ks_problem_desc *d, ks_problem **out) {
   if (!out) return set_error(KS_EINVAL, "null output handle");
   *out = nullptr;
-  KS_TRY(validate(d));
+  KS_TRY(validate_desc(d));
   ks_problem *kp = new (std::nothrow) ks_problem();
   if (!kp) return set_error(KS_ENOMEM, "host allocation failed");
   Problem &P = kp->P;

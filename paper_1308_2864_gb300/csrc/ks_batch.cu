@@ -579,6 +579,14 @@ extern "C" {
 ks_status ks_batch_create(const ks_problem_desc *descs, int njobs, void *stream, ks_batch **out) {
   if (!out || !descs || njobs < 1) return set_error(KS_EINVAL, "bad argument");
   *out = nullptr;
+  // every description is checked before the first device call
+  for (int j = 0; j < njobs; ++j) {
+    KS_TRY(validate_desc(&descs[j]));
+    if (descs[j].p > 104) return set_error(KS_EINVAL, "batch: job %d has p > 104", j);
+    if (descs[j].kinetic != KS_KIN_ORBITALS || descs[j].mass != KS_MASS_CONSISTENT)
+      return set_error(KS_EINVAL,
+                       "batch: job %d is orbital-free or lumped (single-system path only)", j);
+  }
   ks_batch *kb = new (std::nothrow) ks_batch();
   if (!kb) return set_error(KS_ENOMEM, "host allocation failed");
   Batch &B = kb->B;
@@ -601,10 +609,6 @@ ks_status ks_batch_create(const ks_problem_desc *descs, int njobs, void *stream,
     B.own_stream = true;
   }
   for (int j = 0; j < njobs; ++j) {
-    if (descs[j].p > 104) return fail(set_error(KS_EINVAL, "batch: job %d has p > 104", j));
-    if (descs[j].kinetic != KS_KIN_ORBITALS || descs[j].mass != KS_MASS_CONSISTENT)
-      return fail(set_error(KS_EINVAL,
-                            "batch: job %d is orbital-free or lumped (single-system path only)", j));
     ks_problem_desc d = descs[j];
     d.stream = B.stream;
     ks_problem *p = nullptr;

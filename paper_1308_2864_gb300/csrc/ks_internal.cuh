@@ -159,6 +159,9 @@ struct Problem {
 };
 
 size_t problem_bytes(int N, int p, int sms);
+// Checks every field of a problem description on the host (no device call);
+// KS_EINVAL with the reason recorded, else KS_OK.
+ks_status validate_desc(const ks_problem_desc *d);
 
 // ---------------------------------------------------------------- profiling
 enum ProfClass : int {

@@ -113,6 +113,7 @@ ks_status ks_minimize_refine(const ks_problem_desc *desc, int levels, const doub
                              const ks_opts *opts, double coarse_gtol, double *X_host_out,
                              ks_result *level_results) {
   if (!desc || !X0_host || !opts || !level_results) return set_error(KS_EINVAL, "null argument");
+  KS_TRY(validate_desc(desc));
   if (levels < 1 || levels > 10) return set_error(KS_EINVAL, "levels = %d out of range", levels);
   if ((desc->N + 1) % (1 << (levels - 1)) != 0)
     return set_error(KS_EINVAL, "N + 1 = %d is not divisible by 2^(levels - 1)", desc->N + 1);
