@@ -307,13 +307,15 @@ ks_status ks_server_submit(ks_server *srv, const ks_problem_desc *desc, const ks
 /* Result of a job: KS_EAGAIN while it is queued or running (wait = 0), or
  * blocks until it finishes (wait != 0).  On completion fills res, X_host
  * (HOST n x p, may be NULL) and latency_s (submit to finish, may be NULL),
- * then forgets the job (a job can be collected once). */
+ * then forgets the job (a job can be collected once: when several threads
+ * wait on the same id, one collects it and the others get KS_EINVAL). */
 ks_status ks_server_poll(ks_server *srv, uint64_t job_id, int wait, ks_result *res,
                          double *X_host, double *latency_s);
 
 ks_status ks_server_stats(ks_server *srv, ks_server_counters *out);
 
-/* Waits for running jobs, drops queued ones, joins the workers. */
+/* Waits for running jobs, drops queued ones, joins the workers.  No other
+ * call on srv may run concurrently with it or follow it. */
 ks_status ks_server_destroy(ks_server *srv);
 
 /* ---------------------------------------------------------------------------

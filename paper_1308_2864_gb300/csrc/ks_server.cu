@@ -204,8 +204,17 @@ ks_status ks_server_poll(ks_server *sv, uint64_t job_id, int wait, ks_result *re
   std::unique_lock<std::mutex> lk(S.mu);
   auto it = S.jobs.find(job_id);
   if (it == S.jobs.end()) return set_error(KS_EINVAL, "unknown job %llu", (unsigned long long)job_id);
+  if (wait) {
+    // look the job up again on every wake-up: another thread's poll of the
+    // same id may have collected (and erased) it meanwhile
+    S.cv_done.wait(lk, [&] {
+      it = S.jobs.find(job_id);
+      return it == S.jobs.end() || it->second->state == 2;
+    });
+    if (it == S.jobs.end())
+      return set_error(KS_EINVAL, "job %llu was collected by another poll", (unsigned long long)job_id);
+  }
   Job &J = *it->second;
-  if (wait) S.cv_done.wait(lk, [&] { return J.state == 2; });
   if (J.state != 2) return KS_EAGAIN;
   if (res) *res = J.result;
   if (X_host) std::memcpy(X_host, J.X.data(), J.X.size() * sizeof(double));

@@ -79,3 +79,33 @@ def test_poll_without_wait_reports_running_jobs():
     rb = srv.poll(b, wait=True)
     srv.close()
     assert ra[0]["iters"] == 300 and rb[0]["iters"] == 5
+
+
+def test_concurrent_polls_of_one_job():
+    # two threads wait on the same id: one collects the job, the other is
+    # told it is gone (never a wait on a job another poll has freed)
+    import threading
+    import paper_1308_2864_gb300 as ks
+    s = ki.config_c1()
+    srv = ks.Server(hbm_budget_bytes=8 << 30, max_slots=1)
+    jid = srv.submit(s, retraction="cayley", maxit=200)
+    out = [None, None]
+
+    def poll(i):
+        try:
+            out[i] = srv.poll(jid, wait=True)
+        except ks.KSError as e:
+            out[i] = e
+
+    ts = [threading.Thread(target=poll, args=(i,)) for i in range(2)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join(timeout=300)
+    alive = any(t.is_alive() for t in ts)
+    srv.close()
+    assert not alive
+    got = [o for o in out if isinstance(o, tuple)]
+    gone = [o for o in out if isinstance(o, ks.KSError)]
+    assert len(got) == 1 and len(gone) == 1
+    assert got[0][0]["iters"] == 200 and gone[0].status == ks.KS_EINVAL
