@@ -776,11 +776,11 @@ ks_status ks_minimize_host(ks_problem *kp, double *Xh, const ks_opts *opts, ks_r
   double *dX = P.blk[B_D1];
   KS_CUDA_TRY(cudaMemcpyAsync(dX, Xh, bytes, cudaMemcpyHostToDevice, P.stream));
   ks_status st = ks_minimize(kp, dX, opts, res);
+  // the staging block may be one of the saved state's slots
+  P.state.valid = false;
   if (st != KS_OK && st != KS_ENOCONV) return st;
   KS_CUDA_TRY(cudaMemcpyAsync(Xh, dX, bytes, cudaMemcpyDeviceToHost, P.stream));
   KS_CUDA_TRY(cudaStreamSynchronize(P.stream));
-  // the staging block may be one of the saved state's slots
-  P.state.valid = false;
   if (res)
     res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   return st;
@@ -836,6 +836,10 @@ ks_status ks_state_load(ks_problem *kp, const void *host_buf, size_t bytes) {
   S.have_prev = hd.have_prev; S.last_improve = hd.last_improve;
   S.C = hd.C; S.Q = hd.Q; S.E = hd.E; S.dnorm2 = hd.dnorm2;
   S.ss = hd.ss; S.sy = hd.sy; S.yy = hd.yy; S.best = hd.best; S.last_tau = hd.last_tau;
+  if (hd.retraction != KS_QR && hd.retraction != KS_CAYLEY)
+    return set_error(KS_EINVAL, "saved state has an unknown retraction");
+  // the blocks are overwritten below: a copy that fails leaves no state
+  P.state.valid = false;
   // canonical slots: current in slot 0, previous in slot 1
   const int order[9] = {B_X0, B_MX0, B_EX0, B_D0, B_MD0, B_X1, B_MX1, B_D1, B_MD1};
   const char *src = (const char *)host_buf + sizeof(hd);

@@ -313,6 +313,35 @@ def test_checkpoint_resume_is_bitwise(precision):
     assert rb["iters"] == 20 and rc["iters"] == 20
 
 
+def test_state_load_rejects_bad_checkpoints():
+    # a checkpoint of another grid, a truncated one and one whose header
+    # names an unknown retraction are refused; a refused load leaves nothing
+    # to resume from, and the intact checkpoint still resumes
+    import struct
+    import paper_1308_2864_gb300 as ks
+    s = ki.small_system(N=12, L=7.0, natoms=2, p=4, Z=4.0, seed=11)
+    kw = dict(retraction="qr", gtol=1e-12)
+    P = make(s)
+    P.minimize(dev(s.x0()), maxit=5, **kw)
+    blob = P.state_save()
+    bad = bytearray(blob)
+    struct.pack_into("<i", bad, 24, 7)           # u64 magic, i32 version, N, p, elem, retraction
+    Q = make(s)
+    for b in (bytes(bad), blob[:200], b"\0" * len(blob)):
+        with pytest.raises(ks.KSError) as e:
+            Q.state_load(b)
+        assert e.value.status == ks.KS_EINVAL
+    with pytest.raises(ks.KSError):
+        Q.minimize(dev(s.x0()), maxit=10, resume=1, **kw)
+    other = make(ki.small_system(N=11, L=7.0, natoms=2, p=4, Z=4.0, seed=11))
+    with pytest.raises(ks.KSError):
+        other.state_load(blob)
+    Q.state_load(blob)
+    r = Q.minimize(torch.empty((s.n, s.p), dtype=torch.float64, device="cuda"), maxit=10,
+                   resume=1, **kw)
+    assert r["iters"] == 5
+
+
 @pytest.mark.parametrize("shape", [(13, 70, 70), (16, 64, 64), (11, 130, 70), (9, 12, 9),
                                    (9, 300, 260)])
 @pytest.mark.parametrize("tc", [0, 2], ids=["fp32-pipes", "tensor-cores"])
