@@ -545,16 +545,7 @@ class Server:
     def submit(self, s, x0: np.ndarray | None = None, **opts) -> int:
         """Queue the ks_inputs.System `s` (initial block s.x0() unless given)."""
         x0 = np.ascontiguousarray(s.x0() if x0 is None else x0, dtype=np.float64)
-        atoms = np.ascontiguousarray(np.asarray(s.atoms, dtype=np.float64).reshape(-1, 3))
-        Z = np.ascontiguousarray(np.asarray(s.Z, dtype=np.float64).reshape(-1))
-        d = ProblemDesc()
-        d.N, d.L, d.natoms = s.N, s.L, len(Z)
-        d.R = atoms.ctypes.data_as(_DP)
-        d.Z = Z.ctypes.data_as(_DP)
-        d.rc, d.p, d.occ, d.xc = s.rc, s.p, s.occ, s.xc
-        d.cg_tol, d.cg_maxit, d.precision, d.cg_precond = 1e-10, 20000, KS_FP64, 1
-        d.kinetic, d.mu = getattr(s, "kinetic", KS_KIN_ORBITALS), getattr(s, "mu", 1.0)
-        d.mass = getattr(s, "mass", KS_MASS_CONSISTENT)
+        d, keep = _system_desc(s)
         o = default_opts(**opts)
         jid = ctypes.c_uint64()
         _check(load_library().ks_server_submit(self._h, ctypes.byref(d), ctypes.byref(o),
@@ -605,17 +596,9 @@ class Batch:
         n = len(self.systems)
         descs = (ProblemDesc * n)()
         self._keep = []
-        for d, s in zip(descs, self.systems):
-            atoms = np.ascontiguousarray(np.asarray(s.atoms, dtype=np.float64).reshape(-1, 3))
-            Z = np.ascontiguousarray(np.asarray(s.Z, dtype=np.float64).reshape(-1))
-            self._keep += [atoms, Z]
-            d.N, d.L, d.natoms = s.N, s.L, len(Z)
-            d.R = atoms.ctypes.data_as(_DP)
-            d.Z = Z.ctypes.data_as(_DP)
-            d.rc, d.p, d.occ, d.xc = s.rc, s.p, s.occ, s.xc
-            d.cg_tol, d.cg_maxit, d.precision, d.cg_precond = 1e-10, 20000, KS_FP64, 1
-            d.kinetic, d.mu = getattr(s, "kinetic", KS_KIN_ORBITALS), getattr(s, "mu", 1.0)
-            d.mass = getattr(s, "mass", KS_MASS_CONSISTENT)
+        for j, s in enumerate(self.systems):
+            descs[j], keep = _system_desc(s)
+            self._keep.append(keep)
         h = ctypes.c_void_p()
         st = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
         _check(lib.ks_batch_create(descs, n, st, ctypes.byref(h)))

@@ -225,3 +225,15 @@ def test_option_defaults_match_the_header(lib):
     b = ks.default_opts()
     for f, _ in ks.Opts._fields_:
         assert getattr(b, f) == getattr(o, f), f
+
+
+def test_binding_batch_refuses_unsupported_jobs_before_device_calls():
+    # the Python job table marshals each system through the same description
+    # as the single-system path; refused jobs raise before any device work
+    import ks_inputs as ki
+    ok = ki.small_system(N=8, L=6.0, natoms=1, p=2, Z=4.0, seed=3)
+    for bad, why in [(ki.small_of_system(N=8), "orbital-free"),
+                     (ki.small_system(N=8, L=6.0, natoms=1, p=105, Z=4.0, seed=3), "p > 104")]:
+        with pytest.raises(ks.KSError) as e:
+            ks.Batch([ok, bad])
+        assert e.value.status == ks.KS_EINVAL and why in str(e.value)
