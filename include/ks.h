@@ -158,7 +158,7 @@ void ks_opts_default(ks_opts *opts);
  * tabulates the external potential (sum of -Z erf(r/rc)/r) and the ion-ion
  * energy (Eq. EKS, E_II).  *out is NULL on failure.  The description is
  * checked on the host before any device call: 2 <= N <= 2048, L > 0,
- * 1 <= p <= N^3, natoms >= 0 with R and Z given when natoms > 0, rc > 0,
+ * 1 <= p <= N^3, N^3 p <= 2^31 - 1 (32-bit entry indices), natoms >= 0 with R and Z given when natoms > 0, rc > 0,
  * known xc, precision, mass and kinetic values, cg_tol > 0, cg_maxit >= 1,
  * and for KS_KIN_TFW p = 1 and a finite mu >= 0; KS_EINVAL otherwise. */
 ks_status ks_problem_create(const ks_problem_desc *desc, ks_problem **out);

@@ -74,6 +74,11 @@ ks_status validate_desc(const ks_problem_desc *d) {
   if (!(d->L > 0.0)) return set_error(KS_EINVAL, "L must be positive");
   if (d->p < 1 || (long long)d->p > (long long)d->N * d->N * d->N)
     return set_error(KS_EINVAL, "p = %d out of range", d->p);
+  // node and entry indices of an n x p block are 32-bit (2^31 - 1 FP64
+  // entries per block is already 223 GB for the 13 blocks of a problem)
+  if ((long long)d->N * d->N * d->N * d->p > 0x7fffffffLL)
+    return set_error(KS_EINVAL, "n p = %lld entries exceeds 2^31 - 1",
+                     (long long)d->N * d->N * d->N * d->p);
   if (d->natoms < 0 || (d->natoms > 0 && (!d->R || !d->Z)))
     return set_error(KS_EINVAL, "bad atom arrays");
   if (!(d->rc > 0.0)) return set_error(KS_EINVAL, "rc must be positive");

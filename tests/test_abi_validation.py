@@ -43,6 +43,7 @@ BAD_DESCS = [
     ({"N": 1}, "N = 1"), ({"N": 2049}, "N = 2049"),
     ({"L": 0.0}, "L must"), ({"L": -1.0}, "L must"), ({"L": math.nan}, "L must"),
     ({"p": 0}, "p = 0"), ({"N": 2, "p": 9}, "p = 9"),
+    ({"N": 1291, "p": 1}, "2^31"), ({"N": 2048, "p": 1}, "2^31"), ({"N": 128, "p": 1024}, "2^31"),
     ({"natoms": -1}, "atom"), ({"R": NULL_R}, "atom"), ({"Z": NULL_R}, "atom"),
     ({"rc": 0.0}, "rc"), ({"xc": 7}, "xc"), ({"precision": 2}, "precision"),
     ({"cg_tol": 0.0}, "CG"), ({"cg_maxit": 0}, "CG"),
@@ -87,6 +88,10 @@ def test_problem_bytes_of_valid_descriptions(lib):
     assert sizes[17, 8] > 5 * 17 ** 3 * 8 * 8
     d, keep = valid_desc(kinetic=ks.KS_KIN_TFW, p=1, mu=0.0, mass=ks.KS_MASS_LUMPED)
     assert lib.ks_problem_bytes(ctypes.byref(d)) > 0
+    # the largest grids with 32-bit entry indices: sizes computed without overflow
+    for N, p in [(1290, 1), (128, 1023)]:
+        d, keep = valid_desc(N=N, p=p)
+        assert lib.ks_problem_bytes(ctypes.byref(d)) > 13 * N ** 3 * p * 8
 
 
 def test_valid_problem_without_a_device_is_a_cuda_error(lib):
