@@ -30,13 +30,30 @@ def test_fcc_clusters_have_the_papers_atom_counts():
 
 
 def test_refinement_grids_match_the_oracle():
-    import importlib.util
-    spec = importlib.util.find_spec("paper_1308_2864_gb300")
-    assert spec is not None
-    # the binding's helper is pure Python (no library load)
-    src = open(spec.origin).read()
-    assert "def refine_grids" in src
-    ns = {}
-    exec(src[src.index("def refine_grids"):src.index("def minimize_refine")], ns)
+    # the binding's helper is pure Python: importing the package loads no
+    # device code
+    import paper_1308_2864_gb300 as ks
     for N, levels in [(15, 3), (159, 2), (255, 4), (11, 1)]:
-        assert ns["refine_grids"](N, levels) == ost.refine_levels(N, levels)
+        assert ks.refine_grids(N, levels) == ost.refine_levels(N, levels)
+
+
+def test_splitmix64_known_outputs():
+    # splitmix64 (Steele, Lea and Flood, OOPSLA 2014): the first outputs of
+    # the generator from state 1234567, and from state 0, as the public-domain
+    # reference implementation prints them
+    g = ki.SplitMix64(1234567)
+    assert [g.next_u64() for _ in range(5)] == [
+        6457827717110365317, 3203168211198807973, 9817491932198370423,
+        4593380528125082431, 16408922859458223821]
+    assert ki.SplitMix64(0).next_u64() == 0xE220A8397B1DCDAF
+
+
+def test_vectorised_stream_equals_the_scalar_one():
+    # uniform_block (numpy, wrapping uint64) and SplitMix64.uniform (Python
+    # integers, masked) give the same doubles, from any offset
+    key = ki.stream_key(1001, 7, ki.STREAM_X0)
+    g = ki.SplitMix64(key)
+    scalar = [g.uniform() for _ in range(300)]
+    assert list(ki.uniform_block(key, 300)) == scalar
+    assert list(ki.uniform_block(key, 100, start=200)) == scalar[200:]
+    assert all(0.0 <= u < 1.0 for u in scalar)
