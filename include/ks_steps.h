@@ -57,10 +57,12 @@ ks_status ks_step_hamiltonian(ks_problem *prob, const double *X, const double *v
 ks_status ks_step_hamiltonian_f32(ks_problem *prob, const float *X, const double *veff,
                                   float *EX, float *MX, double *kinetic);
 
-/* MX = M X (consistent Q1 mass).  DEVICE n x p. */
+/* MX = M X with the problem's mass (consistent Q1, or h^3 I when lumped).
+ * DEVICE n x p. */
 ks_status ks_step_mass(ks_problem *prob, const double *X, double *MX);
 
-/* G = M^{-1} E (three tridiagonal line sweeps).  DEVICE n x p. */
+/* G = M^{-1} E (consistent mass: three tridiagonal line sweeps; lumped:
+ * h^-3 E).  DEVICE n x p; G must not alias E. */
 ks_status ks_step_mass_inverse(ks_problem *prob, const double *E, double *G);
 
 /* out = A^T B: A DEVICE n x pa, B DEVICE n x qb, out DEVICE pa x qb
@@ -75,14 +77,18 @@ ks_status ks_set_tensor_cores(ks_problem *prob, int mode);
 
 /* FP64 Grams A^T B and updates A1 C1 + A2 C2 (ks_step_gram, ks_step_combine and
  * every FP64 product of a minimisation) on the tensor cores by error-free
- * splitting.  Each FP64 entry becomes 8 signed 6-bit digits below the
- * largest exponent of its Gram column (update: of its row of A, of its
- * column of C), 48 bits in all.  Every digit product is exact in a BF16 MMA
- * whose FP32 accumulation stays exact (512-row chunks for the Gram, K <= 128
- * for the update), and the digit groups are combined exactly before one FP64
- * rounding.  The result differs from the FP64-pipe product by at most ~2^-46
- * of sum_k |a_k| |b_k| (the dropped bits), against ~K 2^-53 for FP64
- * summation.
+ * splitting.  Each FP64 entry becomes 8 signed digits below the largest
+ * exponent of its line: 6-bit digits (48 bits) below its Gram column's,
+ * 7-bit digits (56 bits) below its update row's (A) or column's (C).  Every
+ * digit product is exact in a BF16 MMA whose FP32 accumulation stays exact
+ * (512-row chunks for the Gram, K <= 128 for the update); digit pairs of
+ * weight below 2^(-8 b) are not formed, and the digit groups are combined
+ * exactly before one FP64 rounding.  Truncating an entry a_k of a line with
+ * largest magnitude amax loses less than 2^-47 amax (Gram) or 2^-55 amax
+ * (update), so an entry of A^T B differs from the exact sum by about
+ * 2^-47 (max|a| sum|b_k| + max|b| sum|a_k|) plus one rounding, and an update
+ * entry by about 2^-55 (max_k|a_k| sum|c_k| + max_k|c_k| sum|a_k|) plus the
+ * roundings of alpha, beta and Bm; FP64 summation gives ~K 2^-53 sum|a_k b_k|.
  *   mode 0: never (default);
  *   mode 1: Grams whose operands both have at least 48 columns, and updates
  *     with K <= 128 and at least 48 output columns;
