@@ -62,7 +62,7 @@ enum { KS_MASS_CONSISTENT = 0, KS_MASS_LUMPED = 1 };
 
 /* One discretised KS system (Eq. EKS discretised, Sec. 2.3). */
 typedef struct {
-  int N;              /* interior nodes per edge (>= 2) */
+  int N;              /* interior nodes per edge (2 .. 2048, with N^3 p <= 2^31 - 1) */
   double L;           /* cube side in bohr */
   int natoms;         /* number of pseudo-atoms (>= 0) */
   const double *R;    /* HOST, 3*natoms positions (x, y, z) in bohr; copied */
