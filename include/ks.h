@@ -365,8 +365,10 @@ ks_status ks_batch_autotune(ks_batch *batch, int out[4]);
  * result overwrites it).  opts as for ks_minimize (retraction must be KS_QR;
  * KS_MIXED runs the FP32 phase for all jobs, then the FP64 polish for the
  * jobs that reached polish_gtol or stagnated); results: njobs entries.
- * Returns KS_OK when every job converged, KS_ENOCONV when some did not (see
- * results[j].status), another code when the batch could not run. */
+ * results may be NULL; results[j].ortho_err is not computed (-1) and
+ * results[j].seconds is the whole call's wall time.  Returns KS_OK when every
+ * job converged, KS_ENOCONV when some did not (see results[j].status),
+ * another code when the batch could not run. */
 ks_status ks_batch_minimize(ks_batch *batch, double *const *X_inout, const ks_opts *opts,
                             ks_result *results);
 
