@@ -125,7 +125,9 @@ typedef struct {
   double stall_df;    /* stagnation threshold of the FP32 phase (1e-11) */
   int resume;         /* 1: continue from the state of the last ks_minimize on this problem
                          or from ks_state_load (X_inout is then output only); maxit counts
-                         all iterations including those before the checkpoint (0) */
+                         all iterations including those before the checkpoint.
+                         ks_energy_grad, ks_retract, ks_orthonormalize and ks_minimize_host
+                         work in the blocks that hold the state and discard it (0) */
   double mixed_cg_tol; /* KS_MIXED: Hartree CG tolerance during the FP32 phase, clamped to
                           [cg_tol, 1e-3]; FP32 orbitals carry about 1e-7 relative
                           error, so a tighter solve buys nothing there (1e-7).  The FP64
@@ -195,7 +197,9 @@ ks_status ks_retract(ks_problem *prob, int kind, const double *X, const double *
                      double tau, double *Xout);
 
 /* X <- X L^{-T} with X^T M X = L L^T, applied twice (Cholesky QR in the M
- * inner product, Alg. ChQR).  X is DEVICE n x p, updated in place. */
+ * inner product, Alg. ChQR).  X is DEVICE n x p, updated in place; when X^T M X
+ * is not positive definite (dependent or zero columns) returns KS_ENOTPD and
+ * leaves X unchanged. */
 ks_status ks_orthonormalize(ks_problem *prob, double *X);
 
 /* Alg. ConOptM from X_inout (DEVICE n x p, any full-rank block; it is

@@ -702,6 +702,7 @@ ks_status ks_energy_grad(ks_problem *kp, const double *X, double *E, double *EX,
                          double *gradnorm) {
   if (!kp || !X || !E) return set_error(KS_EINVAL, "null argument");
   Problem &P = kp->P;
+  P.state.valid = false;   // the workspace below holds the saved state's blocks
   const size_t bytes = (size_t)P.n * P.p * sizeof(double);
   double e = 0;
   KS_TRY(evaluate<double>(P, X, P.blk[B_EX0], P.blk[B_MX0], &e));
@@ -730,6 +731,7 @@ ks_status ks_retract(ks_problem *kp, int kind, const double *X, const double *EX
   if (kind != KS_QR && kind != KS_CAYLEY) return set_error(KS_EINVAL, "bad retraction kind");
   if (Xout == X || Xout == EX) return set_error(KS_EINVAL, "Xout aliases an input");
   Problem &P = kp->P;
+  P.state.valid = false;
   KS_TRY(launch_mass<double>(P, X, P.blk[B_MX0]));
   Traces tr;
   KS_TRY(project<double>(P, kind, X, EX, P.blk[B_MX0], P.blk[B_D0], P.blk[B_MD0], nullptr, &tr));
@@ -744,7 +746,15 @@ ks_status ks_retract(ks_problem *kp, int kind, const double *X, const double *EX
 ks_status ks_orthonormalize(ks_problem *kp, double *X) {
   if (!kp || !X) return set_error(KS_EINVAL, "null argument");
   Problem &P = kp->P;
-  return orthonormalize<double>(P, X, P.blk[B_X2], P.blk[B_MX2], 2);
+  P.state.valid = false;
+  // work on a copy, so that X is left unchanged when the factor fails
+  const size_t bytes = (size_t)P.n * P.p * sizeof(double);
+  double *W = P.blk[B_X1];
+  KS_CUDA_TRY(cudaMemcpyAsync(W, X, bytes, cudaMemcpyDeviceToDevice, P.stream));
+  KS_TRY(orthonormalize<double>(P, W, P.blk[B_X2], P.blk[B_MX2], 2));
+  KS_CUDA_TRY(cudaMemcpyAsync(X, W, bytes, cudaMemcpyDeviceToDevice, P.stream));
+  KS_CUDA_TRY(cudaStreamSynchronize(P.stream));
+  return KS_OK;
 }
 
 ks_status ks_minimize(ks_problem *kp, double *X_inout, const ks_opts *opts, ks_result *res) {

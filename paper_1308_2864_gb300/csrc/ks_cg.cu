@@ -382,7 +382,8 @@ __device__ void cg_body(const CgArgs &a) {
   int it = 0;
   double beta = 0.0;
   double *pold = a.pa, *pnew = a.pb;
-  bool bad = false;
+  // a non-finite right-hand side or start makes every comparison below false
+  bool bad = !isfinite(rr) || !isfinite(bb);
   while (rr > thr && it < a.maxit) {
     // phase 1: p = s + beta p_old (own nodes), q = K p, p.q
     double pq_l = 0.0;

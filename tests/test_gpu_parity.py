@@ -313,6 +313,64 @@ def test_checkpoint_resume_is_bitwise(precision):
     assert rb["iters"] == 20 and rc["iters"] == 20
 
 
+def test_failures_are_reported_and_leave_the_problem_usable():
+    # host-visible failure paths on inputs that no kernel can fault on: a NaN
+    # orbital entry (KS_ENAN from the energy and from the Hartree step) and a
+    # zero column (KS_ENOTPD from the Cholesky factor, X left unchanged); the
+    # same problem then evaluates a good block to the oracle's energy
+    import paper_1308_2864_gb300 as ks
+    s = ki.small_system(N=10, L=7.0, natoms=2, p=2, Z=2.0, seed=11)
+    model = oe.Model.from_system(s)
+    Xg = ost.m_orthonormalize(model, s.x0())
+    ref = oe.evaluate(model, Xg).E
+    P = make(s, cg_tol=1e-13)
+    Xn = Xg.copy()
+    Xn[123, 1] = float("nan")
+    with pytest.raises(ks.KSError) as e:
+        P.energy_grad(dev(Xn))
+    assert e.value.status == ks.KS_ENAN
+    rho = torch.full((s.n,), float("nan"), dtype=torch.float64, device="cuda")
+    with pytest.raises(ks.KSError) as e:
+        P.step_hartree(rho)
+    assert e.value.status == ks.KS_ENAN
+    Xz = Xg.copy()
+    Xz[:, 1] = 0.0
+    Xd = dev(Xz)
+    with pytest.raises(ks.KSError) as e:
+        P.orthonormalize(Xd)
+    assert e.value.status == ks.KS_ENOTPD
+    assert np.array_equal(host(Xd), Xz)
+    E = P.energy_grad(dev(Xg))[0]
+    assert E == pytest.approx(ref, rel=1e-11)
+    Xo = P.orthonormalize(dev(s.x0()))
+    assert ost.ortho_error(model, host(Xo)) < 1e-12
+
+
+def test_workspace_calls_discard_the_saved_state():
+    # ks_energy_grad, ks_retract and ks_orthonormalize reuse the blocks that
+    # hold a minimisation's state, so afterwards there is nothing to resume
+    import paper_1308_2864_gb300 as ks
+    s = ki.small_system(N=10, L=7.0, natoms=2, p=2, Z=2.0, seed=11)
+    kw = dict(retraction="qr", gtol=1e-12)
+    for call in ("energy_grad", "retract", "orthonormalize"):
+        P = make(s)
+        X = dev(s.x0())
+        P.minimize(X, maxit=5, **kw)
+        assert len(P.state_save()) > 0
+        if call == "energy_grad":
+            P.energy_grad(X)
+        elif call == "retract":
+            E, EX, D, g = P.energy_grad(X, want_ex=True)
+            P.minimize(X, maxit=5, **kw)
+            P.retract(ks.KS_QR, X, EX, 1e-3)
+        else:
+            P.orthonormalize(X)
+        with pytest.raises(ks.KSError):
+            P.state_save()
+        with pytest.raises(ks.KSError):
+            P.minimize(X, maxit=10, resume=1, **kw)
+
+
 def test_state_load_rejects_bad_checkpoints():
     # a checkpoint of another grid, a truncated one and one whose header
     # names an unknown retraction are refused; a refused load leaves nothing
