@@ -127,6 +127,19 @@ ks_status ks_step_combine(ks_problem *prob, const double *A1, int k1, const doub
                           const double *A2, int k2, const double *C2, double alpha,
                           double beta, const double *Bm, double *out, int q);
 
+/* Self-test of the bounded device waits.  Every device-side wait of the
+ * library (the software grid barrier of the cooperative kernels, the
+ * mbarrier waits of the TMA and tensor-core pipelines) gives up after a fixed
+ * number of polls, records KS_ETIMEOUT in the launch's status word and
+ * returns.  The probe runs the grid barrier in a one-block launch while the
+ * barrier expects two blocks, so its wait expires.
+ *   stream   cudaStream_t, or NULL for the legacy default stream
+ *   status   HOST, receives the status the probe recorded (KS_ETIMEOUT when
+ *            the bound works)
+ *   seconds  HOST or NULL, wall time of the call (about a second)
+ * Returns KS_OK when the probe ran and the context is still usable. */
+ks_status ks_selftest_wait_timeout(void *stream, int *status, double *seconds);
+
 /* Allocation-free variant of ks_step_gram, for callers that cannot call
  * cudaMalloc: code that runs while a CUDA graph is being captured (where
  * allocation calls are not permitted), hosts whose device memory is owned by

@@ -120,6 +120,7 @@ SIGNATURES = [
     ("ks_step_combine_f32", _I, [_P, _P, _I, _P, _P, _I, _P, _D, _D, _P, _P, _I]),
     ("ks_step_combine", _I, [_P, _P, _I, _P, _P, _I, _P, _D, _D, _P, _P, _I]),
     ("ks_gram_noalloc", _I, [_P, _I, _P, _I, ctypes.c_longlong, _P, _P]),
+    ("ks_selftest_wait_timeout", _I, [_P, ctypes.POINTER(_I), _DP]),
     ("ks_server_create", _I, [ctypes.c_size_t, _I, ctypes.POINTER(_P)]),
     ("ks_server_submit", _I, [_P, ctypes.POINTER(ProblemDesc), ctypes.POINTER(Opts), _DP,
                               ctypes.POINTER(ctypes.c_uint64)]),
@@ -262,6 +263,16 @@ def prolong(Xc, Nc: int):
     else:
         _check(lib.ks_prolong_f32(Nc, p, _ptr32(Xc), _ptr32(out), st))
     return out
+
+
+def selftest_wait_timeout(stream=None) -> tuple[int, float]:
+    """Run the bounded-wait probe (ks_selftest_wait_timeout): a grid-barrier
+    wait that cannot complete.  Returns (recorded status, seconds)."""
+    st = ctypes.c_int()
+    sec = ctypes.c_double()
+    s = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+    _check(load_library().ks_selftest_wait_timeout(s, ctypes.byref(st), ctypes.byref(sec)))
+    return st.value, sec.value
 
 
 def refine_grids(N: int, levels: int) -> list[int]:

@@ -192,6 +192,7 @@ def test_null_handles_are_rejected(lib):
     assert lib.ks_server_create(1 << 30, 257, ctypes.byref(h)) == ks.KS_EINVAL
     assert lib.ks_server_create(0, 4, ctypes.byref(h)) == ks.KS_EINVAL
     assert lib.ks_server_create(1 << 30, 4, None) == ks.KS_EINVAL
+    assert lib.ks_selftest_wait_timeout(None, None, None) == ks.KS_EINVAL
 
 
 def documented_defaults() -> dict:

@@ -644,3 +644,17 @@ def test_fp64_split_products_reach_the_same_minimiser():
         E.append(r["E"])
         assert ost.ortho_error(oe.Model.from_system(s), host(X)) < 1e-11
     assert E[1] == pytest.approx(E[0], abs=1e-9)
+
+
+def test_bounded_wait_expires_and_the_context_survives():
+    # a grid-barrier wait that nothing completes gives up after its spin
+    # limit and records KS_ETIMEOUT; the next launches run normally
+    import paper_1308_2864_gb300 as ks
+    st, sec = ks.selftest_wait_timeout()
+    assert st == ks.KS_ETIMEOUT
+    assert sec < 60.0
+    s = ki.small_system(N=10, L=7.0, natoms=2, p=2, Z=2.0, seed=11)
+    model = oe.Model.from_system(s)
+    Xg = ost.m_orthonormalize(model, s.x0())
+    E = make(s, cg_tol=1e-13).energy_grad(dev(Xg))[0]
+    assert E == pytest.approx(oe.evaluate(model, Xg).E, rel=1e-11)
