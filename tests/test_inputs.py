@@ -57,3 +57,55 @@ def test_vectorised_stream_equals_the_scalar_one():
     assert list(ki.uniform_block(key, 300)) == scalar
     assert list(ki.uniform_block(key, 100, start=200)) == scalar[200:]
     assert all(0.0 <= u < 1.0 for u in scalar)
+
+
+def _min_separation(atoms):
+    import numpy as np
+    d = np.linalg.norm(atoms[:, None, :] - atoms[None, :, :], axis=-1)
+    d[np.diag_indices(len(atoms))] = np.inf
+    return d.min()
+
+
+def test_single_system_recipes():
+    # the configurations the bench and the parity tests use: grids, atom
+    # placement, charges (2 p electrons = sum Z) and functionals
+    import numpy as np
+    c1 = ki.config_c1()
+    assert (c1.N, c1.L, c1.p, c1.xc, c1.retraction) == (24, 10.0, 4, 0, "cayley")
+    assert c1.h == 0.4 and len(c1.atoms) == 2
+    assert c1.atoms.min() >= 2.5 and c1.atoms.max() <= 7.5
+    assert _min_separation(c1.atoms) >= 1.5
+    for c, (N, L, grid, p) in ((ki.config_c2(), (64, 20.0, (4, 4, 2), 64)),
+                               (ki.config_c3(), (128, 40.0, (8, 8, 4), 512))):
+        assert (c.N, c.L, c.p, c.xc, c.retraction) == (N, L, p, 1, "qr")
+        assert len(c.atoms) == np.prod(grid) and 2 * c.p == c.Z.sum()
+        # every atom within 0.3 bohr (per axis) of its own simple-cubic site
+        sites = np.array([((i + 0.5) * L / grid[0], (j + 0.5) * L / grid[1],
+                           (l + 0.5) * L / grid[2])
+                          for i in range(grid[0]) for j in range(grid[1]) for l in range(grid[2])])
+        assert np.abs(c.atoms - sites).max() <= 0.3
+    for c in (c1, ki.config_c2(), ki.config_c3()):
+        assert c.rc == 0.5 and c.occ == 2.0 and np.all(c.Z == 4.0)
+
+
+def test_job_stream_recipes():
+    import numpy as np
+    jobs = ki.config_c4_jobs()
+    assert len(jobs) == 256
+    Ns = np.array([s.N for s in jobs])
+    assert Ns.min() >= 20 and Ns.max() <= 48 and len(set(Ns)) > 15
+    for s in jobs:
+        natoms = len(s.atoms)
+        assert 2 <= natoms <= 16 and s.p == 2 * natoms and s.L == 0.4 * (s.N + 1)
+        assert s.atoms.min() >= 1.5 and s.atoms.max() <= s.L - 1.5
+        assert _min_separation(s.atoms) >= 0.8
+    stream = ki.config_c5_jobs()
+    for s in stream:
+        assert 24 <= s.N <= 96 and 8 <= s.p <= 128 and s.p % 2 == 0
+        assert len(s.atoms) == s.p // 2
+    # the same seed gives the same jobs
+    again = ki.config_c4_jobs(njobs=3)
+    assert all(np.array_equal(a.atoms, b.atoms) for a, b in zip(again, jobs[:3]))
+    t = ki.poisson_arrivals(1004, 2000, rate=4.0)
+    assert np.all(np.diff(t) > 0)
+    assert abs(len(t) / t[-1] - 4.0) < 0.4                   # mean rate
