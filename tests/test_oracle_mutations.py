@@ -185,6 +185,19 @@ def prolong_midpoints_quartered(mp):
     mp.setattr(fe, "prolong_1d", p1)
 
 
+def vw_weight_ignored(mp):
+    mp.setattr(energy.Model, "kin_weight", property(lambda self: 1.0))
+
+
+def lumped_mass_ignored(mp):
+    mp.setattr(energy.Model, "apply_M", lambda self, X: fe.apply_M(X, self.N, self.h))
+
+
+def tf_potential_without_five_thirds(mp):
+    orig = energy.thomas_fermi
+    mp.setattr(energy, "thomas_fermi", lambda rho: (orig(rho)[0], 0.6 * orig(rho)[1]))
+
+
 SCF_CASE = dict(N=7, L=6.0, natoms=1, p=1, Z=2.0, seed=7)
 EXT_ONLY = dict(use_hartree=False, use_xc=False)
 
@@ -224,6 +237,10 @@ CASES = {
                                       [pof.test_thomas_fermi_is_the_free_electron_gas]),
     "prolongation midpoints 1/4": (prolong_midpoints_quartered,
                                    [pre.test_prolong_is_the_trilinear_interpolant]),
+    "von Weizsaecker weight ignored": (vw_weight_ignored, [pof.test_of_parts]),
+    "lumped mass ignored": (lumped_mass_ignored, [pof.test_of_parts]),
+    "v_TF without 5/3": (tf_potential_without_five_thirds,
+                         [pof.test_thomas_fermi_potential_is_the_derivative]),
 }
 
 

@@ -85,7 +85,8 @@ def test_of_gradient_central_difference(terms):
 
 
 def test_of_parts():
-    model, s = _of_model()
+    # a von Weizsaecker weight other than 1, so that the weight is pinned
+    model, s = _of_model(mu=0.37)
     c = stiefel.m_orthonormalize(model, s.x0())
     ev = energy.evaluate(model, c)
     assert ev.E == pytest.approx(sum(ev.parts.values()), rel=1e-15)
@@ -94,7 +95,8 @@ def test_of_parts():
     tf = model.h ** 3 * float(np.sum(energy.thomas_fermi(rho)[0]))
     KX = fe.apply_K(c, model.N, model.h)
     vw = 0.5 * model.occ * float(np.sum(c * KX))
-    assert ev.parts["kinetic"] == pytest.approx(model.mu * vw + tf, rel=1e-14)
+    assert model.mu == 0.37
+    assert ev.parts["kinetic"] == pytest.approx(0.37 * vw + tf, rel=1e-14)
     assert tf > 0 and vw > 0
     # the electron count the constraint fixes, f c^T M c = N_e, is the
     # integral of the nodal density under the lumped mass
