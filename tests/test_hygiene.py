@@ -32,7 +32,8 @@ def test_no_batched_copy_entry_points():
 
 def test_code_does_not_point_into_planning_documents():
     words = ["SURVEY", "DESIGN" + ".md", "BASELINE" + ".json", "BASELINE" + ".md", "VERDICT",
-             "ADVICE" + ".md", "north" + "_star", "gpu" + "run", "/root" + "/", "configs" + "["]
+             "ADVICE" + ".md", "north" + "_star", "gpu" + "run", "/root" + "/", "configs" + "[",
+             "_work" + "/"]
     me = os.path.abspath(__file__)
     for path in sources():
         if os.path.abspath(path) == me:
