@@ -1,6 +1,7 @@
 """Pins of the oracle's KS functional (Eq. EKS discretised, Sec. 2.3) and its
 derivative E_X (Eq. "partial deriv"), LDA, external potential and E_II."""
 import math
+from pathlib import Path
 
 import numpy as np
 import pytest
@@ -29,6 +30,50 @@ def test_pz81_branches_meet_at_rs1():
     assert abs(below[0][0] - above[0][0]) < 1e-13
     assert abs(below[1][0] - above[1][0]) < 1e-12
     assert round(energy.PZ_C, 4) == 0.0020 and round(energy.PZ_D, 4) == -0.0116
+
+
+GOLDEN = Path(__file__).parent / "golden"
+
+
+def published_pz81():
+    """The unpolarised PZ81 parameters as printed in the publication
+    (tests/golden/pz81_unpolarized.txt, with its citation)."""
+    out = {}
+    for line in (GOLDEN / "pz81_unpolarized.txt").read_text().splitlines():
+        if line.strip() and not line.startswith("#"):
+            name, value = line.split()
+            out[name] = float(value)
+    return out
+
+
+def test_pz81_constants_are_the_published_ones():
+    # gamma, beta1, beta2, A and B are taken as printed; C and D are the
+    # continuity coefficients, which must round to the printed 4 decimals.
+    pub = published_pz81()
+    assert energy.PZ_GAMMA == pub["gamma"]
+    assert energy.PZ_BETA1 == pub["beta1"]
+    assert energy.PZ_BETA2 == pub["beta2"]
+    assert energy.PZ_A == pub["A"]
+    assert energy.PZ_B == pub["B"]
+    assert abs(energy.PZ_C - pub["C"]) <= 0.5e-4
+    assert abs(energy.PZ_D - pub["D"]) <= 0.5e-4
+
+
+def test_pz81_low_density_branch_uses_the_published_parameters():
+    # On the r_s >= 1 branch eps_c depends only on gamma, beta1 and beta2:
+    # evaluated with the printed values it must match the oracle to rounding
+    # (a transposed digit in beta2, 0.3334 -> 0.3343, moves eps_c(r_s = 10)
+    # by 3e-5 relative).
+    pub = published_pz81()
+    rs = np.array([1.0, 2.0, 5.0, 10.0, 40.0])
+    rho = 3.0 / (4.0 * math.pi * rs ** 3)
+    want = pub["gamma"] / (1.0 + pub["beta1"] * np.sqrt(rs) + pub["beta2"] * rs)
+    got = energy.pz81(rho * (1.0 - 1e-15))[0]
+    np.testing.assert_allclose(got, want, rtol=1e-12)
+    # and the r_s < 1 branch at r_s -> 0 follows A ln r_s + B to O(r_s ln r_s)
+    r = np.array([1e-6, 1e-7])
+    e = energy.pz81(3.0 / (4.0 * math.pi * r ** 3))[0]
+    np.testing.assert_allclose(e, pub["A"] * np.log(r) + pub["B"], rtol=0, atol=1e-7)
 
 
 def test_pz81_energy_is_smooth_across_rs1():

@@ -78,6 +78,10 @@ def pz81_beta2_sign(mp):
     mp.setattr(energy, "PZ_BETA2", -energy.PZ_BETA2)
 
 
+def pz81_beta2_digits_transposed(mp):
+    mp.setattr(energy, "PZ_BETA2", 0.3343)
+
+
 def eii_double_counted(mp):
     orig = energy.e_ii
     mp.setattr(energy, "e_ii", lambda atoms, Z: 2.0 * orig(atoms, Z))
@@ -214,6 +218,10 @@ CASES = {
     "v_x equal to eps_x": (slater_potential_is_energy_density,
                            [lambda: pen.test_vxc_is_derivative_of_rho_eps(energy.XC_SLATER)]),
     "PZ81 beta2 sign": (pz81_beta2_sign, [pen.test_pz81_branches_meet_at_rs1]),
+    "PZ81 beta2 digits transposed": (
+        pz81_beta2_digits_transposed,
+        [pen.test_pz81_constants_are_the_published_ones,
+         pen.test_pz81_low_density_branch_uses_the_published_parameters]),
     "E_II double counted": (eii_double_counted, [pen.test_eii_two_atoms]),
     "Hartree without 4 pi": (hartree_without_4pi,
                              [lambda: pst.test_minimize_interacting_matches_scf(SCF_CASE, "qr")]),
