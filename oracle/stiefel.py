@@ -152,6 +152,13 @@ class Options:
     tau_max: float = 1e10
     max_backtrack: int = 10
     ortho_tol: float = 1e-12
+    # Rounding slack of the Armijo test: when set, a trial is also accepted
+    # if its energy exceeds C - rho1 tau ||D||^2 by at most
+    # 4 eps sum |E_parts| (eps = 2^-52), the rounding of the energy sums.
+    # In exact arithmetic the test of Eq. NMLS-Armijo always accepts a small
+    # enough step; in FP64 near convergence the required decrease falls below
+    # that rounding and the exact test backtracks at random.  Off by default.
+    armijo_slack: bool = False
 
 
 @dataclass
@@ -191,6 +198,13 @@ def bb_step(k: int, ss: float, sy: float, yy: float, opt: Options) -> float:
     return min(max(tau, opt.tau_min), opt.tau_max)
 
 
+def armijo_slack(parts: dict, opt: Options) -> float:
+    """4 eps sum |E_parts| when opt.armijo_slack is set, else 0."""
+    if not opt.armijo_slack:
+        return 0.0
+    return 4.0 * 2.220446049250313e-16 * sum(abs(v) for v in parts.values())
+
+
 def minimize(model: Model, X0: np.ndarray, opt: Options | None = None,
              orthonormalize: bool = True, callback=None) -> Result:
     """Alg. ConOptM.  X0 is M-orthonormalised first unless told otherwise."""
@@ -213,7 +227,9 @@ def minimize(model: Model, X0: np.ndarray, opt: Options | None = None,
         while True:
             Xn = retract(model, cur, tau)
             trial = point_at(model, Xn, cur.ev.vH)
-            ok = trial.E <= C - opt.rho1 * tau * cur.dnorm2
+            bound = C - opt.rho1 * tau * cur.dnorm2
+            slack = armijo_slack(trial.ev.parts, opt)
+            ok = trial.E <= bound + slack
             if ok or h == opt.max_backtrack:
                 break
             tau *= opt.delta
@@ -230,7 +246,7 @@ def minimize(model: Model, X0: np.ndarray, opt: Options | None = None,
             trial = point_at(model, m_orthonormalize(model, trial.X, passes=1), cur.ev.vH)
         history.append({"k": k, "E": trial.E, "dnorm": trial.dnorm, "tau": tau, "h": h,
                         "C": C, "Q": Q, "ortho": oerr, "cg": trial.ev.cg_iters,
-                        "forced": not ok})
+                        "forced": not ok, "excess": trial.E - bound, "slack": slack})
         prev, cur = cur, trial
         k += 1
         if callback is not None:

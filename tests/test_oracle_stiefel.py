@@ -183,3 +183,28 @@ def test_forced_acceptance_restarts_the_reference():
         assert h["C"] == h["E"] and h["Q"] == 1.0
     assert all(h["C"] >= h["E"] - 1e-12 * abs(h["E"]) for h in r.history)
 
+
+
+def test_armijo_rounding_slack_stays_within_its_bound():
+    # The rounding slack of the FP64 line search (accept a rise of at most
+    # 4 eps sum |E_parts| above the Armijo bound of Eq. NMLS-Armijo): with it
+    # on, no unforced step exceeds the exact test's bound by more than the
+    # slack, and the run reaches the same minimiser as the exact test, deep
+    # into the regime where the required decrease is below the rounding of E.
+    model, s = _model(N=6, L=6.0, natoms=2, p=2, Z=2.0)
+    exact = stiefel.minimize(model, s.x0(), stiefel.Options(gtol=1e-9, maxit=600))
+    opt = stiefel.Options(gtol=1e-9, maxit=600, armijo_slack=True)
+    slack = stiefel.minimize(model, s.x0(), opt)
+    assert exact.converged and slack.converged
+    eps = 2.220446049250313e-16
+    for h in slack.history:
+        assert 0.0 < h["slack"] < 1e-12
+        if not h["forced"]:
+            assert h["excess"] <= h["slack"]
+    assert slack.E == pytest.approx(exact.E, abs=1e-11)
+    assert all(h["excess"] <= 0.0 or h["forced"] for h in exact.history)
+    # and the bound is the stated one: recompute it from a trial's parts
+    pt = _feasible_point(model, s)
+    assert stiefel.armijo_slack(pt.ev.parts, opt) == pytest.approx(
+        4.0 * eps * sum(abs(v) for v in pt.ev.parts.values()), rel=1e-15)
+    assert stiefel.armijo_slack(pt.ev.parts, stiefel.Options()) == 0.0
