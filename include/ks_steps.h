@@ -140,26 +140,47 @@ ks_status ks_step_combine(ks_problem *prob, const double *A1, int k1, const doub
  * Returns KS_OK when the probe ran and the context is still usable. */
 ks_status ks_selftest_wait_timeout(void *stream, int *status, double *seconds);
 
+/* Peak-rate probe of the FMA pipes, the denominator of the roofline of the
+ * FP64 n p^2 contractions (Grams and updates of Sec. 3, rows of Alg. ConOptM)
+ * and of the FP32 SIMT kernels.  Enqueues one kernel of `blocks` blocks of
+ * 256 threads on `stream`; each thread runs 8 independent FMA recurrences
+ * for 4 * iters rounds with no memory traffic.  The caller times the launch
+ * (e.g. with events on the same stream); nothing is synchronised here.
+ *   fp64    nonzero: FP64 FMAs; zero: FP32 FMAs
+ *   blocks  grid size (a multiple of the SM count keeps every SM busy)
+ *   iters   rounds of 4 x 8 FMAs per thread
+ *   stream  cudaStream_t, or NULL for the legacy default stream
+ *   sink    DEVICE, at least `blocks` doubles; written only under a condition
+ *           the recurrence never meets, so its contents stay as they are
+ *   flops   HOST, receives the flop count of the launch (2 per FMA)
+ * Returns KS_EINVAL for null pointers or non-positive sizes. */
+ks_status ks_probe_fma(int fp64, int blocks, int iters, void *stream, double *sink,
+                       double *flops);
+
 /* Allocation-free variant of ks_step_gram, for callers that cannot call
- * cudaMalloc: code that runs while a CUDA graph is being captured (where
- * allocation calls are not permitted), hosts whose device memory is owned by
- * their own allocator or a fixed budget, and latency-bound loops that must not
- * pay for an allocation.  It needs no ks_problem (ks_problem_create
- * allocates) and calls no allocating routine: the per-chunk partial sums live
- * in a file-scope device array of 2^21 doubles (16 MiB) that every GPU which
- * loads the library holds until the process exits.  The paper has no
- * counterpart; this is a deployment convenience around the Gram of Sec. 3.
+ * cudaMalloc: a host process whose device memory is owned by its own
+ * allocator or reserved up front under a fixed budget (a serving process that
+ * must not grow past what it reserved), code running inside another library's
+ * callback where calling into the CUDA allocator is not allowed, and
+ * latency-bound loops that must not pay for an allocation.  It needs no
+ * ks_problem (ks_problem_create allocates) and calls no allocating routine:
+ * the per-chunk partial sums live in a file-scope device array of 2^21
+ * doubles (16 MiB) that every GPU which loads the library holds until the
+ * process exits.  The paper has no counterpart.
  *   A    DEVICE n x pa (row-major, FP64)
  *   B    DEVICE n x qb (row-major, FP64)
  *   out  DEVICE pa x qb, receives A^T B
  *   stream  cudaStream_t to issue on (NULL = legacy default stream)
  * Requires pa * qb <= 2^21 (returns KS_EINVAL otherwise).  The first call on a
  * device looks up the array's device address for that device (with it
- * current); make that first call before any stream capture.  The call only
- * enqueues work: the result is ready when `stream` reaches it.  All calls in
- * the process share the one array and every call overwrites all of it that
- * it reads, so calls whose executions overlap on the GPU (for example on two
- * streams at once) race and must be serialised by the caller. */
+ * current) and keeps it for the life of the process; make that first call
+ * before any stream capture, and do not use this entry point after a
+ * cudaDeviceReset in the same process (the kept address would be stale).
+ * The call only enqueues work: the result is ready when `stream` reaches it.
+ * All calls in the process share the one array and every call overwrites all
+ * of it that it reads, so calls whose executions overlap on the GPU (for
+ * example on two streams at once) race and must be serialised by the
+ * caller. */
 ks_status ks_gram_noalloc(const double *A, int pa, const double *B, int qb, long long n,
                           double *out, void *stream);
 

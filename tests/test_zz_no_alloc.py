@@ -1,8 +1,10 @@
 """The allocation-free Gram entry point (ks_gram_noalloc), called through the
 C ABI, against the problem-based entry point (ks_step_gram).  It exists for
-callers that cannot allocate device memory (graph capture, host-owned memory
-budgets), so it takes its scratch from a file-scope device array instead of
-cudaMalloc.  Kept in a file of its own that pytest collects last."""
+callers that cannot allocate device memory: processes whose device memory is
+owned by their own allocator or reserved under a fixed budget, and code that
+must not call into the CUDA allocator.  Its scratch is a file-scope device
+array instead of memory from cudaMalloc.  Kept in a file of its own that
+pytest collects last."""
 import ctypes
 
 import numpy as np
@@ -32,6 +34,26 @@ def test_noalloc_gram_matches_problem_gram_twice():
         want = P.step_gram(A, B)
         out = torch.full((s.p, s.p - 3), float("nan"), dtype=torch.float64, device="cuda")
         st = lib.ks_gram_noalloc(A.data_ptr(), s.p, B.data_ptr(), s.p - 3, s.n, out.data_ptr(),
+                                 ctypes.c_void_p(stream.cuda_stream))
+        assert st == ks.KS_OK
+        stream.synchronize()
+        assert _rel(out, want) <= 1e-12
+
+
+def test_noalloc_gram_small_widths_twice():
+    # widths below one 64-wide tile (the padded tile path), two calls in a row
+    import paper_1308_2864_gb300 as ks
+    lib = ks.load_library()
+    s = ki.small_system(N=11, L=6.0, natoms=1, p=5, Z=2.0, seed=9)
+    P = ks.Problem.from_system(s)
+    stream = torch.cuda.current_stream()
+    rng = np.random.default_rng(23)
+    for pa, qb in ((5, 3), (1, 8)):
+        A = torch.from_numpy(rng.standard_normal((s.n, pa))).cuda()
+        B = torch.from_numpy(rng.standard_normal((s.n, qb))).cuda()
+        want = P.step_gram(A, B)
+        out = torch.full((pa, qb), float("nan"), dtype=torch.float64, device="cuda")
+        st = lib.ks_gram_noalloc(A.data_ptr(), pa, B.data_ptr(), qb, s.n, out.data_ptr(),
                                  ctypes.c_void_p(stream.cuda_stream))
         assert st == ks.KS_OK
         stream.synchronize()
