@@ -136,6 +136,19 @@ typedef struct {
                          the tensor cores by exact digit splitting (ks_set_fp64_emulation 1);
                          2: all of them; 0: the problem's own setting (0).  ks_batch_minimize
                          ignores it (the batched kernels do not split) */
+  int fp32_increment; /* KS_MIXED: 1: the FP32 phase carries X = X_b + delta, an FP64 base
+                         (refreshed every 32 iterations, M-orthonormalised in FP64) plus an
+                         FP32 increment; the density, kinetic energy and retraction are
+                         formed on the increment and the rest of the energy from the FP64
+                         density (FP64 xc, Hartree to cg_tol), so its rounding scales with
+                         |delta|.  The gradient is formed the same way (E_X, the Gram
+                         E_X^T X and D as FP64 values at the base plus FP32 increments), so
+                         the phase runs to gtol itself, or until ||D||_M has not improved by
+                         0.1 % for 50000 iterations (stall_iters = 1); the FP64 polish then
+                         confirms gtol; polish_gtol, stall_df and mixed_cg_tol do not apply.
+                         0: the FP32 phase on an FP32 iterate (stops at its rounding floor,
+                         ||D||_M ~ 1e-3 on large systems) (1).  ks_batch_minimize ignores
+                         it */
 } ks_opts;
 
 typedef struct {

@@ -54,7 +54,7 @@ class Opts(ctypes.Structure):
                 ("precision", ctypes.c_int), ("polish_gtol", ctypes.c_double),
                 ("stall_iters", ctypes.c_int), ("stall_df", ctypes.c_double),
                 ("resume", ctypes.c_int), ("mixed_cg_tol", ctypes.c_double),
-                ("fp64_split", ctypes.c_int)]
+                ("fp64_split", ctypes.c_int), ("fp32_increment", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -121,6 +121,7 @@ SIGNATURES = [
     ("ks_step_combine", _I, [_P, _P, _I, _P, _P, _I, _P, _D, _D, _P, _P, _I]),
     ("ks_gram_noalloc", _I, [_P, _I, _P, _I, ctypes.c_longlong, _P, _P]),
     ("ks_selftest_wait_timeout", _I, [_P, ctypes.POINTER(_I), _DP]),
+    ("ks_probe_fma", _I, [_I, _I, _I, _P, _P, _DP]),
     ("ks_server_create", _I, [ctypes.c_size_t, _I, ctypes.POINTER(_P)]),
     ("ks_server_submit", _I, [_P, ctypes.POINTER(ProblemDesc), ctypes.POINTER(Opts), _DP,
                               ctypes.POINTER(ctypes.c_uint64)]),
@@ -273,6 +274,21 @@ def selftest_wait_timeout(stream=None) -> tuple[int, float]:
     s = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
     _check(load_library().ks_selftest_wait_timeout(s, ctypes.byref(st), ctypes.byref(sec)))
     return st.value, sec.value
+
+
+def probe_fma(fp64: bool, blocks: int, iters: int, sink, stream=None) -> float:
+    """Enqueue the FMA peak-rate probe (ks_probe_fma) on `stream` (a torch
+    stream; default the current one); `sink` is a device float64 tensor of at
+    least `blocks` entries.  Returns the launch's flop count; the caller
+    times it."""
+    import torch
+    if sink.dtype != torch.float64 or not sink.is_cuda or sink.numel() < blocks:
+        raise TypeError("sink must be a CUDA float64 tensor with at least `blocks` entries")
+    st = (stream or torch.cuda.current_stream()).cuda_stream
+    fl = ctypes.c_double()
+    _check(load_library().ks_probe_fma(1 if fp64 else 0, blocks, iters, ctypes.c_void_p(st),
+                                       _ptr(sink), ctypes.byref(fl)))
+    return fl.value
 
 
 def refine_grids(N: int, levels: int) -> list[int]:

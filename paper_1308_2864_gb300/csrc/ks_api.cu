@@ -49,9 +49,9 @@ static size_t gram_partials_len(int p, int sms) {
 
 size_t problem_bytes(int N, int p, int sms) {
   const size_t n = (size_t)N * N * N;
-  size_t b = 9 * n * sizeof(double) + 2 * n * sizeof(float);          // n-vectors
+  size_t b = 12 * n * sizeof(double) + 2 * n * sizeof(float);         // n-vectors
   b += ((size_t)N * N + 2 * N) * sizeof(float);                      // sine basis
-  b += (size_t)Problem::kNBlocks * n * p * sizeof(double);            // n x p blocks
+  b += (size_t)Problem::kNBlocks * (n * p * sizeof(double) + 256);    // n x p blocks
   b += (size_t)S_COUNT * p * p * sizeof(double);                      // small matrices
   b += (size_t)2 * p * p * sizeof(float);                             // FP32 coefficients
   b += tc_image_floats(p) * sizeof(float);                            // tensor-core image
@@ -104,7 +104,7 @@ ks_status validate_desc(const ks_problem_desc *d) {
 static void free_problem(Problem &P) {
   cudaStream_t s = P.stream;
   auto f = [s](void *q) { if (q) cudaFreeAsync(q, s); };
-  f(P.vext); f(P.rho); f(P.vH); f(P.veff); f(P.cg_r); f(P.cg_pa); f(P.cg_pb); f(P.cg_q);
+  f(P.vext); f(P.rho); f(P.vH); f(P.veff); f(P.rho_b); f(P.veff_b); f(P.zero_n); f(P.cg_r); f(P.cg_pa); f(P.cg_pb); f(P.cg_q);
   f(P.cg_z); f(P.cg_t1); f(P.cg_t2); f(P.dst_phi); f(P.dst_kap); f(P.dst_mu);
   for (auto &b : P.blk) f(b);
   f(P.pp); f(P.cf); f(P.tc_img); f(P.oz_emax); f(P.oz_img); f(P.oz_rowexp); f(P.partials); f(P.scal); f(P.atoms_dev); f(P.thomas_w); f(P.bar); f(P.red_counter); f(P.dstatus);
@@ -343,6 +343,7 @@ static ks_status run_phase(Problem &P, const T *Xstart, T *Xend, const ks_opts &
   auto save_state = [&]() {
     S.valid = true;
     S.elem = (int)sizeof(T);
+    S.split = 0;
     S.retraction = o.retraction;
     S.first_k = first_k;
     S.k = k;
@@ -447,6 +448,370 @@ static ks_status run_phase(Problem &P, const T *Xstart, T *Xend, const ks_opts &
   return KS_OK;
 }
 
+// ---------------------------------------------------------------- increment form
+// FP32 phase that carries its iterate as X = X_b + delta: an FP64 base X_b,
+// held as two FP32 blocks hi + lo, and an FP32 increment delta.  At the base
+// everything is evaluated in FP64 -- energy, density rho_b, potential V_b,
+// gradient E_b = E_X(X_b), the Gram S_b = E_b^T X_b and the projected
+// gradient D_b = M^{-1} E_b - X_b S_b (Eq. def-nablaE) -- and between
+// refreshes only increments are formed in FP32:
+//   rho = rho_b + f sum delta (2 X_b + delta)
+//   T   = T_b + sum delta . (f K X_b + (f/2) K delta)   (compensated sum)
+//   E_ext, E_H, E_xc from rho in FP64 (FP64 xc, Hartree CG to cg_tol)
+//   e   = E_X - E_b = f K delta + 2 f h^3 (Diag(V - V_b) X_b + Diag(V) delta)
+//   dS  = S - S_b = E_b^T delta + e^T X
+//   D   = D_b + M^{-1} e - delta S_b - X dS
+// so every FP32 rounding scales with |delta|, |e| or ||D||, never with |X|
+// or |E_X|: the energies the line search compares and the direction it takes
+// stay as accurate as FP64 ones far below the FP32 rounding of the orbitals.
+// The retraction forms delta+ = X_b (A - I) + delta A + D B (retract_split).
+// Every kRebaseEvery accepted iterations the base absorbs the increment in
+// FP64 (and is re-M-orthonormalised when it has drifted).
+//
+// Storage: the iterate blocks hold delta in their lower half and the FP32
+// copy X32 = fl32(X_b + delta) in their upper half; the E_X blocks hold e;
+// the upper halves of B_MX0, B_MX1, B_MX2 and B_G hold hi, lo, fl32(E_b) and
+// fl32(D_b); rho_b, V_b are n-vectors and S_b is a p x p matrix.
+#ifndef KS_REBASE_EVERY
+#define KS_REBASE_EVERY 32
+#endif
+namespace {
+constexpr int kRebaseEvery = KS_REBASE_EVERY;
+constexpr double kSplitOrthoTol = 1e-13;
+constexpr int kSplitStallWindow = 50000;
+}  // namespace
+
+static float *lower32(Problem &P, int b) { return reinterpret_cast<float *>(P.blk[b]); }
+static float *upper32(Problem &P, int b) {
+  return reinterpret_cast<float *>(reinterpret_cast<char *>(P.blk[b]) + P.half_off);
+}
+static float *base_hi(Problem &P) { return upper32(P, B_MX0); }
+static float *base_lo(Problem &P) { return upper32(P, B_MX1); }
+static float *base_eb(Problem &P) { return upper32(P, B_MX2); }
+static float *base_db(Problem &P) { return upper32(P, B_G); }
+
+// Energy at X_b + delta (delta in the lower half of block bx), the gradient
+// increment e and M delta.
+static ks_status evaluate_split(Problem &P, int bx, float *e, float *Md, double *E) {
+  const float *d = lower32(P, bx);
+  KS_TRY(launch_density_inc(P, d, base_hi(P), P.rho_b, P.rho));
+  KS_TRY(launch_cg(P, P.rho, P.vH, P.cg_r, P.vH_valid));
+  KS_TRY(launch_potential(P, P.rho, P.vH, P.cg_r, P.veff, true, false));
+  KS_TRY(launch_hamiltonian_inc(P, d, P.veff, P.veff_b, base_hi(P), base_eb(P), e, Md,
+                                P.scal + SC_EKIN));
+  ks_status st = sync_scalars(P);
+  if (st != KS_OK) {
+    P.vH_valid = false;
+    return st;
+  }
+  P.vH_valid = true;
+  const double *s = P.scal_host;
+  const double ekin = P.state.T_b + s[SC_EKIN];
+  P.last_parts[0] = ekin + s[SC_ETF];
+  P.last_parts[1] = s[SC_EEXT];
+  P.last_parts[2] = s[SC_EH];
+  P.last_parts[3] = s[SC_EXC];
+  P.last_parts[4] = s[SC_EII];
+  P.last_cg_iters = (int)s[SC_CG_ITERS];
+  P.last_E = ekin + s[SC_ETF] + s[SC_EEXT] + s[SC_EH] + s[SC_EXC] + s[SC_EII];
+  if (!std::isfinite(P.last_E)) return set_error(KS_ENAN, "non-finite energy");
+  *E = P.last_E;
+  return KS_OK;
+}
+
+// Projected gradient at the iterate of block bx (delta and X32) with
+// gradient increment e and M delta: D = D_b + M^{-1} e - delta S_b - X dS,
+// S = S_b + dS, the BB traces on the increments (X_b is common to both
+// iterates), and the Grams the retraction needs: R = D^T M D, T = X^T M D,
+// and for Cayley A = S^T, B = E_X^T G = E_X^T D + S S, O = I.
+static ks_status project_split(Problem &P, int retraction, int bx, const float *e,
+                               const float *Md, float *D, float *MD, const BBPrevT<float> *prev,
+                               Traces *tr) {
+  const int p = P.p;
+  float *Gi = lower32(P, B_G);
+  const float *X32 = upper32(P, bx), *d = lower32(P, bx);
+  KS_TRY(launch_mass_inverse<float>(P, e, Gi));
+  KS_TRY(launch_axpy_f32(P, Gi, 1.0f, base_db(P), Gi));                    // D_b + M^{-1} e
+  KS_TRY(launch_gram<float>(P, base_eb(P), p, d, p, sm(P, S_DS)));          // E_b^T delta
+  KS_TRY(launch_gram<float>(P, e, p, X32, p, sm(P, S_E1)));                 // e^T X
+  KS_TRY(launch_add_pp(P, sm(P, S_DS), 1.0, sm(P, S_E1), sm(P, S_DS)));     // dS
+  KS_TRY(launch_add_pp(P, sm(P, S_SB), 1.0, sm(P, S_DS), sm(P, S_S)));      // S
+  KS_TRY(launch_combine<float>(P, d, p, sm(P, S_SB), X32, p, sm(P, S_DS), -1.0, 1.0, Gi, D, p));
+  KS_TRY(launch_mass_dots<float>(P, D, MD, d, Md, prev, P.scal + SC_DNORM2));
+  KS_TRY(launch_gram<float>(P, D, p, MD, p, sm(P, S_DMD)));
+  KS_TRY(launch_gram<float>(P, X32, p, MD, p, sm(P, S_XMD)));
+  if (retraction != KS_QR) {
+    KS_TRY(launch_transpose(P, sm(P, S_S), sm(P, S_A)));
+    KS_TRY(launch_gram<float>(P, base_eb(P), p, D, p, sm(P, S_B)));         // E_b^T D
+    KS_TRY(launch_gram<float>(P, e, p, D, p, sm(P, S_E1)));                 // e^T D
+    KS_TRY(launch_add_pp(P, sm(P, S_B), 1.0, sm(P, S_E1), sm(P, S_B)));
+    KS_TRY(launch_small_gemm(P, 0, sm(P, S_S), 0, sm(P, S_S), 1.0, 1.0, sm(P, S_B)));  // + S S
+    // X^T M X = I up to the increment's rounding
+    KS_CUDA_TRY(cudaMemsetAsync(sm(P, S_O), 0, (size_t)p * p * sizeof(double), P.stream));
+    KS_TRY(launch_add_identity(P, sm(P, S_O), 1.0, sm(P, S_O)));
+  }
+  KS_TRY(sync_scalars(P));
+  tr->dnorm2 = P.scal_host[SC_DNORM2];
+  if (prev) {
+    tr->ss = P.scal_host[SC_BB_SS];
+    tr->sy = P.scal_host[SC_BB_SY];
+    tr->yy = P.scal_host[SC_BB_YY];
+  }
+  if (!std::isfinite(tr->dnorm2)) return set_error(KS_ENAN, "non-finite gradient norm");
+  return KS_OK;
+}
+
+// Trial increment in block bt from the iterate in block bx along -D (QR) or
+// along the Cayley curve, with its FP32 copy X32 = X_b + delta+.  Both steps
+// are written on the basis [X, D], X+ = X A + D B, and A, B are
+// right-multiplied by L^{-T} with L L^T = Y^T M Y formed exactly from
+// X^T M X = I, T = X^T M D and R = D^T M D (p x p Grams): the trial is
+// M-orthonormal to the rounding of those Grams even though D carries FP32
+// rounding normal to the manifold (Alg. ChQR with the explicit Y^T M Y;
+// Prop. 3.1's I + tau^2 R would leave the trial off the manifold by tau
+// times that component, an error whose energy, amplified by the Lagrange
+// multipliers, can exceed the decrease the line search asks for).
+//   QR:     A = I, B = -tau I; Y^T M Y = I - tau (T + T^T) + tau^2 R.
+//   Cayley: X+ = X C1 + G C2 (Eq. WY3) with G = D + X S gives A = C1 + S C2,
+//           B = C2; Y^T M Y = A^T A + A^T T B + B^T T^T A + B^T R B.
+// The increment is then delta+ = X_b (A - I) + delta A + D B.
+static ks_status retract_split(Problem &P, int retraction, int bx, const float *D, double tau,
+                               int bt) {
+  const int p = P.p;
+  const size_t pp = (size_t)p * p * sizeof(double);
+  const double *Ac, *Bc;
+  if (retraction == KS_QR) {
+    KS_TRY(launch_qr_exact_gram(P, sm(P, S_DMD), sm(P, S_XMD), tau, sm(P, S_E1)));
+    KS_TRY(launch_qr_factor(P, sm(P, S_E1), nullptr, tau, sm(P, S_C1), sm(P, S_C2)));
+    Ac = sm(P, S_C1);
+    Bc = sm(P, S_C2);
+  } else {
+    double *A = sm(P, S_C1), *B = sm(P, S_C2);
+    double *E1 = sm(P, S_E1), *E2 = sm(P, S_E2), *E3 = sm(P, S_E3);
+    KS_TRY(launch_cayley_factor(P, sm(P, S_A), sm(P, S_S), sm(P, S_B), sm(P, S_O), tau, E1, B));
+    KS_CUDA_TRY(cudaMemcpyAsync(A, E1, pp, cudaMemcpyDeviceToDevice, P.stream));
+    KS_TRY(launch_small_gemm(P, 0, sm(P, S_S), 0, B, 1.0, 1.0, A));        // A = C1 + S C2
+    KS_TRY(launch_small_gemm(P, 0, sm(P, S_XMD), 0, B, 1.0, 0.0, E2));     // T B
+    KS_TRY(launch_small_gemm(P, 1, A, 0, E2, 1.0, 0.0, E1));               // A^T T B
+    KS_TRY(launch_small_gemm(P, 0, sm(P, S_DMD), 0, B, 1.0, 0.0, E3));     // R B
+    KS_TRY(launch_small_gemm(P, 1, B, 0, E3, 1.0, 0.0, E2));               // B^T R B
+    KS_TRY(launch_small_gemm(P, 1, A, 0, A, 1.0, 1.0, E2));                // + A^T A
+    KS_TRY(launch_sym_add(P, E2, E1, E3));                                 // Y^T M Y
+    KS_TRY(launch_qr_factor(P, nullptr, E3, 0.0, E1, nullptr));            // L^{-T}
+    KS_TRY(launch_small_gemm(P, 0, A, 0, E1, 1.0, 0.0, E3));               // A L^{-T}
+    KS_TRY(launch_small_gemm(P, 0, B, 0, E1, 1.0, 0.0, E2));               // B L^{-T}
+    Ac = E3;
+    Bc = E2;
+  }
+  float *dt = lower32(P, bt), *xt = upper32(P, bt);
+  KS_TRY(launch_add_identity(P, Ac, -1.0, sm(P, S_T)));
+  // X_b (A - I) + D B into the trial's upper half, then delta A added
+  KS_TRY(launch_combine<float>(P, base_hi(P), p, sm(P, S_T), D, p, Bc, 1.0, 0.0, nullptr, xt, p));
+  KS_TRY(launch_combine<float>(P, lower32(P, bx), p, Ac, nullptr, 0, nullptr, 1.0, 1.0, xt, dt,
+                               p));
+  return launch_axpy_f32(P, base_hi(P), 1.0f, dt, xt);
+}
+
+// The base absorbs the increment of block bx (gradient increment in block
+// bex, M delta in bmx): X_b <- X_b + delta, formed in FP64 in block b64 and
+// evaluated there in FP64 (energy *E, rho_b, V_b, E_b, T_b; the Hartree
+// solve warm-started), re-M-orthonormalised when ||X_b^T M X_b - I||_F >
+// kSplitOrthoTol (X_b <- X_b L^{-T}, applied as the small correction
+// X_b (L^{-T} - I) formed in FP32, then evaluated again), then S_b and D_b
+// are formed in FP64 (scratch: blocks bex and B_G), delta, M delta and e
+// become 0, and the previous increment (block bxp, M delta in bmxp; -1: none)
+// is re-expressed against the new base.  scratch: a free FP32 n x p block.
+static ks_status rebase_split(Problem &P, int bx, int bmx, int bex, int bxp, int bmxp, int b64,
+                              float *scratch, double *E) {
+  const int p = P.p;
+  double *xb = P.blk[b64];
+  double *w1 = P.blk[bex];     // E_b, then D_b
+  double *w2 = P.blk[B_G];     // M X_b, then M^{-1} E_b
+  KS_TRY(launch_split_join(P, base_hi(P), base_lo(P), lower32(P, bx), xb));
+  for (int pass = 0; pass < 2; ++pass) {
+    KS_TRY(evaluate<double>(P, xb, w1, w2, E));
+    KS_TRY(launch_gram<double>(P, xb, p, w2, p, sm(P, S_O)));
+    KS_TRY(launch_ortho_err(P, sm(P, S_O), P.scal + SC_ORTHO));
+    KS_TRY(sync_scalars(P));
+    if (pass == 1 || std::sqrt(P.scal_host[SC_ORTHO]) <= kSplitOrthoTol) break;
+    KS_TRY(launch_qr_factor(P, nullptr, sm(P, S_O), 0.0, sm(P, S_C1), nullptr));
+    KS_TRY(launch_add_identity(P, sm(P, S_C1), -1.0, sm(P, S_T)));
+    KS_TRY(launch_combine<float>(P, upper32(P, bx), p, sm(P, S_T), nullptr, 0, nullptr, 1.0, 0.0,
+                                 nullptr, scratch, p));
+    KS_TRY(launch_add_f64_f32(P, xb, scratch));
+  }
+  P.state.T_b = P.scal_host[SC_EKIN];
+  KS_CUDA_TRY(cudaMemcpyAsync(P.rho_b, P.rho, (size_t)P.n * sizeof(double),
+                              cudaMemcpyDeviceToDevice, P.stream));
+  KS_CUDA_TRY(cudaMemcpyAsync(P.veff_b, P.veff, (size_t)P.n * sizeof(double),
+                              cudaMemcpyDeviceToDevice, P.stream));
+  // S_b = E_b^T X_b and D_b = M^{-1} E_b - X_b S_b in FP64
+  KS_TRY(launch_mass_inverse<double>(P, w1, w2));
+  KS_TRY(launch_gram<double>(P, w1, p, xb, p, sm(P, S_SB)));
+  KS_TRY(launch_convert(P, w1, base_eb(P)));
+  KS_TRY(launch_combine<double>(P, xb, p, sm(P, S_SB), nullptr, 0, nullptr, -1.0, 1.0, w2, w1, p));
+  KS_TRY(launch_convert(P, w1, base_db(P)));
+  KS_TRY(launch_split_hilo(P, xb, base_hi(P), base_lo(P)));
+  if (bxp >= 0) {
+    KS_TRY(launch_axpy_f32(P, lower32(P, bxp), -1.0f, lower32(P, bx), lower32(P, bxp)));
+    KS_TRY(launch_axpy_f32(P, lower32(P, bmxp), -1.0f, lower32(P, bmx), lower32(P, bmxp)));
+  }
+  const size_t b32 = (size_t)P.n * p * sizeof(float);
+  KS_CUDA_TRY(cudaMemsetAsync(lower32(P, bx), 0, b32, P.stream));
+  KS_CUDA_TRY(cudaMemsetAsync(lower32(P, bmx), 0, b32, P.stream));
+  KS_CUDA_TRY(cudaMemsetAsync(lower32(P, bex), 0, b32, P.stream));
+  KS_CUDA_TRY(cudaMemcpyAsync(upper32(P, bx), base_hi(P), b32, cudaMemcpyDeviceToDevice,
+                              P.stream));
+  P.state.since_rebase = 0;
+  return KS_OK;
+}
+
+// Alg. ConOptM in the increment form from the FP64 block Xstart (copied,
+// then M-orthonormalised in FP64) -- or, with `resume`, from the saved
+// state -- until ||D||_M <= gtol, maxit iterations in total, or (stall > 0)
+// no 0.1 % improvement of the best ||D||_M for kStallWindow iterations (the
+// limit of the FP32 direction).  The final X = X_b + delta is written to
+// Xend in FP64.  The line search treats the energies like FP64 ones
+// (rounding slack and restart of the reference after a forced acceptance).
+static ks_status run_phase_split(Problem &P, const double *Xstart, double *Xend,
+                                 const ks_opts &o, double gtol, int maxit, int stall,
+                                 bool resume, PhaseResult *out) {
+  const int p = P.p;
+  Problem::RunState &S = P.state;
+  int ix[3] = {B_X0, B_X1, B_X2};
+  int imx[3] = {B_MX0, B_MX1, B_MX2};
+  int iex[2] = {B_EX0, B_EX1};
+  int id[2] = {B_D0, B_D1};
+  int imd[2] = {B_MD0, B_MD1};
+  auto MD_ = [&](int s) { return lower32(P, imx[s]); };
+  auto EX = [&](int s) { return lower32(P, iex[s]); };   // gradient increments e
+  auto D = [&](int s) { return lower32(P, id[s]); };
+  auto MDd = [&](int s) { return lower32(P, imd[s]); };
+  double E = 0, C = 0, Q = 1.0, best = 0;
+  int k = 0, last_improve = 0, cg_total = 0;
+  bool have_prev = false;
+  Traces tr;
+  P.cg_tol_phase = 0.0;
+  if (resume) {
+    for (int i = 0; i < 3; ++i) { ix[i] = S.ix[i]; imx[i] = S.imx[i]; }
+    for (int i = 0; i < 2; ++i) { iex[i] = S.iex[i]; id[i] = S.id[i]; imd[i] = S.imd[i]; }
+    k = S.k;
+    E = S.E; C = S.C; Q = S.Q; best = S.best; last_improve = S.last_improve;
+    out->last_tau = S.last_tau;
+    have_prev = S.have_prev != 0;
+    P.vH_valid = true;
+    BBPrevT<float> prev{lower32(P, ix[1]), MD_(1), D(1), MDd(1)};
+    KS_TRY(project_split(P, S.retraction, ix[0], EX(0), MD_(0), D(0), MDd(0),
+                         have_prev ? &prev : nullptr, &tr));
+  } else {
+    // FP64 start: X_b = CholQR2(Xstart) in block ix[2], delta = 0
+    double *x64 = P.blk[ix[2]];
+    KS_CUDA_TRY(cudaMemcpyAsync(x64, Xstart, (size_t)P.n * p * sizeof(double),
+                                cudaMemcpyDeviceToDevice, P.stream));
+    KS_TRY(orthonormalize<double>(P, x64, P.blk[iex[1]], P.blk[B_G], 2));
+    KS_TRY(launch_split_hilo(P, x64, base_hi(P), base_lo(P)));
+    KS_CUDA_TRY(cudaMemsetAsync(lower32(P, ix[0]), 0, (size_t)P.n * p * sizeof(float),
+                                P.stream));
+    KS_CUDA_TRY(cudaMemcpyAsync(upper32(P, ix[0]), base_hi(P), (size_t)P.n * p * sizeof(float),
+                                cudaMemcpyDeviceToDevice, P.stream));
+    KS_TRY(rebase_split(P, ix[0], imx[0], iex[0], -1, -1, ix[2], MD_(2), &E));
+    cg_total = P.last_cg_iters;
+    KS_TRY(project_split(P, o.retraction, ix[0], EX(0), MD_(0), D(0), MDd(0), nullptr, &tr));
+    C = E;
+    best = std::sqrt(std::fmax(tr.dnorm2, 0.0));
+    S.since_rebase = 0;
+  }
+  const int k0 = k;
+  int backtracks = 0;
+  bool stalled = false;
+  auto save_state = [&]() {
+    S.valid = true;
+    S.elem = 4;
+    S.split = 1;
+    S.retraction = o.retraction;
+    S.first_k = 0;
+    S.k = k;
+    S.have_prev = have_prev ? 1 : 0;
+    S.C = C; S.Q = Q; S.E = E; S.best = best; S.last_improve = last_improve;
+    S.last_tau = out->last_tau;
+    S.dnorm2 = tr.dnorm2; S.ss = tr.ss; S.sy = tr.sy; S.yy = tr.yy;
+    for (int i = 0; i < 3; ++i) { S.ix[i] = ix[i]; S.imx[i] = imx[i]; }
+    for (int i = 0; i < 2; ++i) { S.iex[i] = iex[i]; S.id[i] = id[i]; S.imd[i] = imd[i]; }
+  };
+  save_state();
+  while (std::sqrt(std::fmax(tr.dnorm2, 0.0)) > gtol && k < maxit) {
+    double tau = have_prev ? bb_step(k, tr, o) : o.tau0;
+    int h = 0;
+    double Et = 0;
+    bool forced = false;
+    for (;;) {
+      KS_TRY(retract_split(P, o.retraction, ix[0], D(0), tau, ix[2]));
+      KS_TRY(evaluate_split(P, ix[2], EX(1), MD_(2), &Et));
+      cg_total += P.last_cg_iters;
+      const bool ok = Et <= C - o.rho1 * tau * tr.dnorm2 + armijo_slack<double>(P.last_parts);
+      if (ok || h == o.max_backtrack) {
+        forced = !ok;
+        break;
+      }
+      tau *= o.delta;
+      ++h;
+    }
+    backtracks += h;
+    out->last_tau = tau;
+    const double Qn = o.eta * Q + 1.0;
+    C = (o.eta * Q * C + Et) / Qn;
+    Q = Qn;
+    if (forced) {
+      C = Et;
+      Q = 1.0;
+    }
+    std::swap(ix[1], ix[0]);
+    std::swap(ix[0], ix[2]);
+    std::swap(imx[1], imx[0]);
+    std::swap(imx[0], imx[2]);
+    std::swap(iex[0], iex[1]);
+    std::swap(id[0], id[1]);
+    std::swap(imd[0], imd[1]);
+    E = Et;
+    ++k;
+    if (++S.since_rebase >= kRebaseEvery) {
+      // the base absorbs the increment (an FP64 evaluation at the same point)
+      KS_TRY(rebase_split(P, ix[0], imx[0], iex[0], ix[1], imx[1], ix[2], MD_(2), &E));
+      cg_total += P.last_cg_iters;
+    }
+    BBPrevT<float> prev{lower32(P, ix[1]), MD_(1), D(1), MDd(1)};
+    KS_TRY(project_split(P, o.retraction, ix[0], EX(0), MD_(0), D(0), MDd(0), &prev, &tr));
+    have_prev = true;
+    const double dn = std::sqrt(std::fmax(tr.dnorm2, 0.0));
+    if (dn < 0.999 * best) {
+      best = dn;
+      last_improve = k;
+    }
+    // the direction is accurate to FP32 rounding relative to ||D||, so the
+    // phase has no floor above gtol to detect: only a run whose best ||D||
+    // stays put for kSplitStallWindow iterations (far longer than the
+    // plateaus of the BB iteration on slowly converging systems) hands over
+    bool stop = false;
+    if (stall > 0 && k - last_improve >= kSplitStallWindow) {
+      stalled = true;
+      stop = true;
+    }
+    save_state();
+    if (o.verbose > 0 && k % o.verbose == 0)
+      fprintf(stderr, "ks_minimize[fp32+base]: k=%d E=%.12f |D|=%.3e tau=%.3e h=%d cg=%d\n", k, E,
+              dn, tau, h, P.last_cg_iters);
+    if (stop) break;
+  }
+  KS_TRY(launch_split_join(P, base_hi(P), base_lo(P), lower32(P, ix[0]), Xend));
+  out->E = E;
+  out->dnorm = std::sqrt(std::fmax(tr.dnorm2, 0.0));
+  out->iters = k - k0;
+  out->cg = cg_total;
+  out->backtracks = backtracks;
+  out->stalled = stalled;
+  return KS_OK;
+}
+
 static ks_status minimize_device(Problem &P, double *X_inout, const ks_opts &o, ks_result *res,
                                  bool resume) {
   const auto t0 = std::chrono::steady_clock::now();
@@ -457,31 +822,46 @@ static ks_status minimize_device(Problem &P, double *X_inout, const ks_opts &o, 
   int done = resume ? P.state.first_k + P.state.k : 0;   // iterations before this call
   double polish_tau = 0.0;
   if (o.precision == KS_MIXED && (!resume || resume_fp32)) {
-    // FP32 phase (Hartree, energy sums and p x p algebra stay FP64), then
-    // an FP64 polish from its last iterate.
-    float *xs = blk<float>(P, B_G);
-    if (!resume) KS_TRY(launch_convert(P, X_inout, xs));
     PhaseResult mr;
-    P.cg_tol_phase = o.mixed_cg_tol > P.cg_tol ? std::fmin(o.mixed_cg_tol, 1e-3) : 0.0;
-    const ks_status pst = run_phase<float>(P, xs, xs, o, std::fmax(o.polish_gtol, o.gtol), o.maxit,
-                                           o.stall_iters, 0, std::fmax(o.ortho_tol, 1e-5),
-                                           resume_fp32, &mr);
-    P.cg_tol_phase = 0.0;
-    KS_TRY(pst);
+    const bool inc = resume ? P.state.split != 0 : o.fp32_increment != 0;
+    bool limit_hit = false;
+    if (inc) {
+      // FP32 phase in increment form (X = X_b + delta), to gtol or until the
+      // FP32 direction stops improving; the result is written to X_inout in
+      // FP64
+      const ks_status pst = run_phase_split(P, X_inout, X_inout, o, o.gtol, o.maxit,
+                                            o.stall_iters, resume_fp32, &mr);
+      KS_TRY(pst);
+      P.mixed_iters = P.state.k;
+      limit_hit = P.mixed_iters >= o.maxit && !mr.stalled && mr.dnorm > o.gtol;
+    } else {
+      // FP32 phase (Hartree, energy sums and p x p algebra stay FP64), then
+      // an FP64 polish from its last iterate.
+      float *xs = blk<float>(P, B_G);
+      if (!resume) KS_TRY(launch_convert(P, X_inout, xs));
+      P.cg_tol_phase = o.mixed_cg_tol > P.cg_tol ? std::fmin(o.mixed_cg_tol, 1e-3) : 0.0;
+      const ks_status pst = run_phase<float>(P, xs, xs, o, std::fmax(o.polish_gtol, o.gtol),
+                                             o.maxit, o.stall_iters, 0,
+                                             std::fmax(o.ortho_tol, 1e-5), resume_fp32, &mr);
+      P.cg_tol_phase = 0.0;
+      KS_TRY(pst);
+      P.mixed_iters = P.state.first_k + P.state.k;
+      double *xd = blk<double>(P, B_MD1);
+      KS_TRY(launch_convert(P, xs, xd));
+      KS_CUDA_TRY(cudaMemcpyAsync(X_inout, xd, (size_t)P.n * P.p * sizeof(double),
+                                  cudaMemcpyDeviceToDevice, P.stream));
+      limit_hit = P.mixed_iters >= o.maxit && !mr.stalled &&
+                  mr.dnorm > std::fmax(o.polish_gtol, o.gtol);
+    }
     iters += mr.iters;
     cg += mr.cg;
     backtracks += mr.backtracks;
     polish_tau = mr.last_tau;
-    P.mixed_iters = P.state.first_k + P.state.k;
     P.mixed_dnorm = mr.dnorm;
     P.mixed_E = mr.E;
-    double *xd = blk<double>(P, B_MD1);
-    KS_TRY(launch_convert(P, xs, xd));
-    KS_CUDA_TRY(cudaMemcpyAsync(X_inout, xd, (size_t)P.n * P.p * sizeof(double),
-                                cudaMemcpyDeviceToDevice, P.stream));
     done = P.mixed_iters;
     resume_fp64 = false;
-    if (done >= o.maxit && !mr.stalled && mr.dnorm > std::fmax(o.polish_gtol, o.gtol)) {
+    if (limit_hit) {
       // iteration limit inside the FP32 phase: no polish; the FP32 state
       // stays resumable and X_inout holds the FP32 iterate in FP64
       if (res) {
@@ -534,15 +914,26 @@ static ks_status minimize_device(Problem &P, double *X_inout, const ks_opts &o, 
 }
 
 // Checkpoint layout: header, then the current X, MX, E_X, D, MD and the
-// previous X, MX, D, MD blocks (elem bytes per entry), then vH (FP64).
+// previous X, MX, D, MD blocks (elem bytes per entry), then vH (FP64).  A
+// state of the FP32 phase in increment form (split = 1) instead holds all
+// n x p blocks at full capacity in their own slots (the base quantities share
+// them with the increments), then vH, rho_b, V_b and S_b.
 struct StateHeader {
   uint64_t magic;
   int32_t version, N, p, elem, retraction, first_k, k, have_prev, last_improve;
   double C, Q, E, dnorm2, ss, sy, yy, best, last_tau;
+  int32_t split, since_rebase;
+  double T_b;
+  int32_t slots[13];
 };
 constexpr uint64_t kStateMagic = 0x4b53535441544531ull;   // "KSSTATE1"
 
-static size_t state_bytes(const Problem &P, int elem) {
+static size_t block_capacity(const Problem &P) { return ((size_t)P.n * P.p + 32) * sizeof(double); }
+
+static size_t state_bytes(const Problem &P, int elem, int split) {
+  if (split)
+    return sizeof(StateHeader) + (size_t)Problem::kNBlocks * block_capacity(P) +
+           (size_t)3 * P.n * sizeof(double) + (size_t)P.p * P.p * sizeof(double);
   return sizeof(StateHeader) + (size_t)9 * P.n * P.p * elem + (size_t)P.n * sizeof(double);
 }
 
@@ -574,6 +965,7 @@ void ks_opts_default(ks_opts *o) {
   o->resume = 0;
   o->mixed_cg_tol = 1e-7;
   o->fp64_split = 0;
+  o->fp32_increment = 1;
 }
 
 const char *ks_last_error_string(void) { return g_err; }
@@ -640,10 +1032,14 @@ ks_status ks_problem_create(const ks_problem_desc *d, ks_problem **out) {
 #define ALLOC(ptr, cnt) \
   if ((st = dalloc(&(ptr), (cnt), P)) != KS_OK) return fail(st);
   ALLOC(P.vext, n); ALLOC(P.rho, n); ALLOC(P.vH, n); ALLOC(P.veff, n);
+  ALLOC(P.rho_b, n); ALLOC(P.veff_b, n); ALLOC(P.zero_n, n);
   ALLOC(P.cg_r, n); ALLOC(P.cg_pa, n); ALLOC(P.cg_pb, n); ALLOC(P.cg_q, n); ALLOC(P.cg_z, n);
   ALLOC(P.cg_t1, n); ALLOC(P.cg_t2, n);
   ALLOC(P.dst_phi, (size_t)P.N * P.N); ALLOC(P.dst_kap, (size_t)P.N); ALLOC(P.dst_mu, (size_t)P.N);
-  for (auto &b : P.blk) { ALLOC(b, np); }
+  // FP64 capacity plus 256 bytes, so that an FP32 block fits in the upper
+  // half at a 256-byte aligned offset
+  P.half_off = (np * sizeof(float) + 255) / 256 * 256;
+  for (auto &b : P.blk) { ALLOC(b, np + 32); }
   P.pp_len = (size_t)S_COUNT * P.p * P.p;
   ALLOC(P.pp, P.pp_len);
   ALLOC(P.cf, (size_t)2 * P.p * P.p);
@@ -680,6 +1076,8 @@ ks_status ks_problem_create(const ks_problem_desc *d, ks_problem **out) {
   e = cudaMemsetAsync(P.dstatus, 0, sizeof(int), P.stream);
   if (e != cudaSuccess) return fail(cuda_error(e, "memset"));
   e = cudaMemsetAsync(P.vH, 0, n * sizeof(double), P.stream);
+  if (e != cudaSuccess) return fail(cuda_error(e, "memset"));
+  e = cudaMemsetAsync(P.zero_n, 0, n * sizeof(double), P.stream);
   if (e != cudaSuccess) return fail(cuda_error(e, "memset"));
   if ((st = configure_small_kernels()) != KS_OK) return fail(st);
   if ((st = configure_tc_kernels()) != KS_OK) return fail(st);
@@ -803,7 +1201,7 @@ ks_status ks_minimize_host(ks_problem *kp, double *Xh, const ks_opts *opts, ks_r
 
 size_t ks_state_bytes(ks_problem *kp) {
   if (!kp || !kp->P.state.valid) return 0;
-  return state_bytes(kp->P, kp->P.state.elem);
+  return state_bytes(kp->P, kp->P.state.elem, kp->P.state.split);
 }
 
 ks_status ks_state_save(ks_problem *kp, void *host_buf, size_t bytes) {
@@ -811,10 +1209,15 @@ ks_status ks_state_save(ks_problem *kp, void *host_buf, size_t bytes) {
   Problem &P = kp->P;
   const Problem::RunState &S = P.state;
   if (!S.valid) return set_error(KS_EINVAL, "no minimisation state to save");
-  if (bytes < state_bytes(P, S.elem)) return set_error(KS_EINVAL, "buffer too small");
+  if (bytes < state_bytes(P, S.elem, S.split)) return set_error(KS_EINVAL, "buffer too small");
   StateHeader hd{};
   hd.magic = kStateMagic;
-  hd.version = 2;
+  hd.version = 3;
+  hd.split = S.split; hd.since_rebase = S.since_rebase; hd.T_b = S.T_b;
+  for (int i = 0; i < 3; ++i) { hd.slots[i] = S.ix[i]; hd.slots[3 + i] = S.imx[i]; }
+  for (int i = 0; i < 2; ++i) {
+    hd.slots[6 + i] = S.iex[i]; hd.slots[8 + i] = S.id[i]; hd.slots[10 + i] = S.imd[i];
+  }
   hd.N = P.N; hd.p = P.p; hd.elem = S.elem; hd.retraction = S.retraction;
   hd.first_k = S.first_k; hd.k = S.k; hd.have_prev = S.have_prev; hd.last_improve = S.last_improve;
   hd.C = S.C; hd.Q = S.Q; hd.E = S.E; hd.dnorm2 = S.dnorm2;
@@ -822,6 +1225,26 @@ ks_status ks_state_save(ks_problem *kp, void *host_buf, size_t bytes) {
   char *dst = (char *)host_buf;
   std::memcpy(dst, &hd, sizeof(hd));
   dst += sizeof(hd);
+  if (S.split) {
+    for (int b = 0; b < Problem::kNBlocks; ++b) {
+      KS_CUDA_TRY(cudaMemcpyAsync(dst, P.blk[b], block_capacity(P), cudaMemcpyDeviceToHost,
+                                  P.stream));
+      dst += block_capacity(P);
+    }
+    KS_CUDA_TRY(cudaMemcpyAsync(dst, P.vH, (size_t)P.n * sizeof(double), cudaMemcpyDeviceToHost,
+                                P.stream));
+    dst += (size_t)P.n * sizeof(double);
+    KS_CUDA_TRY(cudaMemcpyAsync(dst, P.rho_b, (size_t)P.n * sizeof(double),
+                                cudaMemcpyDeviceToHost, P.stream));
+    dst += (size_t)P.n * sizeof(double);
+    KS_CUDA_TRY(cudaMemcpyAsync(dst, P.veff_b, (size_t)P.n * sizeof(double),
+                                cudaMemcpyDeviceToHost, P.stream));
+    dst += (size_t)P.n * sizeof(double);
+    KS_CUDA_TRY(cudaMemcpyAsync(dst, sm(P, S_SB), (size_t)P.p * P.p * sizeof(double),
+                                cudaMemcpyDeviceToHost, P.stream));
+    KS_CUDA_TRY(cudaStreamSynchronize(P.stream));
+    return KS_OK;
+  }
   const int order[9] = {S.ix[0], S.imx[0], S.iex[0], S.id[0], S.imd[0],
                         S.ix[1], S.imx[1], S.id[1], S.imd[1]};
   const size_t blkb = (size_t)P.n * P.p * S.elem;
@@ -841,10 +1264,25 @@ ks_status ks_state_load(ks_problem *kp, const void *host_buf, size_t bytes) {
   StateHeader hd;
   if (bytes < sizeof(hd)) return set_error(KS_EINVAL, "buffer too small");
   std::memcpy(&hd, host_buf, sizeof(hd));
-  if (hd.magic != kStateMagic || hd.version != 2) return set_error(KS_EINVAL, "not a saved state");
-  if (hd.N != P.N || hd.p != P.p || (hd.elem != 4 && hd.elem != 8))
+  if (hd.magic != kStateMagic || hd.version != 3) return set_error(KS_EINVAL, "not a saved state");
+  if (hd.N != P.N || hd.p != P.p || (hd.elem != 4 && hd.elem != 8) ||
+      (hd.split != 0 && (hd.split != 1 || hd.elem != 4)))
     return set_error(KS_EINVAL, "saved state does not match this problem");
-  if (bytes < state_bytes(P, hd.elem)) return set_error(KS_EINVAL, "buffer too small");
+  if (bytes < state_bytes(P, hd.elem, hd.split)) return set_error(KS_EINVAL, "buffer too small");
+  if (hd.split) {
+    // the slots must be a permutation of the blocks with X, MX, E_X, D, MD
+    // in their own families
+    int seen = 0;
+    const int lo[5] = {B_X0, B_MX0, B_EX0, B_D0, B_MD0}, cnt[5] = {3, 3, 2, 2, 2};
+    int at = 0;
+    for (int f = 0; f < 5; ++f)
+      for (int i = 0; i < cnt[f]; ++i, ++at) {
+        const int b = hd.slots[at];
+        if (b < lo[f] || b >= lo[f] + cnt[f] || (seen & (1 << b)))
+          return set_error(KS_EINVAL, "saved state has invalid block slots");
+        seen |= 1 << b;
+      }
+  }
   Problem::RunState S;
   S.valid = true;
   S.elem = hd.elem; S.retraction = hd.retraction; S.first_k = hd.first_k; S.k = hd.k;
@@ -853,8 +1291,37 @@ ks_status ks_state_load(ks_problem *kp, const void *host_buf, size_t bytes) {
   S.ss = hd.ss; S.sy = hd.sy; S.yy = hd.yy; S.best = hd.best; S.last_tau = hd.last_tau;
   if (hd.retraction != KS_QR && hd.retraction != KS_CAYLEY)
     return set_error(KS_EINVAL, "saved state has an unknown retraction");
+  S.split = hd.split;
+  S.since_rebase = hd.since_rebase;
+  S.T_b = hd.T_b;
   // the blocks are overwritten below: a copy that fails leaves no state
   P.state.valid = false;
+  if (hd.split) {
+    for (int i = 0; i < 3; ++i) { S.ix[i] = hd.slots[i]; S.imx[i] = hd.slots[3 + i]; }
+    for (int i = 0; i < 2; ++i) {
+      S.iex[i] = hd.slots[6 + i]; S.id[i] = hd.slots[8 + i]; S.imd[i] = hd.slots[10 + i];
+    }
+    const char *src = (const char *)host_buf + sizeof(hd);
+    for (int b = 0; b < Problem::kNBlocks; ++b) {
+      KS_CUDA_TRY(cudaMemcpyAsync(P.blk[b], src, block_capacity(P), cudaMemcpyHostToDevice,
+                                  P.stream));
+      src += block_capacity(P);
+    }
+    KS_CUDA_TRY(cudaMemcpyAsync(P.vH, src, (size_t)P.n * sizeof(double), cudaMemcpyHostToDevice,
+                                P.stream));
+    src += (size_t)P.n * sizeof(double);
+    KS_CUDA_TRY(cudaMemcpyAsync(P.rho_b, src, (size_t)P.n * sizeof(double),
+                                cudaMemcpyHostToDevice, P.stream));
+    src += (size_t)P.n * sizeof(double);
+    KS_CUDA_TRY(cudaMemcpyAsync(P.veff_b, src, (size_t)P.n * sizeof(double),
+                                cudaMemcpyHostToDevice, P.stream));
+    src += (size_t)P.n * sizeof(double);
+    KS_CUDA_TRY(cudaMemcpyAsync(sm(P, S_SB), src, (size_t)P.p * P.p * sizeof(double),
+                                cudaMemcpyHostToDevice, P.stream));
+    KS_CUDA_TRY(cudaStreamSynchronize(P.stream));
+    P.state = S;
+    return KS_OK;
+  }
   // canonical slots: current in slot 0, previous in slot 1
   const int order[9] = {B_X0, B_MX0, B_EX0, B_D0, B_MD0, B_X1, B_MX1, B_D1, B_MD1};
   const char *src = (const char *)host_buf + sizeof(hd);

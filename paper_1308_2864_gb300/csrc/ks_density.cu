@@ -76,6 +76,81 @@ ks_status launch_density(Problem &P, const T *X, double *rho) {
   return KS_OK;
 }
 
+// Increment form of the FP32 phase (X = X_b + delta, base hi part xb):
+// rho = rho_b + f sum_i delta_i (2 xb_i + delta_i), with rho_b = f sum X_b^2
+// in FP64.  The FP32 row sum carries rounding relative to the increment, not
+// to rho, so the density of the iterate stays accurate to the FP64 level of
+// rho_b plus eps_32 |delta| |X|.
+__global__ void density_inc_warp_kernel(int n, int p, double occ, const float *__restrict__ d,
+                                        const float *__restrict__ xb,
+                                        const double *__restrict__ rho_b,
+                                        double *__restrict__ rho) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long k0 = warp * 32; k0 < n; k0 += nwarps * 32) {
+    float mine = 0;
+    const int cnt = (int)min(32LL, (long long)n - k0);
+    for (int j0 = 0; j0 < cnt; j0 += kDenRows) {
+      float acc[kDenRows];
+#pragma unroll
+      for (int u = 0; u < kDenRows; ++u) acc[u] = 0;
+      for (int i = lane; i < p; i += 32) {
+        float vd[kDenRows], vx[kDenRows];
+#pragma unroll
+        for (int u = 0; u < kDenRows; ++u) {
+          const bool ok = j0 + u < cnt;
+          const long long idx = (k0 + j0 + u) * p + i;
+          vd[u] = ok ? d[idx] : 0.f;
+          vx[u] = ok ? xb[idx] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < kDenRows; ++u) acc[u] = fmaf(vd[u], fmaf(2.f, vx[u], vd[u]), acc[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < kDenRows; ++u) {
+        float a = acc[u];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == j0 + u) mine = a;
+      }
+    }
+    if (lane < cnt) rho[k0 + lane] = rho_b[k0 + lane] + occ * (double)mine;
+  }
+}
+
+__global__ void density_inc_thread_kernel(int n, int p, double occ, const float *__restrict__ d,
+                                          const float *__restrict__ xb,
+                                          const double *__restrict__ rho_b,
+                                          double *__restrict__ rho) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const float *rd = d + k * p;
+  const float *rx = xb + k * p;
+  float acc = 0;
+  for (int i = 0; i < p; ++i) acc = fmaf(rd[i], fmaf(2.f, rx[i], rd[i]), acc);
+  rho[k] = rho_b[k] + occ * (double)acc;
+}
+
+ks_status launch_density_inc(Problem &P, const float *d, const float *xb, const double *rho_b,
+                             double *rho) {
+  const double bytes = 8.0 * P.n * P.p + 16.0 * P.n;
+  if (P.p >= 32) {
+    const long long warps = (P.n + 31) / 32;
+    long long blocks = (warps * 32 + kThreads - 1) / kThreads;
+    if (blocks > 64LL * P.sms) blocks = 64LL * P.sms;
+    ProfScope ps_(P.stream, KP_DENSITY, 3.0 * P.n * P.p, bytes);
+    density_inc_warp_kernel<<<(int)blocks, kThreads, 0, P.stream>>>(P.n, P.p, P.occ, d, xb,
+                                                                     rho_b, rho);
+  } else {
+    ProfScope ps_(P.stream, KP_DENSITY, 3.0 * P.n * P.p, bytes);
+    density_inc_thread_kernel<<<(P.n + kThreads - 1) / kThreads, kThreads, 0, P.stream>>>(
+        P.n, P.p, P.occ, d, xb, rho_b, rho);
+  }
+  KS_CUDA_TRY(cudaGetLastError());
+  return KS_OK;
+}
+
 // Batched: one thread per node of every active job.
 template <typename T>
 __global__ void density_batch_kernel(const BJob *__restrict__ jobs, const int *__restrict__ start,

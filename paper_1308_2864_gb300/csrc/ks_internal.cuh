@@ -94,6 +94,9 @@ struct Problem {
 
   // n-vectors
   double *vext = nullptr, *rho = nullptr, *vH = nullptr, *veff = nullptr;
+  double *rho_b = nullptr;         // density of the base X_b (FP32 phase, increment form)
+  double *veff_b = nullptr;        // V_eff at the base X_b
+  double *zero_n = nullptr;        // n zeros (V_eff = 0: the kinetic part f K X alone)
   double *cg_r = nullptr, *cg_pa = nullptr, *cg_pb = nullptr, *cg_q = nullptr;
   double *cg_z = nullptr;          // preconditioned residual
   float *cg_t1 = nullptr, *cg_t2 = nullptr;  // sine-transform work (FP32)
@@ -109,9 +112,11 @@ struct Problem {
   int use_tma = 1;                 // TMA plane staging in the stencils (when the layout allows)
   bool vH_valid = false;           // warm start available
 
-  // n x p blocks
+  // n x p blocks (FP64 capacity plus 256 bytes; the FP32 phase keeps a second
+  // FP32 block in the upper half, at byte offset half_off, 256-byte aligned)
   static constexpr int kNBlocks = 13;
   double *blk[kNBlocks] = {};
+  size_t half_off = 0;
 
   // p x p work (all FP64)
   double *pp = nullptr;            // pool of small matrices
@@ -144,6 +149,11 @@ struct Problem {
     double last_tau = 0;           // last accepted step (carried into the FP64 polish)
     int last_improve = 0;
     int ix[3] = {0, 1, 2}, imx[3] = {3, 4, 5}, iex[2] = {6, 7}, id[2] = {9, 10}, imd[2] = {11, 12};
+    // FP32 phase in increment form: X = X_b + delta, with the base's kinetic
+    // energy T_b (the base blocks live in the upper halves of B_MX0..2)
+    int split = 0;
+    int since_rebase = 0;          // accepted iterations since the base was refreshed
+    double T_b = 0;
   } state;
 
   // last mixed-precision phase
@@ -193,6 +203,32 @@ ks_status launch_setup(Problem &P);
 // ks_density.cu: rho_k = f sum_i X_ki^2 (X FP64 or FP32, rho FP64)
 template <typename T>
 ks_status launch_density(Problem &P, const T *X, double *rho);
+// Increment form: rho = rho_b + f sum_i d_i (2 xb_i + d_i) (d, xb FP32 n x p)
+ks_status launch_density_inc(Problem &P, const float *d, const float *xb, const double *rho_b,
+                             double *rho);
+// ks_split.cu: elementwise kernels of the increment form (n x p blocks)
+// out = (hi + lo) + d in FP64
+ks_status launch_split_join(Problem &P, const float *hi, const float *lo, const float *d,
+                            double *out);
+// hi = fl32(x), lo = fl32(x - hi)
+ks_status launch_split_hilo(Problem &P, const double *x, float *hi, float *lo);
+// out = a + s b (FP32)
+ks_status launch_axpy_f32(Problem &P, const float *a, float s, const float *b, float *out);
+// x += d (x FP64, d FP32)
+ks_status launch_add_f64_f32(Problem &P, double *x, const float *d);
+// out = A + s I (p x p); out may be A
+ks_status launch_add_identity(Problem &P, const double *A, double s, double *out);
+// C = alpha op(A) op(B) + beta C (p x p FP64, op = transpose when the flag is set;
+// C must not alias A or B)
+ks_status launch_small_gemm(Problem &P, int ta, const double *A, int tb, const double *B,
+                            double alpha, double beta, double *C);
+// out = A + s B (p x p; out may be A or B)
+ks_status launch_add_pp(Problem &P, const double *A, double s, const double *B, double *out);
+// out = X + Y + Y^T (p x p; out must not alias Y)
+ks_status launch_sym_add(Problem &P, const double *X, const double *Y, double *out);
+// out = R - (T + T^T) / tau (p x p)
+ks_status launch_qr_exact_gram(Problem &P, const double *R, const double *T, double tau,
+                               double *out);
 // ks_cg.cu: K v = 4 pi h^3 rho; v in/out (warm if warm), r out
 ks_status launch_cg(Problem &P, const double *rho, double *v, double *r, bool warm);
 ks_status launch_sine_setup(Problem &P);
@@ -219,6 +255,15 @@ ks_status launch_hamiltonian(Problem &P, const T *X, const double *veff, T *EX, 
                              double *ekin_out);
 template <typename T>
 ks_status launch_mass(Problem &P, const T *X, T *MX);
+// Increment form (FP32 phase with X = X_b + d): the change of the gradient
+// from the base, e = f K d + 2 f h^3 (Diag(veff - veff_b) xb + Diag(veff) d),
+// Md = M d (may be null), and the kinetic energy change from the base,
+// sum d . (f K X_b + (f/2) K d) with f K X_b = eb - 2 f h^3 veff_b xb, into
+// *dkin_out.  xb = fl32(X_b), eb = fl32(E_X at X_b with veff_b) (f = occ, or
+// mu occ for TFW).
+ks_status launch_hamiltonian_inc(Problem &P, const float *d, const double *veff,
+                                 const double *veff_b, const float *xb, const float *eb,
+                                 float *e, float *Md, double *dkin_out);
 // MD = M D; dnorm2 = sum D.MD; with prev != null also the BB traces.
 template <typename T>
 struct BBPrevT { const T *X, *MX, *D, *MD; };
@@ -271,7 +316,9 @@ enum Block { B_X0 = 0, B_X1, B_X2, B_MX0, B_MX1, B_MX2, B_EX0, B_EX1, B_G, B_D0,
 
 // Offsets (in units of p*p) of the small matrices in the pp pool; the first
 // 6 p^2 are scratch of the factor kernels.
-enum Small { S_WORK = 0, S_S = 6, S_DMD, S_O, S_A, S_B, S_C1, S_C2, S_T, S_COUNT };
+// S_XMD .. S_E3: the FP32 phase in increment form (X^T M D and work).
+enum Small { S_WORK = 0, S_S = 6, S_DMD, S_O, S_A, S_B, S_C1, S_C2, S_T, S_XMD, S_E1, S_E2, S_E3,
+             S_SB, S_DS, S_COUNT };
 
 // Slack of the Armijo test for the rounding of the energy sums: in the FP64
 // phase a trial is not rejected for a rise below 4 eps sum |E_parts| (near

@@ -7,6 +7,15 @@
 //   mass:         M X
 //   mass_dots:    M D, ||D||_M^2 = sum D . M D and the Barzilai-Borwein
 //                 traces of Eq. bb-1 in the M inner product.
+//   hamiltonian, increment form (FP32 phase with X = X_b + delta): the
+//                 stencil runs on delta and, with the base X_b, its gradient
+//                 E_b = f K X_b + 2 f h^3 Diag(V_b) X_b and potential V_b,
+//                 gives the change of the gradient from the base,
+//                 e = E_X - E_b = f K delta + 2 f h^3 (Diag(V - V_b) X_b
+//                 + Diag(V) delta), M delta, and the change of the kinetic
+//                 energy, sum delta . (f K X_b + (f/2) K delta) with
+//                 f K X_b = E_b - 2 f h^3 V_b X_b, accumulated with
+//                 compensation; every rounding scales with delta or V - V_b.
 //
 // Plane-marching form.  For a plane z' and a node (x, y) let
 //   c(z') = X(x, y, z'),  f(z') = sum of the 4 in-plane face neighbours,
@@ -36,7 +45,7 @@
 
 namespace ks {
 
-enum StencilKind : int { SK_HAM = 0, SK_MASS = 1, SK_MASS_DOT = 2, SK_MASS_BB = 3 };
+enum StencilKind : int { SK_HAM = 0, SK_MASS = 1, SK_MASS_DOT = 2, SK_MASS_BB = 3, SK_HAM_INC = 4 };
 
 constexpr int kStThreads = 256;
 constexpr int kStNodesPerThread = 4;
@@ -59,7 +68,8 @@ struct StArgs {
   void *out1;                 // E_X (SK_HAM) or M A
   void *out2;                 // M X (SK_HAM, optional)
   const double *veff;
-  const void *X, *MX, *Xp, *MXp, *Dp, *MDp;   // SK_MASS_BB
+  const void *X, *MX, *Xp, *MXp, *Dp, *MDp;   // SK_MASS_BB; SK_HAM_INC: X = X_b, MX = E_b
+  const double *veff_b;       // SK_HAM_INC: V_b
   double *part;               // block partials, channel-major
   int nb;                     // number of blocks (partials stride)
   double *red_out;            // reduced channels (scaled by red_scale)
@@ -188,6 +198,20 @@ __device__ __forceinline__ void stencil_plain_body(const StArgs &a, int vb) {
           ((T *)a.out1)[idx] = kin * kx + vscale * (T)a.veff[k] * centre;
           if (a.out2) ((T *)a.out2)[idx] = m;
           acc0 = fma(centre, kx, acc0);
+        } else if (Kind == SK_HAM_INC) {
+          const T kx = k0 * centre + ke * edges + kc * corners;
+          const T xb = ((const T *)a.X)[idx], eb = ((const T *)a.MX)[idx];
+          const T v = (T)a.veff[k], vb = (T)a.veff_b[k], dv = (T)(a.veff[k] - a.veff_b[k]);
+          ((T *)a.out1)[idx] = kin * kx + vscale * (dv * xb + v * centre);
+          if (a.out2) ((T *)a.out2)[idx] = m;
+          // compensated sum of delta . (2 f K X_b + f K delta); acc1 holds the
+          // running rounding error
+          const T fkxb = eb - vscale * vb * xb;
+          const T t = centre * ((T)2 * fkxb + kin * kx);
+          const T y = t - acc1;
+          const T sum = acc0 + y;
+          acc1 = (sum - acc0) - y;
+          acc0 = sum;
         } else {
           ((T *)a.out1)[idx] = m;
           if (Kind >= SK_MASS_DOT) acc0 = fma(centre, m, acc0);
@@ -207,7 +231,8 @@ __device__ __forceinline__ void stencil_plain_body(const StArgs &a, int vb) {
     }
   }
   if (Kind == SK_MASS) return;
-  const double s0 = block_sum((double)acc0, smem);
+  const double s0 =
+      block_sum(Kind == SK_HAM_INC ? (double)acc0 - (double)acc1 : (double)acc0, smem);
   if (threadIdx.x == 0) a.part[vb] = s0;
   if (Kind == SK_MASS_BB) {
     const double s1 = block_sum((double)acc1, smem);
@@ -255,6 +280,9 @@ __global__ void __launch_bounds__(kStThreads, 2) stencil_tma_kernel(const __grid
   T *ring = reinterpret_cast<T *>(st_ring_raw + ((128u - (smem_addr(st_ring_raw) & 127u)) & 127u));
   __shared__ __align__(8) uint64_t full[kStStages];
   __shared__ T vs[3][TXY];
+  // SK_HAM_INC: V_b and V - V_b (formed in FP64) of the same planes
+  __shared__ T vbs[Kind == SK_HAM_INC ? 3 : 1][Kind == SK_HAM_INC ? TXY : 1];
+  __shared__ T dvs[Kind == SK_HAM_INC ? 3 : 1][Kind == SK_HAM_INC ? TXY : 1];
   __shared__ double smem[33];
   const StArgs &a = ta.a;
   const int N = a.N, p = a.p;
@@ -295,9 +323,13 @@ __global__ void __launch_bounds__(kStThreads, 2) stencil_tma_kernel(const __grid
   // V_eff of plane z0 - 1 + q is read one iteration ahead by the thread that
   // owns the node, converted once and kept in vs[q % 3]
   const int vx = x0 + (int)threadIdx.x % Tl::TX, vy = y0 + (int)threadIdx.x / Tl::TX;
-  const bool vown = Kind == SK_HAM && (int)threadIdx.x < TXY && vx < N && vy < N;
-  double vreg = 0.0;
-  if (vown && z0 >= 1) vreg = a.veff[((long long)(z0 - 1) * N + vy) * N + vx];
+  constexpr bool kHam = Kind == SK_HAM || Kind == SK_HAM_INC;
+  const bool vown = kHam && (int)threadIdx.x < TXY && vx < N && vy < N;
+  double vreg = 0.0, vbreg = 0.0;
+  if (vown && z0 >= 1) {
+    vreg = a.veff[((long long)(z0 - 1) * N + vy) * N + vx];
+    if (Kind == SK_HAM_INC) vbreg = a.veff_b[((long long)(z0 - 1) * N + vy) * N + vx];
+  }
 
   const StCoefT<T> cf(a);
   T acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
@@ -307,10 +339,18 @@ __global__ void __launch_bounds__(kStThreads, 2) stencil_tma_kernel(const __grid
   for (int q = 0; q < nplanes; ++q) {
     const int zp = z0 - 1 + q;
     const int st = q % kStStages;
-    if (Kind == SK_HAM && (int)threadIdx.x < TXY) {
+    if (kHam && (int)threadIdx.x < TXY) {
       vs[q % 3][threadIdx.x] = (T)vreg;
+      if (Kind == SK_HAM_INC) {
+        vbs[q % 3][threadIdx.x] = (T)vbreg;
+        dvs[q % 3][threadIdx.x] = (T)(vreg - vbreg);
+      }
       vreg = 0.0;
-      if (vown && zp + 1 < N) vreg = a.veff[((long long)(zp + 1) * N + vy) * N + vx];
+      vbreg = 0.0;
+      if (vown && zp + 1 < N) {
+        vreg = a.veff[((long long)(zp + 1) * N + vy) * N + vx];
+        if (Kind == SK_HAM_INC) vbreg = a.veff_b[((long long)(zp + 1) * N + vy) * N + vx];
+      }
     }
     const bool got = mbar_wait_parity(&full[st], (uint32_t)((q / kStStages) & 1));
     const T *tile = ring + st * Rg::STAGE;
@@ -353,6 +393,17 @@ __global__ void __launch_bounds__(kStThreads, 2) stencil_tma_kernel(const __grid
           }
         }
       }
+      if (Kind == SK_HAM_INC) {
+#pragma unroll
+        for (int r = 0; r < kStNodesPerThread; ++r) {
+          const int gx = x0 + lx[r], gy = y0 + ly[r];
+          if (ovalid && gx < N && gy < N) {
+            const long long idx = (((long long)z * N + gy) * N + gx) * p + o;
+            bb[0][r] = ((const T *)a.X)[idx];
+            bb[1][r] = ((const T *)a.MX)[idx];
+          }
+        }
+      }
 #pragma unroll
       for (int r = 0; r < kStNodesPerThread; ++r) {
         const int gx = x0 + lx[r], gy = y0 + ly[r];
@@ -369,6 +420,20 @@ __global__ void __launch_bounds__(kStThreads, 2) stencil_tma_kernel(const __grid
             ((T *)a.out1)[idx] = cf.kin * kx + cf.vscale * vz[ly[r] * Tl::TX + lx[r]] * centre;
             if (a.out2) ((T *)a.out2)[idx] = m;
             acc0 = fma(centre, kx, acc0);
+          } else if (Kind == SK_HAM_INC) {
+            const T kx = cf.k0 * centre + cf.ke * edges + cf.kc * corners;
+            const T xb = bb[0][r], eb = bb[1][r];
+            const int nd = ly[r] * Tl::TX + lx[r];
+            const int pl = (q + 2) % 3;
+            const T v = vz[nd], vb = vbs[pl][nd], dv = dvs[pl][nd];
+            ((T *)a.out1)[idx] = cf.kin * kx + cf.vscale * (dv * xb + v * centre);
+            if (a.out2) ((T *)a.out2)[idx] = m;
+            const T fkxb = eb - cf.vscale * vb * xb;
+            const T t = centre * ((T)2 * fkxb + cf.kin * kx);
+            const T y = t - acc1;
+            const T sum = acc0 + y;
+            acc1 = (sum - acc0) - y;
+            acc0 = sum;
           } else {
             ((T *)a.out1)[idx] = m;
             if (Kind >= SK_MASS_DOT) acc0 = fma(centre, m, acc0);
@@ -402,7 +467,8 @@ __global__ void __launch_bounds__(kStThreads, 2) stencil_tma_kernel(const __grid
     acc0 = acc1 = acc2 = acc3 = 0;
   }
   if (Kind == SK_MASS) return;
-  const double s0 = block_sum((double)acc0, smem);
+  const double s0 =
+      block_sum(Kind == SK_HAM_INC ? (double)acc0 - (double)acc1 : (double)acc0, smem);
   if (threadIdx.x == 0) a.part[blockIdx.x] = s0;
   if (Kind == SK_MASS_BB) {
     const double s1 = block_sum((double)acc1, smem);
@@ -493,7 +559,7 @@ static ks_status stencil_launch_pc(Problem &P, StArgs &a, int nchan, double flop
   a.part = P.partials;
   a.counter = P.red_counter;
   a.status = P.dstatus;
-  const int cls = Kind == SK_HAM ? KP_HAMILTONIAN : KP_MASS;
+  const int cls = (Kind == SK_HAM || Kind == SK_HAM_INC) ? KP_HAMILTONIAN : KP_MASS;
   ks_status st;
   // one amplitude (PC = 1, p = 1) has an 8-byte row pitch, which no tensor
   // map can describe: plain staging only
@@ -532,6 +598,27 @@ ks_status launch_hamiltonian(Problem &P, const T *X, const double *veff, T *EX, 
   const double total = (double)P.n * P.p;
   return stencil_launch<T, SK_HAM>(P, a, 1, 27.0 * total,
                                    total * sizeof(T) * (MX ? 3 : 2) + 8.0 * P.n);
+}
+
+ks_status launch_hamiltonian_inc(Problem &P, const float *d, const double *veff,
+                                 const double *veff_b, const float *xb, const float *eb,
+                                 float *e, float *Md, double *dkin_out) {
+  StArgs a{};
+  a.occ = P.occ;
+  a.kfac = P.occ * P.kin_w;
+  a.h3 = P.h * P.h * P.h;
+  a.A = d;
+  a.out1 = e;
+  a.out2 = Md;
+  a.veff = veff;
+  a.veff_b = veff_b;
+  a.X = xb;
+  a.MX = eb;
+  a.red_out = dkin_out;
+  a.red_scale = 0.5;
+  const double total = (double)P.n * P.p;
+  return stencil_launch<float, SK_HAM_INC>(P, a, 1, 33.0 * total,
+                                           total * sizeof(float) * (Md ? 5 : 4) + 8.0 * P.n);
 }
 
 template <typename T>
