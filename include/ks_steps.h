@@ -143,12 +143,13 @@ ks_status ks_selftest_wait_timeout(void *stream, int *status, double *seconds);
 /* Peak-rate probe of the FMA pipes, the denominator of the roofline of the
  * FP64 n p^2 contractions (Grams and updates of Sec. 3, rows of Alg. ConOptM)
  * and of the FP32 SIMT kernels.  Enqueues one kernel of `blocks` blocks of
- * 256 threads on `stream`; each thread runs 8 independent FMA recurrences
- * for 4 * iters rounds with no memory traffic.  The caller times the launch
- * (e.g. with events on the same stream); nothing is synchronised here.
+ * 256 threads on `stream`; each thread updates a 4 x 4 block of accumulators
+ * with the outer product of two register 4-vectors `iters` times (16
+ * independent FMA chains) with no memory traffic.  The caller times the
+ * launch (e.g. with events on the same stream); nothing is synchronised here.
  *   fp64    nonzero: FP64 FMAs; zero: FP32 FMAs
  *   blocks  grid size (a multiple of the SM count keeps every SM busy)
- *   iters   rounds of 4 x 8 FMAs per thread
+ *   iters   rounds of 16 FMAs per thread
  *   stream  cudaStream_t, or NULL for the legacy default stream
  *   sink    DEVICE, at least `blocks` doubles; written only under a condition
  *           the recurrence never meets, so its contents stay as they are
