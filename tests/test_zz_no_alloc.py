@@ -44,7 +44,7 @@ def test_noalloc_gram_small_widths_twice():
     # widths below one 64-wide tile (the padded tile path), two calls in a row
     import paper_1308_2864_gb300 as ks
     lib = ks.load_library()
-    s = ki.small_system(N=11, L=6.0, natoms=1, p=5, Z=2.0, seed=9)
+    s = ki.small_system(N=11, L=6.0, natoms=1, p=8, Z=2.0, seed=9)
     P = ks.Problem.from_system(s)
     stream = torch.cuda.current_stream()
     rng = np.random.default_rng(23)
