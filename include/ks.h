@@ -109,11 +109,13 @@ typedef struct {
   double ortho_tol;   /* re-orthonormalise when ||X^T M X - I||_F > ortho_tol (1e-12) */
   int ortho_every;    /* QR path: check ||X^T M X - I|| every this many iterations (20) */
   int verbose;        /* > 0: print E, ||D||_M and tau to stderr every `verbose` iterations (0) */
-  int precision;      /* KS_FP64, or KS_MIXED: FP32 orbital blocks until ||D||_M <= polish_gtol
-                         (or no progress for stall_iters iterations), then an FP64 polish
-                         to gtol; the Hartree solve, energy sums and p x p algebra are FP64
-                         in both (the FP32 phase evaluates eps_xc and v_xc in FP32 and
-                         solves to mixed_cg_tol) (KS_FP64) */
+  int precision;      /* KS_FP64, or KS_MIXED: an FP32 phase, then an FP64 polish to gtol.
+                         The FP32 phase carries the iterate as an FP64 base plus FP32
+                         increments (fp32_increment = 1, below) and runs to gtol itself; with
+                         fp32_increment = 0 it holds FP32 orbital blocks until ||D||_M <=
+                         polish_gtol (or no progress for stall_iters iterations), evaluates
+                         eps_xc and v_xc in FP32 and solves the Hartree CG to mixed_cg_tol.
+                         The energy sums and p x p algebra are FP64 in every form (KS_FP64) */
   double polish_gtol; /* switch from the FP32 phase to the FP64 polish (1e-4) */
   int stall_iters;    /* 1: the FP32 phase also ends when it stagnates, i.e. the mean of
                          df_k = |E_{k-1} - E_k| / (|E_{k-1}| + 1) over the last three

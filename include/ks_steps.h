@@ -149,7 +149,7 @@ ks_status ks_selftest_wait_timeout(void *stream, int *status, double *seconds);
  * launch (e.g. with events on the same stream); nothing is synchronised here.
  *   fp64    nonzero: FP64 FMAs; zero: FP32 FMAs
  *   blocks  grid size (a multiple of the SM count keeps every SM busy)
- *   iters   rounds of 16 FMAs per thread
+ *   iters   rounds of 16 FMAs per thread (rounded up to a multiple of 4)
  *   stream  cudaStream_t, or NULL for the legacy default stream
  *   sink    DEVICE, at least `blocks` doubles; written only under a condition
  *           the recurrence never meets, so its contents stay as they are

@@ -53,7 +53,7 @@ size_t problem_bytes(int N, int p, int sms) {
   b += ((size_t)N * N + 2 * N) * sizeof(float);                      // sine basis
   b += (size_t)Problem::kNBlocks * (n * p * sizeof(double) + 256);    // n x p blocks
   b += (size_t)S_COUNT * p * p * sizeof(double);                      // small matrices
-  b += (size_t)2 * p * p * sizeof(float);                             // FP32 coefficients
+  b += (size_t)3 * p * p * sizeof(float);                             // FP32 coefficients
   b += tc_image_floats(p) * sizeof(float);                            // tensor-core image
   b += (size_t)(2 * p + 128) * sizeof(int);                           // split exponents
   b += oz_image_bytes(p);                                             // split coefficients
@@ -530,8 +530,7 @@ static ks_status project_split(Problem &P, int retraction, int bx, const float *
   const int p = P.p;
   float *Gi = lower32(P, B_G);
   const float *X32 = upper32(P, bx), *d = lower32(P, bx);
-  KS_TRY(launch_mass_inverse<float>(P, e, Gi));
-  KS_TRY(launch_axpy_f32(P, Gi, 1.0f, base_db(P), Gi));                    // D_b + M^{-1} e
+  KS_TRY(launch_mass_inverse<float>(P, e, Gi, base_db(P)));                // D_b + M^{-1} e
   KS_TRY(launch_gram<float>(P, base_eb(P), p, d, p, sm(P, S_DS)));          // E_b^T delta
   KS_TRY(launch_gram<float>(P, e, p, X32, p, sm(P, S_E1)));                 // e^T X
   KS_TRY(launch_add_pp(P, sm(P, S_DS), 1.0, sm(P, S_E1), sm(P, S_DS)));     // dS
@@ -565,16 +564,20 @@ static ks_status project_split(Problem &P, int retraction, int bx, const float *
 // along the Cayley curve, with its FP32 copy X32 = X_b + delta+.  Both steps
 // are written on the basis [X, D], X+ = X A + D B, and A, B are
 // right-multiplied by L^{-T} with L L^T = Y^T M Y formed exactly from
-// X^T M X = I, T = X^T M D and R = D^T M D (p x p Grams): the trial is
-// M-orthonormal to the rounding of those Grams even though D carries FP32
-// rounding normal to the manifold (Alg. ChQR with the explicit Y^T M Y;
-// Prop. 3.1's I + tau^2 R would leave the trial off the manifold by tau
-// times that component, an error whose energy, amplified by the Lagrange
-// multipliers, can exceed the decrease the line search asks for).
-//   QR:     A = I, B = -tau I; Y^T M Y = I - tau (T + T^T) + tau^2 R.
+// X^T M X = I, T = X^T M D and R = D^T M D (p x p Grams):
+//   QR:     A = I, B = -tau I; Y^T M Y = I - tau (T + T^T) + tau^2 R
+//           (Alg. ChQR with the explicit Y^T M Y).
 //   Cayley: X+ = X C1 + G C2 (Eq. WY3) with G = D + X S gives A = C1 + S C2,
 //           B = C2; Y^T M Y = A^T A + A^T T B + B^T T^T A + B^T R B.
-// The increment is then delta+ = X_b (A - I) + delta A + D B.
+// The first-order term matters here.  With a drift eta = X^T M X - I the
+// projected gradient has X^T M D = -eta S, and Prop. 3.1's I + tau^2 R
+// would carry eta into the trial as eta + tau (eta S + S eta): growth by
+// about 1 + 2 tau ||S|| per step (the Lagrange multipliers reach ~27 per
+// orbital on the 64^3 system, about 100x over the 32 steps between
+// refreshes), and an energy error of order tr(Lambda eta) that the line
+// search sees.  With the measured T the trial keeps X^T M X - I = eta.  The
+// increment is then delta+ = X_b (A - I) + delta A + D B, with A - I formed
+// in FP64.
 static ks_status retract_split(Problem &P, int retraction, int bx, const float *D, double tau,
                                int bt) {
   const int p = P.p;
@@ -605,6 +608,10 @@ static ks_status retract_split(Problem &P, int retraction, int bx, const float *
   }
   float *dt = lower32(P, bt), *xt = upper32(P, bt);
   KS_TRY(launch_add_identity(P, Ac, -1.0, sm(P, S_T)));
+  if (combine3_f32_applies(P, p, p, p, p))
+    // one pass: delta+ and its FP32 copy X_b + delta+
+    return launch_combine3_f32(P, base_hi(P), p, sm(P, S_T), lower32(P, bx), p, Ac, D, p, Bc, dt,
+                               base_hi(P), xt, p);
   // X_b (A - I) + D B into the trial's upper half, then delta A added
   KS_TRY(launch_combine<float>(P, base_hi(P), p, sm(P, S_T), D, p, Bc, 1.0, 0.0, nullptr, xt, p));
   KS_TRY(launch_combine<float>(P, lower32(P, bx), p, Ac, nullptr, 0, nullptr, 1.0, 1.0, xt, dt,
@@ -1042,7 +1049,7 @@ ks_status ks_problem_create(const ks_problem_desc *d, ks_problem **out) {
   for (auto &b : P.blk) { ALLOC(b, np + 32); }
   P.pp_len = (size_t)S_COUNT * P.p * P.p;
   ALLOC(P.pp, P.pp_len);
-  ALLOC(P.cf, (size_t)2 * P.p * P.p);
+  ALLOC(P.cf, (size_t)3 * P.p * P.p);
   P.tc_img_len = tc_image_floats(P.p);
   ALLOC(P.tc_img, P.tc_img_len);
   P.oz_emax_len = 2 * P.p + 128;
@@ -1081,6 +1088,7 @@ ks_status ks_problem_create(const ks_problem_desc *d, ks_problem **out) {
   if (e != cudaSuccess) return fail(cuda_error(e, "memset"));
   if ((st = configure_small_kernels()) != KS_OK) return fail(st);
   if ((st = configure_tc_kernels()) != KS_OK) return fail(st);
+  if ((st = configure_blas_kernels()) != KS_OK) return fail(st);
   if ((st = launch_setup(P)) != KS_OK) return fail(st);
   if ((st = launch_sine_setup(P)) != KS_OK) return fail(st);
   if ((st = sync_scalars(P)) != KS_OK) return fail(st);

@@ -9,10 +9,22 @@
 // thread, strided so that shared-memory reads are conflict-free.
 #include <mutex>
 
+#include "ks_async.cuh"
 #include "ks_device.cuh"
 #include "ks_steps.h"
 
 namespace ks {
+
+// 16-byte global -> shared copy (cp.async, L2 only); src_bytes = 0 copies
+// nothing and zero-fills the 16 bytes.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src),
+               "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
 
 // Tensor cores for the FP32 phase when the products are wide enough for the
 // SIMT FP32 pipes to be the bound (use_tc = 1: from 256 columns; 2: always;
@@ -307,6 +319,84 @@ __global__ void __launch_bounds__(256) gram_small_kernel(long long n, int pa, in
   gram_small_body<T>(n, pa, qb, rows_per, A, B, part, blockIdx.x);
 }
 
+// Pipelined FP32 Gram for 32 < max(pa, qb) <= 64 and 16-byte-aligned
+// operands (widths multiples of 4): persistent blocks take stages of 32 rows
+// in turn (block b: stages b, b + G, ...), copied global -> shared by
+// cp.async three stages ahead (columns beyond pa, qb zero-filled), and keep
+// one 64 x 64 FP32 tile (4 x 4 per thread) over all their rows; each block
+// writes one FP64 partial tile, summed afterwards in block order.
+constexpr int kGaStages = 3, kGaRows = 32;
+constexpr size_t kGaSmem = (size_t)kGaStages * 2 * kGaRows * kTile * sizeof(float);
+
+__global__ void __launch_bounds__(256, 4) gram_ta_kernel(long long n, int pa, int qb,
+                                                         const float *__restrict__ A,
+                                                         const float *__restrict__ B,
+                                                         double *__restrict__ part) {
+  extern __shared__ __align__(16) float ga_smem[];
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const long long nst = (n + kGaRows - 1) / kGaRows;
+  const long long W = nst > blockIdx.x ? (nst - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  auto issue = [&](long long w) {
+    const long long r0 = (blockIdx.x + w * gridDim.x) * kGaRows;
+    float *dst = ga_smem + (size_t)(w % kGaStages) * 2 * kGaRows * kTile;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int idx = tid + t * 256;               // 0..1023: operand, row, 4-column chunk
+      const int op = idx >> 9, rr = (idx >> 4) & 31, c4 = (idx & 15) * 4;
+      const long long row = r0 + rr;
+      const int w_ = op ? qb : pa;
+      const float *M = op ? B : A;
+      const float *src = A;
+      uint32_t bytes = 0;
+      if (row < n && c4 < w_) {
+        src = M + row * w_ + c4;
+        bytes = 16;
+      }
+      cp_async16(smem_addr(dst + (size_t)op * kGaRows * kTile + rr * kTile + c4), src, bytes);
+    }
+  };
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  for (int st = 0; st < kGaStages - 1; ++st) {
+    if (st < W) issue(st);
+    cp_async_commit();
+  }
+  for (long long w = 0; w < W; ++w) {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(kGaStages - 2) : "memory");
+    __syncthreads();
+    if (w + kGaStages - 1 < W) issue(w + kGaStages - 1);
+    cp_async_commit();
+    const float *As = ga_smem + (size_t)(w % kGaStages) * 2 * kGaRows * kTile;
+    const float *Bs = As + kGaRows * kTile;
+#pragma unroll 8
+    for (int r = 0; r < kGaRows; ++r) {
+      const float4 av = *reinterpret_cast<const float4 *>(As + r * kTile + 4 * ty);
+      const float4 bv = *reinterpret_cast<const float4 *>(Bs + r * kTile + 4 * tx);
+      const float a4[4] = {av.x, av.y, av.z, av.w};
+      const float b4[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a4[i], b4[j], acc[i][j]);
+    }
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  double *dst = part + (long long)blockIdx.x * pa * qb;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int a = 4 * ty + i;
+    if (a >= pa) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int b = 4 * tx + j;
+      if (b < qb) dst[(long long)a * qb + b] = (double)acc[i][j];
+    }
+  }
+}
+
 template <typename T>
 ks_status launch_gram(Problem &P, const T *A, int pa, const T *B, int qb, double *out) {
   if (sizeof(T) == 8 && P.use_oz > 0 && pa + qb <= P.oz_emax_len &&
@@ -337,6 +427,33 @@ ks_status launch_gram(Problem &P, const T *A, int pa, const T *B, int qb, double
       ProfScope ps_(P.stream, KP_REDUCE);
       gram_reduce_kernel<<<(int)((8 * len + kThreads - 1) / kThreads), kThreads, 0, P.stream>>>(
           chunks, len, P.partials, out);
+    }
+    KS_CUDA_TRY(cudaGetLastError());
+    return KS_OK;
+  }
+#ifndef KS_NO_TA
+  if (sizeof(T) == 4 && pa <= kTile && qb <= kTile && (pa > kMidPQ || qb > kMidPQ) &&
+#else
+  if (false &&
+#endif
+      pa % 4 == 0 && qb % 4 == 0 && reinterpret_cast<uintptr_t>(A) % 16 == 0 &&
+      reinterpret_cast<uintptr_t>(B) % 16 == 0) {
+    const long long nst = (P.n + kGaRows - 1) / kGaRows;
+    long long blocks = 4LL * P.sms;
+    if (blocks > nst) blocks = nst;
+    if ((size_t)blocks * pa * qb > P.partials_len)
+      return set_error(KS_EINVAL, "gram: partial buffer too small");
+    {
+      ProfScope ps_(P.stream, KP_GRAM, 2.0 * P.n * pa * qb, (double)P.n * (pa + qb) * sizeof(T));
+      gram_ta_kernel<<<(int)blocks, 256, kGaSmem, P.stream>>>(P.n, pa, qb, (const float *)A,
+                                                             (const float *)B, P.partials);
+    }
+    KS_CUDA_TRY(cudaGetLastError());
+    const long long len = (long long)pa * qb;
+    {
+      ProfScope ps_(P.stream, KP_REDUCE);
+      gram_reduce_kernel<<<(int)((8 * len + kThreads - 1) / kThreads), kThreads, 0, P.stream>>>(
+          (int)blocks, len, P.partials, out);
     }
     KS_CUDA_TRY(cudaGetLastError());
     return KS_OK;
@@ -544,6 +661,137 @@ __global__ void __launch_bounds__(256) combine_narrow_kernel(
                          gridDim.x);
 }
 
+// Tall-skinny FP32 update, q <= 64 output columns and K = k1 + k2 + k3 <= 192
+// (the retraction and projection updates of the FP32 phase at p <= 64):
+// persistent blocks keep the whole coefficient matrix [C1; C2] (K x 64, zero
+// padded) in shared memory for the life of the block and stream row tiles
+// of 128 rows of [A1, A2] through a double-buffered stage of 32 K-values,
+// the next stage (of this tile or of the block's next tile) loaded into
+// registers while the current one is consumed.  Thread (ty, tx) of 16 x 16
+// owns rows 8 ty .. 8 ty + 7 and columns 4 tx .. 4 tx + 3 of a tile: 32 FMAs
+// per three vector shared-memory loads.  Each output is the same K-ascending
+// FMA chain (A1 C1, then A2 C2) and the same final alpha/beta step as
+// combine_tile_body, so the two kernels give bitwise-equal results for two
+// blocks.  A third block (A3 C3) and a second output out2 = add2 + out
+// serve the increment form's retraction in one pass.
+constexpr int kTsRows = 128, kTsK = 32, kTsMaxK = 192, kTsLd = kTsRows + 4;
+
+size_t combine_ts_smem(int K) {
+  const int nst = (K + kTsK - 1) / kTsK;
+  return ((size_t)nst * kTsK * kTile + (size_t)2 * kTsK * kTsLd) * sizeof(float);
+}
+
+__global__ void __launch_bounds__(256, 2) combine_ts_kernel(
+    long long n, int q, const float *__restrict__ A1, int k1, const float *__restrict__ c1,
+    const float *__restrict__ A2, int k2, const float *__restrict__ c2,
+    const float *__restrict__ A3, int k3, const float *__restrict__ c3, float alpha, float beta,
+    const float *__restrict__ Bm, float *__restrict__ out, const float *__restrict__ add2,
+    float *__restrict__ out2, long long ntiles) {
+  extern __shared__ __align__(16) float ts_smem[];
+  const int k12 = k1 + (A2 ? k2 : 0);
+  const int K = k12 + (A3 ? k3 : 0);
+  const int nst = (K + kTsK - 1) / kTsK;
+  float *Cs = ts_smem;                              // [nst * kTsK][64]
+  float *As = ts_smem + (size_t)nst * kTsK * kTile;  // [2][kTsK][kTsLd]
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  for (int e = tid; e < nst * kTsK * kTile; e += 256) {
+    const int r = e / kTile, c = e % kTile;
+    float v = 0.f;
+    if (c < q) {
+      if (r < k1) v = c1[(long long)r * q + c];
+      else if (r < k12) v = c2[(long long)(r - k1) * q + c];
+      else if (r < K) v = c3[(long long)(r - k12) * q + c];
+    }
+    Cs[e] = v;
+  }
+  const long long mine = ntiles > blockIdx.x ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  const long long W = mine * nst;                   // (tile, stage) steps of this block
+  constexpr int kPer = kTsRows * kTsK / 256;       // staged A values per thread
+  float ra[kPer];
+  auto fetch = [&](long long w) {
+    const long long tile = blockIdx.x + (w / nst) * gridDim.x;
+    const int k0 = (int)(w % nst) * kTsK;
+#pragma unroll
+    for (int t = 0; t < kPer; ++t) {
+      const int idx = tid + t * 256;
+      const int rr = idx / kTsK, kk = idx % kTsK;
+      const long long row = tile * kTsRows + rr;
+      const int k = k0 + kk;
+      float v = 0.f;
+      if (row < n) {
+        if (k < k1) v = A1[row * k1 + k];
+        else if (k < k12) v = A2[row * k2 + (k - k1)];
+        else if (k < K) v = A3[row * k3 + (k - k12)];
+      }
+      ra[t] = v;
+    }
+  };
+  auto stash = [&](int buf) {
+#pragma unroll
+    for (int t = 0; t < kPer; ++t) {
+      const int idx = tid + t * 256;
+      As[((size_t)buf * kTsK + idx % kTsK) * kTsLd + idx / kTsK] = ra[t];
+    }
+  };
+  float acc[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  if (W > 0) {
+    fetch(0);
+    stash(0);
+  }
+  __syncthreads();
+  for (long long w = 0; w < W; ++w) {
+    const int buf = (int)(w & 1);
+    const bool more = w + 1 < W;
+    if (more) fetch(w + 1);
+    const int k0 = (int)(w % nst) * kTsK;
+    const float *Ab = As + (size_t)buf * kTsK * kTsLd;
+#pragma unroll 8
+    for (int k = 0; k < kTsK; ++k) {
+      const float4 a0 = *reinterpret_cast<const float4 *>(Ab + k * kTsLd + 8 * ty);
+      const float4 a1 = *reinterpret_cast<const float4 *>(Ab + k * kTsLd + 8 * ty + 4);
+      const float4 cv = *reinterpret_cast<const float4 *>(Cs + (size_t)(k0 + k) * kTile + 4 * tx);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float cc[4] = {cv.x, cv.y, cv.z, cv.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], cc[j], acc[i][j]);
+    }
+    if (w % nst == nst - 1) {
+      const long long tile = blockIdx.x + (w / nst) * gridDim.x;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const long long row = tile * kTsRows + 8 * ty + i;
+        if (row < n) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int col = 4 * tx + j;
+            if (col < q) {
+              float v = alpha * acc[i][j];
+              if (Bm) v = fmaf(beta, Bm[row * q + col], v);
+              out[row * q + col] = v;
+              if (out2) out2[row * q + col] = add2[row * q + col] + v;
+            }
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+      }
+    }
+    if (more) stash(buf ^ 1);
+    __syncthreads();
+  }
+}
+
+static void launch_ts(Problem &P, int q, const float *A1, int k1, const float *c1,
+                      const float *A2, int k2, const float *c2, const float *A3, int k3,
+                      const float *c3, float alpha, float beta, const float *Bm, float *out,
+                      const float *add2, float *out2);
+
 // FP32 copies of the update coefficients (one launch for both matrices).
 __global__ void coef_convert_kernel(long long len1, const double *__restrict__ C1,
                                     float *__restrict__ c1, long long len2,
@@ -585,6 +833,16 @@ ks_status launch_combine(Problem &P, const T *A1, int k1, const double *C1, cons
           len1, C1, c1, len2, C2, c2);
     }
     KS_CUDA_TRY(cudaGetLastError());
+    const int K = k1 + (A2 ? k2 : 0);
+    if (q <= kTile && K <= kTsMaxK) {
+      ProfScope ps_(P.stream, KP_COMBINE, 2.0 * P.n * q * K,
+                    (double)P.n * (K + q * (Bm ? 2 : 1)) * sizeof(T));
+      launch_ts(P, q, (const float *)A1, k1, c1, (const float *)A2, k2, A2 ? c2 : nullptr, nullptr,
+                0, nullptr, (float)alpha, (float)beta, (const float *)Bm, (float *)out, nullptr,
+                nullptr);
+      KS_CUDA_TRY(cudaGetLastError());
+      return KS_OK;
+    }
     ProfScope ps_(P.stream, KP_COMBINE, 2.0 * P.n * q * (k1 + (A2 ? k2 : 0)),
                   (double)P.n * ((k1 + (A2 ? k2 : 0)) + q * (Bm ? 2 : 1)) * sizeof(T));
     combine_kernel<T, float><<<grid, 256, 0, P.stream>>>(P.n, q, A1, k1, c1, A2, k2,
@@ -812,6 +1070,204 @@ template ks_status batch_convert<float, float>(Batch &, int, int);
 template ks_status launch_gram<double>(Problem &, const double *, int, const double *, int,
                                        double *);
 template ks_status launch_gram<float>(Problem &, const float *, int, const float *, int, double *);
+// Pipelined form of combine_ts_kernel for 16-byte-aligned operands (every k
+// a multiple of 4 and every A base 16-byte aligned): the A stages are copied
+// global -> shared by cp.async (16 bytes per copy, zero-filled past the last
+// row and past K) three stages ahead, row-major with a 4-float pad, so no
+// registers hold staged data and three stages of loads are in flight per
+// block.  A thread reads, per 4 K-values, one float4 of each of its 8 rows
+// and one float4 of C per K-value: 128 FMAs per 12 vector loads.  The FMA
+// chains and the final step are those of combine_ts_kernel (K ascending).
+constexpr int kTaStages = 3, kTaLd = kTsK + 4;
+
+size_t combine_ta_smem(int K) {
+  const int nst = (K + kTsK - 1) / kTsK;
+  return ((size_t)nst * kTsK * kTile + (size_t)kTaStages * kTsRows * kTaLd) * sizeof(float);
+}
+
+
+__global__ void __launch_bounds__(256, 2) combine_ta_kernel(
+    long long n, int q, const float *__restrict__ A1, int k1, const float *__restrict__ c1,
+    const float *__restrict__ A2, int k2, const float *__restrict__ c2,
+    const float *__restrict__ A3, int k3, const float *__restrict__ c3, float alpha, float beta,
+    const float *__restrict__ Bm, float *__restrict__ out, const float *__restrict__ add2,
+    float *__restrict__ out2, long long ntiles) {
+  extern __shared__ __align__(16) float ta_smem[];
+  const int k12 = k1 + (A2 ? k2 : 0);
+  const int K = k12 + (A3 ? k3 : 0);
+  const int nst = (K + kTsK - 1) / kTsK;
+  float *Cs = ta_smem;                                  // [nst * kTsK][64]
+  float *As = ta_smem + (size_t)nst * kTsK * kTile;     // [kTaStages][kTsRows][kTaLd]
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  for (int e = tid; e < nst * kTsK * kTile; e += 256) {
+    const int r = e / kTile, c = e % kTile;
+    float v = 0.f;
+    if (c < q) {
+      if (r < k1) v = c1[(long long)r * q + c];
+      else if (r < k12) v = c2[(long long)(r - k1) * q + c];
+      else if (r < K) v = c3[(long long)(r - k12) * q + c];
+    }
+    Cs[e] = v;
+  }
+  const long long mine = ntiles > blockIdx.x ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  const long long W = mine * nst;
+  // stage w: 128 rows x 32 K-values = 1024 16-byte copies, 4 per thread
+  auto issue = [&](long long w) {
+    const long long tile = blockIdx.x + (w / nst) * gridDim.x;
+    const int k0 = (int)(w % nst) * kTsK;
+    float *dst = As + (size_t)(w % kTaStages) * kTsRows * kTaLd;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int idx = tid + t * 256;
+      const int rr = idx >> 3, kq = (idx & 7) * 4;
+      const long long row = tile * kTsRows + rr;
+      const int k = k0 + kq;
+      const float *src = A1;
+      uint32_t bytes = 0;
+      if (row < n) {
+        if (k < k1) { src = A1 + row * k1 + k; bytes = 16; }
+        else if (k < k12) { src = A2 + row * k2 + (k - k1); bytes = 16; }
+        else if (k < K) { src = A3 + row * k3 + (k - k12); bytes = 16; }
+      }
+      cp_async16(smem_addr(dst + rr * kTaLd + kq), src, bytes);
+    }
+  };
+  float acc[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  for (int st = 0; st < kTaStages - 1; ++st) {
+    if (st < W) issue(st);
+    cp_async_commit();
+  }
+  __syncthreads();                                      // C staged
+  for (long long w = 0; w < W; ++w) {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(kTaStages - 2) : "memory");  // stage w landed
+    __syncthreads();                                    // ... everyone's; stage w-1 consumed
+    if (w + kTaStages - 1 < W) issue(w + kTaStages - 1);
+    cp_async_commit();
+    const int k0 = (int)(w % nst) * kTsK;
+    const float *Ab = As + (size_t)(w % kTaStages) * kTsRows * kTaLd + (size_t)8 * ty * kTaLd;
+#pragma unroll 2
+    for (int kq = 0; kq < kTsK; kq += 4) {
+      float4 a[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) a[i] = *reinterpret_cast<const float4 *>(Ab + i * kTaLd + kq);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const float4 cv = *reinterpret_cast<const float4 *>(Cs + (size_t)(k0 + kq + kk) * kTile +
+                                                            4 * tx);
+        const float cc[4] = {cv.x, cv.y, cv.z, cv.w};
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const float av = kk == 0 ? a[i].x : kk == 1 ? a[i].y : kk == 2 ? a[i].z : a[i].w;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av, cc[j], acc[i][j]);
+        }
+      }
+    }
+    if (w % nst == nst - 1) {
+      const long long tile = blockIdx.x + (w / nst) * gridDim.x;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const long long row = tile * kTsRows + 8 * ty + i;
+        if (row < n) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int col = 4 * tx + j;
+            if (col < q) {
+              float v = alpha * acc[i][j];
+              if (Bm) v = fmaf(beta, Bm[row * q + col], v);
+              out[row * q + col] = v;
+              if (out2) out2[row * q + col] = add2[row * q + col] + v;
+            }
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+      }
+    }
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+// The pipelined kernel applies when every 16-byte copy of A stays inside one
+// row of one operand: each width a multiple of 4 and each base 16-byte aligned.
+static bool ta_aligned(const float *A1, int k1, const float *A2, int k2, const float *A3, int k3) {
+  auto ok = [](const float *A, int k) {
+    return !A || (k % 4 == 0 && reinterpret_cast<uintptr_t>(A) % 16 == 0);
+  };
+  return ok(A1, k1) && ok(A2, k2) && ok(A3, k3);
+}
+
+// Launch of the tall-skinny update (pipelined when aligned).
+static void launch_ts(Problem &P, int q, const float *A1, int k1, const float *c1,
+                      const float *A2, int k2, const float *c2, const float *A3, int k3,
+                      const float *c3, float alpha, float beta, const float *Bm, float *out,
+                      const float *add2, float *out2) {
+  const int K = k1 + (A2 ? k2 : 0) + (A3 ? k3 : 0);
+  const long long ntiles = (P.n + kTsRows - 1) / kTsRows;
+  long long nb = 2LL * P.sms;
+  if (nb > ntiles) nb = ntiles;
+#ifndef KS_NO_TA
+  if (ta_aligned(A1, k1, A2, k2, A3, k3))
+#else
+  if (false)
+#endif
+    combine_ta_kernel<<<(int)nb, 256, combine_ta_smem(K), P.stream>>>(
+        P.n, q, A1, k1, c1, A2, k2, c2, A3, k3, c3, alpha, beta, Bm, out, add2, out2, ntiles);
+  else
+    combine_ts_kernel<<<(int)nb, 256, combine_ts_smem(K), P.stream>>>(
+        P.n, q, A1, k1, c1, A2, k2, c2, A3, k3, c3, alpha, beta, Bm, out, add2, out2, ntiles);
+}
+
+// out = A1 C1 + A2 C2 + A3 C3 and out2 = add2 + out in one pass of the
+// tall-skinny FP32 kernel (n x q blocks, q <= 64, k1 + k2 + k3 <= 192); false
+// (nothing launched) for other shapes or when the tensor cores take the
+// products.
+bool combine3_f32_applies(const Problem &P, int k1, int k2, int k3, int q) {
+  return q <= kTile && k1 + k2 + k3 <= kTsMaxK && !use_tensor_cores(P, k1, q);
+}
+
+ks_status launch_combine3_f32(Problem &P, const float *A1, int k1, const double *C1,
+                              const float *A2, int k2, const double *C2, const float *A3, int k3,
+                              const double *C3, float *out, const float *add2, float *out2, int q) {
+  if (!combine3_f32_applies(P, k1, k2, k3, q))
+    return set_error(KS_EINVAL, "combine3: shape outside the tall-skinny kernel");
+  // FP32 images of C1, C2, C3 one after the other in P.cf (3 p^2 floats)
+  float *c1 = P.cf, *c2 = P.cf + (size_t)k1 * q, *c3 = c2 + (size_t)k2 * q;
+  if ((size_t)(k1 + k2 + k3) * q > (size_t)3 * P.p * P.p)
+    return set_error(KS_EINVAL, "combine3: coefficient image too small");
+  const long long len1 = (long long)k1 * q, len2 = (long long)k2 * q, len3 = (long long)k3 * q;
+  {
+    ProfScope ps_(P.stream, KP_REDUCE);
+    coef_convert_kernel<<<(int)((len1 + len2 + 255) / 256), 256, 0, P.stream>>>(len1, C1, c1,
+                                                                                len2, C2, c2);
+    coef_convert_kernel<<<(int)((len3 + 255) / 256), 256, 0, P.stream>>>(len3, C3, c3, 0,
+                                                                         nullptr, nullptr);
+  }
+  KS_CUDA_TRY(cudaGetLastError());
+  const int K = k1 + k2 + k3;
+  {
+    ProfScope ps_(P.stream, KP_COMBINE, 2.0 * P.n * q * K,
+                  (double)P.n * (K + q * (out2 ? 3 : 1)) * sizeof(float));
+    launch_ts(P, q, A1, k1, c1, A2, k2, c2, A3, k3, c3, 1.0f, 0.0f, nullptr, out, add2, out2);
+  }
+  KS_CUDA_TRY(cudaGetLastError());
+  return KS_OK;
+}
+
+// Dynamic shared memory of the tall-skinny update beyond the default 48 KiB
+// (on the current device; called when a problem is created).
+ks_status configure_blas_kernels() {
+  KS_CUDA_TRY(cudaFuncSetAttribute(combine_ts_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)combine_ts_smem(kTsMaxK)));
+  KS_CUDA_TRY(cudaFuncSetAttribute(combine_ta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)combine_ta_smem(kTsMaxK)));
+  return KS_OK;
+}
+
 template ks_status launch_combine<double>(Problem &, const double *, int, const double *,
                                           const double *, int, const double *, double, double,
                                           const double *, double *, int);

@@ -120,7 +120,7 @@ struct Problem {
 
   // p x p work (all FP64)
   double *pp = nullptr;            // pool of small matrices
-  float *cf = nullptr;             // 2 p^2: FP32 copies of the update coefficients
+  float *cf = nullptr;             // 3 p^2: FP32 copies of the update coefficients
   float *tc_img = nullptr;         // coefficient image of the tensor-core update
   size_t tc_img_len = 0;
   size_t pp_len = 0;
@@ -270,9 +270,9 @@ struct BBPrevT { const T *X, *MX, *D, *MD; };
 template <typename T>
 ks_status launch_mass_dots(Problem &P, const T *D, T *MD, const T *X, const T *MX,
                            const BBPrevT<T> *prev, double *out4);
-// ks_minv.cu: G = M^{-1} E
+// ks_minv.cu: G = M^{-1} E (+ add, folded into the last sweep, when given)
 template <typename T>
-ks_status launch_mass_inverse(Problem &P, const T *E, T *G);
+ks_status launch_mass_inverse(Problem &P, const T *E, T *G, const T *add = nullptr);
 // ks_blas.cu
 // out (pa x qb, FP64) = A^T B with A n x pa, B n x qb (row-major, ld = pa, qb)
 template <typename T>
@@ -282,6 +282,14 @@ ks_status launch_gram(Problem &P, const T *A, int pa, const T *B, int qb, double
 template <typename T>
 ks_status launch_combine(Problem &P, const T *A1, int k1, const double *C1, const T *A2, int k2,
                          const double *C2, double alpha, double beta, const T *Bm, T *out, int q);
+// Function attributes of the update kernels (once per problem creation).
+ks_status configure_blas_kernels();
+// out = A1 C1 + A2 C2 + A3 C3 and out2 = add2 + out (FP32 n x q, q <= 64,
+// k1 + k2 + k3 <= 192, C FP64) in one pass; combine3_f32_applies says when.
+bool combine3_f32_applies(const Problem &P, int k1, int k2, int k3, int q);
+ks_status launch_combine3_f32(Problem &P, const float *A1, int k1, const double *C1,
+                              const float *A2, int k2, const double *C2, const float *A3, int k3,
+                              const double *C3, float *out, const float *add2, float *out2, int q);
 // elementwise precision conversion of an n x p block
 ks_status launch_convert(Problem &P, const double *in, float *out);
 ks_status launch_convert(Problem &P, const float *in, double *out);
@@ -316,7 +324,8 @@ enum Block { B_X0 = 0, B_X1, B_X2, B_MX0, B_MX1, B_MX2, B_EX0, B_EX1, B_G, B_D0,
 
 // Offsets (in units of p*p) of the small matrices in the pp pool; the first
 // 6 p^2 are scratch of the factor kernels.
-// S_XMD .. S_E3: the FP32 phase in increment form (X^T M D and work).
+// S_XMD .. S_DS: the FP32 phase in increment form (X^T M D, work, S_b and
+// S - S_b).
 enum Small { S_WORK = 0, S_S = 6, S_DMD, S_O, S_A, S_B, S_C1, S_C2, S_T, S_XMD, S_E1, S_E2, S_E3,
              S_SB, S_DS, S_COUNT };
 

@@ -19,9 +19,12 @@ namespace ks {
 constexpr int kAhead = 8;
 
 // One (line, orbital) pair t of a sweep; w: the pivots in shared memory.
+// add (nullable, same layout as out): added to every final value written,
+// while the recurrence runs on the solution itself.
 template <typename T>
 __device__ __forceinline__ void thomas_line(long long t, int N, int p, int axis, T scale,
-                                            const T *w, const T *in, T *out) {
+                                            const T *w, const T *in, T *out,
+                                            const T *add = nullptr) {
   const long long lines = (long long)N * N;
   if (t >= lines * p) return;
   const int i = (int)(t % p);
@@ -56,6 +59,7 @@ __device__ __forceinline__ void thomas_line(long long t, int N, int p, int axis,
       }
   }
   // back substitution (prev holds entry N-1, which is final)
+  if (add) dst[(long long)(N - 1) * es] = prev + add[(base + (long long)(N - 1) * stride) * p + i];
   T next = prev;
   for (int j1 = N - 2; j1 >= 0; j1 -= kAhead) {
     T v[kAhead];
@@ -66,7 +70,8 @@ __device__ __forceinline__ void thomas_line(long long t, int N, int p, int axis,
     for (int u = 0; u < kAhead; ++u)
       if (j1 - u >= 0) {
         next = v[u] - w[j1 - u] * next;
-        dst[(long long)(j1 - u) * es] = next;
+        dst[(long long)(j1 - u) * es] =
+            add ? next + add[(base + (long long)(j1 - u) * stride) * p + i] : next;
       }
   }
 }
@@ -74,13 +79,13 @@ __device__ __forceinline__ void thomas_line(long long t, int N, int p, int axis,
 template <typename T>
 __global__ void __launch_bounds__(256) thomas_kernel(int N, int p, int axis, double scale_d,
                                                      const double *__restrict__ w_d, const T *in,
-                                                     T *out) {
+                                                     T *out, const T *add) {
   extern __shared__ unsigned char thomas_smem[];
   T *w = reinterpret_cast<T *>(thomas_smem);
   for (int j = threadIdx.x; j < N; j += blockDim.x) w[j] = (T)w_d[j];
   __syncthreads();
   thomas_line<T>((long long)blockIdx.x * blockDim.x + threadIdx.x, N, p, axis, (T)scale_d, w, in,
-                 out);
+                 out, add);
 }
 
 // Batched: the blocks of job j cover its N^2 p (line, orbital) pairs.
@@ -126,23 +131,24 @@ ks_status batch_mass_inverse(Batch &B, int sE, int sG) {
 template ks_status batch_mass_inverse<double>(Batch &, int, int);
 template ks_status batch_mass_inverse<float>(Batch &, int, int);
 
-// G = s E elementwise (the inverse of the lumped mass h^3 I); E and G may alias.
+// G = s E elementwise (the inverse of the lumped mass h^3 I), plus add when
+// given; E and G may alias.
 template <typename T>
-__global__ void scale_kernel(long long len, T s, const T *E, T *G) {
+__global__ void scale_kernel(long long len, T s, const T *E, T *G, const T *add) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len;
        i += (long long)gridDim.x * blockDim.x)
-    G[i] = s * E[i];
+    G[i] = add ? s * E[i] + add[i] : s * E[i];
 }
 
 template <typename T>
-ks_status launch_mass_inverse(Problem &P, const T *E, T *G) {
+ks_status launch_mass_inverse(Problem &P, const T *E, T *G, const T *add) {
   if (P.mass == KS_MASS_LUMPED) {
     const long long len = (long long)P.n * P.p;
     long long nb = (len + 4LL * kThreads - 1) / (4LL * kThreads);
     if (nb > 64LL * P.sms) nb = 64LL * P.sms;
     const double h = P.h;
     ProfScope ps_(P.stream, KP_MASS_INV, (double)len, 2.0 * len * sizeof(T));
-    scale_kernel<T><<<(int)nb, kThreads, 0, P.stream>>>(len, (T)(1.0 / (h * h * h)), E, G);
+    scale_kernel<T><<<(int)nb, kThreads, 0, P.stream>>>(len, (T)(1.0 / (h * h * h)), E, G, add);
     KS_CUDA_TRY(cudaGetLastError());
     return KS_OK;
   }
@@ -152,23 +158,26 @@ ks_status launch_mass_inverse(Problem &P, const T *E, T *G) {
   const size_t smem = (size_t)P.N * sizeof(T);
   {
     ProfScope ps_(P.stream, KP_MASS_INV, 4.0 * P.n * P.p, 2.0 * P.n * P.p * sizeof(T));
-    thomas_kernel<T><<<nb, kThreads, smem, P.stream>>>(P.N, P.p, 0, s * s * s, P.thomas_w, E, G);
+    thomas_kernel<T><<<nb, kThreads, smem, P.stream>>>(P.N, P.p, 0, s * s * s, P.thomas_w, E, G,
+                                                       nullptr);
   }
   KS_CUDA_TRY(cudaGetLastError());
   {
     ProfScope ps_(P.stream, KP_MASS_INV, 4.0 * P.n * P.p, 2.0 * P.n * P.p * sizeof(T));
-    thomas_kernel<T><<<nb, kThreads, smem, P.stream>>>(P.N, P.p, 1, 1.0, P.thomas_w, G, G);
+    thomas_kernel<T><<<nb, kThreads, smem, P.stream>>>(P.N, P.p, 1, 1.0, P.thomas_w, G, G,
+                                                       nullptr);
   }
   KS_CUDA_TRY(cudaGetLastError());
   {
     ProfScope ps_(P.stream, KP_MASS_INV, 4.0 * P.n * P.p, 2.0 * P.n * P.p * sizeof(T));
-    thomas_kernel<T><<<nb, kThreads, smem, P.stream>>>(P.N, P.p, 2, 1.0, P.thomas_w, G, G);
+    thomas_kernel<T><<<nb, kThreads, smem, P.stream>>>(P.N, P.p, 2, 1.0, P.thomas_w, G, G, add);
   }
   KS_CUDA_TRY(cudaGetLastError());
   return KS_OK;
 }
 
-template ks_status launch_mass_inverse<double>(Problem &, const double *, double *);
-template ks_status launch_mass_inverse<float>(Problem &, const float *, float *);
+template ks_status launch_mass_inverse<double>(Problem &, const double *, double *,
+                                               const double *);
+template ks_status launch_mass_inverse<float>(Problem &, const float *, float *, const float *);
 
 }  // namespace ks

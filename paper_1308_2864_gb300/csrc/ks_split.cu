@@ -83,6 +83,12 @@ __global__ void small_gemm_kernel(int p, int ta, const double *__restrict__ A, i
   }
 }
 
+// out = A + s B (p x p); out may be A or B
+__global__ void add_pp_kernel(int p, const double *A, double s, const double *B, double *out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p * p; i += gridDim.x * blockDim.x)
+    out[i] = A[i] + s * B[i];
+}
+
 // out = R - (T + T^T) / tau: with it, I + tau^2 out = I - tau (T + T^T) + tau^2 R
 // is the exact Gram (X - tau D)^T M (X - tau D) when X^T M X = I, T = X^T M D
 // and R = D^T M D.
@@ -93,12 +99,6 @@ __global__ void qr_exact_gram_kernel(int p, const double *__restrict__ R,
     const int r = i / p, c = i % p;
     out[i] = R[i] - (T[i] + T[(size_t)c * p + r]) / tau;
   }
-}
-
-// out = A + s B (p x p); out may be A or B
-__global__ void add_pp_kernel(int p, const double *A, double s, const double *B, double *out) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p * p; i += gridDim.x * blockDim.x)
-    out[i] = A[i] + s * B[i];
 }
 
 // out = X + Y + Y^T (p x p)
@@ -170,6 +170,16 @@ ks_status launch_small_gemm(Problem &P, int ta, const double *A, int tb, const d
   return KS_OK;
 }
 
+ks_status launch_add_pp(Problem &P, const double *A, double s, const double *B, double *out) {
+  const int len = P.p * P.p;
+  {
+    ProfScope ps_(P.stream, KP_SMALL);
+    add_pp_kernel<<<(len + kThreads - 1) / kThreads, kThreads, 0, P.stream>>>(P.p, A, s, B, out);
+  }
+  KS_CUDA_TRY(cudaGetLastError());
+  return KS_OK;
+}
+
 ks_status launch_qr_exact_gram(Problem &P, const double *R, const double *T, double tau,
                                double *out) {
   const int len = P.p * P.p;
@@ -177,16 +187,6 @@ ks_status launch_qr_exact_gram(Problem &P, const double *R, const double *T, dou
     ProfScope ps_(P.stream, KP_SMALL);
     qr_exact_gram_kernel<<<(len + kThreads - 1) / kThreads, kThreads, 0, P.stream>>>(P.p, R, T,
                                                                                     tau, out);
-  }
-  KS_CUDA_TRY(cudaGetLastError());
-  return KS_OK;
-}
-
-ks_status launch_add_pp(Problem &P, const double *A, double s, const double *B, double *out) {
-  const int len = P.p * P.p;
-  {
-    ProfScope ps_(P.stream, KP_SMALL);
-    add_pp_kernel<<<(len + kThreads - 1) / kThreads, kThreads, 0, P.stream>>>(P.p, A, s, B, out);
   }
   KS_CUDA_TRY(cudaGetLastError());
   return KS_OK;

@@ -62,3 +62,28 @@ def test_reference_arm_prints_one_contract_line():
     assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
     assert line["config"]["workload"] == bench.WORKLOAD
+    # a step is one timed oracle iteration: steps x ms_per_step is the timed
+    # work, and the extrapolated solve is reported separately
+    cfg = line["config"]
+    assert line["ms_per_step"] == pytest.approx(1e3 * cfg["oracle_seconds_per_iteration"])
+    assert cfg["extrapolated_solve_seconds"] == pytest.approx(1.0 / line["value"])
+    st = cb["single_thread"]
+    assert st["seconds_per_iteration"] > 0 and st["value"] > 0
+
+
+def test_roofline_of_the_dominant_class():
+    peaks = {"sms": 152, "fp32_tflops": 78.0, "fp64_tflops": 1.1}
+    clocks = {"sm_mhz": 2000.0, "sm_max_mhz": 2070.0}
+    # an FP32 contraction class dominates: FMA bound against unit counts x clock
+    prof = {"combine": (50.0, 100, 2.0e12, 1.0e10), "hamiltonian": (20.0, 40, 1e9, 4.0e10)}
+    r = bench.roofline(prof, clocks, peaks)
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert r["peak"] == pytest.approx(152 * 128 * 2 * 2000e6 / 1e12)
+    assert r["achieved"] == pytest.approx(2.0e12 / 0.05 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert r["frac_of_probe"] == pytest.approx(r["achieved"] / 78.0)
+    # a stencil class dominates: HBM bound in GB/s
+    prof = {"combine": (5.0, 10, 2.0e11, 1.0e9), "hamiltonian": (20.0, 40, 1e9, 4.0e10)}
+    r = bench.roofline(prof, clocks, peaks)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert r["achieved"] == pytest.approx(4.0e10 / 0.02 / 1e9)
