@@ -3,24 +3,35 @@ minimisation (Alg. ConOptM, QR retraction) on the 64^3-grid, 32-atom,
 p = 64 synthetic system (cube 20 bohr, Z = 4 Gaussian pseudo-atoms on a
 jittered 4x4x2 lattice, Slater + PZ81) on one GB300.
 
-One step = one solve from the seeded initial block until ||D||_M <= 1e-6 or
-300 iterations (the iteration cap of the 24^3 protocol and of ks_opts), in
-the plain FP64 form (value), in the FP32-phase mixed form (config.mixed) and
-in FP64 with the Grams and updates on the tensor cores by exact digit
-splitting (config.fp64_split).
-Prints ONE JSON line on rank 0.
+The timed region is ONE complete solve from the seeded initial block to
+||D||_M <= 1e-6 in the mixed-precision form (the FP32 phase in increment
+form, then the FP64 polish that confirms the tolerance), cut into --steps
+segments of equal iteration count (the solve is resumed between segments,
+which reproduces an uninterrupted run bitwise; the last segment runs to
+convergence).  value = 1 / (that solve's time) in solves/s.  --warmup
+segments of a separate solve precede it.  Beside it: the iteration rate of
+the same workload in plain FP64, in FP64 with split tensor-core products and
+in the mixed form; complete time-to-solution comparisons (mixed against plain
+FP64 at equal final accuracy) on the 24^3 two-atom system and four systems
+of the batched-jobs recipe, with the error of the mixed result before its
+FP64 polish against the oracle's converged energy; a bounded mixed solve of
+the 128^3, p = 512 system with the tensor-core Gram and update rates and the
+energy error of its result; the FMA peaks measured in the same run; the
+oracle on the host cores.  Prints ONE JSON line on rank 0.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 --impl reference times the plain FP64 CPU oracle on the host cores on a
 bounded sample of the same workload: W untimed and K timed iterations of the
-same solve (one iteration per step), scaled to a 300-iteration solve.  Under torchrun each rank solves its own
-replica (no data-path collective).
+same solve (one oracle iteration per step), its solve time extrapolated from
+the measured time per iteration and the FP64 iteration count of this solve.
+Under torchrun each rank solves its own replica (no data-path collective).
 """
 from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -37,15 +48,17 @@ import numpy as np
 METRIC = "time-to-||grad||<=1e-6 & solves/s, p50/p99 latency; mixed vs plain FP64 GPU"
 WORKLOAD = "c2: cube 20 bohr, 64^3 Q1 grid, 32 atoms Z=4 jittered 4x4x2 lattice, p=64, Slater+PZ81, QR"
 GTOL = 1e-6
-MAXIT = 300
+# Iterations of the c2 solve to ||D||_M <= 1e-6 from the seeded block, as
+# measured on GB300 (profiles/c2_time_to_solution.md); the solve is
+# deterministic (fixed reduction orders), so these set the segment length of
+# the timed solve and the oracle's extrapolated solve.
+C2_ITERS_MIXED = 98539
+C2_ITERS_FP64 = 99874
 # jobs of the batched-jobs recipe (seed 1003) that reach ||D||_M <= 1e-6 in
-# a few thousand iterations (1-9 s each)
+# a few thousand iterations
 C4_TTS_JOBS = (1, 2, 4, 5)
-# DRAM bytes per launch of the FP64 update kernel: dram__bytes_read.sum +
-# dram__bytes_write.sum of one ncu capture of its projection and retraction
-# launches on this workload (mean of the two).  Must be re-measured, or set
-# to None, whenever that kernel changes.
-COMBINE_FP64_TRAFFIC_BYTES = 3.695e8
+MAXIT = 400000
+GOLDEN_C1 = os.path.join(ROOT, "tests", "golden", "c1_converged.json")
 
 
 def dist_env():
@@ -108,12 +121,13 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_sample(iters: int = 3, warmup: int = 0):
+# ---------------------------------------------------------------- oracle
+
+def oracle_sample_inline(iters: int, warmup: int) -> dict:
     """Time the oracle's Alg. ConOptM on the workload, as it stands: its
     one-time set-up (orthonormalisation and the first evaluation), then
     `warmup` untimed and `iters` timed iterations of one solve, each timed
-    from the previous iteration's end.  Returns (mean seconds per timed
-    iteration, set-up seconds, threads used)."""
+    from the previous iteration's end."""
     import ks_inputs as ki
     from oracle import energy as oe
     from oracle import stiefel as ost
@@ -127,37 +141,62 @@ def oracle_sample(iters: int = 3, warmup: int = 0):
     t0 = time.perf_counter()
     ost.minimize(model, s.x0(), ost.Options(retraction="qr", gtol=GTOL, maxit=warmup + iters),
                  callback=lambda k, pt: ends.append(time.perf_counter()))
-    # iteration k ends at ends[k]; the first starts once the set-up is done
     spans = np.diff([t0 + t_setup] + ends)
-    per_iter = float(np.mean(spans[warmup:warmup + iters]))
-    threads = int(os.environ.get("OMP_NUM_THREADS", "0")) or os.cpu_count()
-    return per_iter, t_setup, threads
+    return {"per_iter": float(np.mean(spans[warmup:warmup + iters])), "setup": t_setup,
+            "iters": iters, "warmup": warmup}
+
+
+def oracle_sample(iters: int, warmup: int, threads: int) -> dict:
+    """oracle_sample_inline in a child process whose BLAS and OpenMP pools
+    have exactly `threads` threads (they are fixed when numpy loads)."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = str(threads)
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample",
+                        str(iters), str(warmup)], capture_output=True, text=True, env=env,
+                       cwd=ROOT, timeout=3600)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    out["threads"] = threads
+    return out
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    iters = MAXIT
     steps = max(args.steps, 1)
-    per_iter, t_setup, threads = oracle_sample(steps, args.warmup)
-    t_solve = t_setup + per_iter * iters
+    cores = os.cpu_count() or 1
+    allc = oracle_sample(steps, args.warmup, cores)
+    one = oracle_sample(1, 0, 1)
+    t_solve = allc["setup"] + allc["per_iter"] * C2_ITERS_FP64
     value = 1.0 / t_solve
+    t_one = one["setup"] + one["per_iter"] * C2_ITERS_FP64
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": t_solve * 1e3, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": allc["per_iter"] * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "iterations_assumed": iters,
-                   "oracle_seconds_per_iteration": per_iter, "oracle_setup_seconds": t_setup},
-        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": threads, "kind": "oracle",
+        "config": {"workload": WORKLOAD, "step": "one oracle iteration of the c2 solve",
+                   "oracle_seconds_per_iteration": allc["per_iter"],
+                   "oracle_setup_seconds": allc["setup"],
+                   "iterations_to_solution": C2_ITERS_FP64,
+                   "extrapolated_solve_seconds": t_solve},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
                          "sample": f"{args.warmup} untimed + {steps} timed oracle iterations of "
-                                   f"the c2 solve ({per_iter:.2f} s each) + set-up "
-                                   f"({t_setup:.1f} s), scaled to a {iters}-iteration solve"},
+                                   f"the c2 solve ({allc['per_iter']:.2f} s each, {cores} "
+                                   f"threads) + set-up ({allc['setup']:.1f} s), extrapolated to "
+                                   f"the {C2_ITERS_FP64}-iteration FP64 solve",
+                         "single_thread": {"seconds_per_iteration": one["per_iter"],
+                                           "setup_seconds": one["setup"],
+                                           "value": 1.0 / t_one}},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
+
+# ---------------------------------------------------------------- GPU arm
 
 def class_shares(prof) -> dict:
     """Share of each kernel class in the live per-class CUDA-event timings."""
@@ -165,41 +204,203 @@ def class_shares(prof) -> dict:
     return {k: round(v[0] / total, 4) for k, v in prof.items() if v[1] > 0}
 
 
-def timed_solves(P, X, X0, opts, steps, warmup, stream, barrier, clk=None):
-    """W untimed and K timed solves; returns (ms over the K solves, results,
-    per-class profile, kernel launches in the timed region)."""
+def fma_peaks(stream) -> dict:
+    """FP64 and FP32 FMA rates of ks_probe_fma on all SMs, timed with CUDA
+    events on `stream` (median of 5 launches after 2 untimed), in TFLOP/s."""
     import torch
     import paper_1308_2864_gb300 as ks
+    sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    blocks = 8 * sm
+    sink = torch.zeros(blocks, dtype=torch.float64, device="cuda")
+    out = {"sms": sm}
+    for name, fp64, iters in (("fp64", True, 12000), ("fp32", False, 400000)):
+        with torch.cuda.stream(stream):
+            for _ in range(2):
+                ks.probe_fma(fp64, blocks, iters, sink, stream)
+            rates = []
+            for _ in range(5):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fl = ks.probe_fma(fp64, blocks, iters, sink, stream)
+                e1.record(stream)
+                e1.synchronize()
+                rates.append(fl / (e0.elapsed_time(e1) / 1e3) / 1e12)
+        out[name + "_tflops"] = statistics.median(rates)
+    return out
 
-    def solve():
-        X.copy_(X0)
-        return P.minimize(X, **opts)
 
+# Unit counts of the GB300 SM (per clock): FP32 FMA lanes and FP64 FMA units.
+FP32_FMA_PER_CLK_SM = 128
+FP64_FMA_PER_CLK_SM = 2
+ALU_CLASSES = ("gram", "combine", "small_factor")
+
+
+def roofline(prof, clocks, peaks) -> dict:
+    """Roofline object of the dominant kernel class: FP32 FMA bound for the
+    n p^2 contractions (peak = SMs x 128 FMA/clk x 2 flop x the SM clock
+    measured during the timed region; the probe's measured rate beside it),
+    HBM bound otherwise (peak = MEASURED_PEAKS.json hbm_gbs)."""
+    name, (dms, dcnt, dfl, dby) = max(prof.items(), key=lambda kv: kv[1][0])
+    mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
+    if name in ALU_CLASSES:
+        peak = peaks["sms"] * FP32_FMA_PER_CLK_SM * 2 * mhz * 1e6 / 1e12
+        achieved = dfl / (dms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak,
+                "peak_source": f"{peaks['sms']} SMs x {FP32_FMA_PER_CLK_SM} FP32 FMA/clk x 2 flop "
+                               f"x {mhz:.0f} MHz (median SM clock of the timed region)",
+                "probe_tflops": peaks["fp32_tflops"],
+                "frac_of_probe": achieved / peaks["fp32_tflops"]}
+    else:
+        mp_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        mp = json.load(open(mp_path)) if os.path.exists(mp_path) else {}
+        hbm = mp.get("hbm_gbs", 6800.0)
+        achieved = dby / (dms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm,
+                "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)" if mp else
+                               "of fallback (6.8 TB/s)"}
+    roof.update({"kernel": f"{name} (class of the timed solve)", "launches": dcnt,
+                 "ms": dms, "traffic": None})
+    return roof
+
+
+def segmented_solve(P, X, X0, opts, steps, seg, stream, clk=None, profile=False):
+    """One solve from X0, in `steps` segments of `seg` iterations (the last
+    one to convergence), each segment a resumed ks_minimize.  Returns
+    (ms over the whole solve, final result with iters, backtracks and CG
+    iterations summed over the segments, per-step ms, profile, launches)."""
+    import torch
+    import paper_1308_2864_gb300 as ks
     with torch.cuda.stream(stream):
-        for _ in range(warmup):
-            solve()
+        X.copy_(X0)
         stream.synchronize()
-        barrier()
-        torch.cuda.synchronize()
         launches0 = ks.kernel_launches()
-        ks.profile_start()
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        results = []
+        if profile:
+            ks.profile_start()
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
         if clk:
             clk.__enter__()
-        ev0.record(stream)
-        for _ in range(steps):
-            results.append(solve())
-        ev1.record(stream)
-        ev1.synchronize()
+        evs[0].record(stream)
+        r = None
+        tot = {"iters": 0, "backtracks": 0, "cg_iters_total": 0}
+        for i in range(steps):
+            last = i == steps - 1
+            mx = MAXIT if last else (i + 1) * seg
+            r = P.minimize(X, **opts, maxit=mx, resume=0 if i == 0 else 1)
+            evs[i + 1].record(stream)
+            for k in tot:
+                tot[k] += r[k]
+        evs[-1].synchronize()
         if clk:
             clk.__exit__(None, None, None)
-        prof = ks.profile_stop()
+        prof = ks.profile_stop() if profile else None
         launches = ks.kernel_launches() - launches0
-        torch.cuda.synchronize()
-        barrier()
-    return ev0.elapsed_time(ev1), results, prof, launches
+    per = [evs[i].elapsed_time(evs[i + 1]) for i in range(steps)]
+    r = {**r, **tot}
+    return evs[0].elapsed_time(evs[-1]), r, per, prof, launches
+
+
+def iteration_rate(P, X, X0, opts, iters, stream):
+    """ms per iteration over iterations 20..20+iters of the solve from X0."""
+    import torch
+    with torch.cuda.stream(stream):
+        X.copy_(X0)
+        P.minimize(X, **opts, maxit=20)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = P.minimize(X, **opts, maxit=20 + iters, resume=1)
+        e1.record(stream)
+        e1.synchronize()
+    return e0.elapsed_time(e1) / max(iters, 1), r
+
+
+def time_to_solution(s, opts, stream, emulation=0):
+    """Complete solve of system s from its seeded block (after a 3-iteration
+    warm-up): seconds from CUDA events, and the result."""
+    import torch
+    import paper_1308_2864_gb300 as ks
+    with torch.cuda.stream(stream):
+        P = ks.Problem.from_system(s, stream=stream)
+        P.set_fp64_emulation(emulation)
+        X0 = torch.from_numpy(np.ascontiguousarray(s.x0())).cuda()
+        X = X0.clone()
+        P.minimize(X, **{**opts, "maxit": 3})
+        X.copy_(X0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = P.minimize(X, **opts)
+        e1.record(stream)
+        e1.synchronize()
+        P.close()
+    return e0.elapsed_time(e1) / 1e3, r
+
+
+def c3_leg(stream, iters: int = 33):
+    """Bounded mixed solve of the 128^3, p = 512 system: per-iteration time,
+    tensor-core Gram and update rates (live class timings), and the energy
+    error of the returned X against its FP64 evaluation, whose density terms
+    the oracle computes from the returned block."""
+    import torch
+    import ks_inputs as ki
+    import paper_1308_2864_gb300 as ks
+    from oracle import energy as oe
+    from oracle import fe as ofe
+    free, _ = torch.cuda.mem_get_info()
+    if free < 140 * 2 ** 30:
+        return {"skipped": f"needs about 130 GB of free device memory, {free / 2**30:.0f} GB free"}
+    s = ki.config_c3()
+    with torch.cuda.stream(stream):
+        P = ks.Problem.from_system(s, stream=stream)
+        P.set_fp64_emulation(1)
+        X = torch.from_numpy(np.ascontiguousarray(s.x0())).cuda()
+        opts = dict(retraction="qr", gtol=GTOL, precision="mixed", stall_iters=0)
+        # the start (FP64 orthonormalisation and base) outside the timing
+        r0 = P.minimize(X, **opts, maxit=3)
+        stream.synchronize()
+        ks.profile_start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = P.minimize(X, **opts, maxit=3 + iters, resume=1)
+        e1.record(stream)
+        e1.synchronize()
+        prof = ks.profile_stop()
+        E64, _, _, g64 = P.energy_grad(X, want_ex=False, want_d=True)
+        parts = P.energy_parts()
+        Xh = X.cpu().numpy()
+        P.close()
+        del X
+    ms = e0.elapsed_time(e1)
+    model = oe.Model.from_system(s)
+    h3 = model.h ** 3
+    rho = oe.density(Xh, model.occ)
+    del Xh
+    vH = ofe.poisson_exact(4.0 * math.pi * h3 * rho, model.N, model.h)
+    eps, _ = oe.lda(rho, model.xc)
+    E_or = parts[0] + h3 * float(model.vext() @ rho) + 0.5 * h3 * float(vH @ rho) \
+        + h3 * float(rho @ eps) + model.eii()
+    peak_tf32 = 0.5 * json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"] \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 0.5 * 1900.0
+
+    def rate(cls):
+        t, n, fl, _ = prof[cls]
+        return {"ms": t, "launches": n, "tflops_useful": fl / (t / 1e3) / 1e12 if t > 0 else None,
+                "frac_of_tf32_peak": (fl / (t / 1e3) / 1e12) / peak_tf32 if t > 0 else None}
+    return {"system": "c3: 128^3 grid, 256 atoms, p=512, QR, mixed (FP32 increment form, "
+                      "3xTF32 tensor-core Grams and updates), FP64 emulation for the base",
+            "iterations": r["iters"], "start_seconds": r0["seconds"],
+            "ms_per_iteration": ms / max(r["iters"], 1),
+            "gradnorm": r["gradnorm"], "energy_mixed": r["E"], "energy_fp64_gpu": E64,
+            "energy_fp64_density_terms_by_oracle": E_or,
+            "mixed_minus_fp64_Ha": r["E"] - E64, "mixed_minus_oracle_Ha": r["E"] - E_or,
+            "gram": rate("gram"), "combine": rate("combine"),
+            "tf32_peak_tflops": peak_tf32, "tf32_peak_note": "0.5 x the measured BF16 burst "
+                                                           "(the nominal TF32/BF16 ratio)",
+            "kernel_shares": class_shares(prof)}
 
 
 def run_gpu(args):
@@ -225,129 +426,66 @@ def run_gpu(args):
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    s = ki.config_c2()
     stream = torch.cuda.Stream()
+    peaks = fma_peaks(stream)
+
+    s = ki.config_c2()
     with torch.cuda.stream(stream):
         P = ks.Problem.from_system(s, stream=stream)
+        P.set_fp64_emulation(1)
         X0 = torch.from_numpy(np.ascontiguousarray(s.x0())).cuda()
         X = torch.empty_like(X0)
-    fp64 = dict(retraction="qr", gtol=GTOL, maxit=MAXIT, precision="fp64")
-    mixed = dict(retraction="qr", gtol=GTOL, maxit=MAXIT, precision="mixed")
-
-    clk = ClockSampler(local)
-    ms, results, prof, launches = timed_solves(P, X, X0, fp64, args.steps, args.warmup, stream,
-                                               barrier, clk)
-    ms_max = max_over_ranks(ms)
-    value = world * args.steps / (ms_max / 1e3)
-    ms_m, res_m, prof_m, _ = timed_solves(P, X, X0, mixed, args.steps, args.warmup, stream, barrier)
-    ms_m = max_over_ranks(ms_m)
-    # the same FP64 solve with its Grams and updates on the tensor cores by
-    # exact digit splitting (ks_set_fp64_emulation 1)
-    P.set_fp64_emulation(1)
-    ms_s, res_s, prof_s, _ = timed_solves(P, X, X0, fp64, args.steps, args.warmup, stream, barrier)
-    ms_s = max_over_ranks(ms_s)
-    P.set_fp64_emulation(0)
-
-    # time to ||D||_M <= 1e-6 with and without the split products on a
-    # 48-orbital system that converges (14^3 grid, 24 atoms)
-    sp = ki.small_system(N=14, L=8.0, natoms=24, p=48, Z=4.0, seed=5)
-    sp.rc = 1.0
-    split_tts = {}
-    for mode in (0, 1):
+    mixed = dict(retraction="qr", gtol=GTOL, precision="mixed")
+    steps = max(args.steps, 1)
+    seg = max(1, int(0.9 * C2_ITERS_MIXED) // steps)
+    # warm-up: the first W segments of a separate solve, with per-class CUDA
+    # events on every launch (the live kernel shares and the roofline); the
+    # timed solve runs without them, since two events per launch slow a
+    # launch-bound iteration down by several per cent
+    prof = None
+    if args.warmup > 0:
         with torch.cuda.stream(stream):
-            Ps = ks.Problem.from_system(sp, stream=stream)
-            Ps.set_fp64_emulation(mode)
-            Xs = torch.from_numpy(np.ascontiguousarray(sp.x0())).cuda()
+            X.copy_(X0)
             stream.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            rs = Ps.minimize(Xs, gtol=GTOL, maxit=20000)
-            e1.record(stream)
-            e1.synchronize()
-        split_tts["split" if mode else "fp64"] = {
-            "seconds": e0.elapsed_time(e1) / 1e3, "iters": rs["iters"], "energy": rs["E"],
-            "converged": rs["status"] == 0}
-        Ps.close()
-    split_tts["energy_difference_Ha"] = split_tts["split"]["energy"] - split_tts["fp64"]["energy"]
-    split_tts["system"] = "14^3 grid, 24 atoms (Z=4, rc=1), p=48, QR, to ||D||_M <= 1e-6"
+            ks.profile_start()
+            for i in range(args.warmup):
+                P.minimize(X, **mixed, maxit=(i + 1) * seg, resume=0 if i == 0 else 1)
+            stream.synchronize()
+            prof = ks.profile_stop()
+    barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    ms, r0, per_step, prof_t, launches = segmented_solve(P, X, X0, mixed, steps, seg, stream, clk)
+    if prof is None:
+        prof = prof_t
+    torch.cuda.synchronize()
+    barrier()
+    ms_max = max_over_ranks(ms)
+    value = world / (ms_max / 1e3)
 
-    # time to ||D||_M <= 1e-6 on the 24^3 two-atom system (it converges in
-    # ~1300 iterations): plain FP64 against the FP32 phase + FP64 polish
-    c1 = ki.config_c1()
-    with torch.cuda.stream(stream):
-        P1 = ks.Problem.from_system(c1, stream=stream)
-        X1 = torch.from_numpy(np.ascontiguousarray(c1.x0())).cuda()
-        Y1 = torch.empty_like(X1)
-    c1_out = {}
-    for prec in ("fp64", "mixed"):
-        o = dict(retraction="cayley", gtol=GTOL, maxit=20000, precision=prec)
-        with torch.cuda.stream(stream):
-            Y1.copy_(X1)
-            P1.minimize(Y1, **o)                      # warm-up
-            Y1.copy_(X1)
-            ev0 = torch.cuda.Event(enable_timing=True)
-            ev1 = torch.cuda.Event(enable_timing=True)
-            ev0.record(stream)
-            r1 = P1.minimize(Y1, **o)
-            ev1.record(stream)
-            ev1.synchronize()
-        sec = ev0.elapsed_time(ev1) / 1e3
-        c1_out[prec] = {"seconds": sec, "iters": r1["iters"],
-                        "us_per_iteration": 1e6 * sec / max(r1["iters"], 1),
-                        "cg_iters_total": r1["cg_iters_total"], "backtracks": r1["backtracks"],
-                        "fp32_phase_iters": r1["mixed_iters"], "gradnorm": r1["gradnorm"],
-                        "energy": r1["E"], "converged": r1["status"] == 0}
-    c1_out["energy_difference_Ha"] = c1_out["mixed"]["energy"] - c1_out["fp64"]["energy"]
-    P1.close()
-
-    # time to ||D||_M <= 1e-6 on converging systems of the batched-jobs
-    # recipe (grids 24^3..38^3, p = 26..32): plain FP64 against the mixed form
-    c4_out = {"jobs": [], "fp64_s": 0.0, "mixed_s": 0.0}
-    c4_jobs = ki.config_c4_jobs(njobs=8)
-    for j in C4_TTS_JOBS:
-        sj = c4_jobs[j]
-        with torch.cuda.stream(stream):
-            Pj = ks.Problem.from_system(sj, stream=stream)
-            Xj0 = torch.from_numpy(np.ascontiguousarray(sj.x0())).cuda()
-            Yj = torch.empty_like(Xj0)
-        row = {"job": j, "N": sj.N, "p": sj.p}
-        for prec in ("fp64", "mixed"):
-            o = dict(retraction="qr", gtol=GTOL, maxit=20000, precision=prec)
-            with torch.cuda.stream(stream):
-                Yj.copy_(Xj0)
-                Pj.minimize(Yj, **{**o, "maxit": 3})         # warm-up
-                Yj.copy_(Xj0)
-                ev0 = torch.cuda.Event(enable_timing=True)
-                ev1 = torch.cuda.Event(enable_timing=True)
-                ev0.record(stream)
-                rj = Pj.minimize(Yj, **o)
-                ev1.record(stream)
-                ev1.synchronize()
-            secs = ev0.elapsed_time(ev1) / 1e3
-            row[prec] = {"seconds": secs, "iters": rj["iters"], "energy": rj["E"],
-                         "converged": rj["status"] == 0, "fp32_phase_iters": rj["mixed_iters"]}
-            c4_out[prec + "_s"] += secs
-        row["energy_difference_Ha"] = row["mixed"]["energy"] - row["fp64"]["energy"]
-        c4_out["jobs"].append(row)
-        Pj.close()
-    c4_out["speedup"] = c4_out["fp64_s"] / max(c4_out["mixed_s"], 1e-12)
+    # iteration rates of the three forms on the same workload
+    rates = {}
+    for name, opts, emul in (("fp64", dict(retraction="qr", precision="fp64"), 0),
+                             ("fp64_split", dict(retraction="qr", precision="fp64"), 1),
+                             ("mixed", dict(retraction="qr", precision="mixed", stall_iters=0), 1)):
+        P.set_fp64_emulation(emul)
+        t, rr = iteration_rate(P, X, X0, {**opts, "gtol": 1e-12}, 30, stream)
+        rates[name] = {"ms_per_iteration": t}
+    P.set_fp64_emulation(1)
 
     # end to end through the host entry point: X0 from pinned host memory in,
-    # the final block back out, every step
+    # the final block back out, one complete solve
     x0_np = s.x0()
     Xh = torch.from_numpy(np.ascontiguousarray(x0_np)).pin_memory()
     Xh_np = Xh.numpy()
-    e2e_steps = max(1, min(args.steps, 3))
     torch.cuda.synchronize()
     barrier()
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        np.copyto(Xh_np, x0_np)
-        P.minimize_host(Xh_np, **fp64)
+    re = P.minimize_host(Xh_np, **mixed, maxit=MAXIT)
     torch.cuda.synchronize()
-    e2e_value = world * e2e_steps / max_over_ranks(time.perf_counter() - t0)
+    e2e_value = world / max_over_ranks(time.perf_counter() - t0)
     nbytes = s.n * s.p * 8
+    P.close()
 
     if rank != 0:
         if world > 1:
@@ -355,68 +493,89 @@ def run_gpu(args):
             dist.destroy_process_group()
         return
 
-    # roofline of the dominant kernel class from the live CUDA-event timings
-    # and the library's algorithmic work counts
-    total_ms = sum(v[0] for v in prof.values())
-    name, (dms, dcnt, dfl, dby) = max(prof.items(), key=lambda kv: kv[1][0])
-    shares = {k: round(v[0] / total_ms, 4) for k, v in prof.items() if v[1] > 0}
-    fp64_peak = 152 * 4 * 2.07e9 / 1e12       # TFLOP/s: 2 DFMA/clk/SM at 2070 MHz
-    achieved = dfl / (dms / 1e3) / 1e12
-    roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-            "frac": achieved / fp64_peak,
-            "traffic": COMBINE_FP64_TRAFFIC_BYTES if name == "combine" else None,
-            "kernel": f"{name} (FP64)", "launches": dcnt,
-            "peak_note": "FP64 FMA peak derived from 152 SMs x 4 flop/clk x 2.07 GHz "
-                         "(probe measured 1.20 TFLOP/s at 1.99 GHz)"}
-    r0 = results[-1]
-    rm = res_m[-1]
-    per_iter, t_setup, threads = oracle_sample(3)
-    cpu_value = 1.0 / (t_setup + per_iter * max(r0["iters"], 1))
-    per_solve = [r["seconds"] for r in results]
-    mixed_kernel = class_shares(prof_m)
+    gold = json.load(open(GOLDEN_C1))
+    # 24^3 two-atom system: plain FP64 against the mixed form, both to 1e-6
+    c1 = ki.config_c1()
+    c1_out = {}
+    for prec in ("fp64", "mixed"):
+        sec, rr = time_to_solution(c1, dict(retraction="cayley", gtol=GTOL, maxit=20000,
+                                            precision=prec), stream)
+        c1_out[prec] = {"seconds": sec, "iters": rr["iters"], "backtracks": rr["backtracks"],
+                        "fp32_phase_iters": rr["mixed_iters"], "gradnorm": rr["gradnorm"],
+                        "energy_minus_oracle_Ha": rr["E"] - gold["E"],
+                        "converged": rr["status"] == 0}
+        if prec == "mixed":
+            c1_out[prec]["before_polish_minus_oracle_Ha"] = rr["mixed_E"] - gold["E"]
+            c1_out[prec]["before_polish_gradnorm"] = rr["mixed_gradnorm"]
+    c1_out["speedup_mixed_over_fp64"] = c1_out["fp64"]["seconds"] / c1_out["mixed"]["seconds"]
+
+    # converging systems of the batched-jobs recipe: plain FP64 against mixed
+    c4_out = {"jobs": [], "fp64_s": 0.0, "mixed_s": 0.0}
+    c4_jobs = ki.config_c4_jobs(njobs=8)
+    for j in C4_TTS_JOBS:
+        sj = c4_jobs[j]
+        row = {"job": j, "N": sj.N, "p": sj.p}
+        for prec in ("fp64", "mixed"):
+            sec, rr = time_to_solution(sj, dict(retraction="qr", gtol=GTOL, maxit=40000,
+                                                precision=prec), stream)
+            row[prec] = {"seconds": sec, "iters": rr["iters"], "energy": rr["E"],
+                         "converged": rr["status"] == 0, "fp32_phase_iters": rr["mixed_iters"]}
+            c4_out[prec + "_s"] += sec
+        row["energy_difference_Ha"] = row["mixed"]["energy"] - row["fp64"]["energy"]
+        c4_out["jobs"].append(row)
+    c4_out["speedup"] = c4_out["fp64_s"] / max(c4_out["mixed_s"], 1e-12)
+
+    try:
+        c3 = c3_leg(stream)
+    except Exception as e:  # reported in the line rather than losing the run
+        c3 = {"error": f"{type(e).__name__}: {e}"[:300]}
+
+    # roofline of the dominant kernel class of the timed solve, from the live
+    # per-class CUDA-event timings and the library's algorithmic work counts
+    clocks = clk.summary()
+    roof = roofline(prof, clocks, peaks)
+    allc = oracle_sample(3, 0, os.cpu_count() or 1)
+    one = oracle_sample(1, 0, 1)
+    cpu_value = 1.0 / (allc["setup"] + allc["per_iter"] * C2_ITERS_FP64)
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "precision": "fp64", "retraction": "qr", "gtol": GTOL,
-                   "maxit": MAXIT, "iters_per_solve": r0["iters"],
+        "config": {"workload": WORKLOAD, "form": "mixed: FP32 phase in increment form "
+                   "(X = X_b + delta, FP64 base refreshed every 32 iterations), then the FP64 "
+                   "polish (split tensor-core products)", "retraction": "qr", "gtol": GTOL,
+                   "step": f"{seg} iterations of one solve (the last step to convergence)",
+                   "backtracks": r0["backtracks"], "cg_iters": r0["cg_iters_total"],
+                   "steps_with_work": sum(1 for t in per_step if t > 50.0),
+                   "iters_per_solve": r0["iters"], "fp32_phase_iters": r0["mixed_iters"],
                    "converged": r0["status"] == 0, "final_gradnorm": r0["gradnorm"],
-                   "final_energy": r0["E"], "ms_per_iteration": ms_max / args.steps / max(r0["iters"], 1),
-                   "cg_iters_per_solve": r0["cg_iters_total"],
-                   "p50_s": statistics.median(per_solve),
-                   "p99_s": float(np.percentile(per_solve, 99)),
+                   "final_energy": r0["E"], "step_ms": per_step,
+                   "p50_step_ms": statistics.median(per_step),
+                   "p99_step_ms": float(np.percentile(per_step, 99)),
                    "l2": "working set ~1.7 GB > 129 MB L2 (no flush needed)",
                    "parallelism": f"replicas x{world}",
-                   "mixed": {"solves_per_s": world * args.steps / (ms_m / 1e3),
-                             "ms_per_step": ms_m / args.steps, "iters_per_solve": rm["iters"],
-                             "fp32_phase_iters": rm["mixed_iters"],
-                             "final_gradnorm": rm["gradnorm"], "final_energy": rm["E"],
-                             "energy_minus_fp64_Ha": rm["E"] - r0["E"],
-                             "kernel_shares": mixed_kernel},
-                   "fp64_split": {"solves_per_s": world * args.steps / (ms_s / 1e3),
-                                  "ms_per_step": ms_s / args.steps,
-                                  "ms_per_iteration": ms_s / args.steps / max(res_s[0]["iters"], 1),
-                                  "iters_per_solve": res_s[0]["iters"],
-                                  "final_gradnorm": res_s[0]["gradnorm"],
-                                  "final_energy": res_s[0]["E"],
-                                  "energy_minus_fp64_Ha": res_s[0]["E"] - r0["E"],
-                                  "kernel_shares": class_shares(prof_s),
-                                  "note": "Grams and updates as BF16 tcgen05 MMAs of exact digit "
-                                          "splits (48/56 bits per operand), folded in int64 "
-                                          "before one FP64 rounding",
-                                  "time_to_solution": split_tts},
+                   "iteration_ms": rates,
                    "c1_time_to_solution": c1_out,
-                   "c4_time_to_solution": c4_out},
+                   "c4_time_to_solution": c4_out,
+                   "c3_precision_form": c3,
+                   "fma_peaks_measured": peaks},
         "roofline": roof,
-        "kernel_shares": shares,
-        "cpu_baseline": {"value": cpu_value, "unit": "solves/s", "cores": threads, "kind": "oracle",
-                         "sample": f"3 oracle iterations of the same solve ({per_iter:.2f} s each) "
-                                   f"+ set-up {t_setup:.2f} s, scaled to {r0['iters']} iterations"},
+        "kernel_shares": class_shares(prof),
+        "kernel_shares_note": "live per-class CUDA events over the warm-up segments",
+        "cpu_baseline": {"value": cpu_value, "unit": "solves/s", "cores": allc["threads"],
+                         "kind": "oracle",
+                         "sample": f"3 oracle iterations of the same solve "
+                                   f"({allc['per_iter']:.2f} s each) + set-up "
+                                   f"{allc['setup']:.2f} s, extrapolated to the "
+                                   f"{C2_ITERS_FP64}-iteration FP64 solve",
+                         "single_thread": {"seconds_per_iteration": one["per_iter"],
+                                           "value": 1.0 / (one["setup"] + one["per_iter"]
+                                                           * C2_ITERS_FP64)}},
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": nbytes,
-                "d2h_bytes_per_step": nbytes},
+                "d2h_bytes_per_step": nbytes, "iters": re["iters"]},
         "gpu_launches": int(launches),
-        "clocks": clk.summary(),
+        "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -425,9 +584,12 @@ def run_gpu(args):
 
 
 def main():
+    if len(sys.argv) >= 2 and sys.argv[1] == "--oracle-sample":
+        print(json.dumps(oracle_sample_inline(int(sys.argv[2]), int(sys.argv[3]))), flush=True)
+        return
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     args = ap.parse_args()
