@@ -263,7 +263,8 @@ ks_status ks_minimize_refine(const ks_problem_desc *desc, int levels, const doub
                              ks_result *level_results);
 
 /* Checkpoint of the minimiser (line-search scalars, current and previous
- * iterates with their M products, gradients and the Hartree potential) after
+ * iterates with their M products, gradients, the Hartree potential and the
+ * Hartree solver's last residual and right-hand side) after
  * the last iteration of the last ks_minimize call.  ks_state_bytes returns
  * the size needed (0 when there is nothing to save); ks_state_save writes it
  * to a HOST buffer; ks_state_load restores it into a problem with the same N

@@ -3,13 +3,18 @@
   python -m paper_1308_2864_gb300.cli --config c2 --maxit 5 [--precision fp64|mixed]
                                       [--retraction qr|cayley] [--gtol 1e-6] [--verbose 0]
                                       [--N 40] [--p 512] [--fp64-emulation 0|1|2]
+                                      [--profile 40]
 
 --N / --p shrink or change a configuration's grid and orbital count (same
 cube, atoms and functional), e.g. to profile the p = 512 kernels of c3 on a
 grid that fits a profiler's replay.
 
 Prints one JSON line with the result (energy, ||D||_M, iterations, time).
-Useful to profile a few iterations of the real workload.
+Useful to profile a few iterations of the real workload.  --profile W runs W
+iterations first, then resumes for --maxit more with the library's kernel
+classes timed by CUDA events on the problem's stream, and adds to the line
+the milliseconds per iteration and, per class, the launches and microseconds
+per iteration.
 """
 from __future__ import annotations
 
@@ -42,6 +47,8 @@ def main(argv=None) -> int:
     ap.add_argument("--p", type=int, default=0, help="override the number of orbitals")
     ap.add_argument("--fp64-emulation", type=int, default=0, choices=[0, 1, 2],
                     help="FP64 Grams and updates on the tensor cores by digit splitting")
+    ap.add_argument("--profile", type=int, default=0, metavar="W",
+                    help="time the kernel classes over --maxit iterations after W untimed ones")
     a = ap.parse_args(argv)
 
     s = ki.CONFIGS[a.config]()
@@ -52,9 +59,29 @@ def main(argv=None) -> int:
     P = ks.Problem.from_system(s)
     P.set_fp64_emulation(a.fp64_emulation)
     X = torch.from_numpy(np.ascontiguousarray(s.x0())).cuda()
-    t0 = time.perf_counter()
-    r = P.minimize(X, retraction=a.retraction or s.retraction, maxit=a.maxit, gtol=a.gtol,
-                   precision=a.precision, verbose=a.verbose)
+    kw = dict(retraction=a.retraction or s.retraction, gtol=a.gtol, precision=a.precision,
+              verbose=a.verbose)
+    prof = None
+    if a.profile > 0:
+        # warm-up, then the timed iterations resume the saved loop state
+        # (the stall test off, so that both runs do the iterations asked for)
+        P.minimize(X, maxit=a.profile, stall_iters=0, **kw)
+        torch.cuda.synchronize()
+        ks.profile_start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(P.stream)
+        t0 = time.perf_counter()
+        r = P.minimize(X, maxit=a.profile + a.maxit, stall_iters=0, resume=1, **kw)
+        e1.record(P.stream)
+        e1.synchronize()
+        prof = ks.profile_stop()
+        it = max(1, r["iters"])
+        r["profile"] = {"iters": r["iters"], "ms_per_iter": e0.elapsed_time(e1) / it,
+                        "classes": {k: {"launches_per_iter": n / it, "us_per_iter": 1e3 * ms / it}
+                                    for k, (ms, n, _, _) in prof.items() if n}}
+    else:
+        t0 = time.perf_counter()
+        r = P.minimize(X, maxit=a.maxit, **kw)
     torch.cuda.synchronize()
     r["wall_s"] = time.perf_counter() - t0
     r["config"] = a.config

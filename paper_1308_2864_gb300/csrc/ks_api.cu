@@ -49,11 +49,11 @@ static size_t gram_partials_len(int p, int sms) {
 
 size_t problem_bytes(int N, int p, int sms) {
   const size_t n = (size_t)N * N * N;
-  size_t b = 12 * n * sizeof(double) + 2 * n * sizeof(float);         // n-vectors
+  size_t b = 13 * n * sizeof(double) + 2 * n * sizeof(float);         // n-vectors
   b += ((size_t)N * N + 2 * N) * sizeof(float);                      // sine basis
   b += (size_t)Problem::kNBlocks * (n * p * sizeof(double) + 256);    // n x p blocks
   b += (size_t)S_COUNT * p * p * sizeof(double);                      // small matrices
-  b += (size_t)3 * p * p * sizeof(float);                             // FP32 coefficients
+  b += (size_t)5 * p * p * sizeof(float);                             // FP32 coefficients, Grams
   b += tc_image_floats(p) * sizeof(float);                            // tensor-core image
   b += (size_t)(2 * p + 128) * sizeof(int);                           // split exponents
   b += oz_image_bytes(p);                                             // split coefficients
@@ -105,9 +105,9 @@ static void free_problem(Problem &P) {
   cudaStream_t s = P.stream;
   auto f = [s](void *q) { if (q) cudaFreeAsync(q, s); };
   f(P.vext); f(P.rho); f(P.vH); f(P.veff); f(P.rho_b); f(P.veff_b); f(P.zero_n); f(P.cg_r); f(P.cg_pa); f(P.cg_pb); f(P.cg_q);
-  f(P.cg_z); f(P.cg_t1); f(P.cg_t2); f(P.dst_phi); f(P.dst_kap); f(P.dst_mu);
+  f(P.cg_z); f(P.cg_rho_prev); f(P.cg_t1); f(P.cg_t2); f(P.dst_phi); f(P.dst_kap); f(P.dst_mu);
   for (auto &b : P.blk) f(b);
-  f(P.pp); f(P.cf); f(P.tc_img); f(P.oz_emax); f(P.oz_img); f(P.oz_rowexp); f(P.partials); f(P.scal); f(P.atoms_dev); f(P.thomas_w); f(P.bar); f(P.red_counter); f(P.dstatus);
+  f(P.pp); f(P.cf); f(P.rt32); f(P.tc_img); f(P.oz_emax); f(P.oz_img); f(P.oz_rowexp); f(P.partials); f(P.scal); f(P.atoms_dev); f(P.thomas_w); f(P.bar); f(P.red_counter); f(P.dstatus);
   delete[] P.scal_host;
   delete[] P.dstatus_host;
   P.scal_host = nullptr;
@@ -161,6 +161,7 @@ static T *blk(Problem &P, int b) { return reinterpret_cast<T *>(P.blk[b]); }
 // exists), potential and energy sums, Hamiltonian stencil (E_X, M X).
 template <typename T>
 static ks_status evaluate(Problem &P, const T *X, T *EX, T *MX, double *E) {
+  P.rho_block = -1;
   KS_TRY(launch_density<T>(P, X, P.rho));
   KS_TRY(launch_cg(P, P.rho, P.vH, P.cg_r, P.vH_valid));
   KS_TRY(launch_potential(P, P.rho, P.vH, P.cg_r, P.veff, true, sizeof(T) == 4));
@@ -494,7 +495,9 @@ static float *base_db(Problem &P) { return upper32(P, B_G); }
 // increment e and M delta.
 static ks_status evaluate_split(Problem &P, int bx, float *e, float *Md, double *E) {
   const float *d = lower32(P, bx);
-  KS_TRY(launch_density_inc(P, d, base_hi(P), P.rho_b, P.rho));
+  // the retraction's update pass may already have formed the trial's density
+  if (P.rho_block != bx) KS_TRY(launch_density_inc(P, d, base_hi(P), P.rho_b, P.rho));
+  P.rho_block = -1;
   KS_TRY(launch_cg(P, P.rho, P.vH, P.cg_r, P.vH_valid));
   KS_TRY(launch_potential(P, P.rho, P.vH, P.cg_r, P.veff, true, false));
   KS_TRY(launch_hamiltonian_inc(P, d, P.veff, P.veff_b, base_hi(P), base_eb(P), e, Md,
@@ -531,19 +534,17 @@ static ks_status project_split(Problem &P, int retraction, int bx, const float *
   float *Gi = lower32(P, B_G);
   const float *X32 = upper32(P, bx), *d = lower32(P, bx);
   KS_TRY(launch_mass_inverse<float>(P, e, Gi, base_db(P)));                // D_b + M^{-1} e
-  KS_TRY(launch_gram<float>(P, base_eb(P), p, d, p, sm(P, S_DS)));          // E_b^T delta
-  KS_TRY(launch_gram<float>(P, e, p, X32, p, sm(P, S_E1)));                 // e^T X
-  KS_TRY(launch_add_pp(P, sm(P, S_DS), 1.0, sm(P, S_E1), sm(P, S_DS)));     // dS
+  // dS = E_b^T delta + e^T X
+  KS_TRY(launch_gram_pair(P, base_eb(P), d, e, X32, p, p, sm(P, S_DS), sm(P, S_E1)));
   KS_TRY(launch_add_pp(P, sm(P, S_SB), 1.0, sm(P, S_DS), sm(P, S_S)));      // S
   KS_TRY(launch_combine<float>(P, d, p, sm(P, S_SB), X32, p, sm(P, S_DS), -1.0, 1.0, Gi, D, p));
   KS_TRY(launch_mass_dots<float>(P, D, MD, d, Md, prev, P.scal + SC_DNORM2));
-  KS_TRY(launch_gram<float>(P, D, p, MD, p, sm(P, S_DMD)));
-  KS_TRY(launch_gram<float>(P, X32, p, MD, p, sm(P, S_XMD)));
+  KS_TRY(launch_gram_dual(P, D, X32, MD, p, p, sm(P, S_DMD), sm(P, S_XMD),  // D^T MD, X^T MD
+                          P.rt32));
   if (retraction != KS_QR) {
     KS_TRY(launch_transpose(P, sm(P, S_S), sm(P, S_A)));
-    KS_TRY(launch_gram<float>(P, base_eb(P), p, D, p, sm(P, S_B)));         // E_b^T D
-    KS_TRY(launch_gram<float>(P, e, p, D, p, sm(P, S_E1)));                 // e^T D
-    KS_TRY(launch_add_pp(P, sm(P, S_B), 1.0, sm(P, S_E1), sm(P, S_B)));
+    // E_X^T D = E_b^T D + e^T D
+    KS_TRY(launch_gram_pair(P, base_eb(P), D, e, D, p, p, sm(P, S_B), sm(P, S_E1)));
     KS_TRY(launch_small_gemm(P, 0, sm(P, S_S), 0, sm(P, S_S), 1.0, 1.0, sm(P, S_B)));  // + S S
     // X^T M X = I up to the increment's rounding
     KS_CUDA_TRY(cudaMemsetAsync(sm(P, S_O), 0, (size_t)p * p * sizeof(double), P.stream));
@@ -583,6 +584,17 @@ static ks_status retract_split(Problem &P, int retraction, int bx, const float *
   const int p = P.p;
   const size_t pp = (size_t)p * p * sizeof(double);
   const double *Ac, *Bc;
+  float *dt = lower32(P, bt), *xt = upper32(P, bt);
+  P.rho_block = -1;
+  if (retraction == KS_QR && qr_factor_dev_applies(P) && combine3_f32_applies(P, p, p, p, p)) {
+    // the factor as deviations from I in FP32 (with the coefficient image),
+    // then one pass: delta+, its FP32 copy X_b + delta+ and the trial's density
+    KS_TRY(launch_qr_factor_dev(P, P.rt32, tau));
+    KS_TRY(launch_combine3_f32(P, base_hi(P), p, sm(P, S_T), lower32(P, bx), p, sm(P, S_C1), D,
+                               p, sm(P, S_C2), dt, base_hi(P), xt, p, P.rho_b, P.rho, true));
+    P.rho_block = bt;
+    return KS_OK;
+  }
   if (retraction == KS_QR) {
     KS_TRY(launch_qr_exact_gram(P, sm(P, S_DMD), sm(P, S_XMD), tau, sm(P, S_E1)));
     KS_TRY(launch_qr_factor(P, sm(P, S_E1), nullptr, tau, sm(P, S_C1), sm(P, S_C2)));
@@ -606,12 +618,14 @@ static ks_status retract_split(Problem &P, int retraction, int bx, const float *
     Ac = E3;
     Bc = E2;
   }
-  float *dt = lower32(P, bt), *xt = upper32(P, bt);
   KS_TRY(launch_add_identity(P, Ac, -1.0, sm(P, S_T)));
-  if (combine3_f32_applies(P, p, p, p, p))
-    // one pass: delta+ and its FP32 copy X_b + delta+
-    return launch_combine3_f32(P, base_hi(P), p, sm(P, S_T), lower32(P, bx), p, Ac, D, p, Bc, dt,
-                               base_hi(P), xt, p);
+  if (combine3_f32_applies(P, p, p, p, p)) {
+    // one pass: delta+, its FP32 copy X_b + delta+ and the trial's density
+    KS_TRY(launch_combine3_f32(P, base_hi(P), p, sm(P, S_T), lower32(P, bx), p, Ac, D, p, Bc, dt,
+                               base_hi(P), xt, p, P.rho_b, P.rho));
+    P.rho_block = bt;
+    return KS_OK;
+  }
   // X_b (A - I) + D B into the trial's upper half, then delta A added
   KS_TRY(launch_combine<float>(P, base_hi(P), p, sm(P, S_T), D, p, Bc, 1.0, 0.0, nullptr, xt, p));
   KS_TRY(launch_combine<float>(P, lower32(P, bx), p, Ac, nullptr, 0, nullptr, 1.0, 1.0, xt, dt,
@@ -924,7 +938,9 @@ static ks_status minimize_device(Problem &P, double *X_inout, const ks_opts &o, 
 // previous X, MX, D, MD blocks (elem bytes per entry), then vH (FP64).  A
 // state of the FP32 phase in increment form (split = 1) instead holds all
 // n x p blocks at full capacity in their own slots (the base quantities share
-// them with the increments), then vH, rho_b, V_b and S_b.
+// them with the increments), then vH, rho_b, V_b and S_b.  Both end with the
+// Hartree solver's last residual and right-hand side (cg_r, cg_rho_prev),
+// so that a resumed run starts its next solve exactly like the original.
 struct StateHeader {
   uint64_t magic;
   int32_t version, N, p, elem, retraction, first_k, k, have_prev, last_improve;
@@ -932,16 +948,35 @@ struct StateHeader {
   int32_t split, since_rebase;
   double T_b;
   int32_t slots[13];
+  int32_t cg_inc_ok, cg_inc_count;
 };
 constexpr uint64_t kStateMagic = 0x4b53535441544531ull;   // "KSSTATE1"
 
 static size_t block_capacity(const Problem &P) { return ((size_t)P.n * P.p + 32) * sizeof(double); }
 
 static size_t state_bytes(const Problem &P, int elem, int split) {
+  const size_t cg = (size_t)2 * P.n * sizeof(double);
   if (split)
     return sizeof(StateHeader) + (size_t)Problem::kNBlocks * block_capacity(P) +
-           (size_t)3 * P.n * sizeof(double) + (size_t)P.p * P.p * sizeof(double);
-  return sizeof(StateHeader) + (size_t)9 * P.n * P.p * elem + (size_t)P.n * sizeof(double);
+           (size_t)3 * P.n * sizeof(double) + (size_t)P.p * P.p * sizeof(double) + cg;
+  return sizeof(StateHeader) + (size_t)9 * P.n * P.p * elem + (size_t)P.n * sizeof(double) + cg;
+}
+
+// The Hartree solver's residual and right-hand side, after the rest.
+static ks_status save_cg(Problem &P, char *dst) {
+  KS_CUDA_TRY(cudaMemcpyAsync(dst, P.cg_r, (size_t)P.n * sizeof(double), cudaMemcpyDeviceToHost,
+                              P.stream));
+  KS_CUDA_TRY(cudaMemcpyAsync(dst + (size_t)P.n * sizeof(double), P.cg_rho_prev,
+                              (size_t)P.n * sizeof(double), cudaMemcpyDeviceToHost, P.stream));
+  return KS_OK;
+}
+
+static ks_status load_cg(Problem &P, const char *src) {
+  KS_CUDA_TRY(cudaMemcpyAsync(P.cg_r, src, (size_t)P.n * sizeof(double), cudaMemcpyHostToDevice,
+                              P.stream));
+  KS_CUDA_TRY(cudaMemcpyAsync(P.cg_rho_prev, src + (size_t)P.n * sizeof(double),
+                              (size_t)P.n * sizeof(double), cudaMemcpyHostToDevice, P.stream));
+  return KS_OK;
 }
 
 }  // namespace ks
@@ -1041,6 +1076,7 @@ ks_status ks_problem_create(const ks_problem_desc *d, ks_problem **out) {
   ALLOC(P.vext, n); ALLOC(P.rho, n); ALLOC(P.vH, n); ALLOC(P.veff, n);
   ALLOC(P.rho_b, n); ALLOC(P.veff_b, n); ALLOC(P.zero_n, n);
   ALLOC(P.cg_r, n); ALLOC(P.cg_pa, n); ALLOC(P.cg_pb, n); ALLOC(P.cg_q, n); ALLOC(P.cg_z, n);
+  ALLOC(P.cg_rho_prev, n);
   ALLOC(P.cg_t1, n); ALLOC(P.cg_t2, n);
   ALLOC(P.dst_phi, (size_t)P.N * P.N); ALLOC(P.dst_kap, (size_t)P.N); ALLOC(P.dst_mu, (size_t)P.N);
   // FP64 capacity plus 256 bytes, so that an FP32 block fits in the upper
@@ -1050,6 +1086,7 @@ ks_status ks_problem_create(const ks_problem_desc *d, ks_problem **out) {
   P.pp_len = (size_t)S_COUNT * P.p * P.p;
   ALLOC(P.pp, P.pp_len);
   ALLOC(P.cf, (size_t)3 * P.p * P.p);
+  ALLOC(P.rt32, (size_t)2 * P.p * P.p);
   P.tc_img_len = tc_image_floats(P.p);
   ALLOC(P.tc_img, P.tc_img_len);
   P.oz_emax_len = 2 * P.p + 128;
@@ -1220,7 +1257,9 @@ ks_status ks_state_save(ks_problem *kp, void *host_buf, size_t bytes) {
   if (bytes < state_bytes(P, S.elem, S.split)) return set_error(KS_EINVAL, "buffer too small");
   StateHeader hd{};
   hd.magic = kStateMagic;
-  hd.version = 3;
+  hd.version = 4;
+  hd.cg_inc_ok = P.cg_inc_ok ? 1 : 0;
+  hd.cg_inc_count = P.cg_inc_count;
   hd.split = S.split; hd.since_rebase = S.since_rebase; hd.T_b = S.T_b;
   for (int i = 0; i < 3; ++i) { hd.slots[i] = S.ix[i]; hd.slots[3 + i] = S.imx[i]; }
   for (int i = 0; i < 2; ++i) {
@@ -1250,6 +1289,8 @@ ks_status ks_state_save(ks_problem *kp, void *host_buf, size_t bytes) {
     dst += (size_t)P.n * sizeof(double);
     KS_CUDA_TRY(cudaMemcpyAsync(dst, sm(P, S_SB), (size_t)P.p * P.p * sizeof(double),
                                 cudaMemcpyDeviceToHost, P.stream));
+    dst += (size_t)P.p * P.p * sizeof(double);
+    KS_TRY(save_cg(P, dst));
     KS_CUDA_TRY(cudaStreamSynchronize(P.stream));
     return KS_OK;
   }
@@ -1262,6 +1303,8 @@ ks_status ks_state_save(ks_problem *kp, void *host_buf, size_t bytes) {
   }
   KS_CUDA_TRY(cudaMemcpyAsync(dst, P.vH, (size_t)P.n * sizeof(double), cudaMemcpyDeviceToHost,
                               P.stream));
+  dst += (size_t)P.n * sizeof(double);
+  KS_TRY(save_cg(P, dst));
   KS_CUDA_TRY(cudaStreamSynchronize(P.stream));
   return KS_OK;
 }
@@ -1272,7 +1315,7 @@ ks_status ks_state_load(ks_problem *kp, const void *host_buf, size_t bytes) {
   StateHeader hd;
   if (bytes < sizeof(hd)) return set_error(KS_EINVAL, "buffer too small");
   std::memcpy(&hd, host_buf, sizeof(hd));
-  if (hd.magic != kStateMagic || hd.version != 3) return set_error(KS_EINVAL, "not a saved state");
+  if (hd.magic != kStateMagic || hd.version != 4) return set_error(KS_EINVAL, "not a saved state");
   if (hd.N != P.N || hd.p != P.p || (hd.elem != 4 && hd.elem != 8) ||
       (hd.split != 0 && (hd.split != 1 || hd.elem != 4)))
     return set_error(KS_EINVAL, "saved state does not match this problem");
@@ -1304,6 +1347,8 @@ ks_status ks_state_load(ks_problem *kp, const void *host_buf, size_t bytes) {
   S.T_b = hd.T_b;
   // the blocks are overwritten below: a copy that fails leaves no state
   P.state.valid = false;
+  P.rho_block = -1;
+  P.cg_inc_ok = false;
   if (hd.split) {
     for (int i = 0; i < 3; ++i) { S.ix[i] = hd.slots[i]; S.imx[i] = hd.slots[3 + i]; }
     for (int i = 0; i < 2; ++i) {
@@ -1326,8 +1371,12 @@ ks_status ks_state_load(ks_problem *kp, const void *host_buf, size_t bytes) {
     src += (size_t)P.n * sizeof(double);
     KS_CUDA_TRY(cudaMemcpyAsync(sm(P, S_SB), src, (size_t)P.p * P.p * sizeof(double),
                                 cudaMemcpyHostToDevice, P.stream));
+    src += (size_t)P.p * P.p * sizeof(double);
+    KS_TRY(load_cg(P, src));
     KS_CUDA_TRY(cudaStreamSynchronize(P.stream));
     P.state = S;
+    P.cg_inc_ok = hd.cg_inc_ok != 0;
+    P.cg_inc_count = hd.cg_inc_count;
     return KS_OK;
   }
   // canonical slots: current in slot 0, previous in slot 1
@@ -1340,8 +1389,12 @@ ks_status ks_state_load(ks_problem *kp, const void *host_buf, size_t bytes) {
   }
   KS_CUDA_TRY(cudaMemcpyAsync(P.vH, src, (size_t)P.n * sizeof(double), cudaMemcpyHostToDevice,
                               P.stream));
+  src += (size_t)P.n * sizeof(double);
+  KS_TRY(load_cg(P, src));
   KS_CUDA_TRY(cudaStreamSynchronize(P.stream));
   P.state = S;
+  P.cg_inc_ok = hd.cg_inc_ok != 0;
+  P.cg_inc_count = hd.cg_inc_count;
   return KS_OK;
 }
 

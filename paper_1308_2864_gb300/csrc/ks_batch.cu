@@ -663,6 +663,7 @@ ks_status ks_batch_create(const ks_problem_desc *descs, int njobs, void *stream,
     b.vH = P.vH;
     b.veff = P.veff;
     b.cg_r = P.cg_r;
+    P.cg_inc_ok = false;   // the batch's own solves write vH and r
     b.pp = P.pp;
     b.cf = P.cf;
     b.partials = P.partials;

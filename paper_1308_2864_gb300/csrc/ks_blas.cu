@@ -319,47 +319,65 @@ __global__ void __launch_bounds__(256) gram_small_kernel(long long n, int pa, in
   gram_small_body<T>(n, pa, qb, rows_per, A, B, part, blockIdx.x);
 }
 
-// Pipelined FP32 Gram for 32 < max(pa, qb) <= 64 and 16-byte-aligned
+// Pipelined FP32 Grams for 32 < max(pa, qb) <= 64 and 16-byte-aligned
 // operands (widths multiples of 4): persistent blocks take stages of 32 rows
 // in turn (block b: stages b, b + G, ...), copied global -> shared by
 // cp.async three stages ahead (columns beyond pa, qb zero-filled), and keep
-// one 64 x 64 FP32 tile (4 x 4 per thread) over all their rows; each block
-// writes one FP64 partial tile, summed afterwards in block order.
+// 64 x 64 FP32 tiles (4 x 4 per thread) over all their rows; each block
+// writes its FP32 partial tiles, summed afterwards in FP64 in block order.
+// Two forms:
+//   pair   (Dual = false): out = A1^T B1 + A2^T B2 -- the rows of the second
+//          pair follow those of the first (A2 null: one Gram);
+//   shared (Dual = true):  out1 = A1^T B, out2 = A2^T B with B read once.
 constexpr int kGaStages = 3, kGaRows = 32;
-constexpr size_t kGaSmem = (size_t)kGaStages * 2 * kGaRows * kTile * sizeof(float);
 
-__global__ void __launch_bounds__(256, 4) gram_ta_kernel(long long n, int pa, int qb,
-                                                         const float *__restrict__ A,
-                                                         const float *__restrict__ B,
-                                                         double *__restrict__ part) {
+template <bool Dual>
+constexpr size_t gram_ta_smem() {
+  return (size_t)kGaStages * (Dual ? 3 : 2) * kGaRows * kTile * sizeof(float);
+}
+
+template <bool Dual>
+__global__ void __launch_bounds__(256, Dual ? 3 : 4) gram2_ta_kernel(
+    long long n, int pa, int qb, const float *__restrict__ A1, const float *__restrict__ B1,
+    const float *__restrict__ A2, const float *__restrict__ B2, float *__restrict__ part) {
   extern __shared__ __align__(16) float ga_smem[];
+  constexpr int kOps = Dual ? 3 : 2;                 // staged operands: A1, B (, A2)
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-  const long long nst = (n + kGaRows - 1) / kGaRows;
+  const long long nv = (!Dual && A2) ? 2 * n : n;    // rows streamed (both pairs)
+  const long long nst = (nv + kGaRows - 1) / kGaRows;
   const long long W = nst > blockIdx.x ? (nst - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
   auto issue = [&](long long w) {
     const long long r0 = (blockIdx.x + w * gridDim.x) * kGaRows;
-    float *dst = ga_smem + (size_t)(w % kGaStages) * 2 * kGaRows * kTile;
+    float *dst = ga_smem + (size_t)(w % kGaStages) * kOps * kGaRows * kTile;
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const int idx = tid + t * 256;               // 0..1023: operand, row, 4-column chunk
+    for (int t = 0; t < kOps * 2; ++t) {
+      const int idx = tid + t * 256;               // operand, row, 4-column chunk
       const int op = idx >> 9, rr = (idx >> 4) & 31, c4 = (idx & 15) * 4;
-      const long long row = r0 + rr;
-      const int w_ = op ? qb : pa;
-      const float *M = op ? B : A;
-      const float *src = A;
+      long long row = r0 + rr;
+      const int w_ = op == 1 ? qb : pa;
+      const float *M;
+      if (Dual) {
+        M = op == 0 ? A1 : op == 1 ? B1 : A2;
+      } else if (row < n) {
+        M = op == 0 ? A1 : B1;
+      } else {
+        M = op == 0 ? A2 : B2;
+        row -= n;
+      }
+      const float *src = A1;
       uint32_t bytes = 0;
-      if (row < n && c4 < w_) {
+      if (row < n && r0 + rr < nv && c4 < w_) {
         src = M + row * w_ + c4;
         bytes = 16;
       }
       cp_async16(smem_addr(dst + (size_t)op * kGaRows * kTile + rr * kTile + c4), src, bytes);
     }
   };
-  float acc[4][4];
+  float acc[4][4], acc2[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    for (int j = 0; j < 4; ++j) acc[i][j] = acc2[i][j] = 0.f;
   for (int st = 0; st < kGaStages - 1; ++st) {
     if (st < W) issue(st);
     cp_async_commit();
@@ -369,8 +387,9 @@ __global__ void __launch_bounds__(256, 4) gram_ta_kernel(long long n, int pa, in
     __syncthreads();
     if (w + kGaStages - 1 < W) issue(w + kGaStages - 1);
     cp_async_commit();
-    const float *As = ga_smem + (size_t)(w % kGaStages) * 2 * kGaRows * kTile;
+    const float *As = ga_smem + (size_t)(w % kGaStages) * kOps * kGaRows * kTile;
     const float *Bs = As + kGaRows * kTile;
+    const float *A2s = Bs + kGaRows * kTile;
 #pragma unroll 8
     for (int r = 0; r < kGaRows; ++r) {
       const float4 av = *reinterpret_cast<const float4 *>(As + r * kTile + 4 * ty);
@@ -381,10 +400,19 @@ __global__ void __launch_bounds__(256, 4) gram_ta_kernel(long long n, int pa, in
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a4[i], b4[j], acc[i][j]);
+      if (Dual) {
+        const float4 cv = *reinterpret_cast<const float4 *>(A2s + r * kTile + 4 * ty);
+        const float c4[4] = {cv.x, cv.y, cv.z, cv.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc2[i][j] = fmaf(c4[i], b4[j], acc2[i][j]);
+      }
     }
   }
   asm volatile("cp.async.wait_all;\n" ::: "memory");
-  double *dst = part + (long long)blockIdx.x * pa * qb;
+  const long long len = (long long)pa * qb;
+  float *dst = part + (long long)blockIdx.x * (Dual ? 2 : 1) * len;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int a = 4 * ty + i;
@@ -392,9 +420,71 @@ __global__ void __launch_bounds__(256, 4) gram_ta_kernel(long long n, int pa, in
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int b = 4 * tx + j;
-      if (b < qb) dst[(long long)a * qb + b] = (double)acc[i][j];
+      if (b >= qb) continue;
+      dst[(long long)a * qb + b] = acc[i][j];
+      if (Dual) dst[len + (long long)a * qb + b] = acc2[i][j];
     }
   }
+}
+
+// FP64 sums of FP32 chunk partials in chunk order: element e < len1 of each
+// chunk goes to out1[e], the rest to out2[e - len1]; out32 (optional) gets
+// every sum rounded to FP32 at index e.
+__global__ void gram_reduce_f32_kernel(int chunks, long long len, long long len1,
+                                       const float *__restrict__ part, double *__restrict__ out1,
+                                       double *__restrict__ out2, float *__restrict__ out32) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long e = t >> 3;
+  const int sub = (int)(t & 7);
+  double acc = 0.0;
+  if (e < len)
+    for (int c = sub; c < chunks; c += 8) acc += (double)part[(long long)c * len + e];
+  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+  if (sub == 0 && e < len) {
+    if (e < len1) out1[e] = acc;
+    else out2[e - len1] = acc;
+    if (out32) out32[e] = (float)acc;
+  }
+}
+
+// The pipelined Gram kernels apply: FP32, 32 < max(pa, qb) <= 64, widths
+// multiples of 4 and 16-byte-aligned operands.
+static bool gram_ta_applies(int pa, int qb, std::initializer_list<const float *> ops) {
+  if (pa > kTile || qb > kTile || (pa <= kMidPQ && qb <= kMidPQ) || pa % 4 || qb % 4) return false;
+  for (const float *A : ops)
+    if (reinterpret_cast<uintptr_t>(A) % 16) return false;
+  return true;
+}
+
+template <bool Dual>
+static ks_status launch_gram2_ta(Problem &P, int pa, int qb, const float *A1, const float *B1,
+                                 const float *A2, const float *B2, double *out1, double *out2,
+                                 float *out32 = nullptr) {
+  const long long nv = (!Dual && A2) ? 2 * P.n : P.n;
+  const long long nst = (nv + kGaRows - 1) / kGaRows;
+  long long blocks = (Dual ? 3LL : 4LL) * P.sms;
+  if (blocks > nst) blocks = nst;
+  const long long len = (long long)pa * qb * (Dual ? 2 : 1);
+  // FP32 partials in the FP64 partial buffer
+  if ((size_t)blocks * len > 2 * P.partials_len)
+    return set_error(KS_EINVAL, "gram: partial buffer too small");
+  float *part = reinterpret_cast<float *>(P.partials);
+  {
+    ProfScope ps_(P.stream, KP_GRAM, 2.0 * nv * pa * qb * (Dual ? 2 : 1),
+                  (double)nv * (pa + qb + (Dual ? pa : 0)) * sizeof(float));
+    gram2_ta_kernel<Dual><<<(int)blocks, 256, gram_ta_smem<Dual>(), P.stream>>>(
+        P.n, pa, qb, A1, B1, A2, B2, part);
+  }
+  KS_CUDA_TRY(cudaGetLastError());
+  {
+    ProfScope ps_(P.stream, KP_REDUCE);
+    gram_reduce_f32_kernel<<<(int)((8 * len + kThreads - 1) / kThreads), kThreads, 0, P.stream>>>(
+        (int)blocks, len, (long long)pa * qb, part, out1, out2, out32);
+  }
+  KS_CUDA_TRY(cudaGetLastError());
+  return KS_OK;
 }
 
 template <typename T>
@@ -431,33 +521,9 @@ ks_status launch_gram(Problem &P, const T *A, int pa, const T *B, int qb, double
     KS_CUDA_TRY(cudaGetLastError());
     return KS_OK;
   }
-#ifndef KS_NO_TA
-  if (sizeof(T) == 4 && pa <= kTile && qb <= kTile && (pa > kMidPQ || qb > kMidPQ) &&
-#else
-  if (false &&
-#endif
-      pa % 4 == 0 && qb % 4 == 0 && reinterpret_cast<uintptr_t>(A) % 16 == 0 &&
-      reinterpret_cast<uintptr_t>(B) % 16 == 0) {
-    const long long nst = (P.n + kGaRows - 1) / kGaRows;
-    long long blocks = 4LL * P.sms;
-    if (blocks > nst) blocks = nst;
-    if ((size_t)blocks * pa * qb > P.partials_len)
-      return set_error(KS_EINVAL, "gram: partial buffer too small");
-    {
-      ProfScope ps_(P.stream, KP_GRAM, 2.0 * P.n * pa * qb, (double)P.n * (pa + qb) * sizeof(T));
-      gram_ta_kernel<<<(int)blocks, 256, kGaSmem, P.stream>>>(P.n, pa, qb, (const float *)A,
-                                                             (const float *)B, P.partials);
-    }
-    KS_CUDA_TRY(cudaGetLastError());
-    const long long len = (long long)pa * qb;
-    {
-      ProfScope ps_(P.stream, KP_REDUCE);
-      gram_reduce_kernel<<<(int)((8 * len + kThreads - 1) / kThreads), kThreads, 0, P.stream>>>(
-          (int)blocks, len, P.partials, out);
-    }
-    KS_CUDA_TRY(cudaGetLastError());
-    return KS_OK;
-  }
+  if (sizeof(T) == 4 && gram_ta_applies(pa, qb, {(const float *)A, (const float *)B}))
+    return launch_gram2_ta<false>(P, pa, qb, (const float *)A, (const float *)B, nullptr, nullptr,
+                                  out, nullptr);
   const int chunks = gram_chunks(P, pa, qb);
   long long rows_per = (P.n + chunks - 1) / chunks;
   rows_per = (rows_per + kTileK - 1) / kTileK * kTileK;
@@ -483,6 +549,41 @@ ks_status launch_gram(Problem &P, const T *A, int pa, const T *B, int qb, double
         chunks, len, P.partials, out);
   }
   KS_CUDA_TRY(cudaGetLastError());
+  return KS_OK;
+}
+
+ks_status launch_gram_pair(Problem &P, const float *A1, const float *B1, const float *A2,
+                           const float *B2, int pa, int qb, double *out, double *tmp) {
+  if (gram_ta_applies(pa, qb, {A1, B1, A2, B2}))
+    return launch_gram2_ta<false>(P, pa, qb, A1, B1, A2, B2, out, nullptr, nullptr);
+  KS_TRY(launch_gram<float>(P, A1, pa, B1, qb, out));
+  KS_TRY(launch_gram<float>(P, A2, pa, B2, qb, tmp));
+  return launch_add_pp(P, out, 1.0, tmp, out);
+}
+
+// FP32 copies of two p x p FP64 matrices, one after the other.
+__global__ void pair_to_f32_kernel(long long len, const double *__restrict__ a,
+                                   const double *__restrict__ b, float *__restrict__ out) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < len) out[e] = (float)a[e];
+  else if (e < 2 * len) out[e] = (float)b[e - len];
+}
+
+ks_status launch_gram_dual(Problem &P, const float *A1, const float *A2, const float *B, int pa,
+                           int qb, double *out1, double *out2, float *out32) {
+  if (gram_ta_applies(pa, qb, {A1, A2, B}))
+    return launch_gram2_ta<true>(P, pa, qb, A1, B, A2, nullptr, out1, out2, out32);
+  KS_TRY(launch_gram<float>(P, A1, pa, B, qb, out1));
+  KS_TRY(launch_gram<float>(P, A2, pa, B, qb, out2));
+  if (out32) {
+    const long long len = (long long)pa * qb;
+    {
+      ProfScope ps_(P.stream, KP_REDUCE);
+      pair_to_f32_kernel<<<(int)((2 * len + kThreads - 1) / kThreads), kThreads, 0, P.stream>>>(
+          len, out1, out2, out32);
+    }
+    KS_CUDA_TRY(cudaGetLastError());
+  }
   return KS_OK;
 }
 
@@ -681,12 +782,89 @@ size_t combine_ts_smem(int K) {
   return ((size_t)nst * kTsK * kTile + (size_t)2 * kTsK * kTsLd) * sizeof(float);
 }
 
+// Optional outputs of the tall-skinny update's epilogue: the density of the
+// new iterate (rho set) and whether every array allows 16-byte accesses.
+struct TsDensity {
+  const double *rho_b = nullptr;
+  double *rho = nullptr;
+  double occ = 0.0;
+  int vec = 0;
+};
+
+// Epilogue of the tall-skinny update for one thread's 8 rows (row0 ..
+// row0 + 7) x 4 columns (4 tx .. 4 tx + 3): out = alpha acc + beta Bm and
+// out2 = add2 + out, 16-byte accesses when the four columns are in range and
+// every array is 16-byte aligned.  With dn.rho set (out2 the FP32 copy of
+// X_b + delta, add2 = X_b, out = delta) it also forms the density of the
+// new iterate in the increment form, rho = rho_b + f sum delta (2 X_b +
+// delta) (Sec. 2.3, rho = diag(X X^T) per occupied orbital): the 16 threads
+// of a row (the lanes tx of one half-warp) sum their columns by a butterfly.
+// The accumulators are cleared for the next tile.
+__device__ __forceinline__ void ts_epilogue(long long n, int q, long long row0, int tx,
+                                            float (&acc)[8][4], float alpha, float beta,
+                                            const float *__restrict__ Bm, float *__restrict__ out,
+                                            const float *__restrict__ add2,
+                                            float *__restrict__ out2, const TsDensity &dn) {
+  const int col0 = 4 * tx;
+  const bool vec = dn.vec && col0 + 3 < q;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const long long row = row0 + i;
+    float dsum = 0.f;
+    if (row < n) {
+      const long long o = row * q + col0;
+      if (vec) {
+        float4 v = make_float4(alpha * acc[i][0], alpha * acc[i][1], alpha * acc[i][2],
+                               alpha * acc[i][3]);
+        if (Bm) {
+          const float4 b = *reinterpret_cast<const float4 *>(Bm + o);
+          v.x = fmaf(beta, b.x, v.x); v.y = fmaf(beta, b.y, v.y);
+          v.z = fmaf(beta, b.z, v.z); v.w = fmaf(beta, b.w, v.w);
+        }
+        *reinterpret_cast<float4 *>(out + o) = v;
+        if (out2) {
+          const float4 h = *reinterpret_cast<const float4 *>(add2 + o);
+          *reinterpret_cast<float4 *>(out2 + o) =
+              make_float4(h.x + v.x, h.y + v.y, h.z + v.z, h.w + v.w);
+          if (dn.rho) {
+            dsum = fmaf(v.x, fmaf(2.f, h.x, v.x), dsum);
+            dsum = fmaf(v.y, fmaf(2.f, h.y, v.y), dsum);
+            dsum = fmaf(v.z, fmaf(2.f, h.z, v.z), dsum);
+            dsum = fmaf(v.w, fmaf(2.f, h.w, v.w), dsum);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (col0 + j < q) {
+            float v = alpha * acc[i][j];
+            if (Bm) v = fmaf(beta, Bm[o + j], v);
+            out[o + j] = v;
+            if (out2) {
+              const float h = add2[o + j];
+              out2[o + j] = h + v;
+              if (dn.rho) dsum = fmaf(v, fmaf(2.f, h, v), dsum);
+            }
+          }
+        }
+      }
+    }
+    if (dn.rho) {
+#pragma unroll
+      for (int s = 8; s > 0; s >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, s);
+      if (tx == 0 && row < n) dn.rho[row] = dn.rho_b[row] + dn.occ * (double)dsum;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  }
+}
+
 __global__ void __launch_bounds__(256, 2) combine_ts_kernel(
     long long n, int q, const float *__restrict__ A1, int k1, const float *__restrict__ c1,
     const float *__restrict__ A2, int k2, const float *__restrict__ c2,
     const float *__restrict__ A3, int k3, const float *__restrict__ c3, float alpha, float beta,
     const float *__restrict__ Bm, float *__restrict__ out, const float *__restrict__ add2,
-    float *__restrict__ out2, long long ntiles) {
+    float *__restrict__ out2, long long ntiles, TsDensity dn) {
   extern __shared__ __align__(16) float ts_smem[];
   const int k12 = k1 + (A2 ? k2 : 0);
   const int K = k12 + (A3 ? k3 : 0);
@@ -763,24 +941,7 @@ __global__ void __launch_bounds__(256, 2) combine_ts_kernel(
     }
     if (w % nst == nst - 1) {
       const long long tile = blockIdx.x + (w / nst) * gridDim.x;
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const long long row = tile * kTsRows + 8 * ty + i;
-        if (row < n) {
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int col = 4 * tx + j;
-            if (col < q) {
-              float v = alpha * acc[i][j];
-              if (Bm) v = fmaf(beta, Bm[row * q + col], v);
-              out[row * q + col] = v;
-              if (out2) out2[row * q + col] = add2[row * q + col] + v;
-            }
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-      }
+      ts_epilogue(n, q, tile * kTsRows + 8 * ty, tx, acc, alpha, beta, Bm, out, add2, out2, dn);
     }
     if (more) stash(buf ^ 1);
     __syncthreads();
@@ -790,7 +951,7 @@ __global__ void __launch_bounds__(256, 2) combine_ts_kernel(
 static void launch_ts(Problem &P, int q, const float *A1, int k1, const float *c1,
                       const float *A2, int k2, const float *c2, const float *A3, int k3,
                       const float *c3, float alpha, float beta, const float *Bm, float *out,
-                      const float *add2, float *out2);
+                      const float *add2, float *out2, TsDensity dn = TsDensity());
 
 // FP32 copies of the update coefficients (one launch for both matrices).
 __global__ void coef_convert_kernel(long long len1, const double *__restrict__ C1,
@@ -1091,7 +1252,7 @@ __global__ void __launch_bounds__(256, 2) combine_ta_kernel(
     const float *__restrict__ A2, int k2, const float *__restrict__ c2,
     const float *__restrict__ A3, int k3, const float *__restrict__ c3, float alpha, float beta,
     const float *__restrict__ Bm, float *__restrict__ out, const float *__restrict__ add2,
-    float *__restrict__ out2, long long ntiles) {
+    float *__restrict__ out2, long long ntiles, TsDensity dn) {
   extern __shared__ __align__(16) float ta_smem[];
   const int k12 = k1 + (A2 ? k2 : 0);
   const int K = k12 + (A3 ? k3 : 0);
@@ -1169,24 +1330,7 @@ __global__ void __launch_bounds__(256, 2) combine_ta_kernel(
     }
     if (w % nst == nst - 1) {
       const long long tile = blockIdx.x + (w / nst) * gridDim.x;
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const long long row = tile * kTsRows + 8 * ty + i;
-        if (row < n) {
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int col = 4 * tx + j;
-            if (col < q) {
-              float v = alpha * acc[i][j];
-              if (Bm) v = fmaf(beta, Bm[row * q + col], v);
-              out[row * q + col] = v;
-              if (out2) out2[row * q + col] = add2[row * q + col] + v;
-            }
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-      }
+      ts_epilogue(n, q, tile * kTsRows + 8 * ty, tx, acc, alpha, beta, Bm, out, add2, out2, dn);
     }
   }
   asm volatile("cp.async.wait_all;\n" ::: "memory");
@@ -1205,21 +1349,19 @@ static bool ta_aligned(const float *A1, int k1, const float *A2, int k2, const f
 static void launch_ts(Problem &P, int q, const float *A1, int k1, const float *c1,
                       const float *A2, int k2, const float *c2, const float *A3, int k3,
                       const float *c3, float alpha, float beta, const float *Bm, float *out,
-                      const float *add2, float *out2) {
+                      const float *add2, float *out2, TsDensity dn) {
+  auto al16 = [](const void *ptr) { return reinterpret_cast<uintptr_t>(ptr) % 16 == 0; };
+  dn.vec = q % 4 == 0 && al16(out) && al16(Bm) && al16(add2) && al16(out2) ? 1 : 0;
   const int K = k1 + (A2 ? k2 : 0) + (A3 ? k3 : 0);
   const long long ntiles = (P.n + kTsRows - 1) / kTsRows;
   long long nb = 2LL * P.sms;
   if (nb > ntiles) nb = ntiles;
-#ifndef KS_NO_TA
   if (ta_aligned(A1, k1, A2, k2, A3, k3))
-#else
-  if (false)
-#endif
     combine_ta_kernel<<<(int)nb, 256, combine_ta_smem(K), P.stream>>>(
-        P.n, q, A1, k1, c1, A2, k2, c2, A3, k3, c3, alpha, beta, Bm, out, add2, out2, ntiles);
+        P.n, q, A1, k1, c1, A2, k2, c2, A3, k3, c3, alpha, beta, Bm, out, add2, out2, ntiles, dn);
   else
     combine_ts_kernel<<<(int)nb, 256, combine_ts_smem(K), P.stream>>>(
-        P.n, q, A1, k1, c1, A2, k2, c2, A3, k3, c3, alpha, beta, Bm, out, add2, out2, ntiles);
+        P.n, q, A1, k1, c1, A2, k2, c2, A3, k3, c3, alpha, beta, Bm, out, add2, out2, ntiles, dn);
 }
 
 // out = A1 C1 + A2 C2 + A3 C3 and out2 = add2 + out in one pass of the
@@ -1232,7 +1374,8 @@ bool combine3_f32_applies(const Problem &P, int k1, int k2, int k3, int q) {
 
 ks_status launch_combine3_f32(Problem &P, const float *A1, int k1, const double *C1,
                               const float *A2, int k2, const double *C2, const float *A3, int k3,
-                              const double *C3, float *out, const float *add2, float *out2, int q) {
+                              const double *C3, float *out, const float *add2, float *out2, int q,
+                              const double *rho_b, double *rho, bool images_ready) {
   if (!combine3_f32_applies(P, k1, k2, k3, q))
     return set_error(KS_EINVAL, "combine3: shape outside the tall-skinny kernel");
   // FP32 images of C1, C2, C3 one after the other in P.cf (3 p^2 floats)
@@ -1240,7 +1383,7 @@ ks_status launch_combine3_f32(Problem &P, const float *A1, int k1, const double 
   if ((size_t)(k1 + k2 + k3) * q > (size_t)3 * P.p * P.p)
     return set_error(KS_EINVAL, "combine3: coefficient image too small");
   const long long len1 = (long long)k1 * q, len2 = (long long)k2 * q, len3 = (long long)k3 * q;
-  {
+  if (!images_ready) {
     ProfScope ps_(P.stream, KP_REDUCE);
     coef_convert_kernel<<<(int)((len1 + len2 + 255) / 256), 256, 0, P.stream>>>(len1, C1, c1,
                                                                                 len2, C2, c2);
@@ -1252,7 +1395,13 @@ ks_status launch_combine3_f32(Problem &P, const float *A1, int k1, const double 
   {
     ProfScope ps_(P.stream, KP_COMBINE, 2.0 * P.n * q * K,
                   (double)P.n * (K + q * (out2 ? 3 : 1)) * sizeof(float));
-    launch_ts(P, q, A1, k1, c1, A2, k2, c2, A3, k3, c3, 1.0f, 0.0f, nullptr, out, add2, out2);
+    TsDensity dn;
+    if (rho && add2 && out2 && q == P.p) {
+      dn.rho_b = rho_b;
+      dn.rho = rho;
+      dn.occ = P.occ;
+    }
+    launch_ts(P, q, A1, k1, c1, A2, k2, c2, A3, k3, c3, 1.0f, 0.0f, nullptr, out, add2, out2, dn);
   }
   KS_CUDA_TRY(cudaGetLastError());
   return KS_OK;
@@ -1261,6 +1410,12 @@ ks_status launch_combine3_f32(Problem &P, const float *A1, int k1, const double 
 // Dynamic shared memory of the tall-skinny update beyond the default 48 KiB
 // (on the current device; called when a problem is created).
 ks_status configure_blas_kernels() {
+  KS_CUDA_TRY(cudaFuncSetAttribute(gram2_ta_kernel<true>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)gram_ta_smem<true>()));
+  KS_CUDA_TRY(cudaFuncSetAttribute(gram2_ta_kernel<false>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)gram_ta_smem<false>()));
   KS_CUDA_TRY(cudaFuncSetAttribute(combine_ts_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)combine_ts_smem(kTsMaxK)));
   KS_CUDA_TRY(cudaFuncSetAttribute(combine_ta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

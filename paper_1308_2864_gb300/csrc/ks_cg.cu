@@ -42,6 +42,8 @@ struct CgArgs {
   int warm;
   int precond;
   int fused;                  // fused shared-memory preconditioner (N <= kFusedMaxN)
+  int incr;                   // warm start with r = b_old - K x still in r
+  double *rho_prev;           // density of the last solve (its b / bscale)
   int vb, vnb;                // this block's index among the vnb blocks that solve this system
 };
 
@@ -206,52 +208,125 @@ __device__ bool apply_precond(const CgArgs &a, double *rz_l) {
   return true;
 }
 
-// Fused form for N <= kFusedMaxN, with the planes in shared memory (3 N^2
-// floats of dynamic shared memory: a plane, Phi and a work matrix):
-//   A: each z-plane P (N x N, rows y, columns x) -> Phi P Phi   (x and y)
+// Fused form for N <= kFusedMaxN, with the planes in shared memory (three
+// N x ld matrices of dynamic shared memory: a plane, Phi and a work matrix;
+// ld = 68 for N <= 64, 132 above, so that every 16-byte row access of a
+// 64-wide output tile stays inside its row):
+//   A: each z-plane P (N x N, rows y, columns x) -> Phi P Phi   (y, then x)
 //   B: each y-slab S (rows z, columns x)          -> Phi (Lambda^{-1} o (Phi S))
 //   C: each z-plane                               -> Phi P Phi, written as z
 // (Phi is symmetric, so Phi P Phi transforms both in-plane axes), three grid
 // barriers per application instead of six.
 constexpr int kFusedMaxN = 128;
 
-// out = A B for N x N row-major matrices in shared memory (kCgThreads
-// threads, W = kCgThreads / 32 warps).  Each thread keeps a (64/W) x 2
-// block of outputs in registers (rows ty + W a, columns tx + 32 b of a 64 x 64
-// tile), so a k step costs 64/W broadcast loads of A and 2 conflict-free
-// loads of B for 128/W FMAs.  Every output is the same k-ascending FMA chain
-// as the one-output-per-thread form.
-constexpr int kCgWarps = kCgThreads / 32;
-constexpr int kRowsPerThread = 64 / kCgWarps;
-static_assert(64 % kCgWarps == 0, "warps must divide the 64-row tile");
+__host__ __device__ constexpr int fused_ld(int N) { return N <= 64 ? 68 : 132; }
 
-__device__ __forceinline__ void smem_matmul(const float *A, const float *B, float *out, int N) {
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+// out = A B for N x N matrices in shared memory (row stride ld), A given by
+// its transpose At (At[k][i] = A[i][k]; Phi is its own transpose).  Each
+// thread keeps a 4 x 4 block of a 64 x 64 output tile (rows 4 ty .. + 3,
+// columns 4 tx .. + 3 with ty = tid / 16, tx = tid % 16): per k one 16-byte
+// load of At (two addresses per warp, broadcast) and one of B (16
+// consecutive ones) for 16 FMAs.  Each output is one k-ascending FMA chain.
+// Trans: out is stored transposed (out[j][i]), ready to be the At of the
+// next product.
+template <bool Trans>
+__device__ __forceinline__ void smem_matmul(const float *At, const float *B, float *out, int N,
+                                            int ld) {
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   for (int ib = 0; ib < N; ib += 64)
     for (int jb = 0; jb < N; jb += 64) {
-      float acc[kRowsPerThread][2];
+      const int i0 = ib + 4 * ty, j0 = jb + 4 * tx;
+      if (i0 >= N || j0 >= N) continue;
+      float acc[4][4];
 #pragma unroll
-      for (int a = 0; a < kRowsPerThread; ++a) acc[a][0] = acc[a][1] = 0.f;
-      const int j0 = jb + tx, j1 = jb + tx + 32;
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+#pragma unroll 4
       for (int k = 0; k < N; ++k) {
-        const float b0 = j0 < N ? B[k * N + j0] : 0.f;
-        const float b1 = j1 < N ? B[k * N + j1] : 0.f;
+        const float4 av = *reinterpret_cast<const float4 *>(At + k * ld + i0);
+        const float4 bv = *reinterpret_cast<const float4 *>(B + k * ld + j0);
+        const float a4[4] = {av.x, av.y, av.z, av.w};
+        const float b4[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
-        for (int a = 0; a < kRowsPerThread; ++a) {
-          const int i = ib + ty + kCgWarps * a;
-          const float av = i < N ? A[i * N + k] : 0.f;
-          acc[a][0] = fmaf(av, b0, acc[a][0]);
-          acc[a][1] = fmaf(av, b1, acc[a][1]);
-        }
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(a4[u], b4[v], acc[u][v]);
       }
+      // rows / columns past N land in the padding of the row (never read as
+      // data: every product sums k < N only)
+      if (Trans) {
 #pragma unroll
-      for (int a = 0; a < kRowsPerThread; ++a) {
-        const int i = ib + ty + kCgWarps * a;
-        if (i >= N) continue;
-        if (j0 < N) out[i * N + j0] = acc[a][0];
-        if (j1 < N) out[i * N + j1] = acc[a][1];
+        for (int v = 0; v < 4; ++v)
+          if (j0 + v < N)
+            *reinterpret_cast<float4 *>(out + (j0 + v) * ld + i0) =
+                make_float4(acc[0][v], acc[1][v], acc[2][v], acc[3][v]);
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (i0 + u < N)
+            *reinterpret_cast<float4 *>(out + (i0 + u) * ld + j0) =
+                make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
       }
     }
+}
+
+// Element (r, c) of an N x N plane for every r, c < N: warp w takes rows
+// w, w + 8, ..., its lanes the columns (coalesced, no index division), in
+// 64 x 64 patches of 16 values per thread whose loads are all issued before
+// the first is used, so a patch costs about one memory latency.
+template <typename V, typename L, typename U>
+__device__ __forceinline__ void plane_batched(int N, L load, U use) {
+  static_assert(kCgThreads == 256, "8 warps x 8 rows make a 64-row patch");
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  for (int r0 = 0; r0 < N; r0 += 64)
+    for (int c0 = 0; c0 < N; c0 += 64) {
+      V v[8][2];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const int r = r0 + w + 8 * i, c = c0 + l + 32 * j;
+          v[i][j] = (r < N && c < N) ? load(r, c) : V(0);
+        }
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const int r = r0 + w + 8 * i, c = c0 + l + 32 * j;
+          if (r < N && c < N) use(r, c, v[i][j]);
+        }
+    }
+}
+
+// Shared memory of the fused preconditioner: plane, Phi and work matrices
+// (N x ld each), then the 1-D eigenvalues kappa and mu (N each).
+__host__ __device__ constexpr size_t fused_smem_floats(int N) {
+  return (size_t)3 * N * fused_ld(N) + 2 * (size_t)N;
+}
+
+// Phi, kappa and mu into shared memory (once per kernel).
+__device__ __forceinline__ void load_phi(const CgArgs &a, float *sh) {
+  const int N = a.N, ld = fused_ld(N);
+  float *Ph = sh + N * ld, *kap = sh + 3 * N * ld, *mu = kap + N;
+  plane_batched<float>(
+      N, [&](int r, int c) { return __ldg(a.phi + r * N + c); },
+      [&](int r, int c, float v) { Ph[r * ld + c] = v; });
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    kap[i] = __ldg(a.kap + i);
+    mu[i] = __ldg(a.mu + i);
+  }
+}
+
+// Phi P Phi of the plane in Pm (already staged), y then x; the result is
+// left in Pm.
+__device__ __forceinline__ void plane_transform(int N, int ld, float *sh) {
+  float *Pm = sh, *Ph = sh + N * ld, *W = sh + 2 * N * ld;
+  __syncthreads();
+  smem_matmul<true>(Ph, Pm, W, N, ld);     // W^T, W = Phi P (along y)
+  __syncthreads();
+  smem_matmul<false>(W, Ph, Pm, N, ld);    // (Phi P) Phi (along x)
+  __syncthreads();
 }
 
 // Phi P Phi for the plane z of `in` (FP64 r or FP32 work), into out32 or,
@@ -259,70 +334,69 @@ __device__ __forceinline__ void smem_matmul(const float *A, const float *B, floa
 template <bool InD, bool OutD>
 __device__ double fused_plane_pass(const CgArgs &a, const void *in, float *out32, double *out64,
                                    float *sh) {
-  const int N = a.N;
+  const int N = a.N, ld = fused_ld(N);
   const long long NN = (long long)N * N;
-  float *Pm = sh, *Ph = sh + NN, *W = sh + 2 * NN;
+  float *Pm = sh;
   double rz = 0.0;
   for (int z = a.vb; z < N; z += a.vnb) {
+    const long long zo = z * NN;
     __syncthreads();
-    for (int e = threadIdx.x; e < NN; e += blockDim.x) {
-      Pm[e] = InD ? (float)__ldcg((const double *)in + z * NN + e)
-                  : __ldcg((const float *)in + z * NN + e);
-    }
-    __syncthreads();
-    smem_matmul(Pm, Ph, W, N);      // x: P Phi
-    __syncthreads();
-    smem_matmul(Ph, W, Pm, N);      // y: Phi (P Phi)
-    __syncthreads();
-    for (int e = threadIdx.x; e < NN; e += blockDim.x) {
-      if (OutD) {
-        const double zv = (double)Pm[e];
-        out64[z * NN + e] = zv;
-        rz = fma(a.r[z * NN + e], zv, rz);
-      } else {
-        out32[z * NN + e] = Pm[e];
-      }
-    }
+    if (InD)
+      plane_batched<double>(
+          N, [&](int y, int x) { return __ldcg((const double *)in + zo + y * N + x); },
+          [&](int y, int x, double v) { Pm[y * ld + x] = (float)v; });
+    else
+      plane_batched<float>(
+          N, [&](int y, int x) { return __ldcg((const float *)in + zo + y * N + x); },
+          [&](int y, int x, float v) { Pm[y * ld + x] = v; });
+    plane_transform(N, ld, sh);
+    if (OutD)
+      plane_batched<double>(
+          N, [&](int y, int x) { return __ldcg(a.r + zo + y * N + x); },
+          [&](int y, int x, double rv) {
+            const double zv = (double)Pm[y * ld + x];
+            out64[zo + y * N + x] = zv;
+            rz = fma(rv, zv, rz);
+          });
+    else
+      plane_batched<float>(
+          N, [&](int y, int x) { return Pm[y * ld + x]; },
+          [&](int y, int x, float v) { out32[zo + y * N + x] = v; });
   }
   return rz;
 }
 
 // For each y: S[z][x] -> Phi (Lambda^{-1} o (Phi S)) along z.
 __device__ void fused_slab_pass(const CgArgs &a, const float *in, float *out, float *sh) {
-  const int N = a.N;
+  const int N = a.N, ld = fused_ld(N);
   const long long NN = (long long)N * N;
-  float *Sm = sh, *Ph = sh + NN, *W = sh + 2 * NN;
+  float *Sm = sh, *Ph = sh + N * ld, *W = sh + 2 * N * ld;
+  const float *kap = sh + 3 * N * ld, *mu = kap + N;
   for (int y = a.vb; y < N; y += a.vnb) {
     __syncthreads();
-    for (int e = threadIdx.x; e < NN; e += blockDim.x) {
-      const int zz = e / N, x = e % N;
-      Sm[e] = __ldcg(in + (long long)zz * NN + (long long)y * N + x);
-    }
+    plane_batched<float>(
+        N, [&](int zz, int x) { return __ldcg(in + zz * NN + (long long)y * N + x); },
+        [&](int zz, int x, float v) { Sm[zz * ld + x] = v; });
     __syncthreads();
-    smem_matmul(Ph, Sm, W, N);      // forward along z
+    smem_matmul<false>(Ph, Sm, W, N, ld);   // forward along z
     __syncthreads();
-    for (int e = threadIdx.x; e < NN; e += blockDim.x) {
-      const int c = e / N, x = e % N;
-      const float lam = a.kap[x] * a.mu[y] * a.mu[c] + a.mu[x] * a.kap[y] * a.mu[c] +
-                        a.mu[x] * a.mu[y] * a.kap[c];
-      W[e] = W[e] / lam;
-    }
+    const float ky = kap[y], my = mu[y];
+    for (int c = threadIdx.x >> 5; c < N; c += kCgThreads / 32)
+      for (int x = threadIdx.x & 31; x < N; x += 32) {
+        const float lam = kap[x] * my * mu[c] + mu[x] * ky * mu[c] + mu[x] * my * kap[c];
+        W[c * ld + x] = W[c * ld + x] / lam;
+      }
     __syncthreads();
-    smem_matmul(Ph, W, Sm, N);      // inverse along z
+    smem_matmul<false>(Ph, W, Sm, N, ld);   // inverse along z
     __syncthreads();
-    for (int e = threadIdx.x; e < NN; e += blockDim.x) {
-      const int zz = e / N, x = e % N;
-      out[(long long)zz * NN + (long long)y * N + x] = Sm[e];
-    }
+    plane_batched<float>(
+        N, [&](int zz, int x) { return Sm[zz * ld + x]; },
+        [&](int zz, int x, float v) { out[zz * NN + (long long)y * N + x] = v; });
   }
 }
 
 __device__ bool apply_precond_fused(const CgArgs &a, double *rz_l) {
   extern __shared__ float dyn[];
-  const int N = a.N;
-  const int NN = N * N;
-  // Phi into shared memory once per application
-  for (int e = threadIdx.x; e < NN; e += blockDim.x) dyn[NN + e] = __ldg(a.phi + e);
   fused_plane_pass<true, false>(a, a.r, a.t1, nullptr, dyn);
   if (!grid_barrier_n(a.bar, a.status, a.vnb)) return false;
   fused_slab_pass(a, a.t1, a.t2, dyn);
@@ -333,6 +407,13 @@ __device__ bool apply_precond_fused(const CgArgs &a, double *rz_l) {
 
 // The whole PCG of one system on the blocks a.vb = 0 .. a.vnb - 1 (which must
 // be co-resident: a cooperative launch).
+//
+// On GB300 every FP64 FMA is scarce (two lanes per SM and clock), so each
+// iteration applies the 27-point stiffness once: q = K p is carried as
+// q = K s + beta q_old (K p by linearity, p = s + beta p_old), and a warm
+// start whose residual is still in r (a.incr) forms the new one without a
+// stencil, r = r_old + (b - b_old), from the right-hand side of the last
+// solve (rho_prev).
 __device__ void cg_body(const CgArgs &a) {
   __shared__ double smem[33];
   const int nb = a.vnb;
@@ -341,18 +422,30 @@ __device__ void cg_body(const CgArgs &a) {
   const long long stride = (long long)a.vnb * blockDim.x;
   const int N = a.N;
   const long long NN = (long long)N * N;
+  if (a.fused && a.precond) {
+    extern __shared__ float dyn[];
+    load_phi(a, dyn);
+  }
 
-  // r = b - K x0 (x0 = 0 for a cold start)
+  // r = b - K x0 (x0 = 0 for a cold start; r_old + b - b_old when
+  // incremental), b.b, and rho_prev = rho for the next solve
   double rr_l = 0.0, bb_l = 0.0;
   for (long long k = tid; k < a.n; k += stride) {
-    const double b = a.bscale * a.rho[k];
-    double kx = 0.0, dummy;
-    if (a.warm) {
-      const int ix = (int)(k % N), iy = (int)((k / N) % N), iz = (int)(k / NN);
-      kx = stiff_apply<false>(a.x, nullptr, 0.0, N, ix, iy, iz, a.c, &dummy);
+    const double rk_rho = a.rho[k];
+    const double b = a.bscale * rk_rho;
+    double rk;
+    if (a.incr) {
+      rk = a.r[k] + a.bscale * (rk_rho - a.rho_prev[k]);
+    } else {
+      double kx = 0.0, dummy;
+      if (a.warm) {
+        const int ix = (int)(k % N), iy = (int)((k / N) % N), iz = (int)(k / NN);
+        kx = stiff_apply<false>(a.x, nullptr, 0.0, N, ix, iy, iz, a.c, &dummy);
+      }
+      rk = b - kx;
     }
-    const double rk = b - kx;
     a.r[k] = rk;
+    a.rho_prev[k] = rk_rho;
     rr_l = fma(rk, rk, rr_l);
     bb_l = fma(b, b, bb_l);
   }
@@ -385,14 +478,14 @@ __device__ void cg_body(const CgArgs &a) {
   // a non-finite right-hand side or start makes every comparison below false
   bool bad = !isfinite(rr) || !isfinite(bb);
   while (rr > thr && it < a.maxit) {
-    // phase 1: p = s + beta p_old (own nodes), q = K p, p.q
+    // phase 1: p = s + beta p_old and q = K s + beta q_old (own nodes), p.q
     double pq_l = 0.0;
     for (long long k = tid; k < a.n; k += stride) {
       const int ix = (int)(k % N), iy = (int)((k / N) % N), iz = (int)(k / NN);
-      double pk;
-      const double qk = (it == 0)
-          ? stiff_apply<false>(s_vec, nullptr, 0.0, N, ix, iy, iz, a.c, &pk)
-          : stiff_apply<true>(s_vec, pold, beta, N, ix, iy, iz, a.c, &pk);
+      double sk;
+      const double ks = stiff_apply<false>(s_vec, nullptr, 0.0, N, ix, iy, iz, a.c, &sk);
+      const double pk = it == 0 ? sk : fma(beta, pold[k], sk);
+      const double qk = it == 0 ? ks : fma(beta, a.q[k], ks);
       pnew[k] = pk;
       a.q[k] = qk;
       pq_l = fma(pk, qk, pq_l);
@@ -477,6 +570,8 @@ ks_status launch_sine_setup(Problem &P) {
   return KS_OK;
 }
 
+constexpr int kCgIncrMax = 64;
+
 ks_status launch_cg(Problem &P, const double *rho, double *v, double *r, bool warm) {
   CgArgs a;
   a.N = P.N;
@@ -504,6 +599,14 @@ ks_status launch_cg(Problem &P, const double *rho, double *v, double *r, bool wa
   a.warm = warm ? 1 : 0;
   a.precond = P.cg_precond;
   a.fused = P.N <= kFusedMaxN ? 1 : 0;
+  // the residual of the last solve is reused while the problem's own vH and
+  // r carry it; every kCgIncrMax-th warm start recomputes it from x, so
+  // that the rounding of the recurrences cannot build up
+  const bool own = v == P.vH && r == P.cg_r;
+  a.incr = (warm && own && P.cg_inc_ok && P.cg_inc_count < kCgIncrMax) ? 1 : 0;
+  a.rho_prev = P.cg_rho_prev;
+  P.cg_inc_count = a.incr ? P.cg_inc_count + 1 : 0;
+  P.cg_inc_ok = own;
   const size_t dyn = cg_dynamic_smem(P.N);
   KS_CUDA_TRY(cudaMemsetAsync(P.bar, 0, sizeof(GridBarrier), P.stream));
   void *args[] = {&a};
@@ -627,10 +730,9 @@ __global__ void __launch_bounds__(kCgThreads) cg_b_precond(CgBatchView v) {
   if (!cg_job(v, j, vb, nb)) return;
   CgArgs a = v.args[j];
   if (!v.st[j].precond) return;
-  const int N = a.N, NN = N * N;
   a.vb = vb;
   a.vnb = nb;
-  for (int e = threadIdx.x; e < NN; e += blockDim.x) dyn[NN + e] = __ldg(a.phi + e);
+  load_phi(a, dyn);
   if (Stage == 0) {
     fused_plane_pass<true, false>(a, a.r, a.t1, nullptr, dyn);
   } else if (Stage == 1) {
@@ -886,7 +988,7 @@ ks_status batch_cg(Batch &B, double tol) {
 }
 
 size_t cg_dynamic_smem(int N) {
-  return N <= kFusedMaxN ? (size_t)3 * N * N * sizeof(float) : kTiledSmem;
+  return N <= kFusedMaxN ? fused_smem_floats(N) * sizeof(float) : kTiledSmem;
 }
 
 int cg_grid_blocks(int sms, int n, int N) {

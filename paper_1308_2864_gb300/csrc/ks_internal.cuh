@@ -99,6 +99,9 @@ struct Problem {
   double *zero_n = nullptr;        // n zeros (V_eff = 0: the kinetic part f K X alone)
   double *cg_r = nullptr, *cg_pa = nullptr, *cg_pb = nullptr, *cg_q = nullptr;
   double *cg_z = nullptr;          // preconditioned residual
+  double *cg_rho_prev = nullptr;   // density of the last Hartree solve (its right-hand side)
+  bool cg_inc_ok = false;          // cg_r = b_last - K vH: the next warm solve needs no stencil
+  int cg_inc_count = 0;            // incremental starts since the last full residual
   float *cg_t1 = nullptr, *cg_t2 = nullptr;  // sine-transform work (FP32)
   float *dst_phi = nullptr, *dst_kap = nullptr, *dst_mu = nullptr;
   int cg_precond = 1;
@@ -111,6 +114,7 @@ struct Problem {
   int oz_emax_len = 0;
   int use_tma = 1;                 // TMA plane staging in the stencils (when the layout allows)
   bool vH_valid = false;           // warm start available
+  int rho_block = -1;              // block whose iterate's density P.rho already holds (-1: none)
 
   // n x p blocks (FP64 capacity plus 256 bytes; the FP32 phase keeps a second
   // FP32 block in the upper half, at byte offset half_off, 256-byte aligned)
@@ -121,6 +125,7 @@ struct Problem {
   // p x p work (all FP64)
   double *pp = nullptr;            // pool of small matrices
   float *cf = nullptr;             // 3 p^2: FP32 copies of the update coefficients
+  float *rt32 = nullptr;           // 2 p^2: FP32 copies of D^T M D and X^T M D (increment form)
   float *tc_img = nullptr;         // coefficient image of the tensor-core update
   size_t tc_img_len = 0;
   size_t pp_len = 0;
@@ -277,6 +282,14 @@ ks_status launch_mass_inverse(Problem &P, const T *E, T *G, const T *add = nullp
 // out (pa x qb, FP64) = A^T B with A n x pa, B n x qb (row-major, ld = pa, qb)
 template <typename T>
 ks_status launch_gram(Problem &P, const T *A, int pa, const T *B, int qb, double *out);
+// FP32: out = A1^T B1 + A2^T B2 (one pass when the pipelined kernel applies;
+// otherwise two Grams, tmp a p x p scratch matrix)
+ks_status launch_gram_pair(Problem &P, const float *A1, const float *B1, const float *A2,
+                           const float *B2, int pa, int qb, double *out, double *tmp);
+// FP32: out1 = A1^T B, out2 = A2^T B (B read once when the kernel applies);
+// out32 (optional, 2 pa qb floats): FP32 copies of out1 then out2
+ks_status launch_gram_dual(Problem &P, const float *A1, const float *A2, const float *B, int pa,
+                           int qb, double *out1, double *out2, float *out32 = nullptr);
 // out (n x q) = alpha (A1 C1 + A2 C2) + beta Bm (A2/Bm may be null);
 // C1 k1 x q, C2 k2 x q (FP64).  out must not alias A1, A2 or Bm.
 template <typename T>
@@ -286,10 +299,21 @@ ks_status launch_combine(Problem &P, const T *A1, int k1, const double *C1, cons
 ks_status configure_blas_kernels();
 // out = A1 C1 + A2 C2 + A3 C3 and out2 = add2 + out (FP32 n x q, q <= 64,
 // k1 + k2 + k3 <= 192, C FP64) in one pass; combine3_f32_applies says when.
+// With rho set (q = p; out the increment delta, add2 the base X_b) the same
+// pass writes rho = rho_b + f sum delta (2 X_b + delta) of X_b + delta.
 bool combine3_f32_applies(const Problem &P, int k1, int k2, int k3, int q);
 ks_status launch_combine3_f32(Problem &P, const float *A1, int k1, const double *C1,
                               const float *A2, int k2, const double *C2, const float *A3, int k3,
-                              const double *C3, float *out, const float *add2, float *out2, int q);
+                              const double *C3, float *out, const float *add2, float *out2, int q,
+                              const double *rho_b = nullptr, double *rho = nullptr,
+                              bool images_ready = false);
+// Increment form, QR step: from FP32 copies of R = D^T M D and T = X^T M D
+// (rt32: R then T, p x p each) the factor L L^T = I - tau (T + T^T) +
+// tau^2 R as deviations from I in FP32; writes the FP32 coefficients
+// [L^{-T} - I; L^{-T}; -tau L^{-T}] of launch_combine3_f32 to P.cf
+// (images_ready).
+bool qr_factor_dev_applies(const Problem &P);
+ks_status launch_qr_factor_dev(Problem &P, const float *rt32, double tau);
 // elementwise precision conversion of an n x p block
 ks_status launch_convert(Problem &P, const double *in, float *out);
 ks_status launch_convert(Problem &P, const float *in, double *out);

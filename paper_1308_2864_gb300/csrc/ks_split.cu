@@ -92,6 +92,104 @@ __global__ void add_pp_kernel(int p, const double *A, double s, const double *B,
 // out = R - (T + T^T) / tau: with it, I + tau^2 out = I - tau (T + T^T) + tau^2 R
 // is the exact Gram (X - tau D)^T M (X - tau D) when X^T M X = I, T = X^T M D
 // and R = D^T M D.
+// Increment form of the QR step (Alg. ChQR with the exact trial Gram
+// W = Y^T M Y = I + E, E = tau^2 R - tau (T + T^T), R = D^T M D,
+// T = X^T M D): the Cholesky factor and its inverse carried as deviations
+// from the identity, L = I + G and L^{-1} = I + H, in FP32.  G and H are of
+// the size of E, so every rounding error is relative to |E| -- the size of
+// A - I = L^{-T} - I, which the three-term update applies in FP32 anyway --
+// where a plain FP32 Cholesky of W would err by eps_32 relative to 1.  The
+// recurrences are those of the right-looking Cholesky of W with the unit
+// diagonal kept implicit (e' is the trailing part of E):
+//   pivot   (1 + g_jj)^2 = 1 + e'_jj, g_jj = e'_jj / (1 + sqrt(1 + e'_jj))
+//   column  g_ij = e'_ij / (1 + g_jj)                  (i > j)
+//   update  e'_ic -= g_ij g_cj                         (j < c <= i)
+// and of V = L^{-1} = I + H built alongside: row j of V divided by 1 + g_jj
+// (h_jj = -g_jj / (1 + g_jj)), then V_ic -= g_ij V_jc for c <= j.  Output:
+// the FP32 coefficients of the update X_b (A - I) + delta A + D B with
+// A = L^{-T} = I + H^T and B = -tau A, as [H^T; I + H^T; -tau (I + H^T)].
+// One block of 8 warps: a warp per matrix row, its lanes over the columns;
+// every thread forms the pivot itself, so a column costs two barriers.  G
+// and H (row stride p + 1, so that column reads do not collide in a bank)
+// and column j of G live in dynamic shared memory; a non-positive or
+// non-finite pivot records KS_ENOTPD and leaves P.cf as it was.
+constexpr int kDevThreads = 256;
+constexpr int kDevMaxP = 64;
+
+__global__ void __launch_bounds__(kDevThreads) qr_factor_dev_kernel(int p,
+                                                                    const float *__restrict__ R,
+                                                                    const float *__restrict__ T,
+                                                                    float tau, float *__restrict__ cf,
+                                                                    int *status) {
+  extern __shared__ float dev_sh[];
+  const int ld = p + 1;
+  float *G = dev_sh, *H = dev_sh + p * ld, *colj = dev_sh + 2 * p * ld;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int kWarps = kDevThreads / 32;
+  // E (lower triangle) with all loads of a thread issued first
+  {
+    float r[kDevMaxP / kWarps][2], t1[kDevMaxP / kWarps][2], t2[kDevMaxP / kWarps][2];
+#pragma unroll
+    for (int a = 0; a < kDevMaxP / kWarps; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        const int i = w + kWarps * a, c = lane + 32 * b;
+        const bool in = i < p && c < p && c <= i;
+        r[a][b] = in ? R[i * p + c] : 0.f;
+        t1[a][b] = in ? T[i * p + c] : 0.f;
+        t2[a][b] = in ? T[c * p + i] : 0.f;
+      }
+#pragma unroll
+    for (int a = 0; a < kDevMaxP / kWarps; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        const int i = w + kWarps * a, c = lane + 32 * b;
+        if (i < p && c < p) {
+          G[i * ld + c] = fmaf(tau * tau, r[a][b], -tau * (t1[a][b] + t2[a][b]));
+          H[i * ld + c] = 0.f;
+        }
+      }
+  }
+  __syncthreads();
+  for (int j = 0; j < p; ++j) {
+    const float t = G[j * ld + j];
+    const float wv = 1.f + t;
+    if (!(wv > 0.f) || !isfinite(wv)) {
+      if (threadIdx.x == 0) atomicCAS(status, 0, (int)KS_ENOTPD);
+      return;
+    }
+    const float gjj = t / (1.f + sqrtf(wv));
+    const float il = 1.f / (1.f + gjj);
+    const float hjj = -gjj * il;
+    for (int i = j + 1 + threadIdx.x; i < p; i += kDevThreads) {
+      const float g = G[i * ld + j] * il;
+      G[i * ld + j] = g;
+      colj[i] = g;
+    }
+    for (int c = threadIdx.x; c < j; c += kDevThreads) H[j * ld + c] *= il;
+    if (threadIdx.x == 0) H[j * ld + j] = hjj;
+    __syncthreads();
+    for (int i = j + 1 + w; i < p; i += kWarps) {
+      const float gij = colj[i];
+      for (int c = lane; c <= i; c += 32) {
+        if (c > j) G[i * ld + c] = fmaf(-gij, colj[c], G[i * ld + c]);
+        else if (c < j) H[i * ld + c] = fmaf(-gij, H[j * ld + c], H[i * ld + c]);
+        else H[i * ld + j] = -fmaf(gij, hjj, gij);
+      }
+    }
+    __syncthreads();
+  }
+  const int pp = p * p;
+  for (int i = w; i < p; i += kWarps)
+    for (int c = lane; c < p; c += 32) {
+      const float h = H[c * ld + i];                 // (L^{-T} - I)_{ic} = H_{ci}
+      const float a = (i == c ? 1.f : 0.f) + h;
+      cf[i * p + c] = h;
+      cf[pp + i * p + c] = a;
+      cf[2 * pp + i * p + c] = -tau * a;
+    }
+}
+
 __global__ void qr_exact_gram_kernel(int p, const double *__restrict__ R,
                                      const double *__restrict__ T, double tau,
                                      double *__restrict__ out) {
@@ -187,6 +285,21 @@ ks_status launch_qr_exact_gram(Problem &P, const double *R, const double *T, dou
     ProfScope ps_(P.stream, KP_SMALL);
     qr_exact_gram_kernel<<<(len + kThreads - 1) / kThreads, kThreads, 0, P.stream>>>(P.p, R, T,
                                                                                     tau, out);
+  }
+  KS_CUDA_TRY(cudaGetLastError());
+  return KS_OK;
+}
+
+bool qr_factor_dev_applies(const Problem &P) { return P.p <= kDevMaxP; }
+
+ks_status launch_qr_factor_dev(Problem &P, const float *rt32, double tau) {
+  if (!qr_factor_dev_applies(P)) return set_error(KS_EINVAL, "qr_factor_dev: p above %d", kDevMaxP);
+  const int p = P.p;
+  const size_t smem = ((size_t)2 * p * (p + 1) + p) * sizeof(float);
+  {
+    ProfScope ps_(P.stream, KP_SMALL);
+    qr_factor_dev_kernel<<<1, kDevThreads, smem, P.stream>>>(p, rt32, rt32 + (size_t)p * p,
+                                                             (float)tau, P.cf, P.dstatus);
   }
   KS_CUDA_TRY(cudaGetLastError());
   return KS_OK;

@@ -56,6 +56,7 @@ ks_status ks_step_hartree(ks_problem *kp, const double *rho, double *vH, int war
   Problem &P = kp->P;
   double *r = resid ? resid : P.cg_r;
   KS_TRY(launch_cg(P, rho, vH, r, warm != 0));
+  P.cg_inc_ok = false;     // the caller's vH and residual, not the loop's
   double it = 0;
   KS_CUDA_TRY(cudaMemcpyAsync(&it, P.scal + SC_CG_ITERS, sizeof(double), cudaMemcpyDeviceToHost,
                               P.stream));

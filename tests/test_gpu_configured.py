@@ -146,7 +146,10 @@ def test_c1_fp64_converged_matches_oracle(c1_golden):
     Xg = host(X)
     model, lam, rho_s = _invariants(s, Xg, c1_golden)
     assert ost.ortho_error(model, Xg) < 1e-12
-    np.testing.assert_allclose(lam, c1_golden["lambda_eigs"], rtol=0, atol=1e-6)
+    # the energy is second order in the distance to the minimiser, the
+    # multipliers and the energy terms first order: two endpoints that both
+    # stop at ||D||_M <= 1e-6 agree in Lambda to a few 1e-6, like the parts
+    np.testing.assert_allclose(lam, c1_golden["lambda_eigs"], rtol=0, atol=1e-5)
     assert rel_err(rho_s, c1_golden["rho_values"]) <= 1e-4
 
 
@@ -167,5 +170,5 @@ def test_c1_mixed_converged_matches_oracle(c1_golden):
     assert abs(r["E"] - c1_golden["E"]) <= 1e-8
     Xg = host(X)
     model, lam, rho_s = _invariants(s, Xg, c1_golden)
-    np.testing.assert_allclose(lam, c1_golden["lambda_eigs"], rtol=0, atol=1e-6)
+    np.testing.assert_allclose(lam, c1_golden["lambda_eigs"], rtol=0, atol=1e-5)
     assert rel_err(rho_s, c1_golden["rho_values"]) <= 1e-4
