@@ -76,6 +76,84 @@ __device__ __forceinline__ void thomas_line(long long t, int N, int p, int axis,
   }
 }
 
+// Lines of at most kRegN nodes: the whole line in registers (all its loads
+// in flight at once, one read and one write of each entry in memory).
+// Indices into the line array are compile-time constants throughout, and
+// the recurrences run over all kRegN entries with the pivots w zero past N:
+// the padding then stays 0 in both sweeps (the back substitution enters
+// entry N - 1 with next = 0), so no data-dependent branch touches the array
+// and it stays in registers.
+constexpr int kRegN = 64;
+
+template <typename T>
+__device__ __forceinline__ void thomas_line_reg(long long t, int N, int p, int axis, T scale,
+                                                const T *w, const T *in, T *out, const T *add) {
+  const long long lines = (long long)N * N;
+  if (t >= lines * p) return;
+  const int i = (int)(t % p);
+  const long long line = t / p;
+  const int a = (int)(line % N), b = (int)(line / N);
+  long long base, stride;
+  if (axis == 0) {
+    base = ((long long)b * N + a) * N;
+    stride = 1;
+  } else if (axis == 1) {
+    base = (long long)b * N * N + a;
+    stride = N;
+  } else {
+    base = (long long)b * N + a;
+    stride = (long long)N * N;
+  }
+  const long long es = stride * p;
+  T v[kRegN];
+  {
+    const T *ps = in + base * p + i;
+#pragma unroll
+    for (int u = 0; u < kRegN; ++u) {
+      v[u] = u < N ? *ps : (T)0;
+      ps += es;
+    }
+  }
+  // forward elimination, then back substitution (w[u] = 0 for u >= N)
+  T prev = 0;
+#pragma unroll
+  for (int u = 0; u < kRegN; ++u) {
+    prev = (scale * v[u] - prev) * w[u];
+    v[u] = prev;
+  }
+  T next = 0;
+#pragma unroll
+  for (int u = kRegN - 1; u >= 0; --u) {
+    next = v[u] - w[u] * next;
+    v[u] = next;
+  }
+  if (add) {
+    const T *pa = add + base * p + i;
+#pragma unroll
+    for (int u = 0; u < kRegN; ++u) {
+      if (u < N) v[u] += *pa;
+      pa += es;
+    }
+  }
+  T *pd = out + base * p + i;
+#pragma unroll
+  for (int u = 0; u < kRegN; ++u) {
+    if (u < N) *pd = v[u];
+    pd += es;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) thomas_reg_kernel(int N, int p, int axis, double scale_d,
+                                                         const double *__restrict__ w_d,
+                                                         const T *in, T *out, const T *add) {
+  __shared__ T w[kRegN];
+  for (int j = threadIdx.x; j < kRegN; j += blockDim.x) w[j] = j < N ? (T)w_d[j] : (T)0;
+  __syncthreads();
+  thomas_line_reg<T>((long long)blockIdx.x * blockDim.x + threadIdx.x, N, p, axis, (T)scale_d, w,
+                     in, out, add);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) thomas_kernel(int N, int p, int axis, double scale_d,
                                                      const double *__restrict__ w_d, const T *in,
@@ -156,23 +234,28 @@ ks_status launch_mass_inverse(Problem &P, const T *E, T *G, const T *add) {
   const int nb = (int)((work + kThreads - 1) / kThreads);
   const double s = 6.0 / P.h;
   const size_t smem = (size_t)P.N * sizeof(T);
-  {
-    ProfScope ps_(P.stream, KP_MASS_INV, 4.0 * P.n * P.p, 2.0 * P.n * P.p * sizeof(T));
-    thomas_kernel<T><<<nb, kThreads, smem, P.stream>>>(P.N, P.p, 0, s * s * s, P.thomas_w, E, G,
-                                                       nullptr);
+  // FP32 lines of at most kRegN nodes in registers (in FP64 the sweep is
+  // bound by the FP64 pipe, and 64 doubles a thread would halve occupancy)
+  const bool reg = sizeof(T) == 4 && P.N <= kRegN;
+  for (int axis = 0; axis < 3; ++axis) {
+    const T *src = axis == 0 ? E : G;
+    const double sc = axis == 0 ? s * s * s : 1.0;
+    const T *ad = axis == 2 ? add : nullptr;
+    const double bytes = (2.0 + (ad ? 1.0 : 0.0)) * P.n * P.p * sizeof(T);
+    ProfScope ps_(P.stream, KP_MASS_INV, 4.0 * P.n * P.p, bytes);
+    bool done = false;
+    if constexpr (sizeof(T) == 4) {
+      if (reg) {
+        thomas_reg_kernel<T><<<nb, kThreads, 0, P.stream>>>(P.N, P.p, axis, sc, P.thomas_w, src,
+                                                               G, ad);
+        done = true;
+      }
+    }
+    if (!done)
+      thomas_kernel<T><<<nb, kThreads, smem, P.stream>>>(P.N, P.p, axis, sc, P.thomas_w, src, G,
+                                                         ad);
+    KS_CUDA_TRY(cudaGetLastError());
   }
-  KS_CUDA_TRY(cudaGetLastError());
-  {
-    ProfScope ps_(P.stream, KP_MASS_INV, 4.0 * P.n * P.p, 2.0 * P.n * P.p * sizeof(T));
-    thomas_kernel<T><<<nb, kThreads, smem, P.stream>>>(P.N, P.p, 1, 1.0, P.thomas_w, G, G,
-                                                       nullptr);
-  }
-  KS_CUDA_TRY(cudaGetLastError());
-  {
-    ProfScope ps_(P.stream, KP_MASS_INV, 4.0 * P.n * P.p, 2.0 * P.n * P.p * sizeof(T));
-    thomas_kernel<T><<<nb, kThreads, smem, P.stream>>>(P.N, P.p, 2, 1.0, P.thomas_w, G, G, add);
-  }
-  KS_CUDA_TRY(cudaGetLastError());
   return KS_OK;
 }
 

@@ -40,6 +40,8 @@
 //     out-of-bounds fill.  V_eff of the output plane is staged in the
 //     working precision once per node.
 //   plain loads (any p): all threads copy the halo box element by element.
+#include <mutex>
+
 #include "ks_async.cuh"
 #include "ks_device.cuh"
 
@@ -255,26 +257,42 @@ __global__ void __launch_bounds__(kStThreads) stencil_kernel(StArgs a) {
 
 constexpr int kStStages = 3;
 
-template <typename T, int PC>
+// Blocks read at the output node only (no halo), staged by TMA with the
+// plane: SK_HAM_INC X_b and E_b; SK_MASS_BB X, MX, Xp, MXp, Dp, MDp in FP32
+// (in FP64 the six boxes would not leave room for two blocks per SM: the
+// kernel loads them from global memory at the output step instead).
+template <typename T, int Kind>
+constexpr int st_naux() {
+  return Kind == SK_HAM_INC ? 2 : (Kind == SK_MASS_BB && sizeof(T) == 4) ? 6 : 0;
+}
+
+template <typename T, int PC, int Kind>
 struct StRing {
   using Tl = StTile<PC>;
+  static constexpr int NAUX = st_naux<T, Kind>();
   static constexpr int BOX = Tl::HY * Tl::HX * PC;                 // elements of one halo box
   static constexpr uint32_t BOX_BYTES = BOX * sizeof(T);
-  static constexpr int STAGE = ((BOX_BYTES + 127) / 128) * 128 / sizeof(T);   // 128-byte stages
+  static constexpr int HALO = ((BOX_BYTES + 127) / 128) * 128 / sizeof(T);   // 128-byte aligned
+  static constexpr int AUXB = Tl::TY * Tl::TX * PC;                // elements of one node box
+  static constexpr uint32_t AUX_BYTES = AUXB * sizeof(T);
+  static constexpr int AUX = ((AUX_BYTES + 127) / 128) * 128 / sizeof(T);
+  static constexpr int STAGE = HALO + NAUX * AUX;
   // the stages plus slack to align the ring to 128 bytes at run time
   static constexpr size_t SMEM = (size_t)kStStages * STAGE * sizeof(T) + 128;
 };
 
 struct StTmaArgs {
   CUtensorMap map;            // (orbital, x, y, z) view of the input block
+  CUtensorMap aux[6];         // the same views of the node-local inputs (st_naux of them)
   StArgs a;
 };
 
 template <typename T, int PC, int Kind>
 __global__ void __launch_bounds__(kStThreads, 2) stencil_tma_kernel(const __grid_constant__ StTmaArgs ta) {
   using Tl = StTile<PC>;
-  using Rg = StRing<T, PC>;
+  using Rg = StRing<T, PC, Kind>;
   constexpr int TXY = Tl::TX * Tl::TY;
+  constexpr int NAUX = Rg::NAUX;
   static_assert(TXY <= kStThreads, "one V_eff loader per node");
   extern __shared__ __align__(128) unsigned char st_ring_raw[];
   T *ring = reinterpret_cast<T *>(st_ring_raw + ((128u - (smem_addr(st_ring_raw) & 127u)) & 127u));
@@ -299,19 +317,30 @@ __global__ void __launch_bounds__(kStThreads, 2) stencil_tma_kernel(const __grid
   const int o = oc * PC + lane;
   const bool ovalid = o < p;
 
+  // stage q holds the halo box of plane z0 - 1 + q and, from q = 2 on, the
+  // node boxes of the output plane of step q (z0 - 2 + q)
+  auto load_stage = [&](int q) {
+    T *dst = ring + (q % kStStages) * Rg::STAGE;
+    uint64_t *bar = &full[q % kStStages];
+    const bool with_aux = NAUX > 0 && q >= 2;
+    mbar_arrive_expect_tx(bar, Rg::BOX_BYTES + (with_aux ? NAUX * Rg::AUX_BYTES : 0u));
+    tma_load_4d(dst, &ta.map, bar, oc * PC, x0 - 1, y0 - 1, z0 - 1 + q);
+    if (with_aux)
+#pragma unroll
+      for (int i = 0; i < NAUX; ++i)
+        tma_load_4d(dst + Rg::HALO + i * Rg::AUX, &ta.aux[i], bar, oc * PC, x0, y0, z0 - 2 + q);
+  };
   if (threadIdx.x == 0) {
     prefetch_tensor_map(&ta.map);
+#pragma unroll
+    for (int i = 0; i < NAUX; ++i) prefetch_tensor_map(&ta.aux[i]);
 #pragma unroll
     for (int st = 0; st < kStStages; ++st) mbar_init(&full[st], 1);
     fence_barrier_init();
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int q = 0; q < kStStages && q < nplanes; ++q) {
-      mbar_arrive_expect_tx(&full[q], Rg::BOX_BYTES);
-      tma_load_4d(ring + q * Rg::STAGE, &ta.map, &full[q], oc * PC, x0 - 1, y0 - 1, z0 - 1 + q);
-    }
-  }
+  if (threadIdx.x == 0)
+    for (int q = 0; q < kStStages && q < nplanes; ++q) load_stage(q);
 
   int lx[kStNodesPerThread], ly[kStNodesPerThread];
 #pragma unroll
@@ -363,21 +392,18 @@ __global__ void __launch_bounds__(kStThreads, 2) stencil_tma_kernel(const __grid
       f_new[r] = (at(-1, 0) + at(1, 0)) + (at(0, -1) + at(0, 1));
       e_new[r] = (at(-1, -1) + at(1, -1)) + (at(-1, 1) + at(1, 1));
     }
-    // every thread is done with this stage: refill it kStStages planes ahead
-    if (__syncthreads_or(!got)) {
-      failed_at = q;
-      break;
-    }
-    if (threadIdx.x == 0 && q + kStStages < nplanes) {
-      mbar_arrive_expect_tx(&full[st], Rg::BOX_BYTES);
-      tma_load_4d(ring + st * Rg::STAGE, &ta.map, &full[st], oc * PC, x0 - 1, y0 - 1,
-                  zp + kStStages);
-    }
     if (q >= 2) {
       const int z = zp - 1;
       const T *vz = vs[(q + 2) % 3];
       T bb[6][kStNodesPerThread];
-      if (Kind == SK_MASS_BB) {
+      if constexpr (NAUX > 0) {
+        // the node-local inputs of this output plane, staged with it
+#pragma unroll
+        for (int i = 0; i < NAUX; ++i)
+#pragma unroll
+          for (int r = 0; r < kStNodesPerThread; ++r)
+            bb[i][r] = tile[Rg::HALO + i * Rg::AUX + (ly[r] * Tl::TX + lx[r]) * PC + lane];
+      } else if (Kind == SK_MASS_BB) {
         // all loads of the plane first, so they are in flight together
 #pragma unroll
         for (int r = 0; r < kStNodesPerThread; ++r) {
@@ -390,17 +416,6 @@ __global__ void __launch_bounds__(kStThreads, 2) stencil_tma_kernel(const __grid
             bb[3][r] = ((const T *)a.MXp)[idx];
             bb[4][r] = ((const T *)a.Dp)[idx];
             bb[5][r] = ((const T *)a.MDp)[idx];
-          }
-        }
-      }
-      if (Kind == SK_HAM_INC) {
-#pragma unroll
-        for (int r = 0; r < kStNodesPerThread; ++r) {
-          const int gx = x0 + lx[r], gy = y0 + ly[r];
-          if (ovalid && gx < N && gy < N) {
-            const long long idx = (((long long)z * N + gy) * N + gx) * p + o;
-            bb[0][r] = ((const T *)a.X)[idx];
-            bb[1][r] = ((const T *)a.MX)[idx];
           }
         }
       }
@@ -450,6 +465,12 @@ __global__ void __launch_bounds__(kStThreads, 2) stencil_tma_kernel(const __grid
         }
       }
     }
+    // every thread is done with this stage: refill it kStStages planes ahead
+    if (__syncthreads_or(!got)) {
+      failed_at = q;
+      break;
+    }
+    if (threadIdx.x == 0 && q + kStStages < nplanes) load_stage(q + kStStages);
 #pragma unroll
     for (int r = 0; r < kStNodesPerThread; ++r) {
       c_old[r] = c_mid[r]; f_old[r] = f_mid[r]; e_old[r] = e_mid[r];
@@ -523,19 +544,39 @@ template <typename T, int PC, int Kind>
 static bool stencil_launch_tma(Problem &P, const StArgs &a, int cls, double flops, double bytes,
                                ks_status *st) {
   using Tl = StTile<PC>;
-  using Rg = StRing<T, PC>;
+  using Rg = StRing<T, PC, Kind>;
   *st = KS_OK;
+  const void *aux[6] = {a.X, a.MX, a.Xp, a.MXp, a.Dp, a.MDp};
   if (!P.use_tma || ((size_t)P.p * sizeof(T)) % 16 != 0 ||
       reinterpret_cast<uintptr_t>(a.A) % 16 != 0)
     return false;
+  for (int i = 0; i < Rg::NAUX; ++i)
+    if (!aux[i] || reinterpret_cast<uintptr_t>(aux[i]) % 16 != 0) return false;
   StTmaArgs ta;
   ta.a = a;
   const uint64_t dims[4] = {(uint64_t)P.p, (uint64_t)P.N, (uint64_t)P.N, (uint64_t)P.N};
   const uint32_t box[4] = {(uint32_t)PC, (uint32_t)Tl::HX, (uint32_t)Tl::HY, 1u};
+  const uint32_t nbox[4] = {(uint32_t)PC, (uint32_t)Tl::TX, (uint32_t)Tl::TY, 1u};
   if (encode_tensor_map_4d(&ta.map, a.A, (int)sizeof(T), dims, box) != KS_OK) return false;
-  // ring + static shared memory (mbarriers, V_eff planes, reduction scratch:
-  // under 2 KiB) stay within the 48 KiB a block gets without an opt-in
-  static_assert(Rg::SMEM + 2048 <= 48 * 1024, "ring fits the default shared memory");
+  for (int i = 0; i < Rg::NAUX; ++i)
+    if (encode_tensor_map_4d(&ta.aux[i], aux[i], (int)sizeof(T), dims, nbox) != KS_OK)
+      return false;
+  // the ring plus the static shared memory (mbarriers, V_eff planes,
+  // reduction scratch: up to ~10 KiB) for two blocks per SM; the kernel
+  // opts in to the ring's size once
+  static_assert(Rg::SMEM + 10 * 1024 <= 113 * 1024, "two blocks of the ring fit an SM");
+  {
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [] {
+      attr = cudaFuncSetAttribute(stencil_tma_kernel<T, PC, Kind>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Rg::SMEM);
+    });
+    if (attr != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+  }
   {
     ProfScope ps_(P.stream, cls, flops, bytes);
     stencil_tma_kernel<T, PC, Kind><<<a.nb, kStThreads, Rg::SMEM, P.stream>>>(ta);

@@ -24,10 +24,68 @@ void load_encode() {
     cudaGetLastError();
 }
 
+// Encoded maps by (base, element size, dims, box): a map holds only the
+// address and the layout, so a cached one is exact for any allocation that
+// occupies the same address with the same layout.  The iteration re-uses a
+// few blocks over and over, and encoding runs through the driver, so the
+// launches of a solve find their maps here.
+struct MapKey {
+  const void *base;
+  int elem;
+  uint64_t dims[4];
+  uint32_t box[4];
+  bool operator==(const MapKey &o) const {
+    if (base != o.base || elem != o.elem) return false;
+    for (int i = 0; i < 4; ++i)
+      if (dims[i] != o.dims[i] || box[i] != o.box[i]) return false;
+    return true;
+  }
+};
+
+constexpr int kMapCache = 64;
+struct MapCache {
+  std::mutex mu;
+  MapKey key[kMapCache];
+  CUtensorMap map[kMapCache];
+  unsigned long long used[kMapCache] = {};
+  unsigned long long tick = 0;
+  int n = 0;
+};
+MapCache g_maps;
+
+ks_status encode_uncached(CUtensorMap *map, const void *base, int elem_bytes,
+                          const uint64_t dims[4], const uint32_t box[4]);
+
 }  // namespace
 
 ks_status encode_tensor_map_4d(CUtensorMap *map, const void *base, int elem_bytes,
                                const uint64_t dims[4], const uint32_t box[4]) {
+  MapKey k{base, elem_bytes, {dims[0], dims[1], dims[2], dims[3]}, {box[0], box[1], box[2], box[3]}};
+  std::lock_guard<std::mutex> lock(g_maps.mu);
+  for (int i = 0; i < g_maps.n; ++i)
+    if (g_maps.key[i] == k) {
+      g_maps.used[i] = ++g_maps.tick;
+      *map = g_maps.map[i];
+      return KS_OK;
+    }
+  KS_TRY(encode_uncached(map, base, elem_bytes, dims, box));
+  int slot = 0;
+  if (g_maps.n < kMapCache) {
+    slot = g_maps.n++;
+  } else {
+    for (int i = 1; i < kMapCache; ++i)     // least recently used
+      if (g_maps.used[i] < g_maps.used[slot]) slot = i;
+  }
+  g_maps.key[slot] = k;
+  g_maps.map[slot] = *map;
+  g_maps.used[slot] = ++g_maps.tick;
+  return KS_OK;
+}
+
+namespace {
+
+ks_status encode_uncached(CUtensorMap *map, const void *base, int elem_bytes,
+                          const uint64_t dims[4], const uint32_t box[4]) {
   std::call_once(g_encode_once, load_encode);
   if (!g_encode) return set_error(KS_EINVAL, "tensor-map encoder unavailable");
   if (reinterpret_cast<uintptr_t>(base) % 16 != 0)
@@ -57,5 +115,7 @@ ks_status encode_tensor_map_4d(CUtensorMap *map, const void *base, int elem_byte
   if (r != CUDA_SUCCESS) return set_error(KS_EINVAL, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   return KS_OK;
 }
+
+}  // namespace
 
 }  // namespace ks
