@@ -72,7 +72,9 @@ ks_status ks_step_gram(ks_problem *prob, const double *A, int pa, const double *
 
 /* Tensor-core use of the FP32 phase: 0 never, 1 (default) for products of
  * at least 256 x 256 columns, 2 always (pa, qb, q > 8 for the Gram, q > 32
- * for the update). */
+ * for the update), 3 as 1 plus the narrow updates (q <= 64, q a multiple
+ * of 4, K <= 192, 16-byte-aligned blocks: the retraction's update and the
+ * projected gradient at p <= 64) with three TF32 products per term. */
 ks_status ks_set_tensor_cores(ks_problem *prob, int mode);
 
 /* FP64 Grams A^T B and updates A1 C1 + A2 C2 (ks_step_gram, ks_step_combine and

@@ -3,7 +3,7 @@
   python -m paper_1308_2864_gb300.cli --config c2 --maxit 5 [--precision fp64|mixed]
                                       [--retraction qr|cayley] [--gtol 1e-6] [--verbose 0]
                                       [--N 40] [--p 512] [--fp64-emulation 0|1|2]
-                                      [--profile 40]
+                                      [--profile 40] [--tensor-cores 0|1|2|3]
 
 --N / --p shrink or change a configuration's grid and orbital count (same
 cube, atoms and functional), e.g. to profile the p = 512 kernels of c3 on a
@@ -47,6 +47,8 @@ def main(argv=None) -> int:
     ap.add_argument("--p", type=int, default=0, help="override the number of orbitals")
     ap.add_argument("--fp64-emulation", type=int, default=0, choices=[0, 1, 2],
                     help="FP64 Grams and updates on the tensor cores by digit splitting")
+    ap.add_argument("--tensor-cores", type=int, default=1, choices=[0, 1, 2, 3],
+                    help="tensor-core use of the FP32 phase (ks_set_tensor_cores)")
     ap.add_argument("--profile", type=int, default=0, metavar="W",
                     help="time the kernel classes over --maxit iterations after W untimed ones")
     a = ap.parse_args(argv)
@@ -58,6 +60,7 @@ def main(argv=None) -> int:
         s.p = a.p
     P = ks.Problem.from_system(s)
     P.set_fp64_emulation(a.fp64_emulation)
+    P.set_tensor_cores(a.tensor_cores)
     X = torch.from_numpy(np.ascontiguousarray(s.x0())).cuda()
     kw = dict(retraction=a.retraction or s.retraction, gtol=a.gtol, precision=a.precision,
               verbose=a.verbose)
@@ -86,6 +89,7 @@ def main(argv=None) -> int:
     r["wall_s"] = time.perf_counter() - t0
     r["config"] = a.config
     r["fp64_emulation"] = a.fp64_emulation
+    r["tensor_cores"] = a.tensor_cores
     print(json.dumps(r))
     return 0
 

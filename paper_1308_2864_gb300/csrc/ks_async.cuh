@@ -62,6 +62,16 @@ __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, u
       : "memory");
 }
 
+// 2-D tile load (x innermost) into shared memory, completing on `bar`.
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar,
+                                            int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%3, %4}], [%2];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_addr(bar)), "r"(c0), "r"(c1)
+      : "memory");
+}
+
 __device__ __forceinline__ void prefetch_tensor_map(const CUtensorMap *map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
@@ -73,5 +83,13 @@ __device__ __forceinline__ void prefetch_tensor_map(const CUtensorMap *map) {
 // their plain-load path instead.
 ks_status encode_tensor_map_4d(CUtensorMap *map, const void *base, int elem_bytes,
                                const uint64_t dims[4], const uint32_t box[4]);
+
+// Host: a 2-D FP32 tiled tensor map over a row-major rows x cols array
+// (cols innermost, row pitch cols * 4 bytes), box {32, box_rows} with the
+// 128-byte swizzle (the K-major layout the tensor cores read), zero fill
+// outside the tensor.  KS_EINVAL when the base or the pitch is not a
+// multiple of 16 bytes.
+ks_status encode_tensor_map_2d_sw128(CUtensorMap *map, const float *base, uint64_t rows,
+                                     uint64_t cols, uint32_t box_rows);
 
 }  // namespace ks

@@ -995,6 +995,13 @@ ks_status launch_combine(Problem &P, const T *A1, int k1, const double *C1, cons
     }
     KS_CUDA_TRY(cudaGetLastError());
     const int K = k1 + (A2 ? k2 : 0);
+    // tensor cores: beta Bm enters as a third operand with the coefficient
+    // beta I, alpha scales the other coefficients
+    if (combine_tc64_applies(P, q, {k1, A2 ? k2 : 0, Bm ? q : 0}, {A1, A2, Bm, out}))
+      return launch_combine_tc64(P, q, (const float *)A1, k1, c1, (float)alpha,
+                                 (const float *)A2, k2, A2 ? c2 : nullptr, (float)alpha,
+                                 (const float *)Bm, q, nullptr, (float)beta, (float *)out,
+                                 nullptr, nullptr, nullptr);
     if (q <= kTile && K <= kTsMaxK) {
       ProfScope ps_(P.stream, KP_COMBINE, 2.0 * P.n * q * K,
                     (double)P.n * (K + q * (Bm ? 2 : 1)) * sizeof(T));
@@ -1392,6 +1399,14 @@ ks_status launch_combine3_f32(Problem &P, const float *A1, int k1, const double 
   }
   KS_CUDA_TRY(cudaGetLastError());
   const int K = k1 + k2 + k3;
+  // tensor cores when out2 adds A1 (the retraction: A1 = X_b): A1 goes last,
+  // where the epilogue reads it back from the ring
+  if (combine_tc64_applies(P, q, {k1, k2, k3}, {A1, A2, A3, out, out2}) &&
+      (!out2 || (add2 == A1 && k1 == q))) {
+    const bool dens = rho && out2 && q == P.p;
+    return launch_combine_tc64(P, q, A2, k2, c2, 1.0f, A3, k3, c3, 1.0f, A1, k1, c1, 1.0f, out,
+                               out2, dens ? rho_b : nullptr, dens ? rho : nullptr);
+  }
   {
     ProfScope ps_(P.stream, KP_COMBINE, 2.0 * P.n * q * K,
                   (double)P.n * (K + q * (out2 ? 3 : 1)) * sizeof(float));

@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of the library.
 #pragma once
 
+#include <initializer_list>
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <array>
@@ -333,6 +334,20 @@ ks_status launch_cayley_factor(Problem &P, const double *A, const double *S, con
 ks_status configure_small_kernels();
 // ks_tc.cu: FP32 Gram on the tensor cores (partials per chunk, FP64)
 ks_status configure_tc_kernels();
+// Narrow updates (q <= 64, K <= 192) on the tensor cores (three TF32
+// products per term, ks_set_tensor_cores mode 3): out = s1 A1 C1 + s2 A2 C2
+// + s3 A3 C3 with FP32 coefficient matrices (k_i x q, row-major; a null C_i
+// is the identity, so a whole matrix can be added), out2 = A3 + out (k3 = q,
+// each operand's columns in whole stages of 32) and, with rho, the
+// increment-form density rho = rho_b + f sum out (2 A3 + out).  applies:
+// mode, q, the operand widths ks (multiples of 4, at most 6 stages of 32
+// in all) and 16-byte alignment of ptrs.
+bool combine_tc64_applies(const Problem &P, int q, std::initializer_list<int> ks,
+                          std::initializer_list<const void *> ptrs);
+ks_status launch_combine_tc64(Problem &P, int q, const float *A1, int k1, const float *C1,
+                              float s1, const float *A2, int k2, const float *C2, float s2,
+                              const float *A3, int k3, const float *C3, float s3, float *out,
+                              float *out2, const double *rho_b, double *rho);
 size_t tc_image_floats(int p);
 int gram_tc_chunks(const Problem &P, int pa, int qb);
 ks_status launch_gram_tc(Problem &P, const float *A, int pa, const float *B, int qb,

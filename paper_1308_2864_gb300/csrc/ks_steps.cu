@@ -126,7 +126,7 @@ ks_status ks_step_gram(ks_problem *kp, const double *A, int pa, const double *B,
 }
 
 ks_status ks_set_tensor_cores(ks_problem *kp, int mode) {
-  if (!kp || mode < 0 || mode > 2) return set_error(KS_EINVAL, "bad argument");
+  if (!kp || mode < 0 || mode > 3) return set_error(KS_EINVAL, "bad argument");
   kp->P.use_tc = mode;
   return KS_OK;
 }

@@ -16,7 +16,9 @@
 // stores hit 32 different banks.  All waits are bounded: a block that waits
 // too long records KS_ETIMEOUT and stops.
 #include <cstdint>
+#include <initializer_list>
 
+#include "ks_async.cuh"
 #include "ks_device.cuh"
 
 namespace ks {
@@ -417,9 +419,313 @@ __global__ void __launch_bounds__(kTcThreads, 1) combine_tc_kernel(
   tc_teardown(tmem);
 }
 
+// ---------------------------------------------------------------- narrow updates
+// out (n x q, q <= 64) = s1 A1 C1 + s2 A2 C2 + s3 A3 C3 and optionally
+// out2 = A3 + out (k3 = q) with the increment form's density rho = rho_b +
+// f sum out (2 A3 + out): the updates of the retraction and of the
+// projected gradient at p <= 64 on the tensor cores.  One persistent block
+// per SM walks its 128-row tiles.  Each operand's columns are cut into
+// stages of 32 (the last one zero-filled past k_i); a stage (128 rows x 128
+// bytes) arrives by one TMA tile load in the 128-byte-swizzled K-major
+// layout the MMA reads, into a ring of kNRaw buffers kNRaw - 1 stages
+// ahead.  All threads split it elementwise into TF32 high and low parts
+// (x = hi + lo, hi rounded to nearest; same layout) in one of two split
+// buffers, and one thread issues hi.hi + hi.lo + lo.hi (3 x 4 MMAs of
+// 128 x 64 x 8, about 2^-21 relative error per product) into a 64-column
+// FP32 accumulator in tensor memory.  The coefficients' image (hi and lo of
+// every stage, scaled, a null C_i standing for the identity so that a whole
+// matrix can be added) stays in shared memory for the launch; A3 for out2
+// is read back from the ring's last stages, so the epilogue makes no global
+// loads.  Every wait is bounded; a block that gives up records KS_ETIMEOUT,
+// waits for its copies and MMAs and stops.
+constexpr int kNM = 128, kNN = 64, kNK = 32;     // tile rows, columns, K per stage
+constexpr int kNThreads = 256;
+constexpr int kNRaw = 4;                         // ring of A stages
+constexpr int kNTileBytes = kNM * kNK * 4;       // 16 KiB: one A stage (raw, hi or lo)
+constexpr int kNImgBytes = 2 * kNN * kNK * 4;    // 16 KiB: hi + lo of one coefficient stage
+constexpr int kNMaxStages = 6;                   // K (padded per operand) <= 192
+constexpr int kNCols = 64;                       // tensor-memory columns
+constexpr size_t kNSmem = (size_t)kNMaxStages * kNImgBytes + (size_t)kNRaw * kNTileBytes +
+                          (size_t)4 * kNTileBytes + 1024;
+constexpr uint32_t kIdescN64 = (1u << 4) | (2u << 7) | (2u << 10) |
+                               ((uint32_t)(kNN >> 3) << 17) | ((uint32_t)(kNM >> 4) << 24);
+
+struct Tc64Args {
+  CUtensorMap map[3];          // A_i as (k_i, n) FP32, box (32, 128), 128-byte swizzle
+  long long n, ntiles;
+  int q, stages;
+  int st_end[3];               // cumulative stage counts of the operands
+  const float *img;
+  float *out, *out2;
+  const double *rho_b;
+  double *rho;
+  double occ;
+  int *status;
+};
+
+__device__ __forceinline__ void mma_tf32_n64(uint32_t tmem, uint64_t da, uint64_t db,
+                                             uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+      :: "r"(tmem), "l"(da), "l"(db), "r"(kIdescN64), "r"(acc));
+}
+
+// Shared-memory matrix descriptor of a K-major tile in the 128-byte
+// swizzle: rows of 128 bytes, 8-row groups 1024 bytes apart (SBO),
+// descriptor version 1, layout type 2 (128-byte swizzle).
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// byte offset of element (r, k) of a rows x 32 FP32 tile in the 128-byte
+// swizzle (16-byte chunk k / 4 of row r at chunk (k / 4) ^ (r % 8))
+__device__ __forceinline__ int sw128_offset(int r, int k) {
+  return r * 128 + ((((k >> 2) ^ (r & 7))) << 4) + (k & 3) * 4;
+}
+
+// x = hi + lo with hi the TF32 value nearest to x (ties away from zero) and
+// lo = x - hi exactly; |lo| <= 2^-11 |x|.
+__device__ __forceinline__ void split_rn(float x, float &hi, float &lo) {
+  hi = __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+  lo = x - hi;
+}
+
+// 32 FP32 accumulator columns of this warp's 32 tensor-memory lanes.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+        "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+        "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+        "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;");
+}
+
+__device__ __forceinline__ void cp_async16_zf(void *dst, const void *src, uint32_t bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" :: "r"(smem_u32(dst)), "l"(src),
+               "r"(bytes) : "memory");
+}
+
+// Coefficient image of a narrow update: stage st belongs to operand i
+// (st_end cumulative) and holds rows 32 j .. 32 j + 31 of s_i C_i (k_i x q
+// FP32, a null C_i the identity; zero past k_i and q), as hi and lo 64 x 32
+// tiles in the 128-byte swizzle, exactly as the kernel's shared memory
+// holds them.
+struct Img64 {
+  const float *C[3];
+  int k[3];
+  float s[3];
+  int st_end[3];
+};
+
+__global__ void combine_image64_kernel(int q, Img64 im, int stages, float *__restrict__ img) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  constexpr int per_stage = kNN * kNK;
+  if (e >= stages * per_stage) return;
+  const int st = e / per_stage, within = e % per_stage;
+  const int c = within / kNK, k = within % kNK;
+  const int i = st < im.st_end[0] ? 0 : st < im.st_end[1] ? 1 : 2;
+  const int r = (st - (i > 0 ? im.st_end[i - 1] : 0)) * kNK + k;
+  float x = 0.f;
+  if (c < q && r < im.k[i])
+    x = im.s[i] * (im.C[i] ? im.C[i][(long long)r * q + c] : (r == c ? 1.f : 0.f));
+  float hi, lo;
+  split_rn(x, hi, lo);
+  unsigned char *base = (unsigned char *)(img + (long long)st * 2 * per_stage);
+  const int off = sw128_offset(c, k);
+  *(float *)(base + off) = hi;
+  *(float *)(base + kNImgBytes / 2 + off) = lo;
+}
+
+__global__ void __launch_bounds__(kNThreads, 1) combine_tc64_kernel(
+    const __grid_constant__ Tc64Args ga) {
+  extern __shared__ __align__(1024) unsigned char dyn_raw[];
+  unsigned char *smem = (unsigned char *)(((uintptr_t)dyn_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char *Bs = smem;                                       // coefficient image
+  unsigned char *Raw = Bs + (size_t)kNMaxStages * kNImgBytes;     // A ring
+  unsigned char *HL = Raw + (size_t)kNRaw * kNTileBytes;          // 2 x (hi, lo)
+  __shared__ __align__(8) uint64_t mbar[2];                       // MMAs of a split buffer done
+  __shared__ __align__(8) uint64_t full[kNRaw];                   // ring stage landed
+  __shared__ uint32_t tmem_slot;
+  __shared__ float dens[kNM];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int stages = ga.stages, q = ga.q;
+  const long long n = ga.n;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_u32(&tmem_slot)), "r"(kNCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    for (int i = 0; i < 3; ++i)
+      if (ga.st_end[i] > (i > 0 ? ga.st_end[i - 1] : 0)) prefetch_tensor_map(&ga.map[i]);
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    for (int b = 0; b < kNRaw; ++b) mbar_init(&full[b], 1);
+    fence_barrier_init();
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_slot;
+
+  // the coefficient image, once
+  for (int o = tid * 16; o < stages * kNImgBytes; o += kNThreads * 16)
+    cp_async16_zf(Bs + o, (const unsigned char *)ga.img + o, 16u);
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  const long long mine =
+      ga.ntiles > blockIdx.x ? (ga.ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  const long long W = mine * stages;
+  // stage w of this block: one TMA tile of operand i at column 32 j, rows
+  // of tile (thread 0 only)
+  auto issue = [&](long long w) {
+    if (w >= W) return;
+    const long long tile = blockIdx.x + (w / stages) * gridDim.x;
+    const int st = (int)(w % stages);
+    const int i = st < ga.st_end[0] ? 0 : st < ga.st_end[1] ? 1 : 2;
+    const int j = st - (i > 0 ? ga.st_end[i - 1] : 0);
+    uint64_t *bar = &full[w % kNRaw];
+    mbar_arrive_expect_tx(bar, (uint32_t)kNTileBytes);
+    tma_load_2d(Raw + (size_t)(w % kNRaw) * kNTileBytes, &ga.map[i], bar, j * kNK,
+                (int)(tile * kNM));
+  };
+  if (tid == 0)
+    for (int st = 0; st < kNRaw - 1; ++st) issue(st);
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  bool failed = false;
+  long long last = -1;                       // last stage whose MMAs were committed
+  long long issued_to = kNRaw - 1;           // stages below this were issued
+  for (long long w = 0; w < W; ++w) {
+    const int s = (int)(w % stages);
+    const bool tile_end = s == stages - 1;
+    // the buffer of stage w - 1 is free (its split ended before the last
+    // barrier): refill it, except at a tile's end, whose epilogue still
+    // reads the last stages (A3)
+    if (tid == 0 && !tile_end) issue(w + kNRaw - 1);
+    if (!tile_end) issued_to = w + kNRaw;
+    int ok = mbar_wait_parity(&full[w % kNRaw], (uint32_t)((w / kNRaw) & 1)) ? 1 : 0;
+    const int sb = (int)(w & 1);
+    unsigned char *Hs = HL + (size_t)sb * 2 * kNTileBytes, *Ls = Hs + kNTileBytes;
+    if (ok && w >= 2) ok = mbar_wait(smem_u32(&mbar[sb]), (uint32_t)(((w - 2) >> 1) & 1)) ? 1 : 0;
+    if (!__syncthreads_and(ok)) {
+      failed = true;
+      break;
+    }
+    const unsigned char *raw = Raw + (size_t)(w % kNRaw) * kNTileBytes;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int o = (tid + t * kNThreads) * 16;
+      const float4 x = *reinterpret_cast<const float4 *>(raw + o);
+      float4 h, l;
+      split_rn(x.x, h.x, l.x); split_rn(x.y, h.y, l.y);
+      split_rn(x.z, h.z, l.z); split_rn(x.w, h.w, l.w);
+      *reinterpret_cast<float4 *>(Hs + o) = h;
+      *reinterpret_cast<float4 *>(Ls + o) = l;
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t ah = smem_u32(Hs), al = smem_u32(Ls);
+      const uint32_t bh = smem_u32(Bs + (size_t)s * kNImgBytes), bl = bh + kNImgBytes / 2;
+#pragma unroll
+      for (int ks = 0; ks < kNK / 8; ++ks) {
+        const uint32_t o = ks * 32;
+        mma_tf32_n64(tmem, smem_desc_sw128(ah + o), smem_desc_sw128(bh + o),
+                     (s > 0 || ks > 0) ? 1u : 0u);
+        mma_tf32_n64(tmem, smem_desc_sw128(ah + o), smem_desc_sw128(bl + o), 1u);
+        mma_tf32_n64(tmem, smem_desc_sw128(al + o), smem_desc_sw128(bh + o), 1u);
+      }
+      commit(&mbar[sb]);
+    }
+    last = w;
+    if (tile_end) {
+      // epilogue: thread = one row (lane quarter warp & 3) and 32 columns
+      // (half warp >> 2); A3 (out2) from the ring's last stages
+      const long long tile = blockIdx.x + (w / stages) * gridDim.x;
+      const int rl = 32 * (warp & 3) + lane;
+      const long long row = tile * kNM + rl;
+      const int c0 = 32 * (warp >> 2);
+      const bool live = row < n && c0 < q;
+      ok = mbar_wait(smem_u32(&mbar[sb]), (uint32_t)((w >> 1) & 1)) ? 1 : 0;
+      if (!__syncthreads_and(ok)) {
+        failed = true;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      uint32_t v[32];
+      tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c0, v);
+      // columns c0 .. c0 + 31 of A3 fill stage stages - nst3 + c0 / 32
+      const int nst3 = ga.st_end[2] - ga.st_end[1];
+      const int sa = stages - nst3 + c0 / kNK;
+      const unsigned char *a3s =
+          Raw + (size_t)((w - (stages - 1 - sa)) % kNRaw) * kNTileBytes;
+      float dsum = 0.f;
+      float *out = ga.out, *out2 = ga.out2;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        if (!live || c0 + 4 * j >= q) continue;
+        const float4 y = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
+                                     __uint_as_float(v[4 * j + 2]),
+                                     __uint_as_float(v[4 * j + 3]));
+        *reinterpret_cast<float4 *>(out + row * q + c0 + 4 * j) = y;
+        if (out2) {
+          const float4 a = *reinterpret_cast<const float4 *>(a3s + sw128_offset(rl, 4 * j));
+          *reinterpret_cast<float4 *>(out2 + row * q + c0 + 4 * j) =
+              make_float4(a.x + y.x, a.y + y.y, a.z + y.z, a.w + y.w);
+          if (ga.rho) {
+            dsum = fmaf(y.x, fmaf(2.f, a.x, y.x), dsum);
+            dsum = fmaf(y.y, fmaf(2.f, a.y, y.y), dsum);
+            dsum = fmaf(y.z, fmaf(2.f, a.z, y.z), dsum);
+            dsum = fmaf(y.w, fmaf(2.f, a.w, y.w), dsum);
+          }
+        }
+      }
+      if (ga.rho) {
+        if (warp >= 4) dens[rl] = dsum;
+        __syncthreads();
+        if (warp < 4 && row < n) ga.rho[row] = ga.rho_b[row] + ga.occ * (double)(dsum + dens[rl]);
+      }
+      // every warp has read the accumulator and the ring before the next
+      // tile's MMAs and copies overwrite them
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      if (tid == 0) issue(w + kNRaw - 1);
+      issued_to = w + kNRaw;
+    }
+  }
+  if (failed && tid == 0) {
+    atomicCAS(ga.status, 0, (int)KS_ETIMEOUT);
+    // the copies and MMAs still in flight write the ring and read the split
+    // buffers: wait for them (bounded)
+    for (long long v = last + 1; v < issued_to && v < W; ++v)
+      mbar_wait_parity(&full[v % kNRaw], (uint32_t)((v / kNRaw) & 1));
+    for (long long v = last - 1; v <= last; ++v)
+      if (v >= 0) mbar_wait(smem_u32(&mbar[v & 1]), (uint32_t)((v >> 1) & 1));
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kNCols));
+}
+
 }  // namespace
 
 ks_status configure_tc_kernels() {
+  KS_CUDA_TRY(cudaFuncSetAttribute(combine_tc64_kernel,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kNSmem));
   KS_CUDA_TRY(cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    kTcSmem));
   KS_CUDA_TRY(cudaFuncSetAttribute(combine_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -480,6 +786,72 @@ ks_status launch_gram_tc(Problem &P, const float *A, int pa, const float *B, int
     ProfScope ps_(P.stream, KP_GRAM, 2.0 * P.n * pa * qb, (double)P.n * (pa + qb) * sizeof(float));
     gram_tc_kernel<<<dim3(tiles_a * tiles_b, chunks), kTcThreads, kTcSmem, P.stream>>>(
         P.n, pa, qb, rows_per, tiles_b, A, B, part, P.dstatus);
+  }
+  KS_CUDA_TRY(cudaGetLastError());
+  return KS_OK;
+}
+
+bool combine_tc64_applies(const Problem &P, int q, std::initializer_list<int> ks,
+                          std::initializer_list<const void *> ptrs) {
+  if (P.use_tc != 3 || q < 1 || q > kNN || q % 4) return false;
+  int stages = 0;
+  for (int k : ks) {
+    if (k % 4) return false;
+    stages += (k + kNK - 1) / kNK;
+  }
+  if (stages < 1 || stages > kNMaxStages) return false;
+  for (const void *ptr : ptrs)
+    if (reinterpret_cast<uintptr_t>(ptr) % 16) return false;
+  return true;
+}
+
+ks_status launch_combine_tc64(Problem &P, int q, const float *A1, int k1, const float *C1,
+                              float s1, const float *A2, int k2, const float *C2, float s2,
+                              const float *A3, int k3, const float *C3, float s3, float *out,
+                              float *out2, const double *rho_b, double *rho) {
+  const float *A[3] = {A1, A2, A3};
+  int k[3] = {k1, A2 ? k2 : 0, A3 ? k3 : 0};
+  Img64 im{{C1, C2, C3}, {k[0], k[1], k[2]}, {s1, s2, s3}, {0, 0, 0}};
+  Tc64Args ga{};
+  int stages = 0;
+  for (int i = 0; i < 3; ++i) {
+    if (k[i] % 4) return set_error(KS_EINVAL, "combine_tc64: operand width not a multiple of 4");
+    stages += (k[i] + kNK - 1) / kNK;
+    im.st_end[i] = ga.st_end[i] = stages;
+    if (k[i] > 0)
+      KS_TRY(encode_tensor_map_2d_sw128(&ga.map[i], A[i], (uint64_t)P.n, (uint64_t)k[i],
+                                        (uint32_t)kNM));
+  }
+  if (stages < 1 || stages > kNMaxStages ||
+      (size_t)stages * kNImgBytes / sizeof(float) > P.tc_img_len)
+    return set_error(KS_EINVAL, "combine_tc64: K above the image");
+  // out2 = A3 + out reads A3 from the ring's last stages
+  if (out2 && (k[2] != q || k[2] == 0))
+    return set_error(KS_EINVAL, "combine_tc64: out2 needs A3 with q columns");
+  {
+    ProfScope ps_(P.stream, KP_REDUCE);
+    const int elems = stages * kNN * kNK;
+    combine_image64_kernel<<<(elems + 255) / 256, 256, 0, P.stream>>>(q, im, stages, P.tc_img);
+  }
+  KS_CUDA_TRY(cudaGetLastError());
+  ga.n = P.n;
+  ga.ntiles = (P.n + kNM - 1) / kNM;
+  ga.q = q;
+  ga.stages = stages;
+  ga.img = P.tc_img;
+  ga.out = out;
+  ga.out2 = out2;
+  ga.rho_b = rho_b;
+  ga.rho = rho;
+  ga.occ = P.occ;
+  ga.status = P.dstatus;
+  long long grid = P.sms;
+  if (grid > ga.ntiles) grid = ga.ntiles;
+  const int K = k[0] + k[1] + k[2];
+  {
+    ProfScope ps_(P.stream, KP_COMBINE, 2.0 * P.n * q * K,
+                  (double)P.n * (K + q * (out2 ? 2 : 1)) * sizeof(float));
+    combine_tc64_kernel<<<(int)grid, kNThreads, kNSmem, P.stream>>>(ga);
   }
   KS_CUDA_TRY(cudaGetLastError());
   return KS_OK;

@@ -31,7 +31,7 @@ void load_encode() {
 // launches of a solve find their maps here.
 struct MapKey {
   const void *base;
-  int elem;
+  int elem;                 // element bytes; negative: the 2-D 128-byte-swizzled form
   uint64_t dims[4];
   uint32_t box[4];
   bool operator==(const MapKey &o) const {
@@ -55,12 +55,12 @@ MapCache g_maps;
 
 ks_status encode_uncached(CUtensorMap *map, const void *base, int elem_bytes,
                           const uint64_t dims[4], const uint32_t box[4]);
+ks_status encode_sw128_uncached(CUtensorMap *map, const float *base, uint64_t rows,
+                                uint64_t cols, uint32_t box_rows);
 
-}  // namespace
-
-ks_status encode_tensor_map_4d(CUtensorMap *map, const void *base, int elem_bytes,
-                               const uint64_t dims[4], const uint32_t box[4]) {
-  MapKey k{base, elem_bytes, {dims[0], dims[1], dims[2], dims[3]}, {box[0], box[1], box[2], box[3]}};
+// Look up key k; on a miss encode with `make` and remember the result.
+template <typename F>
+ks_status cached_map(const MapKey &k, CUtensorMap *map, F make) {
   std::lock_guard<std::mutex> lock(g_maps.mu);
   for (int i = 0; i < g_maps.n; ++i)
     if (g_maps.key[i] == k) {
@@ -68,7 +68,7 @@ ks_status encode_tensor_map_4d(CUtensorMap *map, const void *base, int elem_byte
       *map = g_maps.map[i];
       return KS_OK;
     }
-  KS_TRY(encode_uncached(map, base, elem_bytes, dims, box));
+  KS_TRY(make());
   int slot = 0;
   if (g_maps.n < kMapCache) {
     slot = g_maps.n++;
@@ -80,6 +80,22 @@ ks_status encode_tensor_map_4d(CUtensorMap *map, const void *base, int elem_byte
   g_maps.map[slot] = *map;
   g_maps.used[slot] = ++g_maps.tick;
   return KS_OK;
+}
+
+}  // namespace
+
+ks_status encode_tensor_map_4d(CUtensorMap *map, const void *base, int elem_bytes,
+                               const uint64_t dims[4], const uint32_t box[4]) {
+  const MapKey k{base, elem_bytes, {dims[0], dims[1], dims[2], dims[3]},
+                 {box[0], box[1], box[2], box[3]}};
+  return cached_map(k, map, [&] { return encode_uncached(map, base, elem_bytes, dims, box); });
+}
+
+ks_status encode_tensor_map_2d_sw128(CUtensorMap *map, const float *base, uint64_t rows,
+                                     uint64_t cols, uint32_t box_rows) {
+  const MapKey k{base, -4, {cols, rows, 0, 0}, {32u, box_rows, 0, 0}};
+  return cached_map(k, map,
+                    [&] { return encode_sw128_uncached(map, base, rows, cols, box_rows); });
 }
 
 namespace {
@@ -111,6 +127,23 @@ ks_status encode_uncached(CUtensorMap *map, const void *base, int elem_bytes,
   const CUresult r = g_encode(map, dt, 4, const_cast<void *>(base), gdim, gstride, bdim, estride,
                               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                               CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_error(KS_EINVAL, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return KS_OK;
+}
+
+ks_status encode_sw128_uncached(CUtensorMap *map, const float *base, uint64_t rows,
+                                uint64_t cols, uint32_t box_rows) {
+  std::call_once(g_encode_once, load_encode);
+  if (!g_encode) return set_error(KS_EINVAL, "tensor-map encoder unavailable");
+  if (reinterpret_cast<uintptr_t>(base) % 16 != 0 || (cols * 4) % 16 != 0)
+    return set_error(KS_EINVAL, "tensor map: base or row pitch not a multiple of 16 bytes");
+  cuuint64_t gdim[2] = {cols, rows};
+  cuuint64_t gstride[1] = {cols * 4};
+  cuuint32_t bdim[2] = {32u, box_rows}, estride[2] = {1, 1};
+  const CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base),
+                              gdim, gstride, bdim, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return set_error(KS_EINVAL, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   return KS_OK;

@@ -25,13 +25,17 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
 
 
+@pytest.mark.parametrize("tensor_cores", [1, 3], ids=["simt_updates", "tc_updates"])
 @pytest.mark.parametrize("retraction", ["qr", "cayley"])
-def test_increment_form_on_a_wide_block_follows_fp64(retraction):
+def test_increment_form_on_a_wide_block_follows_fp64(retraction, tensor_cores):
+    # tensor_cores 3 runs the narrow updates on the tensor cores (three TF32
+    # products per term), 1 on the FP32 pipes
     import paper_1308_2864_gb300 as ks
     s = ki.small_system(**CASE)
     model = oe.Model.from_system(s)
     ref = ost.minimize(model, s.x0(), ost.Options(retraction=retraction, maxit=ITERS))
     P = ks.Problem.from_system(s)
+    P.set_tensor_cores(tensor_cores)
     X = dev(s.x0())
     r = P.minimize(X, retraction=retraction, gtol=1e-12, maxit=ITERS, precision="mixed",
                    stall_iters=0)
@@ -47,7 +51,13 @@ def test_increment_form_on_a_wide_block_follows_fp64(retraction):
     ev = oe.evaluate(model, Xh)
     scale = sum(abs(v) for v in ev.parts.values())
     assert abs(r["E"] - ev.E) <= 1e-6 * scale
-    # and the iterates follow the FP64 trajectory
-    assert abs(r["E"] - ref.E) <= 1e-6 * scale
+    # and the iterates follow the FP64 trajectory (the early BB steps
+    # amplify the update's rounding, about eight times larger with three
+    # TF32 products than on the FP32 pipes)
+    assert abs(r["E"] - ref.E) <= (1e-6 if tensor_cores == 1 else 1e-5) * scale
     assert r["gradnorm"] == pytest.approx(ref.dnorm, rel=1e-3)
-    assert ost.ortho_error(model, Xh) < 1e-6
+    # the trial keeps X^T M X - I of the iterate (exact trial Gram) up to the
+    # rounding of the update: about 1e-7 relative per product on the FP32
+    # pipes, 2^-21 with three TF32 products, over twelve steps of the size of
+    # X; an indexing error gives O(1)
+    assert ost.ortho_error(model, Xh) < (1e-6 if tensor_cores == 1 else 1e-4)
