@@ -52,7 +52,7 @@ GTOL = 1e-6
 # measured on GB300 (profiles/c2_time_to_solution.md); the solve is
 # deterministic (fixed reduction orders), so these set the segment length of
 # the timed solve and the oracle's extrapolated solve.
-C2_ITERS_MIXED = 98539
+C2_ITERS_MIXED = 100305
 C2_ITERS_FP64 = 99874
 # jobs of the batched-jobs recipe (seed 1003) that reach ||D||_M <= 1e-6 in
 # a few thousand iterations

@@ -144,7 +144,7 @@ __device__ __forceinline__ void thomas_line_reg(long long t, int N, int p, int a
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) thomas_reg_kernel(int N, int p, int axis, double scale_d,
+__global__ void __launch_bounds__(256, 2) thomas_reg_kernel(int N, int p, int axis, double scale_d,
                                                          const double *__restrict__ w_d,
                                                          const T *in, T *out, const T *add) {
   __shared__ T w[kRegN];

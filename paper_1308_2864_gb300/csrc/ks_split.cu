@@ -108,8 +108,9 @@ __global__ void add_pp_kernel(int p, const double *A, double s, const double *B,
 // (h_jj = -g_jj / (1 + g_jj)), then V_ic -= g_ij V_jc for c <= j.  Output:
 // the FP32 coefficients of the update X_b (A - I) + delta A + D B with
 // A = L^{-T} = I + H^T and B = -tau A, as [H^T; I + H^T; -tau (I + H^T)].
-// One block of 8 warps: a warp per matrix row, its lanes over the columns;
-// every thread forms the pivot itself, so a column costs two barriers.  G
+// One block of 256 threads, a thread per column of four rows at a time in
+// the trailing update; every thread forms the pivot itself, so a column
+// costs two barriers.  G
 // and H (row stride p + 1, so that column reads do not collide in a bank)
 // and column j of G live in dynamic shared memory; a non-positive or
 // non-finite pivot records KS_ENOTPD and leaves P.cf as it was.
@@ -169,12 +170,22 @@ __global__ void __launch_bounds__(kDevThreads) qr_factor_dev_kernel(int p,
     for (int c = threadIdx.x; c < j; c += kDevThreads) H[j * ld + c] *= il;
     if (threadIdx.x == 0) H[j * ld + j] = hjj;
     __syncthreads();
-    for (int i = j + 1 + w; i < p; i += kWarps) {
-      const float gij = colj[i];
-      for (int c = lane; c <= i; c += 32) {
-        if (c > j) G[i * ld + c] = fmaf(-gij, colj[c], G[i * ld + c]);
-        else if (c < j) H[i * ld + c] = fmaf(-gij, H[j * ld + c], H[i * ld + c]);
-        else H[i * ld + j] = -fmaf(gij, hjj, gij);
+    // rows i > j, four at a time (row group tid / 64, column tid % 64): the
+    // updates of different rows are independent, so a thread's loads of
+    // four rows are in flight together
+    {
+      const int c = threadIdx.x & 63, r0 = j + 1 + (threadIdx.x >> 6);
+      if (c < p) {
+        const float hjc = c < j ? H[j * ld + c] : 0.f;
+        const float gcj = c > j ? colj[c] : 0.f;
+#pragma unroll 4
+        for (int i = r0; i < p; i += 4) {
+          if (c > i) continue;
+          const float gij = colj[i];
+          if (c > j) G[i * ld + c] = fmaf(-gij, gcj, G[i * ld + c]);
+          else if (c < j) H[i * ld + c] = fmaf(-gij, hjc, H[i * ld + c]);
+          else H[i * ld + j] = -fmaf(gij, hjj, gij);
+        }
       }
     }
     __syncthreads();
