@@ -278,6 +278,18 @@ ks_status ks_state_load(ks_problem *prob, const void *host_buf, size_t bytes);
 /* Kernels this library has launched in this process so far. */
 unsigned long long ks_kernel_launches(void);
 
+/* Bounds-checked build.  Compiled with -DKS_DEBUG_BOUNDS (the build's
+ * KS_DEBUG_BOUNDS=1), the hot-path kernels -- stencils, density, M^{-1}
+ * sweeps, Grams and updates, the Hartree solver's passes, the p x p factor
+ * and the tensor-core update -- test each computed global and shared-memory
+ * index before the access it guards; an index out of range skips the access
+ * and is counted instead of faulting.  Returns 1 in such a build, 0
+ * otherwise.  *count (when not NULL) receives the number of out-of-range
+ * indices caught since the last call (always 0 in a normal build), *file and
+ * *line the source file and line of the first one (NULL, 0 when none); the
+ * record is then cleared.  Synchronises the device in a checked build. */
+int ks_debug_bounds(unsigned long long *count, const char **file, int *line);
+
 /* Optional timing of the library's kernels by class with CUDA events on the
  * launching stream.  ks_profile_start() clears the totals and switches
  * timing on; ks_profile_stop() waits for the recorded events, switches

@@ -96,6 +96,9 @@ SIGNATURES = [
                                 _DP, ctypes.POINTER(Result)]),
     ("ks_last_error_string", ctypes.c_char_p, []),
     ("ks_kernel_launches", ctypes.c_ulonglong, []),
+    ("ks_debug_bounds", ctypes.c_int, [ctypes.POINTER(ctypes.c_ulonglong),
+                                        ctypes.POINTER(ctypes.c_char_p),
+                                        ctypes.POINTER(ctypes.c_int)]),
     ("ks_state_bytes", ctypes.c_size_t, [_P]),
     ("ks_state_save", _I, [_P, ctypes.c_void_p, ctypes.c_size_t]),
     ("ks_state_load", _I, [_P, ctypes.c_void_p, ctypes.c_size_t]),
@@ -207,6 +210,18 @@ PROF_CLASSES = 12
 def kernel_launches() -> int:
     """Kernels the library has launched in this process."""
     return int(load_library().ks_kernel_launches())
+
+
+def debug_bounds() -> dict:
+    """The bounds-checked build's record (ks_debug_bounds): whether the library
+    is such a build, the out-of-range indices caught since the last call and
+    where the first one was; the record is cleared."""
+    c = ctypes.c_ulonglong()
+    f = ctypes.c_char_p()
+    ln = ctypes.c_int()
+    checked = load_library().ks_debug_bounds(ctypes.byref(c), ctypes.byref(f), ctypes.byref(ln))
+    return {"checked": bool(checked), "count": int(c.value),
+            "file": f.value.decode() if f.value else None, "line": int(ln.value)}
 
 
 def profile_start():

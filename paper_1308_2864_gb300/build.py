@@ -44,9 +44,26 @@ def lib_path() -> str:
     return os.path.join(LIBDIR, LIBNAME)
 
 
+def mode_flags() -> list[str]:
+    """Extra compiler flags of the requested build mode: KS_DEBUG_BOUNDS=1 in
+    the environment selects the bounds-checked build (every checked index
+    tested before its access, see ks_debug_bounds in include/ks.h)."""
+    return ["-DKS_DEBUG_BOUNDS"] if os.environ.get("KS_DEBUG_BOUNDS", "0") not in ("", "0") else []
+
+
+def _stamp_path() -> str:
+    return os.path.join(LIBDIR, "build_flags.txt")
+
+
 def needs_build() -> bool:
     out = lib_path()
     if not os.path.exists(out):
+        return True
+    try:
+        with open(_stamp_path()) as fh:
+            if fh.read().strip() != " ".join(mode_flags()):
+                return True
+    except OSError:
         return True
     t = os.path.getmtime(out)
     return any(os.path.getmtime(f) > t for f in sources() + headers() + [__file__])
@@ -67,14 +84,17 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
         return lib_path()
     os.makedirs(OBJDIR, exist_ok=True)
     srcs = sources()
+    flags = mode_flags() + list(extra or [])
     with ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra or []), srcs))
+        objs = list(ex.map(lambda s: _compile(s, flags), srcs))
     tmp = lib_path() + ".tmp"
     cmd = [nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, lib_path())
+    with open(_stamp_path(), "w") as fh:
+        fh.write(" ".join(mode_flags()))
     if verbose:
         print(f"built {lib_path()}")
     return lib_path()

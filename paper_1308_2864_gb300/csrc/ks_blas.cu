@@ -366,11 +366,12 @@ __global__ void __launch_bounds__(256, Dual ? 3 : 4) gram2_ta_kernel(
       }
       const float *src = A1;
       uint32_t bytes = 0;
-      if (row < n && r0 + rr < nv && c4 < w_) {
+      if (row < n && r0 + rr < nv && c4 < w_ && KS_IN(row * w_ + c4 + 3, n * w_)) {
         src = M + row * w_ + c4;
         bytes = 16;
       }
-      cp_async16(smem_addr(dst + (size_t)op * kGaRows * kTile + rr * kTile + c4), src, bytes);
+      const int di = op * kGaRows * kTile + rr * kTile + c4;
+      if (KS_IN(di + 3, kOps * kGaRows * kTile)) cp_async16(smem_addr(dst + di), src, bytes);
     }
   };
   float acc[4][4], acc2[4][4];
@@ -421,6 +422,9 @@ __global__ void __launch_bounds__(256, Dual ? 3 : 4) gram2_ta_kernel(
     for (int j = 0; j < 4; ++j) {
       const int b = 4 * tx + j;
       if (b >= qb) continue;
+      if (!KS_IN((long long)blockIdx.x * (Dual ? 2 : 1) * len + (Dual ? len : 0) + a * qb + b,
+                 (long long)gridDim.x * (Dual ? 2 : 1) * len))
+        continue;
       dst[(long long)a * qb + b] = acc[i][j];
       if (Dual) dst[len + (long long)a * qb + b] = acc2[i][j];
     }
@@ -811,7 +815,7 @@ __device__ __forceinline__ void ts_epilogue(long long n, int q, long long row0, 
   for (int i = 0; i < 8; ++i) {
     const long long row = row0 + i;
     float dsum = 0.f;
-    if (row < n) {
+    if (row < n && KS_IN(row * q + col0, n * q)) {
       const long long o = row * q + col0;
       if (vec) {
         float4 v = make_float4(alpha * acc[i][0], alpha * acc[i][1], alpha * acc[i][2],
@@ -1293,11 +1297,17 @@ __global__ void __launch_bounds__(256, 2) combine_ta_kernel(
       const float *src = A1;
       uint32_t bytes = 0;
       if (row < n) {
-        if (k < k1) { src = A1 + row * k1 + k; bytes = 16; }
-        else if (k < k12) { src = A2 + row * k2 + (k - k1); bytes = 16; }
-        else if (k < K) { src = A3 + row * k3 + (k - k12); bytes = 16; }
+        if (k < k1) {
+          if (KS_IN(row * k1 + k + 3, n * k1)) { src = A1 + row * k1 + k; bytes = 16; }
+        } else if (k < k12) {
+          if (KS_IN(row * k2 + (k - k1) + 3, n * k2)) { src = A2 + row * k2 + (k - k1); bytes = 16; }
+        } else if (k < K) {
+          if (KS_IN(row * k3 + (k - k12) + 3, n * k3)) { src = A3 + row * k3 + (k - k12); bytes = 16; }
+        }
       }
-      cp_async16(smem_addr(dst + rr * kTaLd + kq), src, bytes);
+      const long long di = (long long)(w % kTaStages) * kTsRows * kTaLd + rr * kTaLd + kq;
+      if (KS_IN(di + 3, (long long)kTaStages * kTsRows * kTaLd))
+        cp_async16(smem_addr(dst + rr * kTaLd + kq), src, bytes);
     }
   };
   float acc[8][4];
@@ -1500,6 +1510,8 @@ std::mutex g_noalloc_mu;
 constexpr int kMaxDevices = 64;
 double *g_noalloc_ptr[kMaxDevices] = {};
 }  // namespace
+
+KS_OOB_READER(blas)
 
 }  // namespace ks
 

@@ -237,6 +237,8 @@ __device__ __forceinline__ void smem_matmul(const float *At, const float *B, flo
     for (int jb = 0; jb < N; jb += 64) {
       const int i0 = ib + 4 * ty, j0 = jb + 4 * tx;
       if (i0 >= N || j0 >= N) continue;
+      // every 16-byte row access of the tile stays inside its row
+      if (!KS_IN(i0 + 3, ld) || !KS_IN(j0 + 3, ld)) continue;
       float acc[4][4];
 #pragma unroll
       for (int u = 0; u < 4; ++u)
@@ -343,11 +345,17 @@ __device__ double fused_plane_pass(const CgArgs &a, const void *in, float *out32
     __syncthreads();
     if (InD)
       plane_batched<double>(
-          N, [&](int y, int x) { return __ldcg((const double *)in + zo + y * N + x); },
+          N,
+          [&](int y, int x) {
+            return KS_IN(zo + y * N + x, a.n) ? __ldcg((const double *)in + zo + y * N + x) : 0.0;
+          },
           [&](int y, int x, double v) { Pm[y * ld + x] = (float)v; });
     else
       plane_batched<float>(
-          N, [&](int y, int x) { return __ldcg((const float *)in + zo + y * N + x); },
+          N,
+          [&](int y, int x) {
+            return KS_IN(zo + y * N + x, a.n) ? __ldcg((const float *)in + zo + y * N + x) : 0.f;
+          },
           [&](int y, int x, float v) { Pm[y * ld + x] = v; });
     plane_transform(N, ld, sh);
     if (OutD)
@@ -355,13 +363,15 @@ __device__ double fused_plane_pass(const CgArgs &a, const void *in, float *out32
           N, [&](int y, int x) { return __ldcg(a.r + zo + y * N + x); },
           [&](int y, int x, double rv) {
             const double zv = (double)Pm[y * ld + x];
-            out64[zo + y * N + x] = zv;
+            if (KS_IN(zo + y * N + x, a.n)) out64[zo + y * N + x] = zv;
             rz = fma(rv, zv, rz);
           });
     else
       plane_batched<float>(
           N, [&](int y, int x) { return Pm[y * ld + x]; },
-          [&](int y, int x, float v) { out32[zo + y * N + x] = v; });
+          [&](int y, int x, float v) {
+            if (KS_IN(zo + y * N + x, a.n)) out32[zo + y * N + x] = v;
+          });
   }
   return rz;
 }
@@ -375,7 +385,11 @@ __device__ void fused_slab_pass(const CgArgs &a, const float *in, float *out, fl
   for (int y = a.vb; y < N; y += a.vnb) {
     __syncthreads();
     plane_batched<float>(
-        N, [&](int zz, int x) { return __ldcg(in + zz * NN + (long long)y * N + x); },
+        N,
+        [&](int zz, int x) {
+          const long long k = zz * NN + (long long)y * N + x;
+          return KS_IN(k, a.n) ? __ldcg(in + k) : 0.f;
+        },
         [&](int zz, int x, float v) { Sm[zz * ld + x] = v; });
     __syncthreads();
     smem_matmul<false>(Ph, Sm, W, N, ld);   // forward along z
@@ -391,7 +405,10 @@ __device__ void fused_slab_pass(const CgArgs &a, const float *in, float *out, fl
     __syncthreads();
     plane_batched<float>(
         N, [&](int zz, int x) { return Sm[zz * ld + x]; },
-        [&](int zz, int x, float v) { out[zz * NN + (long long)y * N + x] = v; });
+        [&](int zz, int x, float v) {
+          const long long k = zz * NN + (long long)y * N + x;
+          if (KS_IN(k, a.n)) out[k] = v;
+        });
   }
 }
 
@@ -1010,5 +1027,7 @@ int cg_grid_blocks(int sms, int n, int N) {
   if (want < 1) want = 1;
   return (int)want;
 }
+
+KS_OOB_READER(cg)
 
 }  // namespace ks

@@ -99,8 +99,8 @@ __global__ void density_inc_warp_kernel(int n, int p, double occ, const float *_
         float vd[kDenRows], vx[kDenRows];
 #pragma unroll
         for (int u = 0; u < kDenRows; ++u) {
-          const bool ok = j0 + u < cnt;
           const long long idx = (k0 + j0 + u) * p + i;
+          const bool ok = j0 + u < cnt && KS_IN(idx, (long long)n * p);
           vd[u] = ok ? d[idx] : 0.f;
           vx[u] = ok ? xb[idx] : 0.f;
         }
@@ -185,5 +185,7 @@ template ks_status batch_density<float>(Batch &, int);
 
 template ks_status launch_density<double>(Problem &, const double *, double *);
 template ks_status launch_density<float>(Problem &, const float *, double *);
+
+KS_OOB_READER(density)
 
 }  // namespace ks

@@ -9,6 +9,48 @@
 
 namespace ks {
 
+// ---------------------------------------------------------------- bounds-checked build
+// Compiled with -DKS_DEBUG_BOUNDS, KS_IN(i, len) checks a computed index
+// before the access it guards: an index outside [0, len) is counted, with
+// the source line of the first one, in this translation unit's device
+// counters, and the guarded access is skipped, so the kernel runs on and the
+// host reads the record through ks_debug_bounds (no trap, no fault).
+// Without the macro KS_IN is `true` and costs nothing.
+#ifdef KS_DEBUG_BOUNDS
+namespace {
+__device__ unsigned long long oob_count;
+__device__ int oob_first_line;
+
+__device__ __noinline__ bool oob_note(int line) {
+  if (atomicAdd(&oob_count, 1ull) == 0ull) oob_first_line = line;
+  return false;
+}
+
+// this translation unit's record, then cleared
+[[maybe_unused]] void oob_collect(unsigned long long *count, int *line) {
+  unsigned long long c = 0;
+  int l = 0;
+  cudaDeviceSynchronize();
+  cudaMemcpyFromSymbol(&c, oob_count, sizeof(c));
+  cudaMemcpyFromSymbol(&l, oob_first_line, sizeof(l));
+  const unsigned long long zc = 0;
+  const int zl = 0;
+  cudaMemcpyToSymbol(oob_count, &zc, sizeof(zc));
+  cudaMemcpyToSymbol(oob_first_line, &zl, sizeof(zl));
+  *count = c;
+  *line = l;
+}
+}  // namespace
+#define KS_IN(i, len) \
+  ((unsigned long long)(long long)(i) < (unsigned long long)(long long)(len) ? true \
+                                                                            : ks::oob_note(__LINE__))
+#define KS_OOB_READER(name) \
+  void oob_read_##name(unsigned long long *c, int *l) { oob_collect(c, l); }
+#else
+#define KS_IN(i, len) true
+#define KS_OOB_READER(name)
+#endif
+
 __device__ __forceinline__ double ldcg(const double *p) { return __ldcg(p); }
 
 // Sum over a block of blockDim.x (a multiple of 32, <= 1024) threads in a

@@ -105,6 +105,8 @@ __device__ __forceinline__ void thomas_line_reg(long long t, int N, int p, int a
     stride = (long long)N * N;
   }
   const long long es = stride * p;
+  // the line's last entry lies inside the block
+  if (!KS_IN(base * p + i + (long long)(N - 1) * es, lines * N * p)) return;
   T v[kRegN];
   {
     const T *ps = in + base * p + i;
@@ -262,5 +264,7 @@ ks_status launch_mass_inverse(Problem &P, const T *E, T *G, const T *add) {
 template ks_status launch_mass_inverse<double>(Problem &, const double *, double *,
                                                const double *);
 template ks_status launch_mass_inverse<float>(Problem &, const float *, float *, const float *);
+
+KS_OOB_READER(minv)
 
 }  // namespace ks

@@ -159,3 +159,52 @@ const char *ks_profile_class_name(int cls) {
 }
 
 }  // extern "C"
+
+#ifdef KS_DEBUG_BOUNDS
+namespace ks {
+void oob_read_stencil(unsigned long long *, int *);
+void oob_read_blas(unsigned long long *, int *);
+void oob_read_density(unsigned long long *, int *);
+void oob_read_minv(unsigned long long *, int *);
+void oob_read_cg(unsigned long long *, int *);
+void oob_read_split(unsigned long long *, int *);
+void oob_read_tc(unsigned long long *, int *);
+}  // namespace ks
+#endif
+
+extern "C" int ks_debug_bounds(unsigned long long *count, const char **file, int *line) {
+  unsigned long long total = 0;
+  const char *first_file = nullptr;
+  int first_line = 0;
+#ifdef KS_DEBUG_BOUNDS
+  struct Reader {
+    const char *file;
+    void (*read)(unsigned long long *, int *);
+  };
+  const Reader readers[] = {{"ks_stencil.cu", ks::oob_read_stencil},
+                            {"ks_blas.cu", ks::oob_read_blas},
+                            {"ks_density.cu", ks::oob_read_density},
+                            {"ks_minv.cu", ks::oob_read_minv},
+                            {"ks_cg.cu", ks::oob_read_cg},
+                            {"ks_split.cu", ks::oob_read_split},
+                            {"ks_tc.cu", ks::oob_read_tc}};
+  for (const Reader &r : readers) {
+    unsigned long long c = 0;
+    int l = 0;
+    r.read(&c, &l);
+    if (c && !first_file) {
+      first_file = r.file;
+      first_line = l;
+    }
+    total += c;
+  }
+#endif
+  if (count) *count = total;
+  if (file) *file = first_file;
+  if (line) *line = first_line;
+#ifdef KS_DEBUG_BOUNDS
+  return 1;
+#else
+  return 0;
+#endif
+}

@@ -163,6 +163,7 @@ __global__ void __launch_bounds__(kDevThreads) qr_factor_dev_kernel(int p,
     const float il = 1.f / (1.f + gjj);
     const float hjj = -gjj * il;
     for (int i = j + 1 + threadIdx.x; i < p; i += kDevThreads) {
+      if (!KS_IN(i * ld + j, p * ld)) continue;
       const float g = G[i * ld + j] * il;
       G[i * ld + j] = g;
       colj[i] = g;
@@ -180,7 +181,7 @@ __global__ void __launch_bounds__(kDevThreads) qr_factor_dev_kernel(int p,
         const float gcj = c > j ? colj[c] : 0.f;
 #pragma unroll 4
         for (int i = r0; i < p; i += 4) {
-          if (c > i) continue;
+          if (c > i || !KS_IN(i * ld + c, p * ld)) continue;
           const float gij = colj[i];
           if (c > j) G[i * ld + c] = fmaf(-gij, gcj, G[i * ld + c]);
           else if (c < j) H[i * ld + c] = fmaf(-gij, hjc, H[i * ld + c]);
@@ -336,5 +337,7 @@ ks_status launch_add_identity(Problem &P, const double *A, double s, double *out
   KS_CUDA_TRY(cudaGetLastError());
   return KS_OK;
 }
+
+KS_OOB_READER(split)
 
 }  // namespace ks

@@ -161,7 +161,10 @@ __device__ __forceinline__ void stencil_plain_body(const StArgs &a, int vb) {
 #pragma unroll
     for (int r = 0; r < kStNodesPerThread; ++r) {
       const int hx = lx[r] + 1, hy = ly[r] + 1;
-      auto at = [&](int dx, int dy) { return tile[((hy + dy) * Tl::HX + hx + dx) * PC + lane]; };
+      auto at = [&](int dx, int dy) {
+        const int ti = ((hy + dy) * Tl::HX + hx + dx) * PC + lane;
+        return KS_IN(ti, kBox) ? tile[ti] : (T)0;
+      };
       c[r] = at(0, 0);
       f[r] = (at(-1, 0) + at(1, 0)) + (at(0, -1) + at(0, 1));
       e[r] = (at(-1, -1) + at(1, -1)) + (at(-1, 1) + at(1, 1));
@@ -191,7 +194,9 @@ __device__ __forceinline__ void stencil_plain_body(const StArgs &a, int vb) {
       const T faces = f_mid[r] + (c_old[r] + c_new[r]);
       const T edges = e_mid[r] + (f_old[r] + f_new[r]);
       const T corners = e_old[r] + e_new[r];
-      if (ovalid && gx < N && gy < N) {
+      const long long nodes = (long long)N * N * N;
+      if (ovalid && gx < N && gy < N && KS_IN(((long long)z * N + gy) * N + gx, nodes) &&
+          KS_IN((((long long)z * N + gy) * N + gx) * p + o, nodes * p)) {
         const long long k = ((long long)z * N + gy) * N + gx;
         const long long idx = k * p + o;
         const T m = m0 * centre + mf * faces + me * edges + mc * corners;
@@ -355,7 +360,8 @@ __global__ void __launch_bounds__(kStThreads, 2) stencil_tma_kernel(const __grid
   constexpr bool kHam = Kind == SK_HAM || Kind == SK_HAM_INC;
   const bool vown = kHam && (int)threadIdx.x < TXY && vx < N && vy < N;
   double vreg = 0.0, vbreg = 0.0;
-  if (vown && z0 >= 1) {
+  const long long nodes = (long long)N * N * N;
+  if (vown && z0 >= 1 && KS_IN(((long long)(z0 - 1) * N + vy) * N + vx, nodes)) {
     vreg = a.veff[((long long)(z0 - 1) * N + vy) * N + vx];
     if (Kind == SK_HAM_INC) vbreg = a.veff_b[((long long)(z0 - 1) * N + vy) * N + vx];
   }
@@ -376,7 +382,7 @@ __global__ void __launch_bounds__(kStThreads, 2) stencil_tma_kernel(const __grid
       }
       vreg = 0.0;
       vbreg = 0.0;
-      if (vown && zp + 1 < N) {
+      if (vown && zp + 1 < N && KS_IN(((long long)(zp + 1) * N + vy) * N + vx, nodes)) {
         vreg = a.veff[((long long)(zp + 1) * N + vy) * N + vx];
         if (Kind == SK_HAM_INC) vbreg = a.veff_b[((long long)(zp + 1) * N + vy) * N + vx];
       }
@@ -387,7 +393,10 @@ __global__ void __launch_bounds__(kStThreads, 2) stencil_tma_kernel(const __grid
 #pragma unroll
     for (int r = 0; r < kStNodesPerThread; ++r) {
       const int hx = lx[r] + 1, hy = ly[r] + 1;
-      auto at = [&](int dx, int dy) { return tile[((hy + dy) * Tl::HX + hx + dx) * PC + lane]; };
+      auto at = [&](int dx, int dy) {
+        const int ti = ((hy + dy) * Tl::HX + hx + dx) * PC + lane;
+        return KS_IN(ti, Rg::BOX) ? tile[ti] : (T)0;
+      };
       c_new[r] = at(0, 0);
       f_new[r] = (at(-1, 0) + at(1, 0)) + (at(0, -1) + at(0, 1));
       e_new[r] = (at(-1, -1) + at(1, -1)) + (at(-1, 1) + at(1, 1));
@@ -402,13 +411,17 @@ __global__ void __launch_bounds__(kStThreads, 2) stencil_tma_kernel(const __grid
         for (int i = 0; i < NAUX; ++i)
 #pragma unroll
           for (int r = 0; r < kStNodesPerThread; ++r)
-            bb[i][r] = tile[Rg::HALO + i * Rg::AUX + (ly[r] * Tl::TX + lx[r]) * PC + lane];
+          {
+            const int ti = (ly[r] * Tl::TX + lx[r]) * PC + lane;
+            bb[i][r] = KS_IN(ti, Rg::AUXB) ? tile[Rg::HALO + i * Rg::AUX + ti] : (T)0;
+          }
       } else if (Kind == SK_MASS_BB) {
         // all loads of the plane first, so they are in flight together
 #pragma unroll
         for (int r = 0; r < kStNodesPerThread; ++r) {
           const int gx = x0 + lx[r], gy = y0 + ly[r];
-          if (ovalid && gx < N && gy < N) {
+          if (ovalid && gx < N && gy < N &&
+              KS_IN((((long long)z * N + gy) * N + gx) * p + o, nodes * p)) {
             const long long idx = (((long long)z * N + gy) * N + gx) * p + o;
             bb[0][r] = ((const T *)a.X)[idx];
             bb[1][r] = ((const T *)a.MX)[idx];
@@ -426,7 +439,8 @@ __global__ void __launch_bounds__(kStThreads, 2) stencil_tma_kernel(const __grid
         const T faces = f_mid[r] + (c_old[r] + c_new[r]);
         const T edges = e_mid[r] + (f_old[r] + f_new[r]);
         const T corners = e_old[r] + e_new[r];
-        if (ovalid && gx < N && gy < N) {
+        if (ovalid && gx < N && gy < N && KS_IN(((long long)z * N + gy) * N + gx, nodes) &&
+            KS_IN((((long long)z * N + gy) * N + gx) * p + o, nodes * p)) {
           const long long k = ((long long)z * N + gy) * N + gx;
           const long long idx = k * p + o;
           const T m = cf.m0 * centre + cf.mf * faces + cf.me * edges + cf.mc * corners;
@@ -818,5 +832,7 @@ KS_BINST(float)
 KS_INST(double)
 KS_INST(float)
 #undef KS_INST
+
+KS_OOB_READER(stencil)
 
 }  // namespace ks

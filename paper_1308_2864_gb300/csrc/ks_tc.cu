@@ -675,13 +675,16 @@ __global__ void __launch_bounds__(kNThreads, 1) combine_tc64_kernel(
       float *out = ga.out, *out2 = ga.out2;
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
-        if (!live || c0 + 4 * j >= q) continue;
+        if (!live || c0 + 4 * j >= q || !KS_IN(row * q + c0 + 4 * j + 3, n * q)) continue;
         const float4 y = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
                                      __uint_as_float(v[4 * j + 2]),
                                      __uint_as_float(v[4 * j + 3]));
         *reinterpret_cast<float4 *>(out + row * q + c0 + 4 * j) = y;
         if (out2) {
-          const float4 a = *reinterpret_cast<const float4 *>(a3s + sw128_offset(rl, 4 * j));
+          const int ao = sw128_offset(rl, 4 * j);
+          const float4 a = KS_IN(ao + 12, kNTileBytes)
+                               ? *reinterpret_cast<const float4 *>(a3s + ao)
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
           *reinterpret_cast<float4 *>(out2 + row * q + c0 + 4 * j) =
               make_float4(a.x + y.x, a.y + y.y, a.z + y.z, a.w + y.w);
           if (ga.rho) {
@@ -856,5 +859,7 @@ ks_status launch_combine_tc64(Problem &P, int q, const float *A1, int k1, const 
   KS_CUDA_TRY(cudaGetLastError());
   return KS_OK;
 }
+
+KS_OOB_READER(tc)
 
 }  // namespace ks

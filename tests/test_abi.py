@@ -9,7 +9,7 @@ import paper_1308_2864_gb300 as ks
 from paper_1308_2864_gb300 import build as kbuild
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-DECL = re.compile(r"^\s*(?:ks_status|size_t|void|unsigned long long|const char\s*\*)\s*\**\s*(ks_\w+)\s*\(", re.M)
+DECL = re.compile(r"^\s*(?:ks_status|size_t|void|int|unsigned long long|const char\s*\*)\s*\**\s*(ks_\w+)\s*\(", re.M)
 
 
 def declared_functions():
