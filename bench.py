@@ -53,11 +53,19 @@ GTOL = 1e-6
 # deterministic (fixed reduction orders), so these set the segment length of
 # the timed solve and the oracle's extrapolated solve.
 C2_ITERS_MIXED = 100305
-C2_ITERS_FP64 = 99874
+C2_ITERS_FP64 = 93799
 # jobs of the batched-jobs recipe (seed 1003) that reach ||D||_M <= 1e-6 in
 # a few thousand iterations
 C4_TTS_JOBS = (1, 2, 4, 5)
 MAXIT = 400000
+# DRAM bytes (read + write) per launch of a class's kernel, from one ncu
+# capture of the current kernels on this workload (profiles/c2_mixed_kernels_ncu.md):
+# the update's two launches of an iteration, 201 + 43 MB (D) and 212 + 97 MB
+# (retraction), averaged.  To be retaken whenever the kernel changes.
+CLASS_TRAFFIC = {
+    "combine": (276.6e6, "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of "
+                         "combine_ta_kernel, mean of its two launches per iteration"),
+}
 GOLDEN_C1 = os.path.join(ROOT, "tests", "golden", "c1_converged.json")
 
 
@@ -261,8 +269,11 @@ def roofline(prof, clocks, peaks) -> dict:
                 "frac": achieved / hbm,
                 "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)" if mp else
                                "of fallback (6.8 TB/s)"}
+    traffic = CLASS_TRAFFIC.get(name)
     roof.update({"kernel": f"{name} (class of the timed solve)", "launches": dcnt,
-                 "ms": dms, "traffic": None})
+                 "ms": dms, "traffic": traffic[0] if traffic else None})
+    if traffic:
+        roof["traffic_source"] = traffic[1]
     return roof
 
 

@@ -815,9 +815,9 @@ __device__ __forceinline__ void ts_epilogue(long long n, int q, long long row0, 
   for (int i = 0; i < 8; ++i) {
     const long long row = row0 + i;
     float dsum = 0.f;
-    if (row < n && KS_IN(row * q + col0, n * q)) {
+    if (row < n) {
       const long long o = row * q + col0;
-      if (vec) {
+      if (vec && KS_IN(o + 3, n * q)) {
         float4 v = make_float4(alpha * acc[i][0], alpha * acc[i][1], alpha * acc[i][2],
                                alpha * acc[i][3]);
         if (Bm) {
@@ -840,7 +840,7 @@ __device__ __forceinline__ void ts_epilogue(long long n, int q, long long row0, 
       } else {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          if (col0 + j < q) {
+          if (col0 + j < q && KS_IN(o + j, n * q)) {
             float v = alpha * acc[i][j];
             if (Bm) v = fmaf(beta, Bm[o + j], v);
             out[o + j] = v;

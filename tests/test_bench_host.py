@@ -82,8 +82,11 @@ def test_roofline_of_the_dominant_class():
     assert r["achieved"] == pytest.approx(2.0e12 / 0.05 / 1e12)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
     assert r["frac_of_probe"] == pytest.approx(r["achieved"] / 78.0)
+    # the class's DRAM traffic per launch comes from an ncu capture of its kernel
+    assert r["traffic"] == bench.CLASS_TRAFFIC["combine"][0] and r["traffic_source"]
     # a stencil class dominates: HBM bound in GB/s
     prof = {"combine": (5.0, 10, 2.0e11, 1.0e9), "hamiltonian": (20.0, 40, 1e9, 4.0e10)}
     r = bench.roofline(prof, clocks, peaks)
     assert r["bound"] == "hbm" and r["unit"] == "GB/s"
     assert r["achieved"] == pytest.approx(4.0e10 / 0.02 / 1e9)
+    assert r["traffic"] is None
