@@ -176,9 +176,9 @@ ks_status ks_probe_fma(int fp64, int blocks, int iters, void *stream, double *si
  *   stream  cudaStream_t to issue on (NULL = legacy default stream)
  * Requires pa * qb <= 2^21 (returns KS_EINVAL otherwise).  The first call on a
  * device looks up the array's device address for that device (with it
- * current) and keeps it for the life of the process; make that first call
- * before any stream capture, and do not use this entry point after a
- * cudaDeviceReset in the same process (the kept address would be stale).
+ * current, a runtime query besides the launches) and keeps it for the life
+ * of the process; do not use this entry point after a cudaDeviceReset in the
+ * same process (the kept address would be stale).
  * The call only enqueues work: the result is ready when `stream` reaches it.
  * All calls in the process share the one array and every call overwrites all
  * of it that it reads, so calls whose executions overlap on the GPU (for
