@@ -427,26 +427,37 @@ __global__ void __launch_bounds__(kTcThreads, 1) combine_tc_kernel(
 // per SM walks its 128-row tiles.  Each operand's columns are cut into
 // stages of 32 (the last one zero-filled past k_i); a stage (128 rows x 128
 // bytes) arrives by one TMA tile load in the 128-byte-swizzled K-major
-// layout the MMA reads, into a ring of kNRaw buffers kNRaw - 1 stages
-// ahead.  All threads split it elementwise into TF32 high and low parts
-// (x = hi + lo, hi rounded to nearest; same layout) in one of two split
-// buffers, and one thread issues hi.hi + hi.lo + lo.hi (3 x 4 MMAs of
-// 128 x 64 x 8, about 2^-21 relative error per product) into a 64-column
-// FP32 accumulator in tensor memory.  The coefficients' image (hi and lo of
-// every stage, scaled, a null C_i standing for the identity so that a whole
-// matrix can be added) stays in shared memory for the launch; A3 for out2
-// is read back from the ring's last stages, so the epilogue makes no global
-// loads.  Every wait is bounded; a block that gives up records KS_ETIMEOUT,
-// waits for its copies and MMAs and stops.
+// layout the MMA reads.  The block's warps take one role each and hand
+// stages on through mbarriers, never a block barrier: one thread issues the
+// copies into a ring of kNRaw slots; four warps split each landed stage
+// elementwise into TF32 high and low parts (x = hi + lo, hi rounded to
+// nearest; hi in place, lo into one of kNLo buffers, same layout); one
+// thread issues hi.hi + hi.lo + lo.hi (3 x 4 MMAs of 128 x 64 x 8, about
+// 2^-21 relative error per product) into one of two 64-column FP32
+// accumulators in tensor memory, and its commits release the slot and the
+// lo buffer; four warps read a finished tile's accumulator (one row per
+// thread) and write it out while the MMAs of the next tile run into the
+// other.  The coefficients' image (hi and lo of every stage, scaled, a null
+// C_i standing for the identity so that a whole matrix can be added) stays
+// in shared memory for the launch; A3 for out2 is read back from global
+// memory (the tile's copy is still in L2).  Every wait is bounded; a role
+// that gives up sets the block's abort flag, the others stop at their next
+// wait, the block waits for its copies and MMAs in flight and records
+// KS_ETIMEOUT.
 constexpr int kNM = 128, kNN = 64, kNK = 32;     // tile rows, columns, K per stage
-constexpr int kNThreads = 256;
-constexpr int kNRaw = 4;                         // ring of A stages
+constexpr int kNEpiWarps = 4, kNSplitWarps = 4;  // warps 0-3 epilogue, 4-7 split
+constexpr int kNProdWarp = 8, kNMmaWarp = 9;     // copies, MMAs (one thread each)
+constexpr int kNThreads = 320;
+constexpr int kNEpiThreads = 32 * kNEpiWarps, kNSplitThreads = 32 * kNSplitWarps;
+constexpr int kNRaw = 6;                         // ring of A stages (raw, then hi in place)
+constexpr int kNLo = 2;                          // lo buffers
 constexpr int kNTileBytes = kNM * kNK * 4;       // 16 KiB: one A stage (raw, hi or lo)
 constexpr int kNImgBytes = 2 * kNN * kNK * 4;    // 16 KiB: hi + lo of one coefficient stage
 constexpr int kNMaxStages = 6;                   // K (padded per operand) <= 192
-constexpr int kNCols = 64;                       // tensor-memory columns
-constexpr size_t kNSmem = (size_t)kNMaxStages * kNImgBytes + (size_t)kNRaw * kNTileBytes +
-                          (size_t)4 * kNTileBytes + 1024;
+constexpr int kNCols = 2 * kNN;                  // tensor-memory columns: two accumulators
+constexpr size_t kNSmem = (size_t)kNMaxStages * kNImgBytes +
+                          (size_t)(kNRaw + kNLo) * kNTileBytes + 1024;
+static_assert(kNTileBytes % (16 * kNSplitThreads) == 0, "split share");
 constexpr uint32_t kIdescN64 = (1u << 4) | (2u << 7) | (2u << 10) |
                                ((uint32_t)(kNN >> 3) << 17) | ((uint32_t)(kNM >> 4) << 24);
 
@@ -456,6 +467,7 @@ struct Tc64Args {
   int q, stages;
   int st_end[3];               // cumulative stage counts of the operands
   const float *img;
+  const float *a3;             // A3 (n x q) for out2
   float *out, *out2;
   const double *rho_b;
   double *rho;
@@ -548,20 +560,71 @@ __global__ void combine_image64_kernel(int q, Img64 im, int stages, float *__res
   *(float *)(base + kNImgBytes / 2 + off) = lo;
 }
 
+// Bounded wait on a phase of an mbarrier that also gives up once another
+// role of the block has set *abort; a wait that runs out sets it.
+__device__ __forceinline__ bool role_wait(uint64_t *bar, uint32_t parity, volatile int *abort) {
+  const uint32_t a = smem_u32(bar);
+  for (long long spins = 0; spins < kSpinLimit; ++spins) {
+    uint32_t done;
+    asm volatile("{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n"
+                 "selp.u32 %0, 1, 0, q;\n}\n"
+                 : "=r"(done) : "r"(a), "r"(parity) : "memory");
+    if (done) return true;
+    if (*abort) return false;
+  }
+  *abort = 1;
+  return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(bar)) : "memory");
+}
+
+// Epilogue of 32 accumulator columns c0 .. c0 + 31 of one row: out, and with
+// out2 the sum A3 + out and the row's share of the density, returned.
+__device__ __forceinline__ float narrow_epilogue(const Tc64Args &ga, const uint32_t (&v)[32],
+                                                 long long row, int c0) {
+  const int q = ga.q;
+  float dsum = 0.f;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int c = c0 + 4 * j;
+    if (c >= q || !KS_IN(row * q + c + 3, ga.n * q)) continue;
+    const float4 y = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
+                                 __uint_as_float(v[4 * j + 2]), __uint_as_float(v[4 * j + 3]));
+    *reinterpret_cast<float4 *>(ga.out + row * q + c) = y;
+    if (ga.out2) {
+      const float4 a = *reinterpret_cast<const float4 *>(ga.a3 + row * q + c);
+      *reinterpret_cast<float4 *>(ga.out2 + row * q + c) =
+          make_float4(a.x + y.x, a.y + y.y, a.z + y.z, a.w + y.w);
+      if (ga.rho) {
+        dsum = fmaf(y.x, fmaf(2.f, a.x, y.x), dsum);
+        dsum = fmaf(y.y, fmaf(2.f, a.y, y.y), dsum);
+        dsum = fmaf(y.z, fmaf(2.f, a.z, y.z), dsum);
+        dsum = fmaf(y.w, fmaf(2.f, a.w, y.w), dsum);
+      }
+    }
+  }
+  return dsum;
+}
+
 __global__ void __launch_bounds__(kNThreads, 1) combine_tc64_kernel(
     const __grid_constant__ Tc64Args ga) {
   extern __shared__ __align__(1024) unsigned char dyn_raw[];
   unsigned char *smem = (unsigned char *)(((uintptr_t)dyn_raw + 1023) & ~(uintptr_t)1023);
   unsigned char *Bs = smem;                                       // coefficient image
-  unsigned char *Raw = Bs + (size_t)kNMaxStages * kNImgBytes;     // A ring
-  unsigned char *HL = Raw + (size_t)kNRaw * kNTileBytes;          // 2 x (hi, lo)
-  __shared__ __align__(8) uint64_t mbar[2];                       // MMAs of a split buffer done
-  __shared__ __align__(8) uint64_t full[kNRaw];                   // ring stage landed
+  unsigned char *Ring = Bs + (size_t)kNMaxStages * kNImgBytes;    // A stages, hi in place
+  unsigned char *Lo = Ring + (size_t)kNRaw * kNTileBytes;         // lo parts
+  __shared__ __align__(8) uint64_t full[kNRaw];        // stage landed
+  __shared__ __align__(8) uint64_t ready[kNRaw];       // stage split (kNSplitThreads arrivals)
+  __shared__ __align__(8) uint64_t slot_free[kNRaw];   // stage's MMAs done: ring slot free
+  __shared__ __align__(8) uint64_t lo_free[kNLo];      // stage's MMAs done: lo buffer free
+  __shared__ __align__(8) uint64_t acc_full[2];        // tile's MMAs done
+  __shared__ __align__(8) uint64_t acc_empty[2];       // tile's accumulator read
   __shared__ uint32_t tmem_slot;
-  __shared__ float dens[kNM];
+  __shared__ int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int stages = ga.stages, q = ga.q;
-  const long long n = ga.n;
+  const int stages = ga.stages;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                  :: "r"(smem_u32(&tmem_slot)), "r"(kNCols));
@@ -570,153 +633,148 @@ __global__ void __launch_bounds__(kNThreads, 1) combine_tc64_kernel(
   if (tid == 0) {
     for (int i = 0; i < 3; ++i)
       if (ga.st_end[i] > (i > 0 ? ga.st_end[i - 1] : 0)) prefetch_tensor_map(&ga.map[i]);
-    mbar_init(&mbar[0], 1);
-    mbar_init(&mbar[1], 1);
-    for (int b = 0; b < kNRaw; ++b) mbar_init(&full[b], 1);
+    for (int b = 0; b < kNRaw; ++b) {
+      mbar_init(&full[b], 1);
+      mbar_init(&ready[b], kNSplitThreads);
+      mbar_init(&slot_free[b], 1);
+    }
+    for (int b = 0; b < kNLo; ++b) mbar_init(&lo_free[b], 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], kNEpiThreads);
+    }
+    abort_flag = 0;
     fence_barrier_init();
   }
+  // the coefficient image, once, made visible to the MMAs' reads
+  for (int o = tid * 16; o < stages * kNImgBytes; o += kNThreads * 16)
+    cp_async16_zf(Bs + o, (const unsigned char *)ga.img + o, 16u);
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_slot;
-
-  // the coefficient image, once
-  for (int o = tid * 16; o < stages * kNImgBytes; o += kNThreads * 16)
-    cp_async16_zf(Bs + o, (const unsigned char *)ga.img + o, 16u);
-  asm volatile("cp.async.commit_group;" ::: "memory");
+  volatile int *abort = &abort_flag;
   const long long mine =
       ga.ntiles > blockIdx.x ? (ga.ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
   const long long W = mine * stages;
-  // stage w of this block: one TMA tile of operand i at column 32 j, rows
-  // of tile (thread 0 only)
-  auto issue = [&](long long w) {
-    if (w >= W) return;
-    const long long tile = blockIdx.x + (w / stages) * gridDim.x;
-    const int st = (int)(w % stages);
-    const int i = st < ga.st_end[0] ? 0 : st < ga.st_end[1] ? 1 : 2;
-    const int j = st - (i > 0 ? ga.st_end[i - 1] : 0);
-    uint64_t *bar = &full[w % kNRaw];
-    mbar_arrive_expect_tx(bar, (uint32_t)kNTileBytes);
-    tma_load_2d(Raw + (size_t)(w % kNRaw) * kNTileBytes, &ga.map[i], bar, j * kNK,
-                (int)(tile * kNM));
-  };
-  if (tid == 0)
-    for (int st = 0; st < kNRaw - 1; ++st) issue(st);
-  asm volatile("cp.async.wait_all;" ::: "memory");
-  bool failed = false;
-  long long last = -1;                       // last stage whose MMAs were committed
-  long long issued_to = kNRaw - 1;           // stages below this were issued
-  for (long long w = 0; w < W; ++w) {
-    const int s = (int)(w % stages);
-    const bool tile_end = s == stages - 1;
-    // the buffer of stage w - 1 is free (its split ended before the last
-    // barrier): refill it, except at a tile's end, whose epilogue still
-    // reads the last stages (A3)
-    if (tid == 0 && !tile_end) issue(w + kNRaw - 1);
-    if (!tile_end) issued_to = w + kNRaw;
-    int ok = mbar_wait_parity(&full[w % kNRaw], (uint32_t)((w / kNRaw) & 1)) ? 1 : 0;
-    const int sb = (int)(w & 1);
-    unsigned char *Hs = HL + (size_t)sb * 2 * kNTileBytes, *Ls = Hs + kNTileBytes;
-    if (ok && w >= 2) ok = mbar_wait(smem_u32(&mbar[sb]), (uint32_t)(((w - 2) >> 1) & 1)) ? 1 : 0;
-    if (!__syncthreads_and(ok)) {
-      failed = true;
-      break;
-    }
-    const unsigned char *raw = Raw + (size_t)(w % kNRaw) * kNTileBytes;
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const int o = (tid + t * kNThreads) * 16;
-      const float4 x = *reinterpret_cast<const float4 *>(raw + o);
-      float4 h, l;
-      split_rn(x.x, h.x, l.x); split_rn(x.y, h.y, l.y);
-      split_rn(x.z, h.z, l.z); split_rn(x.w, h.w, l.w);
-      *reinterpret_cast<float4 *>(Hs + o) = h;
-      *reinterpret_cast<float4 *>(Ls + o) = l;
-    }
-    asm volatile("fence.proxy.async.shared::cta;");
-    __syncthreads();
-    if (tid == 0) {
+  long long issued = 0;                      // producer: stages whose copy was issued
+
+  if (warp < kNEpiWarps) {
+    // epilogue: thread = one row of the tile (its warp's quarter of the
+    // accumulator lanes), all q columns
+    const int rl = 32 * warp + lane;
+    for (long long t = 0; t < mine; ++t) {
+      const int b = (int)(t & 1);
+      const bool ok = role_wait(&acc_full[b], (uint32_t)((t >> 1) & 1), abort);
+      if (!__all_sync(0xffffffffu, ok)) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t ah = smem_u32(Hs), al = smem_u32(Ls);
-      const uint32_t bh = smem_u32(Bs + (size_t)s * kNImgBytes), bl = bh + kNImgBytes / 2;
-#pragma unroll
-      for (int ks = 0; ks < kNK / 8; ++ks) {
-        const uint32_t o = ks * 32;
-        mma_tf32_n64(tmem, smem_desc_sw128(ah + o), smem_desc_sw128(bh + o),
-                     (s > 0 || ks > 0) ? 1u : 0u);
-        mma_tf32_n64(tmem, smem_desc_sw128(ah + o), smem_desc_sw128(bl + o), 1u);
-        mma_tf32_n64(tmem, smem_desc_sw128(al + o), smem_desc_sw128(bh + o), 1u);
-      }
-      commit(&mbar[sb]);
-    }
-    last = w;
-    if (tile_end) {
-      // epilogue: thread = one row (lane quarter warp & 3) and 32 columns
-      // (half warp >> 2); A3 (out2) from the ring's last stages
-      const long long tile = blockIdx.x + (w / stages) * gridDim.x;
-      const int rl = 32 * (warp & 3) + lane;
-      const long long row = tile * kNM + rl;
-      const int c0 = 32 * (warp >> 2);
-      const bool live = row < n && c0 < q;
-      ok = mbar_wait(smem_u32(&mbar[sb]), (uint32_t)((w >> 1) & 1)) ? 1 : 0;
-      if (!__syncthreads_and(ok)) {
-        failed = true;
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      uint32_t v[32];
-      tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c0, v);
-      // columns c0 .. c0 + 31 of A3 fill stage stages - nst3 + c0 / 32
-      const int nst3 = ga.st_end[2] - ga.st_end[1];
-      const int sa = stages - nst3 + c0 / kNK;
-      const unsigned char *a3s =
-          Raw + (size_t)((w - (stages - 1 - sa)) % kNRaw) * kNTileBytes;
-      float dsum = 0.f;
-      float *out = ga.out, *out2 = ga.out2;
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        if (!live || c0 + 4 * j >= q || !KS_IN(row * q + c0 + 4 * j + 3, n * q)) continue;
-        const float4 y = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
-                                     __uint_as_float(v[4 * j + 2]),
-                                     __uint_as_float(v[4 * j + 3]));
-        *reinterpret_cast<float4 *>(out + row * q + c0 + 4 * j) = y;
-        if (out2) {
-          const int ao = sw128_offset(rl, 4 * j);
-          const float4 a = KS_IN(ao + 12, kNTileBytes)
-                               ? *reinterpret_cast<const float4 *>(a3s + ao)
-                               : make_float4(0.f, 0.f, 0.f, 0.f);
-          *reinterpret_cast<float4 *>(out2 + row * q + c0 + 4 * j) =
-              make_float4(a.x + y.x, a.y + y.y, a.z + y.z, a.w + y.w);
-          if (ga.rho) {
-            dsum = fmaf(y.x, fmaf(2.f, a.x, y.x), dsum);
-            dsum = fmaf(y.y, fmaf(2.f, a.y, y.y), dsum);
-            dsum = fmaf(y.z, fmaf(2.f, a.z, y.z), dsum);
-            dsum = fmaf(y.w, fmaf(2.f, a.w, y.w), dsum);
-          }
-        }
-      }
-      if (ga.rho) {
-        if (warp >= 4) dens[rl] = dsum;
-        __syncthreads();
-        if (warp < 4 && row < n) ga.rho[row] = ga.rho_b[row] + ga.occ * (double)(dsum + dens[rl]);
-      }
-      // every warp has read the accumulator and the ring before the next
-      // tile's MMAs and copies overwrite them
+      uint32_t v0[32], v1[32];
+      const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(b * kNN);
+      tmem_ld32(ta, v0);
+      tmem_ld32(ta + 32, v1);
       asm volatile("tcgen05.fence::before_thread_sync;");
-      __syncthreads();
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      if (tid == 0) issue(w + kNRaw - 1);
-      issued_to = w + kNRaw;
+      mbar_arrive(&acc_empty[b]);            // the MMAs of tile t + 2 may overwrite it
+      const long long row = (blockIdx.x + t * gridDim.x) * kNM + rl;
+      if (row < ga.n) {
+        const float d0 = narrow_epilogue(ga, v0, row, 0);
+        const float d1 = narrow_epilogue(ga, v1, row, 32);
+        if (ga.rho) ga.rho[row] = ga.rho_b[row] + ga.occ * (double)(d0 + d1);
+      }
     }
+  } else if (warp < kNEpiWarps + kNSplitWarps) {
+    // split: x = hi + lo of each landed stage, hi in place in its ring
+    // slot, lo into the stage's lo buffer once the MMAs that read it before
+    // are done
+    const int st = tid - kNEpiThreads;
+    for (long long v = 0; v < W; ++v) {
+      const int slot = (int)(v % kNRaw), lb = (int)(v % kNLo);
+      if (v >= kNLo && !role_wait(&lo_free[lb], (uint32_t)((v / kNLo - 1) & 1), abort)) break;
+      if (!role_wait(&full[slot], (uint32_t)((v / kNRaw) & 1), abort)) break;
+      unsigned char *H = Ring + (size_t)slot * kNTileBytes, *L = Lo + (size_t)lb * kNTileBytes;
+#pragma unroll
+      for (int t = 0; t < kNTileBytes / 16 / kNSplitThreads; ++t) {
+        const int o = (st + t * kNSplitThreads) * 16;
+        if (!KS_IN(o + 15, kNTileBytes)) continue;
+        const float4 x = *reinterpret_cast<const float4 *>(H + o);
+        float4 h, l;
+        split_rn(x.x, h.x, l.x); split_rn(x.y, h.y, l.y);
+        split_rn(x.z, h.z, l.z); split_rn(x.w, h.w, l.w);
+        *reinterpret_cast<float4 *>(H + o) = h;
+        *reinterpret_cast<float4 *>(L + o) = l;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(&ready[slot]);
+    }
+  } else if (warp == kNProdWarp) {
+    // copies: stage v = one TMA tile of operand i at column 32 j, rows of
+    // the tile, into ring slot v % kNRaw once the MMAs of stage v - kNRaw
+    // have released it
+    if (lane == 0) {
+      for (long long v = 0; v < W; ++v) {
+        const int slot = (int)(v % kNRaw);
+        if (v >= kNRaw &&
+            !role_wait(&slot_free[slot], (uint32_t)((v / kNRaw - 1) & 1), abort))
+          break;
+        const long long tile = blockIdx.x + (v / stages) * gridDim.x;
+        const int s = (int)(v % stages);
+        const int i = s < ga.st_end[0] ? 0 : s < ga.st_end[1] ? 1 : 2;
+        const int j = s - (i > 0 ? ga.st_end[i - 1] : 0);
+        mbar_arrive_expect_tx(&full[slot], (uint32_t)kNTileBytes);
+        tma_load_2d(Ring + (size_t)slot * kNTileBytes, &ga.map[i], &full[slot], j * kNK,
+                    (int)(tile * kNM));
+        issued = v + 1;
+      }
+    }
+    __syncwarp();
+  } else if (warp == kNMmaWarp) {
+    // MMAs: hi.hi + hi.lo + lo.hi of each split stage into the tile's
+    // accumulator (two alternate, so the epilogue of tile t overlaps the
+    // MMAs of tile t + 1)
+    if (lane == 0) {
+      long long v = 0;
+      for (; v < W; ++v) {
+        const long long t = v / stages;
+        const int s = (int)(v % stages), b = (int)(t & 1);
+        const int slot = (int)(v % kNRaw), lb = (int)(v % kNLo);
+        if (s == 0 && t >= 2 &&
+            !role_wait(&acc_empty[b], (uint32_t)((t / 2 - 1) & 1), abort))
+          break;
+        if (!role_wait(&ready[slot], (uint32_t)((v / kNRaw) & 1), abort)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t ah = smem_u32(Ring + (size_t)slot * kNTileBytes);
+        const uint32_t al = smem_u32(Lo + (size_t)lb * kNTileBytes);
+        const uint32_t bh = smem_u32(Bs + (size_t)s * kNImgBytes), bl = bh + kNImgBytes / 2;
+        const uint32_t d = tmem + (uint32_t)(b * kNN);
+#pragma unroll
+        for (int ks = 0; ks < kNK / 8; ++ks) {
+          const uint32_t o = ks * 32;
+          mma_tf32_n64(d, smem_desc_sw128(ah + o), smem_desc_sw128(bh + o),
+                       (s > 0 || ks > 0) ? 1u : 0u);
+          mma_tf32_n64(d, smem_desc_sw128(ah + o), smem_desc_sw128(bl + o), 1u);
+          mma_tf32_n64(d, smem_desc_sw128(al + o), smem_desc_sw128(bh + o), 1u);
+        }
+        // slot_free last: its arrival means the others have arrived
+        if (s == stages - 1) commit(&acc_full[b]);
+        commit(&lo_free[lb]);
+        commit(&slot_free[slot]);
+      }
+      // this thread's MMAs still running read the ring: wait for the last
+      // (bounded, whatever the flag says)
+      if (v > 0) mbar_wait_parity(&slot_free[(v - 1) % kNRaw], (uint32_t)(((v - 1) / kNRaw) & 1));
+    }
+    __syncwarp();
   }
-  if (failed && tid == 0) {
-    atomicCAS(ga.status, 0, (int)KS_ETIMEOUT);
-    // the copies and MMAs still in flight write the ring and read the split
-    // buffers: wait for them (bounded)
-    for (long long v = last + 1; v < issued_to && v < W; ++v)
-      mbar_wait_parity(&full[v % kNRaw], (uint32_t)((v / kNRaw) & 1));
-    for (long long v = last - 1; v <= last; ++v)
-      if (v >= 0) mbar_wait(smem_u32(&mbar[v & 1]), (uint32_t)((v >> 1) & 1));
+  __syncthreads();
+  if (*abort) {
+    if (tid == 0) atomicCAS(ga.status, 0, (int)KS_ETIMEOUT);
+    // copies still in flight write the ring: wait for the last use of each
+    // slot (bounded)
+    if (warp == kNProdWarp && lane == 0)
+      for (long long u = issued > kNRaw ? issued - kNRaw : 0; u < issued; ++u)
+        mbar_wait_parity(&full[u % kNRaw], (uint32_t)((u / kNRaw) & 1));
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -828,9 +886,11 @@ ks_status launch_combine_tc64(Problem &P, int q, const float *A1, int k1, const 
   if (stages < 1 || stages > kNMaxStages ||
       (size_t)stages * kNImgBytes / sizeof(float) > P.tc_img_len)
     return set_error(KS_EINVAL, "combine_tc64: K above the image");
-  // out2 = A3 + out reads A3 from the ring's last stages
+  // out2 = A3 + out reads A3 back row by row
   if (out2 && (k[2] != q || k[2] == 0))
     return set_error(KS_EINVAL, "combine_tc64: out2 needs A3 with q columns");
+  if (out2 && (const void *)out == (const void *)A3)
+    return set_error(KS_EINVAL, "combine_tc64: out must not alias A3 when out2 is formed");
   {
     ProfScope ps_(P.stream, KP_REDUCE);
     const int elems = stages * kNN * kNK;
@@ -842,6 +902,7 @@ ks_status launch_combine_tc64(Problem &P, int q, const float *A1, int k1, const 
   ga.q = q;
   ga.stages = stages;
   ga.img = P.tc_img;
+  ga.a3 = A3;
   ga.out = out;
   ga.out2 = out2;
   ga.rho_b = rho_b;
