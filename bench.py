@@ -483,6 +483,16 @@ def run_gpu(args):
         t, rr = iteration_rate(P, X, X0, {**opts, "gtol": 1e-12}, 30, stream)
         rates[name] = {"ms_per_iteration": t}
     P.set_fp64_emulation(1)
+    # the mixed form with its narrow updates on the tensor cores (mode 3)
+    try:
+        P.set_tensor_cores(3)
+        t, rr = iteration_rate(P, X, X0, {"retraction": "qr", "precision": "mixed",
+                                          "stall_iters": 0, "gtol": 1e-12}, 30, stream)
+        rates["mixed_tensor_core_updates"] = {"ms_per_iteration": t}
+    except ks.KSError as e:  # reported in the line rather than losing the run
+        rates["mixed_tensor_core_updates"] = {"error": str(e)[:300]}
+    finally:
+        P.set_tensor_cores(1)
 
     # end to end through the host entry point: X0 from pinned host memory in,
     # the final block back out, one complete solve

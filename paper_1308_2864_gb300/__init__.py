@@ -528,7 +528,8 @@ class Problem:
         return out
 
     def set_tensor_cores(self, mode: int):
-        """FP32-phase tensor cores: 0 never, 1 wide products (default), 2 always."""
+        """FP32-phase tensor cores: 0 never, 1 wide products (default), 2 always,
+        3 wide products and the narrow updates (q <= 64, warp-specialised)."""
         _check(load_library().ks_set_tensor_cores(self._h, mode))
 
     def set_fp64_emulation(self, mode: int):
