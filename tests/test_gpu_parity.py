@@ -422,14 +422,16 @@ def test_fp32_gram_tensor_cores(shape, tc):
 
 
 @pytest.mark.parametrize("shape", [(13, 70, 70), (16, 64, 64), (9, 40, 33), (11, 12, 20),
-                                   (9, 300, 300), (12, 4, 8)])
+                                   (9, 300, 300), (12, 4, 8), (40, 64, 64)])
 @pytest.mark.parametrize("tc", [0, 2, 3], ids=["fp32-pipes", "tensor-cores", "narrow-tc"])
 def test_fp32_update_tensor_cores(shape, tc):
     # FP32 update X C1 + D C2 of the mixed phase (tensor cores for q > 32,
     # one thread per entry below; with tc = 3 the narrow form, q <= 64 and
-    # widths a multiple of 4, takes the three terms as TMA stages through a
-    # ring that holds four stages ahead), against the exact FP64 result of
-    # the same FP32 inputs and the FP64 C matrices.
+    # widths a multiple of 4, takes the three terms as TMA stages of 128
+    # rows, and a block accumulates its tiles in two alternating tensor-
+    # memory accumulators: n = 40^3 gives 500 tiles, several per block),
+    # against the exact FP64 result of the same FP32 inputs and the FP64 C
+    # matrices.
     N, k, q = shape
     s = ki.small_system(N=N, L=7.0, natoms=2, p=max(k, q), Z=4.0, seed=4)
     P = make(s)
