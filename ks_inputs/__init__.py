@@ -43,6 +43,7 @@ STREAM_ATOMS = 0
 STREAM_X0 = 1
 STREAM_JOBSIZE = 2
 STREAM_ARRIVALS = 3
+STREAM_SUBSAMPLE = 4
 
 
 def _mix64(z: int) -> int:
@@ -232,6 +233,21 @@ def poisson_arrivals(seed: int, njobs: int, rate: float) -> np.ndarray:
     cumulative exponential gaps -ln(1-u)/rate from the arrivals stream."""
     u = uniform_block(stream_key(seed, 0, STREAM_ARRIVALS), njobs)
     return np.cumsum(-np.log1p(-u) / rate)
+
+
+def stream_subsample(k: int, njobs: int = 512, seed: int = 1004) -> list[int]:
+    """k distinct indices of a stream of njobs jobs, in increasing order: a
+    seeded partial Fisher-Yates shuffle (swap position i with a uniform pick
+    among i .. njobs - 1, for i < k).  The jobs a slower form runs in place
+    of the whole stream; k >= njobs gives every index."""
+    if k >= njobs:
+        return list(range(njobs))
+    idx = list(range(njobs))
+    rng = SplitMix64(stream_key(seed, 0, STREAM_SUBSAMPLE))
+    for i in range(max(k, 0)):
+        j = i + int(rng.uniform() * (njobs - i))
+        idx[i], idx[j] = idx[j], idx[i]
+    return sorted(idx[:max(k, 0)])
 
 
 def small_system(N: int = 6, L: float = 6.0, natoms: int = 1, p: int = 2,
